@@ -1,0 +1,255 @@
+"""Periodized sums (oracle, FP64): Sec. 4.2 and Sec. 6.1-6.2.
+
+The periodic single-layer traction at a target is split (Eq. GperDecomp,
+Eq. Stsplit) into
+  * a NEAR image sum of free-space kernels over the 3 x 3 block of lattice
+    translates m e1 + n e2, m, n in {-1, 0, 1}, of every source, and
+  * a CORRECTION: the solution of the empty-box BVP (Eqs. emptyBoxEq1-4)
+    whose wall discrepancy cancels that of the near sum and adds the net-force
+    traction jumps F/(2|e2|) on L-R and F/(2|e1|) on D-U (Eqs.
+    SLPdiscrepCorr1-4, algorithm of Sec. 6.2 step 3), represented by M proxy
+    Stokeslets (Eq. vrep) fitted by least squares at Gauss-Legendre
+    collocation points on the walls L and D (Sec. 6.1).
+
+Wall normal convention (fixed by the consistency computation of App. B): the
+traction on L and R is taken with the outward normal of L, and on D and U with
+the outward normal of D, so that int_L g2 + int_D g4 = 0 holds for any net
+force (Eq. gforce).
+"""
+import numpy as np
+
+from . import kernels
+
+IMAGES_3x3 = [(m, n) for n in (-1, 0, 1) for m in (-1, 0, 1)]
+
+
+def image_shifts(e1, e2, images=IMAGES_3x3):
+    return [m * e1 + n * e2 for (m, n) in images]
+
+
+# ----------------------------------------------------------------------------
+# direct sums
+# ----------------------------------------------------------------------------
+def near_traction(xt, nt, ys, qs, shifts, self_index=None, chunk=256):
+    """sum_shift sum_j G^t(x_i, y_j + shift; n_i) q_j  (Sec. 6.2 step 1).
+
+    self_index[i] = j marks source j as the same point as target i; that pair
+    is skipped for the zero shift (the caller adds the on-curve limit).
+    """
+    xt = np.atleast_2d(xt)
+    out = np.zeros_like(xt)
+    for s0 in range(0, xt.shape[0], chunk):
+        sl = slice(s0, s0 + chunk)
+        acc = np.zeros_like(xt[sl])
+        for sh in shifts:
+            r = xt[sl, None, :] - (ys[None, :, :] + sh[None, None, :])
+            if self_index is not None and sh[0] == 0.0 and sh[1] == 0.0:
+                mask = self_index[sl, None] == np.arange(ys.shape[0])[None, :]
+                r = np.where(mask[..., None], 1.0, r)
+                contrib = kernels.traction(r, nt[sl, None, :], qs[None, :, :])
+                contrib = np.where(mask[..., None], 0.0, contrib)
+            else:
+                contrib = kernels.traction(r, nt[sl, None, :], qs[None, :, :])
+            acc += contrib.sum(axis=1)
+        out[sl] = acc
+    return out
+
+
+def near_velocity(xt, ys, qs, shifts, mu, chunk=256):
+    """sum_shift sum_j G(x_i, y_j + shift) q_j."""
+    xt = np.atleast_2d(xt)
+    out = np.zeros_like(xt)
+    for s0 in range(0, xt.shape[0], chunk):
+        sl = slice(s0, s0 + chunk)
+        acc = np.zeros_like(xt[sl])
+        for sh in shifts:
+            r = xt[sl, None, :] - (ys[None, :, :] + sh[None, None, :])
+            acc += kernels.stokeslet(r, qs[None, :, :], mu).sum(axis=1)
+        out[sl] = acc
+    return out
+
+
+def near_vorticity(xt, ys, qs, shifts, mu):
+    xt = np.atleast_2d(xt)
+    acc = np.zeros(xt.shape[0])
+    for sh in shifts:
+        r = xt[:, None, :] - (ys[None, :, :] + sh[None, None, :])
+        acc += kernels.stokeslet_vorticity(r, qs[None, :, :], mu).sum(axis=1)
+    return acc
+
+
+# ----------------------------------------------------------------------------
+# walls, collocation and proxies (Sec. 6.1)
+# ----------------------------------------------------------------------------
+def gauss_legendre_unit(m):
+    """m Gauss-Legendre nodes on (-1/2, 1/2) and weights summing to 1."""
+    s, w = np.polynomial.legendre.leggauss(m)
+    return 0.5 * s, 0.5 * w
+
+
+def wall_normals(e1, e2):
+    """Unit outward normals of the walls L (parallel to e2) and D (parallel
+    to e1): nu_L is orthogonal to e2 with nu_L . e1 < 0, nu_D is orthogonal
+    to e1 with nu_D . e2 < 0."""
+    nl = np.array([e2[1], -e2[0]]) / np.hypot(*e2)
+    if nl @ e1 > 0:
+        nl = -nl
+    nd = np.array([e1[1], -e1[0]]) / np.hypot(*e1)
+    if nd @ e2 > 0:
+        nd = -nd
+    return nl, nd
+
+
+def collocation(e1, e2, centre, m):
+    """Collocation points on L = {c - e1/2 + s e2} and D = {c - e2/2 + s e1},
+    s at Gauss-Legendre nodes of (-1/2, 1/2); with arc-length weights."""
+    s, w = gauss_legendre_unit(m)
+    xl = centre[None, :] - 0.5 * e1[None, :] + s[:, None] * e2[None, :]
+    xd = centre[None, :] - 0.5 * e2[None, :] + s[:, None] * e1[None, :]
+    return xl, xd, w * np.hypot(*e2), w * np.hypot(*e1)
+
+
+def proxy_points(centre, radius, M):
+    ang = 2.0 * np.pi * np.arange(M) / M
+    return centre[None, :] + radius * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+
+
+def _split(v):
+    """(m, 2) -> [all 1-components; all 2-components] (Sec. 6.1 ordering)."""
+    return np.concatenate([v[:, 0], v[:, 1]])
+
+
+def proxy_matrix(e1, e2, centre, m, yp, mu):
+    """Q = [Q1; Q2; Q3; Q4] (8m x 2M): discrepancies on the walls of the unit
+    proxy Stokeslets (Sec. 6.1).  Columns: xi_1 of every proxy, then xi_2."""
+    xl, xd, _, _ = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    M = yp.shape[0]
+    Q = np.zeros((8 * m, 2 * M))
+    for comp in range(2):
+        f = np.zeros((M, 2))
+        f[:, comp] = 1.0
+        for p in range(M):
+            fp = f[p]
+            def vel(x):
+                return kernels.stokeslet(x - yp[p], fp[None, :], mu)
+            def trac(x, nu):
+                return kernels.traction(x - yp[p], nu[None, :], fp[None, :])
+            col = comp * M + p
+            Q[0 * m:2 * m, col] = _split(vel(xl + e1) - vel(xl))
+            Q[2 * m:4 * m, col] = _split(trac(xl + e1, nl) - trac(xl, nl))
+            Q[4 * m:6 * m, col] = _split(vel(xd + e2) - vel(xd))
+            Q[6 * m:8 * m, col] = _split(trac(xd + e2, nd) - trac(xd, nd))
+    return Q
+
+
+def consistency_matrix(e1, e2, centre, m):
+    """W^T (3 x 8m) of Eq. (W), read as the discrete Eqs. (gforce), (gvol):
+    rows 1-2 integrate g2 over L plus g4 over D (net force), row 3 integrates
+    the normal flux g1 . nu_L over L plus g3 . nu_D over D (volume)."""
+    _, _, wl, wd = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    z = np.zeros(m)
+    W = np.zeros((3, 8 * m))
+    W[0] = np.concatenate([z, z, wl, z, z, z, wd, z])
+    W[1] = np.concatenate([z, z, z, wl, z, z, z, wd])
+    W[2] = np.concatenate([wl * nl[0], wl * nl[1], z, z, wd * nd[0], wd * nd[1], z, z])
+    return W
+
+
+def near_discrepancy(e1, e2, centre, m, ys, qs, mu):
+    """g = [g1; g2; g3; g4] of the near sum (Sec. 6.2 step 2), using the
+    translation invariance of the kernels: of the 3 x 3 images only the
+    columns m = -2 (seen from R, i.e. shifted) and m = +1 survive in
+    S_near(x + e1) - S_near(x), and likewise rows for U - D, so every
+    evaluation is at least about one cell width from its source."""
+    xl, xd, _, _ = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    plus_lr = [-2 * e1 + n * e2 for n in (-1, 0, 1)]
+    minus_lr = [e1 + n * e2 for n in (-1, 0, 1)]
+    plus_du = [k * e1 - 2 * e2 for k in (-1, 0, 1)]
+    minus_du = [k * e1 + e2 for k in (-1, 0, 1)]
+    nlm = np.repeat(nl[None, :], m, axis=0)
+    ndm = np.repeat(nd[None, :], m, axis=0)
+    g1 = near_velocity(xl, ys, qs, plus_lr, mu) - near_velocity(xl, ys, qs, minus_lr, mu)
+    g2 = near_traction(xl, nlm, ys, qs, plus_lr) - near_traction(xl, nlm, ys, qs, minus_lr)
+    g3 = near_velocity(xd, ys, qs, plus_du, mu) - near_velocity(xd, ys, qs, minus_du, mu)
+    g4 = near_traction(xd, ndm, ys, qs, plus_du) - near_traction(xd, ndm, ys, qs, minus_du)
+    return np.concatenate([_split(g1), _split(g2), _split(g3), _split(g4)])
+
+
+def near_discrepancy_direct(e1, e2, centre, m, ys, qs, mu):
+    """The same g computed literally as S_near(R) - S_near(L) etc. with the
+    full 3 x 3 sums (used only to pin the cancellation form)."""
+    xl, xd, _, _ = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    sh = image_shifts(e1, e2)
+    nlm = np.repeat(nl[None, :], m, axis=0)
+    ndm = np.repeat(nd[None, :], m, axis=0)
+    g1 = near_velocity(xl + e1, ys, qs, sh, mu) - near_velocity(xl, ys, qs, sh, mu)
+    g2 = near_traction(xl + e1, nlm, ys, qs, sh) - near_traction(xl, nlm, ys, qs, sh)
+    g3 = near_velocity(xd + e2, ys, qs, sh, mu) - near_velocity(xd, ys, qs, sh, mu)
+    g4 = near_traction(xd + e2, ndm, ys, qs, sh) - near_traction(xd, ndm, ys, qs, sh)
+    return np.concatenate([_split(g1), _split(g2), _split(g3), _split(g4)])
+
+
+def corrected_discrepancy(g, F, e1, e2, m):
+    """g~ = g0 - g with g0 = [0; F/(2|e2|); 0; F/(2|e1|)] (Sec. 6.2 step 3)."""
+    g0 = np.zeros(8 * m)
+    l2, l1 = np.hypot(*e2), np.hypot(*e1)
+    g0[2 * m:3 * m] = F[0] / (2 * l2)
+    g0[3 * m:4 * m] = F[1] / (2 * l2)
+    g0[6 * m:7 * m] = F[0] / (2 * l1)
+    g0[7 * m:8 * m] = F[1] / (2 * l1)
+    return g0 - g
+
+
+def proxy_solution_operator(Q, lam_rel=1e-8):
+    """Solution operator P (2M x 8m) of the least-squares fit Q xi = d of
+    Sec. 6.1, xi = P d.  Q is rectangular and ill-conditioned (Sec. 6.1), so
+    "least squares" is read as the Tikhonov-regularised problem
+        min |Q xi - d|^2 + lam^2 |xi|^2,   lam = lam_rel * ||Q||_F,
+    whose solution is unique and depends smoothly on Q.  It is obtained here
+    from numpy's least-squares solver on the stacked system [Q; lam I]."""
+    lam = lam_rel * np.linalg.norm(Q)
+    k, n = Q.shape
+    A = np.vstack([Q, lam * np.eye(n)])
+    B = np.vstack([np.eye(k), np.zeros((n, k))])
+    return np.linalg.lstsq(A, B, rcond=None)[0]
+
+
+def xi_pairs(xi):
+    M = xi.shape[0] // 2
+    return np.stack([xi[:M], xi[M:]], axis=1)
+
+
+def correction_traction(xt, nt, yp, xi):
+    """T(v, q) at targets of the proxy representation, Eqs. (vrep), (qrep)."""
+    f = xi_pairs(xi)
+    r = np.atleast_2d(xt)[:, None, :] - yp[None, :, :]
+    return kernels.traction(r, np.atleast_2d(nt)[:, None, :], f[None, :, :]).sum(axis=1)
+
+
+def correction_velocity(xt, yp, xi, mu):
+    f = xi_pairs(xi)
+    r = np.atleast_2d(xt)[:, None, :] - yp[None, :, :]
+    return kernels.stokeslet(r, f[None, :, :], mu).sum(axis=1)
+
+
+def correction_vorticity(xt, yp, xi, mu):
+    f = xi_pairs(xi)
+    r = np.atleast_2d(xt)[:, None, :] - yp[None, :, :]
+    return kernels.stokeslet_vorticity(r, f[None, :, :], mu).sum(axis=1)
+
+
+def proxy_points_box(e1, e2, centre, M):
+    """The paper's own proxy placement (Sec. 6.1, remark after Eq. W): M
+    points on the walls of the doubled cell U~ (walls at lattice coordinate
+    +-1), M/4 per wall at the midpoints of equal sub-intervals."""
+    k = M // 4
+    s = (np.arange(k) + 0.5) / k * 2.0 - 1.0
+    pts = []
+    for side in (-1.0, 1.0):
+        pts.append(centre[None, :] + side * e1[None, :] + s[:, None] * e2[None, :])
+        pts.append(centre[None, :] + side * e2[None, :] + s[:, None] * e1[None, :])
+    return np.concatenate(pts)

@@ -1,0 +1,150 @@
+"""Seeded synthetic suspensions (input generators only).
+
+This module draws body descriptions -- ellipse semi-axes, centres, angles and
+node counts -- for unit cells shaped like the suspensions studied in
+arXiv 1912.04501 (ellipses at a given area fraction and minimum gap).  It holds
+none of the boundary-integral arithmetic: it is read both by the GPU library's
+callers and by the CPU oracle's tests, and imports neither.
+
+Every function returns a plain dict:
+    e1, e2, centre : lattice vectors and cell centre (lists of 2 floats)
+    mu, gamma      : viscosity and shear rate
+    bodies         : list of {"a", "b", "xc": [x, y], "theta", "n"}
+    solver         : suggested n_proxy, proxy_radius, n_coll, gmres_tol
+    dt, steps      : time-stepping parameters of the workload
+"""
+import math
+
+import numpy as np
+
+SAMPLES = 1024  # boundary samples per ellipse used by the gap estimate
+
+
+def _outline(a, b, xc, theta, k=SAMPLES):
+    t = 2.0 * np.pi * np.arange(k) / k
+    c, s = math.cos(theta), math.sin(theta)
+    px, py = a * np.cos(t), b * np.sin(t)
+    return np.stack([xc[0] + c * px - s * py, xc[1] + s * px + c * py], axis=1)
+
+
+def _inside(a, b, xc, theta, pts):
+    c, s = math.cos(theta), math.sin(theta)
+    d = pts - np.asarray(xc)[None, :]
+    u = c * d[:, 0] + s * d[:, 1]
+    v = -s * d[:, 0] + c * d[:, 1]
+    return (u / a) ** 2 + (v / b) ** 2 < 1.0
+
+
+def gap_estimate(b1, b2, shift=(0.0, 0.0)):
+    """Minimum distance between two ellipse outlines sampled at SAMPLES points
+    each (negative if they overlap).  shift translates the second body."""
+    p = _outline(b1["a"], b1["b"], b1["xc"], b1["theta"])
+    xc2 = [b2["xc"][0] + shift[0], b2["xc"][1] + shift[1]]
+    q = _outline(b2["a"], b2["b"], xc2, b2["theta"])
+    if _inside(b1["a"], b1["b"], b1["xc"], b1["theta"], q).any() or \
+            _inside(b2["a"], b2["b"], xc2, b2["theta"], p).any():
+        return -1.0
+    d2 = ((p[:, None, :] - q[None, :, :]) ** 2).sum(-1)
+    return float(np.sqrt(d2.min()))
+
+
+def min_gap(cell):
+    """Smallest gap between any two bodies of the cell, periodic images
+    included (sampling estimate)."""
+    e1, e2 = np.asarray(cell["e1"]), np.asarray(cell["e2"])
+    bodies = cell["bodies"]
+    best = np.inf
+    for i in range(len(bodies)):
+        for j in range(i, len(bodies)):
+            for m in (-1, 0, 1):
+                for n in (-1, 0, 1):
+                    if i == j and m == 0 and n == 0:
+                        continue
+                    sh = m * e1 + n * e2
+                    ci, cj = np.asarray(bodies[i]["xc"]), np.asarray(bodies[j]["xc"]) + sh
+                    reach = max(bodies[i]["a"], bodies[i]["b"]) + max(bodies[j]["a"], bodies[j]["b"])
+                    if np.hypot(*(ci - cj)) - reach > best:
+                        continue
+                    best = min(best, gap_estimate(bodies[i], bodies[j], sh))
+    return best
+
+
+def config1():
+    """Unit cell (1,0),(0,1) centred at (0.5,0.5); mu = gamma = 1; one
+    ellipse 0.2 x 0.1 at the centre, angle 0, 128 nodes; 16 proxy Stokeslets
+    on a circle of radius 1.5; GMRES tolerance 1e-10; 10 Euler steps of 0.01."""
+    return dict(e1=[1.0, 0.0], e2=[0.0, 1.0], centre=[0.5, 0.5], mu=1.0, gamma=1.0,
+                bodies=[dict(a=0.2, b=0.1, xc=[0.5, 0.5], theta=0.0, n=128)],
+                solver=dict(n_proxy=16, proxy_radius=1.5, n_coll=16, gmres_tol=1e-10),
+                dt=0.01, steps=10)
+
+
+def random_cell(n_bodies, phi, aspect, min_gap_target, nodes, seed,
+                e1=(1.0, 0.0), e2=(0.0, 1.0), centre=(0.5, 0.5), equal_area=True,
+                max_tries=200000):
+    """Random sequential placement of n_bodies ellipses of total area fraction
+    phi and aspect ratios uniform in `aspect`, angles uniform in [0, pi), every
+    gap (periodic images included) at least min_gap_target.  nodes is an int
+    or a callable(a, b) -> int."""
+    rng = np.random.default_rng(seed)
+    e1, e2, centre = np.asarray(e1, float), np.asarray(e2, float), np.asarray(centre, float)
+    area_cell = abs(e1[0] * e2[1] - e1[1] * e2[0])
+    if equal_area:
+        areas = np.full(n_bodies, phi * area_cell / n_bodies)
+    else:
+        w = rng.uniform(0.5, 1.5, n_bodies)
+        areas = phi * area_cell * w / w.sum()
+    bodies = []
+    tries = 0
+    for k in range(n_bodies):
+        alpha = rng.uniform(*aspect)
+        a = math.sqrt(areas[k] * alpha / math.pi)
+        b = math.sqrt(areas[k] / (alpha * math.pi))
+        while True:
+            tries += 1
+            if tries > max_tries:
+                raise RuntimeError("placement failed; lower phi or min_gap")
+            uv = rng.uniform(-0.5, 0.5, 2)
+            xc = centre + uv[0] * e1 + uv[1] * e2
+            cand = dict(a=a, b=b, xc=[float(xc[0]), float(xc[1])], theta=float(rng.uniform(0, math.pi)))
+            ok = True
+            for other in bodies:
+                for m in (-1, 0, 1):
+                    for n in (-1, 0, 1):
+                        sh = m * e1 + n * e2
+                        d = np.hypot(*(np.asarray(other["xc"]) + sh - xc))
+                        if d - (max(a, b) + max(other["a"], other["b"])) > min_gap_target:
+                            continue
+                        if gap_estimate(cand, other, sh) < min_gap_target:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                break
+        cand["n"] = int(nodes(a, b) if callable(nodes) else nodes)
+        bodies.append(cand)
+    return dict(e1=e1.tolist(), e2=e2.tolist(), centre=centre.tolist(), mu=1.0, gamma=1.0,
+                bodies=bodies)
+
+
+def config2(seed=2):
+    """25 equal-area ellipses, area fraction 0.3, aspect ratios uniform in
+    [1, 3], minimum gap 1e-2, 256 nodes per body (6400 nodes); 100 Euler
+    steps of 1e-3 with the lattice skewing."""
+    cell = random_cell(25, 0.3, (1.0, 3.0), 1e-2, 256, seed)
+    cell.update(solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10),
+                dt=1e-3, steps=100)
+    return cell
+
+
+def small_cell(n_bodies=3, nodes=64, seed=0, phi=0.2, gap=0.05, e2=(0.0, 1.0)):
+    """A few-body cell for quick parity checks (several tiles, ragged sizes)."""
+    cell = random_cell(n_bodies, phi, (1.0, 2.5), gap,
+                       nodes if callable(nodes) else (lambda a, b, _n=nodes: _n), seed, e2=e2,
+                       equal_area=False)
+    cell.update(solver=dict(n_proxy=32, proxy_radius=1.5, n_coll=16, gmres_tol=1e-10),
+                dt=1e-3, steps=2)
+    return cell

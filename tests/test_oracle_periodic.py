@@ -1,0 +1,198 @@
+"""Pins of the oracle's periodizing machinery (Sec. 4.2, Sec. 6.1, Sec. 6.2).
+
+* App. B / Eq. (W): the discrepancy of the near sum, corrected by g0, is
+  consistent (W^T g~ = 0) for ANY density, including non-zero net force; and
+  W^T Q = 0.  Flipping the wall normal convention breaks this (planted mistake).
+* The cancellation form of the discrepancy equals the literal difference of
+  3x3 sums (translation invariance, Sec. 6.2 step 2).
+* Sec. 6.1 Example 1 (golden setup): the EBVP for a known Stokeslet field
+  converges exponentially in the number of proxies.
+* The assembled periodic single layer is periodic in velocity and traction
+  when the net force is zero, and its traction jumps by F/(2|e2|), F/(2|e1|)
+  otherwise (Definition of G_per, Eqs. gperdiscrep1-4, Remark r:notper); by
+  the uniqueness theorem this fixes it up to constants.
+* A 5x5 near sum with its own correction gives the same traction after the
+  pressure-constant fix (G_per does not depend on the near/correction split).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import geometry, kernels, periodic
+from paper_1912_04501_gb300 import workloads
+from tests.conftest import oracle_operator, oracle_suspension
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ebvp_example.txt")
+
+
+def _cell(e2=(0.3, 1.0), seed=0):
+    return workloads.small_cell(n_bodies=3, nodes=64, seed=seed, e2=e2)
+
+
+@pytest.mark.parametrize("e2", [(0.0, 1.0), (0.3, 1.0), (-0.45, 1.0)])
+def test_consistency_any_net_force(e2):
+    cell = _cell(e2)
+    op = oracle_operator(cell)
+    s = op.s
+    W = periodic.consistency_matrix(s.e1, s.e2, s.centre, op.m)
+    rng = np.random.default_rng(3)
+    sig = rng.normal(size=(s.N, 2))
+    q, F, _ = op.density_moments(sig)
+    assert np.abs(F).max() > 1e-2
+    _, dt = op.proxy_strengths(q)
+    assert np.abs(W @ dt).max() < 1e-12 * max(1.0, np.abs(dt).max())
+    assert np.abs(W @ op.Q).max() < 1e-13 * np.abs(op.Q).max()
+
+
+def test_consistency_fails_with_flipped_wall_normals(monkeypatch):
+    """Plant the other normal convention in the oracle: consistency breaks by
+    O(F), so the test above really checks the sign."""
+    cell = _cell()
+    orig = periodic.wall_normals
+    monkeypatch.setattr(periodic, "wall_normals", lambda e1, e2: tuple(-v for v in orig(e1, e2)))
+    op = oracle_operator(cell)
+    s = op.s
+    W = periodic.consistency_matrix(s.e1, s.e2, s.centre, op.m)
+    sig = np.random.default_rng(3).normal(size=(s.N, 2))
+    q, F, _ = op.density_moments(sig)
+    _, dt = op.proxy_strengths(q)
+    assert np.abs(W[:2] @ dt - 2 * F.sum(0)).max() < 1e-10
+
+
+def test_discrepancy_cancellation_matches_literal_difference():
+    cell = _cell()
+    # bodies well inside the cell so the literal difference is not ill-conditioned
+    for bd in cell["bodies"]:
+        bd["xc"] = [0.5 + 0.25 * (bd["xc"][0] - 0.5), 0.5 + 0.25 * (bd["xc"][1] - 0.5)]
+        bd["a"] *= 0.5
+        bd["b"] *= 0.5
+    s = oracle_suspension(cell)
+    q = np.random.default_rng(1).normal(size=(s.N, 2)) * s.w[:, None]
+    g_fast = periodic.near_discrepancy(s.e1, s.e2, s.centre, 12, s.x, q, s.mu)
+    g_lit = periodic.near_discrepancy_direct(s.e1, s.e2, s.centre, 12, s.x, q, s.mu)
+    np.testing.assert_allclose(g_fast, g_lit, atol=1e-12 * np.abs(g_lit).max())
+
+
+def _read_golden():
+    vals = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        vals[k] = v
+    ev = lambda t: eval(t, {"cos": math.cos, "sin": math.sin, "pi": math.pi})
+    mu = float(vals["mu"][0])
+    y0 = np.array([ev(t) for t in vals["y0"]])
+    f0 = np.array([float(t) for t in vals["f0"]])
+    cells = {}
+    for key in ("cell_square", "cell_skew"):
+        v = vals[key]
+        cells[key] = (np.array([ev(v[1]), ev(v[2])]), np.array([ev(v[4]), ev(v[5])]),
+                      np.array([ev(v[7]), ev(v[8])]))
+    return mu, y0, f0, cells, int(vals["grid"][0])
+
+
+def _ebvp_error(mu, y0, f0, e1, e2, c, M, m, ngrid):
+    yp = periodic.proxy_points_box(e1, e2, c, M)
+    Q = periodic.proxy_matrix(e1, e2, c, m, yp, mu)
+    xl, xd, _, _ = periodic.collocation(e1, e2, c, m)
+    nl, nd = periodic.wall_normals(e1, e2)
+    v = lambda x: kernels.stokeslet(x - y0, f0[None, :], mu)
+    t = lambda x, nu: kernels.traction(x - y0, np.repeat(nu[None], len(x), 0), f0[None, :])
+    sp = periodic._split
+    d = np.concatenate([sp(v(xl + e1) - v(xl)), sp(t(xl + e1, nl) - t(xl, nl)),
+                        sp(v(xd + e2) - v(xd)), sp(t(xd + e2, nd) - t(xd, nd))])
+    xi = periodic.proxy_solution_operator(Q) @ d
+    s = np.linspace(-0.5, 0.5, ngrid)
+    S1, S2 = np.meshgrid(s, s, indexing="ij")
+    grid = c + S1.reshape(-1, 1) * e1 + S2.reshape(-1, 1) * e2
+    err = periodic.correction_velocity(grid, yp, xi, mu) - v(grid)
+    err -= err[0]
+    return np.abs(err).max() / np.abs(v(grid)).max()
+
+
+@pytest.mark.parametrize("key", ["cell_square", "cell_skew"])
+def test_ebvp_example_converges(key):
+    mu, y0, f0, cells, ngrid = _read_golden()
+    e1, e2, c = cells[key]
+    errs = [_ebvp_error(mu, y0, f0, e1, e2, c, M, m, ngrid)
+            for M, m in [(16, 8), (32, 16), (48, 24), (64, 32)]]
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[1] / errs[0] < 0.1 and errs[2] / errs[1] < 0.1
+    assert errs[3] < 1e-7
+
+
+def _periodic_fields(op, sig):
+    s = op.s
+    q, _, _ = op.density_moments(sig)
+    xi, _ = op.proxy_strengths(q)
+    U = lambda x: periodic.near_velocity(x, s.x, q, op.shifts, s.mu) + \
+        periodic.correction_velocity(x, op.yp, xi, s.mu)
+    T = lambda x, nu: periodic.near_traction(x, np.repeat(nu[None], len(x), 0), s.x, q, op.shifts) + \
+        periodic.correction_traction(x, np.repeat(nu[None], len(x), 0), op.yp, xi)
+    return U, T, q
+
+
+@pytest.mark.parametrize("e2", [(0.0, 1.0), (0.3, 1.0)])
+def test_periodic_and_force_jump(e2):
+    cell = _cell(e2)
+    op = oracle_operator(cell, n_proxy=48, n_coll=24)
+    s = op.s
+    rng = np.random.default_rng(11)
+    sig = rng.normal(size=(s.N, 2))
+    nl, nd = periodic.wall_normals(s.e1, s.e2)
+    sl = rng.uniform(-0.5, 0.5, 15)
+    xl = s.centre - 0.5 * s.e1 + sl[:, None] * s.e2
+    xd = s.centre - 0.5 * s.e2 + sl[:, None] * s.e1
+    # zero net force: remove the mean of q body by body
+    sig0 = sig.copy()
+    for b in range(len(s.bodies)):
+        k = slice(s.offsets[b], s.offsets[b + 1])
+        sig0[k] -= (sig0[k] * s.w[k, None]).sum(0) / s.w[k].sum()
+    U, T, q = _periodic_fields(op, sig0)
+    scale = np.abs(U(xl)).max()
+    assert np.abs(U(xl + s.e1) - U(xl)).max() < 3e-8 * max(1, scale)
+    assert np.abs(U(xd + s.e2) - U(xd)).max() < 3e-8 * max(1, scale)
+    assert np.abs(T(xl + s.e1, nl) - T(xl, nl)).max() < 3e-8 * max(1, np.abs(T(xl, nl)).max())
+    # non-zero net force: velocity still periodic, traction jumps by F/(2|e|)
+    U, T, q = _periodic_fields(op, sig)
+    F = q.sum(0)
+    assert np.abs(U(xl + s.e1) - U(xl)).max() < 3e-8 * max(1, np.abs(U(xl)).max())
+    jump_lr = T(xl + s.e1, nl) - T(xl, nl)
+    jump_du = T(xd + s.e2, nd) - T(xd, nd)
+    np.testing.assert_allclose(jump_lr, np.repeat((F / (2 * np.hypot(*s.e2)))[None], 15, 0), atol=3e-8)
+    np.testing.assert_allclose(jump_du, np.repeat((F / (2 * np.hypot(*s.e1)))[None], 15, 0), atol=3e-8)
+
+
+def test_near_split_independence_5x5():
+    """G_per is unique up to constants (Thm t:consistency + Lemma l:bvpunique):
+    a 5x5 near sum corrected by its own MFS fit gives the same traction as the
+    3x3 one once the pressure constant (a multiple of n) is removed."""
+    cell = _cell((0.2, 1.0))
+    op = oracle_operator(cell, n_proxy=48, n_coll=24, use_close=False)
+    s = op.s
+    sig = np.random.default_rng(4).normal(size=(s.N, 2))
+    T3 = op.traction(sig)
+    # 5x5 variant assembled from the same oracle pieces with a wider discrepancy
+    shifts5 = [m * s.e1 + n * s.e2 for n in range(-2, 3) for m in range(-2, 3)]
+    q, _, _ = op.density_moments(sig)
+    T5 = periodic.near_traction(s.x, s.n, s.x, q, shifts5, self_index=np.arange(s.N))
+    T5 += kernels.traction_self(s.kappa, s.tau, q)
+    xl, xd, _, _ = periodic.collocation(s.e1, s.e2, s.centre, op.m)
+    nl, nd = periodic.wall_normals(s.e1, s.e2)
+    m = op.m
+    nlm, ndm = np.repeat(nl[None], m, 0), np.repeat(nd[None], m, 0)
+    # 5x5 discrepancy, computed literally (sources are >= ~1.5 cells from the walls' far images)
+    g1 = periodic.near_velocity(xl + s.e1, s.x, q, shifts5, s.mu) - periodic.near_velocity(xl, s.x, q, shifts5, s.mu)
+    g2 = periodic.near_traction(xl + s.e1, nlm, s.x, q, shifts5) - periodic.near_traction(xl, nlm, s.x, q, shifts5)
+    g3 = periodic.near_velocity(xd + s.e2, s.x, q, shifts5, s.mu) - periodic.near_velocity(xd, s.x, q, shifts5, s.mu)
+    g4 = periodic.near_traction(xd + s.e2, ndm, s.x, q, shifts5) - periodic.near_traction(xd, ndm, s.x, q, shifts5)
+    sp = periodic._split
+    g = np.concatenate([sp(g1), sp(g2), sp(g3), sp(g4)])
+    dt = periodic.corrected_discrepancy(g, q.sum(0), s.e1, s.e2, m)
+    T5 += periodic.correction_traction(s.x, s.n, op.yp, op.Qp @ dt)
+    fix = lambda T: T - (T[0] @ s.n[0]) * s.n
+    d = fix(T3) - fix(T5)
+    assert np.abs(d).max() < 3e-7 * np.abs(fix(T3)).max()
