@@ -1,0 +1,188 @@
+/*
+ * bie.h -- C ABI of the GB300 (sm_103a) periodized Stokes boundary-integral
+ * library: the mobility problem of rigid bodies in a doubly periodic, sheared
+ * two-dimensional Stokes flow, after Wang, Nazockdast & Barnett,
+ * arXiv 1912.04501.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - All floating-point data are IEEE double unless stated otherwise.
+ *  - Nodes are numbered body by body; on body i the nodes are the periodic
+ *    trapezoidal nodes t_k = 2*pi*k/N_i, k = 0..N_i-1, of the parametrisation
+ *    x(t) = x^c + R(theta) (a cos t, b sin t), counter-clockwise (Sec. 6, first
+ *    paragraph).  N is the total node count.
+ *  - A density or a traction is a vector of 2N doubles, node-major:
+ *    (v_x[0], v_y[0], v_x[1], v_y[1], ...).
+ *  - Pointers flagged `on_device` are device pointers on the context's GPU;
+ *    otherwise they are host pointers (pageable or pinned).  The caller owns
+ *    every array it passes; the library reads or writes it only during the
+ *    call.  The library owns the device memory it allocates in bie_init.
+ *  - Every function returns BIE_OK (0) or a negative BIE_E* code; the text of
+ *    the last error is available from bie_last_error.  A context is not
+ *    thread-safe: calls on one context must not overlap.
+ */
+#ifndef BIE_H
+#define BIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIE_OK 0
+#define BIE_EINVAL (-1)   /* bad argument, size or geometry */
+#define BIE_ENOCONV (-2)  /* solver stopped above its tolerance; outputs hold the last iterate */
+#define BIE_ECOLLIDE (-3) /* two bodies closer than the allowed minimum gap */
+#define BIE_ENUMERIC (-4) /* NaN or Inf met in a residual */
+#define BIE_ECUDA (-5)    /* a CUDA runtime call failed */
+#define BIE_ENOMEM (-6)   /* device allocation failed */
+
+#define BIE_FP64 0  /* every pair sum in double precision */
+#define BIE_MIXED 1 /* pair sums in single precision inside FP64 iterative refinement */
+
+typedef struct bie_ctx bie_ctx;
+
+/* Lattice vectors e1, e2 and the centre of the unit cell U (Sec. 2). */
+typedef struct {
+    double e1[2];
+    double e2[2];
+    double center[2];
+} bie_lattice;
+
+/* One rigid body: an ellipse with semi-axes a = p[0], b = p[1] (shape 0; the
+ * only shape of this version), centroid xc and angle theta, discretised by
+ * n_nodes trapezoidal nodes (n_nodes even, 8 <= n_nodes <= 4096). */
+typedef struct {
+    int32_t n_nodes;
+    int32_t shape;
+    double p[4];
+    double xc[2];
+    double theta;
+} bie_body;
+
+/* Numerical parameters.  bie_default_opts fills every field. */
+typedef struct {
+    int32_t precision;    /* BIE_FP64 or BIE_MIXED (solver and time step) */
+    int32_t n_proxy;      /* M proxy Stokeslets on a circle about the cell centre (Sec. 6.1), 4..256 */
+    double proxy_radius;  /* radius of that circle */
+    int32_t n_coll;       /* m Gauss-Legendre collocation points per wall (Sec. 6.1), 2..128 */
+    double lam_rel;       /* Tikhonov parameter of the proxy least-squares fit, relative to ||Q||_F */
+    double gmres_tol;     /* target relative residual ||b - A sigma|| / ||b|| (FP64 operator) */
+    int32_t gmres_max;    /* maximum Krylov dimension of one GMRES cycle, 1..1000 */
+    double inner_tol;     /* relative tolerance of each single-precision inner solve (BIE_MIXED) */
+    int32_t max_refine;   /* maximum outer refinement sweeps (BIE_MIXED) */
+    int32_t warm_start;   /* bie_step initial guess: 0 = zero, 1 = previous step's density */
+    double min_gap;       /* bie_step fails with BIE_ECOLLIDE below this body gap (node-sampled); 0 = off */
+    int32_t device;       /* CUDA device ordinal */
+} bie_opts;
+
+typedef struct {
+    int32_t iterations;   /* Krylov iterations, all cycles and sweeps */
+    int32_t refinements;  /* outer refinement sweeps (BIE_MIXED), else GMRES cycles */
+    int32_t applies64;    /* FP64 operator applications */
+    int32_t applies32;    /* single-precision operator applications */
+    double rel_residual;  /* final ||b - A sigma|| / ||b||, FP64 operator */
+} bie_solve_info;
+
+/* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
+ * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
+ * warm_start 1, min_gap 0, device 0. */
+void bie_default_opts(bie_opts* opts);
+
+/* Create a context for one unit cell: lattice, viscosity mu, shear rate
+ * gamma (background flow u0 = (gamma x2, 0), Sec. 3) and n_bodies bodies.
+ * Copies the inputs, allocates the device buffers, discretises the bodies on
+ * the GPU and builds the proxy fit.  opts may be NULL (defaults).
+ * Errors: BIE_EINVAL (sizes, degenerate lattice, non-positive axes),
+ * BIE_ENOMEM, BIE_ECUDA.  On error *ctx is set to NULL. */
+int bie_init(bie_ctx** ctx, const bie_lattice* lattice, double mu, double gamma,
+             int32_t n_bodies, const bie_body* bodies, const bie_opts* opts);
+
+void bie_destroy(bie_ctx* ctx);
+const char* bie_last_error(const bie_ctx* ctx);
+
+/* Total node count N and body count. */
+int bie_size(const bie_ctx* ctx, int32_t* n_nodes, int32_t* n_bodies);
+
+/* Make the library launch on the given cudaStream_t (NULL = legacy default). */
+int bie_set_stream(bie_ctx* ctx, void* stream);
+
+/* Copy the current discretisation to the caller: positions x (2N), outward
+ * unit normals n (2N), trapezoidal weights w (N), curvature kappa (N).  Any
+ * pointer may be NULL.  Host pointers unless on_device. */
+int bie_nodes(bie_ctx* ctx, double* x, double* n, double* w, double* kappa, int32_t on_device);
+
+/* out = A sigma, the discretised operator of Eq. (BIEdiscretized) completed
+ * by L (Eq. BIEPerturbed2) with the pressure fix of Sec. 6.2:
+ *   out_i = sigma_i/2 + T_i + alpha n_i + F_b + (x_i - x^c_b)^perp tau_b,
+ *   T = 3x3 near image sum of G^t (Eq. Gt) with the on-curve diagonal limit
+ *       + proxy-Stokeslet correction fitted to the wall discrepancy (Sec. 6.2
+ *       steps 1-4),  alpha = -T_0 . n_0.
+ * precision: BIE_FP64 or BIE_MIXED (single-precision pair sums).
+ * sigma and out: 2N doubles each, must not overlap. */
+int bie_apply(bie_ctx* ctx, const double* sigma, double* out, int32_t precision, int32_t on_device);
+
+/* The right-hand side -T(u0, p0) = -mu gamma (n_2, n_1) of Eq. (BIEPerturbed)
+ * at every node (2N doubles). */
+int bie_rhs(bie_ctx* ctx, double* b, int32_t on_device);
+
+/* Solve A sigma = b to opts.gmres_tol (relative FP64 residual) by GMRES
+ * (opts.precision = BIE_FP64) or by single-precision GMRES inside FP64
+ * iterative refinement (BIE_MIXED).  rhs NULL means -T(u0, p0).  sigma holds
+ * the initial guess on entry when use_guess != 0 and the solution on exit
+ * (2N doubles).  info may be NULL.  Returns BIE_ENOCONV if the tolerance was
+ * not met (sigma then holds the best iterate), BIE_ENUMERIC on NaN/Inf. */
+int bie_solve(bie_ctx* ctx, const double* rhs, double* sigma, int32_t use_guess, int32_t on_device,
+              bie_solve_info* info);
+
+/* Rigid-body velocities and effective viscosity from a density sigma (2N):
+ * v (2 n_bodies) = (u + u0) at each centroid, omega (n_bodies) = half the
+ * vorticity there, u the periodic single layer with its free constant fixed
+ * by a zero proxy velocity at the cell centre; mu_eff (1) the particle-stress
+ * average mu - (1/(gamma |U|)) sum_b int (x_2 - x^c_2) sigma_1 ds.  Outputs
+ * may be NULL; they are host pointers unless on_device. */
+int bie_velocities(bie_ctx* ctx, const double* sigma, double* v, double* omega, double* mu_eff,
+                   int32_t on_device);
+
+/* Advance n_steps forward-Euler steps of size dt (Sec. 7): solve, extract
+ * (v, omega, mu_eff), move and rotate the bodies, shear the lattice
+ * e2(t) = (gamma t L2 reduced by the nearest multiple of e1, L2) and re-wrap
+ * the centres into the cell.  Requires e1 = (L1, 0).  The density of the
+ * last solve stays in the context as the next warm start.  mu_eff_out, if not
+ * NULL, receives n_steps host doubles; info (host) the last solve's info.
+ * Returns BIE_ECOLLIDE if opts.min_gap > 0 and a gap falls below it. */
+int bie_step(bie_ctx* ctx, double dt, int32_t n_steps, double* mu_eff_out, bie_solve_info* info);
+
+/* Checkpoint: time t, current e2, centroids xc (2 n_bodies), angles theta
+ * (n_bodies), last density sigma (2N, may be NULL).  Host pointers. */
+int bie_get_state(bie_ctx* ctx, double* t, double* e2, double* xc, double* theta, double* sigma);
+
+/* Restore a checkpoint taken from a context with the same bodies and node
+ * counts; re-discretises and rebuilds the proxy fit.  sigma may be NULL
+ * (warm start cleared). */
+int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, const double* theta,
+                  const double* sigma);
+
+/* Profiling aid (no counterpart in the paper: it instruments the kernels
+ * above).  bie_profile(ctx, 1) starts recording a CUDA event pair on the
+ * context stream around every near-image-sum launch and counting every kernel
+ * the library launches; bie_profile(ctx, 0) stops.  bie_profile_read
+ * synchronises the stream, returns the totals since the last read and resets
+ * them. */
+typedef struct {
+    int64_t launches;        /* all kernels launched by the library */
+    int32_t near32_launches; /* single-precision near-sum launches */
+    double near32_ms;        /* their summed device time (CUDA events) */
+    int32_t near64_launches; /* double-precision near-sum launches */
+    double near64_ms;
+} bie_profile_info;
+
+int bie_profile(bie_ctx* ctx, int32_t enable);
+int bie_profile_read(bie_ctx* ctx, bie_profile_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIE_H */

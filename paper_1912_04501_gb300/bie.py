@@ -1,0 +1,259 @@
+"""Python binding of libbie.so (include/bie.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python
+arguments to the C structs and pointers of the ABI.  Host arrays are numpy
+float64 arrays; device arrays are torch CUDA float64 tensors (passed by data
+pointer with on_device = 1).  If the library has not been built the first
+call raises -- there is no fallback implementation.
+
+The functions carry the C names:
+    bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
+    bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
+    bie_set_state, bie_set_stream, bie_profile, bie_profile_read
+and `Context` wraps them for a workload dict (see workloads.py).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbie.so")
+
+BIE_OK, BIE_EINVAL, BIE_ENOCONV, BIE_ECOLLIDE, BIE_ENUMERIC, BIE_ECUDA, BIE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+BIE_FP64, BIE_MIXED = 0, 1
+_NAMES = {0: "BIE_OK", -1: "BIE_EINVAL", -2: "BIE_ENOCONV", -3: "BIE_ECOLLIDE", -4: "BIE_ENUMERIC",
+          -5: "BIE_ECUDA", -6: "BIE_ENOMEM"}
+
+c_double, c_int32, c_void_p = ctypes.c_double, ctypes.c_int32, ctypes.c_void_p
+P_DOUBLE = ctypes.POINTER(ctypes.c_double)
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("e1", c_double * 2), ("e2", c_double * 2), ("center", c_double * 2)]
+
+
+class Body(ctypes.Structure):
+    _fields_ = [("n_nodes", c_int32), ("shape", c_int32), ("p", c_double * 4), ("xc", c_double * 2),
+                ("theta", c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("n_proxy", c_int32), ("proxy_radius", c_double), ("n_coll", c_int32),
+                ("lam_rel", c_double), ("gmres_tol", c_double), ("gmres_max", c_int32), ("inner_tol", c_double),
+                ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("refinements", c_int32), ("applies64", c_int32),
+                ("applies32", c_int32), ("rel_residual", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ProfileInfo(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("near32_launches", c_int32), ("near32_ms", c_double),
+                ("near64_launches", c_int32), ("near64_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library():
+    """Load libbie.so (raises if it is missing: build it with
+    paper_1912_04501_gb300._build.build() or __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build the CUDA library first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = c_void_p
+    sig = {
+        "bie_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "bie_init": (c_int32, [ctypes.POINTER(vp), ctypes.POINTER(Lattice), c_double, c_double, c_int32,
+                               ctypes.POINTER(Body), ctypes.POINTER(Opts)]),
+        "bie_destroy": (None, [vp]),
+        "bie_last_error": (ctypes.c_char_p, [vp]),
+        "bie_size": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+        "bie_set_stream": (c_int32, [vp, vp]),
+        "bie_nodes": (c_int32, [vp, vp, vp, vp, vp, c_int32]),
+        "bie_apply": (c_int32, [vp, vp, vp, c_int32, c_int32]),
+        "bie_rhs": (c_int32, [vp, vp, c_int32]),
+        "bie_solve": (c_int32, [vp, vp, vp, c_int32, c_int32, ctypes.POINTER(SolveInfo)]),
+        "bie_velocities": (c_int32, [vp, vp, vp, vp, vp, c_int32]),
+        "bie_step": (c_int32, [vp, c_double, c_int32, vp, ctypes.POINTER(SolveInfo)]),
+        "bie_get_state": (c_int32, [vp, vp, vp, vp, vp, vp]),
+        "bie_set_state": (c_int32, [vp, c_double, vp, vp, vp, vp]),
+        "bie_profile": (c_int32, [vp, c_int32]),
+        "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared in include/bie.h that the loaded library exports."""
+    L = library()
+    return [n for n in ("bie_default_opts", "bie_init", "bie_destroy", "bie_last_error", "bie_size",
+                        "bie_set_stream", "bie_nodes", "bie_apply", "bie_rhs", "bie_solve", "bie_velocities",
+                        "bie_step", "bie_get_state", "bie_set_state", "bie_profile", "bie_profile_read")
+            if hasattr(L, n)]
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy float64 array or a torch float64 tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous float64")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def bie_default_opts():
+    o = Opts()
+    library().bie_default_opts(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """One unit cell on the GPU (bie_init ... bie_destroy)."""
+
+    def __init__(self, cell, precision=BIE_MIXED, **opts):
+        L = library()
+        o = bie_default_opts()
+        sv = cell.get("solver", {})
+        o.precision = precision
+        for k in ("n_proxy", "proxy_radius", "n_coll"):
+            if k in sv:
+                setattr(o, k, sv[k])
+        if "gmres_tol" in sv:
+            o.gmres_tol = sv["gmres_tol"]
+        for k, v in opts.items():
+            setattr(o, k, v)
+        lat = Lattice((c_double * 2)(*cell["e1"]), (c_double * 2)(*cell["e2"]), (c_double * 2)(*cell["centre"]))
+        bodies = (Body * len(cell["bodies"]))()
+        for b, bd in zip(bodies, cell["bodies"]):
+            b.n_nodes = int(bd["n"])
+            b.shape = 0
+            b.p = (c_double * 4)(bd["a"], bd["b"], 0.0, 0.0)
+            b.xc = (c_double * 2)(*bd["xc"])
+            b.theta = bd["theta"]
+        h = c_void_p()
+        rc = L.bie_init(ctypes.byref(h), ctypes.byref(lat), cell["mu"], cell["gamma"], len(cell["bodies"]),
+                        bodies, ctypes.byref(o))
+        if rc != 0:
+            raise BieError(rc, "bie_init failed (invalid input or CUDA error)")
+        self.h = h
+        self.opts = o
+        n, nb = c_int32(), c_int32()
+        L.bie_size(h, ctypes.byref(n), ctypes.byref(nb))
+        self.N, self.n_bodies = n.value, nb.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise BieError(rc, library().bie_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().bie_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        self._check(library().bie_set_stream(self.h, c_void_p(stream_handle)))
+
+    def nodes(self):
+        x, n = np.zeros(2 * self.N), np.zeros(2 * self.N)
+        w, k = np.zeros(self.N), np.zeros(self.N)
+        self._check(library().bie_nodes(self.h, x.ctypes.data, n.ctypes.data, w.ctypes.data, k.ctypes.data, 0))
+        return x.reshape(-1, 2), n.reshape(-1, 2), w, k
+
+    def apply(self, sigma, out=None, precision=BIE_FP64):
+        if out is None:
+            out = np.zeros(2 * self.N)
+        ps, ds = _ptr(sigma)
+        po, do = _ptr(out)
+        if ds != do:
+            raise ValueError("sigma and out must both be host or both device")
+        self._check(library().bie_apply(self.h, ps, po, precision, ds))
+        return out
+
+    def rhs(self):
+        b = np.zeros(2 * self.N)
+        self._check(library().bie_rhs(self.h, b.ctypes.data, 0))
+        return b
+
+    def solve(self, rhs=None, guess=None, allow_noconv=False):
+        sigma = np.zeros(2 * self.N) if guess is None else np.array(guess, dtype=np.float64).ravel()
+        info = SolveInfo()
+        pr, _ = _ptr(None if rhs is None else np.ascontiguousarray(rhs, dtype=np.float64).ravel())
+        rc = library().bie_solve(self.h, pr, sigma.ctypes.data, 0 if guess is None else 1, 0, ctypes.byref(info))
+        if rc != 0 and not (allow_noconv and rc == BIE_ENOCONV):
+            self._check(rc)
+        return sigma, info.as_dict()
+
+    def velocities(self, sigma):
+        v, om, mu = np.zeros(2 * self.n_bodies), np.zeros(self.n_bodies), np.zeros(1)
+        s = np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+        self._check(library().bie_velocities(self.h, s.ctypes.data, v.ctypes.data, om.ctypes.data,
+                                             mu.ctypes.data, 0))
+        return v.reshape(-1, 2), om, float(mu[0])
+
+    def step(self, dt, n_steps=1):
+        mu = np.zeros(max(1, n_steps))
+        info = SolveInfo()
+        self._check(library().bie_step(self.h, dt, n_steps, mu.ctypes.data, ctypes.byref(info)))
+        return mu[:n_steps], info.as_dict()
+
+    def get_state(self):
+        t = np.zeros(1)
+        e2 = np.zeros(2)
+        xc = np.zeros(2 * self.n_bodies)
+        th = np.zeros(self.n_bodies)
+        sg = np.zeros(2 * self.N)
+        self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
+                                            th.ctypes.data, sg.ctypes.data))
+        return dict(t=float(t[0]), e2=e2, xc=xc.reshape(-1, 2), theta=th, sigma=sg)
+
+    def profile(self, enable=True):
+        self._check(library().bie_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        info = ProfileInfo()
+        self._check(library().bie_profile_read(self.h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def set_state(self, t, e2, xc, theta, sigma=None):
+        e2 = np.ascontiguousarray(e2, dtype=np.float64)
+        xc = np.ascontiguousarray(xc, dtype=np.float64).ravel()
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+        self._check(library().bie_set_state(self.h, float(t), e2.ctypes.data, xc.ctypes.data, th.ctypes.data,
+                                            None if sg is None else sg.ctypes.data))

@@ -1,0 +1,532 @@
+// C ABI entry points (include/bie.h): argument checking, device memory
+// ownership, host <-> device staging, and the forward-Euler time loop.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bie_internal.cuh"
+
+namespace bie {
+
+int fail(bie_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(bie_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? BIE_ENOMEM : BIE_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+static int dalloc(bie_ctx* c, T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc");
+    return BIE_OK;
+}
+
+static void free_all(bie_ctx* c) {
+    void* ptrs[] = {c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body, c->tgt32, c->gl_s, c->A, c->beta,
+                    c->P, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.bodyF,
+                    c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
+                    c->sv.d, c->sv.h, c->sv.red, c->sv.sigma_prev};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto e : c->ev_pool)
+        if (e) cudaEventDestroy(e);
+    c->ev_pool.clear();
+}
+
+// Lattice of Sec. 7: e1 = (L1, 0) fixed, e2 = (s0 + gamma t L2 - L1 round(.), L2).
+static void lattice_at(const bie_ctx* c, double t, double* e2) {
+    double L1 = c->e1[0];
+    double sx = c->e2_0[0] + c->gamma * t * c->e2_0[1];
+    sx -= L1 * std::round(sx / L1);
+    e2[0] = sx;
+    e2[1] = c->e2_0[1];
+}
+
+__global__ void k_euler(double* __restrict__ body, int nb, const double* __restrict__ v,
+                        const double* __restrict__ om, double dt, double e1x, double e1y, double e2x, double e2y,
+                        double Cx, double Cy) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double* bd = body + 8 * b;
+    double X = bd[2] + dt * v[2 * b], Y = bd[3] + dt * v[2 * b + 1];
+    bd[4] += dt * om[b];
+    // wrap: lattice coordinates about the centre into [-1/2, 1/2)
+    double det = e1x * e2y - e1y * e2x;
+    double px = X - Cx, py = Y - Cy;
+    double a = (px * e2y - py * e2x) / det, bb = (e1x * py - e1y * px) / det;
+    double sa = floor(a + 0.5), sb = floor(bb + 0.5);
+    bd[2] = X - (sa * e1x + sb * e2x);
+    bd[3] = Y - (sa * e1y + sb * e2y);
+}
+
+constexpr int kEventPairs = 1024;
+
+int prof_begin(bie_ctx* c, int kind) {
+    if (!c->prof) return BIE_OK;
+    if (c->ev_used == kEventPairs) {
+        int rc = prof_fold(c);
+        if (rc) return rc;
+    }
+    if (c->ev_pool.empty()) {
+        c->ev_pool.resize(2 * kEventPairs);
+        c->ev_kind.resize(kEventPairs);
+        for (auto& e : c->ev_pool) BIE_CUDA(c, cudaEventCreate(&e));
+    }
+    c->ev_kind[c->ev_used] = kind;
+    BIE_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used], c->stream));
+    return BIE_OK;
+}
+
+int prof_end(bie_ctx* c) {
+    if (!c->prof) return BIE_OK;
+    BIE_CUDA(c, cudaEventRecord(c->ev_pool[2 * c->ev_used + 1], c->stream));
+    ++c->ev_used;
+    return BIE_OK;
+}
+
+int prof_fold(bie_ctx* c) {
+    if (c->ev_used == 0) return BIE_OK;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < c->ev_used; ++k) {
+        float ms = 0;
+        BIE_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]));
+        if (c->ev_kind[k] == 0) {
+            c->prof_acc.near32_launches++;
+            c->prof_acc.near32_ms += ms;
+        } else {
+            c->prof_acc.near64_launches++;
+            c->prof_acc.near64_ms += ms;
+        }
+    }
+    c->ev_used = 0;
+    return BIE_OK;
+}
+
+static int rebuild(bie_ctx* c) {
+    int rc = build_geometry(c);
+    if (rc) return rc;
+    return build_proxy_fit(c);
+}
+
+}  // namespace bie
+
+using namespace bie;
+
+extern "C" {
+
+void bie_default_opts(bie_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BIE_MIXED;
+    o->n_proxy = 48;
+    o->proxy_radius = 1.5;
+    o->n_coll = 24;
+    o->lam_rel = 1e-8;
+    o->gmres_tol = 1e-10;
+    o->gmres_max = 200;
+    o->inner_tol = 1e-5;
+    o->max_refine = 8;
+    o->warm_start = 1;
+    o->min_gap = 0.0;
+    o->device = 0;
+}
+
+int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int32_t n_bodies,
+             const bie_body* bodies, const bie_opts* opts) {
+    if (!out) return BIE_EINVAL;
+    *out = nullptr;
+    if (!lat || !bodies || n_bodies <= 0) return BIE_EINVAL;
+    bie_ctx* c = new (std::nothrow) bie_ctx();
+    if (!c) return BIE_ENOMEM;
+    if (opts) c->opts = *opts;
+    else bie_default_opts(&c->opts);
+    auto bad = [&](const std::string& m) {
+        c->err = m;
+        delete c;
+        return BIE_EINVAL;
+    };
+    const bie_opts& o = c->opts;
+    if (o.precision != BIE_FP64 && o.precision != BIE_MIXED) return bad("precision must be BIE_FP64 or BIE_MIXED");
+    if (o.n_proxy < 4 || o.n_proxy > kMaxProxy) return bad("n_proxy out of range");
+    if (o.n_coll < 2 || o.n_coll > kMaxColl) return bad("n_coll out of range");
+    if (!(o.proxy_radius > 0) || !(o.lam_rel >= 0) || !(o.gmres_tol > 0) || !(o.inner_tol > 0))
+        return bad("non-positive tolerance or radius");
+    if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) return bad("gmres_max / max_refine out of range");
+    if (!(mu > 0) || !std::isfinite(gamma)) return bad("mu must be positive, gamma finite");
+    double det = lat->e1[0] * lat->e2[1] - lat->e1[1] * lat->e2[0];
+    if (!(std::fabs(det) > 1e-12)) return bad("degenerate lattice");
+    c->device = o.device;
+    for (int k = 0; k < 2; ++k) {
+        c->e1[k] = lat->e1[k];
+        c->e2[k] = c->e2_0[k] = lat->e2[k];
+        c->C[k] = lat->center[k];
+    }
+    c->mu = mu;
+    c->gamma = gamma;
+    c->nb = n_bodies;
+    c->M = o.n_proxy;
+    c->m = o.n_coll;
+    c->offsets.assign(n_bodies + 1, 0);
+    c->body_host.assign(8 * (size_t)n_bodies, 0.0);
+    long long N = 0;
+    for (int b = 0; b < n_bodies; ++b) {
+        const bie_body& bd = bodies[b];
+        if (bd.shape != 0) return bad("only shape 0 (ellipse) is supported");
+        if (bd.n_nodes < 8 || bd.n_nodes > 4096 || (bd.n_nodes & 1)) return bad("n_nodes must be even, 8..4096");
+        if (!(bd.p[0] > 0) || !(bd.p[1] > 0)) return bad("ellipse semi-axes must be positive");
+        if (!std::isfinite(bd.xc[0]) || !std::isfinite(bd.xc[1]) || !std::isfinite(bd.theta))
+            return bad("non-finite body position");
+        c->n_nodes.push_back(bd.n_nodes);
+        c->offsets[b] = (int)N;
+        double* h = &c->body_host[8 * (size_t)b];
+        h[0] = bd.p[0];
+        h[1] = bd.p[1];
+        h[2] = bd.xc[0];
+        h[3] = bd.xc[1];
+        h[4] = bd.theta;
+        h[5] = bd.n_nodes;
+        h[6] = (double)N;
+        N += bd.n_nodes;
+    }
+    if (N > (1 << 24)) return bad("too many nodes");
+    c->N = (int)N;
+    c->offsets[n_bodies] = c->N;
+
+    auto cu = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess) {
+            int code = cuda_check(c, e, what);
+            return code;
+        }
+        return 0;
+    };
+    int rc;
+    if ((rc = cu(cudaSetDevice(c->device), "cudaSetDevice"))) {
+        delete c;
+        return rc;
+    }
+    const int n = c->N, nb = c->nb, M = c->M, m = c->m;
+    const int R = 8 * m + 2 * M, Cc = 2 * M;
+    int tiles32 = (n + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
+    int tiles64 = (n + kNearThreads - 1) / kNearThreads;
+    int maxsplit = std::max(1, n / 256);
+    c->near_splits32 = std::min(maxsplit, std::max(1, (4 * kSMs + tiles32 - 1) / tiles32));
+    c->near_splits64 = std::min(maxsplit, std::max(1, (4 * kSMs + tiles64 - 1) / tiles64));
+    size_t part = std::max((size_t)c->near_splits32 * n * sizeof(float2), (size_t)c->near_splits64 * n * sizeof(double2));
+    c->sv.kmax = o.gmres_max;
+    int kk = c->sv.kmax;
+    rc = 0;
+    rc = rc ? rc : dalloc(c, &c->x, n);
+    rc = rc ? rc : dalloc(c, &c->y, n);
+    rc = rc ? rc : dalloc(c, &c->nx, n);
+    rc = rc ? rc : dalloc(c, &c->ny, n);
+    rc = rc ? rc : dalloc(c, &c->w, n);
+    rc = rc ? rc : dalloc(c, &c->kap, n);
+    rc = rc ? rc : dalloc(c, &c->owner, n);
+    rc = rc ? rc : dalloc(c, &c->body, 8 * (size_t)nb);
+    rc = rc ? rc : dalloc(c, &c->tgt32, n);
+    rc = rc ? rc : dalloc(c, &c->gl_s, m);
+    rc = rc ? rc : dalloc(c, &c->A, (size_t)R * Cc);
+    rc = rc ? rc : dalloc(c, &c->beta, 2 * (size_t)Cc);
+    rc = rc ? rc : dalloc(c, &c->P, (size_t)Cc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->yp, 2 * (size_t)M);
+    rc = rc ? rc : dalloc(c, &c->scal, 3 * (size_t)nb + 8);
+    rc = rc ? rc : dalloc(c, &c->ws.sigma, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->ws.out, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->ws.src64, n);
+    rc = rc ? rc : dalloc(c, &c->ws.src32, n);
+    rc = rc ? rc : dalloc(c, &c->ws.bodyF, 3 * (size_t)nb);
+    rc = rc ? rc : dalloc(c, (char**)&c->ws.part, part);
+    rc = rc ? rc : dalloc(c, &c->ws.gpart, (size_t)kDiscBlocks * 2 * m * 4);
+    rc = rc ? rc : dalloc(c, &c->ws.xi, 2 * (size_t)M);
+    rc = rc ? rc : dalloc(c, &c->ws.T, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1) * 2 * n);
+    rc = rc ? rc : dalloc(c, &c->sv.w, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.r, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.x, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.b, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.d, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.h, 3 * (size_t)(kk + 2) + 8);
+    rc = rc ? rc : dalloc(c, &c->sv.red, 8);
+    rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
+    c->ws.part_bytes = part;
+    if (rc) {
+        free_all(c);
+        std::string e = c->err;
+        delete c;
+        (void)e;
+        return rc;
+    }
+    std::vector<int> owner(n);
+    for (int b = 0; b < nb; ++b)
+        for (int k = c->offsets[b]; k < c->offsets[b + 1]; ++k) owner[k] = b;
+    gauss_legendre_half(m, c->gl_host);
+    std::vector<double> yp(2 * (size_t)M);
+    for (int p = 0; p < M; ++p) {
+        double a = 2.0 * kPi * p / M;
+        yp[2 * p] = c->C[0] + o.proxy_radius * std::cos(a);
+        yp[2 * p + 1] = c->C[1] + o.proxy_radius * std::sin(a);
+    }
+    auto up = [&](void* d, const void* h, size_t bytes) {
+        return cu(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice), "cudaMemcpy");
+    };
+    rc = up(c->owner, owner.data(), n * sizeof(int));
+    rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
+    rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
+    rc = rc ? rc : up(c->yp, yp.data(), yp.size() * sizeof(double));
+    rc = rc ? rc : rebuild(c);
+    rc = rc ? rc : cu(cudaStreamSynchronize(c->stream), "init sync");
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return BIE_OK;
+}
+
+void bie_destroy(bie_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+const char* bie_last_error(const bie_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int bie_size(const bie_ctx* c, int32_t* n_nodes, int32_t* n_bodies) {
+    if (!c) return BIE_EINVAL;
+    if (n_nodes) *n_nodes = c->N;
+    if (n_bodies) *n_bodies = c->nb;
+    return BIE_OK;
+}
+
+int bie_set_stream(bie_ctx* c, void* stream) {
+    if (!c) return BIE_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return BIE_OK;
+}
+
+static int copy_out(bie_ctx* c, double* dst, const double* dev, size_t count, int on_device) {
+    if (!dst) return BIE_OK;
+    BIE_CUDA(c, cudaMemcpyAsync(dst, dev, count * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    return BIE_OK;
+}
+
+int bie_nodes(bie_ctx* c, double* x, double* n, double* w, double* kappa, int32_t on_device) {
+    if (!c) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t N = c->N;
+    auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (x) {
+        BIE_CUDA(c, cudaMemcpy2DAsync(x, 2 * sizeof(double), c->x, sizeof(double), sizeof(double), N, kind, c->stream));
+        BIE_CUDA(c, cudaMemcpy2DAsync(x + 1, 2 * sizeof(double), c->y, sizeof(double), sizeof(double), N, kind, c->stream));
+    }
+    if (n) {
+        BIE_CUDA(c, cudaMemcpy2DAsync(n, 2 * sizeof(double), c->nx, sizeof(double), sizeof(double), N, kind, c->stream));
+        BIE_CUDA(c, cudaMemcpy2DAsync(n + 1, 2 * sizeof(double), c->ny, sizeof(double), sizeof(double), N, kind, c->stream));
+    }
+    int rc = copy_out(c, w, c->w, N, on_device);
+    if (rc) return rc;
+    rc = copy_out(c, kappa, c->kap, N, on_device);
+    if (rc) return rc;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_apply(bie_ctx* c, const double* sigma, double* out, int32_t precision, int32_t on_device) {
+    if (!c || !sigma || !out) return BIE_EINVAL;
+    if (precision != BIE_FP64 && precision != BIE_MIXED) return fail(c, BIE_EINVAL, "bad precision");
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t n2 = 2 * (size_t)c->N;
+    const double* din = sigma;
+    double* dout = out;
+    if (!on_device) {
+        BIE_CUDA(c, cudaMemcpyAsync(c->ws.sigma, sigma, n2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        din = c->ws.sigma;
+        dout = c->ws.out;
+    }
+    int rc = apply_device(c, din, dout, precision);
+    if (rc) return rc;
+    if (!on_device)
+        BIE_CUDA(c, cudaMemcpyAsync(out, c->ws.out, n2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_rhs(bie_ctx* c, double* b, int32_t on_device) {
+    if (!c || !b) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    int rc = rhs_device(c, on_device ? b : c->ws.out);
+    if (rc) return rc;
+    if (!on_device)
+        BIE_CUDA(c, cudaMemcpyAsync(b, c->ws.out, 2 * (size_t)c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_solve(bie_ctx* c, const double* rhs, double* sigma, int32_t use_guess, int32_t on_device,
+              bie_solve_info* info) {
+    if (!c || !sigma) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t n2 = 2 * (size_t)c->N;
+    auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int rc;
+    if (rhs) BIE_CUDA(c, cudaMemcpyAsync(c->sv.b, rhs, n2 * sizeof(double), kind, c->stream));
+    else if ((rc = rhs_device(c, c->sv.b))) return rc;
+    if (use_guess) BIE_CUDA(c, cudaMemcpyAsync(c->sv.x, sigma, n2 * sizeof(double), kind, c->stream));
+    int src = solve_device(c, c->sv.b, c->sv.x, use_guess != 0, info);
+    if (src && src != BIE_ENOCONV) return src;
+    BIE_CUDA(c, cudaMemcpyAsync(sigma, c->sv.x, n2 * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, c->sv.x, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->sv.have_prev = true;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return src;
+}
+
+int bie_velocities(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff, int32_t on_device) {
+    if (!c || !sigma) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t n2 = 2 * (size_t)c->N;
+    const double* din = sigma;
+    if (!on_device) {
+        BIE_CUDA(c, cudaMemcpyAsync(c->ws.sigma, sigma, n2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        din = c->ws.sigma;
+    }
+    double* dv = c->scal;
+    double* dom = c->scal + 2 * c->nb;
+    double* dmu = c->scal + 3 * c->nb;
+    int rc = velocities_device(c, din, dv, dom, dmu);
+    if (rc) return rc;
+    if ((rc = copy_out(c, v, dv, 2 * (size_t)c->nb, on_device))) return rc;
+    if ((rc = copy_out(c, omega, dom, c->nb, on_device))) return rc;
+    if ((rc = copy_out(c, mu_eff, dmu, 1, on_device))) return rc;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_solve_info* info) {
+    if (!c || n_steps < 0 || !std::isfinite(dt)) return BIE_EINVAL;
+    if (c->e1[1] != 0.0) return fail(c, BIE_EINVAL, "time stepping needs e1 = (L1, 0)");
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t n2 = 2 * (size_t)c->N;
+    double* dv = c->scal;
+    double* dom = c->scal + 2 * c->nb;
+    double* dmu = c->scal + 3 * c->nb;
+    for (int s = 0; s < n_steps; ++s) {
+        int rc = rhs_device(c, c->sv.b);
+        if (rc) return rc;
+        bool guess = c->opts.warm_start == 1 && c->sv.have_prev;
+        if (guess)
+            BIE_CUDA(c, cudaMemcpyAsync(c->sv.x, c->sv.sigma_prev, n2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        c->stream));
+        bie_solve_info inf{};
+        rc = solve_device(c, c->sv.b, c->sv.x, guess, &inf);
+        if (info) *info = inf;
+        if (rc) return rc;
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, c->sv.x, n2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        c->sv.have_prev = true;
+        rc = velocities_device(c, c->sv.x, dv, dom, dmu);
+        if (rc) return rc;
+        if (mu_eff_out)
+            BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + s, dmu, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        c->t += dt;
+        lattice_at(c, c->t, c->e2);
+        k_euler<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->body, c->nb, dv, dom, dt, c->e1[0], c->e1[1],
+                                                            c->e2[0], c->e2[1], c->C[0], c->C[1]);
+        BIE_LAUNCH(c, "k_euler");
+        rc = rebuild(c);
+        if (rc) return rc;
+    }
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_get_state(bie_ctx* c, double* t, double* e2, double* xc, double* theta, double* sigma) {
+    if (!c) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    std::vector<double> h(8 * (size_t)c->nb);
+    BIE_CUDA(c, cudaMemcpyAsync(h.data(), c->body, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (sigma) {
+        if (c->sv.have_prev)
+            BIE_CUDA(c, cudaMemcpyAsync(sigma, c->sv.sigma_prev, 2 * (size_t)c->N * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        else
+            std::memset(sigma, 0, 2 * (size_t)c->N * sizeof(double));
+    }
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (t) *t = c->t;
+    if (e2) {
+        e2[0] = c->e2[0];
+        e2[1] = c->e2[1];
+    }
+    for (int b = 0; b < c->nb; ++b) {
+        if (xc) {
+            xc[2 * b] = h[8 * b + 2];
+            xc[2 * b + 1] = h[8 * b + 3];
+        }
+        if (theta) theta[b] = h[8 * b + 4];
+    }
+    return BIE_OK;
+}
+
+int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, const double* theta,
+                  const double* sigma) {
+    if (!c || !e2 || !xc || !theta) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    std::vector<double> h(8 * (size_t)c->nb);
+    BIE_CUDA(c, cudaMemcpy(h.data(), c->body, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < c->nb; ++b) {
+        h[8 * b + 2] = xc[2 * b];
+        h[8 * b + 3] = xc[2 * b + 1];
+        h[8 * b + 4] = theta[b];
+    }
+    c->t = t;
+    c->e2[0] = e2[0];
+    c->e2[1] = e2[1];
+    BIE_CUDA(c, cudaMemcpyAsync(c->body, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (sigma) {
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, sigma, 2 * (size_t)c->N * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->sv.have_prev = true;
+    } else {
+        c->sv.have_prev = false;
+    }
+    int rc = rebuild(c);
+    if (rc) return rc;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_profile(bie_ctx* c, int32_t enable) {
+    if (!c) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    if (!enable && c->prof) {
+        int rc = prof_fold(c);
+        if (rc) return rc;
+    }
+    c->prof = enable != 0;
+    return BIE_OK;
+}
+
+int bie_profile_read(bie_ctx* c, bie_profile_info* info) {
+    if (!c || !info) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    int rc = prof_fold(c);
+    if (rc) return rc;
+    *info = c->prof_acc;
+    info->launches = c->launches;
+    c->prof_acc = bie_profile_info{};
+    c->launches = 0;
+    return BIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,607 @@
+// The operator application y = A sigma (Eq. BIEdiscretized + L + pressure fix)
+// and the velocity / effective-viscosity extraction.
+//
+// Launch sequence of one application (all on the context stream):
+//   k_pack          q = sigma w; single- or double-precision source records
+//   k_body_moments  F_b = sum q, tau_b = sum (x - x^c)^perp . q  (one CTA per body)
+//   k_near32/64     3x3 near image sum of G^t at every node (Sec. 6.2 step 1),
+//                   split over source chunks -> partial sums
+//   k_disc          wall discrepancy of the near sum with the far-image
+//                   cancellation (Sec. 6.2 step 2), split over source chunks
+//   k_xi            g~ = g0 - g, xi = P g~ (Sec. 6.2 step 3)
+//   k_correct       T = sum of partials + on-curve diagonal + proxy traction (step 4)
+//   k_finish        alpha = -T_0 . n_0;  y = sigma/2 + T + alpha n + L sigma
+#include "bie_internal.cuh"
+
+namespace bie {
+
+__device__ inline double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline double block_sum_d(double v, double* red) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum_d(s);
+        if (lane == 0) red[32] = s;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_pack(const double2* __restrict__ sigma, const double* __restrict__ x,
+                       const double* __restrict__ y, const double* __restrict__ w, int N, double Cx,
+                       double Cy, float4* __restrict__ src32, Src64* __restrict__ src64) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 s = sigma[i];
+    double wi = w[i];
+    double qx = s.x * wi, qy = s.y * wi;
+    if (src32) src32[i] = make_float4((float)(x[i] - Cx), (float)(y[i] - Cy), (float)qx, (float)qy);
+    if (src64) src64[i] = Src64{x[i], y[i], qx, qy};
+}
+
+__global__ void k_body_moments(const double2* __restrict__ sigma, const double* __restrict__ x,
+                               const double* __restrict__ y, const double* __restrict__ w,
+                               const double* __restrict__ body, double* __restrict__ bodyF) {
+    __shared__ double red[33];
+    int b = blockIdx.x;
+    const double* bd = body + 8 * b;
+    double xc = bd[2], yc = bd[3];
+    int n = (int)bd[5], off = (int)bd[6];
+    double fx = 0, fy = 0, tq = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int i = off + k;
+        double2 s = sigma[i];
+        double qx = s.x * w[i], qy = s.y * w[i];
+        fx += qx;
+        fy += qy;
+        tq += -(y[i] - yc) * qx + (x[i] - xc) * qy;
+    }
+    fx = block_sum_d(fx, red);
+    fy = block_sum_d(fy, red);
+    tq = block_sum_d(tq, red);
+    if (threadIdx.x == 0) {
+        bodyF[3 * b] = fx;
+        bodyF[3 * b + 1] = fy;
+        bodyF[3 * b + 2] = tq;
+    }
+}
+
+struct Shifts9 {
+    float x[9], y[9];
+};
+struct Shifts9d {
+    double x[9], y[9];
+};
+
+// ---------------------------------------------------------------------------
+// Near image sum, single precision.  Block: kNearThreads threads, each owning
+// TPT targets; grid.x over target tiles, grid.y over source chunks.  The 9
+// image shifts are applied to the target (x_t - s) so every staged source is
+// reused by 9 * TPT pair evaluations.  Per pair: 13 FP32 instructions and one
+// MUFU reciprocal.  The zero-distance self pair is absorbed by a 1e-30 floor
+// on r^2 (its r.n and r.q are exactly zero, so it contributes 0).
+// ---------------------------------------------------------------------------
+template <int TPT>
+__global__ void __launch_bounds__(kNearThreads)
+k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, int chunk, Shifts9 sh,
+         float2* __restrict__ part) {
+    __shared__ float4 s_src[kNearTile];
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    float px[TPT][9], py[TPT][9], nxv[TPT], nyv[TPT];
+    float ax[TPT][3], ay[TPT][3];
+    int tbase = blockIdx.x * (kNearThreads * TPT) + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        int i = tbase + t * kNearThreads;
+        float4 tv = i < N ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            px[t][k] = tv.x - sh.x[k];
+            py[t][k] = tv.y - sh.y[k];
+        }
+        nxv[t] = tv.z;
+        nyv[t] = tv.w;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ax[t][r] = ay[t][r] = 0.f;
+    }
+    for (int jt = j0; jt < j1; jt += kNearTile) {
+        int cnt = min(kNearTile, j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < cnt; ++k) {
+            float4 s = s_src[k];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+#pragma unroll
+                for (int im = 0; im < 9; ++im) {
+                    float dx = px[t][im] - s.x;
+                    float dy = py[t][im] - s.y;
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
+                    float rn = fmaf(dy, nyv[t], dx * nxv[t]);
+                    float rq = fmaf(dy, s.w, dx * s.z);
+                    float inv = rcp_approx(r2);
+                    float cc = (rn * inv) * (rq * inv);
+                    ax[t][im / 3] = fmaf(cc, dx, ax[t][im / 3]);
+                    ay[t][im / 3] = fmaf(cc, dy, ay[t][im / 3]);
+                }
+            }
+        }
+    }
+    const float c = (float)(-1.0 / kPi);
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        int i = tbase + t * kNearThreads;
+        if (i < N)
+            part[(size_t)blockIdx.y * N + i] =
+                make_float2(c * (ax[t][0] + ax[t][1] + ax[t][2]), c * (ay[t][0] + ay[t][1] + ay[t][2]));
+    }
+}
+
+// Near image sum, double precision (one target per thread).  Same structure;
+// the self pair is absorbed by a 1e-300 floor on r^2.
+__global__ void __launch_bounds__(kNearThreads)
+k_near64(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
+         const double* __restrict__ ny, const Src64* __restrict__ src, int N, int chunk, Shifts9d sh,
+         double2* __restrict__ part) {
+    __shared__ Src64 s_src[kNearTile];
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    int i = blockIdx.x * kNearThreads + threadIdx.x;
+    double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
+    if (i < N) {
+        tx = x[i];
+        ty = y[i];
+        tnx = nx[i];
+        tny = ny[i];
+    }
+    double px[9], py[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        px[k] = tx - sh.x[k];
+        py[k] = ty - sh.y[k];
+    }
+    double ax[3] = {0, 0, 0}, ay[3] = {0, 0, 0};
+    for (int jt = j0; jt < j1; jt += kNearTile) {
+        int cnt = min(kNearTile, j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            Src64 s = s_src[k];
+#pragma unroll
+            for (int im = 0; im < 9; ++im) {
+                double dx = px[im] - s.x;
+                double dy = py[im] - s.y;
+                double r2 = fma(dx, dx, fma(dy, dy, 1e-300));
+                double rn = fma(dy, tny, dx * tnx);
+                double rq = fma(dy, s.w, dx * s.z);
+                double inv = 1.0 / r2;
+                double cc = (rn * inv) * (rq * inv);
+                ax[im / 3] = fma(cc, dx, ax[im / 3]);
+                ay[im / 3] = fma(cc, dy, ay[im / 3]);
+            }
+        }
+    }
+    if (i < N) {
+        const double c = -1.0 / kPi;
+        part[(size_t)blockIdx.y * N + i] = make_double2(c * (ax[0] + ax[1] + ax[2]), c * (ay[0] + ay[1] + ay[2]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Wall discrepancy (Sec. 6.2 step 2).  For a collocation point x on L,
+//   S_near(x + e1) - S_near(x) = sum_n sum_j [K(x, y_j - 2 e1 + n e2) - K(x, y_j + e1 + n e2)] q_j
+// and on D with the roles of e1, e2 exchanged; K is the velocity kernel G or
+// the traction kernel G^t with the wall normal.  Block b handles a source
+// chunk; thread (wp, sub): wall point wp in [0, 2m) (L points then D points),
+// sources sub, sub + S, ...; output per block and wall point:
+// (u_x, u_y, t_x, t_y).
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void k_disc(const Src64* __restrict__ src, int N, int chunk, int m,
+                       const double* __restrict__ gl_s, double e1x, double e1y, double e2x, double e2y,
+                       double Cx, double Cy, double mu, double* __restrict__ gpart) {
+    extern __shared__ double sacc[];  // blockDim.x x 4
+    int twm = 2 * m;
+    int wp = threadIdx.x % twm, sub = threadIdx.x / twm, S = blockDim.x / twm;
+    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
+    wall_normals(e1, e2, nl, nd);
+    Real ux = 0, uy = 0, tx = 0, ty = 0;
+    if (sub < S) {
+        bool isL = wp < m;
+        double s = gl_s[isL ? wp : wp - m];
+        double X, Y, nu0, nu1, ax, ay, bx, by;  // ax/ay: step along the wall's rows
+        if (isL) {
+            X = Cx - 0.5 * e1x + s * e2x;
+            Y = Cy - 0.5 * e1y + s * e2y;
+            nu0 = nl[0];
+            nu1 = nl[1];
+        } else {
+            X = Cx - 0.5 * e2x + s * e1x;
+            Y = Cy - 0.5 * e2y + s * e1y;
+            nu0 = nd[0];
+            nu1 = nd[1];
+        }
+        // plus images: -2 a + k b ; minus images: a + k b  (a = e1, b = e2 on L; swapped on D)
+        if (isL) { ax = e1x; ay = e1y; bx = e2x; by = e2y; }
+        else { ax = e2x; ay = e2y; bx = e1x; by = e1y; }
+        const Real c4 = (Real)(1.0 / (4.0 * kPi * mu));
+        const Real ct = (Real)(-1.0 / kPi);
+        int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
+        for (int j = j0 + sub; j < j1; j += S) {
+            Src64 q = src[j];
+            for (int k = -1; k <= 1; ++k) {
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    double shx = (sgn == 0 ? -2.0 * ax : ax) + k * bx;
+                    double shy = (sgn == 0 ? -2.0 * ay : ay) + k * by;
+                    Real rx = (Real)(X - (q.x + shx)), ry = (Real)(Y - (q.y + shy));
+                    Real qx = (Real)q.z, qy = (Real)q.w;
+                    Real r2 = rx * rx + ry * ry;
+                    Real inv = (Real)1 / r2;
+                    Real rq = rx * qx + ry * qy;
+                    Real l = (Real)(-0.5) * log(r2);
+                    Real vx = (l * qx + rx * rq * inv) * c4, vy = (l * qy + ry * rq * inv) * c4;
+                    Real cc = ct * (rx * (Real)nu0 + ry * (Real)nu1) * rq * inv * inv;
+                    Real sg = sgn == 0 ? (Real)1 : (Real)-1;
+                    ux += sg * vx;
+                    uy += sg * vy;
+                    tx += sg * cc * rx;
+                    ty += sg * cc * ry;
+                }
+            }
+        }
+    }
+    sacc[4 * threadIdx.x + 0] = ux;
+    sacc[4 * threadIdx.x + 1] = uy;
+    sacc[4 * threadIdx.x + 2] = tx;
+    sacc[4 * threadIdx.x + 3] = ty;
+    __syncthreads();
+    if (threadIdx.x < twm) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int u = 0; u < S; ++u) {
+            int t = u * twm + threadIdx.x;
+            a0 += sacc[4 * t];
+            a1 += sacc[4 * t + 1];
+            a2 += sacc[4 * t + 2];
+            a3 += sacc[4 * t + 3];
+        }
+        double* o = gpart + ((size_t)blockIdx.x * twm + threadIdx.x) * 4;
+        o[0] = a0;
+        o[1] = a1;
+        o[2] = a2;
+        o[3] = a3;
+    }
+}
+
+// g~ and xi = P g~ (Sec. 6.2 step 3).  One CTA.
+__global__ void k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __restrict__ bodyF,
+                     int nb, double l1, double l2, const double* __restrict__ P, double* __restrict__ xi) {
+    extern __shared__ double d[];  // 8m
+    __shared__ double Fs[2];
+    int tid = threadIdx.x;
+    if (tid == 0) {
+        double fx = 0, fy = 0;
+        for (int b = 0; b < nb; ++b) {
+            fx += bodyF[3 * b];
+            fy += bodyF[3 * b + 1];
+        }
+        Fs[0] = fx;
+        Fs[1] = fy;
+    }
+    __syncthreads();
+    for (int wp = tid; wp < 2 * m; wp += blockDim.x) {
+        double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+        for (int b = 0; b < nblk; ++b) {
+            const double* o = gpart + ((size_t)b * 2 * m + wp) * 4;
+            g0 += o[0];
+            g1 += o[1];
+            g2 += o[2];
+            g3 += o[3];
+        }
+        if (wp < m) {  // L: rows of blocks 1 (velocity) and 2 (traction)
+            int l = wp;
+            d[l] = -g0;
+            d[m + l] = -g1;
+            d[2 * m + l] = Fs[0] / (2.0 * l2) - g2;
+            d[3 * m + l] = Fs[1] / (2.0 * l2) - g3;
+        } else {  // D: blocks 3 and 4
+            int l = wp - m;
+            d[4 * m + l] = -g0;
+            d[5 * m + l] = -g1;
+            d[6 * m + l] = Fs[0] / (2.0 * l1) - g2;
+            d[7 * m + l] = Fs[1] / (2.0 * l1) - g3;
+        }
+    }
+    __syncthreads();
+    int C = 2 * M;
+    for (int r = tid; r < C; r += blockDim.x) {
+        double s = 0;
+        for (int cc = 0; cc < 8 * m; ++cc) s += P[r + (size_t)cc * C] * d[cc];
+        xi[r] = s;
+    }
+}
+
+// T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy traction.
+template <typename PartT>
+__global__ void k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __restrict__ sigma,
+                          const double* __restrict__ x, const double* __restrict__ y,
+                          const double* __restrict__ nx, const double* __restrict__ ny,
+                          const double* __restrict__ w, const double* __restrict__ kap,
+                          const double* __restrict__ yp, const double* __restrict__ xi, int M,
+                          double2* __restrict__ T) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double tx = 0, ty = 0;
+    for (int s = 0; s < splits; ++s) {
+        PartT p = part[(size_t)s * N + i];
+        tx += (double)p.x;
+        ty += (double)p.y;
+    }
+    double2 sg = sigma[i];
+    double n0 = nx[i], n1 = ny[i];
+    double t0 = -n1, t1 = n0;  // unit tangent
+    double qx = sg.x * w[i], qy = sg.y * w[i];
+    double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
+    tx += dg * t0;
+    ty += dg * t1;
+    double X = x[i], Y = y[i];
+    double cx = 0, cy = 0;
+    for (int p = 0; p < M; ++p) {
+        double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
+        double fx = xi[p], fy = xi[M + p];
+        double r2 = rx * rx + ry * ry;
+        double cc = (rx * n0 + ry * n1) * (rx * fx + ry * fy) / (r2 * r2);
+        cx += cc * rx;
+        cy += cc * ry;
+    }
+    tx += -cx / kPi;
+    ty += -cy / kPi;
+    T[i] = make_double2(tx, ty);
+}
+
+__global__ void k_finish(const double2* __restrict__ T, const double2* __restrict__ sigma, int N,
+                         const double* __restrict__ x, const double* __restrict__ y,
+                         const double* __restrict__ nx, const double* __restrict__ ny,
+                         const int* __restrict__ owner, const double* __restrict__ body,
+                         const double* __restrict__ bodyF, double2* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 T0 = T[0];
+    double alpha = -(T0.x * nx[0] + T0.y * ny[0]);
+    int b = owner[i];
+    double xc = body[8 * b + 2], yc = body[8 * b + 3];
+    double Fx = bodyF[3 * b], Fy = bodyF[3 * b + 1], tq = bodyF[3 * b + 2];
+    double2 Ti = T[i], s = sigma[i];
+    double ox = 0.5 * s.x + Ti.x + alpha * nx[i] + Fx - (y[i] - yc) * tq;
+    double oy = 0.5 * s.y + Ti.y + alpha * ny[i] + Fy + (x[i] - xc) * tq;
+    out[i] = make_double2(ox, oy);
+}
+
+__global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ ny, int N, double mg,
+                      double2* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) b[i] = make_double2(-mg * ny[i], -mg * nx[i]);
+}
+
+// ---------------------------------------------------------------------------
+static void shifts(const bie_ctx* c, double* sx, double* sy, bool centred) {
+    int k = 0;
+    for (int n = -1; n <= 1; ++n)
+        for (int mm = -1; mm <= 1; ++mm, ++k) {
+            sx[k] = mm * c->e1[0] + n * c->e2[0];
+            sy[k] = mm * c->e1[1] + n * c->e2[1];
+        }
+    (void)centred;
+}
+
+int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
+    const int N = c->N;
+    const int bs = 256, gs = (N + bs - 1) / bs;
+    const double2* sg = reinterpret_cast<const double2*>(sigma);
+    bool f32 = precision == BIE_MIXED;
+    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], f32 ? c->ws.src32 : nullptr,
+                                     c->ws.src64);
+    BIE_LAUNCH(c, "k_pack");
+    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
+    BIE_LAUNCH(c, "k_body_moments");
+    double sx[9], sy[9];
+    shifts(c, sx, sy, false);
+    int splits;
+    if (f32) {
+        Shifts9 s9;
+        for (int k = 0; k < 9; ++k) {
+            s9.x[k] = (float)sx[k];
+            s9.y[k] = (float)sy[k];
+        }
+        splits = c->near_splits32;
+        int tiles = (N + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
+        int chunk = (N + splits - 1) / splits;
+        dim3 grid(tiles, splits);
+        if (int rc = prof_begin(c, 0)) return rc;
+        k_near32<kNear32TPT><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
+                                                                   (float2*)c->ws.part);
+        BIE_LAUNCH(c, "k_near32");
+        if (int rc = prof_end(c)) return rc;
+    } else {
+        Shifts9d s9;
+        for (int k = 0; k < 9; ++k) {
+            s9.x[k] = sx[k];
+            s9.y[k] = sy[k];
+        }
+        splits = c->near_splits64;
+        int tiles = (N + kNearThreads - 1) / kNearThreads;
+        int chunk = (N + splits - 1) / splits;
+        dim3 grid(tiles, splits);
+        if (int rc = prof_begin(c, 1)) return rc;
+        k_near64<<<grid, kNearThreads, 0, c->stream>>>(c->x, c->y, c->nx, c->ny, c->ws.src64, N, chunk, s9,
+                                                       (double2*)c->ws.part);
+        BIE_LAUNCH(c, "k_near64");
+        if (int rc = prof_end(c)) return rc;
+    }
+    {
+        int twm = 2 * c->m;
+        int dbs = (256 / twm) * twm;
+        if (dbs < twm) dbs = twm;
+        int chunk = (N + kDiscBlocks - 1) / kDiscBlocks;
+        size_t shm = (size_t)dbs * 4 * sizeof(double);
+        if (f32)
+            k_disc<float><<<kDiscBlocks, dbs, shm, c->stream>>>(c->ws.src64, N, chunk, c->m, c->gl_s, c->e1[0],
+                                                                c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1],
+                                                                c->mu, c->ws.gpart);
+        else
+            k_disc<double><<<kDiscBlocks, dbs, shm, c->stream>>>(c->ws.src64, N, chunk, c->m, c->gl_s,
+                                                                 c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0],
+                                                                 c->C[1], c->mu, c->ws.gpart);
+        BIE_LAUNCH(c, "k_disc");
+    }
+    double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
+    double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
+    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscBlocks, c->m, c->M, c->ws.bodyF,
+                                                          c->nb, l1, l2, c->P, c->ws.xi);
+    BIE_LAUNCH(c, "k_xi");
+    double2* T = reinterpret_cast<double2*>(c->ws.T);
+    if (f32)
+        k_correct<float2><<<gs, bs, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y, c->nx,
+                                                    c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M, T);
+    else
+        k_correct<double2><<<gs, bs, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x, c->y,
+                                                     c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M, T);
+    BIE_LAUNCH(c, "k_correct");
+    k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, c->ws.bodyF,
+                                       reinterpret_cast<double2*>(yout));
+    BIE_LAUNCH(c, "k_finish");
+    return BIE_OK;
+}
+
+int rhs_device(bie_ctx* c, double* b) {
+    int bs = 256, gs = (c->N + bs - 1) / bs;
+    k_rhs<<<gs, bs, 0, c->stream>>>(c->nx, c->ny, c->N, c->mu * c->gamma, reinterpret_cast<double2*>(b));
+    BIE_LAUNCH(c, "k_rhs");
+    return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Rigid-body velocities at the centroids (one CTA per body) and mu_eff.
+// u(x^c) = sum_images sum_j G(x^c, y_j + s) q_j + sum_p G(x^c, y_p) xi_p
+//          - sum_p G(C, y_p) xi_p;  curl by the closed form of the Stokeslet.
+// ---------------------------------------------------------------------------
+__global__ void k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __restrict__ body,
+                             const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx,
+                             double Cy, double mu, double gamma, double* __restrict__ v, double* __restrict__ om) {
+    __shared__ double red[33];
+    int b = blockIdx.x;
+    double X = body[8 * b + 2], Y = body[8 * b + 3];
+    double ux = 0, uy = 0, cu = 0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        Src64 q = src[j];
+        for (int k = 0; k < 9; ++k) {
+            double rx = X - (q.x + sh.x[k]), ry = Y - (q.y + sh.y[k]);
+            double r2 = rx * rx + ry * ry;
+            double rq = (rx * q.z + ry * q.w) / r2;
+            double l = -0.5 * log(r2);
+            ux += l * q.z + rx * rq;
+            uy += l * q.w + ry * rq;
+            cu += (ry * q.z - rx * q.w) / r2;
+        }
+    }
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        double fx = xi[p], fy = xi[M + p];
+        double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
+        double r2 = rx * rx + ry * ry;
+        double rq = (rx * fx + ry * fy) / r2;
+        double l = -0.5 * log(r2);
+        ux += l * fx + rx * rq;
+        uy += l * fy + ry * rq;
+        cu += (ry * fx - rx * fy) / r2;
+        rx = Cx - yp[2 * p];
+        ry = Cy - yp[2 * p + 1];
+        r2 = rx * rx + ry * ry;
+        rq = (rx * fx + ry * fy) / r2;
+        l = -0.5 * log(r2);
+        ux -= l * fx + rx * rq;
+        uy -= l * fy + ry * rq;
+    }
+    ux = block_sum_d(ux, red);
+    uy = block_sum_d(uy, red);
+    cu = block_sum_d(cu, red);
+    if (threadIdx.x == 0) {
+        double c4 = 1.0 / (4.0 * kPi * mu);
+        v[2 * b] = ux * c4 + gamma * Y;
+        v[2 * b + 1] = uy * c4;
+        om[b] = 0.5 * (cu / (2.0 * kPi * mu) - gamma);
+    }
+}
+
+__global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __restrict__ y,
+                         const double* __restrict__ w, const int* __restrict__ owner,
+                         const double* __restrict__ body, int N, double mu, double gamma, double area,
+                         double* __restrict__ out) {
+    __shared__ double red[33];
+    double s = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += sigma[i].x * (y[i] - body[8 * owner[i] + 3]) * w[i];
+    s = block_sum_d(s, red);
+    if (threadIdx.x == 0) *out = mu - s / (gamma * area);
+}
+
+int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff) {
+    const int N = c->N;
+    const int bs = 256, gs = (N + bs - 1) / bs;
+    const double2* sg = reinterpret_cast<const double2*>(sigma);
+    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], nullptr, c->ws.src64);
+    BIE_LAUNCH(c, "k_pack");
+    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
+    BIE_LAUNCH(c, "k_body_moments");
+    int twm = 2 * c->m;
+    int dbs = (256 / twm) * twm;
+    if (dbs < twm) dbs = twm;
+    int chunk = (N + kDiscBlocks - 1) / kDiscBlocks;
+    k_disc<double><<<kDiscBlocks, dbs, (size_t)dbs * 4 * sizeof(double), c->stream>>>(
+        c->ws.src64, N, chunk, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
+        c->ws.gpart);
+    BIE_LAUNCH(c, "k_disc");
+    double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
+    double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
+    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscBlocks, c->m, c->M, c->ws.bodyF,
+                                                          c->nb, l1, l2, c->P, c->ws.xi);
+    BIE_LAUNCH(c, "k_xi");
+    double sx[9], sy[9];
+    shifts(c, sx, sy, false);
+    Shifts9d s9;
+    for (int k = 0; k < 9; ++k) {
+        s9.x[k] = sx[k];
+        s9.y[k] = sy[k];
+    }
+    if (v || omega) {
+        k_velocities<<<c->nb, 256, 0, c->stream>>>(c->ws.src64, N, s9, c->body, c->yp, c->ws.xi, c->M, c->C[0],
+                                                   c->C[1], c->mu, c->gamma, v, omega);
+        BIE_LAUNCH(c, "k_velocities");
+    }
+    if (mu_eff) {
+        double area = fabs(c->e1[0] * c->e2[1] - c->e1[1] * c->e2[0]);
+        k_mu_eff<<<1, 1024, 0, c->stream>>>(sg, c->y, c->w, c->owner, c->body, N, c->mu, c->gamma, area, mu_eff);
+        BIE_LAUNCH(c, "k_mu_eff");
+    }
+    return BIE_OK;
+}
+
+}  // namespace bie

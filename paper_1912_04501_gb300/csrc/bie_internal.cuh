@@ -1,0 +1,148 @@
+// Internal declarations of the GB300 periodized Stokes BIE library.
+// Layout in HBM (all device arrays owned by the context):
+//   geometry  : x, y, nx, ny, w, kappa   (N doubles each, SoA)
+//               owner (N ints), body (nb x 8 doubles: a, b, xc, yc, theta, n, off, h)
+//               tgt32 (N float4: x - C, y - C, nx, ny)  -- single-precision targets
+//   densities : 2N doubles, node-major (x, y interleaved) == double2[N]
+//   sources   : src32 (N float4: x - C, y - C, qx, qy), src64 (N Src64: x, y, qx, qy)
+//   proxy fit : Q stacked with lam*I (column-major, R = 8m + 2M rows, 2M cols),
+//               Householder betas, P (2M x 8m, column-major), proxies yp (M double2)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bie.h"
+
+namespace bie {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
+constexpr int kNearThreads = 128;     // threads per near-sum block
+constexpr int kNearTile = 256;        // sources staged per shared-memory tile
+constexpr int kNear32TPT = 2;         // targets per thread, single precision
+constexpr int kDiscBlocks = 96;       // source splits of the wall-discrepancy kernel
+constexpr int kMaxProxy = 256;
+constexpr int kMaxColl = 128;
+
+// Double-precision source record: position and premultiplied density q = sigma w.
+struct __align__(16) Src64 {
+    double x, y, z, w;
+};
+
+struct Workspace {
+    double* sigma = nullptr;    // 2N  staging for host inputs
+    double* out = nullptr;      // 2N  staging for host outputs
+    Src64* src64 = nullptr;   // N
+    float4* src32 = nullptr;    // N
+    double* bodyF = nullptr;    // 3 nb  (F_x, F_y, tau) per body
+    void* part = nullptr;       // near-sum partials: splits x N (float2 or double2)
+    size_t part_bytes = 0;
+    double* gpart = nullptr;    // kDiscBlocks x 2m x 4 discrepancy partials
+    double* xi = nullptr;       // 2M proxy strengths
+    double* T = nullptr;        // 2N traction before the pressure fix
+};
+
+struct Solver {
+    int kmax = 0;
+    double* V = nullptr;     // (kmax + 1) x 2N Krylov basis
+    double* w = nullptr;     // 2N
+    double* r = nullptr;     // 2N
+    double* x = nullptr;     // 2N current solution
+    double* b = nullptr;     // 2N right-hand side
+    double* d = nullptr;     // 2N correction (mixed)
+    double* h = nullptr;     // kmax + 2 dot products
+    double* red = nullptr;   // reduction scratch
+    double* sigma_prev = nullptr;  // 2N warm start of the next step
+    bool have_prev = false;
+};
+
+}  // namespace bie
+
+struct bie_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bie_opts opts{};
+    double e1[2]{}, e2[2]{}, e2_0[2]{}, C[2]{};
+    double mu = 1, gamma = 1, t = 0;
+    int nb = 0, N = 0, M = 0, m = 0;
+    std::vector<int> n_nodes, offsets;
+    std::vector<double> body_host;  // nb x 8 (a, b, xc, yc, theta, n, off, h)
+    // device geometry
+    double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kap = nullptr;
+    int* owner = nullptr;
+    double* body = nullptr;
+    float4* tgt32 = nullptr;
+    // proxy fit
+    double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
+    double* A = nullptr;        // stacked [Q; lam I], column-major
+    double* beta = nullptr;     // 2M Householder scalars
+    double* P = nullptr;        // 2M x 8m solution operator, column-major
+    double* yp = nullptr;       // 2M proxies (x, y) interleaved
+    double* scal = nullptr;     // misc device scalars
+    bie::Workspace ws;
+    bie::Solver sv;
+    int near_splits32 = 1, near_splits64 = 1;
+    // profiling (bie_profile): launch counter and event pairs around near sums
+    bool prof = false;
+    long long launches = 0;
+    std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
+    std::vector<int> ev_kind;           // 0 = near32, 1 = near64 per pair
+    int ev_used = 0;
+    bie_profile_info prof_acc{};
+    std::string err;
+    std::vector<double> gl_host;
+};
+
+namespace bie {
+
+// status helpers -------------------------------------------------------------
+int fail(bie_ctx* c, int code, const std::string& msg);
+int cuda_check(bie_ctx* c, cudaError_t e, const char* what);
+#define BIE_CUDA(c, call)                                  \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return bie::cuda_check(c, _e, #call); \
+    } while (0)
+#define BIE_LAUNCH(c, what)                                \
+    do {                                                   \
+        cudaError_t _e = cudaGetLastError();               \
+        if (_e != cudaSuccess) return bie::cuda_check(c, _e, what); \
+        ++(c)->launches;                                   \
+    } while (0)
+
+// profiling: event pair around a launch (no-op unless bie_profile is on)
+int prof_begin(bie_ctx* c, int kind);
+int prof_end(bie_ctx* c);
+int prof_fold(bie_ctx* c);
+
+// geometry.cu ---------------------------------------------------------------
+int build_geometry(bie_ctx* c);   // nodes from body state
+int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P
+void gauss_legendre_half(int m, std::vector<double>& s);
+
+// apply.cu ------------------------------------------------------------------
+// y = A sigma for device sigma, y (2N each); precision BIE_FP64 / BIE_MIXED
+int apply_device(bie_ctx* c, const double* sigma, double* y, int precision);
+int rhs_device(bie_ctx* c, double* b);
+int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff);
+
+// solve.cu ------------------------------------------------------------------
+int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info);
+
+// small device math shared by the kernels --------------------------------------
+__host__ __device__ inline void wall_normals(const double* e1, const double* e2, double* nl, double* nd) {
+    double l2 = sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
+    nl[0] = e2[1] / l2;
+    nl[1] = -e2[0] / l2;
+    if (nl[0] * e1[0] + nl[1] * e1[1] > 0) { nl[0] = -nl[0]; nl[1] = -nl[1]; }
+    double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    nd[0] = e1[1] / l1;
+    nd[1] = -e1[0] / l1;
+    if (nd[0] * e2[0] + nd[1] * e2[1] > 0) { nd[0] = -nd[0]; nd[1] = -nd[1]; }
+}
+
+}  // namespace bie

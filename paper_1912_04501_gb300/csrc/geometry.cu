@@ -1,0 +1,255 @@
+// Per-geometry precompute: boundary nodes (Sec. 6, trapezoidal rule on each
+// ellipse) and the proxy-Stokeslet least-squares operator of Sec. 6.1.
+//
+// The proxy fit solves min |Q xi - d|^2 + lam^2 |xi|^2 (lam = lam_rel ||Q||_F),
+// i.e. the least-squares problem of the stacked matrix [Q; lam I], by
+// Householder QR in double precision.  The explicit operator P with
+// xi = P d is formed once per geometry so that each operator application
+// needs a single small matrix-vector product.
+#include <cmath>
+
+#include "bie_internal.cuh"
+
+namespace bie {
+
+// ---------------------------------------------------------------------------
+// nodes, normals, weights, curvature
+// ---------------------------------------------------------------------------
+__global__ void k_geometry(const double* __restrict__ body, const int* __restrict__ owner, int N,
+                           double Cx, double Cy, double* __restrict__ x, double* __restrict__ y,
+                           double* __restrict__ nx, double* __restrict__ ny, double* __restrict__ w,
+                           double* __restrict__ kap, float4* __restrict__ tgt32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double* bd = body + 8 * owner[i];
+    double a = bd[0], b = bd[1], xc = bd[2], yc = bd[3], th = bd[4];
+    int n = (int)bd[5], off = (int)bd[6];
+    int k = i - off;
+    double t = (2.0 * kPi * k) / n;
+    double st, ct, s, c;
+    sincos(t, &st, &ct);
+    sincos(th, &s, &c);
+    double px = a * ct, py = b * st, dpx = -a * st, dpy = b * ct;
+    double X = xc + (c * px - s * py), Y = yc + (s * px + c * py);
+    double dX = c * dpx - s * dpy, dY = s * dpx + c * dpy;
+    double ddX = -(c * px - s * py), ddY = -(s * px + c * py);
+    double sp = sqrt(dX * dX + dY * dY);
+    double tx = dX / sp, ty = dY / sp;
+    x[i] = X;
+    y[i] = Y;
+    nx[i] = ty;
+    ny[i] = -tx;
+    w[i] = (2.0 * kPi / n) * sp;
+    kap[i] = (dX * ddY - dY * ddX) / (sp * sp * sp);
+    tgt32[i] = make_float4((float)(X - Cx), (float)(Y - Cy), (float)ty, (float)(-tx));
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes on (-1/2, 1/2) by Newton's method on P_m (host, once)
+// ---------------------------------------------------------------------------
+void gauss_legendre_half(int m, std::vector<double>& s) {
+    s.assign(m, 0.0);
+    for (int i = 0; i < m; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (m + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= m; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (m == 1) { p1 = z; p0 = 1.0; }
+            double dp = m * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        s[m - 1 - i] = 0.5 * z;  // ascending order
+    }
+}
+
+// ---------------------------------------------------------------------------
+// proxy matrix Q (Sec. 6.1): rows [g1; g2; g3; g4] x (1-comps, 2-comps),
+// columns (xi_1 of all proxies, xi_2 of all proxies)
+// ---------------------------------------------------------------------------
+__device__ inline void stokeslet_d(double rx, double ry, double fx, double fy, double c4,
+                                   double& ux, double& uy) {
+    double r2 = rx * rx + ry * ry;
+    double rf = (rx * fx + ry * fy) / r2;
+    double l = -0.5 * log(r2);
+    ux = (l * fx + rx * rf) * c4;
+    uy = (l * fy + ry * rf) * c4;
+}
+
+__device__ inline void traction_d(double rx, double ry, double nx, double ny, double fx, double fy,
+                                  double& tx, double& ty) {
+    double r2 = rx * rx + ry * ry;
+    double cc = -(rx * nx + ry * ny) * (rx * fx + ry * fy) / (kPi * r2 * r2);
+    tx = cc * rx;
+    ty = cc * ry;
+}
+
+__global__ void k_build_Q(double* __restrict__ A, int R, int m, int M, const double* __restrict__ gl_s,
+                          const double* __restrict__ yp, double e1x, double e1y, double e2x, double e2y,
+                          double Cx, double Cy, double mu) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * M) return;
+    int l = idx % m, p = idx / m;
+    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
+    wall_normals(e1, e2, nl, nd);
+    double s = gl_s[l];
+    double xL = Cx - 0.5 * e1x + s * e2x, yL = Cy - 0.5 * e1y + s * e2y;
+    double xD = Cx - 0.5 * e2x + s * e1x, yD = Cy - 0.5 * e2y + s * e1y;
+    double px = yp[2 * p], py = yp[2 * p + 1];
+    double c4 = 1.0 / (4.0 * kPi * mu);
+    for (int comp = 0; comp < 2; ++comp) {
+        double fx = comp == 0 ? 1.0 : 0.0, fy = comp == 0 ? 0.0 : 1.0;
+        double* col = A + (size_t)(comp * M + p) * R;
+        double ua, va, ub, vb;
+        // g1: velocity R - L
+        stokeslet_d(xL + e1x - px, yL + e1y - py, fx, fy, c4, ua, va);
+        stokeslet_d(xL - px, yL - py, fx, fy, c4, ub, vb);
+        col[l] = ua - ub;
+        col[m + l] = va - vb;
+        // g2: traction R - L, normal nu_L
+        traction_d(xL + e1x - px, yL + e1y - py, nl[0], nl[1], fx, fy, ua, va);
+        traction_d(xL - px, yL - py, nl[0], nl[1], fx, fy, ub, vb);
+        col[2 * m + l] = ua - ub;
+        col[3 * m + l] = va - vb;
+        // g3: velocity U - D
+        stokeslet_d(xD + e2x - px, yD + e2y - py, fx, fy, c4, ua, va);
+        stokeslet_d(xD - px, yD - py, fx, fy, c4, ub, vb);
+        col[4 * m + l] = ua - ub;
+        col[5 * m + l] = va - vb;
+        // g4: traction U - D, normal nu_D
+        traction_d(xD + e2x - px, yD + e2y - py, nd[0], nd[1], fx, fy, ua, va);
+        traction_d(xD - px, yD - py, nd[0], nd[1], fx, fy, ub, vb);
+        col[6 * m + l] = ua - ub;
+        col[7 * m + l] = va - vb;
+    }
+}
+
+__device__ inline double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; every thread receives the result.  red: >= 33 doubles.
+__device__ inline double block_sum(double v, double* red) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Householder QR of the stacked R x C matrix A = [Q; lam I] (column-major),
+// in place: the reflector v_k is stored in A[k:, k] (v_k[k] = A[k, k]),
+// beta[k] its scalar, rdiag[k] the diagonal of the triangular factor.
+// One CTA; the first Qrows rows hold Q on entry, the rest are filled here.
+__global__ void k_qr(double* __restrict__ A, int R, int C, int Qrows, double lam_rel,
+                     double* __restrict__ beta, double* __restrict__ rdiag) {
+    __shared__ double red[33];
+    int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    double ss = 0.0;
+    for (long long idx = tid; idx < (long long)Qrows * C; idx += nt) {
+        int i = (int)(idx % Qrows), j = (int)(idx / Qrows);
+        double a = A[i + (size_t)j * R];
+        ss += a * a;
+    }
+    double lam = lam_rel * sqrt(block_sum(ss, red));
+    int L = R - Qrows;
+    for (long long idx = tid; idx < (long long)L * C; idx += nt) {
+        int i = (int)(idx % L), j = (int)(idx / L);
+        A[Qrows + i + (size_t)j * R] = (i == j) ? lam : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < C; ++k) {
+        double* a = A + (size_t)k * R;
+        double s = 0.0;
+        for (int i = k + tid; i < R; i += nt) s += a[i] * a[i];
+        s = block_sum(s, red);
+        double akk = a[k];
+        double nrm = sqrt(s);
+        double alpha = akk > 0.0 ? -nrm : nrm;
+        double v0 = akk - alpha;
+        double vn2 = s - akk * akk + v0 * v0;
+        double bk = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            a[k] = v0;
+            beta[k] = bk;
+            rdiag[k] = alpha;
+        }
+        __syncthreads();
+        for (int j = k + 1 + warp; j < C; j += nw) {
+            double* aj = A + (size_t)j * R;
+            double d = 0.0;
+            for (int i = k + lane; i < R; i += 32) d += a[i] * aj[i];
+            d = warp_sum(d) * bk;
+            for (int i = k + lane; i < R; i += 32) aj[i] -= d * a[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Column c of P = first C rows of R^{-1} H_{C-1} ... H_0 e_c, c < Qrows.
+// P is C x Qrows, column-major.  Dynamic shared memory: R doubles.
+__global__ void k_form_P(const double* __restrict__ A, int R, int C, const double* __restrict__ beta,
+                         const double* __restrict__ rdiag, double* __restrict__ P) {
+    extern __shared__ double z[];
+    __shared__ double red[33];
+    int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < R; i += nt) z[i] = (i == c) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < C; ++k) {
+        const double* a = A + (size_t)k * R;
+        double d = 0.0;
+        for (int i = k + tid; i < R; i += nt) d += a[i] * z[i];
+        d = block_sum(d, red) * beta[k];
+        for (int i = k + tid; i < R; i += nt) z[i] -= d * a[i];
+        __syncthreads();
+    }
+    if (warp == 0) {
+        for (int r = C - 1; r >= 0; --r) {
+            double s = 0.0;
+            for (int j = r + 1 + lane; j < C; j += 32) s += A[r + (size_t)j * R] * z[j];
+            s = warp_sum(s);
+            if (lane == 0) z[r] = (z[r] - s) / rdiag[r];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int r = tid; r < C; r += nt) P[r + (size_t)c * C] = z[r];
+}
+
+int build_geometry(bie_ctx* c) {
+    int bs = 256, gs = (c->N + bs - 1) / bs;
+    k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->N, c->C[0], c->C[1], c->x, c->y, c->nx,
+                                        c->ny, c->w, c->kap, c->tgt32);
+    BIE_LAUNCH(c, "k_geometry");
+    return BIE_OK;
+}
+
+int build_proxy_fit(bie_ctx* c) {
+    int m = c->m, M = c->M;
+    int Qrows = 8 * m, C = 2 * M, R = Qrows + C;
+    int bs = 128, gs = (m * M + bs - 1) / bs;
+    k_build_Q<<<gs, bs, 0, c->stream>>>(c->A, R, m, M, c->gl_s, c->yp, c->e1[0], c->e1[1], c->e2[0],
+                                       c->e2[1], c->C[0], c->C[1], c->mu);
+    BIE_LAUNCH(c, "k_build_Q");
+    k_qr<<<1, 1024, 0, c->stream>>>(c->A, R, C, Qrows, c->opts.lam_rel, c->beta, c->beta + C);
+    BIE_LAUNCH(c, "k_qr");
+    k_form_P<<<Qrows, 256, R * sizeof(double), c->stream>>>(c->A, R, C, c->beta, c->beta + C, c->P);
+    BIE_LAUNCH(c, "k_form_P");
+    return BIE_OK;
+}
+
+}  // namespace bie

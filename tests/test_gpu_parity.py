@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+* FP64 operator: relative max-norm 1e-11.  The kernels and the oracle
+  evaluate the same sums in double precision in different orders; the
+  proxy fit (Tikhonov, lam = 1e-8 ||Q||_F) amplifies rounding in Q by at most
+  ~1e-8 / 1e-16 relative on the correction, which is a small part of T.
+* Mixed operator (single-precision pair sums): relative 2e-5 -- the
+  accumulated FP32 rounding of ~9N pair terms with rcp.approx (2 ulp).
+* Solutions: both sides solve to 1e-12 so that the difference is bounded by
+  cond(A) * 2e-12; the tests require 1e-9 relative (spec FP64 target).
+* v, omega, mu_eff: 1e-9 absolute (quantities of order 1).
+"""
+import numpy as np
+import pytest
+
+from oracle import bie as obie
+from paper_1912_04501_gb300 import workloads
+from tests.conftest import oracle_operator
+
+pytestmark = pytest.mark.gpu
+
+bie = pytest.importorskip("paper_1912_04501_gb300.bie")
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+CELLS = {
+    "config1": workloads.config1,
+    "three_ragged": lambda: workloads.small_cell(n_bodies=3, nodes=(lambda a, b: 50 + int(400 * a)), seed=5,
+                                                 e2=(0.3, 1.0)),
+    "five_tiles": lambda: workloads.small_cell(n_bodies=5, nodes=136, seed=7, phi=0.25, e2=(-0.2, 1.0)),
+}
+
+
+@pytest.fixture(scope="module", params=list(CELLS))
+def pair(request):
+    cell = CELLS[request.param]()
+    for bd in cell["bodies"]:
+        bd["n"] += bd["n"] % 2
+    ctx = bie.Context(cell, precision=bie.BIE_FP64, gmres_tol=1e-12)
+    op = oracle_operator(cell)
+    yield cell, ctx, op
+    ctx.close()
+
+
+def test_geometry(pair):
+    cell, ctx, op = pair
+    x, n, w, k = ctx.nodes()
+    s = op.s
+    np.testing.assert_allclose(x, s.x, atol=1e-14)
+    np.testing.assert_allclose(n, s.n, atol=1e-14)
+    np.testing.assert_allclose(w, s.w, rtol=1e-13)
+    np.testing.assert_allclose(k, s.kappa, rtol=1e-12)
+
+
+def test_apply_fp64(pair):
+    cell, ctx, op = pair
+    rng = np.random.default_rng(1)
+    for _ in range(2):
+        sigma = rng.standard_normal(2 * ctx.N)
+        y = ctx.apply(sigma, precision=bie.BIE_FP64)
+        ref = op.apply(sigma.reshape(-1, 2)).ravel()
+        assert _rel(y, ref) < 1e-11
+
+
+def test_apply_mixed(pair):
+    cell, ctx, op = pair
+    sigma = np.random.default_rng(2).standard_normal(2 * ctx.N)
+    y = ctx.apply(sigma, precision=bie.BIE_MIXED)
+    ref = op.apply(sigma.reshape(-1, 2)).ravel()
+    assert _rel(y, ref) < 2e-5
+
+
+def test_rhs(pair):
+    cell, ctx, op = pair
+    np.testing.assert_allclose(ctx.rhs(), op.rhs().ravel(), atol=1e-15)
+
+
+def test_apply_deterministic(pair):
+    cell, ctx, op = pair
+    sigma = np.random.default_rng(3).standard_normal(2 * ctx.N)
+    for prec in (bie.BIE_FP64, bie.BIE_MIXED):
+        a = ctx.apply(sigma, precision=prec)
+        b = ctx.apply(sigma, precision=prec)
+        assert np.array_equal(a, b)
+
+
+def test_solve_fp64_and_velocities(pair):
+    cell, ctx, op = pair
+    sig, info = ctx.solve()
+    assert info["rel_residual"] <= 1e-12
+    ref, _, res = obie.solve(op, tol=1e-12)
+    assert _rel(sig, ref.ravel()) < 1e-9
+    v, om, mu = ctx.velocities(sig)
+    v_ref, om_ref = op.body_velocities(ref)
+    np.testing.assert_allclose(v, v_ref, atol=1e-9)
+    np.testing.assert_allclose(om, om_ref, atol=1e-9)
+    assert abs(mu - op.mu_eff(ref)) < 1e-9
+
+
+def test_solve_mixed_refinement():
+    cell = CELLS["five_tiles"]()
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED, gmres_tol=1e-12)
+    op = oracle_operator(cell)
+    sig, info = ctx.solve()
+    assert info["rel_residual"] <= 1e-12
+    assert info["applies32"] > info["applies64"]
+    ref, _, _ = obie.solve(op, tol=1e-12)
+    assert _rel(sig, ref.ravel()) < 1e-9
+    ctx.close()
+
+
+def test_step_matches_oracle():
+    cell = workloads.config1()
+    cell["bodies"][0]["theta"] = 0.3
+    cell["bodies"][0]["xc"] = [0.6, 0.45]
+    ctx = bie.Context(cell, precision=bie.BIE_FP64, gmres_tol=1e-12)
+    from tests.conftest import oracle_suspension
+    s = oracle_suspension(cell)
+    kw = dict(n_proxy=16, proxy_radius=1.5, n_coll=16)
+    t = 0.0
+    dt = 0.05
+    mus_ref = []
+    for _ in range(3):
+        s, t, out = obie.euler_step(s, cell["e2"], t, dt, kw, tol=1e-12)
+        mus_ref.append(out["mu_eff"])
+    mus, info = ctx.step(dt, 3)
+    st = ctx.get_state()
+    np.testing.assert_allclose(mus, mus_ref, atol=1e-9)
+    np.testing.assert_allclose(st["xc"], s.xc, atol=1e-9)
+    np.testing.assert_allclose(st["theta"], [b["theta"] for b in s.bodies], atol=1e-9)
+    np.testing.assert_allclose(st["e2"], s.e2, atol=1e-15)
+    ctx.close()
+
+
+def test_checkpoint_resume_bitwise():
+    cell = CELLS["three_ragged"]()
+    for bd in cell["bodies"]:
+        bd["n"] += bd["n"] % 2
+    a = bie.Context(cell, precision=bie.BIE_MIXED)
+    a.step(1e-3, 2)
+    st = a.get_state()
+    mu_a, _ = a.step(1e-3, 1)
+    after_a = a.get_state()
+    b = bie.Context(cell, precision=bie.BIE_MIXED)
+    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"])
+    mu_b, _ = b.step(1e-3, 1)
+    after_b = b.get_state()
+    assert mu_a[0] == mu_b[0]
+    assert np.array_equal(after_a["xc"], after_b["xc"]) and np.array_equal(after_a["sigma"], after_b["sigma"])
+    a.close()
+    b.close()
+
+
+def test_device_pointers_match_host():
+    torch = pytest.importorskip("torch")
+    cell = workloads.config1()
+    ctx = bie.Context(cell, precision=bie.BIE_FP64)
+    sigma = np.random.default_rng(4).standard_normal(2 * ctx.N)
+    host = ctx.apply(sigma, precision=bie.BIE_FP64)
+    ds = torch.tensor(sigma, dtype=torch.float64, device="cuda")
+    do = torch.empty_like(ds)
+    torch.cuda.synchronize()
+    ctx.apply(ds, do, precision=bie.BIE_FP64)
+    assert np.array_equal(do.cpu().numpy(), host)
+    ctx.close()
+
+
+def test_invalid_inputs_rejected():
+    cell = workloads.config1()
+    bad = dict(cell, bodies=[dict(cell["bodies"][0], n=7)])
+    with pytest.raises(bie.BieError) as e:
+        bie.Context(bad)
+    assert e.value.code == bie.BIE_EINVAL
+    ctx = bie.Context(cell)
+    with pytest.raises(bie.BieError):
+        ctx.apply(np.zeros(2 * ctx.N), precision=7)
+    ctx.close()
+
+
+def test_full_size_config2_sampled():
+    """configs[1]-sized cell (25 ellipses, 6400 nodes): FP64 and mixed apply
+    at 48 sampled targets against the oracle evaluated there alone."""
+    cell = workloads.config2()
+    ctx = bie.Context(cell, precision=bie.BIE_FP64)
+    op = oracle_operator(cell)
+    rng = np.random.default_rng(6)
+    sigma = rng.standard_normal(2 * ctx.N)
+    idx = np.sort(rng.choice(ctx.N, 48, replace=False))
+    ref = op.apply(sigma.reshape(-1, 2), targets=idx)
+    y64 = ctx.apply(sigma, precision=bie.BIE_FP64).reshape(-1, 2)[idx]
+    y32 = ctx.apply(sigma, precision=bie.BIE_MIXED).reshape(-1, 2)[idx]
+    assert _rel(y64, ref) < 1e-11
+    assert _rel(y32, ref) < 5e-5
+    ctx.close()

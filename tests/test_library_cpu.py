@@ -1,0 +1,62 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol declared in include/bie.h, and rejects invalid input before touching a
+GPU.  No compute call is made."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1912_04501_gb300 import _build, bie
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return bie.library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bie.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bie_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(bie.exported_symbols()) == names
+
+
+def test_default_opts(lib):
+    o = bie.bie_default_opts()
+    assert o.precision == bie.BIE_MIXED and o.n_proxy == 48 and o.n_coll == 24
+    assert o.gmres_tol == 1e-10 and o.lam_rel == 1e-8
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda c: c["bodies"][0].update(n=7),
+    lambda c: c["bodies"][0].update(n=4),
+    lambda c: c["bodies"][0].update(a=-0.1),
+    lambda c: c.update(e2=[2.0, 0.0]),
+    lambda c: c.update(mu=0.0),
+])
+def test_invalid_input_rejected_without_gpu(lib, mutate):
+    from paper_1912_04501_gb300 import workloads
+    cell = workloads.config1()
+    mutate(cell)
+    with pytest.raises(bie.BieError) as e:
+        bie.Context(cell)
+    assert e.value.code == bie.BIE_EINVAL
+
+
+def test_null_arguments(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.bie_init(ctypes.byref(h), None, 1.0, 1.0, 1, None, None) == bie.BIE_EINVAL
+    assert lib.bie_apply(None, None, None, 0, 0) == bie.BIE_EINVAL
+    assert lib.bie_size(None, None, None) == bie.BIE_EINVAL
