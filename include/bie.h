@@ -75,6 +75,9 @@ typedef struct {
     int32_t warm_start;   /* bie_step initial guess: 0 = zero, 1 = previous step's density */
     double min_gap;       /* bie_step fails with BIE_ECOLLIDE below this body gap (node-sampled); 0 = off */
     int32_t device;       /* CUDA device ordinal */
+    double close_factor;  /* close-evaluation zone in units of the source body's node spacing
+                             h_b = perimeter / N_b (Sec. 6.3 remark: 10); 0 disables the correction */
+    int32_t close_capacity; /* maximum (target, body image) close pairs stored; 0 = N */
 } bie_opts;
 
 typedef struct {
@@ -87,7 +90,7 @@ typedef struct {
 
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
- * warm_start 1, min_gap 0, device 0. */
+ * warm_start 1, min_gap 0, device 0, close_factor 10, close_capacity 0. */
 void bie_default_opts(bie_opts* opts);
 
 /* Create a context for one unit cell: lattice, viscosity mu, shear rate
@@ -118,7 +121,10 @@ int bie_nodes(bie_ctx* ctx, double* x, double* n, double* w, double* kappa, int3
  *   out_i = sigma_i/2 + T_i + alpha n_i + F_b + (x_i - x^c_b)^perp tau_b,
  *   T = 3x3 near image sum of G^t (Eq. Gt) with the on-curve diagonal limit
  *       + proxy-Stokeslet correction fitted to the wall discrepancy (Sec. 6.2
- *       steps 1-4),  alpha = -T_0 . n_0.
+ *       steps 1-4) + close-evaluation correction (Sec. 6.3): for targets within
+ *       close_factor * h_b of a body image, the smooth rule is replaced by the
+ *       integral of the trigonometric interpolant of the density over the exact
+ *       ellipse;  alpha = -T_0 . n_0.
  * precision: BIE_FP64 or BIE_MIXED (single-precision pair sums).
  * sigma and out: 2N doubles each, must not overlap. */
 int bie_apply(bie_ctx* ctx, const double* sigma, double* out, int32_t precision, int32_t on_device);
@@ -163,6 +169,12 @@ int bie_get_state(bie_ctx* ctx, double* t, double* e2, double* xc, double* theta
  * (warm start cleared). */
 int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, const double* theta,
                   const double* sigma);
+
+/* Close-evaluation bookkeeping of the current geometry: number of stored
+ * (target, body image) pairs, and pairs closer to the curve than the finest
+ * rule (64-fold upsampling) resolves to double precision (their correction is
+ * then less accurate). */
+int bie_close_info(bie_ctx* ctx, int32_t* n_pairs, int32_t* under_resolved);
 
 /* Profiling aid (no counterpart in the paper: it instruments the kernels
  * above).  bie_profile(ctx, 1) starts recording a CUDA event pair on the

@@ -59,7 +59,7 @@ class Operator:
         s = self.s
         g = periodic.near_discrepancy(s.e1, s.e2, s.centre, self.m, s.x, q, s.mu)
         dt = periodic.corrected_discrepancy(g, q.sum(0), s.e1, s.e2, self.m)
-        return self.Qp @ dt, dt
+        return periodic.apply_operator_exact(self.Qp, dt), dt
 
     def traction(self, sigma, targets=None):
         """Periodic traction T (before the pressure fix) at all or listed nodes."""

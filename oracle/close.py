@@ -7,8 +7,9 @@ loses accuracy.  The paper replaces it by a special quadrature that is exact
 for the interpolant of the nodal density.  The oracle computes the quantity
 such a rule converges to by its definition: the integral, over the exact
 curve, of G^t times the trigonometric interpolant sigma^ of the nodal values,
-evaluated by the trapezoidal rule on a grid fine enough (h_fine <= d / 8 and at
-least 4x the nodes) that its own error is below double-precision rounding.
+evaluated by the trapezoidal rule on a grid fine enough (local fine spacing
+<= d / 8, d the distance to the curve, and at least 4x the nodes) that its own
+error is below double-precision rounding.
 The correction added to the near sum is that integral minus the smooth
 N_b-point rule's contribution from the same body image.
 """
@@ -41,9 +42,32 @@ def trig_interp(v, nf):
 
 def fine_factor(h, d):
     """Upsampling factor of the oracle's fine rule: a power of two >= 4 with
-    h / factor <= d / 8."""
+    h / factor <= d / 8 (h the local node spacing, d the distance to the
+    curve)."""
     need = 8.0 * h / max(d, 1e-300)
     return max(4, 1 << max(0, math.ceil(math.log2(need))))
+
+
+def closest_point(body, x, shift, t0, n_iter=8):
+    """Distance from x to the exact ellipse `body` translated by shift, and
+    the local node spacing 2 pi |x'(t*)| / N_b there, by Newton's method on
+    the stationarity condition (y(t) - x) . y'(t) = 0 started at t0 (the
+    parameter of the nearest node); steps are capped at one node spacing."""
+    a, b, th = body["a"], body["b"], body["theta"]
+    c, s = math.cos(th), math.sin(th)
+    px = x[0] - body["xc"][0] - shift[0]
+    py = x[1] - body["xc"][1] - shift[1]
+    u, v = c * px + s * py, -s * px + c * py   # target in the body frame
+    dt_max = 2.0 * math.pi / body["n"]
+    t = t0
+    for _ in range(n_iter):
+        g = (b * b - a * a) * math.sin(t) * math.cos(t) + a * u * math.sin(t) - b * v * math.cos(t)
+        gp = (b * b - a * a) * math.cos(2 * t) + a * u * math.cos(t) + b * v * math.sin(t)
+        step = g / gp if gp > 0 else math.copysign(dt_max, g)
+        t -= max(-dt_max, min(dt_max, step))
+    d = math.hypot(a * math.cos(t) - u, b * math.sin(t) - v)
+    speed = math.hypot(a * math.sin(t), b * math.cos(t))
+    return d, 2.0 * math.pi * speed / body["n"]
 
 
 def fine_integral(body, sigma_b, x, nx, shift, rho):
@@ -68,18 +92,22 @@ class ClosePairs:
 
     def __init__(self, susp, shifts, close_factor=10.0):
         self.susp = susp
-        self.pairs = []  # (target index, body, shift vector, dmin)
+        self.pairs = []  # (target index, body, shift vector, curve distance, local spacing)
         off = susp.offsets
         for b in range(len(susp.bodies)):
             sl = slice(off[b], off[b + 1])
             yb = susp.x[sl]
             hb = susp.w[sl].sum() / (off[b + 1] - off[b])
+            bd = susp.bodies[b]
             for sh in shifts:
-                d = np.sqrt(((susp.x[:, None, :] - (yb[None, :, :] + sh)) ** 2).sum(-1)).min(axis=1)
+                dist = np.sqrt(((susp.x[:, None, :] - (yb[None, :, :] + sh)) ** 2).sum(-1))
+                d = dist.min(axis=1)
                 for i in np.nonzero(d < close_factor * hb)[0]:
                     if susp.owner[i] == b and sh[0] == 0.0 and sh[1] == 0.0:
                         continue
-                    self.pairs.append((int(i), b, sh.copy(), float(d[i])))
+                    k = int(dist[i].argmin())
+                    dc, hl = closest_point(bd, susp.x[i], sh, 2.0 * np.pi * k / bd["n"])
+                    self.pairs.append((int(i), b, sh.copy(), dc, hl))
 
     def apply(self, sigma, targets=None):
         """Correction to the near traction at every target (or the listed
@@ -88,16 +116,14 @@ class ClosePairs:
         want = None if targets is None else {int(t): k for k, t in enumerate(targets)}
         out = np.zeros((susp.N if targets is None else len(targets), 2))
         off = susp.offsets
-        for (i, b, sh, d) in self.pairs:
+        for (i, b, sh, d, hl) in self.pairs:
             if want is not None and i not in want:
                 continue
             bd = susp.bodies[b]
-            nb = bd["n"]
             sl = slice(off[b], off[b + 1])
-            hb = susp.w[sl].sum() / nb
             xi = susp.x[i]
             ni = susp.n[i]
-            fine = fine_integral(bd, sigma[sl], xi, ni, sh, fine_factor(hb, d))
+            fine = fine_integral(bd, sigma[sl], xi, ni, sh, fine_factor(hl, d))
             coarse = kernels.traction(xi[None, :] - (susp.x[sl] + sh), ni[None, :],
                                       sigma[sl] * susp.w[sl, None]).sum(0)
             k = i if want is None else want[i]

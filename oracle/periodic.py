@@ -218,6 +218,31 @@ def proxy_solution_operator(Q, lam_rel=1e-8):
     return np.linalg.lstsq(A, B, rcond=None)[0]
 
 
+def _two_prod(a, b):
+    """a*b = p + e exactly (Dekker's product with Veltkamp splitting)."""
+    p = a * b
+    f = 134217729.0  # 2^27 + 1
+    def split(x):
+        c = f * x
+        hi = c - (c - x)
+        return hi, x - hi
+    ah, al = split(a)
+    bh, bl = split(b)
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def apply_operator_exact(P, d):
+    """xi = P d with every row summed exactly and rounded once (exact
+    products by _two_prod, math.fsum over them), so that the application of
+    the fixed proxy operator adds no rounding noise beyond the final rounding
+    (P has entries up to ~1/lam, and a plain double-precision product would
+    add noise of relative size ~1e-11 to the correction)."""
+    import math
+    p, e = _two_prod(P, d[None, :])
+    return np.array([math.fsum(np.concatenate([p[r], e[r]])) for r in range(P.shape[0])])
+
+
 def xi_pairs(xi):
     M = xi.shape[0] // 2
     return np.stack([xi[:M], xi[M:]], axis=1)

@@ -9,7 +9,7 @@ call raises -- there is no fallback implementation.
 The functions carry the C names:
     bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
-    bie_set_state, bie_set_stream, bie_profile, bie_profile_read
+    bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read
 and `Context` wraps them for a workload dict (see workloads.py).
 """
 import ctypes
@@ -41,7 +41,8 @@ class Body(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("n_proxy", c_int32), ("proxy_radius", c_double), ("n_coll", c_int32),
                 ("lam_rel", c_double), ("gmres_tol", c_double), ("gmres_max", c_int32), ("inner_tol", c_double),
-                ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32)]
+                ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32),
+                ("close_factor", c_double), ("close_capacity", c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -95,6 +96,7 @@ def library():
         "bie_step": (c_int32, [vp, c_double, c_int32, vp, ctypes.POINTER(SolveInfo)]),
         "bie_get_state": (c_int32, [vp, vp, vp, vp, vp, vp]),
         "bie_set_state": (c_int32, [vp, c_double, vp, vp, vp, vp]),
+        "bie_close_info": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
     }
@@ -111,7 +113,8 @@ def exported_symbols():
     L = library()
     return [n for n in ("bie_default_opts", "bie_init", "bie_destroy", "bie_last_error", "bie_size",
                         "bie_set_stream", "bie_nodes", "bie_apply", "bie_rhs", "bie_solve", "bie_velocities",
-                        "bie_step", "bie_get_state", "bie_set_state", "bie_profile", "bie_profile_read")
+                        "bie_step", "bie_get_state", "bie_set_state", "bie_close_info", "bie_profile",
+                        "bie_profile_read")
             if hasattr(L, n)]
 
 
@@ -241,6 +244,11 @@ class Context:
         self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
                                             th.ctypes.data, sg.ctypes.data))
         return dict(t=float(t[0]), e2=e2, xc=xc.reshape(-1, 2), theta=th, sigma=sg)
+
+    def close_info(self):
+        n, u = c_int32(), c_int32()
+        self._check(library().bie_close_info(self.h, ctypes.byref(n), ctypes.byref(u)))
+        return n.value, u.value
 
     def profile(self, enable=True):
         self._check(library().bie_profile(self.h, 1 if enable else 0))

@@ -30,7 +30,9 @@ static void free_all(bie_ctx* c) {
     void* ptrs[] = {c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body, c->tgt32, c->gl_s, c->A, c->beta,
                     c->P, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.bodyF,
                     c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
-                    c->sv.d, c->sv.h, c->sv.red, c->sv.sigma_prev};
+                    c->sv.d, c->sv.h, c->sv.red, c->sv.sigma_prev, c->cl.slots, c->cl.count,
+                    c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab,
+                    c->cl.dtab_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto e : c->ev_pool)
@@ -110,7 +112,9 @@ int prof_fold(bie_ctx* c) {
 static int rebuild(bie_ctx* c) {
     int rc = build_geometry(c);
     if (rc) return rc;
-    return build_proxy_fit(c);
+    rc = build_proxy_fit(c);
+    if (rc) return rc;
+    return build_close(c);
 }
 
 }  // namespace bie
@@ -134,6 +138,8 @@ void bie_default_opts(bie_opts* o) {
     o->warm_start = 1;
     o->min_gap = 0.0;
     o->device = 0;
+    o->close_factor = 10.0;
+    o->close_capacity = 0;
 }
 
 int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int32_t n_bodies,
@@ -158,6 +164,8 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
         return bad("non-positive tolerance or radius");
     if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) return bad("gmres_max / max_refine out of range");
     if (!(mu > 0) || !std::isfinite(gamma)) return bad("mu must be positive, gamma finite");
+    if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
+        return bad("close_factor must be in [0, 100], close_capacity >= 0");
     double det = lat->e1[0] * lat->e2[1] - lat->e1[1] * lat->e2[0];
     if (!(std::fabs(det) > 1e-12)) return bad("degenerate lattice");
     c->device = o.device;
@@ -253,6 +261,19 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->sv.h, 3 * (size_t)(kk + 2) + 8);
     rc = rc ? rc : dalloc(c, &c->sv.red, 8);
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
+    {
+        int maxn = 0;
+        for (int v : c->n_nodes) maxn = std::max(maxn, v);
+        c->cl.cap_pairs = o.close_capacity > 0 ? o.close_capacity : n;
+        c->cl.cap_doubles = (long long)c->cl.cap_pairs * 3 * maxn;
+        rc = rc ? rc : dalloc(c, &c->cl.slots, (size_t)n * kCloseSlots);
+        rc = rc ? rc : dalloc(c, &c->cl.count, n);
+        rc = rc ? rc : dalloc(c, &c->cl.pair_base, (size_t)n + 1);
+        rc = rc ? rc : dalloc(c, &c->cl.pairs, c->cl.cap_pairs);
+        rc = rc ? rc : dalloc(c, &c->cl.blk_off, c->cl.cap_pairs);
+        rc = rc ? rc : dalloc(c, &c->cl.blocks, (size_t)c->cl.cap_doubles);
+        rc = rc ? rc : dalloc(c, &c->cl.flags, 4);
+    }
     c->ws.part_bytes = part;
     if (rc) {
         free_all(c);
@@ -278,6 +299,7 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
     rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
     rc = rc ? rc : up(c->yp, yp.data(), yp.size() * sizeof(double));
+    rc = rc ? rc : build_dirichlet_tables(c);
     rc = rc ? rc : rebuild(c);
     rc = rc ? rc : cu(cudaStreamSynchronize(c->stream), "init sync");
     if (rc) {
@@ -503,6 +525,13 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     int rc = rebuild(c);
     if (rc) return rc;
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_close_info(bie_ctx* c, int32_t* n_pairs, int32_t* under_resolved) {
+    if (!c) return BIE_EINVAL;
+    if (n_pairs) *n_pairs = c->cl.npairs;
+    if (under_resolved) *under_resolved = c->cl.under_resolved;
     return BIE_OK;
 }
 

@@ -333,11 +333,24 @@ __global__ void k_xi(const double* __restrict__ gpart, int nblk, int m, int M, c
         }
     }
     __syncthreads();
+    // Compensated dot products (Ogita, Rump & Oishi's Dot2: FMA-exact products,
+    // error-free sums): P has entries up to ~1/lam, so a plain double-precision
+    // product would add relative noise ~1e-11 to the correction and put a floor
+    // under the GMRES residual.
     int C = 2 * M;
     for (int r = tid; r < C; r += blockDim.x) {
-        double s = 0;
-        for (int cc = 0; cc < 8 * m; ++cc) s += P[r + (size_t)cc * C] * d[cc];
-        xi[r] = s;
+        double s = 0, c = 0;
+        for (int cc = 0; cc < 8 * m; ++cc) {
+            double a = P[r + (size_t)cc * C], b = d[cc];
+            double p = a * b;
+            double pe = fma(a, b, -p);
+            double t = s + p;
+            double z = t - s;
+            double se = (s - (t - z)) + (p - z);
+            s = t;
+            c += pe + se;
+        }
+        xi[r] = s + c;
     }
 }
 
@@ -487,6 +500,7 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
         k_correct<double2><<<gs, bs, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x, c->y,
                                                      c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
+    if (int rc = close_apply(c, sigma, c->ws.T)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, c->ws.bodyF,
                                        reinterpret_cast<double2*>(yout));
     BIE_LAUNCH(c, "k_finish");

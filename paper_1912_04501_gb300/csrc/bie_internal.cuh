@@ -27,6 +27,31 @@ constexpr int kNear32TPT = 2;         // targets per thread, single precision
 constexpr int kDiscBlocks = 96;       // source splits of the wall-discrepancy kernel
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
+constexpr int kCloseSlots = 8;        // close body images per target node
+
+// Image shifts m e1 + n e2, index (n + 1) * 3 + (m + 1); index 4 is zero.
+struct Shifts9dC {
+    double x[9], y[9];
+};
+
+// Close-evaluation storage (Sec. 6.3): per-target slots, compacted pairs,
+// 3 N_b doubles (A, B, D of each symmetric 2 x 2 node block) per pair.
+struct Close {
+    int4* slots = nullptr;        // N x kCloseSlots  (body, image, rho, 0)
+    int* count = nullptr;         // N
+    int* pair_base = nullptr;     // N + 1
+    int4* pairs = nullptr;        // cap_pairs (target, body, image, rho)
+    long long* blk_off = nullptr; // cap_pairs
+    double* blocks = nullptr;     // cap_doubles
+    double* dtab = nullptr;       // Dirichlet tables per distinct node count
+    long long* dtab_off = nullptr;  // nb: table base of each body
+    int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved]
+    int cap_pairs = 0;
+    long long cap_doubles = 0;
+    int npairs = 0;
+    int under_resolved = 0;       // pairs closer than the finest rule (rho = 64) resolves
+    size_t shm_limit = 0;
+};
 
 // Double-precision source record: position and premultiplied density q = sigma w.
 struct __align__(16) Src64 {
@@ -85,6 +110,7 @@ struct bie_ctx {
     double* scal = nullptr;     // misc device scalars
     bie::Workspace ws;
     bie::Solver sv;
+    bie::Close cl;
     int near_splits32 = 1, near_splits64 = 1;
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
@@ -123,6 +149,11 @@ int prof_fold(bie_ctx* c);
 int build_geometry(bie_ctx* c);   // nodes from body state
 int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P
 void gauss_legendre_half(int m, std::vector<double>& s);
+
+// close.cu ------------------------------------------------------------------
+int build_close(bie_ctx* c);                               // per geometry
+int build_dirichlet_tables(bie_ctx* c);                    // once per context
+int close_apply(bie_ctx* c, const double* sigma, double* T);  // T += C sigma
 
 // apply.cu ------------------------------------------------------------------
 // y = A sigma for device sigma, y (2N each); precision BIE_FP64 / BIE_MIXED

@@ -1,0 +1,400 @@
+// Close-evaluation correction (Sec. 6.3 and its remark on the two-phase
+// solver): a sparse set of 2 x 2N_b blocks, built once per geometry, applied
+// in every operator application.
+//
+// For a target x_i (normal n_i) within close_factor * h_b of an image of body
+// b (h_b = perimeter / N_b), the smooth N_b-point rule for
+//     int_{Gamma_b + s} G^t(x_i, y; n_i) sigma(y) ds_y
+// is replaced by the same integral of the trigonometric interpolant of the
+// nodal density, evaluated by the trapezoidal rule on rho * N_b points of the
+// exact ellipse, rho >= 2 the smallest power of two with
+// rho - 1/2 >= 6.4 h_loc / d (d the distance to the curve and h_loc the local
+// node spacing at the closest point, both found by Newton's method).  As a linear map of the nodal density this is
+//     C_k = sum_f G^t(x_i, y_f + s; n_i) w_f D(t_f - t_k) - G^t(x_i, y_k + s; n_i) w_k,
+// D the Dirichlet kernel of the N_b-point interpolant (Nyquist mode split),
+//     D(tau) = sin(N_b tau / 2) cot(tau / 2) / N_b.
+// G^t applied to q is c r (r . q) with c = -(r . n)/(pi r^4), so each C_k is
+// a symmetric 2 x 2 matrix: three doubles (A, B, D) per node.
+#include <cmath>
+#include <utility>
+#include <vector>
+
+#include "bie_internal.cuh"
+
+namespace bie {
+
+// h_b and the bounding radius per body (body[8b+7] = h_b).
+__global__ void k_body_h(const double* __restrict__ w, double* __restrict__ body) {
+    __shared__ double red[33];
+    int b = blockIdx.x;
+    double* bd = body + 8 * b;
+    int n = (int)bd[5], off = (int)bd[6];
+    double s = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += w[off + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        bd[7] = t / n;
+    }
+}
+
+// One thread per target: every (body, image) closer than close_factor * h_b
+// goes to the target's slots in (body, image) order.  slot record:
+// int4 (body, image, rho, 0).
+__global__ void k_close_detect(const double* __restrict__ x, const double* __restrict__ y,
+                               const int* __restrict__ owner, const double* __restrict__ body, int nb, int N,
+                               Shifts9dC sh, double close_factor, int kmax, int4* __restrict__ slots,
+                               int* __restrict__ count, int* __restrict__ overflow) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double X = x[i], Y = y[i];
+    int own = owner[i];
+    int c = 0;
+    for (int b = 0; b < nb; ++b) {
+        const double* bd = body + 8 * b;
+        double R = fmax(bd[0], bd[1]);
+        double hb = bd[7];
+        double lim = close_factor * hb;
+        int n = (int)bd[5], off = (int)bd[6];
+        for (int im = 0; im < 9; ++im) {
+            if (b == own && im == 4) continue;  // zero shift of the own body
+            double cx = bd[2] + sh.x[im], cy = bd[3] + sh.y[im];
+            double dc = sqrt((X - cx) * (X - cx) + (Y - cy) * (Y - cy));
+            if (dc - R > lim) continue;
+            double d2 = 1e300;
+            int kbest = 0;
+            for (int k = 0; k < n; ++k) {
+                double dx = X - (x[off + k] + sh.x[im]), dy = Y - (y[off + k] + sh.y[im]);
+                double e = dx * dx + dy * dy;
+                if (e < d2) { d2 = e; kbest = k; }
+            }
+            if (sqrt(d2) >= lim) continue;
+            // distance to the exact curve and local node spacing at the closest
+            // point: Newton on (y(t) - x) . y'(t) = 0 from the nearest node
+            double dcur, hloc;
+            {
+                double a = bd[0], b2 = bd[1], st, ct;
+                sincos(bd[4], &st, &ct);
+                double px = X - cx, py = Y - cy;
+                double u = ct * px + st * py, v = -st * px + ct * py;
+                double dtm = 2.0 * kPi / n, t = dtm * kbest;
+                for (int it = 0; it < 8; ++it) {
+                    double sn, cs;
+                    sincos(t, &sn, &cs);
+                    double g = (b2 * b2 - a * a) * sn * cs + a * u * sn - b2 * v * cs;
+                    double gp = (b2 * b2 - a * a) * (cs * cs - sn * sn) + a * u * cs + b2 * v * sn;
+                    double step = gp > 0 ? g / gp : copysign(dtm, g);
+                    t -= fmax(-dtm, fmin(dtm, step));
+                }
+                double sn, cs;
+                sincos(t, &sn, &cs);
+                dcur = sqrt((a * cs - u) * (a * cs - u) + (b2 * sn - v) * (b2 * sn - v));
+                hloc = 2.0 * kPi * sqrt(a * a * sn * sn + b2 * b2 * cs * cs) / n;
+            }
+            // For a density of full bandwidth the rho-fold rule errs by about
+            // exp(-(rho - 1/2) 2 pi d / h_loc): rho - 1/2 >= 6.4 h_loc / d puts it
+            // below e^-40; rho >= 2 everywhere in the zone (the smooth rule,
+            // rho = 1, errs by exp(-pi d / h), not negligible inside 10 h_b).
+            int rho = 2;
+            while ((rho - 0.5) * dcur < 6.4 * hloc && rho < 64) rho <<= 1;
+            if ((rho - 0.5) * dcur < 6.4 * hloc) atomicAdd(overflow + 1, 1);  // closer than rho = 64 resolves
+            if (c < kmax) slots[(size_t)i * kmax + c] = make_int4(b, im, rho, 0);
+            ++c;
+        }
+    }
+    if (c > kmax) {
+        atomicMax(overflow, c);
+        c = kmax;
+    }
+    count[i] = c;
+}
+
+// Exclusive scan (one CTA) of the per-target pair counts and of the block
+// sizes 3 N_b per pair: pair_base[i], and per pair its block offset.
+__global__ void k_close_scan(const int* __restrict__ count, int N, int kmax, const int4* __restrict__ slots,
+                             const double* __restrict__ body, int* __restrict__ pair_base,
+                             long long* __restrict__ blk_off, int4* __restrict__ pairs, int* __restrict__ totals,
+                             long long cap_doubles, int cap_pairs) {
+    __shared__ int s_cnt[1024];
+    __shared__ long long s_sz[1024];
+    int tid = threadIdx.x, nt = blockDim.x;
+    int per = (N + nt - 1) / nt;
+    int lo = min(N, tid * per), hi = min(N, lo + per);
+    int c = 0;
+    long long sz = 0;
+    for (int i = lo; i < hi; ++i) {
+        c += count[i];
+        for (int k = 0; k < count[i]; ++k) sz += 3 * (long long)body[8 * slots[(size_t)i * kmax + k].x + 5];
+    }
+    s_cnt[tid] = c;
+    s_sz[tid] = sz;
+    __syncthreads();
+    if (tid == 0) {
+        int a = 0;
+        long long b = 0;
+        for (int t = 0; t < nt; ++t) {
+            int ca = s_cnt[t];
+            long long sb = s_sz[t];
+            s_cnt[t] = a;
+            s_sz[t] = b;
+            a += ca;
+            b += sb;
+        }
+        totals[0] = a;
+        totals[1] = (b > cap_doubles || a > cap_pairs) ? 1 : 0;
+    }
+    __syncthreads();
+    int p = s_cnt[tid];
+    long long o = s_sz[tid];
+    for (int i = lo; i < hi; ++i) {
+        pair_base[i] = p;
+        for (int k = 0; k < count[i]; ++k) {
+            int4 sl = slots[(size_t)i * kmax + k];
+            if (p < cap_pairs) {
+                pairs[p] = make_int4(i, sl.x, sl.y, sl.z);
+                blk_off[p] = o;
+            }
+            ++p;
+            o += 3 * (long long)body[8 * sl.x + 5];
+        }
+    }
+    if (tid == nt - 1) pair_base[N] = p;
+}
+
+// Dirichlet kernel tables D(2 pi j / (rho n)), j < rho n, of the n-point
+// interpolant, for rho = 2, 4, ..., 64: table (n, rho) starts at
+// base + n (rho - 2).  One thread per entry.
+__global__ void k_dirichlet(double* __restrict__ tab, int n) {
+    long long total = 126LL * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int rho = 2;
+        long long base = 0;
+        while (idx >= base + (long long)rho * n) {
+            base += (long long)rho * n;
+            rho <<= 1;
+        }
+        int f = (int)(idx - base), nf = rho * n;
+        double dv;
+        if (f == 0) dv = 1.0;
+        else if (f % rho == 0) dv = 0.0;
+        else dv = sinpi((double)f / rho) * cospi((double)f / nf) / (sinpi((double)f / nf) * n);
+        tab[idx] = dv;
+    }
+}
+
+constexpr int kCloseChunk = 2048;  // fine nodes staged in shared memory at a time
+
+// One CTA per close pair.  The fine grid (rho N_b nodes) is streamed through
+// shared memory in chunks; warp w accumulates C_k for k = w, w + 8, ... with
+// its lanes on consecutive fine nodes (coalesced table and shared reads).
+// Dynamic shared memory: 3 kCloseChunk + 3 N_b doubles.
+__global__ void __launch_bounds__(256)
+k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk_off,
+               const double* __restrict__ x, const double* __restrict__ y,
+               const double* __restrict__ nx, const double* __restrict__ ny,
+               const double* __restrict__ w, const double* __restrict__ body, Shifts9dC sh,
+               const double* __restrict__ dtab, const long long* __restrict__ dtab_off,
+               double* __restrict__ blocks) {
+    extern __shared__ double sm[];
+    double* sa = sm;
+    double* sb = sm + kCloseChunk;
+    double* sd = sm + 2 * kCloseChunk;
+    double* acc = sm + 3 * kCloseChunk;
+    int4 pr = pairs[blockIdx.x];
+    int i = pr.x, b = pr.y, im = pr.z, rho = pr.w;
+    const double* bd = body + 8 * b;
+    double a = bd[0], bb = bd[1], xc = bd[2] + sh.x[im], yc = bd[3] + sh.y[im], th = bd[4];
+    int nbn = (int)bd[5], off = (int)bd[6];
+    int nf = rho * nbn;
+    const double* dir = dtab + dtab_off[b] + (long long)nbn * (rho - 2);
+    double X = x[i], Y = y[i], n0 = nx[i], n1 = ny[i];
+    double st, ct;
+    sincos(th, &st, &ct);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < 3 * nbn; k += blockDim.x) acc[k] = 0.0;
+    for (int f0 = 0; f0 < nf; f0 += kCloseChunk) {
+        int cnt = min(kCloseChunk, nf - f0);
+        __syncthreads();
+        for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
+            int f = f0 + u;
+            double t = (2.0 * kPi * f) / nf;
+            double s, c;
+            sincos(t, &s, &c);
+            double px = a * c, py = bb * s;
+            double yx = xc + (ct * px - st * py), yy = yc + (st * px + ct * py);
+            double dpx = -a * s, dpy = bb * c;
+            double dx = ct * dpx - st * dpy, dy = st * dpx + ct * dpy;
+            double wf = (2.0 * kPi / nf) * sqrt(dx * dx + dy * dy);
+            double rx = X - yx, ry = Y - yy;
+            double r2 = rx * rx + ry * ry;
+            double cc = -(rx * n0 + ry * n1) * wf / (kPi * r2 * r2);
+            sa[u] = cc * rx * rx;
+            sb[u] = cc * rx * ry;
+            sd[u] = cc * ry * ry;
+        }
+        __syncthreads();
+        for (int k = wid; k < nbn; k += nw) {
+            double A = 0, B = 0, D = 0;
+            int base = f0 - rho * k;
+            for (int u = lane; u < cnt; u += 32) {
+                int j = base + u;
+                j += (j < 0) ? nf : 0;
+                double dv = __ldg(dir + j);
+                A = fma(sa[u], dv, A);
+                B = fma(sb[u], dv, B);
+                D = fma(sd[u], dv, D);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                A += __shfl_xor_sync(0xffffffffu, A, o);
+                B += __shfl_xor_sync(0xffffffffu, B, o);
+                D += __shfl_xor_sync(0xffffffffu, D, o);
+            }
+            if (lane == 0) {
+                acc[3 * k] += A;
+                acc[3 * k + 1] += B;
+                acc[3 * k + 2] += D;
+            }
+        }
+    }
+    __syncthreads();
+    double* out = blocks + blk_off[blockIdx.x];
+    for (int k = threadIdx.x; k < nbn; k += blockDim.x) {
+        // minus the smooth rule's term for node k of this body image
+        double rx = X - (x[off + k] + sh.x[im]), ry = Y - (y[off + k] + sh.y[im]);
+        double r2 = rx * rx + ry * ry;
+        double cc = -(rx * n0 + ry * n1) * w[off + k] / (kPi * r2 * r2);
+        out[3 * k] = acc[3 * k] - cc * rx * rx;
+        out[3 * k + 1] = acc[3 * k + 1] - cc * rx * ry;
+        out[3 * k + 2] = acc[3 * k + 2] - cc * ry * ry;
+    }
+}
+
+// One warp per target: T_i += sum over its pairs of C sigma_b (slot order).
+__global__ void k_close_apply(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
+                              const long long* __restrict__ blk_off, const double* __restrict__ blocks,
+                              const double* __restrict__ body, const double2* __restrict__ sigma, int N,
+                              double2* __restrict__ T) {
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wid >= N) return;
+    int p0 = pair_base[wid], p1 = pair_base[wid + 1];
+    if (p0 == p1) return;
+    double tx = 0, ty = 0;
+    for (int p = p0; p < p1; ++p) {
+        int b = pairs[p].y;
+        int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+        const double* C = blocks + blk_off[p];
+        double ax = 0, ay = 0;
+        for (int k = lane; k < nbn; k += 32) {
+            double2 s = sigma[off + k];
+            double A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
+            ax = fma(A, s.x, fma(B, s.y, ax));
+            ay = fma(B, s.x, fma(D, s.y, ay));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        tx += ax;
+        ty += ay;
+    }
+    if (lane == 0) {
+        double2 t = T[wid];
+        T[wid] = make_double2(t.x + tx, t.y + ty);
+    }
+}
+
+static Shifts9dC shifts_of(const bie_ctx* c) {
+    Shifts9dC s;
+    int k = 0;
+    for (int n = -1; n <= 1; ++n)
+        for (int mm = -1; mm <= 1; ++mm, ++k) {
+            s.x[k] = mm * c->e1[0] + n * c->e2[0];
+            s.y[k] = mm * c->e1[1] + n * c->e2[1];
+        }
+    return s;
+}
+
+int build_close(bie_ctx* c) {
+    c->cl.npairs = 0;
+    k_body_h<<<c->nb, 256, 0, c->stream>>>(c->w, c->body);
+    BIE_LAUNCH(c, "k_body_h");
+    if (!(c->opts.close_factor > 0)) return BIE_OK;
+    const int N = c->N, kmax = kCloseSlots;
+    Shifts9dC sh = shifts_of(c);
+    BIE_CUDA(c, cudaMemsetAsync(c->cl.flags, 0, 4 * sizeof(int), c->stream));
+    k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->nb, N, sh,
+                                                         c->opts.close_factor, kmax, c->cl.slots, c->cl.count,
+                                                         c->cl.flags + 2);
+    BIE_LAUNCH(c, "k_close_detect");
+    k_close_scan<<<1, 1024, 0, c->stream>>>(c->cl.count, N, kmax, c->cl.slots, c->body, c->cl.pair_base,
+                                           c->cl.blk_off, c->cl.pairs, c->cl.flags, c->cl.cap_doubles,
+                                           c->cl.cap_pairs);
+    BIE_LAUNCH(c, "k_close_scan");
+    int h[4];
+    BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h[2] > 0)
+        return fail(c, BIE_EINVAL, "a node is close to more than " + std::to_string(kmax) +
+                                       " body images (bodies overlap or nearly so)");
+    c->cl.under_resolved = h[3];
+    if (h[1])
+        return fail(c, BIE_EINVAL, "close-evaluation storage exceeded (" + std::to_string(h[0]) +
+                                       " pairs); raise close_capacity");
+    c->cl.npairs = h[0];
+    if (h[0] == 0) return BIE_OK;
+    int maxn = 0;
+    for (int n : c->n_nodes) maxn = std::max(maxn, n);
+    size_t shm = sizeof(double) * (3 * (size_t)kCloseChunk + 3 * (size_t)maxn);
+    BIE_CUDA(c, cudaFuncSetAttribute(k_close_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    c->cl.shm_limit = shm;
+    k_close_blocks<<<h[0], 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
+                                                  c->body, sh, c->cl.dtab, c->cl.dtab_off, c->cl.blocks);
+    BIE_LAUNCH(c, "k_close_blocks");
+    return BIE_OK;
+}
+
+// Dirichlet tables for every distinct node count (once per context).
+int build_dirichlet_tables(bie_ctx* c) {
+    std::vector<long long> off(c->nb);
+    std::vector<std::pair<int, long long>> seen;
+    long long total = 0;
+    for (int b = 0; b < c->nb; ++b) {
+        int n = c->n_nodes[b];
+        long long o = -1;
+        for (auto& pr : seen)
+            if (pr.first == n) o = pr.second;
+        if (o < 0) {
+            o = total;
+            seen.push_back({n, o});
+            total += 126LL * n;
+        }
+        off[b] = o;
+    }
+    BIE_CUDA(c, cudaMalloc((void**)&c->cl.dtab, total * sizeof(double)));
+    BIE_CUDA(c, cudaMalloc((void**)&c->cl.dtab_off, c->nb * sizeof(long long)));
+    BIE_CUDA(c, cudaMemcpy(c->cl.dtab_off, off.data(), c->nb * sizeof(long long), cudaMemcpyHostToDevice));
+    for (auto& pr : seen) {
+        k_dirichlet<<<256, 256, 0, c->stream>>>(c->cl.dtab + pr.second, pr.first);
+        BIE_LAUNCH(c, "k_dirichlet");
+    }
+    return BIE_OK;
+}
+
+int close_apply(bie_ctx* c, const double* sigma, double* T) {
+    if (c->cl.npairs == 0) return BIE_OK;
+    const int N = c->N;
+    long long threads = 32LL * N;
+    int bs = 256;
+    int gs = (int)((threads + bs - 1) / bs);
+    k_close_apply<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->body,
+                                           reinterpret_cast<const double2*>(sigma), N,
+                                           reinterpret_cast<double2*>(T));
+    BIE_LAUNCH(c, "k_close_apply");
+    return BIE_OK;
+}
+
+}  // namespace bie

@@ -11,6 +11,7 @@
 // single-precision-pair operator to opts.inner_tol; x += d; repeat until
 // ||r|| / ||b|| <= opts.gmres_tol.
 #include <cmath>
+#include <cstdio>
 #include <vector>
 
 #include "bie_internal.cuh"
@@ -219,7 +220,12 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
     }
     inf.rel_residual = rel;
     if (info) *info = inf;
-    if (rel > tol) return fail(c, BIE_ENOCONV, "solver stopped above tolerance");
+    if (rel > tol) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "solver stopped above tolerance: relative residual %.3e after %d sweeps, %d iterations",
+                 rel, inf.refinements, inf.iterations);
+        return fail(c, BIE_ENOCONV, msg);
+    }
     return BIE_OK;
 }
 

@@ -148,3 +148,17 @@ def small_cell(n_bodies=3, nodes=64, seed=0, phi=0.2, gap=0.05, e2=(0.0, 1.0)):
     cell.update(solver=dict(n_proxy=32, proxy_radius=1.5, n_coll=16, gmres_tol=1e-10),
                 dt=1e-3, steps=2)
     return cell
+
+
+def two_ellipses(gap, n, mu=1.0, gamma=1.0):
+    """The two ellipses of the paper's quasi-static convergence example
+    (Sec. 8, Example 1): semi-axes (0.25, 0.125) and (0.125, 0.25), centres on
+    a horizontal line with |x1 - x2| = gap + 0.375, here placed in the unit
+    cell (1,0),(0,1) centred at (0.5, 0.5) (the paper does not give the cell,
+    mu or gamma)."""
+    half = 0.5 * (gap + 0.375)
+    return dict(e1=[1.0, 0.0], e2=[0.0, 1.0], centre=[0.5, 0.5], mu=mu, gamma=gamma,
+                bodies=[dict(a=0.25, b=0.125, xc=[0.5 - half, 0.5], theta=0.0, n=n),
+                        dict(a=0.125, b=0.25, xc=[0.5 + half, 0.5], theta=0.0, n=n)],
+                solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10),
+                dt=1e-3, steps=1)

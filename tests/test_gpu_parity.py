@@ -1,10 +1,12 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
 Tolerances:
-* FP64 operator: relative max-norm 1e-11.  The kernels and the oracle
-  evaluate the same sums in double precision in different orders; the
-  proxy fit (Tikhonov, lam = 1e-8 ||Q||_F) amplifies rounding in Q by at most
-  ~1e-8 / 1e-16 relative on the correction, which is a small part of T.
+* FP64 operator: relative max-norm 1e-10.  The kernels and the oracle
+  evaluate the same sums in double precision in different orders, and each
+  side factors its own proxy matrix Q.  The Tikhonov fit (lam = 1e-8 ||Q||_F)
+  carries a rounding-level difference of Q into the pressure-fixed
+  correction with a gain of about 3e-9 / 1e-16 (measured), and the
+  correction is a few per cent of T: ~1e-11, bounded here by 1e-10.
 * Mixed operator (single-precision pair sums): relative 2e-5 -- the
   accumulated FP32 rounding of ~9N pair terms with rcp.approx (2 ulp).
 * Solutions: both sides solve to 1e-12 so that the difference is bounded by
@@ -63,7 +65,7 @@ def test_apply_fp64(pair):
         sigma = rng.standard_normal(2 * ctx.N)
         y = ctx.apply(sigma, precision=bie.BIE_FP64)
         ref = op.apply(sigma.reshape(-1, 2)).ravel()
-        assert _rel(y, ref) < 1e-11
+        assert _rel(y, ref) < 1e-10
 
 
 def test_apply_mixed(pair):
@@ -193,6 +195,35 @@ def test_full_size_config2_sampled():
     ref = op.apply(sigma.reshape(-1, 2), targets=idx)
     y64 = ctx.apply(sigma, precision=bie.BIE_FP64).reshape(-1, 2)[idx]
     y32 = ctx.apply(sigma, precision=bie.BIE_MIXED).reshape(-1, 2)[idx]
-    assert _rel(y64, ref) < 1e-11
+    assert _rel(y64, ref) < 1e-10
     assert _rel(y32, ref) < 5e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("gap,n", [(1e-2, 96), (2e-3, 160), (2e-3, 256)])
+def test_close_evaluation_parity(gap, n):
+    """Two ellipses of Sec. 8 Example 1 at gaps of one node spacing or less:
+    the close-evaluation correction is large (the smooth rule alone is far off)
+    and the GPU matches the oracle's definition of it."""
+    cell = workloads.two_ellipses(gap, n)
+    ctx = bie.Context(cell, precision=bie.BIE_FP64, gmres_tol=1e-12)
+    op = oracle_operator(cell)
+    op_smooth = oracle_operator(cell, use_close=False)
+    npairs, under = ctx.close_info()
+    assert npairs > 0 and under == 0
+    sigma = np.random.default_rng(8).standard_normal(2 * ctx.N)
+    ref = op.apply(sigma.reshape(-1, 2)).ravel()
+    smooth = op_smooth.apply(sigma.reshape(-1, 2)).ravel()
+    assert _rel(smooth, ref) > 1e-6  # the correction matters here
+    y = ctx.apply(sigma, precision=bie.BIE_FP64)
+    assert _rel(y, ref) < 1e-10
+    y32 = ctx.apply(sigma, precision=bie.BIE_MIXED)
+    assert _rel(y32, ref) < 5e-5
+    sig, info = ctx.solve()
+    sref, _, _ = obie.solve(op, tol=1e-12)
+    assert _rel(sig, sref.ravel()) < 1e-9
+    v, om, mu = ctx.velocities(sig)
+    v_ref, om_ref = op.body_velocities(sref)
+    np.testing.assert_allclose(om, om_ref, atol=1e-9)
+    np.testing.assert_allclose(v, v_ref, atol=1e-9)
     ctx.close()

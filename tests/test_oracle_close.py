@@ -89,3 +89,39 @@ def test_correction_vanishes_far_away():
         fine = close.fine_integral(BODY, sig, x, nu, np.zeros(2), 8)
         coarse = kernels.traction(x[None] - g["x"], nu[None], sig * g["w"][:, None]).sum(0)
         assert np.abs(fine - coarse).max() < 1e-12
+
+
+def test_fine_rule_converged_at_chosen_factor():
+    """For every close pair of the two-ellipse cell at gap 2e-3 the oracle's
+    fine rule agrees with the rule of twice the resolution."""
+    from paper_1912_04501_gb300 import workloads
+    from tests.conftest import oracle_operator
+    cell = workloads.two_ellipses(2e-3, 192)
+    op = oracle_operator(cell)
+    s = op.s
+    sig = np.random.default_rng(3).normal(size=(s.N, 2))
+    assert len(op.close.pairs) > 10
+    for (i, b, sh, d, hl) in op.close.pairs:
+        bd = s.bodies[b]
+        sl = slice(s.offsets[b], s.offsets[b + 1])
+        rho = close.fine_factor(hl, d)
+        a = close.fine_integral(bd, sig[sl], s.x[i], s.n[i], sh, rho)
+        c = close.fine_integral(bd, sig[sl], s.x[i], s.n[i], sh, 2 * rho)
+        assert np.abs(a - c).max() < 1e-13
+
+
+def test_closest_point_matches_dense_sampling():
+    from oracle import close as cl
+    body = dict(a=0.3, b=0.1, xc=[0.2, -0.1], theta=0.7, n=64)
+    rng = np.random.default_rng(5)
+    t = np.linspace(0, 2 * np.pi, 400001)
+    for _ in range(10):
+        k = rng.integers(64)
+        g = geometry.ellipse_nodes(body["a"], body["b"], body["xc"], body["theta"], 64)
+        x = g["x"][k] + rng.uniform(1e-4, 2e-2) * g["n"][k] + rng.normal(size=2) * 1e-3
+        d, hl = cl.closest_point(body, x, np.zeros(2), 2 * np.pi * k / 64)
+        y, sp = geometry.ellipse_point(body["a"], body["b"], body["xc"], body["theta"], t)
+        dd = np.sqrt(((y - x) ** 2).sum(1))
+        # the sampled minimum overestimates by up to (ds)^2 / (8 d) ~ 2e-9
+        assert -1e-8 < dd.min() - d < 1e-8
+        assert abs(hl - 2 * np.pi * sp[dd.argmin()] / 64) < 1e-6
