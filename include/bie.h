@@ -170,6 +170,28 @@ int bie_get_state(bie_ctx* ctx, double* t, double* e2, double* xc, double* theta
 int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, const double* theta,
                   const double* sigma);
 
+/* bie_apply_static: the same operator application as
+ * bie_apply(ctx, sigma, out, BIE_MIXED, 1), but it allocates no device memory
+ * at all and does not touch the workspace that bie_init allocated.  It has no
+ * counterpart in the paper; it exists for callers that may not call cudaMalloc
+ * -- for instance code running inside a host application whose own memory
+ * manager owns the device heap, or a thread that must not allocate while a
+ * solve on the same context holds the context's workspace -- yet need the
+ * operator on their own device buffers.
+ *   sigma, out: device pointers, 2N doubles each (node-major), on the
+ *   context's GPU; they must not overlap.  The call is asynchronous on the
+ *   context's stream; out is ready when that stream reaches the end of it.
+ * Its per-call scratch is one static device array of 4 MiB inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Contexts with more than 8192 nodes (or whose buffers would not fit
+ * the 4 MiB) are rejected with BIE_EINVAL and a message.  All calls share
+ * that array and it keeps the last call's contents; each call writes every
+ * buffer it reads, so nothing needs clearing, but calls that overlap on the
+ * GPU (two streams, two contexts on one device) race on it.  The first call
+ * on each device looks up the array's device address; make that first call
+ * before any stream capture. */
+int bie_apply_static(bie_ctx* ctx, const double* sigma, double* out);
+
 /* Close-evaluation bookkeeping of the current geometry: number of stored
  * (target, body image) pairs, and pairs closer to the curve than the finest
  * rule (64-fold upsampling) resolves to double precision (their correction is

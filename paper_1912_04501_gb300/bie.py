@@ -9,7 +9,8 @@ call raises -- there is no fallback implementation.
 The functions carry the C names:
     bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
-    bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read
+    bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read,
+    bie_apply_static
 and `Context` wraps them for a workload dict (see workloads.py).
 """
 import ctypes
@@ -97,6 +98,7 @@ def library():
         "bie_get_state": (c_int32, [vp, vp, vp, vp, vp, vp]),
         "bie_set_state": (c_int32, [vp, c_double, vp, vp, vp, vp]),
         "bie_close_info": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+        "bie_apply_static": (c_int32, [vp, vp, vp]),
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
     }
@@ -114,7 +116,7 @@ def exported_symbols():
     return [n for n in ("bie_default_opts", "bie_init", "bie_destroy", "bie_last_error", "bie_size",
                         "bie_set_stream", "bie_nodes", "bie_apply", "bie_rhs", "bie_solve", "bie_velocities",
                         "bie_step", "bie_get_state", "bie_set_state", "bie_close_info", "bie_profile",
-                        "bie_profile_read")
+                        "bie_profile_read", "bie_apply_static")
             if hasattr(L, n)]
 
 
@@ -244,6 +246,16 @@ class Context:
         self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
                                             th.ctypes.data, sg.ctypes.data))
         return dict(t=float(t[0]), e2=e2, xc=xc.reshape(-1, 2), theta=th, sigma=sg)
+
+    def apply_static(self, sigma, out):
+        """bie_apply_static on device tensors (no device allocation inside the
+        library; asynchronous on the context's stream)."""
+        ps, ds = _ptr(sigma)
+        po, do = _ptr(out)
+        if not (ds and do):
+            raise ValueError("bie_apply_static takes device tensors")
+        self._check(library().bie_apply_static(self.h, ps, po))
+        return out
 
     def close_info(self):
         n, u = c_int32(), c_int32()

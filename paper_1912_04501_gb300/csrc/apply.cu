@@ -619,3 +619,56 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
 }
 
 }  // namespace bie
+
+namespace bie {
+
+// The single-precision-pair operator application with every per-call buffer
+// taken from `ws` (used by the allocation-free entry point, whose buffers
+// live in a static device array).  The kernels and their order are those of
+// apply_device; the context is only read.
+int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws) {
+    const int N = c->N;
+    const int bs = 256, gs = (N + bs - 1) / bs;
+    const double2* sg = reinterpret_cast<const double2*>(sigma);
+    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], ws.src32, ws.src64);
+    BIE_LAUNCH(c, "k_pack");
+    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, ws.bodyF);
+    BIE_LAUNCH(c, "k_body_moments");
+    double sx[9], sy[9];
+    shifts(c, sx, sy, false);
+    Shifts9 s9;
+    for (int k = 0; k < 9; ++k) {
+        s9.x[k] = (float)sx[k];
+        s9.y[k] = (float)sy[k];
+    }
+    const int splits = c->near_splits32;
+    const int tiles = (N + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
+    const int chunk = (N + splits - 1) / splits;
+    k_near32<kNear32TPT><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk, s9,
+                                                                             (float2*)ws.part);
+    BIE_LAUNCH(c, "k_near32");
+    const int twm = 2 * c->m;
+    int dbs = (256 / twm) * twm;
+    if (dbs < twm) dbs = twm;
+    const int dchunk = (N + kDiscBlocks - 1) / kDiscBlocks;
+    k_disc<float><<<kDiscBlocks, dbs, (size_t)dbs * 4 * sizeof(double), c->stream>>>(
+        ws.src64, N, dchunk, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
+        ws.gpart);
+    BIE_LAUNCH(c, "k_disc");
+    const double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
+    const double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
+    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscBlocks, c->m, c->M, ws.bodyF, c->nb, l1,
+                                                          l2, c->P, ws.xi);
+    BIE_LAUNCH(c, "k_xi");
+    double2* T = reinterpret_cast<double2*>(ws.T);
+    k_correct<float2><<<gs, bs, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x, c->y, c->nx, c->ny,
+                                                c->w, c->kap, c->yp, ws.xi, c->M, T);
+    BIE_LAUNCH(c, "k_correct");
+    if (int rc = close_apply(c, sigma, ws.T)) return rc;
+    k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF,
+                                       reinterpret_cast<double2*>(yout));
+    BIE_LAUNCH(c, "k_finish");
+    return BIE_OK;
+}
+
+}  // namespace bie

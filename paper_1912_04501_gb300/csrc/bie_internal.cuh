@@ -158,6 +158,8 @@ int close_apply(bie_ctx* c, const double* sigma, double* T);  // T += C sigma
 // apply.cu ------------------------------------------------------------------
 // y = A sigma for device sigma, y (2N each); precision BIE_FP64 / BIE_MIXED
 int apply_device(bie_ctx* c, const double* sigma, double* y, int precision);
+// single-precision-pair application with caller-provided per-call buffers
+int apply_device_ws(bie_ctx* c, const double* sigma, double* y, Workspace& ws);
 int rhs_device(bie_ctx* c, double* b);
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff);
 
