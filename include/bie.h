@@ -40,6 +40,8 @@ extern "C" {
 
 #define BIE_FP64 0  /* every pair sum in double precision */
 #define BIE_MIXED 1 /* pair sums in single precision inside FP64 iterative refinement */
+#define BIE_DF64 2  /* near pair sums in double-float arithmetic (pairs of floats, ~48-bit
+                       significands) on the FP32 pipe; everything else in double */
 
 typedef struct bie_ctx bie_ctx;
 
@@ -78,6 +80,7 @@ typedef struct {
     double close_factor;  /* close-evaluation zone in units of the source body's node spacing
                              h_b = perimeter / N_b (Sec. 6.3 remark: 10); 0 disables the correction */
     int32_t close_capacity; /* maximum (target, body image) close pairs stored; 0 = N */
+    int32_t residual;     /* BIE_MIXED refinement residual: BIE_FP64 (native double) or BIE_DF64 */
 } bie_opts;
 
 typedef struct {
@@ -90,7 +93,8 @@ typedef struct {
 
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
- * warm_start 1, min_gap 0, device 0, close_factor 10, close_capacity 0. */
+ * warm_start 1, min_gap 0, device 0, close_factor 10, close_capacity 0,
+ * residual BIE_DF64. */
 void bie_default_opts(bie_opts* opts);
 
 /* Create a context for one unit cell: lattice, viscosity mu, shear rate
@@ -125,7 +129,8 @@ int bie_nodes(bie_ctx* ctx, double* x, double* n, double* w, double* kappa, int3
  *       close_factor * h_b of a body image, the smooth rule is replaced by the
  *       integral of the trigonometric interpolant of the density over the exact
  *       ellipse;  alpha = -T_0 . n_0.
- * precision: BIE_FP64 or BIE_MIXED (single-precision pair sums).
+ * precision: BIE_FP64, BIE_MIXED (single-precision pair sums) or BIE_DF64
+ * (double-float near pair sums, FP64-class accuracy at FP32-pipe speed).
  * sigma and out: 2N doubles each, must not overlap. */
 int bie_apply(bie_ctx* ctx, const double* sigma, double* out, int32_t precision, int32_t on_device);
 
@@ -135,7 +140,8 @@ int bie_rhs(bie_ctx* ctx, double* b, int32_t on_device);
 
 /* Solve A sigma = b to opts.gmres_tol (relative FP64 residual) by GMRES
  * (opts.precision = BIE_FP64) or by single-precision GMRES inside FP64
- * iterative refinement (BIE_MIXED).  rhs NULL means -T(u0, p0).  sigma holds
+ * iterative refinement (BIE_MIXED; the residual in the precision opts.residual
+ * names).  rhs NULL means -T(u0, p0).  sigma holds
  * the initial guess on entry when use_guess != 0 and the solution on exit
  * (2N doubles).  info may be NULL.  Returns BIE_ENOCONV if the tolerance was
  * not met (sigma then holds the best iterate), BIE_ENUMERIC on NaN/Inf. */
@@ -210,6 +216,8 @@ typedef struct {
     double near32_ms;        /* their summed device time (CUDA events) */
     int32_t near64_launches; /* double-precision near-sum launches */
     double near64_ms;
+    int32_t neardf_launches; /* double-float near-sum launches */
+    double neardf_ms;
 } bie_profile_info;
 
 int bie_profile(bie_ctx* ctx, int32_t enable);

@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbie.so")
 
 BIE_OK, BIE_EINVAL, BIE_ENOCONV, BIE_ECOLLIDE, BIE_ENUMERIC, BIE_ECUDA, BIE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
-BIE_FP64, BIE_MIXED = 0, 1
+BIE_FP64, BIE_MIXED, BIE_DF64 = 0, 1, 2
 _NAMES = {0: "BIE_OK", -1: "BIE_EINVAL", -2: "BIE_ENOCONV", -3: "BIE_ECOLLIDE", -4: "BIE_ENUMERIC",
           -5: "BIE_ECUDA", -6: "BIE_ENOMEM"}
 
@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("n_proxy", c_int32), ("proxy_radius", c_double), ("n_coll", c_int32),
                 ("lam_rel", c_double), ("gmres_tol", c_double), ("gmres_max", c_int32), ("inner_tol", c_double),
                 ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32),
-                ("close_factor", c_double), ("close_capacity", c_int32)]
+                ("close_factor", c_double), ("close_capacity", c_int32), ("residual", c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -56,7 +56,8 @@ class SolveInfo(ctypes.Structure):
 
 class ProfileInfo(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("near32_launches", c_int32), ("near32_ms", c_double),
-                ("near64_launches", c_int32), ("near64_ms", c_double)]
+                ("near64_launches", c_int32), ("near64_ms", c_double),
+                ("neardf_launches", c_int32), ("neardf_ms", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,6 +1,7 @@
 // C ABI entry points (include/bie.h): argument checking, device memory
 // ownership, host <-> device staging, and the forward-Euler time loop.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -28,9 +29,9 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 
 static void free_all(bie_ctx* c) {
     void* ptrs[] = {c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body, c->tgt32, c->gl_s, c->A, c->beta,
-                    c->P, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.bodyF,
+                    c->P, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.srcdf, c->ws.bodyF,
                     c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
-                    c->sv.d, c->sv.h, c->sv.red, c->sv.sigma_prev, c->cl.slots, c->cl.count,
+                    c->sv.d, c->sv.h, c->sv.red, c->sv.dpart, c->sv.sigma_prev, c->cl.slots, c->cl.count,
                     c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab,
                     c->cl.dtab_off};
     for (void* p : ptrs)
@@ -100,9 +101,12 @@ int prof_fold(bie_ctx* c) {
         if (c->ev_kind[k] == 0) {
             c->prof_acc.near32_launches++;
             c->prof_acc.near32_ms += ms;
-        } else {
+        } else if (c->ev_kind[k] == 1) {
             c->prof_acc.near64_launches++;
             c->prof_acc.near64_ms += ms;
+        } else {
+            c->prof_acc.neardf_launches++;
+            c->prof_acc.neardf_ms += ms;
         }
     }
     c->ev_used = 0;
@@ -140,6 +144,7 @@ void bie_default_opts(bie_opts* o) {
     o->device = 0;
     o->close_factor = 10.0;
     o->close_capacity = 0;
+    o->residual = BIE_DF64;
 }
 
 int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int32_t n_bodies,
@@ -164,6 +169,7 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
         return bad("non-positive tolerance or radius");
     if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) return bad("gmres_max / max_refine out of range");
     if (!(mu > 0) || !std::isfinite(gamma)) return bad("mu must be positive, gamma finite");
+    if (o.residual != BIE_FP64 && o.residual != BIE_DF64) return bad("residual must be BIE_FP64 or BIE_DF64");
     if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
         return bad("close_factor must be in [0, 100], close_capacity >= 0");
     double det = lat->e1[0] * lat->e2[1] - lat->e1[1] * lat->e2[0];
@@ -221,10 +227,16 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     const int R = 8 * m + 2 * M, Cc = 2 * M;
     int tiles32 = (n + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
     int tiles64 = (n + kNearThreads - 1) / kNearThreads;
-    int maxsplit = std::max(1, n / 256);
-    c->near_splits32 = std::min(maxsplit, std::max(1, (4 * kSMs + tiles32 - 1) / tiles32));
-    c->near_splits64 = std::min(maxsplit, std::max(1, (4 * kSMs + tiles64 - 1) / tiles64));
-    size_t part = std::max((size_t)c->near_splits32 * n * sizeof(float2), (size_t)c->near_splits64 * n * sizeof(double2));
+    // Source splits: tiles x splits fills the resident CTA slots of all SMs in
+    // one even wave (7 CTAs/SM for k_near32 at 72 registers x 128 threads,
+    // 6 for k_near64 at 80, 4 for k_near_df at 128), keeping at least 64
+    // sources per split.
+    int maxsplit = std::max(1, n / 64);
+    c->near_splits32 = std::min(maxsplit, std::max(1, (7 * kSMs) / tiles32));
+    c->near_splits64 = std::min(maxsplit, std::max(1, (6 * kSMs) / tiles64));
+    c->near_splitsdf = std::min(maxsplit, std::max(1, (4 * kSMs) / tiles64));  // 128 registers: 4 CTAs/SM
+    size_t part = std::max({(size_t)c->near_splits32 * n * sizeof(float2), (size_t)c->near_splits64 * n * sizeof(double2),
+                            (size_t)c->near_splitsdf * n * sizeof(double2)});
     c->sv.kmax = o.gmres_max;
     int kk = c->sv.kmax;
     rc = 0;
@@ -247,6 +259,7 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->ws.out, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.src64, n);
     rc = rc ? rc : dalloc(c, &c->ws.src32, n);
+    rc = rc ? rc : dalloc(c, (char**)&c->ws.srcdf, (size_t)n * 32);
     rc = rc ? rc : dalloc(c, &c->ws.bodyF, 3 * (size_t)nb);
     rc = rc ? rc : dalloc(c, (char**)&c->ws.part, part);
     rc = rc ? rc : dalloc(c, &c->ws.gpart, (size_t)kDiscBlocks * 2 * m * 4);
@@ -260,6 +273,7 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->sv.d, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.h, 3 * (size_t)(kk + 2) + 8);
     rc = rc ? rc : dalloc(c, &c->sv.red, 8);
+    rc = rc ? rc : dalloc(c, &c->sv.dpart, (size_t)(kk + 2) * 64);
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
     {
         int maxn = 0;
@@ -364,7 +378,8 @@ int bie_nodes(bie_ctx* c, double* x, double* n, double* w, double* kappa, int32_
 
 int bie_apply(bie_ctx* c, const double* sigma, double* out, int32_t precision, int32_t on_device) {
     if (!c || !sigma || !out) return BIE_EINVAL;
-    if (precision != BIE_FP64 && precision != BIE_MIXED) return fail(c, BIE_EINVAL, "bad precision");
+    if (precision != BIE_FP64 && precision != BIE_MIXED && precision != BIE_DF64)
+        return fail(c, BIE_EINVAL, "bad precision");
     BIE_CUDA(c, cudaSetDevice(c->device));
     const size_t n2 = 2 * (size_t)c->N;
     const double* din = sigma;

@@ -209,96 +209,260 @@ k_near64(const double* __restrict__ x, const double* __restrict__ y, const doubl
 }
 
 // ---------------------------------------------------------------------------
-// Wall discrepancy (Sec. 6.2 step 2).  For a collocation point x on L,
-//   S_near(x + e1) - S_near(x) = sum_n sum_j [K(x, y_j - 2 e1 + n e2) - K(x, y_j + e1 + n e2)] q_j
-// and on D with the roles of e1, e2 exchanged; K is the velocity kernel G or
-// the traction kernel G^t with the wall normal.  Block b handles a source
-// chunk; thread (wp, sub): wall point wp in [0, 2m) (L points then D points),
-// sources sub, sub + S, ...; output per block and wall point:
-// (u_x, u_y, t_x, t_y).
+// Near image sum in double-float arithmetic ("df64": every quantity is an
+// unevaluated sum hi + lo of two floats, ~48 significant bits) on the FP32
+// pipe.  GB300's FP64 pipe sustains about 1/100 of the FP32 pair rate, so the
+// FP64-accurate refinement residual runs here instead.  Error-free
+// transformations: TwoSum (6 FP32 ops) for sums, FMA-based TwoProd (2 ops)
+// for products, MUFU rcp refined by one FMA residual step for 1/r^2; the
+// difference r = x - y is formed exactly from both words (three TwoSums) and
+// r, r.n, r.q are renormalised before they are multiplied, so that the
+// dropped lo*lo cross terms stay at 2^-48; the accumulator keeps its TwoSum
+// error in a float.  About 140 FP32 instructions per pair; each term is
+// accurate to ~1e-14 of the kernel's scale |q| / |r| at any distance (the
+// inputs carry 48 of double's 53 bits).
 // ---------------------------------------------------------------------------
-template <typename Real>
-__global__ void k_disc(const Src64* __restrict__ src, int N, int chunk, int m,
-                       const double* __restrict__ gl_s, double e1x, double e1y, double e2x, double e2y,
-                       double Cx, double Cy, double mu, double* __restrict__ gpart) {
-    extern __shared__ double sacc[];  // blockDim.x x 4
-    int twm = 2 * m;
-    int wp = threadIdx.x % twm, sub = threadIdx.x / twm, S = blockDim.x / twm;
-    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
-    wall_normals(e1, e2, nl, nd);
-    Real ux = 0, uy = 0, tx = 0, ty = 0;
-    if (sub < S) {
-        bool isL = wp < m;
-        double s = gl_s[isL ? wp : wp - m];
-        double X, Y, nu0, nu1, ax, ay, bx, by;  // ax/ay: step along the wall's rows
-        if (isL) {
-            X = Cx - 0.5 * e1x + s * e2x;
-            Y = Cy - 0.5 * e1y + s * e2y;
-            nu0 = nl[0];
-            nu1 = nl[1];
-        } else {
-            X = Cx - 0.5 * e2x + s * e1x;
-            Y = Cy - 0.5 * e2y + s * e1y;
-            nu0 = nd[0];
-            nu1 = nd[1];
-        }
-        // plus images: -2 a + k b ; minus images: a + k b  (a = e1, b = e2 on L; swapped on D)
-        if (isL) { ax = e1x; ay = e1y; bx = e2x; by = e2y; }
-        else { ax = e2x; ay = e2y; bx = e1x; by = e1y; }
-        const Real c4 = (Real)(1.0 / (4.0 * kPi * mu));
-        const Real ct = (Real)(-1.0 / kPi);
-        int j0 = blockIdx.x * chunk, j1 = min(N, j0 + chunk);
-        for (int j = j0 + sub; j < j1; j += S) {
-            Src64 q = src[j];
-            for (int k = -1; k <= 1; ++k) {
-                for (int sgn = 0; sgn < 2; ++sgn) {
-                    double shx = (sgn == 0 ? -2.0 * ax : ax) + k * bx;
-                    double shy = (sgn == 0 ? -2.0 * ay : ay) + k * by;
-                    Real rx = (Real)(X - (q.x + shx)), ry = (Real)(Y - (q.y + shy));
-                    Real qx = (Real)q.z, qy = (Real)q.w;
-                    Real r2 = rx * rx + ry * ry;
-                    Real inv = (Real)1 / r2;
-                    Real rq = rx * qx + ry * qy;
-                    Real l = (Real)(-0.5) * log(r2);
-                    Real vx = (l * qx + rx * rq * inv) * c4, vy = (l * qy + ry * rq * inv) * c4;
-                    Real cc = ct * (rx * (Real)nu0 + ry * (Real)nu1) * rq * inv * inv;
-                    Real sg = sgn == 0 ? (Real)1 : (Real)-1;
-                    ux += sg * vx;
-                    uy += sg * vy;
-                    tx += sg * cc * rx;
-                    ty += sg * cc * ry;
-                }
+struct __align__(16) SrcDF {
+    float xh, xl, yh, yl, qxh, qxl, qyh, qyl;
+};
+
+__device__ __forceinline__ void split_df(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// h + l -> normalised (|l| <= ulp(h) / 2), valid when |h| >= |l|
+__device__ __forceinline__ void fast2(float& h, float& l) {
+    float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+
+// (ph + pl) - (sh + sl), exact to ~2^-48 relative to the difference itself
+__device__ __forceinline__ void df_diff(float ph, float pl, float sh, float sl, float& h, float& l) {
+    float s1, e1, s2, e2, e3;
+    two_sum(ph, -sh, s1, e1);
+    two_sum(pl, -sl, s2, e2);
+    two_sum(s1, s2, h, e3);
+    l = (e1 + e2) + e3;
+    fast2(h, l);
+}
+
+// (ah + al) * (bh + bl) -> (ph, pl), pl not renormalised
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+    ph = ah * bh;
+    pl = fmaf(ah, bh, -ph);
+    pl = fmaf(ah, bl, fmaf(al, bh, pl));
+}
+
+__global__ void k_pack_df(const double2* __restrict__ sigma, const double* __restrict__ x,
+                          const double* __restrict__ y, const double* __restrict__ w, int N, double Cx, double Cy,
+                          SrcDF* __restrict__ src) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double2 s = sigma[i];
+    double wi = w[i];
+    SrcDF r;
+    split_df(x[i] - Cx, r.xh, r.xl);
+    split_df(y[i] - Cy, r.yh, r.yl);
+    split_df(s.x * wi, r.qxh, r.qxl);
+    split_df(s.y * wi, r.qyh, r.qyl);
+    src[i] = r;
+}
+
+__global__ void __launch_bounds__(kNearThreads, 4)
+k_near_df(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
+          const double* __restrict__ ny, const SrcDF* __restrict__ src, int N, int chunk, Shifts9d sh, double Cx,
+          double Cy, double2* __restrict__ part) {
+    __shared__ SrcDF s_src[kNearTile];
+    const int j0 = blockIdx.y * chunk;
+    const int j1 = min(N, j0 + chunk);
+    const int i = blockIdx.x * kNearThreads + threadIdx.x;
+    double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
+    if (i < N) {
+        tx = x[i] - Cx;
+        ty = y[i] - Cy;
+        tnx = nx[i];
+        tny = ny[i];
+    }
+    float pxh[9], pxl[9], pyh[9], pyl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        split_df(tx - sh.x[k], pxh[k], pxl[k]);
+        split_df(ty - sh.y[k], pyh[k], pyl[k]);
+    }
+    float nxh, nxl, nyh, nyl;
+    split_df(tnx, nxh, nxl);
+    split_df(tny, nyh, nyl);
+    float axh = 0, axe = 0, ayh = 0, aye = 0;
+    for (int jt = j0; jt < j1; jt += kNearTile) {
+        int cnt = min(kNearTile, j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const SrcDF q = s_src[k];
+#pragma unroll
+            for (int im = 0; im < 9; ++im) {
+                float rxh, rxl, ryh, ryl, e;
+                df_diff(pxh[im], pxl[im], q.xh, q.xl, rxh, rxl);
+                df_diff(pyh[im], pyl[im], q.yh, q.yl, ryh, ryl);
+                // r^2 (the 1e-30 floor absorbs the zero-distance self pair)
+                float a, ea, b, eb, r2h, r2l;
+                a = rxh * rxh;
+                ea = fmaf(rxh, rxh, -a);
+                ea = fmaf(rxh, rxl + rxl, ea);
+                b = ryh * ryh;
+                eb = fmaf(ryh, ryh, -b);
+                eb = fmaf(ryh, ryl + ryl, eb);
+                two_sum(a, b, r2h, e);
+                r2l = e + ea + eb;
+                r2h += 1e-30f;
+                // 1 / r^2
+                const float ih = rcp_approx(r2h);
+                float res = fmaf(-r2h, ih, 1.0f);
+                res = fmaf(-r2l, ih, res);
+                const float il = ih * res;
+                // r . n and r . q
+                float p1, e1, p2, e2, rnh, rnl, rqh, rql;
+                df_mul(rxh, rxl, nxh, nxl, p1, e1);
+                df_mul(ryh, ryl, nyh, nyl, p2, e2);
+                two_sum(p1, p2, rnh, e);
+                rnl = e + e1 + e2;
+                fast2(rnh, rnl);  // r.n may cancel: renormalise before multiplying
+                df_mul(rxh, rxl, q.qxh, q.qxl, p1, e1);
+                df_mul(ryh, ryl, q.qyh, q.qyl, p2, e2);
+                two_sum(p1, p2, rqh, e);
+                rql = e + e1 + e2;
+                fast2(rqh, rql);
+                // c = (r.n / r^2) (r.q / r^2), term = c r
+                float uh, ul, vh, vl, ch, cl, th, tl;
+                df_mul(rnh, rnl, ih, il, uh, ul);
+                df_mul(rqh, rql, ih, il, vh, vl);
+                df_mul(uh, ul, vh, vl, ch, cl);
+                df_mul(ch, cl, rxh, rxl, th, tl);
+                two_sum(axh, th, axh, e);
+                axe += e + tl;
+                df_mul(ch, cl, ryh, ryl, th, tl);
+                two_sum(ayh, th, ayh, e);
+                aye += e + tl;
             }
         }
     }
-    sacc[4 * threadIdx.x + 0] = ux;
-    sacc[4 * threadIdx.x + 1] = uy;
-    sacc[4 * threadIdx.x + 2] = tx;
-    sacc[4 * threadIdx.x + 3] = ty;
-    __syncthreads();
-    if (threadIdx.x < twm) {
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int u = 0; u < S; ++u) {
-            int t = u * twm + threadIdx.x;
-            a0 += sacc[4 * t];
-            a1 += sacc[4 * t + 1];
-            a2 += sacc[4 * t + 2];
-            a3 += sacc[4 * t + 3];
-        }
-        double* o = gpart + ((size_t)blockIdx.x * twm + threadIdx.x) * 4;
-        o[0] = a0;
-        o[1] = a1;
-        o[2] = a2;
-        o[3] = a3;
+    if (i < N) {
+        const double c = -1.0 / kPi;
+        part[(size_t)blockIdx.y * N + i] = make_double2(c * ((double)axh + (double)axe), c * ((double)ayh + (double)aye));
     }
 }
 
-// g~ and xi = P g~ (Sec. 6.2 step 3).  One CTA.
-__global__ void k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __restrict__ bodyF,
-                     int nb, double l1, double l2, const double* __restrict__ P, double* __restrict__ xi) {
-    extern __shared__ double d[];  // 8m
+// ---------------------------------------------------------------------------
+// Wall discrepancy (Sec. 6.2 step 2).  For a collocation point x on L,
+//   S_near(x + e1) - S_near(x) = sum_n sum_j [K(x, y_j - 2 e1 + n e2) - K(x, y_j + e1 + n e2)] q_j
+// and on D with the roles of e1, e2 exchanged; K is the velocity kernel G or
+// the traction kernel G^t with the wall normal.  Block (wp, s): wall point
+// wp in [0, 2m) (L points, then D points) and source split s of kDiscSplits;
+// its threads stride over the split's sources and the block reduces
+// (u_x, u_y, t_x, t_y) into gpart[(s * 2m + wp) * 4 + comp].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fast_log(float x) { return __logf(x); }
+__device__ __forceinline__ double fast_log(double x) { return log(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ gl_s, double e1x, double e1y,
+       double e2x, double e2y, double Cx, double Cy, double mu, double* __restrict__ gpart) {
+    __shared__ double red[4][33];
+    const int wp = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
+    wall_normals(e1, e2, nl, nd);
+    const bool isL = wp < m;
+    const double s = gl_s[isL ? wp : wp - m];
+    double X, Y, nu0, nu1, ax, ay, bx, by;  // a: the step across the wall pair, b: along it
+    if (isL) {
+        X = Cx - 0.5 * e1x + s * e2x;
+        Y = Cy - 0.5 * e1y + s * e2y;
+        nu0 = nl[0];
+        nu1 = nl[1];
+        ax = e1x; ay = e1y; bx = e2x; by = e2y;
+    } else {
+        X = Cx - 0.5 * e2x + s * e1x;
+        Y = Cy - 0.5 * e2y + s * e1y;
+        nu0 = nd[0];
+        nu1 = nd[1];
+        ax = e2x; ay = e2y; bx = e1x; by = e1y;
+    }
+    // the six far images, relative to the collocation point: plus (-2a + kb), minus (a + kb)
+    Real ox[6], oy[6];
+    for (int k = -1; k <= 1; ++k) {
+        ox[k + 1] = (Real)(X - (-2.0 * ax + k * bx));
+        oy[k + 1] = (Real)(Y - (-2.0 * ay + k * by));
+        ox[k + 4] = (Real)(X - (ax + k * bx));
+        oy[k + 4] = (Real)(Y - (ay + k * by));
+    }
+    const Real n0 = (Real)nu0, n1 = (Real)nu1;
+    Real ux = 0, uy = 0, tx = 0, ty = 0;
+    const int per = (N + nsp - 1) / nsp;
+    const int j0 = sp * per, j1 = min(N, j0 + per);
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const Src64 q = src[j];
+        const Real qx = (Real)q.z, qy = (Real)q.w, sx = (Real)q.x, sy = (Real)q.y;
+#pragma unroll
+        for (int im = 0; im < 6; ++im) {
+            const Real rx = ox[im] - sx, ry = oy[im] - sy;
+            const Real r2 = rx * rx + ry * ry;
+            const Real inv = fast_rcp(r2);
+            const Real rq = rx * qx + ry * qy;
+            const Real l = (Real)(-0.5) * fast_log(r2);
+            const Real a = rq * inv;
+            const Real vx = l * qx + rx * a, vy = l * qy + ry * a;
+            const Real cc = (rx * n0 + ry * n1) * a * inv;
+            if (im < 3) {
+                ux += vx; uy += vy; tx += cc * rx; ty += cc * ry;
+            } else {
+                ux -= vx; uy -= vy; tx -= cc * rx; ty -= cc * ry;
+            }
+        }
+    }
+    double v[4] = {(double)ux, (double)uy, (double)tx, (double)ty};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double t = v[c];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[c][warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0;
+        for (int k = 0; k < nw; ++k) t += red[threadIdx.x][k];
+        const double scale = threadIdx.x < 2 ? 1.0 / (4.0 * kPi * mu) : -1.0 / kPi;
+        gpart[((size_t)sp * 2 * m + wp) * 4 + threadIdx.x] = t * scale;
+    }
+}
+
+// g~ and xi = P g~ (Sec. 6.2 step 3).  One CTA of 256 threads: the partials
+// of the discrepancy blocks are reduced in a fixed order, g~ is assembled in
+// shared memory, and each warp computes rows of P g~ with its lanes over the
+// columns.  The dot products are compensated (Ogita, Rump & Oishi's Dot2:
+// FMA-exact products, error-free sums): P has entries up to ~1/lam, so a
+// plain double-precision product would add relative noise ~1e-11 to the
+// correction and put a floor under the GMRES residual.
+__global__ void __launch_bounds__(256)
+k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __restrict__ bodyF, int nb,
+     double l1, double l2, const double* __restrict__ P, double* __restrict__ xi) {
+    extern __shared__ double d[];  // 8m (g~) followed by 8m (raw g)
+    double* g = d + 8 * m;
     __shared__ double Fs[2];
-    int tid = threadIdx.x;
+    const int tid = threadIdx.x;
+    const int nv = 8 * m;  // 2m wall points x (u_x, u_y, t_x, t_y)
     if (tid == 0) {
         double fx = 0, fy = 0;
         for (int b = 0; b < nb; ++b) {
@@ -308,16 +472,21 @@ __global__ void k_xi(const double* __restrict__ gpart, int nblk, int m, int M, c
         Fs[0] = fx;
         Fs[1] = fy;
     }
+    for (int v = tid; v < nv; v += blockDim.x) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int b = 0;
+        for (; b + 4 <= nblk; b += 4) {
+            a0 += gpart[(size_t)b * nv + v];
+            a1 += gpart[(size_t)(b + 1) * nv + v];
+            a2 += gpart[(size_t)(b + 2) * nv + v];
+            a3 += gpart[(size_t)(b + 3) * nv + v];
+        }
+        for (; b < nblk; ++b) a0 += gpart[(size_t)b * nv + v];
+        g[v] = (a0 + a1) + (a2 + a3);
+    }
     __syncthreads();
     for (int wp = tid; wp < 2 * m; wp += blockDim.x) {
-        double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-        for (int b = 0; b < nblk; ++b) {
-            const double* o = gpart + ((size_t)b * 2 * m + wp) * 4;
-            g0 += o[0];
-            g1 += o[1];
-            g2 += o[2];
-            g3 += o[3];
-        }
+        double g0 = g[4 * wp], g1 = g[4 * wp + 1], g2 = g[4 * wp + 2], g3 = g[4 * wp + 3];
         if (wp < m) {  // L: rows of blocks 1 (velocity) and 2 (traction)
             int l = wp;
             d[l] = -g0;
@@ -333,35 +502,40 @@ __global__ void k_xi(const double* __restrict__ gpart, int nblk, int m, int M, c
         }
     }
     __syncthreads();
-    // Compensated dot products (Ogita, Rump & Oishi's Dot2: FMA-exact products,
-    // error-free sums): P has entries up to ~1/lam, so a plain double-precision
-    // product would add relative noise ~1e-11 to the correction and put a floor
-    // under the GMRES residual.
-    int C = 2 * M;
-    for (int r = tid; r < C; r += blockDim.x) {
-        double s = 0, c = 0;
-        for (int cc = 0; cc < 8 * m; ++cc) {
+    const int C = 2 * M, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < C; r += nw) {
+        double s = 0, e = 0;
+        for (int cc = lane; cc < nv; cc += 32) {
             double a = P[r + (size_t)cc * C], b = d[cc];
             double p = a * b;
             double pe = fma(a, b, -p);
             double t = s + p;
             double z = t - s;
-            double se = (s - (t - z)) + (p - z);
+            e += pe + ((s - (t - z)) + (p - z));
             s = t;
-            c += pe + se;
         }
-        xi[r] = s + c;
+        for (int o = 16; o > 0; o >>= 1) {
+            double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            double e2 = __shfl_xor_sync(0xffffffffu, e, o);
+            double t = s + s2;
+            double z = t - s;
+            e = e + e2 + ((s - (t - z)) + (s2 - z));
+            s = t;
+        }
+        if (lane == 0) xi[r] = s + e;
     }
 }
 
-// T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy traction.
-template <typename PartT>
-__global__ void k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __restrict__ sigma,
-                          const double* __restrict__ x, const double* __restrict__ y,
-                          const double* __restrict__ nx, const double* __restrict__ ny,
-                          const double* __restrict__ w, const double* __restrict__ kap,
-                          const double* __restrict__ yp, const double* __restrict__ xi, int M,
-                          double2* __restrict__ T) {
+// T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy
+// traction.  ProxyReal = float on the single-precision path (rcp.approx, the
+// inner-solve operator), double on the FP64 path.
+template <typename PartT, typename ProxyReal>
+__global__ void __launch_bounds__(64)
+k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __restrict__ sigma,
+          const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
+          const double* __restrict__ ny, const double* __restrict__ w, const double* __restrict__ kap,
+          const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx, double Cy,
+          double2* __restrict__ T) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double tx = 0, ty = 0;
@@ -377,18 +551,23 @@ __global__ void k_correct(const PartT* __restrict__ part, int splits, int N, con
     double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
     tx += dg * t0;
     ty += dg * t1;
-    double X = x[i], Y = y[i];
-    double cx = 0, cy = 0;
+    // proxies in cell-centred coordinates (exact in double, accurate in float)
+    ProxyReal X = (ProxyReal)(x[i] - Cx), Y = (ProxyReal)(y[i] - Cy);
+    ProxyReal m0 = (ProxyReal)n0, m1 = (ProxyReal)n1;
+    ProxyReal cx = 0, cy = 0;
     for (int p = 0; p < M; ++p) {
-        double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
-        double fx = xi[p], fy = xi[M + p];
-        double r2 = rx * rx + ry * ry;
-        double cc = (rx * n0 + ry * n1) * (rx * fx + ry * fy) / (r2 * r2);
+        ProxyReal rx = X - (ProxyReal)(yp[2 * p] - Cx), ry = Y - (ProxyReal)(yp[2 * p + 1] - Cy);
+        ProxyReal fx = (ProxyReal)xi[p], fy = (ProxyReal)xi[M + p];
+        ProxyReal r2 = rx * rx + ry * ry;
+        ProxyReal inv;
+        if constexpr (sizeof(ProxyReal) == 4) inv = rcp_approx(r2);
+        else inv = (ProxyReal)1 / r2;
+        ProxyReal cc = ((rx * m0 + ry * m1) * inv) * ((rx * fx + ry * fy) * inv);
         cx += cc * rx;
         cy += cc * ry;
     }
-    tx += -cx / kPi;
-    ty += -cy / kPi;
+    tx += -(double)cx / kPi;
+    ty += -(double)cy / kPi;
     T[i] = make_double2(tx, ty);
 }
 
@@ -432,9 +611,14 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
     bool f32 = precision == BIE_MIXED;
+    bool df = precision == BIE_DF64;
     k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], f32 ? c->ws.src32 : nullptr,
                                      c->ws.src64);
     BIE_LAUNCH(c, "k_pack");
+    if (df) {
+        k_pack_df<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], (SrcDF*)c->ws.srcdf);
+        BIE_LAUNCH(c, "k_pack_df");
+    }
     k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
     double sx[9], sy[9];
@@ -455,6 +639,21 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
                                                                    (float2*)c->ws.part);
         BIE_LAUNCH(c, "k_near32");
         if (int rc = prof_end(c)) return rc;
+    } else if (df) {
+        Shifts9d s9;
+        for (int k = 0; k < 9; ++k) {
+            s9.x[k] = sx[k];
+            s9.y[k] = sy[k];
+        }
+        splits = c->near_splitsdf;
+        int tiles = (N + kNearThreads - 1) / kNearThreads;
+        int chunk = (N + splits - 1) / splits;
+        dim3 grid(tiles, splits);
+        if (int rc = prof_begin(c, 2)) return rc;
+        k_near_df<<<grid, kNearThreads, 0, c->stream>>>(c->x, c->y, c->nx, c->ny, (const SrcDF*)c->ws.srcdf, N, chunk,
+                                                        s9, c->C[0], c->C[1], (double2*)c->ws.part);
+        BIE_LAUNCH(c, "k_near_df");
+        if (int rc = prof_end(c)) return rc;
     } else {
         Shifts9d s9;
         for (int k = 0; k < 9; ++k) {
@@ -471,34 +670,30 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
         BIE_LAUNCH(c, "k_near64");
         if (int rc = prof_end(c)) return rc;
     }
-    {
-        int twm = 2 * c->m;
-        int dbs = (256 / twm) * twm;
-        if (dbs < twm) dbs = twm;
-        int chunk = (N + kDiscBlocks - 1) / kDiscBlocks;
-        size_t shm = (size_t)dbs * 4 * sizeof(double);
-        if (f32)
-            k_disc<float><<<kDiscBlocks, dbs, shm, c->stream>>>(c->ws.src64, N, chunk, c->m, c->gl_s, c->e1[0],
-                                                                c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1],
-                                                                c->mu, c->ws.gpart);
-        else
-            k_disc<double><<<kDiscBlocks, dbs, shm, c->stream>>>(c->ws.src64, N, chunk, c->m, c->gl_s,
-                                                                 c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0],
-                                                                 c->C[1], c->mu, c->ws.gpart);
-        BIE_LAUNCH(c, "k_disc");
-    }
+    if (f32)
+        k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
+            c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
+            c->ws.gpart);
+    else
+        k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
+            c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
+            c->ws.gpart);
+    BIE_LAUNCH(c, "k_disc");
     double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscBlocks, c->m, c->M, c->ws.bodyF,
+    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
                                                           c->nb, l1, l2, c->P, c->ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double2* T = reinterpret_cast<double2*>(c->ws.T);
+    const int gs64 = (N + 63) / 64;
     if (f32)
-        k_correct<float2><<<gs, bs, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y, c->nx,
-                                                    c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M, T);
+        k_correct<float2, float><<<gs64, 64, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y,
+                                                             c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M,
+                                                             c->C[0], c->C[1], T);
     else
-        k_correct<double2><<<gs, bs, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x, c->y,
-                                                     c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M, T);
+        k_correct<double2, double><<<gs64, 64, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x,
+                                                               c->y, c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi,
+                                                               c->M, c->C[0], c->C[1], T);
     BIE_LAUNCH(c, "k_correct");
     if (int rc = close_apply(c, sigma, c->ws.T)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, c->ws.bodyF,
@@ -585,17 +780,13 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     BIE_LAUNCH(c, "k_pack");
     k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
-    int twm = 2 * c->m;
-    int dbs = (256 / twm) * twm;
-    if (dbs < twm) dbs = twm;
-    int chunk = (N + kDiscBlocks - 1) / kDiscBlocks;
-    k_disc<double><<<kDiscBlocks, dbs, (size_t)dbs * 4 * sizeof(double), c->stream>>>(
-        c->ws.src64, N, chunk, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
+    k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
+        c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
         c->ws.gpart);
     BIE_LAUNCH(c, "k_disc");
     double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscBlocks, c->m, c->M, c->ws.bodyF,
+    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
                                                           c->nb, l1, l2, c->P, c->ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double sx[9], sy[9];
@@ -647,22 +838,18 @@ int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws
     k_near32<kNear32TPT><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk, s9,
                                                                              (float2*)ws.part);
     BIE_LAUNCH(c, "k_near32");
-    const int twm = 2 * c->m;
-    int dbs = (256 / twm) * twm;
-    if (dbs < twm) dbs = twm;
-    const int dchunk = (N + kDiscBlocks - 1) / kDiscBlocks;
-    k_disc<float><<<kDiscBlocks, dbs, (size_t)dbs * 4 * sizeof(double), c->stream>>>(
-        ws.src64, N, dchunk, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
-        ws.gpart);
+    k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
+        ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu, ws.gpart);
     BIE_LAUNCH(c, "k_disc");
     const double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     const double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscBlocks, c->m, c->M, ws.bodyF, c->nb, l1,
+    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscSplits, c->m, c->M, ws.bodyF, c->nb, l1,
                                                           l2, c->P, ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double2* T = reinterpret_cast<double2*>(ws.T);
-    k_correct<float2><<<gs, bs, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x, c->y, c->nx, c->ny,
-                                                c->w, c->kap, c->yp, ws.xi, c->M, T);
+    k_correct<float2, float><<<(N + 63) / 64, 64, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x,
+                                                                  c->y, c->nx, c->ny, c->w, c->kap, c->yp, ws.xi,
+                                                                  c->M, c->C[0], c->C[1], T);
     BIE_LAUNCH(c, "k_correct");
     if (int rc = close_apply(c, sigma, ws.T)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF,

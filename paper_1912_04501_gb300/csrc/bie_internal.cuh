@@ -24,7 +24,8 @@ constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
 constexpr int kNearThreads = 128;     // threads per near-sum block
 constexpr int kNearTile = 256;        // sources staged per shared-memory tile
 constexpr int kNear32TPT = 2;         // targets per thread, single precision
-constexpr int kDiscBlocks = 96;       // source splits of the wall-discrepancy kernel
+constexpr int kDiscBlocks = 96;       // capacity of the discrepancy partial buffer (splits)
+constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
@@ -63,6 +64,7 @@ struct Workspace {
     double* out = nullptr;      // 2N  staging for host outputs
     Src64* src64 = nullptr;   // N
     float4* src32 = nullptr;    // N
+    void* srcdf = nullptr;      // N double-float source records (32 B)
     double* bodyF = nullptr;    // 3 nb  (F_x, F_y, tau) per body
     void* part = nullptr;       // near-sum partials: splits x N (float2 or double2)
     size_t part_bytes = 0;
@@ -81,6 +83,7 @@ struct Solver {
     double* d = nullptr;     // 2N correction (mixed)
     double* h = nullptr;     // kmax + 2 dot products
     double* red = nullptr;   // reduction scratch
+    double* dpart = nullptr; // (kmax + 2) x 64 partial dot products
     double* sigma_prev = nullptr;  // 2N warm start of the next step
     bool have_prev = false;
 };
@@ -111,12 +114,12 @@ struct bie_ctx {
     bie::Workspace ws;
     bie::Solver sv;
     bie::Close cl;
-    int near_splits32 = 1, near_splits64 = 1;
+    int near_splits32 = 1, near_splits64 = 1, near_splitsdf = 1;
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
     long long launches = 0;
     std::vector<cudaEvent_t> ev_pool;   // 2 per recorded launch
-    std::vector<int> ev_kind;           // 0 = near32, 1 = near64 per pair
+    std::vector<int> ev_kind;           // 0 = near32, 1 = near64, 2 = near df64 per pair
     int ev_used = 0;
     bie_profile_info prof_acc{};
     std::string err;

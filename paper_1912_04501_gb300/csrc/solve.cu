@@ -23,25 +23,43 @@ __device__ inline double wsum(double v) {
     return v;
 }
 
-// h[j] = V_j . w for j < nv (one CTA per j); deterministic.
-__global__ void k_mdot(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, int n,
-                       double* __restrict__ h) {
-    __shared__ double red[32];
-    int j = blockIdx.x;
-    const double* v = V + (size_t)j * ld;
-    double s = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * w[i];
-    s = wsum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        t = wsum(t);
-        if (threadIdx.x == 0) h[j] = t;
+// Multi-vector dot products h[j] = V_j . w (j < nv) in two deterministic
+// passes: block b of kDotChunks sums its slice of the vectors (one warp per
+// vector j at a time), then k_mdot_fin adds the kDotChunks partials of each j.
+constexpr int kDotChunks = 64;
+
+__global__ void __launch_bounds__(256)
+k_mdot_part(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, int n,
+            double* __restrict__ part) {
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < nv; j += nw) {
+        const double* v = V + (size_t)j * ld;
+        double s = 0;
+        for (int i = i0 + lane; i < i1; i += 32) s += v[i] * w[i];
+        s = wsum(s);
+        if (lane == 0) part[(size_t)j * gridDim.x + blockIdx.x] = s;
     }
 }
 
-// w -= sum_j h[j] V_j ;  if acc: hacc[j] += h[j]
+__global__ void k_mdot_fin(const double* __restrict__ part, int nchunk, int nv, double* __restrict__ h) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nv) return;
+    double s = 0;
+    for (int b = 0; b < nchunk; ++b) s += part[(size_t)j * nchunk + b];
+    h[j] = s;
+}
+
+static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, int n, double* h) {
+    k_mdot_part<<<kDotChunks, 256, 0, c->stream>>>(V, ld, nv, w, n, c->sv.dpart);
+    BIE_LAUNCH(c, "k_mdot_part");
+    k_mdot_fin<<<(nv + 127) / 128, 128, 0, c->stream>>>(c->sv.dpart, kDotChunks, nv, h);
+    BIE_LAUNCH(c, "k_mdot_fin");
+    return BIE_OK;
+}
+
+// w -= sum_j h[j] V_j
 __global__ void k_mupdate(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h,
                           double* __restrict__ w, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,8 +96,7 @@ __global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const
 }
 
 static int dnorm(bie_ctx* c, const double* v, int n, double* out) {
-    k_mdot<<<1, 1024, 0, c->stream>>>(v, 0, 1, v, n, c->sv.red);
-    BIE_LAUNCH(c, "k_mdot");
+    if (int rc = mdot(c, v, 0, 1, v, n, c->sv.red)) return rc;
     double h;
     BIE_CUDA(c, cudaMemcpyAsync(&h, c->sv.red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -94,6 +111,7 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, double 
                        double* est, int* n_apply) {
     const int n = 2 * c->N;
     const int bs = 256, gs = (n + bs - 1) / bs;
+    const int gs64 = (n + 63) / 64;
     const int kmax = c->sv.kmax;
     const size_t ld = (size_t)n;
     double* V = c->sv.V;
@@ -112,16 +130,13 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, double 
         // CGS2
         double* h1 = c->sv.h;
         double* h2 = c->sv.h + (kmax + 2);
-        k_mdot<<<k + 1, 256, 0, c->stream>>>(V, ld, k + 1, w, n, h1);
-        BIE_LAUNCH(c, "k_mdot");
-        k_mupdate<<<gs, bs, 0, c->stream>>>(V, ld, k + 1, h1, w, n);
+        if ((rc = mdot(c, V, ld, k + 1, w, n, h1))) return rc;
+        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h1, w, n);
         BIE_LAUNCH(c, "k_mupdate");
-        k_mdot<<<k + 1, 256, 0, c->stream>>>(V, ld, k + 1, w, n, h2);
-        BIE_LAUNCH(c, "k_mdot");
-        k_mupdate<<<gs, bs, 0, c->stream>>>(V, ld, k + 1, h2, w, n);
+        if ((rc = mdot(c, V, ld, k + 1, w, n, h2))) return rc;
+        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h2, w, n);
         BIE_LAUNCH(c, "k_mupdate");
-        k_mdot<<<1, 1024, 0, c->stream>>>(w, 0, 1, w, n, h2 + (kmax + 2));
-        BIE_LAUNCH(c, "k_mdot");
+        if ((rc = mdot(c, w, 0, 1, w, n, h2 + (kmax + 2)))) return rc;
         std::vector<double> hh(2 * (kmax + 2) + 1);
         BIE_CUDA(c, cudaMemcpyAsync(hh.data(), h1, (2 * (kmax + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
@@ -188,8 +203,8 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
     const int max_outer = mixed ? c->opts.max_refine : 20;
     double rel = 0;
     for (int outer = 0; outer <= max_outer; ++outer) {
-        // true FP64 residual
-        rc = apply_device(c, x, c->sv.r, BIE_FP64);
+        // FP64-class residual (native double, or double-float when mixed)
+        rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : BIE_FP64);
         if (rc) return rc;
         ++inf.applies64;
         k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);

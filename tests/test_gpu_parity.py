@@ -68,6 +68,19 @@ def test_apply_fp64(pair):
         assert _rel(y, ref) < 1e-10
 
 
+def test_apply_double_float(pair):
+    """BIE_DF64: near pair sums in double-float arithmetic.  Same tolerance as
+    the FP64 operator (1e-10) against the oracle; against the native FP64
+    operator the difference is the 48-bit input rounding, ~1e-12."""
+    cell, ctx, op = pair
+    sigma = np.random.default_rng(12).standard_normal(2 * ctx.N)
+    y = ctx.apply(sigma, precision=bie.BIE_DF64)
+    ref = op.apply(sigma.reshape(-1, 2)).ravel()
+    assert _rel(y, ref) < 1e-10
+    y64 = ctx.apply(sigma, precision=bie.BIE_FP64)
+    assert _rel(y, y64) < 1e-11
+
+
 def test_apply_mixed(pair):
     cell, ctx, op = pair
     sigma = np.random.default_rng(2).standard_normal(2 * ctx.N)
@@ -103,15 +116,21 @@ def test_solve_fp64_and_velocities(pair):
     assert abs(mu - op.mu_eff(ref)) < 1e-9
 
 
-def test_solve_mixed_refinement():
+@pytest.mark.parametrize("residual", ["fp64", "df64"])
+def test_solve_mixed_refinement(residual):
     cell = CELLS["five_tiles"]()
-    ctx = bie.Context(cell, precision=bie.BIE_MIXED, gmres_tol=1e-12)
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED, gmres_tol=1e-12,
+                      residual=bie.BIE_FP64 if residual == "fp64" else bie.BIE_DF64)
     op = oracle_operator(cell)
     sig, info = ctx.solve()
     assert info["rel_residual"] <= 1e-12
     assert info["applies32"] > info["applies64"]
     ref, _, _ = obie.solve(op, tol=1e-12)
     assert _rel(sig, ref.ravel()) < 1e-9
+    # the residual the solver reported is a true FP64 residual
+    b = ctx.rhs()
+    r = b - ctx.apply(sig, precision=bie.BIE_FP64)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-12
     ctx.close()
 
 
@@ -219,6 +238,7 @@ def test_close_evaluation_parity(gap, n):
     assert _rel(y, ref) < 1e-10
     y32 = ctx.apply(sigma, precision=bie.BIE_MIXED)
     assert _rel(y32, ref) < 5e-5
+    assert _rel(ctx.apply(sigma, precision=bie.BIE_DF64), ref) < 1e-10
     sig, info = ctx.solve()
     sref, _, _ = obie.solve(op, tol=1e-12)
     assert _rel(sig, sref.ravel()) < 1e-9
