@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mixed-only", action="store_true",
+                   help="time the mixed-precision steps only (no plain-FP64 comparison, no end-to-end loop); "
+                        "used for kernel launch lists")
     return p.parse_args()
 
 
@@ -258,6 +261,16 @@ def main():
         pairs_all, t_ms = pairs, total_ms
     value = pairs_all / (t_ms / 1e3) / 1e9
     ms_per_step = t_ms / args.steps
+
+    if args.mixed_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": ms_per_step, "mixed_only": True,
+                              "gpu_launches": prof["launches"], "profile": prof}), flush=True)
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     # plain FP64 solve per step (reported beside the mixed one)
     ctx64 = bie.Context(cell, precision=bie.BIE_FP64, device=local)

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "bie_internal.cuh"
 
@@ -29,8 +30,8 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 
 static void free_all(bie_ctx* c) {
     void* ptrs[] = {c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body, c->tgt32, c->gl_s, c->A, c->beta,
-                    c->P, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.srcdf, c->ws.bodyF,
-                    c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
+                    c->P, c->wall, c->next.A, c->next.beta, c->next.P, c->next.wall, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.srcdf, c->ws.bodyF,
+                    c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->ws.vpart, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
                     c->sv.d, c->sv.h, c->sv.red, c->sv.dpart, c->sv.sigma_prev, c->cl.slots, c->cl.count,
                     c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab,
                     c->cl.dtab_off};
@@ -39,6 +40,11 @@ static void free_all(bie_ctx* c) {
     for (auto e : c->ev_pool)
         if (e) cudaEventDestroy(e);
     c->ev_pool.clear();
+    if (c->next_done) cudaEventDestroy(c->next_done);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
 }
 
 // Lattice of Sec. 7: e1 = (L1, 0) fixed, e2 = (s0 + gamma t L2 - L1 round(.), L2).
@@ -253,6 +259,13 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->A, (size_t)R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, 2 * (size_t)Cc);
     rc = rc ? rc : dalloc(c, &c->P, (size_t)Cc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->wall, 16 * 2 * (size_t)m);
+    rc = rc ? rc : dalloc(c, &c->next.A, (size_t)R * Cc);
+    rc = rc ? rc : dalloc(c, &c->next.beta, 2 * (size_t)Cc);
+    rc = rc ? rc : dalloc(c, &c->next.P, (size_t)Cc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->next.wall, 16 * 2 * (size_t)m);
+    if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
     rc = rc ? rc : dalloc(c, &c->yp, 2 * (size_t)M);
     rc = rc ? rc : dalloc(c, &c->scal, 3 * (size_t)nb + 8);
     rc = rc ? rc : dalloc(c, &c->ws.sigma, 2 * (size_t)n);
@@ -265,6 +278,7 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->ws.gpart, (size_t)kDiscBlocks * 2 * m * 4);
     rc = rc ? rc : dalloc(c, &c->ws.xi, 2 * (size_t)M);
     rc = rc ? rc : dalloc(c, &c->ws.T, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->ws.vpart, (size_t)nb * kVelSplits * 3);
     rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1) * 2 * n);
     rc = rc ? rc : dalloc(c, &c->sv.w, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.r, 2 * (size_t)n);
@@ -458,6 +472,14 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
     double* dom = c->scal + 2 * c->nb;
     double* dmu = c->scal + 3 * c->nb;
     for (int s = 0; s < n_steps; ++s) {
+        // the next step's lattice is known now: fit its proxies on the side
+        // stream while this step solves (it only depends on e2(t + dt))
+        double e2n[2];
+        lattice_at(c, c->t + dt, e2n);
+        BIE_CUDA(c, cudaEventRecord(c->next_done, c->stream));  // inputs of the fit are ready
+        BIE_CUDA(c, cudaStreamWaitEvent(c->side, c->next_done, 0));
+        if (int rc = build_proxy_fit_to(c, e2n, c->next, c->side)) return rc;
+        BIE_CUDA(c, cudaEventRecord(c->next_done, c->side));
         int rc = rhs_device(c, c->sv.b);
         if (rc) return rc;
         bool guess = c->opts.warm_start == 1 && c->sv.have_prev;
@@ -476,12 +498,19 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         if (mu_eff_out)
             BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + s, dmu, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         c->t += dt;
-        lattice_at(c, c->t, c->e2);
+        c->e2[0] = e2n[0];
+        c->e2[1] = e2n[1];
         k_euler<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->body, c->nb, dv, dom, dt, c->e1[0], c->e1[1],
                                                             c->e2[0], c->e2[1], c->C[0], c->C[1]);
         BIE_LAUNCH(c, "k_euler");
-        rc = rebuild(c);
-        if (rc) return rc;
+        // adopt the prefetched proxy fit, then rebuild nodes and close pairs
+        BIE_CUDA(c, cudaStreamWaitEvent(c->stream, c->next_done, 0));
+        std::swap(c->A, c->next.A);
+        std::swap(c->beta, c->next.beta);
+        std::swap(c->P, c->next.P);
+        std::swap(c->wall, c->next.wall);
+        if ((rc = build_geometry(c))) return rc;
+        if ((rc = build_close(c))) return rc;
     }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;

@@ -362,6 +362,45 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
 }
 
 // ---------------------------------------------------------------------------
+// Wall table (per geometry): for each collocation point (L points, then D
+// points) the point minus each of its six far-image shifts, and the wall
+// normal used for the traction.
+__global__ void k_wall_table(int m, const double* __restrict__ gl_s, double e1x, double e1y, double e2x,
+                             double e2y, double Cx, double Cy, double* __restrict__ wall) {
+    int wp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (wp >= 2 * m) return;
+    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
+    wall_normals(e1, e2, nl, nd);
+    const bool isL = wp < m;
+    const double s = gl_s[isL ? wp : wp - m];
+    double X, Y, ax, ay, bx, by;
+    if (isL) {
+        X = Cx - 0.5 * e1x + s * e2x;
+        Y = Cy - 0.5 * e1y + s * e2y;
+        ax = e1x; ay = e1y; bx = e2x; by = e2y;
+    } else {
+        X = Cx - 0.5 * e2x + s * e1x;
+        Y = Cy - 0.5 * e2y + s * e1y;
+        ax = e2x; ay = e2y; bx = e1x; by = e1y;
+    }
+    double* o = wall + 16 * wp;
+    for (int k = -1; k <= 1; ++k) {
+        o[2 * (k + 1)] = X - (-2.0 * ax + k * bx);
+        o[2 * (k + 1) + 1] = Y - (-2.0 * ay + k * by);
+        o[2 * (k + 4)] = X - (ax + k * bx);
+        o[2 * (k + 4) + 1] = Y - (ay + k * by);
+    }
+    o[12] = isL ? nl[0] : nd[0];
+    o[13] = isL ? nl[1] : nd[1];
+}
+
+int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st) {
+    k_wall_table<<<(2 * c->m + 63) / 64, 64, 0, st>>>(c->m, c->gl_s, c->e1[0], c->e1[1], e2[0], e2[1], c->C[0],
+                                                      c->C[1], wall);
+    BIE_LAUNCH(c, "k_wall_table");
+    return BIE_OK;
+}
+
 // Wall discrepancy (Sec. 6.2 step 2).  For a collocation point x on L,
 //   S_near(x + e1) - S_near(x) = sum_n sum_j [K(x, y_j - 2 e1 + n e2) - K(x, y_j + e1 + n e2)] q_j
 // and on D with the roles of e1, e2 exchanged; K is the velocity kernel G or
@@ -377,37 +416,20 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ gl_s, double e1x, double e1y,
-       double e2x, double e2y, double Cx, double Cy, double mu, double* __restrict__ gpart) {
+k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ wall, double mu,
+       double* __restrict__ gpart) {
     __shared__ double red[4][33];
     const int wp = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
-    double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
-    wall_normals(e1, e2, nl, nd);
-    const bool isL = wp < m;
-    const double s = gl_s[isL ? wp : wp - m];
-    double X, Y, nu0, nu1, ax, ay, bx, by;  // a: the step across the wall pair, b: along it
-    if (isL) {
-        X = Cx - 0.5 * e1x + s * e2x;
-        Y = Cy - 0.5 * e1y + s * e2y;
-        nu0 = nl[0];
-        nu1 = nl[1];
-        ax = e1x; ay = e1y; bx = e2x; by = e2y;
-    } else {
-        X = Cx - 0.5 * e2x + s * e1x;
-        Y = Cy - 0.5 * e2y + s * e1y;
-        nu0 = nd[0];
-        nu1 = nd[1];
-        ax = e2x; ay = e2y; bx = e1x; by = e1y;
-    }
-    // the six far images, relative to the collocation point: plus (-2a + kb), minus (a + kb)
+    // per-geometry table: collocation point minus each of the six far-image
+    // shifts (plus images -2a + kb, then minus images a + kb), and the normal
+    const double* wt = wall + 16 * wp;
     Real ox[6], oy[6];
-    for (int k = -1; k <= 1; ++k) {
-        ox[k + 1] = (Real)(X - (-2.0 * ax + k * bx));
-        oy[k + 1] = (Real)(Y - (-2.0 * ay + k * by));
-        ox[k + 4] = (Real)(X - (ax + k * bx));
-        oy[k + 4] = (Real)(Y - (ay + k * by));
+#pragma unroll
+    for (int im = 0; im < 6; ++im) {
+        ox[im] = (Real)wt[2 * im];
+        oy[im] = (Real)wt[2 * im + 1];
     }
-    const Real n0 = (Real)nu0, n1 = (Real)nu1;
+    const Real n0 = (Real)wt[12], n1 = (Real)wt[13];
     Real ux = 0, uy = 0, tx = 0, ty = 0;
     const int per = (N + nsp - 1) / nsp;
     const int j0 = sp * per, j1 = min(N, j0 + per);
@@ -448,114 +470,100 @@ k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ g
     }
 }
 
-// g~ and xi = P g~ (Sec. 6.2 step 3).  One CTA of 256 threads: the partials
-// of the discrepancy blocks are reduced in a fixed order, g~ is assembled in
-// shared memory, and each warp computes rows of P g~ with its lanes over the
-// columns.  The dot products are compensated (Ogita, Rump & Oishi's Dot2:
-// FMA-exact products, error-free sums): P has entries up to ~1/lam, so a
-// plain double-precision product would add relative noise ~1e-11 to the
-// correction and put a floor under the GMRES residual.
-__global__ void __launch_bounds__(256)
+// g~ and xi = P g~ (Sec. 6.2 step 3).  One warp-sized CTA per row r of P (2M
+// CTAs): GB300's FP64 pipe is narrow, so the compensated products are spread
+// over as many SMs as there are rows.  Every CTA rebuilds g~ from the kDiscSplits
+// partials of the discrepancy kernel (fixed order: deterministic) and then
+// computes xi_r with a compensated dot product (Ogita, Rump & Oishi's Dot2:
+// FMA-exact products, error-free sums; P has entries up to ~1/lam, so a plain
+// double-precision product would add relative noise ~1e-11 to the correction
+// and put a floor under the GMRES residual).
+__global__ void __launch_bounds__(32)
 k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __restrict__ bodyF, int nb,
      double l1, double l2, const double* __restrict__ P, double* __restrict__ xi) {
-    extern __shared__ double d[];  // 8m (g~) followed by 8m (raw g)
-    double* g = d + 8 * m;
-    __shared__ double Fs[2];
-    const int tid = threadIdx.x;
-    const int nv = 8 * m;  // 2m wall points x (u_x, u_y, t_x, t_y)
-    if (tid == 0) {
-        double fx = 0, fy = 0;
-        for (int b = 0; b < nb; ++b) {
-            fx += bodyF[3 * b];
-            fy += bodyF[3 * b + 1];
-        }
-        Fs[0] = fx;
-        Fs[1] = fy;
+    extern __shared__ double d[];  // 8m: g~
+    const int lane = threadIdx.x, r = blockIdx.x;
+    const int nv = 8 * m;
+    double fx = 0, fy = 0;
+    for (int b = lane; b < nb; b += 32) {
+        fx += bodyF[3 * b];
+        fy += bodyF[3 * b + 1];
     }
-    for (int v = tid; v < nv; v += blockDim.x) {
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        int b = 0;
-        for (; b + 4 <= nblk; b += 4) {
-            a0 += gpart[(size_t)b * nv + v];
-            a1 += gpart[(size_t)(b + 1) * nv + v];
-            a2 += gpart[(size_t)(b + 2) * nv + v];
-            a3 += gpart[(size_t)(b + 3) * nv + v];
-        }
-        for (; b < nblk; ++b) a0 += gpart[(size_t)b * nv + v];
-        g[v] = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
     }
-    __syncthreads();
-    for (int wp = tid; wp < 2 * m; wp += blockDim.x) {
-        double g0 = g[4 * wp], g1 = g[4 * wp + 1], g2 = g[4 * wp + 2], g3 = g[4 * wp + 3];
+    for (int wp = lane; wp < 2 * m; wp += 32) {
+        double g[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double a = 0;
+            for (int b = 0; b < nblk; ++b) a += gpart[(size_t)b * nv + 4 * wp + c];
+            g[c] = a;
+        }
         if (wp < m) {  // L: rows of blocks 1 (velocity) and 2 (traction)
-            int l = wp;
-            d[l] = -g0;
-            d[m + l] = -g1;
-            d[2 * m + l] = Fs[0] / (2.0 * l2) - g2;
-            d[3 * m + l] = Fs[1] / (2.0 * l2) - g3;
+            const int l = wp;
+            d[l] = -g[0];
+            d[m + l] = -g[1];
+            d[2 * m + l] = fx / (2.0 * l2) - g[2];
+            d[3 * m + l] = fy / (2.0 * l2) - g[3];
         } else {  // D: blocks 3 and 4
-            int l = wp - m;
-            d[4 * m + l] = -g0;
-            d[5 * m + l] = -g1;
-            d[6 * m + l] = Fs[0] / (2.0 * l1) - g2;
-            d[7 * m + l] = Fs[1] / (2.0 * l1) - g3;
+            const int l = wp - m;
+            d[4 * m + l] = -g[0];
+            d[5 * m + l] = -g[1];
+            d[6 * m + l] = fx / (2.0 * l1) - g[2];
+            d[7 * m + l] = fy / (2.0 * l1) - g[3];
         }
     }
-    __syncthreads();
-    const int C = 2 * M, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < C; r += nw) {
-        double s = 0, e = 0;
-        for (int cc = lane; cc < nv; cc += 32) {
-            double a = P[r + (size_t)cc * C], b = d[cc];
-            double p = a * b;
-            double pe = fma(a, b, -p);
-            double t = s + p;
-            double z = t - s;
-            e += pe + ((s - (t - z)) + (p - z));
-            s = t;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double s2 = __shfl_xor_sync(0xffffffffu, s, o);
-            double e2 = __shfl_xor_sync(0xffffffffu, e, o);
-            double t = s + s2;
-            double z = t - s;
-            e = e + e2 + ((s - (t - z)) + (s2 - z));
-            s = t;
-        }
-        if (lane == 0) xi[r] = s + e;
+    __syncwarp();
+    double s = 0, e = 0;
+    for (int cc = lane; cc < nv; cc += 32) {
+        const double a = P[(size_t)r * nv + cc], b = d[cc];
+        const double p = a * b;
+        const double pe = fma(a, b, -p);
+        const double t = s + p;
+        const double z = t - s;
+        e += pe + ((s - (t - z)) + (p - z));
+        s = t;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const double e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        const double t = s + s2;
+        const double z = t - s;
+        e = e + e2 + ((s - (t - z)) + (s2 - z));
+        s = t;
+    }
+    if (lane == 0) xi[r] = s + e;
 }
 
 // T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy
 // traction.  ProxyReal = float on the single-precision path (rcp.approx, the
 // inner-solve operator), double on the FP64 path.
 template <typename PartT, typename ProxyReal>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(256)
 k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __restrict__ sigma,
           const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
           const double* __restrict__ ny, const double* __restrict__ w, const double* __restrict__ kap,
           const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx, double Cy,
           double2* __restrict__ T) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    // kCorrLanes lanes per target: they split the near-sum partials and the
+    // proxies, then combine with shuffles (fixed order: deterministic)
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kCorrLanes;
+    const int sub = threadIdx.x % kCorrLanes;
+    const int i = g < N ? g : N - 1;
     double tx = 0, ty = 0;
-    for (int s = 0; s < splits; ++s) {
+    for (int s = sub; s < splits; s += kCorrLanes) {
         PartT p = part[(size_t)s * N + i];
         tx += (double)p.x;
         ty += (double)p.y;
     }
-    double2 sg = sigma[i];
-    double n0 = nx[i], n1 = ny[i];
-    double t0 = -n1, t1 = n0;  // unit tangent
-    double qx = sg.x * w[i], qy = sg.y * w[i];
-    double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
-    tx += dg * t0;
-    ty += dg * t1;
+    const double n0 = nx[i], n1 = ny[i];
     // proxies in cell-centred coordinates (exact in double, accurate in float)
-    ProxyReal X = (ProxyReal)(x[i] - Cx), Y = (ProxyReal)(y[i] - Cy);
-    ProxyReal m0 = (ProxyReal)n0, m1 = (ProxyReal)n1;
+    const ProxyReal X = (ProxyReal)(x[i] - Cx), Y = (ProxyReal)(y[i] - Cy);
+    const ProxyReal m0 = (ProxyReal)n0, m1 = (ProxyReal)n1;
     ProxyReal cx = 0, cy = 0;
-    for (int p = 0; p < M; ++p) {
+    for (int p = sub; p < M; p += kCorrLanes) {
         ProxyReal rx = X - (ProxyReal)(yp[2 * p] - Cx), ry = Y - (ProxyReal)(yp[2 * p + 1] - Cy);
         ProxyReal fx = (ProxyReal)xi[p], fy = (ProxyReal)xi[M + p];
         ProxyReal r2 = rx * rx + ry * ry;
@@ -568,7 +576,17 @@ k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __re
     }
     tx += -(double)cx / kPi;
     ty += -(double)cy / kPi;
-    T[i] = make_double2(tx, ty);
+#pragma unroll
+    for (int o = kCorrLanes / 2; o > 0; o >>= 1) {
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+    if (sub != 0 || g >= N) return;
+    const double2 sg = sigma[i];
+    const double t0 = -n1, t1 = n0;  // unit tangent
+    const double qx = sg.x * w[i], qy = sg.y * w[i];
+    const double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
+    T[i] = make_double2(tx + dg * t0, ty + dg * t1);
 }
 
 __global__ void k_finish(const double2* __restrict__ T, const double2* __restrict__ sigma, int N,
@@ -671,27 +689,23 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
         if (int rc = prof_end(c)) return rc;
     }
     if (f32)
-        k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
-            c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
-            c->ws.gpart);
+        k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
     else
-        k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
-            c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
-            c->ws.gpart);
+        k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
     BIE_LAUNCH(c, "k_disc");
     double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
+    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
                                                           c->nb, l1, l2, c->P, c->ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double2* T = reinterpret_cast<double2*>(c->ws.T);
-    const int gs64 = (N + 63) / 64;
+    const int gsc = (N * kCorrLanes + 255) / 256;
     if (f32)
-        k_correct<float2, float><<<gs64, 64, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y,
+        k_correct<float2, float><<<gsc, 256, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y,
                                                              c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M,
                                                              c->C[0], c->C[1], T);
     else
-        k_correct<double2, double><<<gs64, 64, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x,
+        k_correct<double2, double><<<gsc, 256, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x,
                                                                c->y, c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi,
                                                                c->M, c->C[0], c->C[1], T);
     BIE_LAUNCH(c, "k_correct");
@@ -714,14 +728,19 @@ int rhs_device(bie_ctx* c, double* b) {
 // u(x^c) = sum_images sum_j G(x^c, y_j + s) q_j + sum_p G(x^c, y_p) xi_p
 //          - sum_p G(C, y_p) xi_p;  curl by the closed form of the Stokeslet.
 // ---------------------------------------------------------------------------
-__global__ void k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __restrict__ body,
-                             const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx,
-                             double Cy, double mu, double gamma, double* __restrict__ v, double* __restrict__ om) {
+__global__ void __launch_bounds__(256)
+k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __restrict__ body,
+             const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx, double Cy,
+             double* __restrict__ vpart) {
+    // block (b, s): body b's centroid against source split s of gridDim.y;
+    // split 0 also adds the proxy terms.  vpart[(b * splits + s) * 3 + c].
     __shared__ double red[33];
-    int b = blockIdx.x;
-    double X = body[8 * b + 2], Y = body[8 * b + 3];
+    const int b = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+    const double X = body[8 * b + 2], Y = body[8 * b + 3];
     double ux = 0, uy = 0, cu = 0;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int per = (N + nsp - 1) / nsp;
+    const int j0 = sp * per, j1 = min(N, j0 + per);
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         Src64 q = src[j];
         for (int k = 0; k < 9; ++k) {
             double rx = X - (q.x + sh.x[k]), ry = Y - (q.y + sh.y[k]);
@@ -733,32 +752,51 @@ __global__ void k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, 
             cu += (ry * q.z - rx * q.w) / r2;
         }
     }
-    for (int p = threadIdx.x; p < M; p += blockDim.x) {
-        double fx = xi[p], fy = xi[M + p];
-        double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
-        double r2 = rx * rx + ry * ry;
-        double rq = (rx * fx + ry * fy) / r2;
-        double l = -0.5 * log(r2);
-        ux += l * fx + rx * rq;
-        uy += l * fy + ry * rq;
-        cu += (ry * fx - rx * fy) / r2;
-        rx = Cx - yp[2 * p];
-        ry = Cy - yp[2 * p + 1];
-        r2 = rx * rx + ry * ry;
-        rq = (rx * fx + ry * fy) / r2;
-        l = -0.5 * log(r2);
-        ux -= l * fx + rx * rq;
-        uy -= l * fy + ry * rq;
+    if (sp == 0) {
+        for (int p = threadIdx.x; p < M; p += blockDim.x) {
+            double fx = xi[p], fy = xi[M + p];
+            double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
+            double r2 = rx * rx + ry * ry;
+            double rq = (rx * fx + ry * fy) / r2;
+            double l = -0.5 * log(r2);
+            ux += l * fx + rx * rq;
+            uy += l * fy + ry * rq;
+            cu += (ry * fx - rx * fy) / r2;
+            rx = Cx - yp[2 * p];
+            ry = Cy - yp[2 * p + 1];
+            r2 = rx * rx + ry * ry;
+            rq = (rx * fx + ry * fy) / r2;
+            l = -0.5 * log(r2);
+            ux -= l * fx + rx * rq;
+            uy -= l * fy + ry * rq;
+        }
     }
     ux = block_sum_d(ux, red);
     uy = block_sum_d(uy, red);
     cu = block_sum_d(cu, red);
     if (threadIdx.x == 0) {
-        double c4 = 1.0 / (4.0 * kPi * mu);
-        v[2 * b] = ux * c4 + gamma * Y;
-        v[2 * b + 1] = uy * c4;
-        om[b] = 0.5 * (cu / (2.0 * kPi * mu) - gamma);
+        double* o = vpart + ((size_t)b * nsp + sp) * 3;
+        o[0] = ux;
+        o[1] = uy;
+        o[2] = cu;
     }
+}
+
+__global__ void k_velocities_fin(const double* __restrict__ vpart, int nb, int nsp, const double* __restrict__ body,
+                                 double mu, double gamma, double* __restrict__ v, double* __restrict__ om) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double ux = 0, uy = 0, cu = 0;
+    for (int s = 0; s < nsp; ++s) {
+        const double* o = vpart + ((size_t)b * nsp + s) * 3;
+        ux += o[0];
+        uy += o[1];
+        cu += o[2];
+    }
+    const double c4 = 1.0 / (4.0 * kPi * mu);
+    v[2 * b] = ux * c4 + gamma * body[8 * b + 3];
+    v[2 * b + 1] = uy * c4;
+    om[b] = 0.5 * (cu / (2.0 * kPi * mu) - gamma);
 }
 
 __global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __restrict__ y,
@@ -780,13 +818,11 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     BIE_LAUNCH(c, "k_pack");
     k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
-    k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
-        c->ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu,
-        c->ws.gpart);
+    k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
     BIE_LAUNCH(c, "k_disc");
     double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
+    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
                                                           c->nb, l1, l2, c->P, c->ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double sx[9], sy[9];
@@ -797,9 +833,12 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
         s9.y[k] = sy[k];
     }
     if (v || omega) {
-        k_velocities<<<c->nb, 256, 0, c->stream>>>(c->ws.src64, N, s9, c->body, c->yp, c->ws.xi, c->M, c->C[0],
-                                                   c->C[1], c->mu, c->gamma, v, omega);
+        k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, N, s9, c->body, c->yp, c->ws.xi,
+                                                                     c->M, c->C[0], c->C[1], c->ws.vpart);
         BIE_LAUNCH(c, "k_velocities");
+        k_velocities_fin<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->ws.vpart, c->nb, kVelSplits, c->body, c->mu,
+                                                                     c->gamma, v, omega);
+        BIE_LAUNCH(c, "k_velocities_fin");
     }
     if (mu_eff) {
         double area = fabs(c->e1[0] * c->e2[1] - c->e1[1] * c->e2[0]);
@@ -838,16 +877,15 @@ int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws
     k_near32<kNear32TPT><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk, s9,
                                                                              (float2*)ws.part);
     BIE_LAUNCH(c, "k_near32");
-    k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(
-        ws.src64, N, c->m, c->gl_s, c->e1[0], c->e1[1], c->e2[0], c->e2[1], c->C[0], c->C[1], c->mu, ws.gpart);
+    k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(ws.src64, N, c->m, c->wall, c->mu, ws.gpart);
     BIE_LAUNCH(c, "k_disc");
     const double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
     const double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<1, 256, 16 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscSplits, c->m, c->M, ws.bodyF, c->nb, l1,
+    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscSplits, c->m, c->M, ws.bodyF, c->nb, l1,
                                                           l2, c->P, ws.xi);
     BIE_LAUNCH(c, "k_xi");
     double2* T = reinterpret_cast<double2*>(ws.T);
-    k_correct<float2, float><<<(N + 63) / 64, 64, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x,
+    k_correct<float2, float><<<(N * kCorrLanes + 255) / 256, 256, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x,
                                                                   c->y, c->nx, c->ny, c->w, c->kap, c->yp, ws.xi,
                                                                   c->M, c->C[0], c->C[1], T);
     BIE_LAUNCH(c, "k_correct");

@@ -6,7 +6,9 @@
 //   densities : 2N doubles, node-major (x, y interleaved) == double2[N]
 //   sources   : src32 (N float4: x - C, y - C, qx, qy), src64 (N Src64: x, y, qx, qy)
 //   proxy fit : Q stacked with lam*I (column-major, R = 8m + 2M rows, 2M cols),
-//               Householder betas, P (2M x 8m, column-major), proxies yp (M double2)
+//               Householder betas, P (2M x 8m, row-major), proxies yp (M double2),
+//               wall table (2m x 16 doubles: six far-image offsets and the normal per
+//               collocation point)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +28,8 @@ constexpr int kNearTile = 256;        // sources staged per shared-memory tile
 constexpr int kNear32TPT = 2;         // targets per thread, single precision
 constexpr int kDiscBlocks = 96;       // capacity of the discrepancy partial buffer (splits)
 constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
+constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)
+constexpr int kVelSplits = 8;         // source splits per body in the velocity extraction
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
@@ -71,6 +75,16 @@ struct Workspace {
     double* gpart = nullptr;    // kDiscBlocks x 2m x 4 discrepancy partials
     double* xi = nullptr;       // 2M proxy strengths
     double* T = nullptr;        // 2N traction before the pressure fix
+    double* vpart = nullptr;    // nb x kVelSplits x 3 velocity partials
+};
+
+// One proxy least-squares fit (Sec. 6.1) for a given lattice: stacked matrix,
+// Householder scalars and diagonal, solution operator, wall table.
+struct ProxyFit {
+    double* A = nullptr;
+    double* beta = nullptr;
+    double* P = nullptr;
+    double* wall = nullptr;
 };
 
 struct Solver {
@@ -108,7 +122,12 @@ struct bie_ctx {
     double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
     double* A = nullptr;        // stacked [Q; lam I], column-major
     double* beta = nullptr;     // 2M Householder scalars
-    double* P = nullptr;        // 2M x 8m solution operator, column-major
+    double* P = nullptr;        // 2M x 8m solution operator, row-major
+    double* wall = nullptr;     // 2m x 16: collocation point minus each far-image shift (6 x 2), wall normal
+    // the next time step's proxy fit, built on a side stream during the current solve
+    bie::ProxyFit next;
+    cudaStream_t side = nullptr;
+    cudaEvent_t next_done = nullptr;
     double* yp = nullptr;       // 2M proxies (x, y) interleaved
     double* scal = nullptr;     // misc device scalars
     bie::Workspace ws;
@@ -150,7 +169,9 @@ int prof_fold(bie_ctx* c);
 
 // geometry.cu ---------------------------------------------------------------
 int build_geometry(bie_ctx* c);   // nodes from body state
-int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P
+int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P for the current lattice
+int build_proxy_fit_to(bie_ctx* c, const double* e2, ProxyFit& f, cudaStream_t st);
+int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st);
 void gauss_legendre_half(int m, std::vector<double>& s);
 
 // close.cu ------------------------------------------------------------------

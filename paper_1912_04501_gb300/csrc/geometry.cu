@@ -201,7 +201,9 @@ __global__ void k_qr(double* __restrict__ A, int R, int C, int Qrows, double lam
 }
 
 // Column c of P = first C rows of R^{-1} H_{C-1} ... H_0 e_c, c < Qrows.
-// P is C x Qrows, column-major.  Dynamic shared memory: R doubles.
+// P is C x Qrows, stored row-major (P[r * Qrows + c]) so that a warp reading
+// one row of P in the operator application is coalesced.  Dynamic shared
+// memory: R doubles.
 __global__ void k_form_P(const double* __restrict__ A, int R, int C, const double* __restrict__ beta,
                          const double* __restrict__ rdiag, double* __restrict__ P) {
     extern __shared__ double z[];
@@ -227,7 +229,8 @@ __global__ void k_form_P(const double* __restrict__ A, int R, int C, const doubl
         }
     }
     __syncthreads();
-    for (int r = tid; r < C; r += nt) P[r + (size_t)c * C] = z[r];
+    const int Qrows = gridDim.x;
+    for (int r = tid; r < C; r += nt) P[(size_t)r * Qrows + c] = z[r];
 }
 
 int build_geometry(bie_ctx* c) {
@@ -238,18 +241,23 @@ int build_geometry(bie_ctx* c) {
     return BIE_OK;
 }
 
-int build_proxy_fit(bie_ctx* c) {
-    int m = c->m, M = c->M;
-    int Qrows = 8 * m, C = 2 * M, R = Qrows + C;
-    int bs = 128, gs = (m * M + bs - 1) / bs;
-    k_build_Q<<<gs, bs, 0, c->stream>>>(c->A, R, m, M, c->gl_s, c->yp, c->e1[0], c->e1[1], c->e2[0],
-                                       c->e2[1], c->C[0], c->C[1], c->mu);
+int build_proxy_fit_to(bie_ctx* c, const double* e2, ProxyFit& f, cudaStream_t st) {
+    const int m = c->m, M = c->M;
+    const int Qrows = 8 * m, C = 2 * M, R = Qrows + C;
+    const int bs = 128, gs = (m * M + bs - 1) / bs;
+    k_build_Q<<<gs, bs, 0, st>>>(f.A, R, m, M, c->gl_s, c->yp, c->e1[0], c->e1[1], e2[0], e2[1], c->C[0], c->C[1],
+                                 c->mu);
     BIE_LAUNCH(c, "k_build_Q");
-    k_qr<<<1, 1024, 0, c->stream>>>(c->A, R, C, Qrows, c->opts.lam_rel, c->beta, c->beta + C);
+    k_qr<<<1, 1024, 0, st>>>(f.A, R, C, Qrows, c->opts.lam_rel, f.beta, f.beta + C);
     BIE_LAUNCH(c, "k_qr");
-    k_form_P<<<Qrows, 256, R * sizeof(double), c->stream>>>(c->A, R, C, c->beta, c->beta + C, c->P);
+    k_form_P<<<Qrows, 256, R * sizeof(double), st>>>(f.A, R, C, f.beta, f.beta + C, f.P);
     BIE_LAUNCH(c, "k_form_P");
-    return BIE_OK;
+    return build_wall_table(c, e2, f.wall, st);
+}
+
+int build_proxy_fit(bie_ctx* c) {
+    ProxyFit f{c->A, c->beta, c->P, c->wall};
+    return build_proxy_fit_to(c, c->e2, f, c->stream);
 }
 
 }  // namespace bie

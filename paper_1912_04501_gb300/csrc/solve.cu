@@ -43,18 +43,20 @@ k_mdot_part(const double* __restrict__ V, size_t ld, int nv, const double* __res
     }
 }
 
+// one warp per vector j: lanes add the partials, then a shuffle tree
 __global__ void k_mdot_fin(const double* __restrict__ part, int nchunk, int nv, double* __restrict__ h) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (j >= nv) return;
     double s = 0;
-    for (int b = 0; b < nchunk; ++b) s += part[(size_t)j * nchunk + b];
-    h[j] = s;
+    for (int b = lane; b < nchunk; b += 32) s += part[(size_t)j * nchunk + b];
+    s = wsum(s);
+    if (lane == 0) h[j] = s;
 }
 
 static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, int n, double* h) {
     k_mdot_part<<<kDotChunks, 256, 0, c->stream>>>(V, ld, nv, w, n, c->sv.dpart);
     BIE_LAUNCH(c, "k_mdot_part");
-    k_mdot_fin<<<(nv + 127) / 128, 128, 0, c->stream>>>(c->sv.dpart, kDotChunks, nv, h);
+    k_mdot_fin<<<(nv * 32 + 255) / 256, 256, 0, c->stream>>>(c->sv.dpart, kDotChunks, nv, h);
     BIE_LAUNCH(c, "k_mdot_fin");
     return BIE_OK;
 }
@@ -64,9 +66,16 @@ __global__ void k_mupdate(const double* __restrict__ V, size_t ld, int nv, const
                           double* __restrict__ w, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = w[i];
-    for (int j = 0; j < nv; ++j) s -= h[j] * V[(size_t)j * ld + i];
-    w[i] = s;
+    double s0 = w[i], s1 = 0, s2 = 0, s3 = 0;
+    int j = 0;
+    for (; j + 4 <= nv; j += 4) {
+        s0 -= h[j] * V[(size_t)j * ld + i];
+        s1 -= h[j + 1] * V[(size_t)(j + 1) * ld + i];
+        s2 -= h[j + 2] * V[(size_t)(j + 2) * ld + i];
+        s3 -= h[j + 3] * V[(size_t)(j + 3) * ld + i];
+    }
+    for (; j < nv; ++j) s0 -= h[j] * V[(size_t)j * ld + i];
+    w[i] = (s0 + s1) + (s2 + s3);
 }
 
 __global__ void k_scale_copy(const double* __restrict__ src, double a, double* __restrict__ dst, int n) {
