@@ -27,9 +27,15 @@ def nvcc():
     return exe
 
 
+def _defines():
+    """Extra -D flags from BIE_NVCC_DEFINES (space separated NAME=VALUE), used
+    to compare tile shapes without editing the sources."""
+    return ["-D" + d for d in os.environ.get("BIE_NVCC_DEFINES", "").split() if d]
+
+
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *_defines(), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -42,7 +48,7 @@ def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "bie_internal.cuh"),
                                                          os.path.join(HERE, "..", "include", "bie.h")]
-    if not force and os.path.exists(LIB):
+    if not force and not _defines() and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB

@@ -234,11 +234,10 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     int tiles32 = (n + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
     int tiles64 = (n + kNearThreads - 1) / kNearThreads;
     // Source splits: tiles x splits fills the resident CTA slots of all SMs in
-    // one even wave (7 CTAs/SM for k_near32 at 72 registers x 128 threads,
-    // 6 for k_near64 at 80, 4 for k_near_df at 128), keeping at least 64
-    // sources per split.
+    // one even wave (kNear32CtasPerSM for k_near32, 6 for k_near64 at 80
+    // registers, 4 for k_near_df at 128), keeping at least 64 sources per split.
     int maxsplit = std::max(1, n / 64);
-    c->near_splits32 = std::min(maxsplit, std::max(1, (7 * kSMs) / tiles32));
+    c->near_splits32 = std::min(maxsplit, std::max(1, (kNear32CtasPerSM * kSMs) / tiles32));
     c->near_splits64 = std::min(maxsplit, std::max(1, (6 * kSMs) / tiles64));
     c->near_splitsdf = std::min(maxsplit, std::max(1, (4 * kSMs) / tiles64));  // 128 registers: 4 CTAs/SM
     size_t part = std::max({(size_t)c->near_splits32 * n * sizeof(float2), (size_t)c->near_splits64 * n * sizeof(double2),

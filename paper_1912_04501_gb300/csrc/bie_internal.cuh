@@ -23,9 +23,22 @@ namespace bie {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
-constexpr int kNearThreads = 128;     // threads per near-sum block
-constexpr int kNearTile = 256;        // sources staged per shared-memory tile
-constexpr int kNear32TPT = 2;         // targets per thread, single precision
+#ifndef BIE_NEAR_THREADS
+#define BIE_NEAR_THREADS 128
+#endif
+// Tile shape of k_near32 (measured on GB300, 25-ellipse cell: 3 targets per
+// thread at 126 registers / 4 CTAs per SM beat 1, 2 and 4 targets per thread
+// and 256-thread blocks by 2-12 %)
+#ifndef BIE_NEAR32_TPT
+#define BIE_NEAR32_TPT 3
+#endif
+#ifndef BIE_NEAR32_CTAS_PER_SM
+#define BIE_NEAR32_CTAS_PER_SM 4
+#endif
+constexpr int kNearThreads = BIE_NEAR_THREADS;  // threads per near-sum block
+constexpr int kNearTile = 256;                  // sources staged per shared-memory tile
+constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
+constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
 constexpr int kDiscBlocks = 96;       // capacity of the discrepancy partial buffer (splits)
 constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)
