@@ -30,7 +30,7 @@ def perp(v):
 
 class Operator:
     def __init__(self, susp, n_proxy=16, proxy_radius=1.5, n_coll=16,
-                 close_factor=10.0, lam_rel=1e-8, use_close=True):
+                 close_factor=10.0, lam_rel=1e-8, use_close=True, close_targets=None):
         self.s = susp
         self.M = n_proxy
         self.m = n_coll
@@ -39,7 +39,9 @@ class Operator:
         self.Q = periodic.proxy_matrix(susp.e1, susp.e2, susp.centre, n_coll, self.yp, susp.mu)
         self.Qp = periodic.proxy_solution_operator(self.Q, lam_rel)
         self.self_index = np.arange(susp.N)
-        self.close = ClosePairs(susp, self.shifts, close_factor) if use_close else None
+        # close_targets restricts the close-pair search (sampled evaluation of
+        # large cells); apply() is then valid at those targets and node 0 only
+        self.close = ClosePairs(susp, self.shifts, close_factor, close_targets) if use_close else None
 
     # -- pieces ----------------------------------------------------------------
     def density_moments(self, sigma):

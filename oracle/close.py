@@ -90,22 +90,25 @@ class ClosePairs:
     close_factor * h_b, with the same-body zero-shift case excluded (that
     interaction is the smooth rule plus the on-curve diagonal)."""
 
-    def __init__(self, susp, shifts, close_factor=10.0):
+    def __init__(self, susp, shifts, close_factor=10.0, targets=None):
+        """targets: restrict the search to these target nodes (None = all)."""
         self.susp = susp
         self.pairs = []  # (target index, body, shift vector, curve distance, local spacing)
         off = susp.offsets
+        tidx = np.arange(susp.N) if targets is None else np.asarray(targets)
         for b in range(len(susp.bodies)):
             sl = slice(off[b], off[b + 1])
             yb = susp.x[sl]
             hb = susp.w[sl].sum() / (off[b + 1] - off[b])
             bd = susp.bodies[b]
             for sh in shifts:
-                dist = np.sqrt(((susp.x[:, None, :] - (yb[None, :, :] + sh)) ** 2).sum(-1))
+                dist = np.sqrt(((susp.x[tidx, None, :] - (yb[None, :, :] + sh)) ** 2).sum(-1))
                 d = dist.min(axis=1)
-                for i in np.nonzero(d < close_factor * hb)[0]:
+                for row in np.nonzero(d < close_factor * hb)[0]:
+                    i = int(tidx[row])
                     if susp.owner[i] == b and sh[0] == 0.0 and sh[1] == 0.0:
                         continue
-                    k = int(dist[i].argmin())
+                    k = int(dist[row].argmin())
                     dc, hl = closest_point(bd, susp.x[i], sh, 2.0 * np.pi * k / bd["n"])
                     self.pairs.append((int(i), b, sh.copy(), dc, hl))
 

@@ -43,6 +43,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
 // ---------------------------------------------------------------------------
 __global__ void k_pack(const double2* __restrict__ sigma, const double* __restrict__ x,
                        const double* __restrict__ y, const double* __restrict__ w, int N, double Cx,
@@ -98,7 +105,7 @@ struct Shifts9d {
 // MUFU reciprocal.  The zero-distance self pair is absorbed by a 1e-30 floor
 // on r^2 (its r.n and r.q are exactly zero, so it contributes 0).
 // ---------------------------------------------------------------------------
-template <int TPT>
+template <int TPT, bool COMP>
 __global__ void __launch_bounds__(kNearThreads)
 k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, int chunk, Shifts9 sh,
          float2* __restrict__ part) {
@@ -107,6 +114,10 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
     const int j1 = min(N, j0 + chunk);
     float px[TPT][9], py[TPT][9], nxv[TPT], nyv[TPT];
     float ax[TPT][3], ay[TPT][3];
+    // COMP: each source tile's sum is folded into a TwoSum-compensated pair
+    // (hi, lo), so that splits with very many sources keep single-precision
+    // accuracy relative to the sum instead of losing it to rounding growth.
+    float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
     int tbase = blockIdx.x * (kNearThreads * TPT) + threadIdx.x;
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
@@ -121,6 +132,7 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
         nyv[t] = tv.w;
 #pragma unroll
         for (int r = 0; r < 3; ++r) ax[t][r] = ay[t][r] = 0.f;
+        hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
     }
     for (int jt = j0; jt < j1; jt += kNearTile) {
         int cnt = min(kNearTile, j1 - jt);
@@ -146,14 +158,32 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
                 }
             }
         }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float e;
+                float sx_ = (ax[t][0] + ax[t][1]) + ax[t][2];
+                float sy_ = (ay[t][0] + ay[t][1]) + ay[t][2];
+                two_sum(hx[t], sx_, hx[t], e);
+                lx[t] += e;
+                two_sum(hy[t], sy_, hy[t], e);
+                ly[t] += e;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) ax[t][r] = ay[t][r] = 0.f;
+            }
+        }
     }
     const float c = (float)(-1.0 / kPi);
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         int i = tbase + t * kNearThreads;
-        if (i < N)
-            part[(size_t)blockIdx.y * N + i] =
-                make_float2(c * (ax[t][0] + ax[t][1] + ax[t][2]), c * (ay[t][0] + ay[t][1] + ay[t][2]));
+        if (i < N) {
+            if constexpr (COMP)
+                part[(size_t)blockIdx.y * N + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
+            else
+                part[(size_t)blockIdx.y * N + i] =
+                    make_float2(c * (ax[t][0] + ax[t][1] + ax[t][2]), c * (ay[t][0] + ay[t][1] + ay[t][2]));
+        }
     }
 }
 
@@ -231,12 +261,6 @@ __device__ __forceinline__ void split_df(double v, float& h, float& l) {
     l = (float)(v - (double)h);
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    float z = s - a;
-    e = (a - (s - z)) + (b - z);
-}
-
 // h + l -> normalised (|l| <= ulp(h) / 2), valid when |h| >= |l|
 __device__ __forceinline__ void fast2(float& h, float& l) {
     float s = h + l;
@@ -300,9 +324,12 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
     float nxh, nxl, nyh, nyl;
     split_df(tnx, nxh, nxl);
     split_df(tny, nyh, nyl);
-    float axh = 0, axe = 0, ayh = 0, aye = 0;
+    // per tile: hi sums by TwoSum, their errors in a float; folded into double
+    // accumulators after every tile so that neither grows with the source count
+    double dxs = 0, dys = 0;
     for (int jt = j0; jt < j1; jt += kNearTile) {
         int cnt = min(kNearTile, j1 - jt);
+        float axh = 0, axe = 0, ayh = 0, aye = 0;
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
         __syncthreads();
@@ -354,10 +381,12 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
                 aye += e + tl;
             }
         }
+        dxs += (double)axh + (double)axe;
+        dys += (double)ayh + (double)aye;
     }
     if (i < N) {
         const double c = -1.0 / kPi;
-        part[(size_t)blockIdx.y * N + i] = make_double2(c * ((double)axh + (double)axe), c * ((double)ayh + (double)aye));
+        part[(size_t)blockIdx.y * N + i] = make_double2(c * dxs, c * dys);
     }
 }
 
@@ -653,8 +682,12 @@ int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
         int chunk = (N + splits - 1) / splits;
         dim3 grid(tiles, splits);
         if (int rc = prof_begin(c, 0)) return rc;
-        k_near32<kNear32TPT><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
-                                                                   (float2*)c->ws.part);
+        if (chunk > kNear32CompChunk)
+            k_near32<kNear32TPT, true><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
+                                                                             (float2*)c->ws.part);
+        else
+            k_near32<kNear32TPT, false><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
+                                                                              (float2*)c->ws.part);
         BIE_LAUNCH(c, "k_near32");
         if (int rc = prof_end(c)) return rc;
     } else if (df) {
@@ -874,8 +907,12 @@ int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws
     const int splits = c->near_splits32;
     const int tiles = (N + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
     const int chunk = (N + splits - 1) / splits;
-    k_near32<kNear32TPT><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk, s9,
-                                                                             (float2*)ws.part);
+    if (chunk > kNear32CompChunk)
+        k_near32<kNear32TPT, true><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk,
+                                                                                       s9, (float2*)ws.part);
+    else
+        k_near32<kNear32TPT, false><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N,
+                                                                                        chunk, s9, (float2*)ws.part);
     BIE_LAUNCH(c, "k_near32");
     k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(ws.src64, N, c->m, c->wall, c->mu, ws.gpart);
     BIE_LAUNCH(c, "k_disc");

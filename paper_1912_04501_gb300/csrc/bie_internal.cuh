@@ -39,6 +39,7 @@ constexpr int kNearThreads = BIE_NEAR_THREADS;  // threads per near-sum block
 constexpr int kNearTile = 256;                  // sources staged per shared-memory tile
 constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
 constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
+constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
 constexpr int kDiscBlocks = 96;       // capacity of the discrepancy partial buffer (splits)
 constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)

@@ -18,6 +18,7 @@ import math
 import numpy as np
 
 SAMPLES = 1024  # boundary samples per ellipse used by the gap estimate
+FAST_SAMPLES = 256  # coarser outlines for placement loops (distance error ~1e-6 here)
 
 
 def _outline(a, b, xc, theta, k=SAMPLES):
@@ -35,12 +36,12 @@ def _inside(a, b, xc, theta, pts):
     return (u / a) ** 2 + (v / b) ** 2 < 1.0
 
 
-def gap_estimate(b1, b2, shift=(0.0, 0.0)):
-    """Minimum distance between two ellipse outlines sampled at SAMPLES points
+def gap_estimate(b1, b2, shift=(0.0, 0.0), k=SAMPLES):
+    """Minimum distance between two ellipse outlines sampled at k points
     each (negative if they overlap).  shift translates the second body."""
-    p = _outline(b1["a"], b1["b"], b1["xc"], b1["theta"])
+    p = _outline(b1["a"], b1["b"], b1["xc"], b1["theta"], k)
     xc2 = [b2["xc"][0] + shift[0], b2["xc"][1] + shift[1]]
-    q = _outline(b2["a"], b2["b"], xc2, b2["theta"])
+    q = _outline(b2["a"], b2["b"], xc2, b2["theta"], k)
     if _inside(b1["a"], b1["b"], b1["xc"], b1["theta"], q).any() or \
             _inside(b2["a"], b2["b"], xc2, b2["theta"], p).any():
         return -1.0
@@ -96,6 +97,7 @@ def random_cell(n_bodies, phi, aspect, min_gap_target, nodes, seed,
         areas = phi * area_cell * w / w.sum()
     bodies = []
     tries = 0
+    shifts = np.array([m * e1 + n * e2 for m in (-1, 0, 1) for n in (-1, 0, 1)])
     for k in range(n_bodies):
         alpha = rng.uniform(*aspect)
         a = math.sqrt(areas[k] * alpha / math.pi)
@@ -108,20 +110,15 @@ def random_cell(n_bodies, phi, aspect, min_gap_target, nodes, seed,
             xc = centre + uv[0] * e1 + uv[1] * e2
             cand = dict(a=a, b=b, xc=[float(xc[0]), float(xc[1])], theta=float(rng.uniform(0, math.pi)))
             ok = True
-            for other in bodies:
-                for m in (-1, 0, 1):
-                    for n in (-1, 0, 1):
-                        sh = m * e1 + n * e2
-                        d = np.hypot(*(np.asarray(other["xc"]) + sh - xc))
-                        if d - (max(a, b) + max(other["a"], other["b"])) > min_gap_target:
-                            continue
-                        if gap_estimate(cand, other, sh) < min_gap_target:
-                            ok = False
-                            break
-                    if not ok:
+            if bodies:
+                cen = np.array([o["xc"] for o in bodies])
+                rad = np.array([max(o["a"], o["b"]) for o in bodies])
+                d = np.linalg.norm(cen[:, None, :] + shifts[None, :, :] - xc[None, None, :], axis=2)
+                near = np.argwhere(d - (max(a, b) + rad[:, None]) <= min_gap_target)
+                for j, s_ in near:
+                    if gap_estimate(cand, bodies[j], shifts[s_], FAST_SAMPLES) < min_gap_target:
+                        ok = False
                         break
-                if not ok:
-                    break
             if ok:
                 break
         cand["n"] = int(nodes(a, b) if callable(nodes) else nodes)
@@ -162,3 +159,115 @@ def two_ellipses(gap, n, mu=1.0, gamma=1.0):
                         dict(a=0.125, b=0.25, xc=[0.5 + half, 0.5], theta=0.0, n=n)],
                 solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10),
                 dt=1e-3, steps=1)
+
+
+def _neighbour_gaps(bodies, e1, e2, i, reach_pad, k=FAST_SAMPLES):
+    """Gaps of body i to every other body (and its own images) within reach."""
+    bi = bodies[i]
+    shifts = np.array([m * e1 + n * e2 for m in (-1, 0, 1) for n in (-1, 0, 1)])
+    cen = np.array([o["xc"] for o in bodies])
+    rad = np.array([max(o["a"], o["b"]) for o in bodies])
+    d = np.linalg.norm(cen[:, None, :] + shifts[None, :, :] - np.asarray(bi["xc"])[None, None, :], axis=2)
+    near = np.argwhere(d - (max(bi["a"], bi["b"]) + rad[:, None]) <= reach_pad)
+    out = []
+    for j, s_ in near:
+        if j == i and s_ == 4:
+            continue
+        out.append(gap_estimate(bi, bodies[j], shifts[s_], k))
+    return out
+
+
+def compress(cell, phi_target, min_gap_target, seed, step=0.01, moves=30, max_rounds=400):
+    """Raise the area fraction of a placed cell to phi_target: alternate a
+    uniform inflation of every body's size and Monte-Carlo displacements
+    (random small moves and rotations, rejected if any gap falls below
+    min_gap_target).  Deterministic for a given seed."""
+    rng = np.random.default_rng(seed)
+    e1, e2 = np.asarray(cell["e1"], float), np.asarray(cell["e2"], float)
+    area_cell = abs(e1[0] * e2[1] - e1[1] * e2[0])
+    bodies = [dict(b) for b in cell["bodies"]]
+    phi = lambda: sum(math.pi * b["a"] * b["b"] for b in bodies) / area_cell
+    for _ in range(max_rounds):
+        if phi() >= phi_target - 1e-12:
+            break
+        f = min(1.0 + step, math.sqrt(phi_target / phi()))
+        trial = [dict(b, a=b["a"] * f, b=b["b"] * f) for b in bodies]
+        bad = [i for i in range(len(trial)) if min(_neighbour_gaps(trial, e1, e2, i, 0.05) or [1.0]) < min_gap_target]
+        # relieve the offending bodies by random moves at the inflated size
+        for i in bad:
+            for _ in range(moves):
+                old = trial[i]
+                cand = dict(old, xc=[old["xc"][0] + rng.normal(0, 0.01), old["xc"][1] + rng.normal(0, 0.01)],
+                            theta=old["theta"] + rng.normal(0, 0.05))
+                trial[i] = cand
+                if min(_neighbour_gaps(trial, e1, e2, i, 0.05) or [1.0]) >= min_gap_target:
+                    break
+                trial[i] = old
+        if all(min(_neighbour_gaps(trial, e1, e2, i, 0.05) or [1.0]) >= min_gap_target for i in bad):
+            bodies = trial
+        else:
+            step *= 0.5
+            if step < 1e-4:
+                break
+        # a sweep of random moves everywhere keeps the packing from locking up
+        for i in rng.permutation(len(bodies))[: len(bodies) // 4]:
+            old = bodies[i]
+            bodies[i] = dict(old, xc=[old["xc"][0] + rng.normal(0, 0.005), old["xc"][1] + rng.normal(0, 0.005)])
+            if min(_neighbour_gaps(bodies, e1, e2, i, 0.05) or [1.0]) < min_gap_target:
+                bodies[i] = old
+    out = dict(cell)
+    out["bodies"] = bodies
+    return out
+
+
+def config3(seed=3):
+    """Near jamming: 100 ellipses, aspect ratios uniform in [1, 2], placed at
+    area fraction 0.30 and compressed to 0.45 with every gap >= 1e-3; nodes
+    per body N_i = clamp(8 ceil(C P_i / (8 sqrt(d_i))), 128, 512), d_i the
+    body's smallest gap, C such that a gap of 1e-3 gets 512 nodes at the mean
+    perimeter."""
+    cell = random_cell(100, 0.30, (1.0, 2.0), 1e-2, 128, seed, equal_area=False)
+    cell = compress(cell, 0.45, 1e-3, seed)
+    e1, e2 = np.asarray(cell["e1"], float), np.asarray(cell["e2"], float)
+    bodies = cell["bodies"]
+    per = [math.pi * (3 * (b["a"] + b["b"]) - math.sqrt((3 * b["a"] + b["b"]) * (b["a"] + 3 * b["b"])))
+           for b in bodies]
+    cconst = 512.0 * math.sqrt(1e-3) / np.mean(per)
+    for i, b in enumerate(bodies):
+        d = max(min(_neighbour_gaps(bodies, e1, e2, i, 0.2) or [0.1]), 1e-4)
+        b["n"] = int(min(512, max(128, 8 * math.ceil(cconst * per[i] / (8 * math.sqrt(d))))))
+    cell.update(solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10), dt=1e-3, steps=10)
+    return cell
+
+
+def config4(seed=4, n_cells=64):
+    """Batched ensemble: n_cells independent unit cells, cell c drawn with
+    seed seed + c: body count uniform in {5..50}, area fraction uniform in
+    [0.1, 0.4], aspect ratios uniform in [1, 3], minimum gap 1e-2, nodes per
+    body clamp(8 ceil(P_i / (8 h*)), 128, 256) with h* = the mean perimeter
+    over 160 (so a typical body gets ~160 nodes)."""
+    cells = []
+    for c in range(n_cells):
+        rng = np.random.default_rng(seed + c)
+        nb = int(rng.integers(5, 51))
+        phi = float(rng.uniform(0.1, 0.4))
+        cell = random_cell(nb, phi, (1.0, 3.0), 1e-2, 128, seed + c)
+        per = [math.pi * (3 * (b["a"] + b["b"]) - math.sqrt((3 * b["a"] + b["b"]) * (b["a"] + 3 * b["b"])))
+               for b in cell["bodies"]]
+        hstar = np.mean(per) / 160.0
+        for b, p_ in zip(cell["bodies"], per):
+            b["n"] = int(min(256, max(128, 8 * math.ceil(p_ / (8 * hstar)))))
+        cell.update(solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10), dt=1e-3, steps=10)
+        cells.append(cell)
+    return cells
+
+
+def config5(seed=5):
+    """400 ellipses, area fraction 0.35, aspect ratios uniform in [1, 3],
+    minimum gap 2e-3, 256 nodes per body (102400 nodes); 50 Euler steps of
+    1e-3.  (A gap of 1e-2 would be a third of the smaller semi-axes at this
+    size -- an effective area fraction near 0.6 that random placement and
+    compression do not reach.)"""
+    cell = random_cell(400, 0.35, (1.0, 3.0), 2e-3, 256, seed, max_tries=2000000)
+    cell.update(solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10), dt=1e-3, steps=50)
+    return cell

@@ -247,3 +247,74 @@ def test_close_evaluation_parity(gap, n):
     np.testing.assert_allclose(om, om_ref, atol=1e-9)
     np.testing.assert_allclose(v, v_ref, atol=1e-9)
     ctx.close()
+
+
+def _sampled_parity(cell, n_samples, seed):
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(ctx.N, n_samples, replace=False))
+    op = oracle_operator(cell, close_targets=np.unique(np.concatenate([[0], idx])))
+    sigma = rng.standard_normal(2 * ctx.N)
+    ref = op.apply(sigma.reshape(-1, 2), targets=idx)
+    for prec, tol in ((bie.BIE_FP64, 1e-10), (bie.BIE_DF64, 1e-10), (bie.BIE_MIXED, 5e-5)):
+        y = ctx.apply(sigma, precision=prec).reshape(-1, 2)[idx]
+        assert _rel(y, ref) < tol, (prec, _rel(y, ref))
+    return ctx
+
+
+def _solution_invariants(ctx, cell):
+    """At the solution the density carries no net force and torque on any
+    body (Lemma after Eq. BIEPerturbed2) and the FP64 residual meets the
+    tolerance (checked with the native double operator).  The completion L
+    enforces the torque through (x - x^c)^perp with gain ~ |x - x^c|^2 x
+    perimeter (~1e-4 for bodies of radius ~0.03), so a relative residual of
+    1e-10 leaves torques up to ~1e-6 of the body's torque scale
+    sum |x - x^c| |q|; forces are enforced with gain ~perimeter."""
+    sig, info = ctx.solve()
+    b = ctx.rhs()
+    r = b - ctx.apply(sig, precision=bie.BIE_FP64)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    x, n, w, _ = ctx.nodes()
+    s = sig.reshape(-1, 2)
+    off = np.cumsum([0] + [bd["n"] for bd in cell["bodies"]])
+    for k, bd in enumerate(cell["bodies"]):
+        sl = slice(off[k], off[k + 1])
+        q = s[sl] * w[sl, None]
+        F = q.sum(0)
+        dx = x[sl] - np.asarray(bd["xc"])
+        tq = (-dx[:, 1] * q[:, 0] + dx[:, 0] * q[:, 1]).sum()
+        fscale = np.abs(q).sum()
+        tscale = (np.hypot(dx[:, 0], dx[:, 1]) * np.hypot(q[:, 0], q[:, 1])).sum()
+        assert np.abs(F).max() < 1e-9 * fscale and abs(tq) < 1e-6 * tscale
+    return info
+
+
+def test_full_size_config3_near_jamming():
+    """100 ellipses compressed to area fraction 0.45, gaps down to ~1e-3,
+    128-512 nodes per body (~23k nodes): sampled parity of all three
+    operators, then the mixed solve and its invariants."""
+    cell = workloads.config3()
+    ctx = _sampled_parity(cell, 24, 31)
+    npairs, under = ctx.close_info()
+    assert npairs > 1000 and under == 0
+    _solution_invariants(ctx, cell)
+    ctx.close()
+
+
+def test_full_size_config5_400_ellipses():
+    """400 ellipses at area fraction 0.35, 256 nodes per body (102400 nodes):
+    sampled parity, then the mixed solve (double-float residual) and its
+    invariants."""
+    cell = workloads.config5()
+    ctx = _sampled_parity(cell, 16, 51)
+    _solution_invariants(ctx, cell)
+    ctx.close()
+
+
+def test_config4_cells_sampled():
+    """Two of the 64 independent cells of the batched ensemble workload
+    (uneven body and node counts), each through its own context."""
+    cells = workloads.config4()
+    for k in (0, 7):
+        ctx = _sampled_parity(cells[k], 24, 41 + k)
+        ctx.close()
