@@ -20,6 +20,11 @@
  *  - Every function returns BIE_OK (0) or a negative BIE_E* code; the text of
  *    the last error is available from bie_last_error.  A context is not
  *    thread-safe: calls on one context must not overlap.
+ *  - A context holds one unit cell (bie_init) or a batch of independent unit
+ *    cells (bie_init_batch; the paper has no batches -- it is how many
+ *    independent suspensions share one GPU).  Nodes and bodies of all cells
+ *    are numbered cell after cell, so a density is still 2N doubles; every
+ *    per-cell output (mu_eff, e2) has one entry per cell in cell order.
  */
 #ifndef BIE_H
 #define BIE_H
@@ -63,6 +68,15 @@ typedef struct {
     double theta;
 } bie_body;
 
+/* One unit cell of a batch: lattice, viscosity mu, shear rate gamma and the
+ * number of its bodies (the next n_bodies entries of the bodies array). */
+typedef struct {
+    bie_lattice lattice;
+    double mu;
+    double gamma;
+    int32_t n_bodies;
+} bie_cell;
+
 /* Numerical parameters.  bie_default_opts fills every field. */
 typedef struct {
     int32_t precision;    /* BIE_FP64 or BIE_MIXED (solver and time step) */
@@ -88,7 +102,8 @@ typedef struct {
     int32_t refinements;  /* outer refinement sweeps (BIE_MIXED), else GMRES cycles */
     int32_t applies64;    /* FP64 operator applications */
     int32_t applies32;    /* single-precision operator applications */
-    double rel_residual;  /* final ||b - A sigma|| / ||b||, FP64 operator */
+    double rel_residual;  /* final ||b - A sigma|| / ||b||, FP64 operator (batches: the
+                             largest over the cells, each cell's norms taken over its own nodes) */
 } bie_solve_info;
 
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
@@ -105,6 +120,25 @@ void bie_default_opts(bie_opts* opts);
  * BIE_ENOMEM, BIE_ECUDA.  On error *ctx is set to NULL. */
 int bie_init(bie_ctx** ctx, const bie_lattice* lattice, double mu, double gamma,
              int32_t n_bodies, const bie_body* bodies, const bie_opts* opts);
+
+/* Create a context for n_cells independent unit cells (1..4096) solved
+ * together: one kernel launch serves every cell (the near-sum work of all
+ * cells is split into even waves across the SMs), the GMRES iterations of the
+ * cells run in lockstep with per-cell Arnoldi processes and convergence tests,
+ * and a converged cell drops out of the near sums.  bodies holds the bodies of
+ * cell 0, then of cell 1, and so on.  opts applies to every cell.  Each cell
+ * gives the same results (up to rounding order in the reductions) as a
+ * context of its own.  Errors as bie_init. */
+int bie_init_batch(bie_ctx** ctx, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
+                   const bie_opts* opts);
+
+/* Batch layout and the last solve per cell: n_cells; node_offset and
+ * body_offset (n_cells + 1 entries each: first node / body of every cell and
+ * the totals); last_solve (n_cells) the last bie_solve's or bie_step's
+ * statistics per cell (iterations and sweeps the cell took part in, its own
+ * relative residual).  Any pointer may be NULL; host pointers. */
+int bie_cells(const bie_ctx* ctx, int32_t* n_cells, int32_t* node_offset, int32_t* body_offset,
+              bie_solve_info* last_solve);
 
 void bie_destroy(bie_ctx* ctx);
 const char* bie_last_error(const bie_ctx* ctx);
@@ -151,9 +185,9 @@ int bie_solve(bie_ctx* ctx, const double* rhs, double* sigma, int32_t use_guess,
 /* Rigid-body velocities and effective viscosity from a density sigma (2N):
  * v (2 n_bodies) = (u + u0) at each centroid, omega (n_bodies) = half the
  * vorticity there, u the periodic single layer with its free constant fixed
- * by a zero proxy velocity at the cell centre; mu_eff (1) the particle-stress
- * average mu - (1/(gamma |U|)) sum_b int (x_2 - x^c_2) sigma_1 ds.  Outputs
- * may be NULL; they are host pointers unless on_device. */
+ * by a zero proxy velocity at the cell centre; mu_eff (one per cell) the
+ * particle-stress average mu - (1/(gamma |U|)) sum_b int (x_2 - x^c_2) sigma_1 ds.
+ * Outputs may be NULL; they are host pointers unless on_device. */
 int bie_velocities(bie_ctx* ctx, const double* sigma, double* v, double* omega, double* mu_eff,
                    int32_t on_device);
 
@@ -162,12 +196,13 @@ int bie_velocities(bie_ctx* ctx, const double* sigma, double* v, double* omega, 
  * e2(t) = (gamma t L2 reduced by the nearest multiple of e1, L2) and re-wrap
  * the centres into the cell.  Requires e1 = (L1, 0).  The density of the
  * last solve stays in the context as the next warm start.  mu_eff_out, if not
- * NULL, receives n_steps host doubles; info (host) the last solve's info.
+ * NULL, receives n_steps x n_cells host doubles (step-major); info (host) the
+ * last solve's info.  Every cell of a batch steps with the same dt.
  * Returns BIE_ECOLLIDE if opts.min_gap > 0 and a gap falls below it. */
 int bie_step(bie_ctx* ctx, double dt, int32_t n_steps, double* mu_eff_out, bie_solve_info* info);
 
-/* Checkpoint: time t, current e2, centroids xc (2 n_bodies), angles theta
- * (n_bodies), last density sigma (2N, may be NULL).  Host pointers. */
+/* Checkpoint: time t, current e2 (2 per cell), centroids xc (2 n_bodies),
+ * angles theta (n_bodies), last density sigma (2N, may be NULL).  Host pointers. */
 int bie_get_state(bie_ctx* ctx, double* t, double* e2, double* xc, double* theta, double* sigma);
 
 /* Restore a checkpoint taken from a context with the same bodies and node

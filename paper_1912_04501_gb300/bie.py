@@ -10,8 +10,9 @@ The functions carry the C names:
     bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
     bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read,
-    bie_apply_static
-and `Context` wraps them for a workload dict (see workloads.py).
+    bie_apply_static, bie_init_batch, bie_cells
+and `Context` wraps them for a workload dict, or a list of them for a batch
+of independent cells (see workloads.py).
 """
 import ctypes
 import os
@@ -37,6 +38,10 @@ class Lattice(ctypes.Structure):
 class Body(ctypes.Structure):
     _fields_ = [("n_nodes", c_int32), ("shape", c_int32), ("p", c_double * 4), ("xc", c_double * 2),
                 ("theta", c_double)]
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("lattice", Lattice), ("mu", c_double), ("gamma", c_double), ("n_bodies", c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -86,6 +91,9 @@ def library():
         "bie_default_opts": (None, [ctypes.POINTER(Opts)]),
         "bie_init": (c_int32, [ctypes.POINTER(vp), ctypes.POINTER(Lattice), c_double, c_double, c_int32,
                                ctypes.POINTER(Body), ctypes.POINTER(Opts)]),
+        "bie_init_batch": (c_int32, [ctypes.POINTER(vp), c_int32, ctypes.POINTER(Cell), ctypes.POINTER(Body),
+                                     ctypes.POINTER(Opts)]),
+        "bie_cells": (c_int32, [vp, ctypes.POINTER(c_int32), vp, vp, ctypes.POINTER(SolveInfo)]),
         "bie_destroy": (None, [vp]),
         "bie_last_error": (ctypes.c_char_p, [vp]),
         "bie_size": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
@@ -117,7 +125,7 @@ def exported_symbols():
     return [n for n in ("bie_default_opts", "bie_init", "bie_destroy", "bie_last_error", "bie_size",
                         "bie_set_stream", "bie_nodes", "bie_apply", "bie_rhs", "bie_solve", "bie_velocities",
                         "bie_step", "bie_get_state", "bie_set_state", "bie_close_info", "bie_profile",
-                        "bie_profile_read", "bie_apply_static")
+                        "bie_profile_read", "bie_apply_static", "bie_init_batch", "bie_cells")
             if hasattr(L, n)]
 
 
@@ -142,13 +150,20 @@ def bie_default_opts():
     return o
 
 
+def _lattice(cell):
+    return Lattice((c_double * 2)(*cell["e1"]), (c_double * 2)(*cell["e2"]), (c_double * 2)(*cell["centre"]))
+
+
 class Context:
-    """One unit cell on the GPU (bie_init ... bie_destroy)."""
+    """One unit cell (a workload dict: bie_init) or a batch of independent
+    cells (a list of them: bie_init_batch) on the GPU."""
 
     def __init__(self, cell, precision=BIE_MIXED, **opts):
         L = library()
         o = bie_default_opts()
-        sv = cell.get("solver", {})
+        cells = list(cell) if isinstance(cell, (list, tuple)) else [cell]
+        self.batch = isinstance(cell, (list, tuple))
+        sv = cells[0].get("solver", {})
         o.precision = precision
         for k in ("n_proxy", "proxy_radius", "n_coll"):
             if k in sv:
@@ -157,17 +172,25 @@ class Context:
             o.gmres_tol = sv["gmres_tol"]
         for k, v in opts.items():
             setattr(o, k, v)
-        lat = Lattice((c_double * 2)(*cell["e1"]), (c_double * 2)(*cell["e2"]), (c_double * 2)(*cell["centre"]))
-        bodies = (Body * len(cell["bodies"]))()
-        for b, bd in zip(bodies, cell["bodies"]):
+        all_bodies = [bd for c in cells for bd in c["bodies"]]
+        bodies = (Body * len(all_bodies))()
+        for b, bd in zip(bodies, all_bodies):
             b.n_nodes = int(bd["n"])
             b.shape = 0
             b.p = (c_double * 4)(bd["a"], bd["b"], 0.0, 0.0)
             b.xc = (c_double * 2)(*bd["xc"])
             b.theta = bd["theta"]
         h = c_void_p()
-        rc = L.bie_init(ctypes.byref(h), ctypes.byref(lat), cell["mu"], cell["gamma"], len(cell["bodies"]),
-                        bodies, ctypes.byref(o))
+        if self.batch:
+            cs = (Cell * len(cells))()
+            for ct, c in zip(cs, cells):
+                ct.lattice = _lattice(c)
+                ct.mu, ct.gamma, ct.n_bodies = c["mu"], c["gamma"], len(c["bodies"])
+            rc = L.bie_init_batch(ctypes.byref(h), len(cells), cs, bodies, ctypes.byref(o))
+        else:
+            lat = _lattice(cell)
+            rc = L.bie_init(ctypes.byref(h), ctypes.byref(lat), cell["mu"], cell["gamma"], len(cell["bodies"]),
+                            bodies, ctypes.byref(o))
         if rc != 0:
             raise BieError(rc, "bie_init failed (invalid input or CUDA error)")
         self.h = h
@@ -175,6 +198,11 @@ class Context:
         n, nb = c_int32(), c_int32()
         L.bie_size(h, ctypes.byref(n), ctypes.byref(nb))
         self.N, self.n_bodies = n.value, nb.value
+        self.n_cells = len(cells)
+        no = np.zeros(self.n_cells + 1, dtype=np.int32)
+        bo = np.zeros(self.n_cells + 1, dtype=np.int32)
+        self._check(L.bie_cells(h, None, no.ctypes.data, bo.ctypes.data, None))
+        self.node_offsets, self.body_offsets = no, bo
 
     def _check(self, rc):
         if rc != 0:
@@ -225,28 +253,39 @@ class Context:
             self._check(rc)
         return sigma, info.as_dict()
 
+    def cell_info(self):
+        """Per-cell statistics of the last solve (list of dicts)."""
+        infos = (SolveInfo * self.n_cells)()
+        self._check(library().bie_cells(self.h, None, None, None, infos))
+        return [i.as_dict() for i in infos]
+
     def velocities(self, sigma):
-        v, om, mu = np.zeros(2 * self.n_bodies), np.zeros(self.n_bodies), np.zeros(1)
+        """(v (n_bodies x 2), omega, mu_eff): mu_eff a float for one cell, an
+        array of one value per cell for a batch."""
+        v, om, mu = np.zeros(2 * self.n_bodies), np.zeros(self.n_bodies), np.zeros(self.n_cells)
         s = np.ascontiguousarray(sigma, dtype=np.float64).ravel()
         self._check(library().bie_velocities(self.h, s.ctypes.data, v.ctypes.data, om.ctypes.data,
                                              mu.ctypes.data, 0))
-        return v.reshape(-1, 2), om, float(mu[0])
+        return v.reshape(-1, 2), om, (mu if self.batch else float(mu[0]))
 
     def step(self, dt, n_steps=1):
-        mu = np.zeros(max(1, n_steps))
+        """mu_eff per step (n_steps) for one cell, (n_steps x n_cells) for a batch."""
+        mu = np.zeros(max(1, n_steps) * self.n_cells)
         info = SolveInfo()
         self._check(library().bie_step(self.h, dt, n_steps, mu.ctypes.data, ctypes.byref(info)))
-        return mu[:n_steps], info.as_dict()
+        mu = mu[:n_steps * self.n_cells]
+        return (mu.reshape(n_steps, self.n_cells) if self.batch else mu), info.as_dict()
 
     def get_state(self):
         t = np.zeros(1)
-        e2 = np.zeros(2)
+        e2 = np.zeros(2 * self.n_cells)
         xc = np.zeros(2 * self.n_bodies)
         th = np.zeros(self.n_bodies)
         sg = np.zeros(2 * self.N)
         self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
                                             th.ctypes.data, sg.ctypes.data))
-        return dict(t=float(t[0]), e2=e2, xc=xc.reshape(-1, 2), theta=th, sigma=sg)
+        return dict(t=float(t[0]), e2=(e2.reshape(-1, 2) if self.batch else e2), xc=xc.reshape(-1, 2), theta=th,
+                    sigma=sg)
 
     def apply_static(self, sigma, out):
         """bie_apply_static on device tensors (no device allocation inside the
@@ -272,7 +311,9 @@ class Context:
         return info.as_dict()
 
     def set_state(self, t, e2, xc, theta, sigma=None):
-        e2 = np.ascontiguousarray(e2, dtype=np.float64)
+        e2 = np.ascontiguousarray(e2, dtype=np.float64).ravel()
+        if e2.size != 2 * self.n_cells:
+            raise ValueError("e2 needs two entries per cell")
         xc = np.ascontiguousarray(xc, dtype=np.float64).ravel()
         th = np.ascontiguousarray(theta, dtype=np.float64)
         sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64).ravel()

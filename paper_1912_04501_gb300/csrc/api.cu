@@ -2,6 +2,7 @@
 // ownership, host <-> device staging, and the forward-Euler time loop.
 #include <cmath>
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -29,12 +30,14 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 }
 
 static void free_all(bie_ctx* c) {
-    void* ptrs[] = {c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body, c->tgt32, c->gl_s, c->A, c->beta,
-                    c->P, c->wall, c->next.A, c->next.beta, c->next.P, c->next.wall, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32, c->ws.srcdf, c->ws.bodyF,
-                    c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->ws.vpart, c->sv.V, c->sv.w, c->sv.r, c->sv.x, c->sv.b,
-                    c->sv.d, c->sv.h, c->sv.red, c->sv.dpart, c->sv.sigma_prev, c->cl.slots, c->cl.count,
-                    c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab,
-                    c->cl.dtab_off};
+    void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
+                    c->tgt32, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
+                    c->next.wall, c->next.e2, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
+                    c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->ws.vpart, c->sv.V,
+                    c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.dpart, c->sv.chunks,
+                    c->sv.cell_chunks, c->sv.sigma_prev, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
+                    c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
+                    c->near[1].items, c->near[2].items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto e : c->ev_pool)
@@ -47,26 +50,58 @@ static void free_all(bie_ctx* c) {
     }
 }
 
-// Lattice of Sec. 7: e1 = (L1, 0) fixed, e2 = (s0 + gamma t L2 - L1 round(.), L2).
-static void lattice_at(const bie_ctx* c, double t, double* e2) {
-    double L1 = c->e1[0];
-    double sx = c->e2_0[0] + c->gamma * t * c->e2_0[1];
-    sx -= L1 * std::round(sx / L1);
-    e2[0] = sx;
-    e2[1] = c->e2_0[1];
+// Lattice vectors, image shifts m e1 + n e2 (index (n + 1) * 3 + (m + 1)) and
+// wall lengths of one cell.
+void cell_set_lattice(Cell& cl, const double* e1, const double* e2) {
+    for (int k = 0; k < 2; ++k) {
+        cl.e1[k] = e1[k];
+        cl.e2[k] = e2[k];
+    }
+    int idx = 0;
+    for (int n = -1; n <= 1; ++n)
+        for (int m = -1; m <= 1; ++m, ++idx) {
+            cl.sx[idx] = m * e1[0] + n * e2[0];
+            cl.sy[idx] = m * e1[1] + n * e2[1];
+            cl.sxf[idx] = (float)cl.sx[idx];
+            cl.syf[idx] = (float)cl.sy[idx];
+        }
+    cl.l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+    cl.l2 = std::sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
 }
 
-__global__ void k_euler(double* __restrict__ body, int nb, const double* __restrict__ v,
-                        const double* __restrict__ om, double dt, double e1x, double e1y, double e2x, double e2y,
-                        double Cx, double Cy) {
+// Stream-ordered upload of the host mirror of the cell table (the pageable
+// source is staged by the driver before the call returns).
+int upload_cells(bie_ctx* c, cudaStream_t st) {
+    BIE_CUDA(c, cudaMemcpyAsync(c->cells, c->cells_h.data(), c->cells_h.size() * sizeof(Cell), cudaMemcpyHostToDevice,
+                                st));
+    return BIE_OK;
+}
+
+// Lattice of Sec. 7 per cell: e1 = (L1, 0) fixed,
+// e2(t) = (s0 + gamma t L2 - L1 round(.), L2), round half away from zero.
+static void lattice_at(const bie_ctx* c, int cell, double t, double* e2) {
+    const Cell& cl = c->cells_h[cell];
+    const double L1 = cl.e1[0];
+    double sx = c->e2_0[2 * cell] + cl.gamma * t * c->e2_0[2 * cell + 1];
+    sx -= L1 * std::round(sx / L1);
+    e2[0] = sx;
+    e2[1] = c->e2_0[2 * cell + 1];
+}
+
+// Move and rotate every body by (v, omega) dt and wrap its centroid into its
+// cell: lattice coordinates about the cell centre into [-1/2, 1/2).
+__global__ void k_euler(double* __restrict__ body, int nb, const int* __restrict__ body_cell,
+                        const Cell* __restrict__ cells, const double* __restrict__ v, const double* __restrict__ om,
+                        double dt) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
+    const Cell& cl = cells[body_cell[b]];
+    const double e1x = cl.e1[0], e1y = cl.e1[1], e2x = cl.e2[0], e2y = cl.e2[1];
     double* bd = body + 8 * b;
     double X = bd[2] + dt * v[2 * b], Y = bd[3] + dt * v[2 * b + 1];
     bd[4] += dt * om[b];
-    // wrap: lattice coordinates about the centre into [-1/2, 1/2)
     double det = e1x * e2y - e1y * e2x;
-    double px = X - Cx, py = Y - Cy;
+    double px = X - cl.C[0], py = Y - cl.C[1];
     double a = (px * e2y - py * e2x) / det, bb = (e1x * py - e1y * px) / det;
     double sa = floor(a + 0.5), sb = floor(bb + 0.5);
     bd[2] = X - (sa * e1x + sb * e2x);
@@ -127,6 +162,35 @@ static int rebuild(bie_ctx* c) {
     return build_close(c);
 }
 
+// The current lattices' e2 (host mirror) to the device array the proxy fits read.
+static int upload_e2(bie_ctx* c, double* dst, const std::vector<double>& e2, cudaStream_t st) {
+    BIE_CUDA(c, cudaMemcpyAsync(dst, e2.data(), e2.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    return BIE_OK;
+}
+
+static std::vector<double> current_e2(const bie_ctx* c) {
+    std::vector<double> e2(2 * (size_t)c->ncell);
+    for (int k = 0; k < c->ncell; ++k) {
+        e2[2 * k] = c->cells_h[k].e2[0];
+        e2[2 * k + 1] = c->cells_h[k].e2[1];
+    }
+    return e2;
+}
+
+static int check_opts(const bie_opts& o, std::string& why) {
+    if (o.precision != BIE_FP64 && o.precision != BIE_MIXED) why = "precision must be BIE_FP64 or BIE_MIXED";
+    else if (o.n_proxy < 4 || o.n_proxy > kMaxProxy) why = "n_proxy out of range";
+    else if (o.n_coll < 2 || o.n_coll > kMaxColl) why = "n_coll out of range";
+    else if (!(o.proxy_radius > 0) || !(o.lam_rel >= 0) || !(o.gmres_tol > 0) || !(o.inner_tol > 0))
+        why = "non-positive tolerance or radius";
+    else if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) why = "gmres_max / max_refine out of range";
+    else if (o.residual != BIE_FP64 && o.residual != BIE_DF64) why = "residual must be BIE_FP64 or BIE_DF64";
+    else if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
+        why = "close_factor must be in [0, 100], close_capacity >= 0";
+    else return 0;
+    return 1;
+}
+
 }  // namespace bie
 
 using namespace bie;
@@ -153,11 +217,11 @@ void bie_default_opts(bie_opts* o) {
     o->residual = BIE_DF64;
 }
 
-int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int32_t n_bodies,
-             const bie_body* bodies, const bie_opts* opts) {
+int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
+                   const bie_opts* opts) {
     if (!out) return BIE_EINVAL;
     *out = nullptr;
-    if (!lat || !bodies || n_bodies <= 0) return BIE_EINVAL;
+    if (!cells || !bodies || n_cells <= 0 || n_cells > kMaxCells) return BIE_EINVAL;
     bie_ctx* c = new (std::nothrow) bie_ctx();
     if (!c) return BIE_ENOMEM;
     if (opts) c->opts = *opts;
@@ -168,60 +232,65 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
         return BIE_EINVAL;
     };
     const bie_opts& o = c->opts;
-    if (o.precision != BIE_FP64 && o.precision != BIE_MIXED) return bad("precision must be BIE_FP64 or BIE_MIXED");
-    if (o.n_proxy < 4 || o.n_proxy > kMaxProxy) return bad("n_proxy out of range");
-    if (o.n_coll < 2 || o.n_coll > kMaxColl) return bad("n_coll out of range");
-    if (!(o.proxy_radius > 0) || !(o.lam_rel >= 0) || !(o.gmres_tol > 0) || !(o.inner_tol > 0))
-        return bad("non-positive tolerance or radius");
-    if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) return bad("gmres_max / max_refine out of range");
-    if (!(mu > 0) || !std::isfinite(gamma)) return bad("mu must be positive, gamma finite");
-    if (o.residual != BIE_FP64 && o.residual != BIE_DF64) return bad("residual must be BIE_FP64 or BIE_DF64");
-    if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
-        return bad("close_factor must be in [0, 100], close_capacity >= 0");
-    double det = lat->e1[0] * lat->e2[1] - lat->e1[1] * lat->e2[0];
-    if (!(std::fabs(det) > 1e-12)) return bad("degenerate lattice");
-    c->device = o.device;
-    for (int k = 0; k < 2; ++k) {
-        c->e1[k] = lat->e1[k];
-        c->e2[k] = c->e2_0[k] = lat->e2[k];
-        c->C[k] = lat->center[k];
+    {
+        std::string why;
+        if (check_opts(o, why)) return bad(why);
     }
-    c->mu = mu;
-    c->gamma = gamma;
-    c->nb = n_bodies;
+    c->device = o.device;
+    c->ncell = n_cells;
     c->M = o.n_proxy;
     c->m = o.n_coll;
-    c->offsets.assign(n_bodies + 1, 0);
-    c->body_host.assign(8 * (size_t)n_bodies, 0.0);
-    long long N = 0;
-    for (int b = 0; b < n_bodies; ++b) {
-        const bie_body& bd = bodies[b];
-        if (bd.shape != 0) return bad("only shape 0 (ellipse) is supported");
-        if (bd.n_nodes < 8 || bd.n_nodes > 4096 || (bd.n_nodes & 1)) return bad("n_nodes must be even, 8..4096");
-        if (!(bd.p[0] > 0) || !(bd.p[1] > 0)) return bad("ellipse semi-axes must be positive");
-        if (!std::isfinite(bd.xc[0]) || !std::isfinite(bd.xc[1]) || !std::isfinite(bd.theta))
-            return bad("non-finite body position");
-        c->n_nodes.push_back(bd.n_nodes);
-        c->offsets[b] = (int)N;
-        double* h = &c->body_host[8 * (size_t)b];
-        h[0] = bd.p[0];
-        h[1] = bd.p[1];
-        h[2] = bd.xc[0];
-        h[3] = bd.xc[1];
-        h[4] = bd.theta;
-        h[5] = bd.n_nodes;
-        h[6] = (double)N;
-        N += bd.n_nodes;
+    c->cells_h.assign(n_cells, Cell{});
+    c->e2_0.assign(2 * (size_t)n_cells, 0.0);
+    long long N = 0, nb = 0;
+    for (int k = 0; k < n_cells; ++k) {
+        const bie_cell& in = cells[k];
+        if (in.n_bodies <= 0) return bad("every cell needs at least one body");
+        if (!(in.mu > 0) || !std::isfinite(in.gamma)) return bad("mu must be positive, gamma finite");
+        const bie_lattice& lat = in.lattice;
+        double det = lat.e1[0] * lat.e2[1] - lat.e1[1] * lat.e2[0];
+        if (!(std::fabs(det) > 1e-12)) return bad("degenerate lattice");
+        Cell& cl = c->cells_h[k];
+        cell_set_lattice(cl, lat.e1, lat.e2);
+        cl.C[0] = lat.center[0];
+        cl.C[1] = lat.center[1];
+        cl.mu = in.mu;
+        cl.gamma = in.gamma;
+        cl.active = 1;
+        c->e2_0[2 * k] = lat.e2[0];
+        c->e2_0[2 * k + 1] = lat.e2[1];
+        cl.body_off = (int)nb;
+        cl.n_bodies = in.n_bodies;
+        cl.node_off = (int)N;
+        for (int j = 0; j < in.n_bodies; ++j, ++nb) {
+            const bie_body& bd = bodies[nb];
+            if (bd.shape != 0) return bad("only shape 0 (ellipse) is supported");
+            if (bd.n_nodes < 8 || bd.n_nodes > 4096 || (bd.n_nodes & 1)) return bad("n_nodes must be even, 8..4096");
+            if (!(bd.p[0] > 0) || !(bd.p[1] > 0)) return bad("ellipse semi-axes must be positive");
+            if (!std::isfinite(bd.xc[0]) || !std::isfinite(bd.xc[1]) || !std::isfinite(bd.theta))
+                return bad("non-finite body position");
+            c->n_nodes.push_back(bd.n_nodes);
+            c->offsets.push_back((int)N);
+            for (int q = 0; q < 8; ++q) c->body_host.push_back(0.0);
+            double* h = &c->body_host[8 * (size_t)nb];
+            h[0] = bd.p[0];
+            h[1] = bd.p[1];
+            h[2] = bd.xc[0];
+            h[3] = bd.xc[1];
+            h[4] = bd.theta;
+            h[5] = bd.n_nodes;
+            h[6] = (double)N;
+            N += bd.n_nodes;
+            if (N > (1 << 24)) return bad("too many nodes");
+        }
+        cl.n_nodes = (int)(N - cl.node_off);
     }
-    if (N > (1 << 24)) return bad("too many nodes");
     c->N = (int)N;
-    c->offsets[n_bodies] = c->N;
+    c->nb = (int)nb;
+    c->offsets.push_back(c->N);
 
     auto cu = [&](cudaError_t e, const char* what) {
-        if (e != cudaSuccess) {
-            int code = cuda_check(c, e, what);
-            return code;
-        }
+        if (e != cudaSuccess) return cuda_check(c, e, what);
         return 0;
     };
     int rc;
@@ -229,22 +298,17 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
         delete c;
         return rc;
     }
-    const int n = c->N, nb = c->nb, M = c->M, m = c->m;
+    const int n = c->N, M = c->M, m = c->m;
+    const size_t nc = (size_t)n_cells, nbs = (size_t)c->nb;
     const int R = 8 * m + 2 * M, Cc = 2 * M;
-    int tiles32 = (n + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
-    int tiles64 = (n + kNearThreads - 1) / kNearThreads;
-    // Source splits: tiles x splits fills the resident CTA slots of all SMs in
-    // one even wave (kNear32CtasPerSM for k_near32, 6 for k_near64 at 80
-    // registers, 4 for k_near_df at 128), keeping at least 64 sources per split.
-    int maxsplit = std::max(1, n / 64);
-    c->near_splits32 = std::min(maxsplit, std::max(1, (kNear32CtasPerSM * kSMs) / tiles32));
-    c->near_splits64 = std::min(maxsplit, std::max(1, (6 * kSMs) / tiles64));
-    c->near_splitsdf = std::min(maxsplit, std::max(1, (4 * kSMs) / tiles64));  // 128 registers: 4 CTAs/SM
-    size_t part = std::max({(size_t)c->near_splits32 * n * sizeof(float2), (size_t)c->near_splits64 * n * sizeof(double2),
-                            (size_t)c->near_splitsdf * n * sizeof(double2)});
+    // near-sum splits for the partial buffer (the same rule fills the items below)
+    const size_t part = near_part_bytes(c);
     c->sv.kmax = o.gmres_max;
-    int kk = c->sv.kmax;
+    const int kk = c->sv.kmax;
     rc = 0;
+    rc = rc ? rc : dalloc(c, &c->cells, nc);
+    rc = rc ? rc : dalloc(c, &c->node_cell, n);
+    rc = rc ? rc : dalloc(c, &c->body_cell, nbs);
     rc = rc ? rc : dalloc(c, &c->x, n);
     rc = rc ? rc : dalloc(c, &c->y, n);
     rc = rc ? rc : dalloc(c, &c->nx, n);
@@ -252,41 +316,41 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
     rc = rc ? rc : dalloc(c, &c->w, n);
     rc = rc ? rc : dalloc(c, &c->kap, n);
     rc = rc ? rc : dalloc(c, &c->owner, n);
-    rc = rc ? rc : dalloc(c, &c->body, 8 * (size_t)nb);
+    rc = rc ? rc : dalloc(c, &c->body, 8 * nbs);
     rc = rc ? rc : dalloc(c, &c->tgt32, n);
     rc = rc ? rc : dalloc(c, &c->gl_s, m);
-    rc = rc ? rc : dalloc(c, &c->A, (size_t)R * Cc);
-    rc = rc ? rc : dalloc(c, &c->beta, 2 * (size_t)Cc);
-    rc = rc ? rc : dalloc(c, &c->P, (size_t)Cc * 8 * m);
-    rc = rc ? rc : dalloc(c, &c->wall, 16 * 2 * (size_t)m);
-    rc = rc ? rc : dalloc(c, &c->next.A, (size_t)R * Cc);
-    rc = rc ? rc : dalloc(c, &c->next.beta, 2 * (size_t)Cc);
-    rc = rc ? rc : dalloc(c, &c->next.P, (size_t)Cc * 8 * m);
-    rc = rc ? rc : dalloc(c, &c->next.wall, 16 * 2 * (size_t)m);
+    rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
+    rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);
+    rc = rc ? rc : dalloc(c, &c->P, nc * Cc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->wall, nc * 16 * 2 * m);
+    rc = rc ? rc : dalloc(c, &c->e2d, 2 * nc);
+    rc = rc ? rc : dalloc(c, &c->next.A, nc * R * Cc);
+    rc = rc ? rc : dalloc(c, &c->next.beta, nc * 2 * Cc);
+    rc = rc ? rc : dalloc(c, &c->next.P, nc * Cc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->next.wall, nc * 16 * 2 * m);
+    rc = rc ? rc : dalloc(c, &c->next.e2, 2 * nc);
     if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
-    rc = rc ? rc : dalloc(c, &c->yp, 2 * (size_t)M);
-    rc = rc ? rc : dalloc(c, &c->scal, 3 * (size_t)nb + 8);
+    rc = rc ? rc : dalloc(c, &c->yp, nc * 2 * M);
+    rc = rc ? rc : dalloc(c, &c->scal, 3 * nbs + nc + 8);
     rc = rc ? rc : dalloc(c, &c->ws.sigma, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.out, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.src64, n);
     rc = rc ? rc : dalloc(c, &c->ws.src32, n);
     rc = rc ? rc : dalloc(c, (char**)&c->ws.srcdf, (size_t)n * 32);
-    rc = rc ? rc : dalloc(c, &c->ws.bodyF, 3 * (size_t)nb);
+    rc = rc ? rc : dalloc(c, &c->ws.bodyF, 3 * nbs);
     rc = rc ? rc : dalloc(c, (char**)&c->ws.part, part);
-    rc = rc ? rc : dalloc(c, &c->ws.gpart, (size_t)kDiscBlocks * 2 * m * 4);
-    rc = rc ? rc : dalloc(c, &c->ws.xi, 2 * (size_t)M);
+    rc = rc ? rc : dalloc(c, &c->ws.gpart, nc * kDiscSplits * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->ws.xi, nc * 2 * M);
     rc = rc ? rc : dalloc(c, &c->ws.T, 2 * (size_t)n);
-    rc = rc ? rc : dalloc(c, &c->ws.vpart, (size_t)nb * kVelSplits * 3);
+    rc = rc ? rc : dalloc(c, &c->ws.vpart, nbs * kVelSplits * 3);
     rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1) * 2 * n);
     rc = rc ? rc : dalloc(c, &c->sv.w, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.r, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.x, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.b, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.d, 2 * (size_t)n);
-    rc = rc ? rc : dalloc(c, &c->sv.h, 3 * (size_t)(kk + 2) + 8);
-    rc = rc ? rc : dalloc(c, &c->sv.red, 8);
-    rc = rc ? rc : dalloc(c, &c->sv.dpart, (size_t)(kk + 2) * 64);
+    rc = rc ? rc : dalloc(c, &c->sv.h, (3 * (size_t)(kk + 2) + 1) * nc);
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
     {
         int maxn = 0;
@@ -299,43 +363,70 @@ int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int
         rc = rc ? rc : dalloc(c, &c->cl.pairs, c->cl.cap_pairs);
         rc = rc ? rc : dalloc(c, &c->cl.blk_off, c->cl.cap_pairs);
         rc = rc ? rc : dalloc(c, &c->cl.blocks, (size_t)c->cl.cap_doubles);
-        rc = rc ? rc : dalloc(c, &c->cl.flags, 4);
+        rc = rc ? rc : dalloc(c, &c->cl.flags, 6);
     }
     c->ws.part_bytes = part;
+    // zeroed once: a cell that the solver switches off keeps finite partials
+    if (!rc) rc = cu(cudaMemset(c->ws.part, 0, part), "cudaMemset");
     if (rc) {
         free_all(c);
-        std::string e = c->err;
         delete c;
-        (void)e;
         return rc;
     }
-    std::vector<int> owner(n);
-    for (int b = 0; b < nb; ++b)
+    std::vector<int> owner(n), node_cell(n), body_cell(c->nb);
+    for (int b = 0; b < c->nb; ++b)
         for (int k = c->offsets[b]; k < c->offsets[b + 1]; ++k) owner[k] = b;
-    gauss_legendre_half(m, c->gl_host);
-    std::vector<double> yp(2 * (size_t)M);
-    for (int p = 0; p < M; ++p) {
-        double a = 2.0 * kPi * p / M;
-        yp[2 * p] = c->C[0] + o.proxy_radius * std::cos(a);
-        yp[2 * p + 1] = c->C[1] + o.proxy_radius * std::sin(a);
+    for (int k = 0; k < n_cells; ++k) {
+        const Cell& cl = c->cells_h[k];
+        for (int i = cl.node_off; i < cl.node_off + cl.n_nodes; ++i) node_cell[i] = k;
+        for (int b = cl.body_off; b < cl.body_off + cl.n_bodies; ++b) body_cell[b] = k;
     }
+    gauss_legendre_half(m, c->gl_host);
+    std::vector<double> yp(nc * 2 * M);
+    for (int k = 0; k < n_cells; ++k)
+        for (int p = 0; p < M; ++p) {
+            double a = 2.0 * kPi * p / M;
+            yp[(size_t)k * 2 * M + 2 * p] = c->cells_h[k].C[0] + o.proxy_radius * std::cos(a);
+            yp[(size_t)k * 2 * M + 2 * p + 1] = c->cells_h[k].C[1] + o.proxy_radius * std::sin(a);
+        }
     auto up = [&](void* d, const void* h, size_t bytes) {
         return cu(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice), "cudaMemcpy");
     };
     rc = up(c->owner, owner.data(), n * sizeof(int));
+    rc = rc ? rc : up(c->node_cell, node_cell.data(), n * sizeof(int));
+    rc = rc ? rc : up(c->body_cell, body_cell.data(), c->nb * sizeof(int));
     rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
     rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
     rc = rc ? rc : up(c->yp, yp.data(), yp.size() * sizeof(double));
+    rc = rc ? rc : up(c->e2d, c->e2_0.data(), c->e2_0.size() * sizeof(double));
+    rc = rc ? rc : build_near_items(c);
+    rc = rc ? rc : build_dot_chunks(c);
     rc = rc ? rc : build_dirichlet_tables(c);
     rc = rc ? rc : rebuild(c);
     rc = rc ? rc : cu(cudaStreamSynchronize(c->stream), "init sync");
     if (rc) {
+        std::string e = c->err;
         free_all(c);
         delete c;
+        (void)e;
         return rc;
     }
+    c->sv.cell_info.assign(n_cells, bie_solve_info{});
     *out = c;
     return BIE_OK;
+}
+
+int bie_init(bie_ctx** out, const bie_lattice* lat, double mu, double gamma, int32_t n_bodies,
+             const bie_body* bodies, const bie_opts* opts) {
+    if (!out) return BIE_EINVAL;
+    *out = nullptr;
+    if (!lat || !bodies || n_bodies <= 0) return BIE_EINVAL;
+    bie_cell cell;
+    cell.lattice = *lat;
+    cell.mu = mu;
+    cell.gamma = gamma;
+    cell.n_bodies = n_bodies;
+    return bie_init_batch(out, 1, &cell, bodies, opts);
 }
 
 void bie_destroy(bie_ctx* c) {
@@ -352,6 +443,21 @@ int bie_size(const bie_ctx* c, int32_t* n_nodes, int32_t* n_bodies) {
     if (!c) return BIE_EINVAL;
     if (n_nodes) *n_nodes = c->N;
     if (n_bodies) *n_bodies = c->nb;
+    return BIE_OK;
+}
+
+int bie_cells(const bie_ctx* c, int32_t* n_cells, int32_t* node_offset, int32_t* body_offset,
+              bie_solve_info* last_solve) {
+    if (!c) return BIE_EINVAL;
+    if (n_cells) *n_cells = c->ncell;
+    for (int k = 0; k < c->ncell; ++k) {
+        const Cell& cl = c->cells_h[k];
+        if (node_offset) node_offset[k] = cl.node_off;
+        if (body_offset) body_offset[k] = cl.body_off;
+        if (last_solve) last_solve[k] = c->sv.cell_info[k];
+    }
+    if (node_offset) node_offset[c->ncell] = c->N;
+    if (body_offset) body_offset[c->ncell] = c->nb;
     return BIE_OK;
 }
 
@@ -457,27 +563,29 @@ int bie_velocities(bie_ctx* c, const double* sigma, double* v, double* omega, do
     if (rc) return rc;
     if ((rc = copy_out(c, v, dv, 2 * (size_t)c->nb, on_device))) return rc;
     if ((rc = copy_out(c, omega, dom, c->nb, on_device))) return rc;
-    if ((rc = copy_out(c, mu_eff, dmu, 1, on_device))) return rc;
+    if ((rc = copy_out(c, mu_eff, dmu, c->ncell, on_device))) return rc;
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
 }
 
 int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_solve_info* info) {
     if (!c || n_steps < 0 || !std::isfinite(dt)) return BIE_EINVAL;
-    if (c->e1[1] != 0.0) return fail(c, BIE_EINVAL, "time stepping needs e1 = (L1, 0)");
+    for (const Cell& cl : c->cells_h)
+        if (cl.e1[1] != 0.0) return fail(c, BIE_EINVAL, "time stepping needs e1 = (L1, 0)");
     BIE_CUDA(c, cudaSetDevice(c->device));
     const size_t n2 = 2 * (size_t)c->N;
     double* dv = c->scal;
     double* dom = c->scal + 2 * c->nb;
     double* dmu = c->scal + 3 * c->nb;
+    std::vector<double> e2n(2 * (size_t)c->ncell);
     for (int s = 0; s < n_steps; ++s) {
-        // the next step's lattice is known now: fit its proxies on the side
-        // stream while this step solves (it only depends on e2(t + dt))
-        double e2n[2];
-        lattice_at(c, c->t + dt, e2n);
+        // the next step's lattices are known now: fit their proxies on the
+        // side stream while this step solves (the fits only depend on e2(t + dt))
+        for (int k = 0; k < c->ncell; ++k) lattice_at(c, k, c->t + dt, &e2n[2 * k]);
         BIE_CUDA(c, cudaEventRecord(c->next_done, c->stream));  // inputs of the fit are ready
         BIE_CUDA(c, cudaStreamWaitEvent(c->side, c->next_done, 0));
-        if (int rc = build_proxy_fit_to(c, e2n, c->next, c->side)) return rc;
+        if (int rc = upload_e2(c, c->next.e2, e2n, c->side)) return rc;
+        if (int rc = build_proxy_fit_to(c, c->next, c->side)) return rc;
         BIE_CUDA(c, cudaEventRecord(c->next_done, c->side));
         int rc = rhs_device(c, c->sv.b);
         if (rc) return rc;
@@ -495,21 +603,32 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         rc = velocities_device(c, c->sv.x, dv, dom, dmu);
         if (rc) return rc;
         if (mu_eff_out)
-            BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + s, dmu, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + (size_t)s * c->ncell, dmu, c->ncell * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
         c->t += dt;
-        c->e2[0] = e2n[0];
-        c->e2[1] = e2n[1];
-        k_euler<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->body, c->nb, dv, dom, dt, c->e1[0], c->e1[1],
-                                                            c->e2[0], c->e2[1], c->C[0], c->C[1]);
+        for (int k = 0; k < c->ncell; ++k) {
+            Cell& cl = c->cells_h[k];
+            const double e1[2] = {cl.e1[0], cl.e1[1]};
+            cell_set_lattice(cl, e1, &e2n[2 * k]);
+        }
+        if ((rc = upload_cells(c, c->stream))) return rc;
+        k_euler<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->body, c->nb, c->body_cell, c->cells, dv, dom, dt);
         BIE_LAUNCH(c, "k_euler");
-        // adopt the prefetched proxy fit, then rebuild nodes and close pairs
+        // adopt the prefetched proxy fits, then rebuild nodes and close pairs
         BIE_CUDA(c, cudaStreamWaitEvent(c->stream, c->next_done, 0));
         std::swap(c->A, c->next.A);
         std::swap(c->beta, c->next.beta);
         std::swap(c->P, c->next.P);
         std::swap(c->wall, c->next.wall);
+        std::swap(c->e2d, c->next.e2);
         if ((rc = build_geometry(c))) return rc;
         if ((rc = build_close(c))) return rc;
+        if (c->opts.min_gap > 0 && c->cl.min_gap < c->opts.min_gap) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "bodies closer than min_gap after the step to t = %.6g: gap %.3e < %.3e", c->t,
+                     c->cl.min_gap, c->opts.min_gap);
+            return fail(c, BIE_ECOLLIDE, msg);
+        }
     }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
@@ -529,10 +648,11 @@ int bie_get_state(bie_ctx* c, double* t, double* e2, double* xc, double* theta, 
     }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     if (t) *t = c->t;
-    if (e2) {
-        e2[0] = c->e2[0];
-        e2[1] = c->e2[1];
-    }
+    if (e2)
+        for (int k = 0; k < c->ncell; ++k) {
+            e2[2 * k] = c->cells_h[k].e2[0];
+            e2[2 * k + 1] = c->cells_h[k].e2[1];
+        }
     for (int b = 0; b < c->nb; ++b) {
         if (xc) {
             xc[2 * b] = h[8 * b + 2];
@@ -548,6 +668,7 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     if (!c || !e2 || !xc || !theta) return BIE_EINVAL;
     BIE_CUDA(c, cudaSetDevice(c->device));
     std::vector<double> h(8 * (size_t)c->nb);
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     BIE_CUDA(c, cudaMemcpy(h.data(), c->body, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
     for (int b = 0; b < c->nb; ++b) {
         h[8 * b + 2] = xc[2 * b];
@@ -555,8 +676,14 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
         h[8 * b + 4] = theta[b];
     }
     c->t = t;
-    c->e2[0] = e2[0];
-    c->e2[1] = e2[1];
+    for (int k = 0; k < c->ncell; ++k) {
+        Cell& cl = c->cells_h[k];
+        const double e1[2] = {cl.e1[0], cl.e1[1]};
+        cell_set_lattice(cl, e1, e2 + 2 * k);
+    }
+    int rc = upload_cells(c, c->stream);
+    if (rc) return rc;
+    if ((rc = upload_e2(c, c->e2d, current_e2(c), c->stream))) return rc;
     BIE_CUDA(c, cudaMemcpyAsync(c->body, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (sigma) {
         BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, sigma, 2 * (size_t)c->N * sizeof(double),
@@ -565,7 +692,7 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     } else {
         c->sv.have_prev = false;
     }
-    int rc = rebuild(c);
+    rc = rebuild(c);
     if (rc) return rc;
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;

@@ -1,16 +1,22 @@
 // The operator application y = A sigma (Eq. BIEdiscretized + L + pressure fix)
-// and the velocity / effective-viscosity extraction.
+// and the velocity / effective-viscosity extraction, for every cell of the
+// batch at once.
 //
 // Launch sequence of one application (all on the context stream):
-//   k_pack          q = sigma w; single- or double-precision source records
+//   k_pack          q = sigma w; single-, double- or double-float source records
 //   k_body_moments  F_b = sum q, tau_b = sum (x - x^c)^perp . q  (one CTA per body)
-//   k_near32/64     3x3 near image sum of G^t at every node (Sec. 6.2 step 1),
-//                   split over source chunks -> partial sums
+//   k_near32/64/df  3x3 near image sum of G^t at every node (Sec. 6.2 step 1): one
+//                   launch over the work items (cell, target tile, source split) of
+//                   all cells -> partial sums per split
 //   k_disc          wall discrepancy of the near sum with the far-image
-//                   cancellation (Sec. 6.2 step 2), split over source chunks
-//   k_xi            g~ = g0 - g, xi = P g~ (Sec. 6.2 step 3)
+//                   cancellation (Sec. 6.2 step 2), per (wall point, split, cell)
+//   k_xi            g~ = g0 - g, xi = P g~ (Sec. 6.2 step 3), per (row, cell)
 //   k_correct       T = sum of partials + on-curve diagonal + proxy traction (step 4)
-//   k_finish        alpha = -T_0 . n_0;  y = sigma/2 + T + alpha n + L sigma
+//   k_close_apply   close-evaluation correction (Sec. 6.3)
+//   k_finish        alpha = -T_0 . n_0 per cell;  y = sigma/2 + T + alpha n + L sigma
+#include <algorithm>
+#include <cmath>
+
 #include "bie_internal.cuh"
 
 namespace bie {
@@ -52,14 +58,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 // ---------------------------------------------------------------------------
 __global__ void k_pack(const double2* __restrict__ sigma, const double* __restrict__ x,
-                       const double* __restrict__ y, const double* __restrict__ w, int N, double Cx,
-                       double Cy, float4* __restrict__ src32, Src64* __restrict__ src64) {
+                       const double* __restrict__ y, const double* __restrict__ w,
+                       const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
+                       float4* __restrict__ src32, Src64* __restrict__ src64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double2 s = sigma[i];
     double wi = w[i];
     double qx = s.x * wi, qy = s.y * wi;
-    if (src32) src32[i] = make_float4((float)(x[i] - Cx), (float)(y[i] - Cy), (float)qx, (float)qy);
+    if (src32) {
+        const Cell& cl = cells[node_cell[i]];
+        src32[i] = make_float4((float)(x[i] - cl.C[0]), (float)(y[i] - cl.C[1]), (float)qx, (float)qy);
+    }
     if (src64) src64[i] = Src64{x[i], y[i], qx, qy};
 }
 
@@ -90,43 +100,61 @@ __global__ void k_body_moments(const double2* __restrict__ sigma, const double* 
     }
 }
 
-struct Shifts9 {
-    float x[9], y[9];
-};
-struct Shifts9d {
-    double x[9], y[9];
+// Work item of a near-sum launch: cell, target tile and source split.  The
+// tile covers `tile` targets of the cell; the split covers the cell's sources
+// [split * chunk, (split + 1) * chunk), chunk = ceil(N_cell / splits).
+struct ItemRange {
+    int c, i0, i1, j0, j1, nloc;
+    long long out;  // partial base of this split: part_off + split * N_cell - node_off
 };
 
+__device__ __forceinline__ bool item_range(const int4* items, const Cell* cells, int prec, int tile, ItemRange& r) {
+    const int4 it = items[blockIdx.x];
+    const Cell& cl = cells[it.x];
+    if (!cl.active) return false;
+    const int sp = cl.splits[prec];
+    const int chunk = (cl.n_nodes + sp - 1) / sp;
+    r.c = it.x;
+    r.nloc = cl.n_nodes;
+    r.i0 = cl.node_off + it.y * tile;
+    r.i1 = min(cl.node_off + cl.n_nodes, r.i0 + tile);
+    r.j0 = cl.node_off + it.z * chunk;
+    r.j1 = min(cl.node_off + cl.n_nodes, r.j0 + chunk);
+    r.out = cl.part_off[prec] + (long long)it.z * cl.n_nodes - cl.node_off;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
-// Near image sum, single precision.  Block: kNearThreads threads, each owning
-// TPT targets; grid.x over target tiles, grid.y over source chunks.  The 9
-// image shifts are applied to the target (x_t - s) so every staged source is
-// reused by 9 * TPT pair evaluations.  Per pair: 13 FP32 instructions and one
-// MUFU reciprocal.  The zero-distance self pair is absorbed by a 1e-30 floor
-// on r^2 (its r.n and r.q are exactly zero, so it contributes 0).
+// Near image sum, single precision.  One CTA per work item; kNearThreads
+// threads, each owning TPT targets.  The 9 image shifts are applied to the
+// target (x_t - s) so every staged source is reused by 9 * TPT pair
+// evaluations.  Per pair: 13 FP32 instructions and one MUFU reciprocal.  The
+// zero-distance self pair is absorbed by a 1e-30 floor on r^2 (its r.n and
+// r.q are exactly zero, so it contributes 0).
 // ---------------------------------------------------------------------------
 template <int TPT, bool COMP>
 __global__ void __launch_bounds__(kNearThreads)
-k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, int chunk, Shifts9 sh,
-         float2* __restrict__ part) {
+k_near32(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
+         const float4* __restrict__ src, float2* __restrict__ part) {
     __shared__ float4 s_src[kNearTile];
-    const int j0 = blockIdx.y * chunk;
-    const int j1 = min(N, j0 + chunk);
+    ItemRange rg;
+    if (!item_range(items, cells, 0, kNearThreads * TPT, rg)) return;
+    const Cell& cl = cells[rg.c];
     float px[TPT][9], py[TPT][9], nxv[TPT], nyv[TPT];
     float ax[TPT][3], ay[TPT][3];
     // COMP: each source tile's sum is folded into a TwoSum-compensated pair
     // (hi, lo), so that splits with very many sources keep single-precision
     // accuracy relative to the sum instead of losing it to rounding growth.
     float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
-    int tbase = blockIdx.x * (kNearThreads * TPT) + threadIdx.x;
+    const int tbase = rg.i0 + threadIdx.x;
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         int i = tbase + t * kNearThreads;
-        float4 tv = i < N ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
+        float4 tv = i < rg.i1 ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            px[t][k] = tv.x - sh.x[k];
-            py[t][k] = tv.y - sh.y[k];
+            px[t][k] = tv.x - cl.sxf[k];
+            py[t][k] = tv.y - cl.syf[k];
         }
         nxv[t] = tv.z;
         nyv[t] = tv.w;
@@ -134,8 +162,8 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
         for (int r = 0; r < 3; ++r) ax[t][r] = ay[t][r] = 0.f;
         hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
     }
-    for (int jt = j0; jt < j1; jt += kNearTile) {
-        int cnt = min(kNearTile, j1 - jt);
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        int cnt = min(kNearTile, rg.j1 - jt);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
         __syncthreads();
@@ -177,11 +205,11 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         int i = tbase + t * kNearThreads;
-        if (i < N) {
+        if (i < rg.i1) {
             if constexpr (COMP)
-                part[(size_t)blockIdx.y * N + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
+                part[rg.out + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
             else
-                part[(size_t)blockIdx.y * N + i] =
+                part[rg.out + i] =
                     make_float2(c * (ax[t][0] + ax[t][1] + ax[t][2]), c * (ay[t][0] + ay[t][1] + ay[t][2]));
         }
     }
@@ -190,15 +218,16 @@ k_near32(const float4* __restrict__ tgt, const float4* __restrict__ src, int N, 
 // Near image sum, double precision (one target per thread).  Same structure;
 // the self pair is absorbed by a 1e-300 floor on r^2.
 __global__ void __launch_bounds__(kNearThreads)
-k_near64(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
-         const double* __restrict__ ny, const Src64* __restrict__ src, int N, int chunk, Shifts9d sh,
-         double2* __restrict__ part) {
+k_near64(const int4* __restrict__ items, const Cell* __restrict__ cells, const double* __restrict__ x,
+         const double* __restrict__ y, const double* __restrict__ nx, const double* __restrict__ ny,
+         const Src64* __restrict__ src, double2* __restrict__ part) {
     __shared__ Src64 s_src[kNearTile];
-    const int j0 = blockIdx.y * chunk;
-    const int j1 = min(N, j0 + chunk);
-    int i = blockIdx.x * kNearThreads + threadIdx.x;
+    ItemRange rg;
+    if (!item_range(items, cells, 1, kNearThreads, rg)) return;
+    const Cell& cl = cells[rg.c];
+    const int i = rg.i0 + threadIdx.x;
     double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
-    if (i < N) {
+    if (i < rg.i1) {
         tx = x[i];
         ty = y[i];
         tnx = nx[i];
@@ -207,12 +236,12 @@ k_near64(const double* __restrict__ x, const double* __restrict__ y, const doubl
     double px[9], py[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        px[k] = tx - sh.x[k];
-        py[k] = ty - sh.y[k];
+        px[k] = tx - cl.sx[k];
+        py[k] = ty - cl.sy[k];
     }
     double ax[3] = {0, 0, 0}, ay[3] = {0, 0, 0};
-    for (int jt = j0; jt < j1; jt += kNearTile) {
-        int cnt = min(kNearTile, j1 - jt);
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        int cnt = min(kNearTile, rg.j1 - jt);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
         __syncthreads();
@@ -232,9 +261,9 @@ k_near64(const double* __restrict__ x, const double* __restrict__ y, const doubl
             }
         }
     }
-    if (i < N) {
+    if (i < rg.i1) {
         const double c = -1.0 / kPi;
-        part[(size_t)blockIdx.y * N + i] = make_double2(c * (ax[0] + ax[1] + ax[2]), c * (ay[0] + ay[1] + ay[2]));
+        part[rg.out + i] = make_double2(c * (ax[0] + ax[1] + ax[2]), c * (ay[0] + ay[1] + ay[2]));
     }
 }
 
@@ -247,10 +276,11 @@ k_near64(const double* __restrict__ x, const double* __restrict__ y, const doubl
 // for products, MUFU rcp refined by one FMA residual step for 1/r^2; the
 // difference r = x - y is formed exactly from both words (three TwoSums) and
 // r, r.n, r.q are renormalised before they are multiplied, so that the
-// dropped lo*lo cross terms stay at 2^-48; the accumulator keeps its TwoSum
-// error in a float.  About 140 FP32 instructions per pair; each term is
-// accurate to ~1e-14 of the kernel's scale |q| / |r| at any distance (the
-// inputs carry 48 of double's 53 bits).
+// dropped lo*lo cross terms stay at 2^-48; each source tile's sum is kept as
+// (TwoSum hi, float error) and folded into double accumulators.  About 140
+// FP32 instructions per pair; each term is accurate to ~1e-14 of the
+// kernel's scale |q| / |r| at any distance (the inputs carry 48 of double's
+// 53 bits).
 // ---------------------------------------------------------------------------
 struct __align__(16) SrcDF {
     float xh, xl, yh, yl, qxh, qxl, qyh, qyl;
@@ -286,40 +316,43 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
 }
 
 __global__ void k_pack_df(const double2* __restrict__ sigma, const double* __restrict__ x,
-                          const double* __restrict__ y, const double* __restrict__ w, int N, double Cx, double Cy,
+                          const double* __restrict__ y, const double* __restrict__ w,
+                          const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                           SrcDF* __restrict__ src) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const Cell& cl = cells[node_cell[i]];
     double2 s = sigma[i];
     double wi = w[i];
     SrcDF r;
-    split_df(x[i] - Cx, r.xh, r.xl);
-    split_df(y[i] - Cy, r.yh, r.yl);
+    split_df(x[i] - cl.C[0], r.xh, r.xl);
+    split_df(y[i] - cl.C[1], r.yh, r.yl);
     split_df(s.x * wi, r.qxh, r.qxl);
     split_df(s.y * wi, r.qyh, r.qyl);
     src[i] = r;
 }
 
 __global__ void __launch_bounds__(kNearThreads, 4)
-k_near_df(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
-          const double* __restrict__ ny, const SrcDF* __restrict__ src, int N, int chunk, Shifts9d sh, double Cx,
-          double Cy, double2* __restrict__ part) {
+k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const double* __restrict__ x,
+          const double* __restrict__ y, const double* __restrict__ nx, const double* __restrict__ ny,
+          const SrcDF* __restrict__ src, double2* __restrict__ part) {
     __shared__ SrcDF s_src[kNearTile];
-    const int j0 = blockIdx.y * chunk;
-    const int j1 = min(N, j0 + chunk);
-    const int i = blockIdx.x * kNearThreads + threadIdx.x;
+    ItemRange rg;
+    if (!item_range(items, cells, 2, kNearThreads, rg)) return;
+    const Cell& cl = cells[rg.c];
+    const int i = rg.i0 + threadIdx.x;
     double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
-    if (i < N) {
-        tx = x[i] - Cx;
-        ty = y[i] - Cy;
+    if (i < rg.i1) {
+        tx = x[i] - cl.C[0];
+        ty = y[i] - cl.C[1];
         tnx = nx[i];
         tny = ny[i];
     }
     float pxh[9], pxl[9], pyh[9], pyl[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        split_df(tx - sh.x[k], pxh[k], pxl[k]);
-        split_df(ty - sh.y[k], pyh[k], pyl[k]);
+        split_df(tx - cl.sx[k], pxh[k], pxl[k]);
+        split_df(ty - cl.sy[k], pyh[k], pyl[k]);
     }
     float nxh, nxl, nyh, nyl;
     split_df(tnx, nxh, nxl);
@@ -327,8 +360,8 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
     // per tile: hi sums by TwoSum, their errors in a float; folded into double
     // accumulators after every tile so that neither grows with the source count
     double dxs = 0, dys = 0;
-    for (int jt = j0; jt < j1; jt += kNearTile) {
-        int cnt = min(kNearTile, j1 - jt);
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        int cnt = min(kNearTile, rg.j1 - jt);
         float axh = 0, axe = 0, ayh = 0, aye = 0;
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
@@ -369,14 +402,14 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
                 rql = e + e1 + e2;
                 fast2(rqh, rql);
                 // c = (r.n / r^2) (r.q / r^2), term = c r
-                float uh, ul, vh, vl, ch, cl, th, tl;
+                float uh, ul, vh, vl, ch, cl2, th, tl;
                 df_mul(rnh, rnl, ih, il, uh, ul);
                 df_mul(rqh, rql, ih, il, vh, vl);
-                df_mul(uh, ul, vh, vl, ch, cl);
-                df_mul(ch, cl, rxh, rxl, th, tl);
+                df_mul(uh, ul, vh, vl, ch, cl2);
+                df_mul(ch, cl2, rxh, rxl, th, tl);
                 two_sum(axh, th, axh, e);
                 axe += e + tl;
-                df_mul(ch, cl, ryh, ryl, th, tl);
+                df_mul(ch, cl2, ryh, ryl, th, tl);
                 two_sum(ayh, th, ayh, e);
                 aye += e + tl;
             }
@@ -384,20 +417,22 @@ k_near_df(const double* __restrict__ x, const double* __restrict__ y, const doub
         dxs += (double)axh + (double)axe;
         dys += (double)ayh + (double)aye;
     }
-    if (i < N) {
+    if (i < rg.i1) {
         const double c = -1.0 / kPi;
-        part[(size_t)blockIdx.y * N + i] = make_double2(c * dxs, c * dys);
+        part[rg.out + i] = make_double2(c * dxs, c * dys);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Wall table (per geometry): for each collocation point (L points, then D
-// points) the point minus each of its six far-image shifts, and the wall
-// normal used for the traction.
-__global__ void k_wall_table(int m, const double* __restrict__ gl_s, double e1x, double e1y, double e2x,
-                             double e2y, double Cx, double Cy, double* __restrict__ wall) {
-    int wp = blockIdx.x * blockDim.x + threadIdx.x;
+// Wall table (per geometry and cell): for each collocation point (L points,
+// then D points) the point minus each of its six far-image shifts, and the
+// wall normal used for the traction.  grid.y = cell.
+__global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell* __restrict__ cells,
+                             const double* __restrict__ e2v, double* __restrict__ wall) {
+    const int wp = blockIdx.x * blockDim.x + threadIdx.x, cidx = blockIdx.y;
     if (wp >= 2 * m) return;
+    const Cell& cl = cells[cidx];
+    const double e1x = cl.e1[0], e1y = cl.e1[1], e2x = e2v[2 * cidx], e2y = e2v[2 * cidx + 1];
+    const double Cx = cl.C[0], Cy = cl.C[1];
     double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
     wall_normals(e1, e2, nl, nd);
     const bool isL = wp < m;
@@ -412,7 +447,7 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, double e1x,
         Y = Cy - 0.5 * e2y + s * e1y;
         ax = e2x; ay = e2y; bx = e1x; by = e1y;
     }
-    double* o = wall + 16 * wp;
+    double* o = wall + ((size_t)cidx * 2 * m + wp) * 16;
     for (int k = -1; k <= 1; ++k) {
         o[2 * (k + 1)] = X - (-2.0 * ax + k * bx);
         o[2 * (k + 1) + 1] = Y - (-2.0 * ay + k * by);
@@ -424,8 +459,7 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, double e1x,
 }
 
 int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st) {
-    k_wall_table<<<(2 * c->m + 63) / 64, 64, 0, st>>>(c->m, c->gl_s, c->e1[0], c->e1[1], e2[0], e2[1], c->C[0],
-                                                      c->C[1], wall);
+    k_wall_table<<<dim3((2 * c->m + 63) / 64, c->ncell), 64, 0, st>>>(c->m, c->gl_s, c->cells, e2, wall);
     BIE_LAUNCH(c, "k_wall_table");
     return BIE_OK;
 }
@@ -433,11 +467,10 @@ int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st
 // Wall discrepancy (Sec. 6.2 step 2).  For a collocation point x on L,
 //   S_near(x + e1) - S_near(x) = sum_n sum_j [K(x, y_j - 2 e1 + n e2) - K(x, y_j + e1 + n e2)] q_j
 // and on D with the roles of e1, e2 exchanged; K is the velocity kernel G or
-// the traction kernel G^t with the wall normal.  Block (wp, s): wall point
-// wp in [0, 2m) (L points, then D points) and source split s of kDiscSplits;
-// its threads stride over the split's sources and the block reduces
-// (u_x, u_y, t_x, t_y) into gpart[(s * 2m + wp) * 4 + comp].
-// ---------------------------------------------------------------------------
+// the traction kernel G^t with the wall normal.  Block (wp, s, cell): wall
+// point wp in [0, 2m) (L points, then D points) of the cell and source split
+// s of kDiscSplits; its threads stride over the split's sources and the block
+// reduces (u_x, u_y, t_x, t_y) into gpart[((cell * kDiscSplits + s) * 2m + wp) * 4 + comp].
 __device__ __forceinline__ float fast_log(float x) { return __logf(x); }
 __device__ __forceinline__ double fast_log(double x) { return log(x); }
 __device__ __forceinline__ float fast_rcp(float x) { return rcp_approx(x); }
@@ -445,13 +478,15 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ wall, double mu,
+k_disc(const Src64* __restrict__ src, const Cell* __restrict__ cells, int m, const double* __restrict__ wall,
        double* __restrict__ gpart) {
     __shared__ double red[4][33];
-    const int wp = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+    const int wp = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y, cidx = blockIdx.z;
+    const Cell& cl = cells[cidx];
+    if (!cl.active) return;
     // per-geometry table: collocation point minus each of the six far-image
     // shifts (plus images -2a + kb, then minus images a + kb), and the normal
-    const double* wt = wall + 16 * wp;
+    const double* wt = wall + ((size_t)cidx * 2 * m + wp) * 16;
     Real ox[6], oy[6];
 #pragma unroll
     for (int im = 0; im < 6; ++im) {
@@ -460,8 +495,8 @@ k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ w
     }
     const Real n0 = (Real)wt[12], n1 = (Real)wt[13];
     Real ux = 0, uy = 0, tx = 0, ty = 0;
-    const int per = (N + nsp - 1) / nsp;
-    const int j0 = sp * per, j1 = min(N, j0 + per);
+    const int per = (cl.n_nodes + nsp - 1) / nsp;
+    const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const Src64 q = src[j];
         const Real qx = (Real)q.z, qy = (Real)q.w, sx = (Real)q.x, sy = (Real)q.y;
@@ -494,27 +529,31 @@ k_disc(const Src64* __restrict__ src, int N, int m, const double* __restrict__ w
     if (threadIdx.x < 4) {
         double t = 0;
         for (int k = 0; k < nw; ++k) t += red[threadIdx.x][k];
-        const double scale = threadIdx.x < 2 ? 1.0 / (4.0 * kPi * mu) : -1.0 / kPi;
-        gpart[((size_t)sp * 2 * m + wp) * 4 + threadIdx.x] = t * scale;
+        const double scale = threadIdx.x < 2 ? 1.0 / (4.0 * kPi * cl.mu) : -1.0 / kPi;
+        gpart[(((size_t)cidx * kDiscSplits + sp) * 2 * m + wp) * 4 + threadIdx.x] = t * scale;
     }
 }
 
-// g~ and xi = P g~ (Sec. 6.2 step 3).  One warp-sized CTA per row r of P (2M
-// CTAs): GB300's FP64 pipe is narrow, so the compensated products are spread
-// over as many SMs as there are rows.  Every CTA rebuilds g~ from the kDiscSplits
-// partials of the discrepancy kernel (fixed order: deterministic) and then
-// computes xi_r with a compensated dot product (Ogita, Rump & Oishi's Dot2:
-// FMA-exact products, error-free sums; P has entries up to ~1/lam, so a plain
-// double-precision product would add relative noise ~1e-11 to the correction
-// and put a floor under the GMRES residual).
+// g~ and xi = P g~ (Sec. 6.2 step 3).  One warp-sized CTA per (row r of P,
+// cell): GB300's FP64 pipe is narrow, so the compensated products are spread
+// over as many SMs as there are rows.  Every CTA rebuilds g~ from the
+// kDiscSplits partials of the discrepancy kernel (fixed order: deterministic)
+// and then computes xi_r with a compensated dot product (Ogita, Rump &
+// Oishi's Dot2: FMA-exact products, error-free sums; P has entries up to
+// ~1/lam, so a plain double-precision product would add relative noise ~1e-11
+// to the correction and put a floor under the GMRES residual).
 __global__ void __launch_bounds__(32)
-k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __restrict__ bodyF, int nb,
-     double l1, double l2, const double* __restrict__ P, double* __restrict__ xi) {
+k_xi(const double* __restrict__ gpart, int m, int M, const double* __restrict__ bodyF,
+     const Cell* __restrict__ cells, const double* __restrict__ Pall, double* __restrict__ xiall) {
     extern __shared__ double d[];  // 8m: g~
-    const int lane = threadIdx.x, r = blockIdx.x;
+    const int lane = threadIdx.x, r = blockIdx.x, cidx = blockIdx.y;
+    const Cell& cl = cells[cidx];
+    if (!cl.active) return;
     const int nv = 8 * m;
+    const double* gp = gpart + (size_t)cidx * kDiscSplits * nv;
+    const double* P = Pall + (size_t)cidx * 2 * M * nv;
     double fx = 0, fy = 0;
-    for (int b = lane; b < nb; b += 32) {
+    for (int b = cl.body_off + lane; b < cl.body_off + cl.n_bodies; b += 32) {
         fx += bodyF[3 * b];
         fy += bodyF[3 * b + 1];
     }
@@ -522,12 +561,13 @@ k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __r
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
     }
+    const double l1 = cl.l1, l2 = cl.l2;
     for (int wp = lane; wp < 2 * m; wp += 32) {
         double g[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             double a = 0;
-            for (int b = 0; b < nblk; ++b) a += gpart[(size_t)b * nv + 4 * wp + c];
+            for (int b = 0; b < kDiscSplits; ++b) a += gp[(size_t)b * nv + 4 * wp + c];
             g[c] = a;
         }
         if (wp < m) {  // L: rows of blocks 1 (velocity) and 2 (traction)
@@ -563,32 +603,39 @@ k_xi(const double* __restrict__ gpart, int nblk, int m, int M, const double* __r
         e = e + e2 + ((s - (t - z)) + (s2 - z));
         s = t;
     }
-    if (lane == 0) xi[r] = s + e;
+    if (lane == 0) xiall[(size_t)cidx * 2 * M + r] = s + e;
 }
 
 // T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy
 // traction.  ProxyReal = float on the single-precision path (rcp.approx, the
-// inner-solve operator), double on the FP64 path.
+// inner-solve operator), double on the FP64 path.  kCorrLanes lanes per
+// target split the near-sum partials and the proxies, then combine with
+// shuffles (fixed order: deterministic).
 template <typename PartT, typename ProxyReal>
 __global__ void __launch_bounds__(256)
-k_correct(const PartT* __restrict__ part, int splits, int N, const double2* __restrict__ sigma,
-          const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
-          const double* __restrict__ ny, const double* __restrict__ w, const double* __restrict__ kap,
-          const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx, double Cy,
-          double2* __restrict__ T) {
-    // kCorrLanes lanes per target: they split the near-sum partials and the
-    // proxies, then combine with shuffles (fixed order: deterministic)
+k_correct(const PartT* __restrict__ part, int prec, int N, const int* __restrict__ node_cell,
+          const Cell* __restrict__ cells, const double2* __restrict__ sigma, const double* __restrict__ x,
+          const double* __restrict__ y, const double* __restrict__ nx, const double* __restrict__ ny,
+          const double* __restrict__ w, const double* __restrict__ kap, const double* __restrict__ ypall,
+          const double* __restrict__ xiall, int M, double2* __restrict__ T) {
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kCorrLanes;
     const int sub = threadIdx.x % kCorrLanes;
     const int i = g < N ? g : N - 1;
+    const int cidx = node_cell[i];
+    const Cell& cl = cells[cidx];
     double tx = 0, ty = 0;
+    const int splits = cl.splits[prec];
+    const long long base = cl.part_off[prec] + (i - cl.node_off);
     for (int s = sub; s < splits; s += kCorrLanes) {
-        PartT p = part[(size_t)s * N + i];
+        PartT p = part[base + (long long)s * cl.n_nodes];
         tx += (double)p.x;
         ty += (double)p.y;
     }
     const double n0 = nx[i], n1 = ny[i];
     // proxies in cell-centred coordinates (exact in double, accurate in float)
+    const double Cx = cl.C[0], Cy = cl.C[1];
+    const double* yp = ypall + (size_t)cidx * 2 * M;
+    const double* xi = xiall + (size_t)cidx * 2 * M;
     const ProxyReal X = (ProxyReal)(x[i] - Cx), Y = (ProxyReal)(y[i] - Cy);
     const ProxyReal m0 = (ProxyReal)n0, m1 = (ProxyReal)n1;
     ProxyReal cx = 0, cy = 0;
@@ -622,11 +669,13 @@ __global__ void k_finish(const double2* __restrict__ T, const double2* __restric
                          const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ nx, const double* __restrict__ ny,
                          const int* __restrict__ owner, const double* __restrict__ body,
-                         const double* __restrict__ bodyF, double2* __restrict__ out) {
+                         const double* __restrict__ bodyF, const int* __restrict__ node_cell,
+                         const Cell* __restrict__ cells, double2* __restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double2 T0 = T[0];
-    double alpha = -(T0.x * nx[0] + T0.y * ny[0]);
+    const int i0 = cells[node_cell[i]].node_off;  // node 0 of the cell's first body
+    double2 T0 = T[i0];
+    double alpha = -(T0.x * nx[i0] + T0.y * ny[i0]);
     int b = owner[i];
     double xc = body[8 * b + 2], yc = body[8 * b + 3];
     double Fx = bodyF[3 * b], Fy = bodyF[3 * b + 1], tq = bodyF[3 * b + 2];
@@ -636,147 +685,218 @@ __global__ void k_finish(const double2* __restrict__ T, const double2* __restric
     out[i] = make_double2(ox, oy);
 }
 
-__global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ ny, int N, double mg,
+__global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ ny,
+                      const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                       double2* __restrict__ b) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) b[i] = make_double2(-mg * ny[i], -mg * nx[i]);
+    if (i >= N) return;
+    const Cell& cl = cells[node_cell[i]];
+    const double mg = cl.mu * cl.gamma;
+    b[i] = make_double2(-mg * ny[i], -mg * nx[i]);
 }
 
 // ---------------------------------------------------------------------------
-static void shifts(const bie_ctx* c, double* sx, double* sy, bool centred) {
-    int k = 0;
-    for (int n = -1; n <= 1; ++n)
-        for (int mm = -1; mm <= 1; ++mm, ++k) {
-            sx[k] = mm * c->e1[0] + n * c->e2[0];
-            sy[k] = mm * c->e1[1] + n * c->e2[1];
+// near-sum work items
+// ---------------------------------------------------------------------------
+static int near_tile(int prec) { return prec == 0 ? kNearThreads * kNear32TPT : kNearThreads; }
+static int near_ctas_per_sm(int prec) { return prec == 0 ? kNear32CtasPerSM : (prec == 1 ? 5 : 4); }
+
+// Source splits of every cell for one precision.  All items of one launch
+// cost about the same per staged source whatever their targets (masked
+// targets still run), so a launch takes about ceil(items / slots) waves of
+// the longest item.  For w = 1, 2, ... the cells' splits are sized so that
+// their items fill w waves of the resident CTA slots of all SMs (each cell in
+// proportion to its share of the pairs), and the w with the least modelled
+// time wins: waves x (longest source chunk + a per-item overhead of
+// kItemOverhead sources).  Deterministic: no timing is involved.
+static constexpr int kItemOverhead = 32;
+
+static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, std::vector<int>& splits) {
+    double W = 0;
+    for (const Cell& cl : cells) W += (double)cl.n_nodes * cl.n_nodes;
+    double best = 1e300;
+    std::vector<int> sp(cells.size());
+    for (int w = 1; w <= 16; ++w) {
+        long long items = 0;
+        int maxchunk = 0;
+        for (size_t k = 0; k < cells.size(); ++k) {
+            const int n = cells[k].n_nodes;
+            const int tiles = (n + tile - 1) / tile;
+            const double share = (double)w * slots * ((double)n * n / W) / tiles;
+            const int s = std::max(1, std::min((n + 63) / 64, (int)share));
+            sp[k] = s;
+            items += (long long)tiles * s;
+            maxchunk = std::max(maxchunk, (n + s - 1) / s);
         }
-    (void)centred;
+        const double cost = (double)((items + slots - 1) / slots) * (maxchunk + kItemOverhead);
+        if (cost < best * (1 - 1e-9)) {
+            best = cost;
+            splits = sp;
+        }
+    }
 }
 
-int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
+// Items (cell, target tile, source split) for every precision; also sets each
+// cell's splits and partial offsets and uploads the cell table.
+int build_near_items(bie_ctx* c) {
+    for (int prec = 0; prec < 3; ++prec) {
+        const int tile = near_tile(prec);
+        std::vector<int> splits;
+        choose_splits(c->cells_h, tile, near_ctas_per_sm(prec) * kSMs, splits);
+        std::vector<int4> items;
+        long long off = 0;
+        for (int ci = 0; ci < c->ncell; ++ci) {
+            Cell& cl = c->cells_h[ci];
+            const int n = cl.n_nodes;
+            cl.splits[prec] = splits[ci];
+            cl.part_off[prec] = off;
+            off += (long long)splits[ci] * n;
+            const int tiles = (n + tile - 1) / tile;
+            for (int t = 0; t < tiles; ++t)
+                for (int s = 0; s < splits[ci]; ++s) items.push_back(make_int4(ci, t, s, 0));
+        }
+        const size_t bytes = off * (prec == 0 ? sizeof(float2) : sizeof(double2));
+        if (bytes > c->ws.part_bytes) return fail(c, BIE_EINVAL, "near-sum partial buffer too small");
+        if (c->near[prec].items) cudaFree(c->near[prec].items);
+        c->near[prec].items = nullptr;
+        BIE_CUDA(c, cudaMalloc((void**)&c->near[prec].items, items.size() * sizeof(int4)));
+        BIE_CUDA(c, cudaMemcpy(c->near[prec].items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        c->near[prec].count = (int)items.size();
+    }
+    return upload_cells(c, c->stream);
+}
+
+// Bytes of the near-sum partial buffer (largest over the precisions).
+size_t near_part_bytes(const bie_ctx* c) {
+    size_t best = 0;
+    for (int prec = 0; prec < 3; ++prec) {
+        std::vector<int> splits;
+        choose_splits(c->cells_h, near_tile(prec), near_ctas_per_sm(prec) * kSMs, splits);
+        long long off = 0;
+        for (size_t k = 0; k < splits.size(); ++k) off += (long long)splits[k] * c->cells_h[k].n_nodes;
+        best = std::max(best, (size_t)off * (prec == 0 ? sizeof(float2) : sizeof(double2)));
+    }
+    return best;
+}
+
+// Elements of the single-precision partial buffer for the current splits.
+size_t near_part32_elems(const bie_ctx* c) {
+    const Cell& last = c->cells_h.back();
+    return (size_t)(last.part_off[0] + (long long)last.splits[0] * last.n_nodes);
+}
+
+static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
+    const NearItems& it = c->near[0];
+    if (it.count == 0) return BIE_OK;
+    // splits with many sources keep their accuracy through compensated tile sums
+    int maxchunk = 0;
+    for (const Cell& cl : c->cells_h) maxchunk = std::max(maxchunk, (cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
+    if (maxchunk > kNear32CompChunk)
+        k_near32<kNear32TPT, true><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+    else
+        k_near32<kNear32TPT, false><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+    BIE_LAUNCH(c, "k_near32");
+    return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precision, Workspace& ws) {
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
-    bool f32 = precision == BIE_MIXED;
-    bool df = precision == BIE_DF64;
-    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], f32 ? c->ws.src32 : nullptr,
-                                     c->ws.src64);
+    const bool f32 = precision == BIE_MIXED;
+    const bool df = precision == BIE_DF64;
+    const int prec = f32 ? 0 : (df ? 2 : 1);
+    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, f32 ? ws.src32 : nullptr,
+                                     ws.src64);
     BIE_LAUNCH(c, "k_pack");
     if (df) {
-        k_pack_df<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], (SrcDF*)c->ws.srcdf);
+        k_pack_df<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, (SrcDF*)ws.srcdf);
         BIE_LAUNCH(c, "k_pack_df");
     }
-    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
+    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
-    double sx[9], sy[9];
-    shifts(c, sx, sy, false);
-    int splits;
+    if (int rc = prof_begin(c, prec == 0 ? 0 : (prec == 1 ? 1 : 2))) return rc;
     if (f32) {
-        Shifts9 s9;
-        for (int k = 0; k < 9; ++k) {
-            s9.x[k] = (float)sx[k];
-            s9.y[k] = (float)sy[k];
-        }
-        splits = c->near_splits32;
-        int tiles = (N + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
-        int chunk = (N + splits - 1) / splits;
-        dim3 grid(tiles, splits);
-        if (int rc = prof_begin(c, 0)) return rc;
-        if (chunk > kNear32CompChunk)
-            k_near32<kNear32TPT, true><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
-                                                                             (float2*)c->ws.part);
-        else
-            k_near32<kNear32TPT, false><<<grid, kNearThreads, 0, c->stream>>>(c->tgt32, c->ws.src32, N, chunk, s9,
-                                                                              (float2*)c->ws.part);
-        BIE_LAUNCH(c, "k_near32");
-        if (int rc = prof_end(c)) return rc;
+        if (int rc = launch_near32(c, ws.src32, (float2*)ws.part)) return rc;
     } else if (df) {
-        Shifts9d s9;
-        for (int k = 0; k < 9; ++k) {
-            s9.x[k] = sx[k];
-            s9.y[k] = sy[k];
-        }
-        splits = c->near_splitsdf;
-        int tiles = (N + kNearThreads - 1) / kNearThreads;
-        int chunk = (N + splits - 1) / splits;
-        dim3 grid(tiles, splits);
-        if (int rc = prof_begin(c, 2)) return rc;
-        k_near_df<<<grid, kNearThreads, 0, c->stream>>>(c->x, c->y, c->nx, c->ny, (const SrcDF*)c->ws.srcdf, N, chunk,
-                                                        s9, c->C[0], c->C[1], (double2*)c->ws.part);
+        k_near_df<<<c->near[2].count, kNearThreads, 0, c->stream>>>(c->near[2].items, c->cells, c->x, c->y, c->nx,
+                                                                    c->ny, (const SrcDF*)ws.srcdf, (double2*)ws.part);
         BIE_LAUNCH(c, "k_near_df");
-        if (int rc = prof_end(c)) return rc;
     } else {
-        Shifts9d s9;
-        for (int k = 0; k < 9; ++k) {
-            s9.x[k] = sx[k];
-            s9.y[k] = sy[k];
-        }
-        splits = c->near_splits64;
-        int tiles = (N + kNearThreads - 1) / kNearThreads;
-        int chunk = (N + splits - 1) / splits;
-        dim3 grid(tiles, splits);
-        if (int rc = prof_begin(c, 1)) return rc;
-        k_near64<<<grid, kNearThreads, 0, c->stream>>>(c->x, c->y, c->nx, c->ny, c->ws.src64, N, chunk, s9,
-                                                       (double2*)c->ws.part);
+        k_near64<<<c->near[1].count, kNearThreads, 0, c->stream>>>(c->near[1].items, c->cells, c->x, c->y, c->nx,
+                                                                   c->ny, ws.src64, (double2*)ws.part);
         BIE_LAUNCH(c, "k_near64");
-        if (int rc = prof_end(c)) return rc;
     }
+    if (int rc = prof_end(c)) return rc;
+    const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
     if (f32)
-        k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
+        k_disc<float><<<dgrid, 256, 0, c->stream>>>(ws.src64, c->cells, c->m, c->wall, ws.gpart);
     else
-        k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
+        k_disc<double><<<dgrid, 256, 0, c->stream>>>(ws.src64, c->cells, c->m, c->wall, ws.gpart);
     BIE_LAUNCH(c, "k_disc");
-    double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
-    double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
-                                                          c->nb, l1, l2, c->P, c->ws.xi);
+    k_xi<<<dim3(2 * c->M, c->ncell), 32, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, c->m, c->M, ws.bodyF,
+                                                                                 c->cells, c->P, ws.xi);
     BIE_LAUNCH(c, "k_xi");
-    double2* T = reinterpret_cast<double2*>(c->ws.T);
+    double2* T = reinterpret_cast<double2*>(ws.T);
     const int gsc = (N * kCorrLanes + 255) / 256;
     if (f32)
-        k_correct<float2, float><<<gsc, 256, 0, c->stream>>>((const float2*)c->ws.part, splits, N, sg, c->x, c->y,
-                                                             c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi, c->M,
-                                                             c->C[0], c->C[1], T);
+        k_correct<float2, float><<<gsc, 256, 0, c->stream>>>((const float2*)ws.part, prec, N, c->node_cell, c->cells,
+                                                             sg, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->yp,
+                                                             ws.xi, c->M, T);
     else
-        k_correct<double2, double><<<gsc, 256, 0, c->stream>>>((const double2*)c->ws.part, splits, N, sg, c->x,
-                                                               c->y, c->nx, c->ny, c->w, c->kap, c->yp, c->ws.xi,
-                                                               c->M, c->C[0], c->C[1], T);
+        k_correct<double2, double><<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell,
+                                                               c->cells, sg, c->x, c->y, c->nx, c->ny, c->w, c->kap,
+                                                               c->yp, ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
-    if (int rc = close_apply(c, sigma, c->ws.T)) return rc;
-    k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, c->ws.bodyF,
-                                       reinterpret_cast<double2*>(yout));
+    if (int rc = close_apply(c, sigma, ws.T)) return rc;
+    k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
+                                       c->cells, reinterpret_cast<double2*>(yout));
     BIE_LAUNCH(c, "k_finish");
     return BIE_OK;
 }
 
+int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
+    return apply_impl(c, sigma, yout, precision, c->ws);
+}
+
+// The single-precision-pair operator application with every per-call buffer
+// taken from `ws` (used by the allocation-free entry point, whose buffers
+// live in a static device array).  The context is only read.
+int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws) {
+    return apply_impl(c, sigma, yout, BIE_MIXED, ws);
+}
+
 int rhs_device(bie_ctx* c, double* b) {
     int bs = 256, gs = (c->N + bs - 1) / bs;
-    k_rhs<<<gs, bs, 0, c->stream>>>(c->nx, c->ny, c->N, c->mu * c->gamma, reinterpret_cast<double2*>(b));
+    k_rhs<<<gs, bs, 0, c->stream>>>(c->nx, c->ny, c->node_cell, c->cells, c->N, reinterpret_cast<double2*>(b));
     BIE_LAUNCH(c, "k_rhs");
     return BIE_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Rigid-body velocities at the centroids (one CTA per body) and mu_eff.
+// Rigid-body velocities at the centroids and mu_eff.
 // u(x^c) = sum_images sum_j G(x^c, y_j + s) q_j + sum_p G(x^c, y_p) xi_p
 //          - sum_p G(C, y_p) xi_p;  curl by the closed form of the Stokeslet.
+// Block (b, s): body b's centroid against source split s of its cell; split 0
+// also adds the proxy terms.  vpart[(b * splits + s) * 3 + c].
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __restrict__ body,
-             const double* __restrict__ yp, const double* __restrict__ xi, int M, double Cx, double Cy,
-             double* __restrict__ vpart) {
-    // block (b, s): body b's centroid against source split s of gridDim.y;
-    // split 0 also adds the proxy terms.  vpart[(b * splits + s) * 3 + c].
+k_velocities(const Src64* __restrict__ src, const double* __restrict__ body, const int* __restrict__ body_cell,
+             const Cell* __restrict__ cells, const double* __restrict__ ypall, const double* __restrict__ xiall,
+             int M, double* __restrict__ vpart) {
     __shared__ double red[33];
     const int b = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
+    const int cidx = body_cell[b];
+    const Cell& cl = cells[cidx];
     const double X = body[8 * b + 2], Y = body[8 * b + 3];
     double ux = 0, uy = 0, cu = 0;
-    const int per = (N + nsp - 1) / nsp;
-    const int j0 = sp * per, j1 = min(N, j0 + per);
+    const int per = (cl.n_nodes + nsp - 1) / nsp;
+    const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         Src64 q = src[j];
         for (int k = 0; k < 9; ++k) {
-            double rx = X - (q.x + sh.x[k]), ry = Y - (q.y + sh.y[k]);
+            double rx = X - (q.x + cl.sx[k]), ry = Y - (q.y + cl.sy[k]);
             double r2 = rx * rx + ry * ry;
             double rq = (rx * q.z + ry * q.w) / r2;
             double l = -0.5 * log(r2);
@@ -786,6 +906,8 @@ k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __
         }
     }
     if (sp == 0) {
+        const double* yp = ypall + (size_t)cidx * 2 * M;
+        const double* xi = xiall + (size_t)cidx * 2 * M;
         for (int p = threadIdx.x; p < M; p += blockDim.x) {
             double fx = xi[p], fy = xi[M + p];
             double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
@@ -795,8 +917,8 @@ k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __
             ux += l * fx + rx * rq;
             uy += l * fy + ry * rq;
             cu += (ry * fx - rx * fy) / r2;
-            rx = Cx - yp[2 * p];
-            ry = Cy - yp[2 * p + 1];
+            rx = cl.C[0] - yp[2 * p];
+            ry = cl.C[1] - yp[2 * p + 1];
             r2 = rx * rx + ry * ry;
             rq = (rx * fx + ry * fy) / r2;
             l = -0.5 * log(r2);
@@ -816,9 +938,11 @@ k_velocities(const Src64* __restrict__ src, int N, Shifts9d sh, const double* __
 }
 
 __global__ void k_velocities_fin(const double* __restrict__ vpart, int nb, int nsp, const double* __restrict__ body,
-                                 double mu, double gamma, double* __restrict__ v, double* __restrict__ om) {
+                                 const int* __restrict__ body_cell, const Cell* __restrict__ cells,
+                                 double* __restrict__ v, double* __restrict__ om) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
+    const Cell& cl = cells[body_cell[b]];
     double ux = 0, uy = 0, cu = 0;
     for (int s = 0; s < nsp; ++s) {
         const double* o = vpart + ((size_t)b * nsp + s) * 3;
@@ -826,110 +950,52 @@ __global__ void k_velocities_fin(const double* __restrict__ vpart, int nb, int n
         uy += o[1];
         cu += o[2];
     }
-    const double c4 = 1.0 / (4.0 * kPi * mu);
-    v[2 * b] = ux * c4 + gamma * body[8 * b + 3];
+    const double c4 = 1.0 / (4.0 * kPi * cl.mu);
+    v[2 * b] = ux * c4 + cl.gamma * body[8 * b + 3];
     v[2 * b + 1] = uy * c4;
-    om[b] = 0.5 * (cu / (2.0 * kPi * mu) - gamma);
+    om[b] = 0.5 * (cu / (2.0 * kPi * cl.mu) - cl.gamma);
 }
 
+// mu_eff per cell (one CTA per cell): the particle-stress average
 __global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __restrict__ y,
                          const double* __restrict__ w, const int* __restrict__ owner,
-                         const double* __restrict__ body, int N, double mu, double gamma, double area,
-                         double* __restrict__ out) {
+                         const double* __restrict__ body, const Cell* __restrict__ cells, double* __restrict__ out) {
     __shared__ double red[33];
+    const Cell& cl = cells[blockIdx.x];
     double s = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) s += sigma[i].x * (y[i] - body[8 * owner[i] + 3]) * w[i];
+    for (int i = cl.node_off + threadIdx.x; i < cl.node_off + cl.n_nodes; i += blockDim.x)
+        s += sigma[i].x * (y[i] - body[8 * owner[i] + 3]) * w[i];
     s = block_sum_d(s, red);
-    if (threadIdx.x == 0) *out = mu - s / (gamma * area);
+    const double area = fabs(cl.e1[0] * cl.e2[1] - cl.e1[1] * cl.e2[0]);
+    if (threadIdx.x == 0) out[blockIdx.x] = cl.mu - s / (cl.gamma * area);
 }
 
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff) {
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
-    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], nullptr, c->ws.src64);
+    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, nullptr, c->ws.src64);
     BIE_LAUNCH(c, "k_pack");
     k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
-    k_disc<double><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(c->ws.src64, N, c->m, c->wall, c->mu, c->ws.gpart);
+    k_disc<double><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(c->ws.src64, c->cells, c->m, c->wall,
+                                                                                 c->ws.gpart);
     BIE_LAUNCH(c, "k_disc");
-    double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
-    double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, kDiscSplits, c->m, c->M, c->ws.bodyF,
-                                                          c->nb, l1, l2, c->P, c->ws.xi);
+    k_xi<<<dim3(2 * c->M, c->ncell), 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, c->m, c->M,
+                                                                                 c->ws.bodyF, c->cells, c->P, c->ws.xi);
     BIE_LAUNCH(c, "k_xi");
-    double sx[9], sy[9];
-    shifts(c, sx, sy, false);
-    Shifts9d s9;
-    for (int k = 0; k < 9; ++k) {
-        s9.x[k] = sx[k];
-        s9.y[k] = sy[k];
-    }
     if (v || omega) {
-        k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, N, s9, c->body, c->yp, c->ws.xi,
-                                                                     c->M, c->C[0], c->C[1], c->ws.vpart);
+        k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, c->body, c->body_cell, c->cells,
+                                                                     c->yp, c->ws.xi, c->M, c->ws.vpart);
         BIE_LAUNCH(c, "k_velocities");
-        k_velocities_fin<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->ws.vpart, c->nb, kVelSplits, c->body, c->mu,
-                                                                     c->gamma, v, omega);
+        k_velocities_fin<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->ws.vpart, c->nb, kVelSplits, c->body,
+                                                                     c->body_cell, c->cells, v, omega);
         BIE_LAUNCH(c, "k_velocities_fin");
     }
     if (mu_eff) {
-        double area = fabs(c->e1[0] * c->e2[1] - c->e1[1] * c->e2[0]);
-        k_mu_eff<<<1, 1024, 0, c->stream>>>(sg, c->y, c->w, c->owner, c->body, N, c->mu, c->gamma, area, mu_eff);
+        k_mu_eff<<<c->ncell, 256, 0, c->stream>>>(sg, c->y, c->w, c->owner, c->body, c->cells, mu_eff);
         BIE_LAUNCH(c, "k_mu_eff");
     }
-    return BIE_OK;
-}
-
-}  // namespace bie
-
-namespace bie {
-
-// The single-precision-pair operator application with every per-call buffer
-// taken from `ws` (used by the allocation-free entry point, whose buffers
-// live in a static device array).  The kernels and their order are those of
-// apply_device; the context is only read.
-int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws) {
-    const int N = c->N;
-    const int bs = 256, gs = (N + bs - 1) / bs;
-    const double2* sg = reinterpret_cast<const double2*>(sigma);
-    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, N, c->C[0], c->C[1], ws.src32, ws.src64);
-    BIE_LAUNCH(c, "k_pack");
-    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, ws.bodyF);
-    BIE_LAUNCH(c, "k_body_moments");
-    double sx[9], sy[9];
-    shifts(c, sx, sy, false);
-    Shifts9 s9;
-    for (int k = 0; k < 9; ++k) {
-        s9.x[k] = (float)sx[k];
-        s9.y[k] = (float)sy[k];
-    }
-    const int splits = c->near_splits32;
-    const int tiles = (N + kNearThreads * kNear32TPT - 1) / (kNearThreads * kNear32TPT);
-    const int chunk = (N + splits - 1) / splits;
-    if (chunk > kNear32CompChunk)
-        k_near32<kNear32TPT, true><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N, chunk,
-                                                                                       s9, (float2*)ws.part);
-    else
-        k_near32<kNear32TPT, false><<<dim3(tiles, splits), kNearThreads, 0, c->stream>>>(c->tgt32, ws.src32, N,
-                                                                                        chunk, s9, (float2*)ws.part);
-    BIE_LAUNCH(c, "k_near32");
-    k_disc<float><<<dim3(2 * c->m, kDiscSplits), 256, 0, c->stream>>>(ws.src64, N, c->m, c->wall, c->mu, ws.gpart);
-    BIE_LAUNCH(c, "k_disc");
-    const double l1 = sqrt(c->e1[0] * c->e1[0] + c->e1[1] * c->e1[1]);
-    const double l2 = sqrt(c->e2[0] * c->e2[0] + c->e2[1] * c->e2[1]);
-    k_xi<<<2 * c->M, 32, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, kDiscSplits, c->m, c->M, ws.bodyF, c->nb, l1,
-                                                          l2, c->P, ws.xi);
-    BIE_LAUNCH(c, "k_xi");
-    double2* T = reinterpret_cast<double2*>(ws.T);
-    k_correct<float2, float><<<(N * kCorrLanes + 255) / 256, 256, 0, c->stream>>>((const float2*)ws.part, splits, N, sg, c->x,
-                                                                  c->y, c->nx, c->ny, c->w, c->kap, c->yp, ws.xi,
-                                                                  c->M, c->C[0], c->C[1], T);
-    BIE_LAUNCH(c, "k_correct");
-    if (int rc = close_apply(c, sigma, ws.T)) return rc;
-    k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF,
-                                       reinterpret_cast<double2*>(yout));
-    BIE_LAUNCH(c, "k_finish");
     return BIE_OK;
 }
 

@@ -36,10 +36,11 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
     // layout of the per-call buffers inside the static array
     const size_t b_src32 = round256(N * sizeof(float4));
     const size_t b_src64 = round256(N * sizeof(Src64));
-    const size_t b_part = round256((size_t)c->near_splits32 * N * sizeof(float2));
+    const size_t nc = (size_t)c->ncell;
+    const size_t b_part = round256(near_part32_elems(c) * sizeof(float2));
     const size_t b_body = round256(3 * (size_t)c->nb * sizeof(double));
-    const size_t b_gpart = round256((size_t)kDiscBlocks * 2 * c->m * 4 * sizeof(double));
-    const size_t b_xi = round256(2 * (size_t)c->M * sizeof(double));
+    const size_t b_gpart = round256(nc * kDiscSplits * 8 * c->m * sizeof(double));
+    const size_t b_xi = round256(nc * 2 * c->M * sizeof(double));
     const size_t b_T = round256(2 * N * sizeof(double));
     const size_t need = b_src32 + b_src64 + b_part + b_body + b_gpart + b_xi + b_T;
     if (need > BIE_STATIC_SCRATCH_BYTES)

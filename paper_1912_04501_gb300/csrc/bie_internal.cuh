@@ -1,14 +1,22 @@
 // Internal declarations of the GB300 periodized Stokes BIE library.
+//
+// A context holds one or more independent unit cells (a batch); a single cell
+// is a batch of one.  Nodes and bodies of all cells are concatenated; every
+// kernel finds a node's or body's cell through node_cell / body_cell and the
+// per-cell table `cells`.
+//
 // Layout in HBM (all device arrays owned by the context):
-//   geometry  : x, y, nx, ny, w, kappa   (N doubles each, SoA)
-//               owner (N ints), body (nb x 8 doubles: a, b, xc, yc, theta, n, off, h)
-//               tgt32 (N float4: x - C, y - C, nx, ny)  -- single-precision targets
+//   geometry  : x, y, nx, ny, w, kappa (N doubles each, SoA), owner (N ints, global
+//               body index), node_cell (N), body (nb x 8 doubles: a, b, xc, yc, theta,
+//               n, node offset, h), body_cell (nb), tgt32 (N float4: x - C, y - C, nx, ny)
 //   densities : 2N doubles, node-major (x, y interleaved) == double2[N]
-//   sources   : src32 (N float4: x - C, y - C, qx, qy), src64 (N Src64: x, y, qx, qy)
-//   proxy fit : Q stacked with lam*I (column-major, R = 8m + 2M rows, 2M cols),
-//               Householder betas, P (2M x 8m, row-major), proxies yp (M double2),
-//               wall table (2m x 16 doubles: six far-image offsets and the normal per
-//               collocation point)
+//   sources   : src32 (N float4: x - C, y - C, qx, qy), src64 (N Src64: x, y, qx, qy),
+//               srcdf (N double-float records)
+//   per cell  : Cell table; proxies yp (M x 2), stacked [Q; lam I] (column-major,
+//               R = 8m + 2M rows, 2M cols), Householder scalars, P (2M x 8m, row-major),
+//               wall table (2m x 16), proxy strengths xi (2M), discrepancy partials
+//   near sums : work items (cell, target tile, source split) per precision; partial
+//               sums per cell: splits x N_cell (float2 or double2)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,17 +48,25 @@ constexpr int kNearTile = 256;                  // sources staged per shared-mem
 constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
 constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
 constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
-constexpr int kDiscBlocks = 96;       // capacity of the discrepancy partial buffer (splits)
 constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)
 constexpr int kVelSplits = 8;         // source splits per body in the velocity extraction
+constexpr int kDotChunk = 512;        // vector entries per partial dot product (chunks never span cells)
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
+constexpr int kMaxCells = 4096;
 
-// Image shifts m e1 + n e2, index (n + 1) * 3 + (m + 1); index 4 is zero.
-struct Shifts9dC {
-    double x[9], y[9];
+// One unit cell of the batch (device table; the host keeps a mirror).
+struct Cell {
+    double e1[2], e2[2], C[2];
+    double mu, gamma, l1, l2;
+    double sx[9], sy[9];      // image shifts m e1 + n e2, index (n + 1) * 3 + (m + 1); index 4 is zero
+    float sxf[9], syf[9];
+    int node_off, n_nodes, body_off, n_bodies;
+    long long part_off[3];    // near-sum partial base (elements) per precision: 0 f32, 1 f64, 2 df64
+    int splits[3];            // source splits per precision
+    int active;               // solver mask: inactive cells skip the near sums
 };
 
 // Close-evaluation storage (Sec. 6.3): per-target slots, compacted pairs,
@@ -64,11 +80,13 @@ struct Close {
     double* blocks = nullptr;     // cap_doubles
     double* dtab = nullptr;       // Dirichlet tables per distinct node count
     long long* dtab_off = nullptr;  // nb: table base of each body
-    int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved]
+    int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved,
+                                  //  smallest gap below min_gap (8 bytes)]
     int cap_pairs = 0;
     long long cap_doubles = 0;
     int npairs = 0;
     int under_resolved = 0;       // pairs closer than the finest rule (rho = 64) resolves
+    double min_gap = 0;           // smallest node-to-curve gap below opts.min_gap (else infinity)
     size_t shm_limit = 0;
 };
 
@@ -80,25 +98,27 @@ struct __align__(16) Src64 {
 struct Workspace {
     double* sigma = nullptr;    // 2N  staging for host inputs
     double* out = nullptr;      // 2N  staging for host outputs
-    Src64* src64 = nullptr;   // N
+    Src64* src64 = nullptr;     // N
     float4* src32 = nullptr;    // N
     void* srcdf = nullptr;      // N double-float source records (32 B)
     double* bodyF = nullptr;    // 3 nb  (F_x, F_y, tau) per body
-    void* part = nullptr;       // near-sum partials: splits x N (float2 or double2)
+    void* part = nullptr;       // near-sum partials (see Cell::part_off)
     size_t part_bytes = 0;
-    double* gpart = nullptr;    // kDiscBlocks x 2m x 4 discrepancy partials
-    double* xi = nullptr;       // 2M proxy strengths
+    double* gpart = nullptr;    // ncell x kDiscSplits x 8m discrepancy partials
+    double* xi = nullptr;       // ncell x 2M proxy strengths
     double* T = nullptr;        // 2N traction before the pressure fix
     double* vpart = nullptr;    // nb x kVelSplits x 3 velocity partials
 };
 
-// One proxy least-squares fit (Sec. 6.1) for a given lattice: stacked matrix,
-// Householder scalars and diagonal, solution operator, wall table.
+// Proxy least-squares fits (Sec. 6.1) of every cell for given lattices:
+// stacked matrices, Householder scalars and diagonals, solution operators,
+// wall tables (each array holds ncell consecutive blocks).
 struct ProxyFit {
     double* A = nullptr;
     double* beta = nullptr;
     double* P = nullptr;
     double* wall = nullptr;
+    double* e2 = nullptr;   // 2 x ncell: the lattice vectors e2 the fits are for
 };
 
 struct Solver {
@@ -109,11 +129,20 @@ struct Solver {
     double* x = nullptr;     // 2N current solution
     double* b = nullptr;     // 2N right-hand side
     double* d = nullptr;     // 2N correction (mixed)
-    double* h = nullptr;     // kmax + 2 dot products
-    double* red = nullptr;   // reduction scratch
-    double* dpart = nullptr; // (kmax + 2) x 64 partial dot products
+    double* h = nullptr;     // (3 (kmax + 2) + 1) x ncell dot products, norms, coefficients
+    double* dpart = nullptr; // (kmax + 2) x nchunks partial dot products
+    int4* chunks = nullptr;  // nchunks: (cell, first entry, end entry, 0)
+    int2* cell_chunks = nullptr;  // ncell: (first chunk, chunk count)
+    int nchunks = 0;
     double* sigma_prev = nullptr;  // 2N warm start of the next step
     bool have_prev = false;
+    std::vector<bie_solve_info> cell_info;  // last solve, per cell
+};
+
+// Near-sum work list of one precision: one CTA per item (cell, tile, split).
+struct NearItems {
+    int4* items = nullptr;
+    int count = 0;
 };
 
 }  // namespace bie
@@ -122,32 +151,37 @@ struct bie_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bie_opts opts{};
-    double e1[2]{}, e2[2]{}, e2_0[2]{}, C[2]{};
-    double mu = 1, gamma = 1, t = 0;
-    int nb = 0, N = 0, M = 0, m = 0;
-    std::vector<int> n_nodes, offsets;
-    std::vector<double> body_host;  // nb x 8 (a, b, xc, yc, theta, n, off, h)
+    double t = 0;
+    int ncell = 0, nb = 0, N = 0, M = 0, m = 0;
+    std::vector<int> n_nodes, offsets;     // per body
+    std::vector<double> body_host;         // nb x 8 (a, b, xc, yc, theta, n, off, h)
+    std::vector<bie::Cell> cells_h;        // host mirror of the cell table
+    std::vector<double> e2_0;              // 2 x ncell lattice vectors e2 at t = 0
+    bie::Cell* cells = nullptr;            // device cell table
+    int* node_cell = nullptr;              // N
+    int* body_cell = nullptr;              // nb
     // device geometry
     double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kap = nullptr;
     int* owner = nullptr;
     double* body = nullptr;
     float4* tgt32 = nullptr;
-    // proxy fit
+    // proxy fits of the current lattices, and of the next time step's (built on
+    // a side stream during the current solve)
     double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
-    double* A = nullptr;        // stacked [Q; lam I], column-major
-    double* beta = nullptr;     // 2M Householder scalars
-    double* P = nullptr;        // 2M x 8m solution operator, row-major
-    double* wall = nullptr;     // 2m x 16: collocation point minus each far-image shift (6 x 2), wall normal
-    // the next time step's proxy fit, built on a side stream during the current solve
+    double* A = nullptr;        // ncell x stacked [Q; lam I], column-major
+    double* beta = nullptr;     // ncell x 4M Householder scalars and diagonal
+    double* P = nullptr;        // ncell x 2M x 8m solution operators, row-major
+    double* wall = nullptr;     // ncell x 2m x 16 wall tables
+    double* e2d = nullptr;      // 2 x ncell current lattice vectors e2 (device)
     bie::ProxyFit next;
     cudaStream_t side = nullptr;
     cudaEvent_t next_done = nullptr;
-    double* yp = nullptr;       // 2M proxies (x, y) interleaved
-    double* scal = nullptr;     // misc device scalars
+    double* yp = nullptr;       // ncell x M x 2 proxy points
+    double* scal = nullptr;     // 3 nb + ncell + 8: velocities, rotation rates, mu_eff
     bie::Workspace ws;
     bie::Solver sv;
     bie::Close cl;
-    int near_splits32 = 1, near_splits64 = 1, near_splitsdf = 1;
+    bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
     long long launches = 0;
@@ -181,11 +215,15 @@ int prof_begin(bie_ctx* c, int kind);
 int prof_end(bie_ctx* c);
 int prof_fold(bie_ctx* c);
 
+// cell table on host and device --------------------------------------------
+void cell_set_lattice(Cell& cell, const double* e1, const double* e2);
+int upload_cells(bie_ctx* c, cudaStream_t st);
+
 // geometry.cu ---------------------------------------------------------------
 int build_geometry(bie_ctx* c);   // nodes from body state
-int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P for the current lattice
-int build_proxy_fit_to(bie_ctx* c, const double* e2, ProxyFit& f, cudaStream_t st);
-int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st);
+int build_proxy_fit(bie_ctx* c);  // Q, QR of [Q; lam I], P for the current lattices
+int build_proxy_fit_to(bie_ctx* c, ProxyFit& f, cudaStream_t st);  // for the lattices f.e2 (device)
+int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st);  // e2: device, 2 x ncell
 void gauss_legendre_half(int m, std::vector<double>& s);
 
 // close.cu ------------------------------------------------------------------
@@ -194,15 +232,21 @@ int build_dirichlet_tables(bie_ctx* c);                    // once per context
 int close_apply(bie_ctx* c, const double* sigma, double* T);  // T += C sigma
 
 // apply.cu ------------------------------------------------------------------
-// y = A sigma for device sigma, y (2N each); precision BIE_FP64 / BIE_MIXED
+// near-sum work items (and partial offsets) for the current cell sizes
+int build_near_items(bie_ctx* c);
+size_t near_part_bytes(const bie_ctx* c);     // partial buffer the items need
+size_t near_part32_elems(const bie_ctx* c);   // single-precision partials of the current items
+// y = A sigma for device sigma, y (2N each); precision BIE_FP64 / BIE_MIXED / BIE_DF64
 int apply_device(bie_ctx* c, const double* sigma, double* y, int precision);
 // single-precision-pair application with caller-provided per-call buffers
 int apply_device_ws(bie_ctx* c, const double* sigma, double* y, Workspace& ws);
 int rhs_device(bie_ctx* c, double* b);
+// per body v (2 nb), omega (nb); per cell mu_eff (ncell)
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff);
 
 // solve.cu ------------------------------------------------------------------
 int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info);
+int build_dot_chunks(bie_ctx* c);
 
 // small device math shared by the kernels --------------------------------------
 __host__ __device__ inline void wall_normals(const double* e1, const double* e2, double* nl, double* nd) {

@@ -16,6 +16,7 @@
 // G^t applied to q is c r (r . q) with c = -(r . n)/(pi r^4), so each C_k is
 // a symmetric 2 x 2 matrix: three doubles (A, B, D) per node.
 #include <cmath>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -41,33 +42,39 @@ __global__ void k_body_h(const double* __restrict__ w, double* __restrict__ body
     }
 }
 
-// One thread per target: every (body, image) closer than close_factor * h_b
-// goes to the target's slots in (body, image) order.  slot record:
-// int4 (body, image, rho, 0).
+// One thread per target: every (body, image) of the target's cell closer than
+// close_factor * h_b goes to the target's slots in (body, image) order.  slot
+// record: int4 (body, image, rho, 0).  Distances to the curve below gap_lim
+// (other bodies and the target's own periodic images) lower *gap_min, the
+// bit pattern of a non-negative double (such patterns order like integers).
 __global__ void k_close_detect(const double* __restrict__ x, const double* __restrict__ y,
-                               const int* __restrict__ owner, const double* __restrict__ body, int nb, int N,
-                               Shifts9dC sh, double close_factor, int kmax, int4* __restrict__ slots,
-                               int* __restrict__ count, int* __restrict__ overflow) {
+                               const int* __restrict__ owner, const double* __restrict__ body,
+                               const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
+                               double close_factor, double gap_lim, int kmax, int4* __restrict__ slots,
+                               int* __restrict__ count, int* __restrict__ overflow,
+                               unsigned long long* __restrict__ gap_min) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const Cell& sh = cells[node_cell[i]];
     double X = x[i], Y = y[i];
     int own = owner[i];
     int c = 0;
-    for (int b = 0; b < nb; ++b) {
+    for (int b = sh.body_off; b < sh.body_off + sh.n_bodies; ++b) {
         const double* bd = body + 8 * b;
         double R = fmax(bd[0], bd[1]);
         double hb = bd[7];
-        double lim = close_factor * hb;
+        double zone = close_factor * hb;
+        double lim = fmax(zone, gap_lim);
         int n = (int)bd[5], off = (int)bd[6];
         for (int im = 0; im < 9; ++im) {
             if (b == own && im == 4) continue;  // zero shift of the own body
-            double cx = bd[2] + sh.x[im], cy = bd[3] + sh.y[im];
+            double cx = bd[2] + sh.sx[im], cy = bd[3] + sh.sy[im];
             double dc = sqrt((X - cx) * (X - cx) + (Y - cy) * (Y - cy));
             if (dc - R > lim) continue;
             double d2 = 1e300;
             int kbest = 0;
             for (int k = 0; k < n; ++k) {
-                double dx = X - (x[off + k] + sh.x[im]), dy = Y - (y[off + k] + sh.y[im]);
+                double dx = X - (x[off + k] + sh.sx[im]), dy = Y - (y[off + k] + sh.sy[im]);
                 double e = dx * dx + dy * dy;
                 if (e < d2) { d2 = e; kbest = k; }
             }
@@ -94,6 +101,8 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
                 dcur = sqrt((a * cs - u) * (a * cs - u) + (b2 * sn - v) * (b2 * sn - v));
                 hloc = 2.0 * kPi * sqrt(a * a * sn * sn + b2 * b2 * cs * cs) / n;
             }
+            if (dcur < gap_lim) atomicMin(gap_min, (unsigned long long)__double_as_longlong(dcur));
+            if (!(sqrt(d2) < zone)) continue;
             // For a density of full bandwidth the rho-fold rule errs by about
             // exp(-(rho - 1/2) 2 pi d / h_loc): rho - 1/2 >= 6.4 h_loc / d puts it
             // below e^-40; rho >= 2 everywhere in the zone (the smooth rule,
@@ -196,7 +205,8 @@ __global__ void __launch_bounds__(256)
 k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk_off,
                const double* __restrict__ x, const double* __restrict__ y,
                const double* __restrict__ nx, const double* __restrict__ ny,
-               const double* __restrict__ w, const double* __restrict__ body, Shifts9dC sh,
+               const double* __restrict__ w, const double* __restrict__ body,
+               const int* __restrict__ node_cell, const Cell* __restrict__ cells,
                const double* __restrict__ dtab, const long long* __restrict__ dtab_off,
                double* __restrict__ blocks) {
     extern __shared__ double sm[];
@@ -206,8 +216,9 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
     double* acc = sm + 3 * kCloseChunk;
     int4 pr = pairs[blockIdx.x];
     int i = pr.x, b = pr.y, im = pr.z, rho = pr.w;
+    const Cell& sh = cells[node_cell[i]];
     const double* bd = body + 8 * b;
-    double a = bd[0], bb = bd[1], xc = bd[2] + sh.x[im], yc = bd[3] + sh.y[im], th = bd[4];
+    double a = bd[0], bb = bd[1], xc = bd[2] + sh.sx[im], yc = bd[3] + sh.sy[im], th = bd[4];
     int nbn = (int)bd[5], off = (int)bd[6];
     int nf = rho * nbn;
     const double* dir = dtab + dtab_off[b] + (long long)nbn * (rho - 2);
@@ -264,7 +275,7 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
     double* out = blocks + blk_off[blockIdx.x];
     for (int k = threadIdx.x; k < nbn; k += blockDim.x) {
         // minus the smooth rule's term for node k of this body image
-        double rx = X - (x[off + k] + sh.x[im]), ry = Y - (y[off + k] + sh.y[im]);
+        double rx = X - (x[off + k] + sh.sx[im]), ry = Y - (y[off + k] + sh.sy[im]);
         double r2 = rx * rx + ry * ry;
         double cc = -(rx * n0 + ry * n1) * w[off + k] / (kPi * r2 * r2);
         out[3 * k] = acc[3 * k] - cc * rx * rx;
@@ -307,36 +318,31 @@ __global__ void k_close_apply(const int* __restrict__ pair_base, const int4* __r
     }
 }
 
-static Shifts9dC shifts_of(const bie_ctx* c) {
-    Shifts9dC s;
-    int k = 0;
-    for (int n = -1; n <= 1; ++n)
-        for (int mm = -1; mm <= 1; ++mm, ++k) {
-            s.x[k] = mm * c->e1[0] + n * c->e2[0];
-            s.y[k] = mm * c->e1[1] + n * c->e2[1];
-        }
-    return s;
-}
-
 int build_close(bie_ctx* c) {
     c->cl.npairs = 0;
     k_body_h<<<c->nb, 256, 0, c->stream>>>(c->w, c->body);
     BIE_LAUNCH(c, "k_body_h");
-    if (!(c->opts.close_factor > 0)) return BIE_OK;
+    c->cl.min_gap = INFINITY;
+    const double gap_lim = c->opts.min_gap > 0 ? c->opts.min_gap : 0.0;
+    if (!(c->opts.close_factor > 0) && !(gap_lim > 0)) return BIE_OK;
     const int N = c->N, kmax = kCloseSlots;
-    Shifts9dC sh = shifts_of(c);
     BIE_CUDA(c, cudaMemsetAsync(c->cl.flags, 0, 4 * sizeof(int), c->stream));
-    k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->nb, N, sh,
-                                                         c->opts.close_factor, kmax, c->cl.slots, c->cl.count,
-                                                         c->cl.flags + 2);
+    unsigned long long* gap_min = reinterpret_cast<unsigned long long*>(c->cl.flags + 4);
+    BIE_CUDA(c, cudaMemsetAsync(gap_min, 0xFF, sizeof(unsigned long long), c->stream));
+    k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->node_cell, c->cells, N,
+                                                         c->opts.close_factor, gap_lim, kmax, c->cl.slots,
+                                                         c->cl.count, c->cl.flags + 2, gap_min);
     BIE_LAUNCH(c, "k_close_detect");
     k_close_scan<<<1, 1024, 0, c->stream>>>(c->cl.count, N, kmax, c->cl.slots, c->body, c->cl.pair_base,
                                            c->cl.blk_off, c->cl.pairs, c->cl.flags, c->cl.cap_doubles,
                                            c->cl.cap_pairs);
     BIE_LAUNCH(c, "k_close_scan");
     int h[4];
+    unsigned long long gm = 0;
     BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaMemcpyAsync(&gm, gap_min, sizeof gm, cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (gm != ~0ULL) std::memcpy(&c->cl.min_gap, &gm, sizeof gm);
     if (h[2] > 0)
         return fail(c, BIE_EINVAL, "a node is close to more than " + std::to_string(kmax) +
                                        " body images (bodies overlap or nearly so)");
@@ -352,7 +358,7 @@ int build_close(bie_ctx* c) {
     BIE_CUDA(c, cudaFuncSetAttribute(k_close_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     c->cl.shm_limit = shm;
     k_close_blocks<<<h[0], 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
-                                                  c->body, sh, c->cl.dtab, c->cl.dtab_off, c->cl.blocks);
+                                                  c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off, c->cl.blocks);
     BIE_LAUNCH(c, "k_close_blocks");
     return BIE_OK;
 }

@@ -1,11 +1,13 @@
 // Per-geometry precompute: boundary nodes (Sec. 6, trapezoidal rule on each
-// ellipse) and the proxy-Stokeslet least-squares operator of Sec. 6.1.
+// ellipse) and, per cell, the proxy-Stokeslet least-squares operator of
+// Sec. 6.1.
 //
 // The proxy fit solves min |Q xi - d|^2 + lam^2 |xi|^2 (lam = lam_rel ||Q||_F),
 // i.e. the least-squares problem of the stacked matrix [Q; lam I], by
 // Householder QR in double precision.  The explicit operator P with
 // xi = P d is formed once per geometry so that each operator application
-// needs a single small matrix-vector product.
+// needs a single small matrix-vector product.  Cells are independent: every
+// kernel runs over all cells of the batch at once (grid dimension "cell").
 #include <cmath>
 
 #include "bie_internal.cuh"
@@ -15,13 +17,15 @@ namespace bie {
 // ---------------------------------------------------------------------------
 // nodes, normals, weights, curvature
 // ---------------------------------------------------------------------------
-__global__ void k_geometry(const double* __restrict__ body, const int* __restrict__ owner, int N,
-                           double Cx, double Cy, double* __restrict__ x, double* __restrict__ y,
-                           double* __restrict__ nx, double* __restrict__ ny, double* __restrict__ w,
-                           double* __restrict__ kap, float4* __restrict__ tgt32) {
+__global__ void k_geometry(const double* __restrict__ body, const int* __restrict__ owner,
+                           const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
+                           double* __restrict__ x, double* __restrict__ y, double* __restrict__ nx,
+                           double* __restrict__ ny, double* __restrict__ w, double* __restrict__ kap,
+                           float4* __restrict__ tgt32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double* bd = body + 8 * owner[i];
+    const Cell& cl = cells[node_cell[i]];
     double a = bd[0], b = bd[1], xc = bd[2], yc = bd[3], th = bd[4];
     int n = (int)bd[5], off = (int)bd[6];
     int k = i - off;
@@ -41,7 +45,7 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
     ny[i] = -tx;
     w[i] = (2.0 * kPi / n) * sp;
     kap[i] = (dX * ddY - dY * ddX) / (sp * sp * sp);
-    tgt32[i] = make_float4((float)(X - Cx), (float)(Y - Cy), (float)ty, (float)(-tx));
+    tgt32[i] = make_float4((float)(X - cl.C[0]), (float)(Y - cl.C[1]), (float)ty, (float)(-tx));
 }
 
 // ---------------------------------------------------------------------------
@@ -70,7 +74,7 @@ void gauss_legendre_half(int m, std::vector<double>& s) {
 
 // ---------------------------------------------------------------------------
 // proxy matrix Q (Sec. 6.1): rows [g1; g2; g3; g4] x (1-comps, 2-comps),
-// columns (xi_1 of all proxies, xi_2 of all proxies)
+// columns (xi_1 of all proxies, xi_2 of all proxies); grid.y = cell
 // ---------------------------------------------------------------------------
 __device__ inline void stokeslet_d(double rx, double ry, double fx, double fy, double c4,
                                    double& ux, double& uy) {
@@ -90,21 +94,26 @@ __device__ inline void traction_d(double rx, double ry, double nx, double ny, do
 }
 
 __global__ void k_build_Q(double* __restrict__ A, int R, int m, int M, const double* __restrict__ gl_s,
-                          const double* __restrict__ yp, double e1x, double e1y, double e2x, double e2y,
-                          double Cx, double Cy, double mu) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+                          const double* __restrict__ yp, const Cell* __restrict__ cells,
+                          const double* __restrict__ e2v) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x, cidx = blockIdx.y;
     if (idx >= m * M) return;
-    int l = idx % m, p = idx / m;
+    const Cell& cl = cells[cidx];
+    const int l = idx % m, p = idx / m;
+    const double e1x = cl.e1[0], e1y = cl.e1[1], e2x = e2v[2 * cidx], e2y = e2v[2 * cidx + 1];
+    const double Cx = cl.C[0], Cy = cl.C[1];
     double e1[2] = {e1x, e1y}, e2[2] = {e2x, e2y}, nl[2], nd[2];
     wall_normals(e1, e2, nl, nd);
     double s = gl_s[l];
     double xL = Cx - 0.5 * e1x + s * e2x, yL = Cy - 0.5 * e1y + s * e2y;
     double xD = Cx - 0.5 * e2x + s * e1x, yD = Cy - 0.5 * e2y + s * e1y;
-    double px = yp[2 * p], py = yp[2 * p + 1];
-    double c4 = 1.0 / (4.0 * kPi * mu);
+    const double* ypc = yp + (size_t)cidx * 2 * M;
+    double px = ypc[2 * p], py = ypc[2 * p + 1];
+    double c4 = 1.0 / (4.0 * kPi * cl.mu);
+    double* Ac = A + (size_t)cidx * R * 2 * M;
     for (int comp = 0; comp < 2; ++comp) {
         double fx = comp == 0 ? 1.0 : 0.0, fy = comp == 0 ? 0.0 : 1.0;
-        double* col = A + (size_t)(comp * M + p) * R;
+        double* col = Ac + (size_t)(comp * M + p) * R;
         double ua, va, ub, vb;
         // g1: velocity R - L
         stokeslet_d(xL + e1x - px, yL + e1y - py, fx, fy, c4, ua, va);
@@ -150,13 +159,17 @@ __device__ inline double block_sum(double v, double* red) {
     return red[32];
 }
 
-// Householder QR of the stacked R x C matrix A = [Q; lam I] (column-major),
-// in place: the reflector v_k is stored in A[k:, k] (v_k[k] = A[k, k]),
-// beta[k] its scalar, rdiag[k] the diagonal of the triangular factor.
-// One CTA; the first Qrows rows hold Q on entry, the rest are filled here.
-__global__ void k_qr(double* __restrict__ A, int R, int C, int Qrows, double lam_rel,
-                     double* __restrict__ beta, double* __restrict__ rdiag) {
+// Householder QR of the stacked R x C matrix A = [Q; lam I] (column-major) of
+// cell blockIdx.x, in place: the reflector v_k is stored in A[k:, k]
+// (v_k[k] = A[k, k]), beta[k] its scalar, beta[C + k] the diagonal of the
+// triangular factor.  One CTA per cell; the first Qrows rows hold Q on entry,
+// the rest are filled here.
+__global__ void k_qr(double* __restrict__ Aall, int R, int C, int Qrows, double lam_rel,
+                     double* __restrict__ betaall) {
     __shared__ double red[33];
+    double* A = Aall + (size_t)blockIdx.x * R * C;
+    double* beta = betaall + (size_t)blockIdx.x * 2 * C;
+    double* rdiag = beta + C;
     int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     double ss = 0.0;
     for (long long idx = tid; idx < (long long)Qrows * C; idx += nt) {
@@ -200,14 +213,19 @@ __global__ void k_qr(double* __restrict__ A, int R, int C, int Qrows, double lam
     }
 }
 
-// Column c of P = first C rows of R^{-1} H_{C-1} ... H_0 e_c, c < Qrows.
-// P is C x Qrows, stored row-major (P[r * Qrows + c]) so that a warp reading
-// one row of P in the operator application is coalesced.  Dynamic shared
-// memory: R doubles.
-__global__ void k_form_P(const double* __restrict__ A, int R, int C, const double* __restrict__ beta,
-                         const double* __restrict__ rdiag, double* __restrict__ P) {
+// Column c of P = first C rows of R^{-1} H_{C-1} ... H_0 e_c, c < Qrows, for
+// cell blockIdx.y.  P is C x Qrows per cell, stored row-major
+// (P[r * Qrows + c]) so that a warp reading one row of P in the operator
+// application is coalesced.  Dynamic shared memory: R doubles.
+__global__ void k_form_P(const double* __restrict__ Aall, int R, int C, const double* __restrict__ betaall,
+                         double* __restrict__ Pall) {
     extern __shared__ double z[];
     __shared__ double red[33];
+    const int Qrows = gridDim.x;
+    const double* A = Aall + (size_t)blockIdx.y * R * C;
+    const double* beta = betaall + (size_t)blockIdx.y * 2 * C;
+    const double* rdiag = beta + C;
+    double* P = Pall + (size_t)blockIdx.y * C * Qrows;
     int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < R; i += nt) z[i] = (i == c) ? 1.0 : 0.0;
     __syncthreads();
@@ -229,35 +247,33 @@ __global__ void k_form_P(const double* __restrict__ A, int R, int C, const doubl
         }
     }
     __syncthreads();
-    const int Qrows = gridDim.x;
     for (int r = tid; r < C; r += nt) P[(size_t)r * Qrows + c] = z[r];
 }
 
 int build_geometry(bie_ctx* c) {
     int bs = 256, gs = (c->N + bs - 1) / bs;
-    k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->N, c->C[0], c->C[1], c->x, c->y, c->nx,
-                                        c->ny, c->w, c->kap, c->tgt32);
+    k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->node_cell, c->cells, c->N, c->x, c->y, c->nx, c->ny,
+                                        c->w, c->kap, c->tgt32);
     BIE_LAUNCH(c, "k_geometry");
     return BIE_OK;
 }
 
-int build_proxy_fit_to(bie_ctx* c, const double* e2, ProxyFit& f, cudaStream_t st) {
+int build_proxy_fit_to(bie_ctx* c, ProxyFit& f, cudaStream_t st) {
     const int m = c->m, M = c->M;
     const int Qrows = 8 * m, C = 2 * M, R = Qrows + C;
-    const int bs = 128, gs = (m * M + bs - 1) / bs;
-    k_build_Q<<<gs, bs, 0, st>>>(f.A, R, m, M, c->gl_s, c->yp, c->e1[0], c->e1[1], e2[0], e2[1], c->C[0], c->C[1],
-                                 c->mu);
+    const int bs = 128;
+    k_build_Q<<<dim3((m * M + bs - 1) / bs, c->ncell), bs, 0, st>>>(f.A, R, m, M, c->gl_s, c->yp, c->cells, f.e2);
     BIE_LAUNCH(c, "k_build_Q");
-    k_qr<<<1, 1024, 0, st>>>(f.A, R, C, Qrows, c->opts.lam_rel, f.beta, f.beta + C);
+    k_qr<<<c->ncell, 1024, 0, st>>>(f.A, R, C, Qrows, c->opts.lam_rel, f.beta);
     BIE_LAUNCH(c, "k_qr");
-    k_form_P<<<Qrows, 256, R * sizeof(double), st>>>(f.A, R, C, f.beta, f.beta + C, f.P);
+    k_form_P<<<dim3(Qrows, c->ncell), 256, R * sizeof(double), st>>>(f.A, R, C, f.beta, f.P);
     BIE_LAUNCH(c, "k_form_P");
-    return build_wall_table(c, e2, f.wall, st);
+    return build_wall_table(c, f.e2, f.wall, st);
 }
 
 int build_proxy_fit(bie_ctx* c) {
-    ProxyFit f{c->A, c->beta, c->P, c->wall};
-    return build_proxy_fit_to(c, c->e2, f, c->stream);
+    ProxyFit f{c->A, c->beta, c->P, c->wall, c->e2d};
+    return build_proxy_fit_to(c, f, c->stream);
 }
 
 }  // namespace bie

@@ -6,10 +6,18 @@
 // reductions.  The (k+2)-entry Hessenberg column is copied to the host, where
 // the Givens rotations and the final triangular solve run (O(k^2) scalars).
 //
+// Batches: the cells of a context are independent systems.  They run in
+// lockstep -- one operator application per iteration serves every cell --
+// but each cell has its own Arnoldi process: the dot products are reduced per
+// cell (the reduction chunks never straddle two cells), the coefficients of
+// every vector update are per cell, and each cell has its own Hessenberg
+// matrix and convergence test.  A converged cell is switched off: the near
+// sums skip its work items and its Krylov vectors stay zero.
+//
 // BIE_MIXED: iterative refinement -- the residual r = b - A64 x uses the
-// double-precision operator; the correction solves A32 d = r by GMRES on the
+// FP64-class operator; the correction solves A32 d = r by GMRES on the
 // single-precision-pair operator to opts.inner_tol; x += d; repeat until
-// ||r|| / ||b|| <= opts.gmres_tol.
+// ||r_c|| / ||b_c|| <= opts.gmres_tol in every cell c.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -23,64 +31,91 @@ __device__ inline double wsum(double v) {
     return v;
 }
 
-// Multi-vector dot products h[j] = V_j . w (j < nv) in two deterministic
-// passes: block b of kDotChunks sums its slice of the vectors (one warp per
-// vector j at a time), then k_mdot_fin adds the kDotChunks partials of each j.
-constexpr int kDotChunks = 64;
+// Reduction chunks of kDotChunk vector entries that never span two cells.
+int build_dot_chunks(bie_ctx* c) {
+    std::vector<int4> ch;
+    std::vector<int2> cc(c->ncell);
+    for (int ci = 0; ci < c->ncell; ++ci) {
+        const Cell& cl = c->cells_h[ci];
+        const int e0 = 2 * cl.node_off, e1 = 2 * (cl.node_off + cl.n_nodes);
+        cc[ci] = make_int2((int)ch.size(), 0);
+        for (int e = e0; e < e1; e += kDotChunk) ch.push_back(make_int4(ci, e, std::min(e1, e + kDotChunk), 0));
+        cc[ci].y = (int)ch.size() - cc[ci].x;
+    }
+    c->sv.nchunks = (int)ch.size();
+    BIE_CUDA(c, cudaMalloc((void**)&c->sv.chunks, ch.size() * sizeof(int4)));
+    BIE_CUDA(c, cudaMalloc((void**)&c->sv.cell_chunks, cc.size() * sizeof(int2)));
+    BIE_CUDA(c, cudaMalloc((void**)&c->sv.dpart, (size_t)(c->sv.kmax + 2) * ch.size() * sizeof(double)));
+    BIE_CUDA(c, cudaMemcpy(c->sv.chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    BIE_CUDA(c, cudaMemcpy(c->sv.cell_chunks, cc.data(), cc.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    return BIE_OK;
+}
 
+// Multi-vector dot products, per cell, h[j * ncell + cell] = V_j . w over the
+// cell's entries (j < nv), in two deterministic passes: block b sums chunk b
+// of every vector (one warp per vector j at a time), then k_mdot_fin adds the
+// chunks of each (j, cell).
 __global__ void __launch_bounds__(256)
-k_mdot_part(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w, int n,
-            double* __restrict__ part) {
-    const int per = (n + gridDim.x - 1) / gridDim.x;
-    const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+k_mdot_part(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w,
+            const int4* __restrict__ chunks, int nchunks, double* __restrict__ part) {
+    const int4 ch = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = warp; j < nv; j += nw) {
         const double* v = V + (size_t)j * ld;
         double s = 0;
-        for (int i = i0 + lane; i < i1; i += 32) s += v[i] * w[i];
+        for (int i = ch.y + lane; i < ch.z; i += 32) s += v[i] * w[i];
         s = wsum(s);
-        if (lane == 0) part[(size_t)j * gridDim.x + blockIdx.x] = s;
+        if (lane == 0) part[(size_t)j * nchunks + blockIdx.x] = s;
     }
 }
 
-// one warp per vector j: lanes add the partials, then a shuffle tree
-__global__ void k_mdot_fin(const double* __restrict__ part, int nchunk, int nv, double* __restrict__ h) {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (j >= nv) return;
+// one warp per (j, cell): lanes add the cell's chunk partials, then a shuffle tree
+__global__ void k_mdot_fin(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
+                           int ncell, double* __restrict__ h) {
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (idx >= nv * ncell) return;
+    const int j = idx / ncell, cell = idx - j * ncell;
+    const int2 cc = cell_chunks[cell];
     double s = 0;
-    for (int b = lane; b < nchunk; b += 32) s += part[(size_t)j * nchunk + b];
+    for (int b = lane; b < cc.y; b += 32) s += part[(size_t)j * nchunks + cc.x + b];
     s = wsum(s);
-    if (lane == 0) h[j] = s;
+    if (lane == 0) h[idx] = s;
 }
 
-static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, int n, double* h) {
-    k_mdot_part<<<kDotChunks, 256, 0, c->stream>>>(V, ld, nv, w, n, c->sv.dpart);
+static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, double* h) {
+    k_mdot_part<<<c->sv.nchunks, 256, 0, c->stream>>>(V, ld, nv, w, c->sv.chunks, c->sv.nchunks, c->sv.dpart);
     BIE_LAUNCH(c, "k_mdot_part");
-    k_mdot_fin<<<(nv * 32 + 255) / 256, 256, 0, c->stream>>>(c->sv.dpart, kDotChunks, nv, h);
+    k_mdot_fin<<<(nv * c->ncell * 32 + 255) / 256, 256, 0, c->stream>>>(c->sv.dpart, c->sv.nchunks, nv,
+                                                                      c->sv.cell_chunks, c->ncell, h);
     BIE_LAUNCH(c, "k_mdot_fin");
     return BIE_OK;
 }
 
-// w -= sum_j h[j] V_j
-__global__ void k_mupdate(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h,
-                          double* __restrict__ w, int n) {
+// w -= sum_j h[j * ncell + cell] V_j  (cell of each entry from node_cell)
+__global__ void k_mupdate(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int ncell,
+                          const int* __restrict__ node_cell, double* __restrict__ w, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double* hc = h + node_cell[i >> 1];
     double s0 = w[i], s1 = 0, s2 = 0, s3 = 0;
     int j = 0;
     for (; j + 4 <= nv; j += 4) {
-        s0 -= h[j] * V[(size_t)j * ld + i];
-        s1 -= h[j + 1] * V[(size_t)(j + 1) * ld + i];
-        s2 -= h[j + 2] * V[(size_t)(j + 2) * ld + i];
-        s3 -= h[j + 3] * V[(size_t)(j + 3) * ld + i];
+        s0 -= hc[(size_t)j * ncell] * V[(size_t)j * ld + i];
+        s1 -= hc[(size_t)(j + 1) * ncell] * V[(size_t)(j + 1) * ld + i];
+        s2 -= hc[(size_t)(j + 2) * ncell] * V[(size_t)(j + 2) * ld + i];
+        s3 -= hc[(size_t)(j + 3) * ncell] * V[(size_t)(j + 3) * ld + i];
     }
-    for (; j < nv; ++j) s0 -= h[j] * V[(size_t)j * ld + i];
+    for (; j < nv; ++j) s0 -= hc[(size_t)j * ncell] * V[(size_t)j * ld + i];
     w[i] = (s0 + s1) + (s2 + s3);
 }
 
-__global__ void k_scale_copy(const double* __restrict__ src, double a, double* __restrict__ dst, int n) {
+// dst = a[cell] src; a zero factor writes zeros (switched-off cells)
+__global__ void k_scale_copy(const double* __restrict__ src, const double* __restrict__ a,
+                             const int* __restrict__ node_cell, double* __restrict__ dst, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = a * src[i];
+    if (i >= n) return;
+    const double f = a[node_cell[i >> 1]];
+    dst[i] = f == 0.0 ? 0.0 : f * src[i];
 }
 
 __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int n) {
@@ -94,160 +129,272 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
     if (i < n) y[i] = a[i] - b[i];
 }
 
-// x += sum_j c[j] V_j  (c on device)
-__global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ c,
-                          double* __restrict__ x, int n) {
+// x += sum_j coef[j * ncell + cell] V_j
+__global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ coef, int ncell,
+                          const int* __restrict__ node_cell, double* __restrict__ x, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double* cc = coef + node_cell[i >> 1];
     double s = x[i];
-    for (int j = 0; j < nv; ++j) s += c[j] * V[(size_t)j * ld + i];
+    for (int j = 0; j < nv; ++j) s += cc[(size_t)j * ncell] * V[(size_t)j * ld + i];
     x[i] = s;
 }
 
-static int dnorm(bie_ctx* c, const double* v, int n, double* out) {
-    if (int rc = mdot(c, v, 0, 1, v, n, c->sv.red)) return rc;
-    double h;
-    BIE_CUDA(c, cudaMemcpyAsync(&h, c->sv.red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+// node_cell of vector entry i is node_cell[i >> 1]; the kernels above index
+// it that way, so the vectors' entries must be node-major (x, y interleaved).
+
+// Per-cell 2-norms of v.
+static int dnorms(bie_ctx* c, const double* v, std::vector<double>& out) {
+    double* d = c->sv.h + 2 * (size_t)c->ncell * (c->sv.kmax + 2);
+    if (int rc = mdot(c, v, 0, 1, v, d)) return rc;
+    out.resize(c->ncell);
+    BIE_CUDA(c, cudaMemcpyAsync(out.data(), d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
-    *out = std::sqrt(h);
+    for (double& x : out) x = std::sqrt(x);
     return BIE_OK;
 }
 
-// One GMRES cycle on A_prec x = b from the current x (device), stopping when
-// the Arnoldi residual estimate is <= atol or after kmax steps.  r must hold
-// b - A x on entry, with norm beta.  Returns iterations in *it.
-static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, double beta, double atol, int* it,
-                       double* est, int* n_apply) {
-    const int n = 2 * c->N;
+// Switch cells on or off for the near sums (uploads the table if it changed).
+static int set_active(bie_ctx* c, const std::vector<char>& on) {
+    bool changed = false;
+    for (int k = 0; k < c->ncell; ++k)
+        if (c->cells_h[k].active != (int)on[k]) {
+            c->cells_h[k].active = on[k];
+            changed = true;
+        }
+    return changed ? upload_cells(c, c->stream) : BIE_OK;
+}
+
+// One GMRES cycle per cell on A_prec x = b from the current x (device),
+// in lockstep.  r holds b - A x on entry with per-cell norms beta (cells with
+// beta = 0 do not take part).  Cell k stops when its Arnoldi residual
+// estimate is <= atol[k] or after kmax steps; its iteration count goes to
+// it[k] and its estimate to est[k].  *n_apply counts operator applications.
+static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const std::vector<double>& beta,
+                       const std::vector<double>& atol, std::vector<int>& it, std::vector<double>& est,
+                       int* n_apply) {
+    const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
     const int gs64 = (n + 63) / 64;
-    const int kmax = c->sv.kmax;
+    const int kmax = c->sv.kmax, S = kmax + 2;
     const size_t ld = (size_t)n;
     double* V = c->sv.V;
-    std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), g(kmax + 1, 0.0);
-    std::vector<double> hcol(kmax + 2);
-    g[0] = beta;
-    k_scale_copy<<<gs, bs, 0, c->stream>>>(r, 1.0 / beta, V, n);
+    double* h1 = c->sv.h;
+    double* h2 = c->sv.h + (size_t)nc * S;
+    double* hn = c->sv.h + 2 * (size_t)nc * S;  // nc norms
+    double* coef = hn + nc;                      // nc x S coefficients
+    std::vector<std::vector<double>> H(nc);      // packed columns: column k holds k + 1 entries
+    std::vector<std::vector<double>> cs(nc), sn(nc), g(nc);
+    std::vector<char> on(nc, 0);
+    std::vector<double> fac(nc, 0.0);
+    it.assign(nc, 0);
+    est.assign(nc, 0.0);
+    int n_on = 0;
+    for (int k = 0; k < nc; ++k) {
+        if (beta[k] > 0) {
+            on[k] = 1;
+            ++n_on;
+            fac[k] = 1.0 / beta[k];
+            g[k].assign(1, beta[k]);
+        }
+        est[k] = beta[k];
+    }
+    if (!n_on) return BIE_OK;
+    if (int rc = set_active(c, on)) return rc;
+    BIE_CUDA(c, cudaMemcpyAsync(coef, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_scale_copy<<<gs, bs, 0, c->stream>>>(r, coef, c->node_cell, V, n);
     BIE_LAUNCH(c, "k_scale_copy");
+    std::vector<double> hh(2 * (size_t)nc * S + nc), hcol(S);
     int k = 0;
-    double res = beta;
-    for (k = 0; k < kmax; ++k) {
+    for (k = 0; k < kmax && n_on > 0; ++k) {
         double* w = c->sv.w;
         int rc = apply_device(c, V + (size_t)k * ld, w, prec);
         if (rc) return rc;
         ++*n_apply;
-        // CGS2
-        double* h1 = c->sv.h;
-        double* h2 = c->sv.h + (kmax + 2);
-        if ((rc = mdot(c, V, ld, k + 1, w, n, h1))) return rc;
-        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h1, w, n);
+        // CGS2, per cell
+        if ((rc = mdot(c, V, ld, k + 1, w, h1))) return rc;
+        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h1, nc, c->node_cell, w, n);
         BIE_LAUNCH(c, "k_mupdate");
-        if ((rc = mdot(c, V, ld, k + 1, w, n, h2))) return rc;
-        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h2, w, n);
+        if ((rc = mdot(c, V, ld, k + 1, w, h2))) return rc;
+        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h2, nc, c->node_cell, w, n);
         BIE_LAUNCH(c, "k_mupdate");
-        if ((rc = mdot(c, w, 0, 1, w, n, h2 + (kmax + 2)))) return rc;
-        std::vector<double> hh(2 * (kmax + 2) + 1);
-        BIE_CUDA(c, cudaMemcpyAsync(hh.data(), h1, (2 * (kmax + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+        if ((rc = mdot(c, w, 0, 1, w, hn))) return rc;
+        const size_t len = (size_t)(k + 1) * nc;
+        BIE_CUDA(c, cudaMemcpyAsync(hh.data(), h1, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(hh.data() + (size_t)nc * S, h2, len * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(hh.data() + 2 * (size_t)nc * S, hn, nc * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
         BIE_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (int j = 0; j <= k; ++j) hcol[j] = hh[j] + hh[(kmax + 2) + j];
-        double hk1 = std::sqrt(hh[2 * (kmax + 2)]);
-        if (!std::isfinite(hk1)) return fail(c, BIE_ENUMERIC, "non-finite Krylov vector in GMRES");
-        hcol[k + 1] = hk1;
-        if (hk1 > 0) {
-            k_scale_copy<<<gs, bs, 0, c->stream>>>(w, 1.0 / hk1, V + (size_t)(k + 1) * ld, n);
+        bool switched = false;
+        for (int q = 0; q < nc; ++q) {
+            if (!on[q]) {
+                fac[q] = 0.0;
+                continue;
+            }
+            for (int j = 0; j <= k; ++j) hcol[j] = hh[(size_t)j * nc + q] + hh[(size_t)nc * S + (size_t)j * nc + q];
+            const double hk1 = std::sqrt(hh[2 * (size_t)nc * S + q]);
+            if (!std::isfinite(hk1)) return fail(c, BIE_ENUMERIC, "non-finite Krylov vector in GMRES");
+            hcol[k + 1] = hk1;
+            fac[q] = hk1 > 0 ? 1.0 / hk1 : 0.0;
+            // Givens
+            for (int j = 0; j < k; ++j) {
+                const double a = cs[q][j] * hcol[j] + sn[q][j] * hcol[j + 1];
+                hcol[j + 1] = -sn[q][j] * hcol[j] + cs[q][j] * hcol[j + 1];
+                hcol[j] = a;
+            }
+            const double den = std::hypot(hcol[k], hcol[k + 1]);
+            cs[q].push_back(hcol[k] / den);
+            sn[q].push_back(hcol[k + 1] / den);
+            hcol[k] = den;
+            g[q].push_back(-sn[q][k] * g[q][k]);
+            g[q][k] = cs[q][k] * g[q][k];
+            H[q].insert(H[q].end(), hcol.begin(), hcol.begin() + k + 1);
+            it[q] = k + 1;
+            est[q] = std::fabs(g[q][k + 1]);
+            if (est[q] <= atol[q] || hk1 == 0.0) {
+                on[q] = 0;
+                fac[q] = 0.0;
+                --n_on;
+                switched = true;
+            }
+        }
+        if (n_on > 0) {
+            // next basis vector, zero in switched-off cells
+            BIE_CUDA(c, cudaMemcpyAsync(coef, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            k_scale_copy<<<gs, bs, 0, c->stream>>>(w, coef, c->node_cell, V + (size_t)(k + 1) * ld, n);
             BIE_LAUNCH(c, "k_scale_copy");
-        }
-        // Givens
-        for (int j = 0; j < k; ++j) {
-            double a = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
-            hcol[j + 1] = -sn[j] * hcol[j] + cs[j] * hcol[j + 1];
-            hcol[j] = a;
-        }
-        double den = std::hypot(hcol[k], hcol[k + 1]);
-        cs[k] = hcol[k] / den;
-        sn[k] = hcol[k + 1] / den;
-        hcol[k] = den;
-        hcol[k + 1] = 0.0;
-        g[k + 1] = -sn[k] * g[k];
-        g[k] = cs[k] * g[k];
-        for (int j = 0; j <= k; ++j) H[(size_t)j * kmax + k] = hcol[j];
-        res = std::fabs(g[k + 1]);
-        if (res <= atol || hk1 == 0.0) {
-            ++k;
-            break;
+            if (switched)
+                if ((rc = set_active(c, on))) return rc;
         }
     }
-    int kk = std::min(k, kmax);
-    std::vector<double> yv(kk);
-    for (int i = kk - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int j = i + 1; j < kk; ++j) s -= H[(size_t)i * kmax + j] * yv[j];
-        yv[i] = s / H[(size_t)i * kmax + i];
+    // per cell: back substitution with its own Krylov dimension
+    int kk = 0;
+    for (int q = 0; q < nc; ++q) kk = std::max(kk, it[q]);
+    std::vector<double> cf((size_t)kk * nc, 0.0);
+    for (int q = 0; q < nc; ++q) {
+        const int kq = it[q];
+        // column j of H[q] starts at j (j + 1) / 2
+        auto Hq = [&](int i, int j) { return H[q][(size_t)j * (j + 1) / 2 + i]; };
+        std::vector<double> yv(kq);
+        for (int i = kq - 1; i >= 0; --i) {
+            double s = g[q][i];
+            for (int j = i + 1; j < kq; ++j) s -= Hq(i, j) * yv[j];
+            yv[i] = s / Hq(i, i);
+        }
+        for (int j = 0; j < kq; ++j) cf[(size_t)j * nc + q] = yv[j];
     }
-    BIE_CUDA(c, cudaMemcpyAsync(c->sv.h, yv.data(), kk * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    k_combine<<<gs, bs, 0, c->stream>>>(V, ld, kk, c->sv.h, x, n);
-    BIE_LAUNCH(c, "k_combine");
-    *it = kk;
-    *est = res;
+    if (kk > 0) {
+        BIE_CUDA(c, cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        k_combine<<<gs, bs, 0, c->stream>>>(V, ld, kk, coef, nc, c->node_cell, x, n);
+        BIE_LAUNCH(c, "k_combine");
+    }
     return BIE_OK;
 }
 
 int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info) {
-    const int n = 2 * c->N;
+    const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
     bie_solve_info inf{};
-    double bnorm;
-    int rc = dnorm(c, b, n, &bnorm);
+    std::vector<bie_solve_info> ci(nc, bie_solve_info{});
+    std::vector<char> all_on(nc, 1);
+    int rc = set_active(c, all_on);
     if (rc) return rc;
-    if (!std::isfinite(bnorm)) return fail(c, BIE_ENUMERIC, "non-finite right-hand side");
-    if (bnorm == 0.0) {
-        BIE_CUDA(c, cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
-        if (info) *info = inf;
-        return BIE_OK;
-    }
+    std::vector<double> bnorm;
+    if ((rc = dnorms(c, b, bnorm))) return rc;
+    for (double v : bnorm)
+        if (!std::isfinite(v)) return fail(c, BIE_ENUMERIC, "non-finite right-hand side");
     if (!use_guess) BIE_CUDA(c, cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
     const double tol = c->opts.gmres_tol;
     const bool mixed = c->opts.precision == BIE_MIXED;
     const int max_outer = mixed ? c->opts.max_refine : 20;
-    double rel = 0;
+    // cells still iterating: a zero right-hand side has the solution 0
+    std::vector<char> todo(nc, 1);
+    for (int q = 0; q < nc; ++q)
+        if (bnorm[q] == 0.0) {
+            todo[q] = 0;
+            const Cell& cl = c->cells_h[q];
+            BIE_CUDA(c, cudaMemsetAsync(x + 2 * (size_t)cl.node_off, 0, 2 * (size_t)cl.n_nodes * sizeof(double),
+                                        c->stream));
+        }
+    std::vector<double> rn, beta(nc), atol(nc), est;
+    std::vector<int> its;
     for (int outer = 0; outer <= max_outer; ++outer) {
-        // FP64-class residual (native double, or double-float when mixed)
+        bool any = false;
+        for (char t : todo) any |= t != 0;
+        if (!any) break;
+        // FP64-class residual (native double, or double-float when mixed) of
+        // the cells still iterating
+        if ((rc = set_active(c, todo))) return rc;
         rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : BIE_FP64);
         if (rc) return rc;
         ++inf.applies64;
         k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);
         BIE_LAUNCH(c, "k_sub");
-        double rn;
-        rc = dnorm(c, c->sv.r, n, &rn);
-        if (rc) return rc;
-        if (!std::isfinite(rn)) return fail(c, BIE_ENUMERIC, "non-finite residual");
-        rel = rn / bnorm;
-        if (rel <= tol || outer == max_outer) break;
-        int it = 0, napply = 0;
-        double est;
+        if ((rc = dnorms(c, c->sv.r, rn))) return rc;
+        bool left = false;
+        for (int q = 0; q < nc; ++q) {
+            beta[q] = 0.0;
+            if (!todo[q]) continue;
+            if (!std::isfinite(rn[q])) return fail(c, BIE_ENUMERIC, "non-finite residual");
+            ci[q].rel_residual = rn[q] / bnorm[q];
+            ++ci[q].applies64;
+            if (ci[q].rel_residual <= tol) {
+                todo[q] = 0;
+                continue;
+            }
+            left = true;
+            beta[q] = rn[q];
+            atol[q] = mixed ? std::max(c->opts.inner_tol * rn[q], 0.5 * tol * bnorm[q]) : 0.5 * tol * bnorm[q];
+        }
+        if (!left || outer == max_outer) break;
+        int napply = 0;
         if (mixed) {
             BIE_CUDA(c, cudaMemsetAsync(c->sv.d, 0, n * sizeof(double), c->stream));
-            double atol = std::max(c->opts.inner_tol * rn, 0.5 * tol * bnorm);
-            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, rn, atol, &it, &est, &napply);
+            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply);
             if (rc) return rc;
             k_axpy<<<gs, bs, 0, c->stream>>>(1.0, c->sv.d, x, n);
             BIE_LAUNCH(c, "k_axpy");
             inf.applies32 += napply;
         } else {
-            rc = gmres_cycle(c, BIE_FP64, x, c->sv.r, rn, 0.5 * tol * bnorm, &it, &est, &napply);
+            rc = gmres_cycle(c, BIE_FP64, x, c->sv.r, beta, atol, its, est, &napply);
             if (rc) return rc;
             inf.applies64 += napply;
         }
-        inf.iterations += it;
+        int kmax_it = 0;
+        for (int q = 0; q < nc; ++q) {
+            if (beta[q] == 0.0) continue;
+            ci[q].iterations += its[q];
+            ci[q].refinements += 1;
+            if (mixed) ci[q].applies32 += its[q];
+            else ci[q].applies64 += its[q];
+            kmax_it = std::max(kmax_it, its[q]);
+        }
+        inf.iterations += kmax_it;
         inf.refinements += 1;
     }
-    inf.rel_residual = rel;
+    if ((rc = set_active(c, all_on))) return rc;
+    double worst = 0;
+    int worst_cell = 0;
+    for (int q = 0; q < nc; ++q)
+        if (ci[q].rel_residual > worst) {
+            worst = ci[q].rel_residual;
+            worst_cell = q;
+        }
+    inf.rel_residual = worst;
+    c->sv.cell_info = ci;
     if (info) *info = inf;
-    if (rel > tol) {
-        char msg[160];
-        snprintf(msg, sizeof msg, "solver stopped above tolerance: relative residual %.3e after %d sweeps, %d iterations",
-                 rel, inf.refinements, inf.iterations);
+    if (worst > tol) {
+        char msg[200];
+        if (nc > 1)
+            snprintf(msg, sizeof msg,
+                     "solver stopped above tolerance: relative residual %.3e in cell %d after %d sweeps, %d "
+                     "iterations",
+                     worst, worst_cell, ci[worst_cell].refinements, ci[worst_cell].iterations);
+        else
+            snprintf(msg, sizeof msg,
+                     "solver stopped above tolerance: relative residual %.3e after %d sweeps, %d iterations", worst,
+                     inf.refinements, inf.iterations);
         return fail(c, BIE_ENOCONV, msg);
     }
     return BIE_OK;
