@@ -34,7 +34,8 @@ static void free_all(bie_ctx* c) {
                     c->tgt32, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->ws.vpart, c->sv.V,
-                    c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.dpart, c->sv.chunks,
+                    c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.ticket, c->sv.dpart,
+                    c->sv.chunks,
                     c->sv.cell_chunks, c->sv.sigma_prev, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
                     c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
                     c->near[1].items, c->near[2].items};
@@ -44,6 +45,11 @@ static void free_all(bie_ctx* c) {
         if (e) cudaEventDestroy(e);
     c->ev_pool.clear();
     if (c->next_done) cudaEventDestroy(c->next_done);
+    for (auto e : c->sv.ev)
+        if (e) cudaEventDestroy(e);
+    if (c->sv.pinned) cudaFreeHost(c->sv.pinned);
+    if (c->cells_pinned) cudaFreeHost(c->cells_pinned);
+    if (c->cells_ev) cudaEventDestroy(c->cells_ev);
     if (c->side) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
@@ -69,11 +75,16 @@ void cell_set_lattice(Cell& cl, const double* e1, const double* e2) {
     cl.l2 = std::sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
 }
 
-// Stream-ordered upload of the host mirror of the cell table (the pageable
-// source is staged by the driver before the call returns).
+// Stream-ordered upload of the host mirror of the cell table through a
+// page-locked staging copy (asynchronous: the host does not wait for the
+// stream).  The staging copy is rewritten only after the previous upload has
+// left it.
 int upload_cells(bie_ctx* c, cudaStream_t st) {
-    BIE_CUDA(c, cudaMemcpyAsync(c->cells, c->cells_h.data(), c->cells_h.size() * sizeof(Cell), cudaMemcpyHostToDevice,
+    BIE_CUDA(c, cudaEventSynchronize(c->cells_ev));
+    std::memcpy(c->cells_pinned, c->cells_h.data(), c->cells_h.size() * sizeof(Cell));
+    BIE_CUDA(c, cudaMemcpyAsync(c->cells, c->cells_pinned, c->cells_h.size() * sizeof(Cell), cudaMemcpyHostToDevice,
                                 st));
+    BIE_CUDA(c, cudaEventRecord(c->cells_ev, st));
     return BIE_OK;
 }
 
@@ -307,6 +318,8 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     const int kk = c->sv.kmax;
     rc = 0;
     rc = rc ? rc : dalloc(c, &c->cells, nc);
+    if (!rc) rc = cu(cudaMallocHost((void**)&c->cells_pinned, nc * sizeof(Cell)), "cudaMallocHost");
+    if (!rc) rc = cu(cudaEventCreateWithFlags(&c->cells_ev, cudaEventDisableTiming), "cudaEventCreate");
     rc = rc ? rc : dalloc(c, &c->node_cell, n);
     rc = rc ? rc : dalloc(c, &c->body_cell, nbs);
     rc = rc ? rc : dalloc(c, &c->x, n);
@@ -350,7 +363,16 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->sv.x, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.b, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.d, 2 * (size_t)n);
-    rc = rc ? rc : dalloc(c, &c->sv.h, (3 * (size_t)(kk + 2) + 1) * nc);
+    {
+        const size_t slot = (2 * (size_t)(kk + 1) + 1) * nc;
+        rc = rc ? rc : dalloc(c, &c->sv.h, 2 * slot + (size_t)kk * nc);
+        rc = rc ? rc : dalloc(c, &c->sv.fac, 2 * nc);
+        rc = rc ? rc : dalloc(c, &c->sv.ticket, 1);
+        if (!rc) rc = cu(cudaMallocHost((void**)&c->sv.pinned, 2 * slot * sizeof(double)), "cudaMallocHost");
+        if (!rc) rc = cu(cudaMemset(c->sv.ticket, 0, sizeof(unsigned int)), "cudaMemset");
+        for (int e = 0; e < 2 && !rc; ++e)
+            rc = cu(cudaEventCreateWithFlags(&c->sv.ev[e], cudaEventDisableTiming), "cudaEventCreate");
+    }
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
     {
         int maxn = 0;

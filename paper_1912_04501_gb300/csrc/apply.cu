@@ -12,7 +12,9 @@
 //                   cancellation (Sec. 6.2 step 2), per (wall point, split, cell)
 //   k_xi            g~ = g0 - g, xi = P g~ (Sec. 6.2 step 3), per (row, cell)
 //   k_correct       T = sum of partials + on-curve diagonal + proxy traction (step 4)
-//   k_close_apply   close-evaluation correction (Sec. 6.3)
+//   k_close_apply   close-evaluation correction (Sec. 6.3); on the single-
+//                   precision path also the own-body and close pairs redone
+//                   with positions differenced in double (k_close_apply32)
 //   k_finish        alpha = -T_0 . n_0 per cell;  y = sigma/2 + T + alpha n + L sigma
 #include <algorithm>
 #include <cmath>
@@ -43,11 +45,6 @@ __device__ inline double block_sum_d(double v, double* red) {
     return r;
 }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // Knuth's TwoSum: s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -174,13 +171,9 @@ k_near32(const int4* __restrict__ items, const Cell* __restrict__ cells, const f
             for (int t = 0; t < TPT; ++t) {
 #pragma unroll
                 for (int im = 0; im < 9; ++im) {
-                    float dx = px[t][im] - s.x;
-                    float dy = py[t][im] - s.y;
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
-                    float rn = fmaf(dy, nyv[t], dx * nxv[t]);
-                    float rq = fmaf(dy, s.w, dx * s.z);
-                    float inv = rcp_approx(r2);
-                    float cc = (rn * inv) * (rq * inv);
+                    const float dx = px[t][im] - s.x;
+                    const float dy = py[t][im] - s.y;
+                    const float cc = pair32(dx, dy, nxv[t], nyv[t], s.z, s.w);
                     ax[t][im / 3] = fmaf(cc, dx, ax[t][im / 3]);
                     ay[t][im / 3] = fmaf(cc, dy, ay[t][im / 3]);
                 }
@@ -849,7 +842,7 @@ static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precisi
                                                                c->cells, sg, c->x, c->y, c->nx, c->ny, c->w, c->kap,
                                                                c->yp, ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
-    if (int rc = close_apply(c, sigma, ws.T)) return rc;
+    if (int rc = close_apply(c, sigma, ws.T, f32 ? ws.src32 : nullptr)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
                                        c->cells, reinterpret_cast<double2*>(yout));
     BIE_LAUNCH(c, "k_finish");

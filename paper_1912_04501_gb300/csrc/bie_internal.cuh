@@ -129,7 +129,12 @@ struct Solver {
     double* x = nullptr;     // 2N current solution
     double* b = nullptr;     // 2N right-hand side
     double* d = nullptr;     // 2N correction (mixed)
-    double* h = nullptr;     // (3 (kmax + 2) + 1) x ncell dot products, norms, coefficients
+    double* h = nullptr;     // 2 slots of (2 (kmax + 1) + 1) x ncell Hessenberg entries, then
+                             // kmax x ncell combination coefficients
+    double* pinned = nullptr;  // host (page-locked): 2 slots, as on the device
+    double* fac = nullptr;   // 2 x ncell: normalisation factors, then per-cell norms
+    unsigned int* ticket = nullptr;  // last-block counter of k_ortho (zero between launches)
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // slot k % 2 copied to the host
     double* dpart = nullptr; // (kmax + 2) x nchunks partial dot products
     int4* chunks = nullptr;  // nchunks: (cell, first entry, end entry, 0)
     int2* cell_chunks = nullptr;  // ncell: (first chunk, chunk count)
@@ -158,6 +163,8 @@ struct bie_ctx {
     std::vector<bie::Cell> cells_h;        // host mirror of the cell table
     std::vector<double> e2_0;              // 2 x ncell lattice vectors e2 at t = 0
     bie::Cell* cells = nullptr;            // device cell table
+    bie::Cell* cells_pinned = nullptr;     // page-locked staging copy for uploads
+    cudaEvent_t cells_ev = nullptr;        // the last upload has read the staging copy
     int* node_cell = nullptr;              // N
     int* body_cell = nullptr;              // nb
     // device geometry
@@ -229,7 +236,10 @@ void gauss_legendre_half(int m, std::vector<double>& s);
 // close.cu ------------------------------------------------------------------
 int build_close(bie_ctx* c);                               // per geometry
 int build_dirichlet_tables(bie_ctx* c);                    // once per context
-int close_apply(bie_ctx* c, const double* sigma, double* T);  // T += C sigma
+// T += C sigma; with src32 (the single-precision path's packed sources) the
+// own-body and close pairs of the single-precision near sum are also redone
+// with positions differenced in double precision
+int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32);
 
 // apply.cu ------------------------------------------------------------------
 // near-sum work items (and partial offsets) for the current cell sizes
@@ -249,6 +259,26 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
 int build_dot_chunks(bie_ctx* c);
 
 // small device math shared by the kernels --------------------------------------
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// The single-precision pair coefficient of the near sum (Eq. Gt without its
+// -1/pi): c = (r.n / r^2) (r.q / r^2) for r = (dx, dy), target normal n and
+// source strength q; the pair's term is c r.  The 1e-30 floor makes the
+// zero-distance self pair contribute 0.  k_near32 and the mixed-precision
+// close pass both evaluate pairs through this function, so that the second
+// can recompute the first's terms bit for bit.
+__device__ __forceinline__ float pair32(float dx, float dy, float nx, float ny, float qx, float qy) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
+    const float rn = fmaf(dy, ny, dx * nx);
+    const float rq = fmaf(dy, qy, dx * qx);
+    const float inv = rcp_approx(r2);
+    return (rn * inv) * (rq * inv);
+}
+
 __host__ __device__ inline void wall_normals(const double* e1, const double* e2, double* nl, double* nd) {
     double l2 = sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
     nl[0] = e2[1] / l2;

@@ -390,12 +390,89 @@ int build_dirichlet_tables(bie_ctx* c) {
     return BIE_OK;
 }
 
-int close_apply(bie_ctx* c, const double* sigma, double* T) {
-    if (c->cl.npairs == 0) return BIE_OK;
+// Single-precision path, one warp per target.  k_near32 sums every pair
+// from single-precision positions relative to the cell centre, whose rounding
+// (~1e-7 of the cell size) is a large relative error in r = x_i - y_j for
+// nodes close to the target, and larger still in r . n_i for the nearly
+// tangent r between neighbours on one curve.  For the target's own body
+// (unshifted) and for each of its close (body, image) pairs, the single-
+// precision terms are recomputed bit for bit (same inputs, same pair32) and
+// replaced by the same terms with r differenced in double precision and then
+// rounded; the close-evaluation block is applied as in k_close_apply.
+__global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
+                                const long long* __restrict__ blk_off, const double* __restrict__ blocks,
+                                int use_pairs, const double* __restrict__ body, const int* __restrict__ owner,
+                                const double2* __restrict__ sigma, int N, const float4* __restrict__ tgt32,
+                                const float4* __restrict__ src32, const double* __restrict__ x,
+                                const double* __restrict__ y, const int* __restrict__ node_cell,
+                                const Cell* __restrict__ cells, double2* __restrict__ T) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const Cell& cl = cells[node_cell[i]];
+    const float4 tv = tgt32[i];
+    const double X = x[i], Y = y[i];
+    float fx = 0.f, fy = 0.f;  // sum of (double-differenced term - single-precision term)
+    auto redo = [&](int j, int im) {
+        const float4 s = src32[j];
+        const float dx = (tv.x - cl.sxf[im]) - s.x;
+        const float dy = (tv.y - cl.syf[im]) - s.y;
+        const float c0 = pair32(dx, dy, tv.z, tv.w, s.z, s.w);
+        const float rx = (float)((X - cl.sx[im]) - x[j]);
+        const float ry = (float)((Y - cl.sy[im]) - y[j]);
+        const float c1 = pair32(rx, ry, tv.z, tv.w, s.z, s.w);
+        fx += c1 * rx - c0 * dx;
+        fy += c1 * ry - c0 * dy;
+    };
+    {
+        const int b = owner[i];
+        const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+        for (int k = lane; k < nbn; k += 32)
+            if (off + k != i) redo(off + k, 4);
+    }
+    double tx = 0, ty = 0;
+    if (use_pairs) {
+        const int p0 = pair_base[i], p1 = pair_base[i + 1];
+        for (int p = p0; p < p1; ++p) {
+            const int4 pr = pairs[p];
+            const int b = pr.y, im = pr.z;
+            const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+            const double* C = blocks + blk_off[p];
+            for (int k = lane; k < nbn; k += 32) {
+                redo(off + k, im);
+                const double2 s = sigma[off + k];
+                const double A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
+                tx = fma(A, s.x, fma(B, s.y, tx));
+                ty = fma(B, s.x, fma(D, s.y, ty));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+    if (lane == 0) {
+        const double c = -1.0 / kPi;
+        const double2 t = T[i];
+        T[i] = make_double2(t.x + tx + c * (double)fx, t.y + ty + c * (double)fy);
+    }
+}
+
+int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32) {
     const int N = c->N;
-    long long threads = 32LL * N;
-    int bs = 256;
-    int gs = (int)((threads + bs - 1) / bs);
+    const long long threads = 32LL * N;
+    const int bs = 256;
+    const int gs = (int)((threads + bs - 1) / bs);
+    if (src32) {
+        k_close_apply32<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks,
+                                                 c->cl.npairs > 0 ? 1 : 0, c->body, c->owner,
+                                                 reinterpret_cast<const double2*>(sigma), N, c->tgt32, src32, c->x,
+                                                 c->y, c->node_cell, c->cells, reinterpret_cast<double2*>(T));
+        BIE_LAUNCH(c, "k_close_apply32");
+        return BIE_OK;
+    }
+    if (c->cl.npairs == 0) return BIE_OK;
     k_close_apply<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->body,
                                            reinterpret_cast<const double2*>(sigma), N,
                                            reinterpret_cast<double2*>(T));

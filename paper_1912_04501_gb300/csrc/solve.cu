@@ -91,22 +91,66 @@ static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w,
     return BIE_OK;
 }
 
-// w -= sum_j h[j * ncell + cell] V_j  (cell of each entry from node_cell)
-__global__ void k_mupdate(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int ncell,
-                          const int* __restrict__ node_cell, double* __restrict__ w, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double* hc = h + node_cell[i >> 1];
-    double s0 = w[i], s1 = 0, s2 = 0, s3 = 0;
-    int j = 0;
-    for (; j + 4 <= nv; j += 4) {
-        s0 -= hc[(size_t)j * ncell] * V[(size_t)j * ld + i];
-        s1 -= hc[(size_t)(j + 1) * ncell] * V[(size_t)(j + 1) * ld + i];
-        s2 -= hc[(size_t)(j + 2) * ncell] * V[(size_t)(j + 2) * ld + i];
-        s3 -= hc[(size_t)(j + 3) * ncell] * V[(size_t)(j + 3) * ld + i];
+// One fused step of classical Gram-Schmidt for every cell at once; block b
+// owns reduction chunk b (kDotChunk entries of one cell).
+//   MODE 0:  h[j, cell] = V_j . w                         (j < nv)
+//   MODE 1:  w -= sum_j hprev[j, cell] V_j;  h[j, cell] = V_j . w
+//   MODE 2:  w -= sum_j hprev[j, cell] V_j;  h[cell] = w . w, and
+//            fac[cell] = 1 / sqrt(h[cell]) for active cells (else 0)
+// h[j, cell] lives at h[j * ncell + cell].  Each block writes its partial dot
+// products; the last block to finish (atomic ticket, after a fence) adds the
+// partials of each (j, cell) in chunk order, so the result does not depend
+// on the block schedule.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_ortho(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, const double* __restrict__ hprev,
+        const int4* __restrict__ chunks, int nchunks, const int2* __restrict__ cell_chunks, int ncell,
+        double* __restrict__ part, double* __restrict__ h, unsigned int* __restrict__ ticket,
+        const Cell* __restrict__ cells, double* __restrict__ fac) {
+    __shared__ double sw[kDotChunk];
+    __shared__ bool last;
+    const int4 ch = chunks[blockIdx.x];
+    const int q = ch.x, e0 = ch.y, len = ch.z - ch.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        double v = w[e0 + t];
+        if (MODE > 0) {
+            double s0 = v, s1 = 0;
+            int j = 0;
+            for (; j + 2 <= nv; j += 2) {
+                s0 -= hprev[(size_t)j * ncell + q] * V[(size_t)j * ld + e0 + t];
+                s1 -= hprev[(size_t)(j + 1) * ncell + q] * V[(size_t)(j + 1) * ld + e0 + t];
+            }
+            if (j < nv) s0 -= hprev[(size_t)j * ncell + q] * V[(size_t)j * ld + e0 + t];
+            v = s0 + s1;
+            w[e0 + t] = v;
+        }
+        sw[t] = v;
     }
-    for (; j < nv; ++j) s0 -= hc[(size_t)j * ncell] * V[(size_t)j * ld + i];
-    w[i] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    const int nd = MODE == 2 ? 1 : nv;
+    for (int j = warp; j < nd; j += nw) {
+        const double* vj = V + (size_t)j * ld + e0;
+        double s = 0;
+        for (int t = lane; t < len; t += 32) s += (MODE == 2 ? sw[t] : vj[t]) * sw[t];
+        s = wsum(s);
+        if (lane == 0) part[(size_t)j * nchunks + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int item = threadIdx.x; item < nd * ncell; item += blockDim.x) {
+        const int j = item / ncell, cq = item - j * ncell;
+        const int2 cc = cell_chunks[cq];
+        double s = 0;
+        for (int b = 0; b < cc.y; ++b) s += __ldcg(part + (size_t)j * nchunks + cc.x + b);
+        h[item] = s;
+        if (MODE == 2) fac[cq] = (cells[cq].active && s > 0) ? 1.0 / sqrt(s) : 0.0;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // dst = a[cell] src; a zero factor writes zeros (switched-off cells)
@@ -136,7 +180,10 @@ __global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const
     if (i >= n) return;
     const double* cc = coef + node_cell[i >> 1];
     double s = x[i];
-    for (int j = 0; j < nv; ++j) s += cc[(size_t)j * ncell] * V[(size_t)j * ld + i];
+    for (int j = 0; j < nv; ++j) {
+        const double a = cc[(size_t)j * ncell];
+        if (a != 0.0) s += a * V[(size_t)j * ld + i];  // vectors past a cell's own dimension are not read
+    }
     x[i] = s;
 }
 
@@ -145,7 +192,7 @@ __global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const
 
 // Per-cell 2-norms of v.
 static int dnorms(bie_ctx* c, const double* v, std::vector<double>& out) {
-    double* d = c->sv.h + 2 * (size_t)c->ncell * (c->sv.kmax + 2);
+    double* d = c->sv.fac + c->ncell;  // ncell scratch after the normalisation factors
     if (int rc = mdot(c, v, 0, 1, v, d)) return rc;
     out.resize(c->ncell);
     BIE_CUDA(c, cudaMemcpyAsync(out.data(), d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -170,23 +217,30 @@ static int set_active(bie_ctx* c, const std::vector<char>& on) {
 // beta = 0 do not take part).  Cell k stops when its Arnoldi residual
 // estimate is <= atol[k] or after kmax steps; its iteration count goes to
 // it[k] and its estimate to est[k].  *n_apply counts operator applications.
+//
+// Pipelining: iteration k+1 (operator application, CGS2, normalisation of
+// the next basis vector with the norm computed on the device) is enqueued
+// before the host waits for iteration k's Hessenberg column, so the host's
+// Givens rotations and convergence test overlap the GPU's next iteration.
+// When the last cell converges at iteration k, iteration k+1 has already
+// run and is discarded; a cell that converges is switched off from
+// iteration k+2 on.
 static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const std::vector<double>& beta,
                        const std::vector<double>& atol, std::vector<int>& it, std::vector<double>& est,
                        int* n_apply) {
     const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
-    const int gs64 = (n + 63) / 64;
-    const int kmax = c->sv.kmax, S = kmax + 2;
+    const int kmax = c->sv.kmax;
     const size_t ld = (size_t)n;
+    const size_t slot = (2 * (size_t)(kmax + 1) + 1) * nc;  // h1, h2, norm of one iteration
     double* V = c->sv.V;
-    double* h1 = c->sv.h;
-    double* h2 = c->sv.h + (size_t)nc * S;
-    double* hn = c->sv.h + 2 * (size_t)nc * S;  // nc norms
-    double* coef = hn + nc;                      // nc x S coefficients
-    std::vector<std::vector<double>> H(nc);      // packed columns: column k holds k + 1 entries
+    double* w = c->sv.w;
+    double* fac_d = c->sv.fac;
+    double* coef = c->sv.h + 2 * slot;  // kmax x nc combination coefficients
+    std::vector<std::vector<double>> H(nc);  // packed columns: column k holds k + 1 entries
     std::vector<std::vector<double>> cs(nc), sn(nc), g(nc);
     std::vector<char> on(nc, 0);
-    std::vector<double> fac(nc, 0.0);
+    std::vector<double> fac(nc, 0.0), hcol(kmax + 2);
     it.assign(nc, 0);
     est.assign(nc, 0.0);
     int n_on = 0;
@@ -201,42 +255,51 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
     }
     if (!n_on) return BIE_OK;
     if (int rc = set_active(c, on)) return rc;
-    BIE_CUDA(c, cudaMemcpyAsync(coef, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    k_scale_copy<<<gs, bs, 0, c->stream>>>(r, coef, c->node_cell, V, n);
+    BIE_CUDA(c, cudaMemcpyAsync(fac_d, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_scale_copy<<<gs, bs, 0, c->stream>>>(r, fac_d, c->node_cell, V, n);
     BIE_LAUNCH(c, "k_scale_copy");
-    std::vector<double> hh(2 * (size_t)nc * S + nc), hcol(S);
-    int k = 0;
-    for (k = 0; k < kmax && n_on > 0; ++k) {
-        double* w = c->sv.w;
-        int rc = apply_device(c, V + (size_t)k * ld, w, prec);
-        if (rc) return rc;
+    // enqueue iteration k: w = A V_k, CGS2, V_{k+1} = w / |w| per cell, and
+    // the Hessenberg entries to the pinned host slot k % 2
+    auto enqueue = [&](int k) -> int {
+        if (int rc = apply_device(c, V + (size_t)k * ld, w, prec)) return rc;
         ++*n_apply;
-        // CGS2, per cell
-        if ((rc = mdot(c, V, ld, k + 1, w, h1))) return rc;
-        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h1, nc, c->node_cell, w, n);
-        BIE_LAUNCH(c, "k_mupdate");
-        if ((rc = mdot(c, V, ld, k + 1, w, h2))) return rc;
-        k_mupdate<<<gs64, 64, 0, c->stream>>>(V, ld, k + 1, h2, nc, c->node_cell, w, n);
-        BIE_LAUNCH(c, "k_mupdate");
-        if ((rc = mdot(c, w, 0, 1, w, hn))) return rc;
-        const size_t len = (size_t)(k + 1) * nc;
-        BIE_CUDA(c, cudaMemcpyAsync(hh.data(), h1, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        BIE_CUDA(c, cudaMemcpyAsync(hh.data() + (size_t)nc * S, h2, len * sizeof(double), cudaMemcpyDeviceToHost,
+        double* hb = c->sv.h + (size_t)(k & 1) * slot;
+        double* h1 = hb;
+        double* h2 = hb + (size_t)(k + 1) * nc;
+        double* hn = hb + 2 * (size_t)(k + 1) * nc;
+        const int nb = c->sv.nchunks;
+        k_ortho<0><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, nullptr, c->sv.chunks, nb, c->sv.cell_chunks, nc,
+                                              c->sv.dpart, h1, c->sv.ticket, c->cells, nullptr);
+        BIE_LAUNCH(c, "k_ortho<0>");
+        k_ortho<1><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, h1, c->sv.chunks, nb, c->sv.cell_chunks, nc,
+                                              c->sv.dpart, h2, c->sv.ticket, c->cells, nullptr);
+        BIE_LAUNCH(c, "k_ortho<1>");
+        k_ortho<2><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, h2, c->sv.chunks, nb, c->sv.cell_chunks, nc,
+                                              c->sv.dpart, hn, c->sv.ticket, c->cells, fac_d);
+        BIE_LAUNCH(c, "k_ortho<2>");
+        k_scale_copy<<<gs, bs, 0, c->stream>>>(w, fac_d, c->node_cell, V + (size_t)(k + 1) * ld, n);
+        BIE_LAUNCH(c, "k_scale_copy");
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.pinned + (size_t)(k & 1) * slot, hb,
+                                    (2 * (size_t)(k + 1) + 1) * nc * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
-        BIE_CUDA(c, cudaMemcpyAsync(hh.data() + 2 * (size_t)nc * S, hn, nc * sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->stream));
-        BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+        BIE_CUDA(c, cudaEventRecord(c->sv.ev[k & 1], c->stream));
+        return BIE_OK;
+    };
+    if (int rc = enqueue(0)) return rc;
+    for (int k = 0; k < kmax && n_on > 0; ++k) {
+        if (k + 1 < kmax)
+            if (int rc = enqueue(k + 1)) return rc;
+        BIE_CUDA(c, cudaEventSynchronize(c->sv.ev[k & 1]));
+        const double* hh = c->sv.pinned + (size_t)(k & 1) * slot;
+        const double* hh2 = hh + (size_t)(k + 1) * nc;
+        const double* hhn = hh + 2 * (size_t)(k + 1) * nc;
         bool switched = false;
         for (int q = 0; q < nc; ++q) {
-            if (!on[q]) {
-                fac[q] = 0.0;
-                continue;
-            }
-            for (int j = 0; j <= k; ++j) hcol[j] = hh[(size_t)j * nc + q] + hh[(size_t)nc * S + (size_t)j * nc + q];
-            const double hk1 = std::sqrt(hh[2 * (size_t)nc * S + q]);
+            if (!on[q]) continue;
+            for (int j = 0; j <= k; ++j) hcol[j] = hh[(size_t)j * nc + q] + hh2[(size_t)j * nc + q];
+            const double hk1 = std::sqrt(hhn[q]);
             if (!std::isfinite(hk1)) return fail(c, BIE_ENUMERIC, "non-finite Krylov vector in GMRES");
             hcol[k + 1] = hk1;
-            fac[q] = hk1 > 0 ? 1.0 / hk1 : 0.0;
             // Givens
             for (int j = 0; j < k; ++j) {
                 const double a = cs[q][j] * hcol[j] + sn[q][j] * hcol[j + 1];
@@ -254,19 +317,12 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
             est[q] = std::fabs(g[q][k + 1]);
             if (est[q] <= atol[q] || hk1 == 0.0) {
                 on[q] = 0;
-                fac[q] = 0.0;
                 --n_on;
                 switched = true;
             }
         }
-        if (n_on > 0) {
-            // next basis vector, zero in switched-off cells
-            BIE_CUDA(c, cudaMemcpyAsync(coef, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-            k_scale_copy<<<gs, bs, 0, c->stream>>>(w, coef, c->node_cell, V + (size_t)(k + 1) * ld, n);
-            BIE_LAUNCH(c, "k_scale_copy");
-            if (switched)
-                if ((rc = set_active(c, on))) return rc;
-        }
+        if (switched && n_on > 0)
+            if (int rc = set_active(c, on)) return rc;
     }
     // per cell: back substitution with its own Krylov dimension
     int kk = 0;
