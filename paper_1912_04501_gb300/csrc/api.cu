@@ -31,13 +31,13 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 
 static void free_all(bie_ctx* c) {
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
-                    c->tgt32, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
-                    c->next.wall, c->next.e2, c->yp, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
-                    c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.xi, c->ws.T, c->ws.vpart, c->sv.V,
-                    c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.ticket, c->sv.dpart,
+                    c->tgt32, c->posdf, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
+                    c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
+                    c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
+                    c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.dpart,
                     c->sv.chunks,
                     c->sv.cell_chunks, c->sv.sigma_prev, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
-                    c->cl.blk_off, c->cl.blocks, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
+                    c->cl.blk_off, c->cl.blocks, c->cl.blocks32, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
                     c->near[1].items, c->near[2].items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -331,6 +331,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->owner, n);
     rc = rc ? rc : dalloc(c, &c->body, 8 * nbs);
     rc = rc ? rc : dalloc(c, &c->tgt32, n);
+    rc = rc ? rc : dalloc(c, &c->posdf, n);
     rc = rc ? rc : dalloc(c, &c->gl_s, m);
     rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);
@@ -345,6 +346,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
     rc = rc ? rc : dalloc(c, &c->yp, nc * 2 * M);
+    rc = rc ? rc : dalloc(c, &c->ypf, nc * M);
     rc = rc ? rc : dalloc(c, &c->scal, 3 * nbs + nc + 8);
     rc = rc ? rc : dalloc(c, &c->ws.sigma, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.out, 2 * (size_t)n);
@@ -355,6 +357,12 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, (char**)&c->ws.part, part);
     rc = rc ? rc : dalloc(c, &c->ws.gpart, nc * kDiscSplits * 8 * m);
     rc = rc ? rc : dalloc(c, &c->ws.xi, nc * 2 * M);
+    rc = rc ? rc : dalloc(c, &c->ws.xif, nc * 2 * M);
+    rc = rc ? rc : dalloc(c, &c->ws.gt, nc * 8 * m);
+    rc = rc ? rc : dalloc(c, &c->ws.dticket, nc * 2 * m);
+    rc = rc ? rc : dalloc(c, &c->sv.ticket, 1);
+    if (!rc) rc = cu(cudaMemset(c->ws.dticket, 0, nc * 2 * m * sizeof(unsigned int)), "cudaMemset");
+    if (!rc) rc = cu(cudaMemset(c->sv.ticket, 0, sizeof(unsigned int)), "cudaMemset");
     rc = rc ? rc : dalloc(c, &c->ws.T, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.vpart, nbs * kVelSplits * 3);
     rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1) * 2 * n);
@@ -367,9 +375,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         const size_t slot = (2 * (size_t)(kk + 1) + 1) * nc;
         rc = rc ? rc : dalloc(c, &c->sv.h, 2 * slot + (size_t)kk * nc);
         rc = rc ? rc : dalloc(c, &c->sv.fac, 2 * nc);
-        rc = rc ? rc : dalloc(c, &c->sv.ticket, 1);
         if (!rc) rc = cu(cudaMallocHost((void**)&c->sv.pinned, 2 * slot * sizeof(double)), "cudaMallocHost");
-        if (!rc) rc = cu(cudaMemset(c->sv.ticket, 0, sizeof(unsigned int)), "cudaMemset");
         for (int e = 0; e < 2 && !rc; ++e)
             rc = cu(cudaEventCreateWithFlags(&c->sv.ev[e], cudaEventDisableTiming), "cudaEventCreate");
     }
@@ -385,6 +391,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         rc = rc ? rc : dalloc(c, &c->cl.pairs, c->cl.cap_pairs);
         rc = rc ? rc : dalloc(c, &c->cl.blk_off, c->cl.cap_pairs);
         rc = rc ? rc : dalloc(c, &c->cl.blocks, (size_t)c->cl.cap_doubles);
+        rc = rc ? rc : dalloc(c, &c->cl.blocks32, (size_t)c->cl.cap_doubles);
         rc = rc ? rc : dalloc(c, &c->cl.flags, 6);
     }
     c->ws.part_bytes = part;
@@ -420,6 +427,14 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
     rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
     rc = rc ? rc : up(c->yp, yp.data(), yp.size() * sizeof(double));
+    {
+        std::vector<float2> ypf(nc * M);
+        for (int k = 0; k < n_cells; ++k)
+            for (int p = 0; p < M; ++p)
+                ypf[(size_t)k * M + p] = make_float2((float)(yp[(size_t)k * 2 * M + 2 * p] - c->cells_h[k].C[0]),
+                                                     (float)(yp[(size_t)k * 2 * M + 2 * p + 1] - c->cells_h[k].C[1]));
+        rc = rc ? rc : up(c->ypf, ypf.data(), ypf.size() * sizeof(float2));
+    }
     rc = rc ? rc : up(c->e2d, c->e2_0.data(), c->e2_0.size() * sizeof(double));
     rc = rc ? rc : build_near_items(c);
     rc = rc ? rc : build_dot_chunks(c);

@@ -10,7 +10,8 @@
 //                   all cells -> partial sums per split
 //   k_disc          wall discrepancy of the near sum with the far-image
 //                   cancellation (Sec. 6.2 step 2), per (wall point, split, cell)
-//   k_xi            g~ = g0 - g, xi = P g~ (Sec. 6.2 step 3), per (row, cell)
+//                   (its last block per wall point forms g~ = g0 - g, Sec. 6.2 step 3)
+//   k_xi            xi = P g~ per (row, cell) (Sec. 6.2 step 3)
 //   k_correct       T = sum of partials + on-curve diagonal + proxy traction (step 4)
 //   k_close_apply   close-evaluation correction (Sec. 6.3); on the single-
 //                   precision path also the own-body and close pairs redone
@@ -18,6 +19,7 @@
 //   k_finish        alpha = -T_0 . n_0 per cell;  y = sigma/2 + T + alpha n + L sigma
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "bie_internal.cuh"
 
@@ -47,11 +49,6 @@ __device__ inline double block_sum_d(double v, double* red) {
 
 
 // Knuth's TwoSum: s + e == a + b exactly
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    float z = s - a;
-    e = (a - (s - z)) + (b - z);
-}
 
 // ---------------------------------------------------------------------------
 __global__ void k_pack(const double2* __restrict__ sigma, const double* __restrict__ x,
@@ -279,28 +276,6 @@ struct __align__(16) SrcDF {
     float xh, xl, yh, yl, qxh, qxl, qyh, qyl;
 };
 
-__device__ __forceinline__ void split_df(double v, float& h, float& l) {
-    h = (float)v;
-    l = (float)(v - (double)h);
-}
-
-// h + l -> normalised (|l| <= ulp(h) / 2), valid when |h| >= |l|
-__device__ __forceinline__ void fast2(float& h, float& l) {
-    float s = h + l;
-    l = l - (s - h);
-    h = s;
-}
-
-// (ph + pl) - (sh + sl), exact to ~2^-48 relative to the difference itself
-__device__ __forceinline__ void df_diff(float ph, float pl, float sh, float sl, float& h, float& l) {
-    float s1, e1, s2, e2, e3;
-    two_sum(ph, -sh, s1, e1);
-    two_sum(pl, -sl, s2, e2);
-    two_sum(s1, s2, h, e3);
-    l = (e1 + e2) + e3;
-    fast2(h, l);
-}
-
 // (ah + al) * (bh + bl) -> (ph, pl), pl not renormalised
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
     ph = ah * bh;
@@ -464,35 +439,48 @@ int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st
 // point wp in [0, 2m) (L points, then D points) of the cell and source split
 // s of kDiscSplits; its threads stride over the split's sources and the block
 // reduces (u_x, u_y, t_x, t_y) into gpart[((cell * kDiscSplits + s) * 2m + wp) * 4 + comp].
+// F32: single precision from the packed cell-centred sources (the inner
+// solve's operator); otherwise double precision.
 __device__ __forceinline__ float fast_log(float x) { return __logf(x); }
 __device__ __forceinline__ double fast_log(double x) { return log(x); }
 __device__ __forceinline__ float fast_rcp(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
-template <typename Real>
+template <bool F32>
 __global__ void __launch_bounds__(256)
-k_disc(const Src64* __restrict__ src, const Cell* __restrict__ cells, int m, const double* __restrict__ wall,
-       double* __restrict__ gpart) {
-    __shared__ double red[4][33];
+k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const Cell* __restrict__ cells, int m,
+       const double* __restrict__ wall, const double* __restrict__ bodyF, double* __restrict__ gpart,
+       unsigned int* __restrict__ ticket, double* __restrict__ gt) {
+    using Real = typename std::conditional<F32, float, double>::type;
+    __shared__ double red[4][8];
+    __shared__ bool last;
     const int wp = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y, cidx = blockIdx.z;
     const Cell& cl = cells[cidx];
     if (!cl.active) return;
     // per-geometry table: collocation point minus each of the six far-image
-    // shifts (plus images -2a + kb, then minus images a + kb), and the normal
+    // shifts (plus images -2a + kb, then minus images a + kb), and the normal;
+    // the single-precision path works in cell-centred coordinates
     const double* wt = wall + ((size_t)cidx * 2 * m + wp) * 16;
+    const double ocx = F32 ? cl.C[0] : 0.0, ocy = F32 ? cl.C[1] : 0.0;
     Real ox[6], oy[6];
 #pragma unroll
     for (int im = 0; im < 6; ++im) {
-        ox[im] = (Real)wt[2 * im];
-        oy[im] = (Real)wt[2 * im + 1];
+        ox[im] = (Real)(wt[2 * im] - ocx);
+        oy[im] = (Real)(wt[2 * im + 1] - ocy);
     }
     const Real n0 = (Real)wt[12], n1 = (Real)wt[13];
     Real ux = 0, uy = 0, tx = 0, ty = 0;
     const int per = (cl.n_nodes + nsp - 1) / nsp;
     const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const Src64 q = src[j];
-        const Real qx = (Real)q.z, qy = (Real)q.w, sx = (Real)q.x, sy = (Real)q.y;
+        Real sx, sy, qx, qy;
+        if constexpr (F32) {
+            const float4 q = src32[j];
+            sx = q.x; sy = q.y; qx = q.z; qy = q.w;
+        } else {
+            const Src64 q = src64[j];
+            sx = q.x; sy = q.y; qx = q.z; qy = q.w;
+        }
 #pragma unroll
         for (int im = 0; im < 6; ++im) {
             const Real rx = ox[im] - sx, ry = oy[im] - sy;
@@ -519,65 +507,62 @@ k_disc(const Src64* __restrict__ src, const Cell* __restrict__ cells, int m, con
         if (lane == 0) red[c][warp] = t;
     }
     __syncthreads();
+    const size_t nv = 8 * (size_t)m;
+    double* gp = gpart + (size_t)cidx * kDiscSplits * nv;
     if (threadIdx.x < 4) {
         double t = 0;
         for (int k = 0; k < nw; ++k) t += red[threadIdx.x][k];
         const double scale = threadIdx.x < 2 ? 1.0 / (4.0 * kPi * cl.mu) : -1.0 / kPi;
-        gpart[(((size_t)cidx * kDiscSplits + sp) * 2 * m + wp) * 4 + threadIdx.x] = t * scale;
+        gp[(size_t)sp * nv + 4 * wp + threadIdx.x] = t * scale;
+    }
+    // the last split of this wall point to finish adds the splits in order
+    // and writes the wall point's entries of g~ = g0 - g (Sec. 6.2 step 3),
+    // g0 = [0; F / 2|e2|; 0; F / 2|e1|] with F the cell's total force
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket + (size_t)cidx * 2 * m + wp, 1u) == (unsigned)nsp - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        // the cell's total force, by one warp
+        double fx = 0, fy = 0;
+        for (int b = cl.body_off + lane; b < cl.body_off + cl.n_bodies; b += 32) {
+            fx += bodyF[3 * b];
+            fy += bodyF[3 * b + 1];
+        }
+        fx = warp_sum_d(fx);
+        fy = warp_sum_d(fy);
+        if (lane < 4) {
+            const int c = lane;
+            double g = 0;
+            for (int b = 0; b < nsp; ++b) g += __ldcg(gp + (size_t)b * nv + 4 * wp + c);
+            const double f = c == 2 ? fx : fy;
+            double* d = gt + (size_t)cidx * nv;
+            const bool L = wp < m;  // L: rows of blocks 1 (velocity) and 2 (traction); D: blocks 3 and 4
+            const int l = L ? wp : wp - m;
+            const int row = (L ? 0 : 4 * m) + c * m + l;
+            d[row] = c < 2 ? -g : f / (2.0 * (L ? cl.l2 : cl.l1)) - g;
+            if (c == 0) ticket[(size_t)cidx * 2 * m + wp] = 0u;
+        }
     }
 }
 
-// g~ and xi = P g~ (Sec. 6.2 step 3).  One warp-sized CTA per (row r of P,
-// cell): GB300's FP64 pipe is narrow, so the compensated products are spread
-// over as many SMs as there are rows.  Every CTA rebuilds g~ from the
-// kDiscSplits partials of the discrepancy kernel (fixed order: deterministic)
-// and then computes xi_r with a compensated dot product (Ogita, Rump &
-// Oishi's Dot2: FMA-exact products, error-free sums; P has entries up to
-// ~1/lam, so a plain double-precision product would add relative noise ~1e-11
-// to the correction and put a floor under the GMRES residual).
+// xi = P g~ (Sec. 6.2 step 3).  One warp-sized CTA per (row r of P, cell):
+// GB300's FP64 pipe is narrow, so the compensated products are spread over as
+// many SMs as there are rows.  Each row is a compensated dot product (Ogita,
+// Rump & Oishi's Dot2: FMA-exact products, error-free sums; P has entries up
+// to ~1/lam, so a plain double-precision product would add relative noise
+// ~1e-11 to the correction and put a floor under the GMRES residual).  xi is
+// also stored in single precision for the single-precision correction.
 __global__ void __launch_bounds__(32)
-k_xi(const double* __restrict__ gpart, int m, int M, const double* __restrict__ bodyF,
-     const Cell* __restrict__ cells, const double* __restrict__ Pall, double* __restrict__ xiall) {
-    extern __shared__ double d[];  // 8m: g~
+k_xi(const double* __restrict__ gt, int m, int M, const Cell* __restrict__ cells, const double* __restrict__ Pall,
+     double* __restrict__ xiall, float* __restrict__ xifall) {
     const int lane = threadIdx.x, r = blockIdx.x, cidx = blockIdx.y;
-    const Cell& cl = cells[cidx];
-    if (!cl.active) return;
+    if (!cells[cidx].active) return;
     const int nv = 8 * m;
-    const double* gp = gpart + (size_t)cidx * kDiscSplits * nv;
+    const double* d = gt + (size_t)cidx * nv;
     const double* P = Pall + (size_t)cidx * 2 * M * nv;
-    double fx = 0, fy = 0;
-    for (int b = cl.body_off + lane; b < cl.body_off + cl.n_bodies; b += 32) {
-        fx += bodyF[3 * b];
-        fy += bodyF[3 * b + 1];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-    }
-    const double l1 = cl.l1, l2 = cl.l2;
-    for (int wp = lane; wp < 2 * m; wp += 32) {
-        double g[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double a = 0;
-            for (int b = 0; b < kDiscSplits; ++b) a += gp[(size_t)b * nv + 4 * wp + c];
-            g[c] = a;
-        }
-        if (wp < m) {  // L: rows of blocks 1 (velocity) and 2 (traction)
-            const int l = wp;
-            d[l] = -g[0];
-            d[m + l] = -g[1];
-            d[2 * m + l] = fx / (2.0 * l2) - g[2];
-            d[3 * m + l] = fy / (2.0 * l2) - g[3];
-        } else {  // D: blocks 3 and 4
-            const int l = wp - m;
-            d[4 * m + l] = -g[0];
-            d[5 * m + l] = -g[1];
-            d[6 * m + l] = fx / (2.0 * l1) - g[2];
-            d[7 * m + l] = fy / (2.0 * l1) - g[3];
-        }
-    }
-    __syncwarp();
     double s = 0, e = 0;
     for (int cc = lane; cc < nv; cc += 32) {
         const double a = P[(size_t)r * nv + cc], b = d[cc];
@@ -596,17 +581,18 @@ k_xi(const double* __restrict__ gpart, int m, int M, const double* __restrict__ 
         e = e + e2 + ((s - (t - z)) + (s2 - z));
         s = t;
     }
-    if (lane == 0) xiall[(size_t)cidx * 2 * M + r] = s + e;
+    if (lane == 0) {
+        xiall[(size_t)cidx * 2 * M + r] = s + e;
+        xifall[(size_t)cidx * 2 * M + r] = (float)(s + e);
+    }
 }
 
 // T = near partials + on-curve diagonal -(kappa/2pi) tau (tau . q) + proxy
-// traction.  ProxyReal = float on the single-precision path (rcp.approx, the
-// inner-solve operator), double on the FP64 path.  kCorrLanes lanes per
-// target split the near-sum partials and the proxies, then combine with
-// shuffles (fixed order: deterministic).
-template <typename PartT, typename ProxyReal>
+// traction, double-precision paths.  kCorrLanes lanes per target split the
+// near-sum partials and the proxies, then combine with shuffles (fixed order:
+// deterministic).
 __global__ void __launch_bounds__(256)
-k_correct(const PartT* __restrict__ part, int prec, int N, const int* __restrict__ node_cell,
+k_correct(const double2* __restrict__ part, int prec, int N, const int* __restrict__ node_cell,
           const Cell* __restrict__ cells, const double2* __restrict__ sigma, const double* __restrict__ x,
           const double* __restrict__ y, const double* __restrict__ nx, const double* __restrict__ ny,
           const double* __restrict__ w, const double* __restrict__ kap, const double* __restrict__ ypall,
@@ -620,37 +606,86 @@ k_correct(const PartT* __restrict__ part, int prec, int N, const int* __restrict
     const int splits = cl.splits[prec];
     const long long base = cl.part_off[prec] + (i - cl.node_off);
     for (int s = sub; s < splits; s += kCorrLanes) {
-        PartT p = part[base + (long long)s * cl.n_nodes];
-        tx += (double)p.x;
-        ty += (double)p.y;
+        const double2 p = part[base + (long long)s * cl.n_nodes];
+        tx += p.x;
+        ty += p.y;
     }
     const double n0 = nx[i], n1 = ny[i];
-    // proxies in cell-centred coordinates (exact in double, accurate in float)
-    const double Cx = cl.C[0], Cy = cl.C[1];
     const double* yp = ypall + (size_t)cidx * 2 * M;
     const double* xi = xiall + (size_t)cidx * 2 * M;
-    const ProxyReal X = (ProxyReal)(x[i] - Cx), Y = (ProxyReal)(y[i] - Cy);
-    const ProxyReal m0 = (ProxyReal)n0, m1 = (ProxyReal)n1;
-    ProxyReal cx = 0, cy = 0;
+    const double X = x[i], Y = y[i];
+    double cx = 0, cy = 0;
     for (int p = sub; p < M; p += kCorrLanes) {
-        ProxyReal rx = X - (ProxyReal)(yp[2 * p] - Cx), ry = Y - (ProxyReal)(yp[2 * p + 1] - Cy);
-        ProxyReal fx = (ProxyReal)xi[p], fy = (ProxyReal)xi[M + p];
-        ProxyReal r2 = rx * rx + ry * ry;
-        ProxyReal inv;
-        if constexpr (sizeof(ProxyReal) == 4) inv = rcp_approx(r2);
-        else inv = (ProxyReal)1 / r2;
-        ProxyReal cc = ((rx * m0 + ry * m1) * inv) * ((rx * fx + ry * fy) * inv);
+        const double rx = X - yp[2 * p], ry = Y - yp[2 * p + 1];
+        const double fx = xi[p], fy = xi[M + p];
+        const double inv = 1.0 / (rx * rx + ry * ry);
+        const double cc = ((rx * n0 + ry * n1) * inv) * ((rx * fx + ry * fy) * inv);
         cx += cc * rx;
         cy += cc * ry;
     }
-    tx += -(double)cx / kPi;
-    ty += -(double)cy / kPi;
+    tx += -cx / kPi;
+    ty += -cy / kPi;
 #pragma unroll
     for (int o = kCorrLanes / 2; o > 0; o >>= 1) {
         tx += __shfl_xor_sync(0xffffffffu, tx, o);
         ty += __shfl_xor_sync(0xffffffffu, ty, o);
     }
     if (sub != 0 || g >= N) return;
+    const double2 sg = sigma[i];
+    const double t0 = -n1, t1 = n0;  // unit tangent
+    const double qx = sg.x * w[i], qy = sg.y * w[i];
+    const double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
+    T[i] = make_double2(tx + dg * t0, ty + dg * t1);
+}
+
+// The same for the single-precision path, on the FP32 pipe: the partials are
+// added with TwoSum compensation, the proxy traction uses the cell-centred
+// single-precision targets, proxies and strengths; only the per-target
+// results and the diagonal term are formed in double.
+__global__ void __launch_bounds__(256)
+k_correct32(const float2* __restrict__ part, int N, const int* __restrict__ node_cell,
+            const Cell* __restrict__ cells, const double2* __restrict__ sigma, const float4* __restrict__ tgt32,
+            const double* __restrict__ nx, const double* __restrict__ ny, const double* __restrict__ w,
+            const double* __restrict__ kap, const float2* __restrict__ ypfall, const float* __restrict__ xifall,
+            int M, double2* __restrict__ T) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kCorrLanes;
+    const int sub = threadIdx.x % kCorrLanes;
+    const int i = g < N ? g : N - 1;
+    const int cidx = node_cell[i];
+    const Cell& cl = cells[cidx];
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, e;
+    const int splits = cl.splits[0];
+    const long long base = cl.part_off[0] + (i - cl.node_off);
+    for (int s = sub; s < splits; s += kCorrLanes) {
+        const float2 p = part[base + (long long)s * cl.n_nodes];
+        two_sum(hx, p.x, hx, e);
+        lx += e;
+        two_sum(hy, p.y, hy, e);
+        ly += e;
+    }
+    const float4 tv = tgt32[i];
+    const float2* yp = ypfall + (size_t)cidx * M;
+    const float* xi = xifall + (size_t)cidx * 2 * M;
+    float cx = 0.f, cy = 0.f;
+    for (int p = sub; p < M; p += kCorrLanes) {
+        const float2 q = yp[p];
+        const float rx = tv.x - q.x, ry = tv.y - q.y;
+        const float fx = xi[p], fy = xi[M + p];
+        const float inv = rcp_approx(fmaf(rx, rx, ry * ry));
+        const float cc = (fmaf(rx, tv.z, ry * tv.w) * inv) * (fmaf(rx, fx, ry * fy) * inv);
+        cx = fmaf(cc, rx, cx);
+        cy = fmaf(cc, ry, cy);
+    }
+    const double c = -1.0 / kPi;
+    double tx = (double)hx + (double)lx + c * (double)cx;
+    double ty = (double)hy + (double)ly + c * (double)cy;
+#pragma unroll
+    for (int o = kCorrLanes / 2; o > 0; o >>= 1) {
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+    if (sub != 0 || g >= N) return;
+    const double n0 = nx[i], n1 = ny[i];
     const double2 sg = sigma[i];
     const double t0 = -n1, t1 = n0;  // unit tangent
     const double qx = sg.x * w[i], qy = sg.y * w[i];
@@ -824,23 +859,22 @@ static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precisi
     if (int rc = prof_end(c)) return rc;
     const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
     if (f32)
-        k_disc<float><<<dgrid, 256, 0, c->stream>>>(ws.src64, c->cells, c->m, c->wall, ws.gpart);
+        k_disc<true><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                   ws.dticket, ws.gt);
     else
-        k_disc<double><<<dgrid, 256, 0, c->stream>>>(ws.src64, c->cells, c->m, c->wall, ws.gpart);
+        k_disc<false><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                    ws.dticket, ws.gt);
     BIE_LAUNCH(c, "k_disc");
-    k_xi<<<dim3(2 * c->M, c->ncell), 32, 8 * c->m * sizeof(double), c->stream>>>(ws.gpart, c->m, c->M, ws.bodyF,
-                                                                                 c->cells, c->P, ws.xi);
+    k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(ws.gt, c->m, c->M, c->cells, c->P, ws.xi, ws.xif);
     BIE_LAUNCH(c, "k_xi");
     double2* T = reinterpret_cast<double2*>(ws.T);
     const int gsc = (N * kCorrLanes + 255) / 256;
     if (f32)
-        k_correct<float2, float><<<gsc, 256, 0, c->stream>>>((const float2*)ws.part, prec, N, c->node_cell, c->cells,
-                                                             sg, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->yp,
-                                                             ws.xi, c->M, T);
+        k_correct32<<<gsc, 256, 0, c->stream>>>((const float2*)ws.part, N, c->node_cell, c->cells, sg, c->tgt32, c->nx,
+                                                c->ny, c->w, c->kap, c->ypf, ws.xif, c->M, T);
     else
-        k_correct<double2, double><<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell,
-                                                               c->cells, sg, c->x, c->y, c->nx, c->ny, c->w, c->kap,
-                                                               c->yp, ws.xi, c->M, T);
+        k_correct<<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell, c->cells, sg, c->x, c->y,
+                                              c->nx, c->ny, c->w, c->kap, c->yp, ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
     if (int rc = close_apply(c, sigma, ws.T, f32 ? ws.src32 : nullptr)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
@@ -971,11 +1005,11 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     BIE_LAUNCH(c, "k_pack");
     k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
     BIE_LAUNCH(c, "k_body_moments");
-    k_disc<double><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(c->ws.src64, c->cells, c->m, c->wall,
-                                                                                 c->ws.gpart);
+    k_disc<false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
+        c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt);
     BIE_LAUNCH(c, "k_disc");
-    k_xi<<<dim3(2 * c->M, c->ncell), 32, 8 * c->m * sizeof(double), c->stream>>>(c->ws.gpart, c->m, c->M,
-                                                                                 c->ws.bodyF, c->cells, c->P, c->ws.xi);
+    k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(c->ws.gt, c->m, c->M, c->cells, c->P, c->ws.xi,
+                                                           c->ws.xif);
     BIE_LAUNCH(c, "k_xi");
     if (v || omega) {
         k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, c->body, c->body_cell, c->cells,

@@ -41,8 +41,11 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
     const size_t b_body = round256(3 * (size_t)c->nb * sizeof(double));
     const size_t b_gpart = round256(nc * kDiscSplits * 8 * c->m * sizeof(double));
     const size_t b_xi = round256(nc * 2 * c->M * sizeof(double));
+    const size_t b_xif = round256(nc * 2 * c->M * sizeof(float));
+    const size_t b_gt = round256(nc * 8 * c->m * sizeof(double));
+    const size_t b_tk = round256(nc * 2 * c->m * sizeof(unsigned int));
     const size_t b_T = round256(2 * N * sizeof(double));
-    const size_t need = b_src32 + b_src64 + b_part + b_body + b_gpart + b_xi + b_T;
+    const size_t need = b_src32 + b_src64 + b_part + b_body + b_gpart + b_xi + b_xif + b_gt + b_tk + b_T;
     if (need > BIE_STATIC_SCRATCH_BYTES)
         return fail(c, BIE_EINVAL, "bie_apply_static: this context needs " + std::to_string(need) +
                                        " bytes of scratch; the static array holds " +
@@ -62,8 +65,8 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
         }
         base = static_cast<unsigned char*>(g_static_addr[c->device]);
     }
-    // Every buffer below is completely written by this call before it is read,
-    // so nothing has to be cleared between calls.
+    // Every buffer below is completely written by this call before it is read
+    // (the counters are cleared first), so nothing carries over between calls.
     Workspace ws;
     size_t o = 0;
     ws.src32 = reinterpret_cast<float4*>(base + o);
@@ -79,6 +82,15 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
     o += b_gpart;
     ws.xi = reinterpret_cast<double*>(base + o);
     o += b_xi;
+    ws.xif = reinterpret_cast<float*>(base + o);
+    o += b_xif;
+    ws.gt = reinterpret_cast<double*>(base + o);
+    o += b_gt;
+    ws.dticket = reinterpret_cast<unsigned int*>(base + o);
+    o += b_tk;
     ws.T = reinterpret_cast<double*>(base + o);
+    // the wall-discrepancy kernel's last-block counters must start at zero
+    // (they return to zero when it finishes)
+    BIE_CUDA(c, cudaMemsetAsync(ws.dticket, 0, b_tk, c->stream));
     return apply_device_ws(c, sigma, out, ws);
 }

@@ -8,7 +8,8 @@
 // Layout in HBM (all device arrays owned by the context):
 //   geometry  : x, y, nx, ny, w, kappa (N doubles each, SoA), owner (N ints, global
 //               body index), node_cell (N), body (nb x 8 doubles: a, b, xc, yc, theta,
-//               n, node offset, h), body_cell (nb), tgt32 (N float4: x - C, y - C, nx, ny)
+//               n, node offset, h), body_cell (nb), tgt32 (N float4: x - C, y - C, nx, ny),
+//               posdf (N float4: x - C, y - C as double-float pairs)
 //   densities : 2N doubles, node-major (x, y interleaved) == double2[N]
 //   sources   : src32 (N float4: x - C, y - C, qx, qy), src64 (N Src64: x, y, qx, qy),
 //               srcdf (N double-float records)
@@ -48,10 +49,10 @@ constexpr int kNearTile = 256;                  // sources staged per shared-mem
 constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
 constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
 constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
-constexpr int kDiscSplits = 4;        // source splits per wall point of the wall-discrepancy kernel
+constexpr int kDiscSplits = 8;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)
 constexpr int kVelSplits = 8;         // source splits per body in the velocity extraction
-constexpr int kDotChunk = 512;        // vector entries per partial dot product (chunks never span cells)
+constexpr int kDotChunk = 256;        // vector entries per partial dot product (chunks never span cells)
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
@@ -78,6 +79,7 @@ struct Close {
     int4* pairs = nullptr;        // cap_pairs (target, body, image, rho)
     long long* blk_off = nullptr; // cap_pairs
     double* blocks = nullptr;     // cap_doubles
+    float* blocks32 = nullptr;    // cap_doubles: the blocks divided by the source weights, single precision
     double* dtab = nullptr;       // Dirichlet tables per distinct node count
     long long* dtab_off = nullptr;  // nb: table base of each body
     int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved,
@@ -105,7 +107,10 @@ struct Workspace {
     void* part = nullptr;       // near-sum partials (see Cell::part_off)
     size_t part_bytes = 0;
     double* gpart = nullptr;    // ncell x kDiscSplits x 8m discrepancy partials
+    double* gt = nullptr;       // ncell x 8m  g~ = g0 - g
+    unsigned int* dticket = nullptr;  // ncell x 2m last-block counters of k_disc (zero between launches)
     double* xi = nullptr;       // ncell x 2M proxy strengths
+    float* xif = nullptr;       // ncell x 2M the same in single precision
     double* T = nullptr;        // 2N traction before the pressure fix
     double* vpart = nullptr;    // nb x kVelSplits x 3 velocity partials
 };
@@ -133,8 +138,8 @@ struct Solver {
                              // kmax x ncell combination coefficients
     double* pinned = nullptr;  // host (page-locked): 2 slots, as on the device
     double* fac = nullptr;   // 2 x ncell: normalisation factors, then per-cell norms
-    unsigned int* ticket = nullptr;  // last-block counter of k_ortho (zero between launches)
     cudaEvent_t ev[2] = {nullptr, nullptr};  // slot k % 2 copied to the host
+    unsigned int* ticket = nullptr;  // last-block counter of k_dots (zero between launches)
     double* dpart = nullptr; // (kmax + 2) x nchunks partial dot products
     int4* chunks = nullptr;  // nchunks: (cell, first entry, end entry, 0)
     int2* cell_chunks = nullptr;  // ncell: (first chunk, chunk count)
@@ -172,6 +177,7 @@ struct bie_ctx {
     int* owner = nullptr;
     double* body = nullptr;
     float4* tgt32 = nullptr;
+    float4* posdf = nullptr;    // N: x - C, y - C as double-float (xh, xl, yh, yl)
     // proxy fits of the current lattices, and of the next time step's (built on
     // a side stream during the current solve)
     double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
@@ -184,6 +190,7 @@ struct bie_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t next_done = nullptr;
     double* yp = nullptr;       // ncell x M x 2 proxy points
+    float2* ypf = nullptr;      // ncell x M proxy points minus the cell centre (single precision)
     double* scal = nullptr;     // 3 nb + ncell + 8: velocities, rotation rates, mu_eff
     bie::Workspace ws;
     bie::Solver sv;
@@ -263,6 +270,36 @@ __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum, 6 operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// Double-float numbers (an unevaluated sum hi + lo of two floats).
+__device__ __forceinline__ void split_df(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// h + l -> normalised (|l| <= ulp(h) / 2), valid when |h| >= |l|
+__device__ __forceinline__ void fast2(float& h, float& l) {
+    float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+
+// (ph + pl) - (sh + sl), exact to ~2^-48 relative to the difference itself
+__device__ __forceinline__ void df_diff(float ph, float pl, float sh, float sl, float& h, float& l) {
+    float s1, e1, s2, e2, e3;
+    two_sum(ph, -sh, s1, e1);
+    two_sum(pl, -sl, s2, e2);
+    two_sum(s1, s2, h, e3);
+    l = (e1 + e2) + e3;
+    fast2(h, l);
 }
 
 // The single-precision pair coefficient of the near sum (Eq. Gt without its

@@ -208,7 +208,7 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
                const double* __restrict__ w, const double* __restrict__ body,
                const int* __restrict__ node_cell, const Cell* __restrict__ cells,
                const double* __restrict__ dtab, const long long* __restrict__ dtab_off,
-               double* __restrict__ blocks) {
+               double* __restrict__ blocks, float* __restrict__ blocks32) {
     extern __shared__ double sm[];
     double* sa = sm;
     double* sb = sm + kCloseChunk;
@@ -278,9 +278,18 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
         double rx = X - (x[off + k] + sh.sx[im]), ry = Y - (y[off + k] + sh.sy[im]);
         double r2 = rx * rx + ry * ry;
         double cc = -(rx * n0 + ry * n1) * w[off + k] / (kPi * r2 * r2);
-        out[3 * k] = acc[3 * k] - cc * rx * rx;
-        out[3 * k + 1] = acc[3 * k + 1] - cc * rx * ry;
-        out[3 * k + 2] = acc[3 * k + 2] - cc * ry * ry;
+        const double A = acc[3 * k] - cc * rx * rx;
+        const double B = acc[3 * k + 1] - cc * rx * ry;
+        const double D = acc[3 * k + 2] - cc * ry * ry;
+        out[3 * k] = A;
+        out[3 * k + 1] = B;
+        out[3 * k + 2] = D;
+        // single-precision copy acting on q = sigma w (the packed sources)
+        const double iw = 1.0 / w[off + k];
+        float* o32 = blocks32 + blk_off[blockIdx.x] + 3 * k;
+        o32[0] = (float)(A * iw);
+        o32[1] = (float)(B * iw);
+        o32[2] = (float)(D * iw);
     }
 }
 
@@ -358,7 +367,8 @@ int build_close(bie_ctx* c) {
     BIE_CUDA(c, cudaFuncSetAttribute(k_close_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     c->cl.shm_limit = shm;
     k_close_blocks<<<h[0], 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
-                                                  c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off, c->cl.blocks);
+                                                  c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off, c->cl.blocks,
+                                                  c->cl.blocks32);
     BIE_LAUNCH(c, "k_close_blocks");
     return BIE_OK;
 }
@@ -397,28 +407,48 @@ int build_dirichlet_tables(bie_ctx* c) {
 // tangent r between neighbours on one curve.  For the target's own body
 // (unshifted) and for each of its close (body, image) pairs, the single-
 // precision terms are recomputed bit for bit (same inputs, same pair32) and
-// replaced by the same terms with r differenced in double precision and then
-// rounded; the close-evaluation block is applied as in k_close_apply.
+// replaced by the same terms with r formed exactly from double-float
+// positions (then rounded to single precision); the close-evaluation blocks
+// are applied in single precision (stored divided by the weights, acting on
+// q = sigma w).  Everything runs on the FP32 pipe.
 __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
-                                const long long* __restrict__ blk_off, const double* __restrict__ blocks,
+                                const long long* __restrict__ blk_off, const float* __restrict__ blocks32,
                                 int use_pairs, const double* __restrict__ body, const int* __restrict__ owner,
                                 const double2* __restrict__ sigma, int N, const float4* __restrict__ tgt32,
-                                const float4* __restrict__ src32, const double* __restrict__ x,
-                                const double* __restrict__ y, const int* __restrict__ node_cell,
-                                const Cell* __restrict__ cells, double2* __restrict__ T) {
+                                const float4* __restrict__ src32, const float4* __restrict__ posdf,
+                                const double* __restrict__ x, const double* __restrict__ y,
+                                const int* __restrict__ node_cell, const Cell* __restrict__ cells,
+                                double2* __restrict__ T) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= N) return;
     const Cell& cl = cells[node_cell[i]];
     const float4 tv = tgt32[i];
-    const double X = x[i], Y = y[i];
-    float fx = 0.f, fy = 0.f;  // sum of (double-differenced term - single-precision term)
-    auto redo = [&](int j, int im) {
+    const double Xc = x[i] - cl.C[0], Yc = y[i] - cl.C[1];
+    float fx = 0.f, fy = 0.f;  // sum of (exactly differenced term - single-precision term)
+    // target shifted by image im as a double-float pair (xh, xl, yh, yl):
+    // formed by lane 0 and broadcast (the FP64 pipe is narrow)
+    auto shifted = [&](int im) {
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane == 0) {
+            split_df(Xc - cl.sx[im], p.x, p.y);
+            split_df(Yc - cl.sy[im], p.z, p.w);
+        }
+        p.x = __shfl_sync(0xffffffffu, p.x, 0);
+        p.y = __shfl_sync(0xffffffffu, p.y, 0);
+        p.z = __shfl_sync(0xffffffffu, p.z, 0);
+        p.w = __shfl_sync(0xffffffffu, p.w, 0);
+        return p;
+    };
+    auto redo = [&](int j, int im, const float4& p) {
         const float4 s = src32[j];
         const float dx = (tv.x - cl.sxf[im]) - s.x;
         const float dy = (tv.y - cl.syf[im]) - s.y;
         const float c0 = pair32(dx, dy, tv.z, tv.w, s.z, s.w);
-        const float rx = (float)((X - cl.sx[im]) - x[j]);
-        const float ry = (float)((Y - cl.sy[im]) - y[j]);
+        const float4 q = posdf[j];
+        float rh, rl, sh, sl;
+        df_diff(p.x, p.y, q.x, q.y, rh, rl);
+        df_diff(p.z, p.w, q.z, q.w, sh, sl);
+        const float rx = rh + rl, ry = sh + sl;
         const float c1 = pair32(rx, ry, tv.z, tv.w, s.z, s.w);
         fx += c1 * rx - c0 * dx;
         fy += c1 * ry - c0 * dy;
@@ -426,26 +456,29 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
     {
         const int b = owner[i];
         const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+        const float4 p = shifted(4);
         for (int k = lane; k < nbn; k += 32)
-            if (off + k != i) redo(off + k, 4);
+            if (off + k != i) redo(off + k, 4, p);
     }
-    double tx = 0, ty = 0;
+    float bx = 0.f, by = 0.f;  // close-evaluation blocks applied to q
     if (use_pairs) {
         const int p0 = pair_base[i], p1 = pair_base[i + 1];
-        for (int p = p0; p < p1; ++p) {
-            const int4 pr = pairs[p];
+        for (int pp = p0; pp < p1; ++pp) {
+            const int4 pr = pairs[pp];
             const int b = pr.y, im = pr.z;
             const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
-            const double* C = blocks + blk_off[p];
+            const float* C = blocks32 + blk_off[pp];
+            const float4 p = shifted(im);
             for (int k = lane; k < nbn; k += 32) {
-                redo(off + k, im);
-                const double2 s = sigma[off + k];
-                const double A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
-                tx = fma(A, s.x, fma(B, s.y, tx));
-                ty = fma(B, s.x, fma(D, s.y, ty));
+                redo(off + k, im, p);
+                const float4 s = src32[off + k];
+                const float A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
+                bx = fmaf(A, s.z, fmaf(B, s.w, bx));
+                by = fmaf(B, s.z, fmaf(D, s.w, by));
             }
         }
     }
+    double tx = bx, ty = by;
     for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
@@ -465,10 +498,10 @@ int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32)
     const int bs = 256;
     const int gs = (int)((threads + bs - 1) / bs);
     if (src32) {
-        k_close_apply32<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks,
+        k_close_apply32<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks32,
                                                  c->cl.npairs > 0 ? 1 : 0, c->body, c->owner,
-                                                 reinterpret_cast<const double2*>(sigma), N, c->tgt32, src32, c->x,
-                                                 c->y, c->node_cell, c->cells, reinterpret_cast<double2*>(T));
+                                                 reinterpret_cast<const double2*>(sigma), N, c->tgt32, src32, c->posdf,
+                                                 c->x, c->y, c->node_cell, c->cells, reinterpret_cast<double2*>(T));
         BIE_LAUNCH(c, "k_close_apply32");
         return BIE_OK;
     }

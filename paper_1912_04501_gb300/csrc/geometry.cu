@@ -21,7 +21,7 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
                            const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                            double* __restrict__ x, double* __restrict__ y, double* __restrict__ nx,
                            double* __restrict__ ny, double* __restrict__ w, double* __restrict__ kap,
-                           float4* __restrict__ tgt32) {
+                           float4* __restrict__ tgt32, float4* __restrict__ posdf) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double* bd = body + 8 * owner[i];
@@ -46,6 +46,10 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
     w[i] = (2.0 * kPi / n) * sp;
     kap[i] = (dX * ddY - dY * ddX) / (sp * sp * sp);
     tgt32[i] = make_float4((float)(X - cl.C[0]), (float)(Y - cl.C[1]), (float)ty, (float)(-tx));
+    float4 pd;
+    split_df(X - cl.C[0], pd.x, pd.y);
+    split_df(Y - cl.C[1], pd.z, pd.w);
+    posdf[i] = pd;
 }
 
 // ---------------------------------------------------------------------------
@@ -253,7 +257,7 @@ __global__ void k_form_P(const double* __restrict__ Aall, int R, int C, const do
 int build_geometry(bie_ctx* c) {
     int bs = 256, gs = (c->N + bs - 1) / bs;
     k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->node_cell, c->cells, c->N, c->x, c->y, c->nx, c->ny,
-                                        c->w, c->kap, c->tgt32);
+                                        c->w, c->kap, c->tgt32, c->posdf);
     BIE_LAUNCH(c, "k_geometry");
     return BIE_OK;
 }

@@ -51,106 +51,100 @@ int build_dot_chunks(bie_ctx* c) {
     return BIE_OK;
 }
 
-// Multi-vector dot products, per cell, h[j * ncell + cell] = V_j . w over the
-// cell's entries (j < nv), in two deterministic passes: block b sums chunk b
-// of every vector (one warp per vector j at a time), then k_mdot_fin adds the
-// chunks of each (j, cell).
+// Classical Gram-Schmidt building blocks for every cell at once.
+// k_dots: block (b, g) writes the partial dot products V_j . w over reduction
+// chunk b (kDotChunk entries of one cell) for the eight vectors j = 8g .. 8g+7
+// (one warp each); V = w with nv = 1 gives the partial squared norms.  With a
+// ticket, the last block to finish also forms the sums of k_fin (below) in
+// the same fixed order, saving a launch when there are few of them.
+__device__ void fin_items(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
+                          int ncell, double* __restrict__ h, const Cell* __restrict__ cells, double* __restrict__ fac,
+                          int first_warp, int warp_stride, bool bypass_l1) {
+    const int lane = threadIdx.x & 31;
+    for (int idx = first_warp; idx < nv * ncell; idx += warp_stride) {
+        const int j = idx / ncell, cell = idx - j * ncell;
+        const int2 cc = cell_chunks[cell];
+        double s = 0;
+        for (int b = lane; b < cc.y; b += 32) {
+            const double* pp = part + (size_t)j * nchunks + cc.x + b;
+            s += bypass_l1 ? __ldcg(pp) : *pp;
+        }
+        s = wsum(s);
+        if (lane == 0) {
+            h[idx] = s;
+            if (fac) fac[cell] = (cells[cell].active && s > 0) ? 1.0 / sqrt(s) : 0.0;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
-k_mdot_part(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w,
-            const int4* __restrict__ chunks, int nchunks, double* __restrict__ part) {
-    const int4 ch = chunks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < nv; j += nw) {
+k_dots(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w,
+       const int4* __restrict__ chunks, int nchunks, double* __restrict__ part, unsigned int* __restrict__ ticket,
+       const int2* __restrict__ cell_chunks, int ncell, double* __restrict__ h, const Cell* __restrict__ cells,
+       double* __restrict__ fac) {
+    __shared__ bool last;
+    const int j = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j < nv) {
+        const int4 ch = chunks[blockIdx.x];
         const double* v = V + (size_t)j * ld;
         double s = 0;
         for (int i = ch.y + lane; i < ch.z; i += 32) s += v[i] * w[i];
         s = wsum(s);
         if (lane == 0) part[(size_t)j * nchunks + blockIdx.x] = s;
     }
-}
-
-// one warp per (j, cell): lanes add the cell's chunk partials, then a shuffle tree
-__global__ void k_mdot_fin(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
-                           int ncell, double* __restrict__ h) {
-    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (idx >= nv * ncell) return;
-    const int j = idx / ncell, cell = idx - j * ncell;
-    const int2 cc = cell_chunks[cell];
-    double s = 0;
-    for (int b = lane; b < cc.y; b += 32) s += part[(size_t)j * nchunks + cc.x + b];
-    s = wsum(s);
-    if (lane == 0) h[idx] = s;
-}
-
-static int mdot(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, double* h) {
-    k_mdot_part<<<c->sv.nchunks, 256, 0, c->stream>>>(V, ld, nv, w, c->sv.chunks, c->sv.nchunks, c->sv.dpart);
-    BIE_LAUNCH(c, "k_mdot_part");
-    k_mdot_fin<<<(nv * c->ncell * 32 + 255) / 256, 256, 0, c->stream>>>(c->sv.dpart, c->sv.nchunks, nv,
-                                                                      c->sv.cell_chunks, c->ncell, h);
-    BIE_LAUNCH(c, "k_mdot_fin");
-    return BIE_OK;
-}
-
-// One fused step of classical Gram-Schmidt for every cell at once; block b
-// owns reduction chunk b (kDotChunk entries of one cell).
-//   MODE 0:  h[j, cell] = V_j . w                         (j < nv)
-//   MODE 1:  w -= sum_j hprev[j, cell] V_j;  h[j, cell] = V_j . w
-//   MODE 2:  w -= sum_j hprev[j, cell] V_j;  h[cell] = w . w, and
-//            fac[cell] = 1 / sqrt(h[cell]) for active cells (else 0)
-// h[j, cell] lives at h[j * ncell + cell].  Each block writes its partial dot
-// products; the last block to finish (atomic ticket, after a fence) adds the
-// partials of each (j, cell) in chunk order, so the result does not depend
-// on the block schedule.
-template <int MODE>
-__global__ void __launch_bounds__(256)
-k_ortho(const double* __restrict__ V, size_t ld, int nv, double* __restrict__ w, const double* __restrict__ hprev,
-        const int4* __restrict__ chunks, int nchunks, const int2* __restrict__ cell_chunks, int ncell,
-        double* __restrict__ part, double* __restrict__ h, unsigned int* __restrict__ ticket,
-        const Cell* __restrict__ cells, double* __restrict__ fac) {
-    __shared__ double sw[kDotChunk];
-    __shared__ bool last;
-    const int4 ch = chunks[blockIdx.x];
-    const int q = ch.x, e0 = ch.y, len = ch.z - ch.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        double v = w[e0 + t];
-        if (MODE > 0) {
-            double s0 = v, s1 = 0;
-            int j = 0;
-            for (; j + 2 <= nv; j += 2) {
-                s0 -= hprev[(size_t)j * ncell + q] * V[(size_t)j * ld + e0 + t];
-                s1 -= hprev[(size_t)(j + 1) * ncell + q] * V[(size_t)(j + 1) * ld + e0 + t];
-            }
-            if (j < nv) s0 -= hprev[(size_t)j * ncell + q] * V[(size_t)j * ld + e0 + t];
-            v = s0 + s1;
-            w[e0 + t] = v;
-        }
-        sw[t] = v;
-    }
-    __syncthreads();
-    const int nd = MODE == 2 ? 1 : nv;
-    for (int j = warp; j < nd; j += nw) {
-        const double* vj = V + (size_t)j * ld + e0;
-        double s = 0;
-        for (int t = lane; t < len; t += 32) s += (MODE == 2 ? sw[t] : vj[t]) * sw[t];
-        s = wsum(s);
-        if (lane == 0) part[(size_t)j * nchunks + blockIdx.x] = s;
-    }
+    if (!ticket) return;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int item = threadIdx.x; item < nd * ncell; item += blockDim.x) {
-        const int j = item / ncell, cq = item - j * ncell;
-        const int2 cc = cell_chunks[cq];
-        double s = 0;
-        for (int b = 0; b < cc.y; ++b) s += __ldcg(part + (size_t)j * nchunks + cc.x + b);
-        h[item] = s;
-        if (MODE == 2) fac[cq] = (cells[cq].active && s > 0) ? 1.0 / sqrt(s) : 0.0;
-    }
+    fin_items(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, threadIdx.x >> 5, blockDim.x >> 5, true);
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// One warp per (j, cell): h[j * ncell + cell] = the cell's chunk partials
+// added in a fixed order.  With fac (squared norms, nv = 1) also the
+// normalisation factor 1 / sqrt(h) of every active cell (0 for the others).
+__global__ void k_fin(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
+                      int ncell, double* __restrict__ h, const Cell* __restrict__ cells, double* __restrict__ fac) {
+    fin_items(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+              (gridDim.x * blockDim.x) >> 5, false);
+}
+
+// w -= sum_j h[j * ncell + cell] V_j  (cell of each entry from node_cell);
+// eight lanes per entry split the vectors and combine with shuffles (fixed
+// order: deterministic), which keeps enough loads in flight for short vectors.
+__global__ void __launch_bounds__(256)
+k_update(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int ncell,
+         const int* __restrict__ node_cell, double* __restrict__ w, int n) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = (int)(t & 7);
+    const int i0 = (int)(t >> 3);
+    const int i = i0 < n ? i0 : n - 1;
+    const double* hc = h + node_cell[i >> 1];
+    double s = 0;
+    for (int j = sub; j < nv; j += 8) s += hc[(size_t)j * ncell] * V[(size_t)j * ld + i];
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (sub == 0 && i0 < n) w[i] -= s;
+}
+
+// h = V^T w per cell (partials, then the fixed-order sums)
+static int mdots(bie_ctx* c, const double* V, size_t ld, int nv, const double* w, double* h, double* fac) {
+    // few sums: the last block of k_dots forms them; many (large batches): k_fin
+    const bool fused = (long long)nv * c->ncell <= 512;
+    k_dots<<<dim3(c->sv.nchunks, (nv + 7) / 8), 256, 0, c->stream>>>(
+        V, ld, nv, w, c->sv.chunks, c->sv.nchunks, c->sv.dpart, fused ? c->sv.ticket : nullptr, c->sv.cell_chunks,
+        c->ncell, h, c->cells, fac);
+    BIE_LAUNCH(c, "k_dots");
+    if (!fused) {
+        k_fin<<<(nv * c->ncell * 32 + 255) / 256, 256, 0, c->stream>>>(c->sv.dpart, c->sv.nchunks, nv,
+                                                                     c->sv.cell_chunks, c->ncell, h, c->cells, fac);
+        BIE_LAUNCH(c, "k_fin");
+    }
+    return BIE_OK;
 }
 
 // dst = a[cell] src; a zero factor writes zeros (switched-off cells)
@@ -193,7 +187,7 @@ __global__ void k_combine(const double* __restrict__ V, size_t ld, int nv, const
 // Per-cell 2-norms of v.
 static int dnorms(bie_ctx* c, const double* v, std::vector<double>& out) {
     double* d = c->sv.fac + c->ncell;  // ncell scratch after the normalisation factors
-    if (int rc = mdot(c, v, 0, 1, v, d)) return rc;
+    if (int rc = mdots(c, v, 0, 1, v, d, nullptr)) return rc;
     out.resize(c->ncell);
     BIE_CUDA(c, cudaMemcpyAsync(out.data(), d, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -267,16 +261,15 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
         double* h1 = hb;
         double* h2 = hb + (size_t)(k + 1) * nc;
         double* hn = hb + 2 * (size_t)(k + 1) * nc;
-        const int nb = c->sv.nchunks;
-        k_ortho<0><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, nullptr, c->sv.chunks, nb, c->sv.cell_chunks, nc,
-                                              c->sv.dpart, h1, c->sv.ticket, c->cells, nullptr);
-        BIE_LAUNCH(c, "k_ortho<0>");
-        k_ortho<1><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, h1, c->sv.chunks, nb, c->sv.cell_chunks, nc,
-                                              c->sv.dpart, h2, c->sv.ticket, c->cells, nullptr);
-        BIE_LAUNCH(c, "k_ortho<1>");
-        k_ortho<2><<<nb, 256, 0, c->stream>>>(V, ld, k + 1, w, h2, c->sv.chunks, nb, c->sv.cell_chunks, nc,
-                                              c->sv.dpart, hn, c->sv.ticket, c->cells, fac_d);
-        BIE_LAUNCH(c, "k_ortho<2>");
+        // CGS2: two projections, then the norm and the normalisation factor
+        const int gu = (int)((8LL * n + 255) / 256);
+        if (int rc = mdots(c, V, ld, k + 1, w, h1, nullptr)) return rc;
+        k_update<<<gu, 256, 0, c->stream>>>(V, ld, k + 1, h1, nc, c->node_cell, w, n);
+        BIE_LAUNCH(c, "k_update");
+        if (int rc = mdots(c, V, ld, k + 1, w, h2, nullptr)) return rc;
+        k_update<<<gu, 256, 0, c->stream>>>(V, ld, k + 1, h2, nc, c->node_cell, w, n);
+        BIE_LAUNCH(c, "k_update");
+        if (int rc = mdots(c, w, 0, 1, w, hn, fac_d)) return rc;
         k_scale_copy<<<gs, bs, 0, c->stream>>>(w, fac_d, c->node_cell, V + (size_t)(k + 1) * ld, n);
         BIE_LAUNCH(c, "k_scale_copy");
         BIE_CUDA(c, cudaMemcpyAsync(c->sv.pinned + (size_t)(k & 1) * slot, hb,
