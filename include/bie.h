@@ -49,6 +49,10 @@ extern "C" {
                        significands) on the FP32 pipe; everything else in double */
 
 typedef struct bie_ctx bie_ctx;
+typedef struct bie_net bie_net;
+
+#define BIE_NET_FEATURES 13 /* node features of the warm-start network (bie_features) */
+#define BIE_NET_HIDDEN 64   /* its hidden width */
 
 /* Lattice vectors e1, e2 and the centre of the unit cell U (Sec. 2). */
 typedef struct {
@@ -88,7 +92,10 @@ typedef struct {
     int32_t gmres_max;    /* maximum Krylov dimension of one GMRES cycle, 1..1000 */
     double inner_tol;     /* relative tolerance of each single-precision inner solve (BIE_MIXED) */
     int32_t max_refine;   /* maximum outer refinement sweeps (BIE_MIXED) */
-    int32_t warm_start;   /* bie_step initial guess: 0 = zero, 1 = previous step's density */
+    int32_t warm_start;   /* bie_step start: 0 = zero; 1 = previous step's density as the initial
+                             guess; 2 = zero start, first GMRES cycle augmented with the previous
+                             density, its last change and the warm-start network's predicted change
+                             (bie_set_warm_net); 3 = as 2 without the network */
     double min_gap;       /* bie_step fails with BIE_ECOLLIDE below this body gap (node-sampled); 0 = off */
     int32_t device;       /* CUDA device ordinal */
     double close_factor;  /* close-evaluation zone in units of the source body's node spacing
@@ -232,6 +239,57 @@ int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, co
  * on each device looks up the array's device address; make that first call
  * before any stream capture. */
 int bie_apply_static(bie_ctx* ctx, const double* sigma, double* out);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper).  A per-node multilayer
+ * perceptron, x (BIE_NET_FEATURES) -> tanh(W1 x + b1) -> tanh(W2 . + b2) ->
+ * W3 . + b3 (2 outputs), hidden width BIE_NET_HIDDEN, predicts the change of
+ * the density over one time step in units of mu |gamma| dt from local features
+ * (bie_features).  Parameters: one float array, W1 (row-major), b1, W2, b2,
+ * W3, b3.  The kernels read bfloat16 weights and compute in FP32; training
+ * keeps FP32 master weights and Adam moments.  With warm_start = 2, bie_step
+ * adds the prediction to the directions of the first GMRES cycle's search
+ * space (see bie_opts.warm_start), so the GMRES residual test at gmres_tol
+ * still decides convergence.
+ * ---------------------------------------------------------------------- */
+
+/* Create a network with n_in inputs (1..16) on a device; parameters are zero
+ * until bie_net_set_params.  Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA. */
+int bie_net_init(bie_net** net, int32_t n_in, int32_t device);
+void bie_net_destroy(bie_net* net);
+const char* bie_net_last_error(const bie_net* net);
+/* inputs, hidden width and parameter count */
+int bie_net_size(const bie_net* net, int32_t* n_in, int32_t* hidden, int32_t* n_params);
+int bie_net_set_stream(bie_net* net, void* stream);
+/* Host float arrays of n_params entries; set also clears the Adam state. */
+int bie_net_set_params(bie_net* net, const float* params);
+int bie_net_get_params(bie_net* net, float* params);
+/* Y (N x 2) = net(X (N x n_in)); device pointers, row-major floats. */
+int bie_net_forward(bie_net* net, const float* X, int32_t N, float* Y);
+/* Loss L = sum_i W_i |net(X_i) - T_i|^2 / sum_i W_i over N nodes (device
+ * pointers: X N x n_in, T N x 2, W N) and its gradient.  grad (host, n_params
+ * floats) may be NULL; the gradient is kept for bie_net_adam_step; loss (host)
+ * may be NULL. */
+int bie_net_loss_grad(bie_net* net, const float* X, const float* T, const float* W, int32_t N, float* grad,
+                      double* loss);
+/* One Adam step (Kingma & Ba, bias-corrected) with the last gradient. */
+int bie_net_adam_step(bie_net* net, double lr, double beta1, double beta2, double eps);
+
+/* The context's BIE_NET_FEATURES node features (N x BIE_NET_FEATURES floats,
+ * row-major) for the current geometry and the stored densities of the last
+ * two solves: normal (2), curvature x h_b, (x - x^c) / max(a, b) (2), last
+ * density / (mu |gamma|) (2), its last change / (mu |gamma| dt) (2, dt the
+ * last bie_step's step), log(d / h_b) with d the distance to the nearest
+ * other curve within the close zone (else the zone's edge), the unit vector
+ * towards it (2), and log(d_prev / d) / (|gamma| dt) (0 if unknown).  Host
+ * pointer unless on_device.  The network's outputs are read as the density
+ * change over the next step in units of mu |gamma| dt. */
+int bie_features(bie_ctx* ctx, float* X, int32_t on_device);
+
+/* Attach (or detach with NULL) the warm-start network used by warm_start = 2.
+ * It must take BIE_NET_FEATURES inputs and live on the context's device; the
+ * caller keeps ownership and must not destroy it while attached. */
+int bie_set_warm_net(bie_ctx* ctx, const bie_net* net);
 
 /* Close-evaluation bookkeeping of the current geometry: number of stored
  * (target, body image) pairs, and pairs closer to the curve than the finest

@@ -22,6 +22,9 @@ slow and as literal as the paper's definitions allow:
                    fix (Eq. BIEdiscretized, Sec. 5, Sec. 6.2 remark), GMRES,
                    velocity extraction, effective viscosity and forward Euler
                    (Sec. 3, Sec. 7).
+* ``mlp``       -- the warm-start network (no counterpart in the paper): a
+                   per-node perceptron, its loss gradient and Adam, from their
+                   definitions.
 
 Pins against values fixed by the paper and by the mathematics live in
 ``tests/test_oracle_*.py``.

@@ -10,9 +10,12 @@ The functions carry the C names:
     bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
     bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read,
-    bie_apply_static, bie_init_batch, bie_cells
+    bie_apply_static, bie_init_batch, bie_cells, bie_features, bie_set_warm_net,
+    bie_net_init, bie_net_destroy, bie_net_last_error, bie_net_size,
+    bie_net_set_stream, bie_net_set_params, bie_net_get_params,
+    bie_net_forward, bie_net_loss_grad, bie_net_adam_step
 and `Context` wraps them for a workload dict, or a list of them for a batch
-of independent cells (see workloads.py).
+of independent cells (see workloads.py); `Net` wraps the warm-start network.
 """
 import ctypes
 import os
@@ -24,6 +27,7 @@ LIB_PATH = os.path.join(HERE, "libbie.so")
 
 BIE_OK, BIE_EINVAL, BIE_ENOCONV, BIE_ECOLLIDE, BIE_ENUMERIC, BIE_ECUDA, BIE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 BIE_FP64, BIE_MIXED, BIE_DF64 = 0, 1, 2
+BIE_NET_FEATURES, BIE_NET_HIDDEN = 13, 64
 _NAMES = {0: "BIE_OK", -1: "BIE_EINVAL", -2: "BIE_ENOCONV", -3: "BIE_ECOLLIDE", -4: "BIE_ENUMERIC",
           -5: "BIE_ECUDA", -6: "BIE_ENOMEM"}
 
@@ -110,6 +114,18 @@ def library():
         "bie_apply_static": (c_int32, [vp, vp, vp]),
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
+        "bie_features": (c_int32, [vp, vp, c_int32]),
+        "bie_set_warm_net": (c_int32, [vp, vp]),
+        "bie_net_init": (c_int32, [ctypes.POINTER(vp), c_int32, c_int32]),
+        "bie_net_destroy": (None, [vp]),
+        "bie_net_last_error": (ctypes.c_char_p, [vp]),
+        "bie_net_size": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+        "bie_net_set_stream": (c_int32, [vp, vp]),
+        "bie_net_set_params": (c_int32, [vp, vp]),
+        "bie_net_get_params": (c_int32, [vp, vp]),
+        "bie_net_forward": (c_int32, [vp, vp, c_int32, vp]),
+        "bie_net_loss_grad": (c_int32, [vp, vp, vp, vp, c_int32, vp, ctypes.POINTER(c_double)]),
+        "bie_net_adam_step": (c_int32, [vp, c_double, c_double, c_double, c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -125,7 +141,10 @@ def exported_symbols():
     return [n for n in ("bie_default_opts", "bie_init", "bie_destroy", "bie_last_error", "bie_size",
                         "bie_set_stream", "bie_nodes", "bie_apply", "bie_rhs", "bie_solve", "bie_velocities",
                         "bie_step", "bie_get_state", "bie_set_state", "bie_close_info", "bie_profile",
-                        "bie_profile_read", "bie_apply_static", "bie_init_batch", "bie_cells")
+                        "bie_profile_read", "bie_apply_static", "bie_init_batch", "bie_cells", "bie_features",
+                        "bie_set_warm_net", "bie_net_init", "bie_net_destroy", "bie_net_last_error",
+                        "bie_net_size", "bie_net_set_stream", "bie_net_set_params", "bie_net_get_params",
+                        "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step")
             if hasattr(L, n)]
 
 
@@ -297,6 +316,21 @@ class Context:
         self._check(library().bie_apply_static(self.h, ps, po))
         return out
 
+    def features(self, out=None):
+        """Node features (N x BIE_NET_FEATURES float32) of the current geometry
+        and stored densities; into a device tensor `out` if given."""
+        if out is None:
+            X = np.zeros((self.N, BIE_NET_FEATURES), dtype=np.float32)
+            self._check(library().bie_features(self.h, X.ctypes.data, 0))
+            return X
+        self._check(library().bie_features(self.h, out.data_ptr(), 1))
+        return out
+
+    def set_warm_net(self, net):
+        """Attach a Net for warm_start = 2 (None detaches)."""
+        self._warm_net = net
+        self._check(library().bie_set_warm_net(self.h, None if net is None else net.h))
+
     def close_info(self):
         n, u = c_int32(), c_int32()
         self._check(library().bie_close_info(self.h, ctypes.byref(n), ctypes.byref(u)))
@@ -319,3 +353,69 @@ class Context:
         sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64).ravel()
         self._check(library().bie_set_state(self.h, float(t), e2.ctypes.data, xc.ctypes.data, th.ctypes.data,
                                             None if sg is None else sg.ctypes.data))
+
+
+class Net:
+    """The warm-start network (bie_net_*): forward, loss gradient and Adam on
+    device tensors (torch float32, contiguous)."""
+
+    def __init__(self, n_in=BIE_NET_FEATURES, device=0):
+        L = library()
+        h = c_void_p()
+        rc = L.bie_net_init(ctypes.byref(h), n_in, device)
+        if rc != 0:
+            raise BieError(rc, "bie_net_init failed")
+        self.h = h
+        ni, hid, npar = c_int32(), c_int32(), c_int32()
+        L.bie_net_size(h, ctypes.byref(ni), ctypes.byref(hid), ctypes.byref(npar))
+        self.n_in, self.hidden, self.n_params = ni.value, hid.value, npar.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise BieError(rc, library().bie_net_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().bie_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        self._check(library().bie_net_set_params(self.h, p.ctypes.data))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        self._check(library().bie_net_get_params(self.h, p.ctypes.data))
+        return p
+
+    @staticmethod
+    def _dev(t, cols):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()):
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        if cols and (t.dim() != 2 or t.shape[1] != cols):
+            raise ValueError(f"expected shape (N, {cols})")
+        return t.data_ptr()
+
+    def forward(self, X, Y):
+        self._check(library().bie_net_forward(self.h, self._dev(X, self.n_in), X.shape[0], self._dev(Y, 2)))
+        return Y
+
+    def loss_grad(self, X, T, W, with_grad=True):
+        g = np.zeros(self.n_params, dtype=np.float32) if with_grad else None
+        loss = c_double()
+        self._check(library().bie_net_loss_grad(self.h, self._dev(X, self.n_in), self._dev(T, 2), self._dev(W, 0),
+                                                X.shape[0], None if g is None else g.ctypes.data,
+                                                ctypes.byref(loss)))
+        return loss.value, g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(library().bie_net_adam_step(self.h, lr, beta1, beta2, eps))

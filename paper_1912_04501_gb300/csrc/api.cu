@@ -36,7 +36,8 @@ static void free_all(bie_ctx* c) {
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
                     c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.dpart,
                     c->sv.chunks,
-                    c->sv.cell_chunks, c->sv.sigma_prev, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
+                    c->sv.cell_chunks, c->sv.sigma_prev, c->sv.sigma_prev2, c->sv.aug,
+                    c->sv.feat, c->sv.pred, c->cl.dmin, c->cl.dmin_prev, c->cl.ddir, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
                     c->cl.blk_off, c->cl.blocks, c->cl.blocks32, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
                     c->near[1].items, c->near[2].items};
     for (void* p : ptrs)
@@ -97,6 +98,64 @@ static void lattice_at(const bie_ctx* c, int cell, double t, double* e2) {
     sx -= L1 * std::round(sx / L1);
     e2[0] = sx;
     e2[1] = c->e2_0[2 * cell + 1];
+}
+
+// out = a - b (vectors of n doubles)
+__global__ void k_diff(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] - b[i];
+}
+
+// network output (predicted density change / (mu |gamma| dt), N x 2 floats)
+// -> a density direction in the solver's units
+__global__ void k_pred_to_density(const float* __restrict__ pred, const int* __restrict__ node_cell,
+                                  const Cell* __restrict__ cells, int N, double dt, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const Cell& cl = cells[node_cell[i]];
+    const double s = cl.mu * fabs(cl.gamma) * dt;
+    out[2 * i] = s * pred[2 * i];
+    out[2 * i + 1] = s * pred[2 * i + 1];
+}
+
+// Keep the last two densities: sigma_prev2 <- sigma_prev <- x.
+static int push_density(bie_ctx* c, const double* x) {
+    const size_t n2 = 2 * (size_t)c->N;
+    if (c->sv.have_prev)
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev2, c->sv.sigma_prev, n2 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    c->sv.have_prev2 = c->sv.have_prev;
+    BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, x, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->sv.have_prev = true;
+    return BIE_OK;
+}
+
+// The augmentation directions of the next solve (warm_start 2 and 3): the
+// previous density, its change over the last step, and (2) the network's
+// predicted change.  Returns their number.
+static int prepare_aug(bie_ctx* c, double dt, int* nu) {
+    *nu = 0;
+    const int mode = c->opts.warm_start;
+    if ((mode != 2 && mode != 3) || !c->sv.have_prev) return BIE_OK;
+    const size_t n2 = 2 * (size_t)c->N;
+    double* U = c->sv.aug;
+    BIE_CUDA(c, cudaMemcpyAsync(U, c->sv.sigma_prev, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    *nu = 1;
+    if (c->sv.have_prev2) {
+        k_diff<<<(int)((n2 + 255) / 256), 256, 0, c->stream>>>(c->sv.sigma_prev, c->sv.sigma_prev2,
+                                                                U + (size_t)(*nu) * n2, (int)n2);
+        BIE_LAUNCH(c, "k_diff");
+        ++*nu;
+    }
+    if (mode == 2 && c->net) {
+        if (int rc = features_device(c, c->sv.feat)) return rc;
+        if (int rc = net_forward_async(c, c->net, c->sv.feat, c->N, c->sv.pred)) return rc;
+        k_pred_to_density<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->sv.pred, c->node_cell, c->cells, c->N, dt,
+                                                                      U + (size_t)(*nu) * n2);
+        BIE_LAUNCH(c, "k_pred_to_density");
+        ++*nu;
+    }
+    return BIE_OK;
 }
 
 // Move and rotate every body by (v, omega) dt and wrap its centroid into its
@@ -196,6 +255,7 @@ static int check_opts(const bie_opts& o, std::string& why) {
         why = "non-positive tolerance or radius";
     else if (o.gmres_max < 1 || o.gmres_max > 1000 || o.max_refine < 1) why = "gmres_max / max_refine out of range";
     else if (o.residual != BIE_FP64 && o.residual != BIE_DF64) why = "residual must be BIE_FP64 or BIE_DF64";
+    else if (o.warm_start < 0 || o.warm_start > 3) why = "warm_start must be 0, 1, 2 or 3";
     else if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
         why = "close_factor must be in [0, 100], close_capacity >= 0";
     else return 0;
@@ -365,21 +425,32 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     if (!rc) rc = cu(cudaMemset(c->sv.ticket, 0, sizeof(unsigned int)), "cudaMemset");
     rc = rc ? rc : dalloc(c, &c->ws.T, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.vpart, nbs * kVelSplits * 3);
-    rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1) * 2 * n);
+    rc = rc ? rc : dalloc(c, &c->sv.V, (size_t)(kk + 1 + 2 * kMaxAug) * 2 * n);
     rc = rc ? rc : dalloc(c, &c->sv.w, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.r, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.x, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.b, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.d, 2 * (size_t)n);
     {
-        const size_t slot = (2 * (size_t)(kk + 1) + 1) * nc;
-        rc = rc ? rc : dalloc(c, &c->sv.h, 2 * slot + (size_t)kk * nc);
-        rc = rc ? rc : dalloc(c, &c->sv.fac, 2 * nc);
+        const size_t slot = (2 * (size_t)(kk + 1 + kMaxAug) + 1) * nc;
+        rc = rc ? rc : dalloc(c, &c->sv.h, 2 * slot + (size_t)(kk + kMaxAug) * nc);
+        rc = rc ? rc : dalloc(c, &c->sv.fac, (2 + (size_t)kMaxAug) * nc);
         if (!rc) rc = cu(cudaMallocHost((void**)&c->sv.pinned, 2 * slot * sizeof(double)), "cudaMallocHost");
         for (int e = 0; e < 2 && !rc; ++e)
             rc = cu(cudaEventCreateWithFlags(&c->sv.ev[e], cudaEventDisableTiming), "cudaEventCreate");
     }
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.sigma_prev2, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->sv.aug, (size_t)kMaxAug * 2 * n);
+    rc = rc ? rc : dalloc(c, &c->sv.feat, (size_t)kNetFeatures * n);
+    rc = rc ? rc : dalloc(c, &c->sv.pred, 2 * (size_t)n);
+    rc = rc ? rc : dalloc(c, &c->cl.dmin, n);
+    rc = rc ? rc : dalloc(c, &c->cl.dmin_prev, n);
+    rc = rc ? rc : dalloc(c, &c->cl.ddir, n);
+    // "no nearby curve" until the first close-pair detection (0x7f7f7f7f ~ 3.4e38)
+    if (!rc) rc = cu(cudaMemset(c->cl.dmin, 0x7f, n * sizeof(float)), "cudaMemset");
+    if (!rc) rc = cu(cudaMemset(c->cl.dmin_prev, 0x7f, n * sizeof(float)), "cudaMemset");
+    if (!rc) rc = cu(cudaMemset(c->cl.ddir, 0, n * sizeof(float2)), "cudaMemset");
     {
         int maxn = 0;
         for (int v : c->n_nodes) maxn = std::max(maxn, v);
@@ -578,8 +649,7 @@ int bie_solve(bie_ctx* c, const double* rhs, double* sigma, int32_t use_guess, i
     if (src && src != BIE_ENOCONV) return src;
     BIE_CUDA(c, cudaMemcpyAsync(sigma, c->sv.x, n2 * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, c->sv.x, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    c->sv.have_prev = true;
+    if ((rc = push_density(c, c->sv.x))) return rc;
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return src;
 }
@@ -630,19 +700,20 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         if (guess)
             BIE_CUDA(c, cudaMemcpyAsync(c->sv.x, c->sv.sigma_prev, n2 * sizeof(double), cudaMemcpyDeviceToDevice,
                                         c->stream));
+        int nu = 0;
+        if ((rc = prepare_aug(c, dt, &nu))) return rc;
         bie_solve_info inf{};
-        rc = solve_device(c, c->sv.b, c->sv.x, guess, &inf);
+        rc = solve_device(c, c->sv.b, c->sv.x, guess, &inf, nu ? c->sv.aug : nullptr, nu);
         if (info) *info = inf;
         if (rc) return rc;
-        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, c->sv.x, n2 * sizeof(double), cudaMemcpyDeviceToDevice,
-                                    c->stream));
-        c->sv.have_prev = true;
+        if ((rc = push_density(c, c->sv.x))) return rc;
         rc = velocities_device(c, c->sv.x, dv, dom, dmu);
         if (rc) return rc;
         if (mu_eff_out)
             BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + (size_t)s * c->ncell, dmu, c->ncell * sizeof(double),
                                         cudaMemcpyDeviceToHost, c->stream));
         c->t += dt;
+        c->sv.dt_prev = dt;
         for (int k = 0; k < c->ncell; ++k) {
             Cell& cl = c->cells_h[k];
             const double e1[2] = {cl.e1[0], cl.e1[1]};
@@ -659,6 +730,8 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         std::swap(c->wall, c->next.wall);
         std::swap(c->e2d, c->next.e2);
         if ((rc = build_geometry(c))) return rc;
+        std::swap(c->cl.dmin, c->cl.dmin_prev);
+        c->cl.have_dprev = true;
         if ((rc = build_close(c))) return rc;
         if (c->opts.min_gap > 0 && c->cl.min_gap < c->opts.min_gap) {
             char msg[160];
@@ -729,8 +802,30 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     } else {
         c->sv.have_prev = false;
     }
+    c->sv.have_prev2 = false;
+    c->cl.have_dprev = false;
     rc = rebuild(c);
     if (rc) return rc;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_set_warm_net(bie_ctx* c, const bie_net* net) {
+    if (!c) return BIE_EINVAL;
+    if (net && net_inputs(net) != kNetFeatures)
+        return fail(c, BIE_EINVAL, "the warm-start network must take " + std::to_string(kNetFeatures) + " inputs");
+    c->net = net;
+    return BIE_OK;
+}
+
+int bie_features(bie_ctx* c, float* X, int32_t on_device) {
+    if (!c || !X) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    int rc = features_device(c, on_device ? X : c->sv.feat);
+    if (rc) return rc;
+    if (!on_device)
+        BIE_CUDA(c, cudaMemcpyAsync(X, c->sv.feat, (size_t)kNetFeatures * c->N * sizeof(float),
+                                    cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
 }

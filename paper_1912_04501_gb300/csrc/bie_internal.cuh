@@ -57,6 +57,10 @@ constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
 constexpr int kMaxCells = 4096;
+constexpr int kNetHidden = 64;        // hidden width of the warm-start network
+constexpr int kNetMaxIn = 16;         // its maximum number of inputs per node
+constexpr int kNetFeatures = 13;      // node features of the warm start (features_device)
+constexpr int kMaxAug = 3;            // augmentation directions of the first GMRES cycle
 
 // One unit cell of the batch (device table; the host keeps a mirror).
 struct Cell {
@@ -89,6 +93,10 @@ struct Close {
     int npairs = 0;
     int under_resolved = 0;       // pairs closer than the finest rule (rho = 64) resolves
     double min_gap = 0;           // smallest node-to-curve gap below opts.min_gap (else infinity)
+    float* dmin = nullptr;        // N: distance to the nearest other curve within the zone (else huge)
+    float* dmin_prev = nullptr;   // N: the same for the previous geometry
+    float2* ddir = nullptr;       // N: unit vector towards that nearest point (0 if none)
+    bool have_dprev = false;
     size_t shm_limit = 0;
 };
 
@@ -128,24 +136,29 @@ struct ProxyFit {
 
 struct Solver {
     int kmax = 0;
-    double* V = nullptr;     // (kmax + 1) x 2N Krylov basis
+    double* V = nullptr;     // (kmax + 1 + 2 kMaxAug) x 2N: [C~ | Krylov basis | U~]
     double* w = nullptr;     // 2N
     double* r = nullptr;     // 2N
     double* x = nullptr;     // 2N current solution
     double* b = nullptr;     // 2N right-hand side
     double* d = nullptr;     // 2N correction (mixed)
-    double* h = nullptr;     // 2 slots of (2 (kmax + 1) + 1) x ncell Hessenberg entries, then
-                             // kmax x ncell combination coefficients
+    double* h = nullptr;     // 2 slots of (2 (kmax + 1 + kMaxAug) + 1) x ncell projections, then
+                             // (kmax + kMaxAug) x ncell combination coefficients
     double* pinned = nullptr;  // host (page-locked): 2 slots, as on the device
-    double* fac = nullptr;   // 2 x ncell: normalisation factors, then per-cell norms
+    double* fac = nullptr;   // (2 + kMaxAug) x ncell: normalisation factors, per-cell norms, scratch
     cudaEvent_t ev[2] = {nullptr, nullptr};  // slot k % 2 copied to the host
     unsigned int* ticket = nullptr;  // last-block counter of k_dots (zero between launches)
     double* dpart = nullptr; // (kmax + 2) x nchunks partial dot products
     int4* chunks = nullptr;  // nchunks: (cell, first entry, end entry, 0)
     int2* cell_chunks = nullptr;  // ncell: (first chunk, chunk count)
     int nchunks = 0;
-    double* sigma_prev = nullptr;  // 2N warm start of the next step
-    bool have_prev = false;
+    double* sigma_prev = nullptr;  // 2N the last step's density (warm start of the next)
+    double* sigma_prev2 = nullptr; // 2N the density of the step before
+    bool have_prev = false, have_prev2 = false;
+    double dt_prev = 0;            // the last time step (scales the change features)
+    double* aug = nullptr;         // kMaxAug x 2N augmentation directions of the next step
+    float* feat = nullptr;         // N x kNetFeatures node features
+    float* pred = nullptr;         // N x 2 network output
     std::vector<bie_solve_info> cell_info;  // last solve, per cell
 };
 
@@ -196,6 +209,7 @@ struct bie_ctx {
     bie::Solver sv;
     bie::Close cl;
     bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
+    const bie_net* net = nullptr;  // warm-start network (not owned)
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
     long long launches = 0;
@@ -261,8 +275,17 @@ int rhs_device(bie_ctx* c, double* b);
 // per body v (2 nb), omega (nb); per cell mu_eff (ncell)
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff);
 
+// net.cu --------------------------------------------------------------------
+int net_forward_async(bie_ctx* c, const bie_net* n, const float* X, int N, float* Y);
+int net_inputs(const bie_net* n);
+// N x kNetFeatures node features of the current geometry and stored densities
+int features_device(bie_ctx* c, float* X);
+
 // solve.cu ------------------------------------------------------------------
-int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info);
+// U: nu augmentation directions (2N each) for the first GMRES cycle when
+// starting from zero (use_guess false); may be null
+int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info,
+                 const double* U = nullptr, int nu = 0);
 int build_dot_chunks(bie_ctx* c);
 
 // small device math shared by the kernels --------------------------------------

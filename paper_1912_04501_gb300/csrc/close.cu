@@ -52,13 +52,15 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
                                const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                                double close_factor, double gap_lim, int kmax, int4* __restrict__ slots,
                                int* __restrict__ count, int* __restrict__ overflow,
-                               unsigned long long* __restrict__ gap_min) {
+                               unsigned long long* __restrict__ gap_min, float* __restrict__ dmin,
+                               float2* __restrict__ ddir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Cell& sh = cells[node_cell[i]];
     double X = x[i], Y = y[i];
     int own = owner[i];
     int c = 0;
+    double dbest = INFINITY, dirx = 0, diry = 0;  // nearest other curve (or own periodic image)
     for (int b = sh.body_off; b < sh.body_off + sh.n_bodies; ++b) {
         const double* bd = body + 8 * b;
         double R = fmax(bd[0], bd[1]);
@@ -100,6 +102,13 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
                 sincos(t, &sn, &cs);
                 dcur = sqrt((a * cs - u) * (a * cs - u) + (b2 * sn - v) * (b2 * sn - v));
                 hloc = 2.0 * kPi * sqrt(a * a * sn * sn + b2 * b2 * cs * cs) / n;
+                if (dcur < dbest && dcur > 0) {
+                    // direction from the target to the closest point, back in the lab frame
+                    const double ex = (a * cs - u) / dcur, ey = (b2 * sn - v) / dcur;
+                    dbest = dcur;
+                    dirx = ct * ex - st * ey;
+                    diry = st * ex + ct * ey;
+                }
             }
             if (dcur < gap_lim) atomicMin(gap_min, (unsigned long long)__double_as_longlong(dcur));
             if (!(sqrt(d2) < zone)) continue;
@@ -119,6 +128,8 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
         c = kmax;
     }
     count[i] = c;
+    dmin[i] = (float)dbest;
+    ddir[i] = make_float2((float)dirx, (float)diry);
 }
 
 // Exclusive scan (one CTA) of the per-target pair counts and of the block
@@ -340,7 +351,8 @@ int build_close(bie_ctx* c) {
     BIE_CUDA(c, cudaMemsetAsync(gap_min, 0xFF, sizeof(unsigned long long), c->stream));
     k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->node_cell, c->cells, N,
                                                          c->opts.close_factor, gap_lim, kmax, c->cl.slots,
-                                                         c->cl.count, c->cl.flags + 2, gap_min);
+                                                         c->cl.count, c->cl.flags + 2, gap_min, c->cl.dmin,
+                                                         c->cl.ddir);
     BIE_LAUNCH(c, "k_close_detect");
     k_close_scan<<<1, 1024, 0, c->stream>>>(c->cl.count, N, kmax, c->cl.slots, c->body, c->cl.pair_base,
                                            c->cl.blk_off, c->cl.pairs, c->cl.flags, c->cl.cap_doubles,

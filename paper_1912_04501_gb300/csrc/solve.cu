@@ -45,7 +45,7 @@ int build_dot_chunks(bie_ctx* c) {
     c->sv.nchunks = (int)ch.size();
     BIE_CUDA(c, cudaMalloc((void**)&c->sv.chunks, ch.size() * sizeof(int4)));
     BIE_CUDA(c, cudaMalloc((void**)&c->sv.cell_chunks, cc.size() * sizeof(int2)));
-    BIE_CUDA(c, cudaMalloc((void**)&c->sv.dpart, (size_t)(c->sv.kmax + 2) * ch.size() * sizeof(double)));
+    BIE_CUDA(c, cudaMalloc((void**)&c->sv.dpart, (size_t)(c->sv.kmax + 2 + kMaxAug) * ch.size() * sizeof(double)));
     BIE_CUDA(c, cudaMemcpy(c->sv.chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice));
     BIE_CUDA(c, cudaMemcpy(c->sv.cell_chunks, cc.data(), cc.size() * sizeof(int2), cudaMemcpyHostToDevice));
     return BIE_OK;
@@ -206,11 +206,56 @@ static int set_active(bie_ctx* c, const std::vector<char>& on) {
     return changed ? upload_cells(c, c->stream) : BIE_OK;
 }
 
+// Orthonormalise the nu augmentation directions per cell: C~ = A U~ with
+// orthonormal columns (classical Gram-Schmidt twice, the same operations on U
+// so that A U~ = C~ stays exact up to rounding).  A direction whose image is
+// (numerically) in the span of the earlier ones, or zero, is dropped (scaled
+// to zero).  Ct and Ut hold A U and U on entry.
+static int orthonormalise_aug(bie_ctx* c, double* Ct, double* Ut, int nu) {
+    const int n = 2 * c->N, nc = c->ncell;
+    const size_t ld = (size_t)n;
+    const int gu = (int)((8LL * n + 255) / 256), gs = (n + 255) / 256;
+    double* hq = c->sv.fac + 2 * (size_t)nc;  // kMaxAug x ncell scratch
+    for (int i = 0; i < nu; ++i) {
+        double* ci = Ct + (size_t)i * ld;
+        double* ui = Ut + (size_t)i * ld;
+        std::vector<double> n0, n1;
+        if (int rc = dnorms(c, ci, n0)) return rc;
+        for (int pass = 0; pass < 2 && i > 0; ++pass) {
+            if (int rc = mdots(c, Ct, ld, i, ci, hq, nullptr)) return rc;
+            k_update<<<gu, 256, 0, c->stream>>>(Ct, ld, i, hq, nc, c->node_cell, ci, n);
+            BIE_LAUNCH(c, "k_update");
+            k_update<<<gu, 256, 0, c->stream>>>(Ut, ld, i, hq, nc, c->node_cell, ui, n);
+            BIE_LAUNCH(c, "k_update");
+        }
+        if (int rc = dnorms(c, ci, n1)) return rc;
+        std::vector<double> f(nc);
+        for (int q = 0; q < nc; ++q)
+            f[q] = (std::isfinite(n1[q]) && n1[q] > 1e-10 * n0[q] && n1[q] > 0) ? 1.0 / n1[q] : 0.0;
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.fac, f.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        k_scale_copy<<<gs, 256, 0, c->stream>>>(ci, c->sv.fac, c->node_cell, ci, n);
+        BIE_LAUNCH(c, "k_scale_copy");
+        k_scale_copy<<<gs, 256, 0, c->stream>>>(ui, c->sv.fac, c->node_cell, ui, n);
+        BIE_LAUNCH(c, "k_scale_copy");
+    }
+    return BIE_OK;
+}
+
 // One GMRES cycle per cell on A_prec x = b from the current x (device),
 // in lockstep.  r holds b - A x on entry with per-cell norms beta (cells with
 // beta = 0 do not take part).  Cell k stops when its Arnoldi residual
 // estimate is <= atol[k] or after kmax steps; its iteration count goes to
 // it[k] and its estimate to est[k].  *n_apply counts operator applications.
+//
+// Augmentation (nu > 0 directions U, 2N each, the same for all cells): the
+// correction is sought in span(U) + K_k(A', r'), with C~ = A U~ orthonormal,
+// r' = r - C~ C~^T r and A' = (I - C~ C~^T) A (a fixed recycled space, as in
+// GCRO).  C~ occupies the first nu columns of the basis, so the Gram-Schmidt
+// passes project it out of every new vector (A V_k = C~ B_k + V_{k+1} H_k);
+// with y the usual GMRES coefficients, the update is V y + U~ (C~^T r - B y)
+// and the residual is the usual GMRES residual of the projected system.
+// Directions that predict the solution well leave a small r'; directions
+// that do not only cost their applications.
 //
 // Pipelining: iteration k+1 (operator application, CGS2, normalisation of
 // the next basis vector with the norm computed on the device) is enqueued
@@ -219,27 +264,61 @@ static int set_active(bie_ctx* c, const std::vector<char>& on) {
 // When the last cell converges at iteration k, iteration k+1 has already
 // run and is discarded; a cell that converges is switched off from
 // iteration k+2 on.
-static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const std::vector<double>& beta,
+static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const std::vector<double>& beta_in,
                        const std::vector<double>& atol, std::vector<int>& it, std::vector<double>& est,
-                       int* n_apply) {
+                       int* n_apply, const double* U = nullptr, int nu = 0) {
     const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
     const int kmax = c->sv.kmax;
     const size_t ld = (size_t)n;
-    const size_t slot = (2 * (size_t)(kmax + 1) + 1) * nc;  // h1, h2, norm of one iteration
-    double* V = c->sv.V;
+    const size_t slot = (2 * (size_t)(kmax + 1 + kMaxAug) + 1) * nc;  // h1, h2, norm of one iteration
+    double* V = c->sv.V;             // [C~ (nu) | Krylov vectors (kmax + 1) | U~ (nu)]
+    double* Vk = V + (size_t)nu * ld;
+    double* Ut = Vk + (size_t)(kmax + 1) * ld;
     double* w = c->sv.w;
     double* fac_d = c->sv.fac;
-    double* coef = c->sv.h + 2 * slot;  // kmax x nc combination coefficients
+    double* coef = c->sv.h + 2 * slot;  // (kmax + kMaxAug) x nc combination coefficients
+    std::vector<double> beta = beta_in;
+    std::vector<double> acoef((size_t)nu * nc, 0.0);  // C~^T r, per direction and cell
+    it.assign(nc, 0);
+    est.assign(nc, 0.0);
+    if (nu > 0) {
+        std::vector<char> on0(nc, 0);
+        for (int q = 0; q < nc; ++q) on0[q] = beta[q] > 0;
+        if (int rc = set_active(c, on0)) return rc;
+        for (int i = 0; i < nu; ++i) {
+            BIE_CUDA(c, cudaMemcpyAsync(Ut + (size_t)i * ld, U + (size_t)i * ld, ld * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            if (int rc = apply_device(c, Ut + (size_t)i * ld, V + (size_t)i * ld, prec)) return rc;
+            ++*n_apply;
+        }
+        if (int rc = orthonormalise_aug(c, V, Ut, nu)) return rc;
+        // r' = r - C~ (C~^T r), twice
+        const int gu = (int)((8LL * n + 255) / 256);
+        double* hq = c->sv.fac + 2 * (size_t)nc;
+        BIE_CUDA(c, cudaMemcpyAsync(w, r, ld * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        for (int pass = 0; pass < 2; ++pass) {
+            if (int rc = mdots(c, V, ld, nu, w, hq, nullptr)) return rc;
+            k_update<<<gu, 256, 0, c->stream>>>(V, ld, nu, hq, nc, c->node_cell, w, n);
+            BIE_LAUNCH(c, "k_update");
+            std::vector<double> hh((size_t)nu * nc);
+            BIE_CUDA(c, cudaMemcpyAsync(hh.data(), hq, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (size_t e = 0; e < hh.size(); ++e) acoef[e] += hh[e];
+        }
+        std::vector<double> b2;
+        if (int rc = dnorms(c, w, b2)) return rc;
+        for (int q = 0; q < nc; ++q) beta[q] = beta[q] > 0 ? b2[q] : 0.0;
+        r = w;
+    }
     std::vector<std::vector<double>> H(nc);  // packed columns: column k holds k + 1 entries
+    std::vector<std::vector<double>> Bc(nc); // C~^T A v_k: nu entries per column
     std::vector<std::vector<double>> cs(nc), sn(nc), g(nc);
     std::vector<char> on(nc, 0);
     std::vector<double> fac(nc, 0.0), hcol(kmax + 2);
-    it.assign(nc, 0);
-    est.assign(nc, 0.0);
     int n_on = 0;
     for (int k = 0; k < nc; ++k) {
-        if (beta[k] > 0) {
+        if (beta[k] > atol[k] || (nu == 0 && beta[k] > 0)) {
             on[k] = 1;
             ++n_on;
             fac[k] = 1.0 / beta[k];
@@ -247,49 +326,55 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
         }
         est[k] = beta[k];
     }
-    if (!n_on) return BIE_OK;
-    if (int rc = set_active(c, on)) return rc;
-    BIE_CUDA(c, cudaMemcpyAsync(fac_d, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    k_scale_copy<<<gs, bs, 0, c->stream>>>(r, fac_d, c->node_cell, V, n);
-    BIE_LAUNCH(c, "k_scale_copy");
-    // enqueue iteration k: w = A V_k, CGS2, V_{k+1} = w / |w| per cell, and
-    // the Hessenberg entries to the pinned host slot k % 2
+    if (n_on) {
+        if (int rc = set_active(c, on)) return rc;
+        BIE_CUDA(c, cudaMemcpyAsync(fac_d, fac.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        k_scale_copy<<<gs, bs, 0, c->stream>>>(r, fac_d, c->node_cell, Vk, n);
+        BIE_LAUNCH(c, "k_scale_copy");
+    }
+    // enqueue iteration k: w = A V_k, CGS2 against [C~, V_0 .. V_k],
+    // V_{k+1} = w / |w| per cell, and the projections to the pinned host slot k % 2
     auto enqueue = [&](int k) -> int {
-        if (int rc = apply_device(c, V + (size_t)k * ld, w, prec)) return rc;
+        if (int rc = apply_device(c, Vk + (size_t)k * ld, w, prec)) return rc;
         ++*n_apply;
+        const int nv = nu + k + 1;
         double* hb = c->sv.h + (size_t)(k & 1) * slot;
         double* h1 = hb;
-        double* h2 = hb + (size_t)(k + 1) * nc;
-        double* hn = hb + 2 * (size_t)(k + 1) * nc;
+        double* h2 = hb + (size_t)nv * nc;
+        double* hn = hb + 2 * (size_t)nv * nc;
         // CGS2: two projections, then the norm and the normalisation factor
         const int gu = (int)((8LL * n + 255) / 256);
-        if (int rc = mdots(c, V, ld, k + 1, w, h1, nullptr)) return rc;
-        k_update<<<gu, 256, 0, c->stream>>>(V, ld, k + 1, h1, nc, c->node_cell, w, n);
+        if (int rc = mdots(c, V, ld, nv, w, h1, nullptr)) return rc;
+        k_update<<<gu, 256, 0, c->stream>>>(V, ld, nv, h1, nc, c->node_cell, w, n);
         BIE_LAUNCH(c, "k_update");
-        if (int rc = mdots(c, V, ld, k + 1, w, h2, nullptr)) return rc;
-        k_update<<<gu, 256, 0, c->stream>>>(V, ld, k + 1, h2, nc, c->node_cell, w, n);
+        if (int rc = mdots(c, V, ld, nv, w, h2, nullptr)) return rc;
+        k_update<<<gu, 256, 0, c->stream>>>(V, ld, nv, h2, nc, c->node_cell, w, n);
         BIE_LAUNCH(c, "k_update");
         if (int rc = mdots(c, w, 0, 1, w, hn, fac_d)) return rc;
-        k_scale_copy<<<gs, bs, 0, c->stream>>>(w, fac_d, c->node_cell, V + (size_t)(k + 1) * ld, n);
+        k_scale_copy<<<gs, bs, 0, c->stream>>>(w, fac_d, c->node_cell, Vk + (size_t)(k + 1) * ld, n);
         BIE_LAUNCH(c, "k_scale_copy");
         BIE_CUDA(c, cudaMemcpyAsync(c->sv.pinned + (size_t)(k & 1) * slot, hb,
-                                    (2 * (size_t)(k + 1) + 1) * nc * sizeof(double), cudaMemcpyDeviceToHost,
+                                    (2 * (size_t)nv + 1) * nc * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
         BIE_CUDA(c, cudaEventRecord(c->sv.ev[k & 1], c->stream));
         return BIE_OK;
     };
-    if (int rc = enqueue(0)) return rc;
+    if (n_on)
+        if (int rc = enqueue(0)) return rc;
     for (int k = 0; k < kmax && n_on > 0; ++k) {
         if (k + 1 < kmax)
             if (int rc = enqueue(k + 1)) return rc;
         BIE_CUDA(c, cudaEventSynchronize(c->sv.ev[k & 1]));
+        const int nv = nu + k + 1;
         const double* hh = c->sv.pinned + (size_t)(k & 1) * slot;
-        const double* hh2 = hh + (size_t)(k + 1) * nc;
-        const double* hhn = hh + 2 * (size_t)(k + 1) * nc;
+        const double* hh2 = hh + (size_t)nv * nc;
+        const double* hhn = hh + 2 * (size_t)nv * nc;
         bool switched = false;
         for (int q = 0; q < nc; ++q) {
             if (!on[q]) continue;
-            for (int j = 0; j <= k; ++j) hcol[j] = hh[(size_t)j * nc + q] + hh2[(size_t)j * nc + q];
+            for (int i = 0; i < nu; ++i) Bc[q].push_back(hh[(size_t)i * nc + q] + hh2[(size_t)i * nc + q]);
+            for (int j = 0; j <= k; ++j)
+                hcol[j] = hh[(size_t)(nu + j) * nc + q] + hh2[(size_t)(nu + j) * nc + q];
             const double hk1 = std::sqrt(hhn[q]);
             if (!std::isfinite(hk1)) return fail(c, BIE_ENUMERIC, "non-finite Krylov vector in GMRES");
             hcol[k + 1] = hk1;
@@ -317,10 +402,11 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
         if (switched && n_on > 0)
             if (int rc = set_active(c, on)) return rc;
     }
-    // per cell: back substitution with its own Krylov dimension
+    // per cell: back substitution with its own Krylov dimension; the
+    // augmentation coefficients C~^T r - B y
     int kk = 0;
     for (int q = 0; q < nc; ++q) kk = std::max(kk, it[q]);
-    std::vector<double> cf((size_t)kk * nc, 0.0);
+    std::vector<double> cf((size_t)kk * nc, 0.0), ca((size_t)nu * nc, 0.0);
     for (int q = 0; q < nc; ++q) {
         const int kq = it[q];
         // column j of H[q] starts at j (j + 1) / 2
@@ -332,16 +418,28 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
             yv[i] = s / Hq(i, i);
         }
         for (int j = 0; j < kq; ++j) cf[(size_t)j * nc + q] = yv[j];
+        for (int i = 0; i < nu; ++i) {
+            double s = acoef[(size_t)i * nc + q];
+            for (int j = 0; j < kq; ++j) s -= Bc[q][(size_t)j * nu + i] * yv[j];
+            ca[(size_t)i * nc + q] = beta_in[q] > 0 ? s : 0.0;
+        }
     }
     if (kk > 0) {
         BIE_CUDA(c, cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        k_combine<<<gs, bs, 0, c->stream>>>(V, ld, kk, coef, nc, c->node_cell, x, n);
+        k_combine<<<gs, bs, 0, c->stream>>>(Vk, ld, kk, coef, nc, c->node_cell, x, n);
+        BIE_LAUNCH(c, "k_combine");
+    }
+    if (nu > 0) {
+        double* coef2 = coef + (size_t)kmax * nc;
+        BIE_CUDA(c, cudaMemcpyAsync(coef2, ca.data(), ca.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        k_combine<<<gs, bs, 0, c->stream>>>(Ut, ld, nu, coef2, nc, c->node_cell, x, n);
         BIE_LAUNCH(c, "k_combine");
     }
     return BIE_OK;
 }
 
-int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info) {
+int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info, const double* U,
+                 int nu) {
     const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
     bie_solve_info inf{};
@@ -373,21 +471,27 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
         for (char t : todo) any |= t != 0;
         if (!any) break;
         // FP64-class residual (native double, or double-float when mixed) of
-        // the cells still iterating
+        // the cells still iterating; from a zero start it is b itself
+        const bool from_zero = outer == 0 && !use_guess;
         if ((rc = set_active(c, todo))) return rc;
-        rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : BIE_FP64);
-        if (rc) return rc;
-        ++inf.applies64;
-        k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);
-        BIE_LAUNCH(c, "k_sub");
-        if ((rc = dnorms(c, c->sv.r, rn))) return rc;
+        if (from_zero) {
+            BIE_CUDA(c, cudaMemcpyAsync(c->sv.r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+            rn = bnorm;
+        } else {
+            rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : BIE_FP64);
+            if (rc) return rc;
+            ++inf.applies64;
+            k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);
+            BIE_LAUNCH(c, "k_sub");
+            if ((rc = dnorms(c, c->sv.r, rn))) return rc;
+        }
         bool left = false;
         for (int q = 0; q < nc; ++q) {
             beta[q] = 0.0;
             if (!todo[q]) continue;
             if (!std::isfinite(rn[q])) return fail(c, BIE_ENUMERIC, "non-finite residual");
             ci[q].rel_residual = rn[q] / bnorm[q];
-            ++ci[q].applies64;
+            if (!from_zero) ++ci[q].applies64;
             if (ci[q].rel_residual <= tol) {
                 todo[q] = 0;
                 continue;
@@ -400,13 +504,15 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
         int napply = 0;
         if (mixed) {
             BIE_CUDA(c, cudaMemsetAsync(c->sv.d, 0, n * sizeof(double), c->stream));
-            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply);
+            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply, from_zero ? U : nullptr,
+                             from_zero ? nu : 0);
             if (rc) return rc;
             k_axpy<<<gs, bs, 0, c->stream>>>(1.0, c->sv.d, x, n);
             BIE_LAUNCH(c, "k_axpy");
             inf.applies32 += napply;
         } else {
-            rc = gmres_cycle(c, BIE_FP64, x, c->sv.r, beta, atol, its, est, &napply);
+            rc = gmres_cycle(c, BIE_FP64, x, c->sv.r, beta, atol, its, est, &napply, from_zero ? U : nullptr,
+                             from_zero ? nu : 0);
             if (rc) return rc;
             inf.applies64 += napply;
         }
