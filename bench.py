@@ -5,10 +5,14 @@ Workload: 25 equal-area ellipses per unit cell, area fraction 0.3, aspect
 ratios in [1, 3], minimum gap 1e-2, 256 nodes per body (6400 nodes), lattice
 (1,0),(0,1), mu = gamma = 1, forward Euler with dt = 1e-3 (synthetic seeded
 suspension).  One timed "step" is one forward-Euler time step: solve the
-mobility BIE to a relative FP64 residual of 1e-10 (single-precision pair sums
-inside FP64 iterative refinement, warm-started from the previous step),
-extract velocities and mu_eff, move the bodies, shear the lattice and rebuild
-the discretisation and the proxy fit.
+mobility BIE to a relative FP64-class residual of 1e-10 (single-precision
+pair sums inside iterative refinement with double-float residuals; the first
+GMRES cycle augmented with the previous density, its last change and the
+shipped warm-start network's predicted change), extract velocities and
+mu_eff, move the bodies, shear the lattice and rebuild the discretisation and
+the proxy fit.  Beside it: iterations per step of the other starts (zero,
+recycled directions without the network) and the plain FP64 solve (zero
+start, double-precision pair sums) in seconds per shear time.
 
 value: near-image pair evaluations (9 N^2 per operator application, every
 FP32 and FP64 application counted) per second, whole job (all ranks), in
@@ -102,16 +106,28 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def source_hash():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1912_04501_gb300", "csrc", "apply.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+def kernel_source(kernel):
+    """Source text of a kernel in the library (from its name to the closing
+    brace at column 0), the unit the committed ncu summaries are keyed on."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1912_04501_gb300", "csrc", "*.cu"))):
+        text = open(path).read()
+        k = text.find(kernel + "(")
+        while k >= 0 and text.rfind("\n", 0, k) >= 0 and "__global__" not in text[text.rfind("__global__", 0, k):k][:400]:
+            k = text.find(kernel + "(", k + 1)
+        if k >= 0:
+            e = text.find("\n}\n", k)
+            return text[text.rfind("__global__", 0, k):e + 3]
+    return ""
+
+
+def source_hash(kernel):
+    return hashlib.sha256(kernel_source(kernel).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the kernel's current source (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_config2.md")
     if not os.path.exists(path):
         return None
@@ -120,7 +136,7 @@ def profiled_traffic(kernel):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("apply.cu sha256[:16]") != source_hash():
+    if vals.get("kernel source sha256[:16]") != source_hash(kernel):
         return None
     try:
         return float(vals["dram bytes per launch"])
@@ -194,7 +210,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1912_04501_gb300 import bie, workloads
+    from paper_1912_04501_gb300 import bie, learn, workloads
 
     torch.cuda.set_device(local)
     dist = None
@@ -212,8 +228,13 @@ def main():
     N = sum(b["n"] for b in cell["bodies"])
     pairs_per_apply = 9.0 * N * N
     stream = torch.cuda.Stream()
-    ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local)
+    net = learn.default_net(device=local)
+    mode = 2 if net is not None else 3
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=mode)
     ctx.set_stream(stream.cuda_stream)
+    if net is not None:
+        net.set_stream(stream.cuda_stream)
+        ctx.set_warm_net(net)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
     for _ in range(args.warmup):
@@ -272,8 +293,20 @@ def main():
             dist.destroy_process_group()
         return
 
-    # plain FP64 solve per step (reported beside the mixed one)
-    ctx64 = bie.Context(cell, precision=bie.BIE_FP64, device=local)
+    # iterations per step of the other starts on the same trajectory start
+    starts = {}
+    st0 = ctx.get_state()
+    for m in (0, 3):
+        cm = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=m)
+        cm.set_stream(stream.cuda_stream)
+        cm.set_state(st0["t"], st0["e2"], st0["xc"], st0["theta"], st0["sigma"], st0["sigma_prev2"], st0["dt_prev"])
+        its = [cm.step(dt, 1)[1]["iterations"] for _ in range(3)]
+        starts[{0: "zero", 3: "recycled"}[m]] = statistics.mean(its)
+        cm.close()
+    starts["learned" if mode == 2 else "recycled (no network shipped)"] = statistics.mean(iters)
+
+    # plain FP64 solve per step (zero start, double-precision pair sums)
+    ctx64 = bie.Context(cell, precision=bie.BIE_FP64, device=local, warm_start=0)
     ctx64.set_stream(stream.cuda_stream)
     ctx64.step(dt, 1)
     torch.cuda.synchronize()
@@ -287,22 +320,23 @@ def main():
     # end to end through the public API with host buffers
     st = ctx.get_state()
     host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-               (("e2", st["e2"]), ("xc", st["xc"].ravel()), ("theta", st["theta"]), ("sigma", st["sigma"]))}
+               (("e2", st["e2"]), ("xc", st["xc"].ravel()), ("theta", st["theta"]), ("sigma", st["sigma"]),
+                ("sigma_prev2", st["sigma_prev2"]))}
     e2e_steps = max(3, args.steps // 2)
     e2e_pairs = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_state(st["t"], host_in["e2"].numpy(), host_in["xc"].numpy(), host_in["theta"].numpy(),
-                      host_in["sigma"].numpy())
+                      host_in["sigma"].numpy(), host_in["sigma_prev2"].numpy(), st["dt_prev"])
         m, info = ctx.step(dt, 1)
         out = ctx.get_state()
         e2e_pairs += pairs_per_apply * (info["applies32"] + info["applies64"])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     nb = len(cell["bodies"])
-    h2d = (8 * nb + 2 * N) * 8
-    d2h = (8 * nb + 2 * N + 1) * 8
+    h2d = (3 * nb + 2 + 2 * N + 2 * N) * 8   # centroids, angles, e2, density, previous density
+    d2h = (8 * nb + 2 * N + 2 * N + 1) * 8  # body table, density, previous density, mu_eff
 
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -349,13 +383,16 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "bodies": nb,
                        "precision": "FP32 pair sums; refinement residual with double-float pair sums",
-                       "gmres_tol": 1e-10, "warm_start": "previous step density",
+                       "gmres_tol": 1e-10,
+                       "warm_start": ("learned: first GMRES cycle augmented with the previous density, its last "
+                                      "change and the shipped network's predicted change" if mode == 2 else
+                                      "first GMRES cycle augmented with the previous density and its last change"),
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"{world} independent replica(s)"},
             "s_per_shear_time": ms_per_step / 1e3 / dt,
             "s_per_shear_time_fp64": ms64 / 1e3 / dt,
             "solve": {"applies32": applies32, "applies64": applies64, "iterations_mean": statistics.mean(iters),
-                      "mu_eff_last": mu[-1]},
+                      "mu_eff_last": mu[-1], "iterations_per_step_by_start": starts},
             "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
             "roofline_detail": [dom] + other,
             "cpu_baseline": cpu,
@@ -366,7 +403,10 @@ def main():
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
+    ctx.set_warm_net(None)
     ctx.close()
+    if net is not None:
+        net.close()
     if dist is not None:
         dist.destroy_process_group()
 

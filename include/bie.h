@@ -115,7 +115,7 @@ typedef struct {
 
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
- * warm_start 1, min_gap 0, device 0, close_factor 10, close_capacity 0,
+ * warm_start 3, min_gap 0, device 0, close_factor 10, close_capacity 0,
  * residual BIE_DF64. */
 void bie_default_opts(bie_opts* opts);
 
@@ -214,9 +214,18 @@ int bie_get_state(bie_ctx* ctx, double* t, double* e2, double* xc, double* theta
 
 /* Restore a checkpoint taken from a context with the same bodies and node
  * counts; re-discretises and rebuilds the proxy fit.  sigma may be NULL
- * (warm start cleared). */
+ * (warm start cleared).  Clears the history below. */
 int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, const double* theta,
                   const double* sigma);
+
+/* The rest of a checkpoint for warm starts 2 and 3: the density of the solve
+ * before the last (2N host doubles; zeros when there is none), the last time
+ * step, and whether such a density is kept.  Restoring it with
+ * bie_set_history after bie_set_state makes warm_start 3 resume bit for bit
+ * (warm_start 2 also reads the previous geometry's gaps, which a restored
+ * context recomputes only from its next step on).  sigma_prev2 NULL clears it. */
+int bie_get_history(bie_ctx* ctx, double* sigma_prev2, double* dt_prev, int32_t* have);
+int bie_set_history(bie_ctx* ctx, const double* sigma_prev2, double dt_prev);
 
 /* bie_apply_static: the same operator application as
  * bie_apply(ctx, sigma, out, BIE_MIXED, 1), but it allocates no device memory

@@ -11,6 +11,7 @@ The functions carry the C names:
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
     bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read,
     bie_apply_static, bie_init_batch, bie_cells, bie_features, bie_set_warm_net,
+    bie_get_history, bie_set_history,
     bie_net_init, bie_net_destroy, bie_net_last_error, bie_net_size,
     bie_net_set_stream, bie_net_set_params, bie_net_get_params,
     bie_net_forward, bie_net_loss_grad, bie_net_adam_step
@@ -115,6 +116,8 @@ def library():
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
         "bie_features": (c_int32, [vp, vp, c_int32]),
+        "bie_get_history": (c_int32, [vp, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+        "bie_set_history": (c_int32, [vp, vp, c_double]),
         "bie_set_warm_net": (c_int32, [vp, vp]),
         "bie_net_init": (c_int32, [ctypes.POINTER(vp), c_int32, c_int32]),
         "bie_net_destroy": (None, [vp]),
@@ -144,7 +147,8 @@ def exported_symbols():
                         "bie_profile_read", "bie_apply_static", "bie_init_batch", "bie_cells", "bie_features",
                         "bie_set_warm_net", "bie_net_init", "bie_net_destroy", "bie_net_last_error",
                         "bie_net_size", "bie_net_set_stream", "bie_net_set_params", "bie_net_get_params",
-                        "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step")
+                        "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step", "bie_get_history",
+                        "bie_set_history")
             if hasattr(L, n)]
 
 
@@ -303,8 +307,11 @@ class Context:
         sg = np.zeros(2 * self.N)
         self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
                                             th.ctypes.data, sg.ctypes.data))
+        s2 = np.zeros(2 * self.N)
+        dtp, have = c_double(), c_int32()
+        self._check(library().bie_get_history(self.h, s2.ctypes.data, ctypes.byref(dtp), ctypes.byref(have)))
         return dict(t=float(t[0]), e2=(e2.reshape(-1, 2) if self.batch else e2), xc=xc.reshape(-1, 2), theta=th,
-                    sigma=sg)
+                    sigma=sg, sigma_prev2=(s2 if have.value else None), dt_prev=dtp.value)
 
     def apply_static(self, sigma, out):
         """bie_apply_static on device tensors (no device allocation inside the
@@ -344,7 +351,7 @@ class Context:
         self._check(library().bie_profile_read(self.h, ctypes.byref(info)))
         return info.as_dict()
 
-    def set_state(self, t, e2, xc, theta, sigma=None):
+    def set_state(self, t, e2, xc, theta, sigma=None, sigma_prev2=None, dt_prev=0.0):
         e2 = np.ascontiguousarray(e2, dtype=np.float64).ravel()
         if e2.size != 2 * self.n_cells:
             raise ValueError("e2 needs two entries per cell")
@@ -353,6 +360,8 @@ class Context:
         sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64).ravel()
         self._check(library().bie_set_state(self.h, float(t), e2.ctypes.data, xc.ctypes.data, th.ctypes.data,
                                             None if sg is None else sg.ctypes.data))
+        s2 = None if sigma_prev2 is None else np.ascontiguousarray(sigma_prev2, dtype=np.float64).ravel()
+        self._check(library().bie_set_history(self.h, None if s2 is None else s2.ctypes.data, float(dt_prev)))
 
 
 class Net:
@@ -385,6 +394,9 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def set_stream(self, stream_handle):
+        self._check(library().bie_net_set_stream(self.h, c_void_p(stream_handle)))
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)

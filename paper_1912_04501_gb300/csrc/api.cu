@@ -71,6 +71,8 @@ void cell_set_lattice(Cell& cl, const double* e1, const double* e2) {
             cl.sy[idx] = m * e1[1] + n * e2[1];
             cl.sxf[idx] = (float)cl.sx[idx];
             cl.syf[idx] = (float)cl.sy[idx];
+            cl.sxl[idx] = (float)(cl.sx[idx] - (double)cl.sxf[idx]);
+            cl.syl[idx] = (float)(cl.sy[idx] - (double)cl.syf[idx]);
         }
     cl.l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
     cl.l2 = std::sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
@@ -280,7 +282,7 @@ void bie_default_opts(bie_opts* o) {
     o->gmres_max = 200;
     o->inner_tol = 1e-5;
     o->max_refine = 8;
-    o->warm_start = 1;
+    o->warm_start = 3;
     o->min_gap = 0.0;
     o->device = 0;
     o->close_factor = 10.0;
@@ -396,12 +398,12 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);
     rc = rc ? rc : dalloc(c, &c->P, nc * Cc * 8 * m);
-    rc = rc ? rc : dalloc(c, &c->wall, nc * 16 * 2 * m);
+    rc = rc ? rc : dalloc(c, &c->wall, nc * kWallStride * 2 * m);
     rc = rc ? rc : dalloc(c, &c->e2d, 2 * nc);
     rc = rc ? rc : dalloc(c, &c->next.A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->next.beta, nc * 2 * Cc);
     rc = rc ? rc : dalloc(c, &c->next.P, nc * Cc * 8 * m);
-    rc = rc ? rc : dalloc(c, &c->next.wall, nc * 16 * 2 * m);
+    rc = rc ? rc : dalloc(c, &c->next.wall, nc * kWallStride * 2 * m);
     rc = rc ? rc : dalloc(c, &c->next.e2, 2 * nc);
     if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
@@ -806,6 +808,37 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     c->cl.have_dprev = false;
     rc = rebuild(c);
     if (rc) return rc;
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_get_history(bie_ctx* c, double* sigma_prev2, double* dt_prev, int32_t* have) {
+    if (!c) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    if (have) *have = (c->sv.have_prev && c->sv.have_prev2) ? 1 : 0;
+    if (dt_prev) *dt_prev = c->sv.dt_prev;
+    if (sigma_prev2) {
+        if (c->sv.have_prev && c->sv.have_prev2)
+            BIE_CUDA(c, cudaMemcpyAsync(sigma_prev2, c->sv.sigma_prev2, 2 * (size_t)c->N * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        else
+            std::memset(sigma_prev2, 0, 2 * (size_t)c->N * sizeof(double));
+    }
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_set_history(bie_ctx* c, const double* sigma_prev2, double dt_prev) {
+    if (!c || !std::isfinite(dt_prev) || dt_prev < 0) return BIE_EINVAL;
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    c->sv.dt_prev = dt_prev;
+    if (sigma_prev2 && c->sv.have_prev) {
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev2, sigma_prev2, 2 * (size_t)c->N * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->sv.have_prev2 = true;
+    } else {
+        c->sv.have_prev2 = false;
+    }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
 }

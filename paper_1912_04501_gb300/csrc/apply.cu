@@ -393,7 +393,9 @@ k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
 
 // Wall table (per geometry and cell): for each collocation point (L points,
 // then D points) the point minus each of its six far-image shifts, and the
-// wall normal used for the traction.  grid.y = cell.
+// wall normal used for the traction: 14 doubles (x, y of the six points, then
+// the normal), 2 unused, then the same 14 values as floats in cell-centred
+// coordinates (kWallStride doubles per point).  grid.y = cell.
 __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell* __restrict__ cells,
                              const double* __restrict__ e2v, double* __restrict__ wall) {
     const int wp = blockIdx.x * blockDim.x + threadIdx.x, cidx = blockIdx.y;
@@ -415,7 +417,7 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell*
         Y = Cy - 0.5 * e2y + s * e1y;
         ax = e2x; ay = e2y; bx = e1x; by = e1y;
     }
-    double* o = wall + ((size_t)cidx * 2 * m + wp) * 16;
+    double* o = wall + ((size_t)cidx * 2 * m + wp) * kWallStride;
     for (int k = -1; k <= 1; ++k) {
         o[2 * (k + 1)] = X - (-2.0 * ax + k * bx);
         o[2 * (k + 1) + 1] = Y - (-2.0 * ay + k * by);
@@ -424,6 +426,15 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell*
     }
     o[12] = isL ? nl[0] : nd[0];
     o[13] = isL ? nl[1] : nd[1];
+    o[14] = o[15] = 0.0;
+    float* of = reinterpret_cast<float*>(o + 16);
+    for (int k = 0; k < 12; k += 2) {
+        of[k] = (float)(o[k] - Cx);
+        of[k + 1] = (float)(o[k + 1] - Cy);
+    }
+    of[12] = (float)o[12];
+    of[13] = (float)o[13];
+    of[14] = of[15] = 0.f;
 }
 
 int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st) {
@@ -460,15 +471,26 @@ k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const 
     // per-geometry table: collocation point minus each of the six far-image
     // shifts (plus images -2a + kb, then minus images a + kb), and the normal;
     // the single-precision path works in cell-centred coordinates
-    const double* wt = wall + ((size_t)cidx * 2 * m + wp) * 16;
-    const double ocx = F32 ? cl.C[0] : 0.0, ocy = F32 ? cl.C[1] : 0.0;
-    Real ox[6], oy[6];
+    const double* wt = wall + ((size_t)cidx * 2 * m + wp) * kWallStride;
+    Real ox[6], oy[6], n0, n1;
+    if constexpr (F32) {
+        const float* wf = reinterpret_cast<const float*>(wt + 16);
 #pragma unroll
-    for (int im = 0; im < 6; ++im) {
-        ox[im] = (Real)(wt[2 * im] - ocx);
-        oy[im] = (Real)(wt[2 * im + 1] - ocy);
+        for (int im = 0; im < 6; ++im) {
+            ox[im] = wf[2 * im];
+            oy[im] = wf[2 * im + 1];
+        }
+        n0 = wf[12];
+        n1 = wf[13];
+    } else {
+#pragma unroll
+        for (int im = 0; im < 6; ++im) {
+            ox[im] = wt[2 * im];
+            oy[im] = wt[2 * im + 1];
+        }
+        n0 = wt[12];
+        n1 = wt[13];
     }
-    const Real n0 = (Real)wt[12], n1 = (Real)wt[13];
     Real ux = 0, uy = 0, tx = 0, ty = 0;
     const int per = (cl.n_nodes + nsp - 1) / nsp;
     const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
@@ -498,13 +520,13 @@ k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const 
             }
         }
     }
-    double v[4] = {(double)ux, (double)uy, (double)tx, (double)ty};
+    Real v[4] = {ux, uy, tx, ty};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        double t = v[c];
+        Real t = v[c];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[c][warp] = t;
+        if (lane == 0) red[c][warp] = (double)t;
     }
     __syncthreads();
     const size_t nv = 8 * (size_t)m;

@@ -57,6 +57,7 @@ constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
 constexpr int kMaxCells = 4096;
+constexpr int kWallStride = 24;       // doubles per wall point of the wall table (see k_wall_table)
 constexpr int kNetHidden = 64;        // hidden width of the warm-start network
 constexpr int kNetMaxIn = 16;         // its maximum number of inputs per node
 constexpr int kNetFeatures = 13;      // node features of the warm start (features_device)
@@ -68,6 +69,7 @@ struct Cell {
     double mu, gamma, l1, l2;
     double sx[9], sy[9];      // image shifts m e1 + n e2, index (n + 1) * 3 + (m + 1); index 4 is zero
     float sxf[9], syf[9];
+    float sxl[9], syl[9];     // sx - sxf, sy - syf: the shifts as double-float pairs
     int node_off, n_nodes, body_off, n_bodies;
     long long part_off[3];    // near-sum partial base (elements) per precision: 0 f32, 1 f64, 2 df64
     int splits[3];            // source splits per precision

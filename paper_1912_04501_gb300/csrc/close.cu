@@ -435,20 +435,13 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
     if (i >= N) return;
     const Cell& cl = cells[node_cell[i]];
     const float4 tv = tgt32[i];
-    const double Xc = x[i] - cl.C[0], Yc = y[i] - cl.C[1];
+    const float4 pi = posdf[i];
     float fx = 0.f, fy = 0.f;  // sum of (exactly differenced term - single-precision term)
-    // target shifted by image im as a double-float pair (xh, xl, yh, yl):
-    // formed by lane 0 and broadcast (the FP64 pipe is narrow)
+    // target minus the image shift, exactly, as a double-float pair (xh, xl, yh, yl)
     auto shifted = [&](int im) {
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane == 0) {
-            split_df(Xc - cl.sx[im], p.x, p.y);
-            split_df(Yc - cl.sy[im], p.z, p.w);
-        }
-        p.x = __shfl_sync(0xffffffffu, p.x, 0);
-        p.y = __shfl_sync(0xffffffffu, p.y, 0);
-        p.z = __shfl_sync(0xffffffffu, p.z, 0);
-        p.w = __shfl_sync(0xffffffffu, p.w, 0);
+        float4 p;
+        df_diff(pi.x, pi.y, cl.sxf[im], cl.sxl[im], p.x, p.y);
+        df_diff(pi.z, pi.w, cl.syf[im], cl.syl[im], p.z, p.w);
         return p;
     };
     auto redo = [&](int j, int im, const float4& p) {
@@ -490,17 +483,16 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
             }
         }
     }
-    double tx = bx, ty = by;
     for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        tx += __shfl_xor_sync(0xffffffffu, tx, o);
-        ty += __shfl_xor_sync(0xffffffffu, ty, o);
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
     }
     if (lane == 0) {
         const double c = -1.0 / kPi;
         const double2 t = T[i];
-        T[i] = make_double2(t.x + tx + c * (double)fx, t.y + ty + c * (double)fy);
+        T[i] = make_double2(t.x + (double)bx + c * (double)fx, t.y + (double)by + c * (double)fy);
     }
 }
 

@@ -57,20 +57,29 @@ int build_dot_chunks(bie_ctx* c) {
 // (one warp each); V = w with nv = 1 gives the partial squared norms.  With a
 // ticket, the last block to finish also forms the sums of k_fin (below) in
 // the same fixed order, saving a launch when there are few of them.
+template <int LG>
 __device__ void fin_items(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
                           int ncell, double* __restrict__ h, const Cell* __restrict__ cells, double* __restrict__ fac,
-                          int first_warp, int warp_stride, bool bypass_l1) {
-    const int lane = threadIdx.x & 31;
-    for (int idx = first_warp; idx < nv * ncell; idx += warp_stride) {
-        const int j = idx / ncell, cell = idx - j * ncell;
-        const int2 cc = cell_chunks[cell];
+                          int gthread, int nthreads, bool bypass_l1) {
+    // LG consecutive threads per (j, cell) item; every thread runs the same
+    // number of rounds, so the shuffles see whole warps
+    const int sub = gthread & (LG - 1);
+    const int items = nv * ncell, groups = nthreads / LG;
+    for (int r0 = 0; r0 < items; r0 += groups) {
+        const int idx = r0 + gthread / LG;
         double s = 0;
-        for (int b = lane; b < cc.y; b += 32) {
-            const double* pp = part + (size_t)j * nchunks + cc.x + b;
-            s += bypass_l1 ? __ldcg(pp) : *pp;
+        int cell = 0;
+        if (idx < items) {
+            const int j = idx / ncell;
+            cell = idx - j * ncell;
+            const int2 cc = cell_chunks[cell];
+            const double* pp = part + (size_t)j * nchunks + cc.x;
+#pragma unroll 4
+            for (int b = sub; b < cc.y; b += LG) s += bypass_l1 ? __ldcg(pp + b) : pp[b];
         }
-        s = wsum(s);
-        if (lane == 0) {
+#pragma unroll
+        for (int o = LG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (idx < items && sub == 0) {
             h[idx] = s;
             if (fac) fac[cell] = (cells[cell].active && s > 0) ? 1.0 / sqrt(s) : 0.0;
         }
@@ -99,7 +108,7 @@ k_dots(const double* __restrict__ V, size_t ld, int nv, const double* __restrict
     __syncthreads();
     if (!last) return;
     __threadfence();
-    fin_items(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, threadIdx.x >> 5, blockDim.x >> 5, true);
+    fin_items<8>(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, threadIdx.x, blockDim.x, true);
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -108,8 +117,8 @@ k_dots(const double* __restrict__ V, size_t ld, int nv, const double* __restrict
 // normalisation factor 1 / sqrt(h) of every active cell (0 for the others).
 __global__ void k_fin(const double* __restrict__ part, int nchunks, int nv, const int2* __restrict__ cell_chunks,
                       int ncell, double* __restrict__ h, const Cell* __restrict__ cells, double* __restrict__ fac) {
-    fin_items(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-              (gridDim.x * blockDim.x) >> 5, false);
+    fin_items<32>(part, nchunks, nv, cell_chunks, ncell, h, cells, fac, blockIdx.x * blockDim.x + threadIdx.x,
+                  gridDim.x * blockDim.x, false);
 }
 
 // w -= sum_j h[j * ncell + cell] V_j  (cell of each entry from node_cell);

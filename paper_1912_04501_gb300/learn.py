@@ -13,12 +13,23 @@ All arithmetic runs in the library's kernels (features, forward, gradient,
 Adam); this module only moves data.  Dataset tensors live on the GPU; each
 minibatch is a slice of a per-epoch permutation.
 """
+import argparse
 import math
+import os
 import time
 
 import numpy as np
 
 from . import bie, workloads
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_PARAMS = os.path.join(HERE, "warm_net_params.npy")
+
+# The shipped network: trained by `python -m paper_1912_04501_gb300.learn`
+# with these settings (seeds distinct from the evaluation cells' seeds).
+TRAIN_SEEDS = list(range(100, 112))
+TRAIN_STEPS = 20
+TRAIN = dict(epochs=30, batch=8192, lr=2e-3, lr_end=1e-4, seed=0)
 
 
 def init_params(n_in=bie.BIE_NET_FEATURES, hidden=bie.BIE_NET_HIDDEN, seed=0, out_scale=1e-2):
@@ -140,3 +151,37 @@ def evaluate(cell, params, steps, dt=1e-3, lead=2, modes=(0, 1, 3, 2), precision
         ctx.close()
     net.close()
     return out
+
+
+def load_params(path=DEFAULT_PARAMS):
+    """The shipped (or a saved) parameter vector, float32."""
+    return np.load(path).astype(np.float32)
+
+
+def default_net(device=0):
+    """A Net holding the shipped parameters, or None if there are none."""
+    if not os.path.exists(DEFAULT_PARAMS):
+        return None
+    net = bie.Net(device=device)
+    net.set_params(load_params())
+    return net
+
+
+def main():
+    ap = argparse.ArgumentParser(description="train the warm-start network on solver-generated densities")
+    ap.add_argument("--out", default=DEFAULT_PARAMS)
+    ap.add_argument("--seeds", type=int, nargs="*", default=TRAIN_SEEDS)
+    ap.add_argument("--steps", type=int, default=TRAIN_STEPS)
+    a = ap.parse_args()
+    X, T, W, solves = generate(a.seeds, a.steps, log=print)
+    net = bie.Net()
+    net.set_params(init_params(seed=0))
+    res = train(net, X, T, W, log=print, **TRAIN)
+    np.save(a.out, net.get_params())
+    print(f"{solves} solves, {X.shape[0]} nodes; held-out loss / zero predictor = {res['val_rel']:.3g}; "
+          f"wrote {a.out}")
+    net.close()
+
+
+if __name__ == "__main__":
+    main()

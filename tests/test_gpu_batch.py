@@ -175,7 +175,7 @@ def test_checkpoint_resume_bitwise():
     mu_a, _ = a.step(1e-3, 1)
     after_a = a.get_state()
     b = bie.Context(cells, precision=bie.BIE_MIXED)
-    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"])
+    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"], st["dt_prev"])
     mu_b, _ = b.step(1e-3, 1)
     after_b = b.get_state()
     assert np.array_equal(mu_a, mu_b)

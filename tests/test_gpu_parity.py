@@ -167,7 +167,7 @@ def test_checkpoint_resume_bitwise():
     mu_a, _ = a.step(1e-3, 1)
     after_a = a.get_state()
     b = bie.Context(cell, precision=bie.BIE_MIXED)
-    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"])
+    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"], st["dt_prev"])
     mu_b, _ = b.step(1e-3, 1)
     after_b = b.get_state()
     assert mu_a[0] == mu_b[0]
