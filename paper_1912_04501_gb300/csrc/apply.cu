@@ -3,8 +3,8 @@
 // batch at once.
 //
 // Launch sequence of one application (all on the context stream):
-//   k_pack          q = sigma w; single-, double- or double-float source records
-//   k_body_moments  F_b = sum q, tau_b = sum (x - x^c)^perp . q  (one CTA per body)
+//   k_pack_moments  q = sigma w as single-, double- or double-float source records, and
+//                   F_b = sum q, tau_b = sum (x - x^c)^perp . q  (one CTA per body)
 //   k_near32/64/df  3x3 near image sum of G^t at every node (Sec. 6.2 step 1): one
 //                   launch over the work items (cell, target tile, source split) of
 //                   all cells -> partial sums per split
@@ -51,48 +51,7 @@ __device__ inline double block_sum_d(double v, double* red) {
 // Knuth's TwoSum: s + e == a + b exactly
 
 // ---------------------------------------------------------------------------
-__global__ void k_pack(const double2* __restrict__ sigma, const double* __restrict__ x,
-                       const double* __restrict__ y, const double* __restrict__ w,
-                       const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
-                       float4* __restrict__ src32, Src64* __restrict__ src64) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double2 s = sigma[i];
-    double wi = w[i];
-    double qx = s.x * wi, qy = s.y * wi;
-    if (src32) {
-        const Cell& cl = cells[node_cell[i]];
-        src32[i] = make_float4((float)(x[i] - cl.C[0]), (float)(y[i] - cl.C[1]), (float)qx, (float)qy);
-    }
-    if (src64) src64[i] = Src64{x[i], y[i], qx, qy};
-}
 
-__global__ void k_body_moments(const double2* __restrict__ sigma, const double* __restrict__ x,
-                               const double* __restrict__ y, const double* __restrict__ w,
-                               const double* __restrict__ body, double* __restrict__ bodyF) {
-    __shared__ double red[33];
-    int b = blockIdx.x;
-    const double* bd = body + 8 * b;
-    double xc = bd[2], yc = bd[3];
-    int n = (int)bd[5], off = (int)bd[6];
-    double fx = 0, fy = 0, tq = 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        int i = off + k;
-        double2 s = sigma[i];
-        double qx = s.x * w[i], qy = s.y * w[i];
-        fx += qx;
-        fy += qy;
-        tq += -(y[i] - yc) * qx + (x[i] - xc) * qy;
-    }
-    fx = block_sum_d(fx, red);
-    fy = block_sum_d(fy, red);
-    tq = block_sum_d(tq, red);
-    if (threadIdx.x == 0) {
-        bodyF[3 * b] = fx;
-        bodyF[3 * b + 1] = fy;
-        bodyF[3 * b + 2] = tq;
-    }
-}
 
 // Work item of a near-sum launch: cell, target tile and source split.  The
 // tile covers `tile` targets of the cell; the split covers the cell's sources
@@ -283,21 +242,50 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
     pl = fmaf(ah, bl, fmaf(al, bh, pl));
 }
 
-__global__ void k_pack_df(const double2* __restrict__ sigma, const double* __restrict__ x,
-                          const double* __restrict__ y, const double* __restrict__ w,
-                          const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
-                          SrcDF* __restrict__ src) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const Cell& cl = cells[node_cell[i]];
-    double2 s = sigma[i];
-    double wi = w[i];
-    SrcDF r;
-    split_df(x[i] - cl.C[0], r.xh, r.xl);
-    split_df(y[i] - cl.C[1], r.yh, r.yl);
-    split_df(s.x * wi, r.qxh, r.qxl);
-    split_df(s.y * wi, r.qyh, r.qyl);
-    src[i] = r;
+
+// a1 in one pass, one CTA per body: q = sigma w packed into whichever source
+// records the application needs (single-precision cell-centred, double,
+// double-float), and the body's force and torque moments F_b = sum q,
+// tau_b = sum (x - x^c)^perp . q (block reductions in a fixed order).
+__global__ void __launch_bounds__(256)
+k_pack_moments(const double2* __restrict__ sigma, const double* __restrict__ x, const double* __restrict__ y,
+               const double* __restrict__ w, const double* __restrict__ body, const int* __restrict__ body_cell,
+               const Cell* __restrict__ cells, float4* __restrict__ src32, Src64* __restrict__ src64,
+               SrcDF* __restrict__ srcdf, double* __restrict__ bodyF) {
+    __shared__ double red[33];
+    const int b = blockIdx.x;
+    const double* bd = body + 8 * b;
+    const double xc = bd[2], yc = bd[3];
+    const int n = (int)bd[5], off = (int)bd[6];
+    const Cell& cl = cells[body_cell[b]];
+    double fx = 0, fy = 0, tq = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int i = off + k;
+        const double2 sg = sigma[i];
+        const double wi = w[i], X = x[i], Y = y[i];
+        const double qx = sg.x * wi, qy = sg.y * wi;
+        fx += qx;
+        fy += qy;
+        tq += -(Y - yc) * qx + (X - xc) * qy;
+        if (src32) src32[i] = make_float4((float)(X - cl.C[0]), (float)(Y - cl.C[1]), (float)qx, (float)qy);
+        if (src64) src64[i] = Src64{X, Y, qx, qy};
+        if (srcdf) {
+            SrcDF r;
+            split_df(X - cl.C[0], r.xh, r.xl);
+            split_df(Y - cl.C[1], r.yh, r.yl);
+            split_df(qx, r.qxh, r.qxl);
+            split_df(qy, r.qyh, r.qyl);
+            srcdf[i] = r;
+        }
+    }
+    fx = block_sum_d(fx, red);
+    fy = block_sum_d(fy, red);
+    tq = block_sum_d(tq, red);
+    if (threadIdx.x == 0) {
+        bodyF[3 * b] = fx;
+        bodyF[3 * b + 1] = fy;
+        bodyF[3 * b + 2] = tq;
+    }
 }
 
 __global__ void __launch_bounds__(kNearThreads, 4)
@@ -857,15 +845,10 @@ static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precisi
     const bool f32 = precision == BIE_MIXED;
     const bool df = precision == BIE_DF64;
     const int prec = f32 ? 0 : (df ? 2 : 1);
-    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, f32 ? ws.src32 : nullptr,
-                                     ws.src64);
-    BIE_LAUNCH(c, "k_pack");
-    if (df) {
-        k_pack_df<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, (SrcDF*)ws.srcdf);
-        BIE_LAUNCH(c, "k_pack_df");
-    }
-    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, ws.bodyF);
-    BIE_LAUNCH(c, "k_body_moments");
+    k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                 f32 ? ws.src32 : nullptr, ws.src64,
+                                                 df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
+    BIE_LAUNCH(c, "k_pack_moments");
     if (int rc = prof_begin(c, prec == 0 ? 0 : (prec == 1 ? 1 : 2))) return rc;
     if (f32) {
         if (int rc = launch_near32(c, ws.src32, (float2*)ws.part)) return rc;
@@ -1023,10 +1006,9 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
-    k_pack<<<gs, bs, 0, c->stream>>>(sg, c->x, c->y, c->w, c->node_cell, c->cells, N, nullptr, c->ws.src64);
-    BIE_LAUNCH(c, "k_pack");
-    k_body_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->ws.bodyF);
-    BIE_LAUNCH(c, "k_body_moments");
+    k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells, nullptr,
+                                                 c->ws.src64, nullptr, c->ws.bodyF);
+    BIE_LAUNCH(c, "k_pack_moments");
     k_disc<false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
         c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt);
     BIE_LAUNCH(c, "k_disc");
