@@ -133,8 +133,8 @@ def profiled_traffic(kernel):
         return None
     vals = {}
     for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
+        if ": " in line and line.startswith("- "):
+            k, v = line[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel source sha256[:16]") != source_hash(kernel):
         return None
