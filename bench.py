@@ -348,12 +348,12 @@ def main():
     ms32 = prof["near32_ms"] / max(1, n32)
     ms64_k = prof["near64_ms"] / max(1, n64)
     msdf = prof["neardf_ms"] / max(1, ndf)
-    roof32 = {"kernel": "k_near32", "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
+    roof32 = {"kernel": "k_near32x2", "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
               "achieved": flops_per_pair * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
               "launch_ms": ms32, "launches": n32, "device_ms_total": prof["near32_ms"],
               "peak_source": f"FP32 CUDA cores 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of "
                              f"{pk_src} peaks file)",
-              "traffic": profiled_traffic("k_near32")}
+              "traffic": profiled_traffic("k_near32x2")}
     roof64 = {"kernel": "k_near64", "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
               "achieved": flops_per_pair * pairs_per_apply / (ms64_k / 1e3) / 1e12 if n64 else None,
               "launch_ms": ms64_k, "launches": n64, "device_ms_total": prof["near64_ms"],

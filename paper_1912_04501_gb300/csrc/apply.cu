@@ -164,6 +164,109 @@ k_near32(const int4* __restrict__ items, const Cell* __restrict__ cells, const f
     }
 }
 
+// The same sum with two images per packed f32x2 instruction: images
+// (0,1), (2,3), (4,5), (6,7) share one packed evaluation, image 8 (the
+// unshifted one) is scalar.  Every half performs exactly the scalar
+// operations of pair32 in the same order, so each pair's term is bit for bit
+// the scalar kernel's (the single-precision close pass relies on that); only
+// the grouping of the accumulations differs (lane 0 sums images 0, 2, 4, 6,
+// lane 1 images 1, 3, 5, 7, a scalar accumulator image 8).
+template <int TPT, bool COMP>
+__global__ void __launch_bounds__(kNearThreads, kNear32CtasPerSM)
+k_near32x2(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
+           const float4* __restrict__ src, float2* __restrict__ part) {
+    __shared__ float4 s_src[kNearTile];
+    ItemRange rg;
+    if (!item_range(items, cells, 0, kNearThreads * TPT, rg)) return;
+    const Cell& cl = cells[rg.c];
+    f32x2 px[TPT][4], py[TPT][4], nx2[TPT], ny2[TPT], ax[TPT], ay[TPT];
+    float px8[TPT], py8[TPT], nxv[TPT], nyv[TPT], ax8[TPT], ay8[TPT];
+    float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
+    const f32x2 eps = pk2(1e-30f, 1e-30f), zero = pk2(0.f, 0.f);
+    const int tbase = rg.i0 + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        const float4 tv = i < rg.i1 ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            px[t][p] = pk2(tv.x - cl.sxf[2 * p], tv.x - cl.sxf[2 * p + 1]);
+            py[t][p] = pk2(tv.y - cl.syf[2 * p], tv.y - cl.syf[2 * p + 1]);
+        }
+        px8[t] = tv.x - cl.sxf[8];
+        py8[t] = tv.y - cl.syf[8];
+        nxv[t] = tv.z;
+        nyv[t] = tv.w;
+        nx2[t] = pk2(tv.z, tv.z);
+        ny2[t] = pk2(tv.w, tv.w);
+        ax[t] = ay[t] = zero;
+        ax8[t] = ay8[t] = 0.f;
+        hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
+    }
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        const int cnt = min(kNearTile, rg.j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < cnt; ++k) {
+            const float4 s = s_src[k];
+            const f32x2 sx = pk2(s.x, s.x), sy = pk2(s.y, s.y), qx = pk2(s.z, s.z), qy = pk2(s.w, s.w);
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const f32x2 dx = sub2(px[t][p], sx);
+                    const f32x2 dy = sub2(py[t][p], sy);
+                    const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
+                    const f32x2 rn = fma2(dy, ny2[t], mul2(dx, nx2[t]));
+                    const f32x2 rq = fma2(dy, qy, mul2(dx, qx));
+                    float ra, rb;
+                    upk2(r2, ra, rb);
+                    const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
+                    const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
+                    ax[t] = fma2(cc, dx, ax[t]);
+                    ay[t] = fma2(cc, dy, ay[t]);
+                }
+                const float dx = px8[t] - s.x;
+                const float dy = py8[t] - s.y;
+                const float cc = pair32(dx, dy, nxv[t], nyv[t], s.z, s.w);
+                ax8[t] = fmaf(cc, dx, ax8[t]);
+                ay8[t] = fmaf(cc, dy, ay8[t]);
+            }
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float a0, a1, b0, b1, e;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                two_sum(hx[t], (a0 + a1) + ax8[t], hx[t], e);
+                lx[t] += e;
+                two_sum(hy[t], (b0 + b1) + ay8[t], hy[t], e);
+                ly[t] += e;
+                ax[t] = ay[t] = zero;
+                ax8[t] = ay8[t] = 0.f;
+            }
+        }
+    }
+    const float c = (float)(-1.0 / kPi);
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        if (i < rg.i1) {
+            if constexpr (COMP) {
+                part[rg.out + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
+            } else {
+                float a0, a1, b0, b1;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                part[rg.out + i] = make_float2(c * ((a0 + a1) + ax8[t]), c * ((b0 + b1) + ay8[t]));
+            }
+        }
+    }
+}
+
 // Near image sum, double precision (one target per thread).  Same structure;
 // the self pair is absorbed by a 1e-300 floor on r^2.
 __global__ void __launch_bounds__(kNearThreads)
@@ -829,10 +932,18 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
     // splits with many sources keep their accuracy through compensated tile sums
     int maxchunk = 0;
     for (const Cell& cl : c->cells_h) maxchunk = std::max(maxchunk, (cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
-    if (maxchunk > kNear32CompChunk)
+    if (kNear32Pack) {
+        if (maxchunk > kNear32CompChunk)
+            k_near32x2<kNear32TPT, true><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src,
+                                                                                  part);
+        else
+            k_near32x2<kNear32TPT, false><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src,
+                                                                                   part);
+    } else if (maxchunk > kNear32CompChunk) {
         k_near32<kNear32TPT, true><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
-    else
+    } else {
         k_near32<kNear32TPT, false><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+    }
     BIE_LAUNCH(c, "k_near32");
     return BIE_OK;
 }

@@ -35,18 +35,25 @@ constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
 #ifndef BIE_NEAR_THREADS
 #define BIE_NEAR_THREADS 128
 #endif
-// Tile shape of k_near32 (measured on GB300, 25-ellipse cell: 3 targets per
-// thread at 126 registers / 4 CTAs per SM beat 1, 2 and 4 targets per thread
-// and 256-thread blocks by 2-12 %)
+// Tile shape of the single-precision near sum, measured on GB300: the packed
+// kernel (two images per f32x2 instruction) with 2 targets per thread (94
+// registers, 5 CTAs per SM) beats the scalar kernel with 3 targets per thread
+// (the best scalar shape) by 1 % on the 25-ellipse cell, 4 % on the
+// 400-ellipse cell and 9 % on the 64-cell ensemble; 3 and 4 targets per
+// thread packed fall in between.
+#ifndef BIE_NEAR32_PACK
+#define BIE_NEAR32_PACK 1
+#endif
 #ifndef BIE_NEAR32_TPT
-#define BIE_NEAR32_TPT 3
+#define BIE_NEAR32_TPT 2
 #endif
 #ifndef BIE_NEAR32_CTAS_PER_SM
-#define BIE_NEAR32_CTAS_PER_SM 4
+#define BIE_NEAR32_CTAS_PER_SM 5
 #endif
 constexpr int kNearThreads = BIE_NEAR_THREADS;  // threads per near-sum block
 constexpr int kNearTile = 256;                  // sources staged per shared-memory tile
 constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
+constexpr bool kNear32Pack = BIE_NEAR32_PACK != 0;  // two images per packed f32x2 instruction
 constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
 constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
 constexpr int kDiscSplits = 8;        // source splits per wall point of the wall-discrepancy kernel
@@ -325,6 +332,34 @@ __device__ __forceinline__ void df_diff(float ph, float pl, float sh, float sl, 
     two_sum(s1, s2, h, e3);
     l = (e1 + e2) + e3;
     fast2(h, l);
+}
+
+// Packed pairs of floats (PTX .f32x2 on sm_100-family GPUs): one instruction
+// performs the same round-to-nearest operation on both halves, so results are
+// bit-identical to the scalar operations, with half the issue slots.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 // The single-precision pair coefficient of the near sum (Eq. Gt without its
