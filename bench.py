@@ -199,6 +199,19 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+def whole_job(units, ms, dist, device):
+    """Whole-job figures of independent replicas: the units of all ranks
+    (sum) and the slowest rank's time (max).  dist None: one process."""
+    if dist is None:
+        return float(units), float(ms)
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u[0]), float(t[0])
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -271,15 +284,7 @@ def main():
     ctx.profile(False)
     pairs = pairs_per_apply * (applies32 + applies64)  # applies64: FP64-class (double-float) residuals
     # whole job: units of all ranks / slowest rank's time
-    tot = torch.tensor([pairs, total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        p_all = tot[0:1].clone()
-        dist.all_reduce(p_all)
-        t_max = tot[1:2].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        pairs_all, t_ms = float(p_all[0]), float(t_max[0])
-    else:
-        pairs_all, t_ms = pairs, total_ms
+    pairs_all, t_ms = whole_job(pairs, total_ms, dist, "cuda")
     value = pairs_all / (t_ms / 1e3) / 1e9
     ms_per_step = t_ms / args.steps
 
