@@ -203,7 +203,7 @@ def test_invalid_inputs_rejected():
 
 
 def test_full_size_config2_sampled():
-    """configs[1]-sized cell (25 ellipses, 6400 nodes): FP64 and mixed apply
+    """The benchmark cell (25 ellipses, 6400 nodes): FP64 and mixed apply
     at 48 sampled targets against the oracle evaluated there alone."""
     cell = workloads.config2()
     ctx = bie.Context(cell, precision=bie.BIE_FP64)

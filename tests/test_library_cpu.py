@@ -44,6 +44,10 @@ def test_default_opts(lib):
     lambda c: c["bodies"][0].update(a=-0.1),
     lambda c: c.update(e2=[2.0, 0.0]),
     lambda c: c.update(mu=0.0),
+    lambda c: c.update(gamma=float("nan")),
+    lambda c: c["bodies"][0].update(n=4098),
+    lambda c: c["bodies"][0].update(xc=[float("inf"), 0.5]),
+    lambda c: c.update(bodies=[]),
 ])
 def test_invalid_input_rejected_without_gpu(lib, mutate):
     from paper_1912_04501_gb300 import workloads
@@ -60,3 +64,36 @@ def test_null_arguments(lib):
     assert lib.bie_init(ctypes.byref(h), None, 1.0, 1.0, 1, None, None) == bie.BIE_EINVAL
     assert lib.bie_apply(None, None, None, 0, 0) == bie.BIE_EINVAL
     assert lib.bie_size(None, None, None) == bie.BIE_EINVAL
+
+
+@pytest.mark.parametrize("opt", [dict(n_proxy=2), dict(n_proxy=300), dict(n_coll=1), dict(gmres_max=0),
+                                 dict(gmres_max=5000), dict(warm_start=4), dict(residual=1),
+                                 dict(close_factor=-1.0), dict(precision=2), dict(gmres_tol=0.0)])
+def test_invalid_options_rejected_without_gpu(lib, opt):
+    from paper_1912_04501_gb300 import workloads
+    with pytest.raises(bie.BieError) as e:
+        bie.Context(workloads.config1(), **{k: v for k, v in opt.items() if k != "precision"},
+                    **({"precision": opt["precision"]} if "precision" in opt else {}))
+    assert e.value.code == bie.BIE_EINVAL
+
+
+def test_invalid_batches_rejected_without_gpu(lib):
+    from paper_1912_04501_gb300 import workloads
+    good = workloads.config1()
+    empty = dict(good, bodies=[])
+    with pytest.raises(bie.BieError) as e:
+        bie.Context([good, empty])
+    assert e.value.code == bie.BIE_EINVAL
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.bie_init_batch(ctypes.byref(h), 0, None, None, None) == bie.BIE_EINVAL
+    assert lib.bie_init_batch(ctypes.byref(h), 5000, None, None, None) == bie.BIE_EINVAL
+
+
+def test_network_arguments_rejected_without_gpu(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.bie_net_init(ctypes.byref(h), 0, 0) == bie.BIE_EINVAL
+    assert lib.bie_net_init(ctypes.byref(h), 17, 0) == bie.BIE_EINVAL
+    assert lib.bie_net_forward(None, None, 0, None) == bie.BIE_EINVAL
+    assert lib.bie_features(None, None, 0) == bie.BIE_EINVAL
