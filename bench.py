@@ -8,7 +8,8 @@ suspension).  One timed "step" is one forward-Euler time step: solve the
 mobility BIE to a relative FP64-class residual of 1e-10 (single-precision
 pair sums inside iterative refinement with double-float residuals; the first
 GMRES cycle augmented with the previous density, its last change and the
-shipped warm-start network's predicted change), extract velocities and
+shipped warm-start network's predicted change, the second refinement sweep
+with the previous step's second-sweep correction), extract velocities and
 mu_eff, move the bodies, shear the lattice and rebuild the discretisation and
 the proxy fit.  Beside it: iterations per step of the other starts (zero,
 recycled directions without the network) and the plain FP64 solve (zero
@@ -304,7 +305,8 @@ def main():
     for m in (0, 3):
         cm = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=m)
         cm.set_stream(stream.cuda_stream)
-        cm.set_state(st0["t"], st0["e2"], st0["xc"], st0["theta"], st0["sigma"], st0["sigma_prev2"], st0["dt_prev"])
+        cm.set_state(st0["t"], st0["e2"], st0["xc"], st0["theta"], st0["sigma"], st0["sigma_prev2"], st0["dt_prev"],
+                     st0["d2"])
         its = [cm.step(dt, 1)[1]["iterations"] for _ in range(3)]
         starts[{0: "zero", 3: "recycled"}[m]] = statistics.mean(its)
         cm.close()
@@ -326,22 +328,23 @@ def main():
     st = ctx.get_state()
     host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
                (("e2", st["e2"]), ("xc", st["xc"].ravel()), ("theta", st["theta"]), ("sigma", st["sigma"]),
-                ("sigma_prev2", st["sigma_prev2"]))}
+                ("sigma_prev2", st["sigma_prev2"]), ("d2", st["d2"]))}
     e2e_steps = max(3, args.steps // 2)
     e2e_pairs = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_state(st["t"], host_in["e2"].numpy(), host_in["xc"].numpy(), host_in["theta"].numpy(),
-                      host_in["sigma"].numpy(), host_in["sigma_prev2"].numpy(), st["dt_prev"])
+                      host_in["sigma"].numpy(), host_in["sigma_prev2"].numpy(), st["dt_prev"],
+                      host_in["d2"].numpy())
         m, info = ctx.step(dt, 1)
         out = ctx.get_state()
         e2e_pairs += pairs_per_apply * (info["applies32"] + info["applies64"])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     nb = len(cell["bodies"])
-    h2d = (3 * nb + 2 + 2 * N + 2 * N) * 8   # centroids, angles, e2, density, previous density
-    d2h = (8 * nb + 2 * N + 2 * N + 1) * 8  # body table, density, previous density, mu_eff
+    h2d = (3 * nb + 2 + 3 * 2 * N) * 8   # centroids, angles, e2, density, previous density, sweep correction
+    d2h = (8 * nb + 3 * 2 * N + 1) * 8  # body table, density, previous density, sweep correction, mu_eff
 
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -390,8 +393,10 @@ def main():
                        "precision": "FP32 pair sums; refinement residual with double-float pair sums",
                        "gmres_tol": 1e-10,
                        "warm_start": ("learned: first GMRES cycle augmented with the previous density, its last "
-                                      "change and the shipped network's predicted change" if mode == 2 else
-                                      "first GMRES cycle augmented with the previous density and its last change"),
+                                      "change and the shipped network's predicted change; second refinement sweep "
+                                      "augmented with the previous step's second-sweep correction" if mode == 2 else
+                                      "first GMRES cycle augmented with the previous density and its last change; "
+                                      "second sweep with the previous second-sweep correction"),
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"{world} independent replica(s)"},
             "s_per_shear_time": ms_per_step / 1e3 / dt,

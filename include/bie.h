@@ -95,7 +95,10 @@ typedef struct {
     int32_t warm_start;   /* bie_step start: 0 = zero; 1 = previous step's density as the initial
                              guess; 2 = zero start, first GMRES cycle augmented with the previous
                              density, its last change and the warm-start network's predicted change
-                             (bie_set_warm_net); 3 = as 2 without the network */
+                             (bie_set_warm_net); with BIE_MIXED the second refinement sweep is
+                             augmented with the previous step's second-sweep correction (the
+                             single-precision operator's error changes little per step);
+                             3 = as 2 without the network */
     double min_gap;       /* bie_step fails with BIE_ECOLLIDE below this body gap (node-sampled); 0 = off */
     int32_t device;       /* CUDA device ordinal */
     double close_factor;  /* close-evaluation zone in units of the source body's node spacing
@@ -219,13 +222,14 @@ int bie_set_state(bie_ctx* ctx, double t, const double* e2, const double* xc, co
                   const double* sigma);
 
 /* The rest of a checkpoint for warm starts 2 and 3: the density of the solve
- * before the last (2N host doubles; zeros when there is none), the last time
- * step, and whether such a density is kept.  Restoring it with
+ * before the last, the last solve's second-sweep correction (BIE_MIXED), both
+ * 2N host doubles (zeros when not kept), the last time step, and which of the
+ * two are kept (bit 0: sigma_prev2, bit 1: d2).  Restoring them with
  * bie_set_history after bie_set_state makes warm_start 3 resume bit for bit
  * (warm_start 2 also reads the previous geometry's gaps, which a restored
- * context recomputes only from its next step on).  sigma_prev2 NULL clears it. */
-int bie_get_history(bie_ctx* ctx, double* sigma_prev2, double* dt_prev, int32_t* have);
-int bie_set_history(bie_ctx* ctx, const double* sigma_prev2, double dt_prev);
+ * context recomputes only from its next step on).  NULL pointers clear them. */
+int bie_get_history(bie_ctx* ctx, double* sigma_prev2, double* d2, double* dt_prev, int32_t* have);
+int bie_set_history(bie_ctx* ctx, const double* sigma_prev2, const double* d2, double dt_prev);
 
 /* bie_apply_static: the same operator application as
  * bie_apply(ctx, sigma, out, BIE_MIXED, 1), but it allocates no device memory

@@ -116,8 +116,8 @@ def library():
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
         "bie_features": (c_int32, [vp, vp, c_int32]),
-        "bie_get_history": (c_int32, [vp, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
-        "bie_set_history": (c_int32, [vp, vp, c_double]),
+        "bie_get_history": (c_int32, [vp, vp, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+        "bie_set_history": (c_int32, [vp, vp, vp, c_double]),
         "bie_set_warm_net": (c_int32, [vp, vp]),
         "bie_net_init": (c_int32, [ctypes.POINTER(vp), c_int32, c_int32]),
         "bie_net_destroy": (None, [vp]),
@@ -307,11 +307,13 @@ class Context:
         sg = np.zeros(2 * self.N)
         self._check(library().bie_get_state(self.h, t.ctypes.data, e2.ctypes.data, xc.ctypes.data,
                                             th.ctypes.data, sg.ctypes.data))
-        s2 = np.zeros(2 * self.N)
+        s2, d2 = np.zeros(2 * self.N), np.zeros(2 * self.N)
         dtp, have = c_double(), c_int32()
-        self._check(library().bie_get_history(self.h, s2.ctypes.data, ctypes.byref(dtp), ctypes.byref(have)))
+        self._check(library().bie_get_history(self.h, s2.ctypes.data, d2.ctypes.data, ctypes.byref(dtp),
+                                              ctypes.byref(have)))
         return dict(t=float(t[0]), e2=(e2.reshape(-1, 2) if self.batch else e2), xc=xc.reshape(-1, 2), theta=th,
-                    sigma=sg, sigma_prev2=(s2 if have.value else None), dt_prev=dtp.value)
+                    sigma=sg, sigma_prev2=(s2 if have.value & 1 else None), d2=(d2 if have.value & 2 else None),
+                    dt_prev=dtp.value)
 
     def apply_static(self, sigma, out):
         """bie_apply_static on device tensors (no device allocation inside the
@@ -351,7 +353,7 @@ class Context:
         self._check(library().bie_profile_read(self.h, ctypes.byref(info)))
         return info.as_dict()
 
-    def set_state(self, t, e2, xc, theta, sigma=None, sigma_prev2=None, dt_prev=0.0):
+    def set_state(self, t, e2, xc, theta, sigma=None, sigma_prev2=None, dt_prev=0.0, d2=None):
         e2 = np.ascontiguousarray(e2, dtype=np.float64).ravel()
         if e2.size != 2 * self.n_cells:
             raise ValueError("e2 needs two entries per cell")
@@ -361,7 +363,9 @@ class Context:
         self._check(library().bie_set_state(self.h, float(t), e2.ctypes.data, xc.ctypes.data, th.ctypes.data,
                                             None if sg is None else sg.ctypes.data))
         s2 = None if sigma_prev2 is None else np.ascontiguousarray(sigma_prev2, dtype=np.float64).ravel()
-        self._check(library().bie_set_history(self.h, None if s2 is None else s2.ctypes.data, float(dt_prev)))
+        dd = None if d2 is None else np.ascontiguousarray(d2, dtype=np.float64).ravel()
+        self._check(library().bie_set_history(self.h, None if s2 is None else s2.ctypes.data,
+                                              None if dd is None else dd.ctypes.data, float(dt_prev)))
 
 
 class Net:

@@ -36,7 +36,7 @@ static void free_all(bie_ctx* c) {
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
                     c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.dpart,
                     c->sv.chunks,
-                    c->sv.cell_chunks, c->sv.sigma_prev, c->sv.sigma_prev2, c->sv.aug,
+                    c->sv.cell_chunks, c->sv.sigma_prev, c->sv.sigma_prev2, c->sv.aug, c->sv.d2,
                     c->sv.feat, c->sv.pred, c->cl.dmin, c->cl.dmin_prev, c->cl.ddir, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
                     c->cl.blk_off, c->cl.blocks, c->cl.blocks32, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
                     c->near[1].items, c->near[2].items};
@@ -138,17 +138,16 @@ static int push_density(bie_ctx* c, const double* x) {
 static int prepare_aug(bie_ctx* c, double dt, int* nu) {
     *nu = 0;
     const int mode = c->opts.warm_start;
-    if ((mode != 2 && mode != 3) || !c->sv.have_prev) return BIE_OK;
+    // the previous density alone is a poor direction (its residual is
+    // concentrated where bodies moved relative to each other and slows the
+    // projected GMRES down): augment only once its last change is known too
+    if ((mode != 2 && mode != 3) || !c->sv.have_prev || !c->sv.have_prev2) return BIE_OK;
     const size_t n2 = 2 * (size_t)c->N;
     double* U = c->sv.aug;
     BIE_CUDA(c, cudaMemcpyAsync(U, c->sv.sigma_prev, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    *nu = 1;
-    if (c->sv.have_prev2) {
-        k_diff<<<(int)((n2 + 255) / 256), 256, 0, c->stream>>>(c->sv.sigma_prev, c->sv.sigma_prev2,
-                                                                U + (size_t)(*nu) * n2, (int)n2);
-        BIE_LAUNCH(c, "k_diff");
-        ++*nu;
-    }
+    k_diff<<<(int)((n2 + 255) / 256), 256, 0, c->stream>>>(c->sv.sigma_prev, c->sv.sigma_prev2, U + n2, (int)n2);
+    BIE_LAUNCH(c, "k_diff");
+    *nu = 2;
     if (mode == 2 && c->net) {
         if (int rc = features_device(c, c->sv.feat)) return rc;
         if (int rc = net_forward_async(c, c->net, c->sv.feat, c->N, c->sv.pred)) return rc;
@@ -444,6 +443,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.sigma_prev2, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.aug, (size_t)kMaxAug * 2 * n);
+    rc = rc ? rc : dalloc(c, &c->sv.d2, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->sv.feat, (size_t)kNetFeatures * n);
     rc = rc ? rc : dalloc(c, &c->sv.pred, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->cl.dmin, n);
@@ -705,7 +705,8 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         int nu = 0;
         if ((rc = prepare_aug(c, dt, &nu))) return rc;
         bie_solve_info inf{};
-        rc = solve_device(c, c->sv.b, c->sv.x, guess, &inf, nu ? c->sv.aug : nullptr, nu);
+        rc = solve_device(c, c->sv.b, c->sv.x, guess, &inf, nu ? c->sv.aug : nullptr, nu,
+                          c->opts.warm_start == 2 || c->opts.warm_start == 3);
         if (info) *info = inf;
         if (rc) return rc;
         if ((rc = push_density(c, c->sv.x))) return rc;
@@ -805,6 +806,7 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
         c->sv.have_prev = false;
     }
     c->sv.have_prev2 = false;
+    c->sv.have_d2 = false;
     c->cl.have_dprev = false;
     rc = rebuild(c);
     if (rc) return rc;
@@ -812,32 +814,39 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     return BIE_OK;
 }
 
-int bie_get_history(bie_ctx* c, double* sigma_prev2, double* dt_prev, int32_t* have) {
+int bie_get_history(bie_ctx* c, double* sigma_prev2, double* d2, double* dt_prev, int32_t* have) {
     if (!c) return BIE_EINVAL;
     BIE_CUDA(c, cudaSetDevice(c->device));
-    if (have) *have = (c->sv.have_prev && c->sv.have_prev2) ? 1 : 0;
+    const bool h1 = c->sv.have_prev && c->sv.have_prev2, h2 = c->sv.have_d2;
+    if (have) *have = (h1 ? 1 : 0) | (h2 ? 2 : 0);
     if (dt_prev) *dt_prev = c->sv.dt_prev;
+    const size_t bytes = 2 * (size_t)c->N * sizeof(double);
     if (sigma_prev2) {
-        if (c->sv.have_prev && c->sv.have_prev2)
-            BIE_CUDA(c, cudaMemcpyAsync(sigma_prev2, c->sv.sigma_prev2, 2 * (size_t)c->N * sizeof(double),
-                                        cudaMemcpyDeviceToHost, c->stream));
-        else
-            std::memset(sigma_prev2, 0, 2 * (size_t)c->N * sizeof(double));
+        if (h1) BIE_CUDA(c, cudaMemcpyAsync(sigma_prev2, c->sv.sigma_prev2, bytes, cudaMemcpyDeviceToHost, c->stream));
+        else std::memset(sigma_prev2, 0, bytes);
+    }
+    if (d2) {
+        if (h2) BIE_CUDA(c, cudaMemcpyAsync(d2, c->sv.d2, bytes, cudaMemcpyDeviceToHost, c->stream));
+        else std::memset(d2, 0, bytes);
     }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
 }
 
-int bie_set_history(bie_ctx* c, const double* sigma_prev2, double dt_prev) {
+int bie_set_history(bie_ctx* c, const double* sigma_prev2, const double* d2, double dt_prev) {
     if (!c || !std::isfinite(dt_prev) || dt_prev < 0) return BIE_EINVAL;
     BIE_CUDA(c, cudaSetDevice(c->device));
+    const size_t bytes = 2 * (size_t)c->N * sizeof(double);
     c->sv.dt_prev = dt_prev;
+    c->sv.have_prev2 = false;
+    c->sv.have_d2 = false;
     if (sigma_prev2 && c->sv.have_prev) {
-        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev2, sigma_prev2, 2 * (size_t)c->N * sizeof(double),
-                                    cudaMemcpyHostToDevice, c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev2, sigma_prev2, bytes, cudaMemcpyHostToDevice, c->stream));
         c->sv.have_prev2 = true;
-    } else {
-        c->sv.have_prev2 = false;
+    }
+    if (d2) {
+        BIE_CUDA(c, cudaMemcpyAsync(c->sv.d2, d2, bytes, cudaMemcpyHostToDevice, c->stream));
+        c->sv.have_d2 = true;
     }
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;

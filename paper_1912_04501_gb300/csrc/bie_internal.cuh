@@ -166,6 +166,8 @@ struct Solver {
     bool have_prev = false, have_prev2 = false;
     double dt_prev = 0;            // the last time step (scales the change features)
     double* aug = nullptr;         // kMaxAug x 2N augmentation directions of the next step
+    double* d2 = nullptr;          // 2N the last second-sweep correction (warm_start 2)
+    bool have_d2 = false;
     float* feat = nullptr;         // N x kNetFeatures node features
     float* pred = nullptr;         // N x 2 network output
     std::vector<bie_solve_info> cell_info;  // last solve, per cell
@@ -292,9 +294,11 @@ int features_device(bie_ctx* c, float* X);
 
 // solve.cu ------------------------------------------------------------------
 // U: nu augmentation directions (2N each) for the first GMRES cycle when
-// starting from zero (use_guess false); may be null
+// starting from zero (use_guess false); may be null.  recycle_second: the
+// second refinement sweep (mixed precision) is augmented with the previous
+// solve's second-sweep correction, and this one's is kept
 int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info,
-                 const double* U = nullptr, int nu = 0);
+                 const double* U = nullptr, int nu = 0, bool recycle_second = false);
 int build_dot_chunks(bie_ctx* c);
 
 // small device math shared by the kernels --------------------------------------

@@ -448,7 +448,7 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
 }
 
 int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_solve_info* info, const double* U,
-                 int nu) {
+                 int nu, bool recycle_second) {
     const int n = 2 * c->N, nc = c->ncell;
     const int bs = 256, gs = (n + bs - 1) / bs;
     bie_solve_info inf{};
@@ -475,6 +475,7 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
         }
     std::vector<double> rn, beta(nc), atol(nc), est;
     std::vector<int> its;
+    bool d2_pending = false, d2_written = false;
     for (int outer = 0; outer <= max_outer; ++outer) {
         bool any = false;
         for (char t : todo) any |= t != 0;
@@ -513,9 +514,21 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
         int napply = 0;
         if (mixed) {
             BIE_CUDA(c, cudaMemsetAsync(c->sv.d, 0, n * sizeof(double), c->stream));
-            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply, from_zero ? U : nullptr,
-                             from_zero ? nu : 0);
+            // the second sweep corrects the single-precision operator's error,
+            // which changes little from one time step to the next: its last
+            // correction is a search direction for this one
+            const bool second = recycle_second && outer == 1;
+            const double* Ua = from_zero ? U : ((second && c->sv.have_d2) ? c->sv.d2 : nullptr);
+            const int na = from_zero ? nu : ((second && c->sv.have_d2) ? 1 : 0);
+            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply, Ua, na);
             if (rc) return rc;
+            if (second) {
+                // kept for the next solve if this solve's first sweep was itself
+                // augmented (a start-up solve's correction is not representative)
+                BIE_CUDA(c, cudaMemcpyAsync(c->sv.d2, c->sv.d, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                            c->stream));
+                d2_pending = d2_written = true;
+            }
             k_axpy<<<gs, bs, 0, c->stream>>>(1.0, c->sv.d, x, n);
             BIE_LAUNCH(c, "k_axpy");
             inf.applies32 += napply;
@@ -545,6 +558,7 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             worst = ci[q].rel_residual;
             worst_cell = q;
         }
+    if (d2_written) c->sv.have_d2 = d2_pending && nu >= 2;
     inf.rel_residual = worst;
     c->sv.cell_info = ci;
     if (info) *info = inf;

@@ -170,12 +170,14 @@ def test_step_matches_single_contexts():
 def test_checkpoint_resume_bitwise():
     cells = _batch()[:3]
     a = bie.Context(cells, precision=bie.BIE_MIXED)
-    a.step(1e-3, 2)
+    a.step(1e-3, 4)  # the recycled directions (densities, second-sweep correction) are in use
     st = a.get_state()
+    assert st["sigma_prev2"] is not None and st["d2"] is not None
     mu_a, _ = a.step(1e-3, 1)
     after_a = a.get_state()
     b = bie.Context(cells, precision=bie.BIE_MIXED)
-    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"], st["dt_prev"])
+    b.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"], st["dt_prev"],
+                st["d2"])
     mu_b, _ = b.step(1e-3, 1)
     after_b = b.get_state()
     assert np.array_equal(mu_a, mu_b)
