@@ -435,7 +435,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     {
         const size_t slot = (2 * (size_t)(kk + 1 + kMaxAug) + 1) * nc;
         rc = rc ? rc : dalloc(c, &c->sv.h, 2 * slot + (size_t)(kk + kMaxAug) * nc);
-        rc = rc ? rc : dalloc(c, &c->sv.fac, (2 + (size_t)kMaxAug) * nc);
+        rc = rc ? rc : dalloc(c, &c->sv.fac, (4 + 3 * (size_t)kMaxAug) * nc);
         if (!rc) rc = cu(cudaMallocHost((void**)&c->sv.pinned, 2 * slot * sizeof(double)), "cudaMallocHost");
         for (int e = 0; e < 2 && !rc; ++e)
             rc = cu(cudaEventCreateWithFlags(&c->sv.ev[e], cudaEventDisableTiming), "cudaEventCreate");
@@ -710,7 +710,7 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         if (info) *info = inf;
         if (rc) return rc;
         if ((rc = push_density(c, c->sv.x))) return rc;
-        rc = velocities_device(c, c->sv.x, dv, dom, dmu);
+        rc = velocities_device(c, c->sv.x, dv, dom, dmu, true);
         if (rc) return rc;
         if (mu_eff_out)
             BIE_CUDA(c, cudaMemcpyAsync(mu_eff_out + (size_t)s * c->ncell, dmu, c->ncell * sizeof(double),

@@ -950,6 +950,7 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
 
 // ---------------------------------------------------------------------------
 static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precision, Workspace& ws) {
+    if (&ws == &c->ws) c->ws_x = nullptr;  // the workspace is about to change
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
@@ -996,6 +997,13 @@ static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precisi
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
                                        c->cells, reinterpret_cast<double2*>(yout));
     BIE_LAUNCH(c, "k_finish");
+    // an FP64-class application over every cell leaves the double-precision
+    // sources, body moments and proxy strengths of sigma in the workspace
+    if (&ws == &c->ws && !f32) {
+        bool all = true;
+        for (const Cell& cl : c->cells_h) all = all && cl.active;
+        if (all) c->ws_x = sigma;
+    }
     return BIE_OK;
 }
 
@@ -1113,19 +1121,24 @@ __global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __rest
     if (threadIdx.x == 0) out[blockIdx.x] = cl.mu - s / (cl.gamma * area);
 }
 
-int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff) {
+int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff, bool reuse_ws) {
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
-    k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells, nullptr,
-                                                 c->ws.src64, nullptr, c->ws.bodyF);
-    BIE_LAUNCH(c, "k_pack_moments");
-    k_disc<false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
-        c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt);
-    BIE_LAUNCH(c, "k_disc");
-    k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(c->ws.gt, c->m, c->M, c->cells, c->P, c->ws.xi,
-                                                           c->ws.xif);
-    BIE_LAUNCH(c, "k_xi");
+    // reuse_ws: the time step calls this right after a solve whose last
+    // (FP64-class) residual application was of this density over every
+    // cell, so its sources, body moments and proxy strengths are reused
+    if (!(reuse_ws && c->ws_x == sigma)) {
+        k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells, nullptr,
+                                                     c->ws.src64, nullptr, c->ws.bodyF);
+        BIE_LAUNCH(c, "k_pack_moments");
+        k_disc<false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
+            c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt);
+        BIE_LAUNCH(c, "k_disc");
+        k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(c->ws.gt, c->m, c->M, c->cells, c->P, c->ws.xi,
+                                                               c->ws.xif);
+        BIE_LAUNCH(c, "k_xi");
+    }
     if (v || omega) {
         k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, c->body, c->body_cell, c->cells,
                                                                      c->yp, c->ws.xi, c->M, c->ws.vpart);

@@ -154,7 +154,7 @@ struct Solver {
     double* h = nullptr;     // 2 slots of (2 (kmax + 1 + kMaxAug) + 1) x ncell projections, then
                              // (kmax + kMaxAug) x ncell combination coefficients
     double* pinned = nullptr;  // host (page-locked): 2 slots, as on the device
-    double* fac = nullptr;   // (2 + kMaxAug) x ncell: normalisation factors, per-cell norms, scratch
+    double* fac = nullptr;   // (4 + 3 kMaxAug) x ncell: normalisation factors, per-cell norms, scratch
     cudaEvent_t ev[2] = {nullptr, nullptr};  // slot k % 2 copied to the host
     unsigned int* ticket = nullptr;  // last-block counter of k_dots (zero between launches)
     double* dpart = nullptr; // (kmax + 2) x nchunks partial dot products
@@ -217,6 +217,7 @@ struct bie_ctx {
     float2* ypf = nullptr;      // ncell x M proxy points minus the cell centre (single precision)
     double* scal = nullptr;     // 3 nb + ncell + 8: velocities, rotation rates, mu_eff
     bie::Workspace ws;
+    const double* ws_x = nullptr;  // density whose FP64-class sources, moments and xi the workspace holds
     bie::Solver sv;
     bie::Close cl;
     bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
@@ -284,7 +285,8 @@ int apply_device(bie_ctx* c, const double* sigma, double* y, int precision);
 int apply_device_ws(bie_ctx* c, const double* sigma, double* y, Workspace& ws);
 int rhs_device(bie_ctx* c, double* b);
 // per body v (2 nb), omega (nb); per cell mu_eff (ncell)
-int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff);
+int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff,
+                      bool reuse_ws = false);
 
 // net.cu --------------------------------------------------------------------
 int net_forward_async(bie_ctx* c, const bie_net* n, const float* X, int N, float* Y);

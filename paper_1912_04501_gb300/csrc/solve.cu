@@ -220,16 +220,42 @@ static int set_active(bie_ctx* c, const std::vector<char>& on) {
 // so that A U~ = C~ stays exact up to rounding).  A direction whose image is
 // (numerically) in the span of the earlier ones, or zero, is dropped (scaled
 // to zero).  Ct and Ut hold A U and U on entry.
+// scratch of the augmentation set-up, after the normalisation factors and the
+// per-cell norms: squared norms before / after projection, projection
+// coefficients of the two passes over r and of the orthonormalisation
+static double* aug_scratch(bie_ctx* c, int slot) {
+    const size_t nc = c->ncell;
+    switch (slot) {
+        case 0: return c->sv.fac + 2 * nc;                 // n0 (nc)
+        case 1: return c->sv.fac + 3 * nc;                 // n1 (nc)
+        case 2: return c->sv.fac + 4 * nc;                 // pass A (kMaxAug x nc)
+        case 3: return c->sv.fac + (4 + kMaxAug) * nc;     // pass B
+        default: return c->sv.fac + (4 + 2 * kMaxAug) * nc;  // orthonormalisation
+    }
+}
+
+// f = 1 / |c| per cell from squared norms n0 (before) and n1 (after
+// projection); 0 when the direction is (numerically) in the span of the
+// earlier ones or zero
+__global__ void k_aug_fac(const double* __restrict__ n0, const double* __restrict__ n1, double* __restrict__ f,
+                          int nc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    const double a = n0[q], b = n1[q];
+    f[q] = (isfinite(b) && b > 0 && b > 1e-20 * a) ? 1.0 / sqrt(b) : 0.0;
+}
+
 static int orthonormalise_aug(bie_ctx* c, double* Ct, double* Ut, int nu) {
     const int n = 2 * c->N, nc = c->ncell;
     const size_t ld = (size_t)n;
     const int gu = (int)((8LL * n + 255) / 256), gs = (n + 255) / 256;
-    double* hq = c->sv.fac + 2 * (size_t)nc;  // kMaxAug x ncell scratch
+    double* n0 = aug_scratch(c, 0);
+    double* n1 = aug_scratch(c, 1);
+    double* hq = aug_scratch(c, 4);
     for (int i = 0; i < nu; ++i) {
         double* ci = Ct + (size_t)i * ld;
         double* ui = Ut + (size_t)i * ld;
-        std::vector<double> n0, n1;
-        if (int rc = dnorms(c, ci, n0)) return rc;
+        if (int rc = mdots(c, ci, 0, 1, ci, n0, nullptr)) return rc;
         for (int pass = 0; pass < 2 && i > 0; ++pass) {
             if (int rc = mdots(c, Ct, ld, i, ci, hq, nullptr)) return rc;
             k_update<<<gu, 256, 0, c->stream>>>(Ct, ld, i, hq, nc, c->node_cell, ci, n);
@@ -237,11 +263,9 @@ static int orthonormalise_aug(bie_ctx* c, double* Ct, double* Ut, int nu) {
             k_update<<<gu, 256, 0, c->stream>>>(Ut, ld, i, hq, nc, c->node_cell, ui, n);
             BIE_LAUNCH(c, "k_update");
         }
-        if (int rc = dnorms(c, ci, n1)) return rc;
-        std::vector<double> f(nc);
-        for (int q = 0; q < nc; ++q)
-            f[q] = (std::isfinite(n1[q]) && n1[q] > 1e-10 * n0[q] && n1[q] > 0) ? 1.0 / n1[q] : 0.0;
-        BIE_CUDA(c, cudaMemcpyAsync(c->sv.fac, f.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (int rc = mdots(c, ci, 0, 1, ci, n1, nullptr)) return rc;
+        k_aug_fac<<<(nc + 255) / 256, 256, 0, c->stream>>>(n0, n1, c->sv.fac, nc);
+        BIE_LAUNCH(c, "k_aug_fac");
         k_scale_copy<<<gs, 256, 0, c->stream>>>(ci, c->sv.fac, c->node_cell, ci, n);
         BIE_LAUNCH(c, "k_scale_copy");
         k_scale_copy<<<gs, 256, 0, c->stream>>>(ui, c->sv.fac, c->node_cell, ui, n);
@@ -302,21 +326,23 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
             ++*n_apply;
         }
         if (int rc = orthonormalise_aug(c, V, Ut, nu)) return rc;
-        // r' = r - C~ (C~^T r), twice
+        // r' = r - C~ (C~^T r), twice; the coefficients stay on the device
+        // until the end of the cycle
         const int gu = (int)((8LL * n + 255) / 256);
-        double* hq = c->sv.fac + 2 * (size_t)nc;
         BIE_CUDA(c, cudaMemcpyAsync(w, r, ld * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         for (int pass = 0; pass < 2; ++pass) {
+            double* hq = aug_scratch(c, 2 + pass);
             if (int rc = mdots(c, V, ld, nu, w, hq, nullptr)) return rc;
             k_update<<<gu, 256, 0, c->stream>>>(V, ld, nu, hq, nc, c->node_cell, w, n);
             BIE_LAUNCH(c, "k_update");
-            std::vector<double> hh((size_t)nu * nc);
-            BIE_CUDA(c, cudaMemcpyAsync(hh.data(), hq, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            BIE_CUDA(c, cudaStreamSynchronize(c->stream));
-            for (size_t e = 0; e < hh.size(); ++e) acoef[e] += hh[e];
         }
         std::vector<double> b2;
-        if (int rc = dnorms(c, w, b2)) return rc;
+        if (int rc = dnorms(c, w, b2)) return rc;  // (synchronises: the passes' coefficients are ready)
+        std::vector<double> hh(2 * (size_t)nu * nc);
+        BIE_CUDA(c, cudaMemcpy(hh.data(), aug_scratch(c, 2), (size_t)nu * nc * sizeof(double), cudaMemcpyDeviceToHost));
+        BIE_CUDA(c, cudaMemcpy(hh.data() + (size_t)nu * nc, aug_scratch(c, 3), (size_t)nu * nc * sizeof(double),
+                               cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < (size_t)nu * nc; ++e) acoef[e] = hh[e] + hh[(size_t)nu * nc + e];
         for (int q = 0; q < nc; ++q) beta[q] = beta[q] > 0 ? b2[q] : 0.0;
         r = w;
     }
