@@ -63,7 +63,7 @@ typedef struct {
 
 /* One rigid body: an ellipse with semi-axes a = p[0], b = p[1] (shape 0; the
  * only shape of this version), centroid xc and angle theta, discretised by
- * n_nodes trapezoidal nodes (n_nodes even, 8 <= n_nodes <= 4096). */
+ * n_nodes trapezoidal nodes (n_nodes even, 8 <= n_nodes <= 16384). */
 typedef struct {
     int32_t n_nodes;
     int32_t shape;
@@ -83,7 +83,7 @@ typedef struct {
 
 /* Numerical parameters.  bie_default_opts fills every field. */
 typedef struct {
-    int32_t precision;    /* BIE_FP64 or BIE_MIXED (solver and time step) */
+    int32_t precision;    /* BIE_FP64, BIE_MIXED or BIE_DF64 (solver and time step) */
     int32_t n_proxy;      /* M proxy Stokeslets on a circle about the cell centre (Sec. 6.1), 4..256 */
     double proxy_radius;  /* radius of that circle */
     int32_t n_coll;       /* m Gauss-Legendre collocation points per wall (Sec. 6.1), 2..128 */
@@ -103,7 +103,8 @@ typedef struct {
     int32_t device;       /* CUDA device ordinal */
     double close_factor;  /* close-evaluation zone in units of the source body's node spacing
                              h_b = perimeter / N_b (Sec. 6.3 remark: 10); 0 disables the correction */
-    int32_t close_capacity; /* maximum (target, body image) close pairs stored; 0 = N */
+    int32_t close_capacity; /* maximum (target, body image) close pairs stored; 0 = no limit
+                             * (the storage grows with the geometry) */
     int32_t residual;     /* BIE_MIXED refinement residual: BIE_FP64 (native double) or BIE_DF64 */
 } bie_opts;
 
@@ -182,10 +183,16 @@ int bie_apply(bie_ctx* ctx, const double* sigma, double* out, int32_t precision,
  * at every node (2N doubles). */
 int bie_rhs(bie_ctx* ctx, double* b, int32_t on_device);
 
-/* Solve A sigma = b to opts.gmres_tol (relative FP64 residual) by GMRES
- * (opts.precision = BIE_FP64) or by single-precision GMRES inside FP64
- * iterative refinement (BIE_MIXED; the residual in the precision opts.residual
- * names).  rhs NULL means -T(u0, p0).  sigma holds
+/* Solve A sigma = b to opts.gmres_tol (relative FP64 residual) by GMRES on
+ * the native-double operator (opts.precision = BIE_FP64), on the double-float
+ * operator (BIE_DF64), or by single-precision GMRES inside FP64 iterative
+ * refinement (BIE_MIXED; the residual in the precision opts.residual names).
+ * A refinement sweep that reaches its inner tolerance yet reduces the
+ * residual less than tenfold (an operator too ill-conditioned for single-
+ * precision pairs, e.g. bodies ~1e-5 apart) switches the remaining sweeps to
+ * GMRES on the double-float operator to the final tolerance; those
+ * applications count as applies64.
+ * rhs NULL means -T(u0, p0).  sigma holds
  * the initial guess on entry when use_guess != 0 and the solution on exit
  * (2N doubles).  info may be NULL.  Returns BIE_ENOCONV if the tolerance was
  * not met (sigma then holds the best iterate), BIE_ENUMERIC on NaN/Inf. */
@@ -306,8 +313,11 @@ int bie_set_warm_net(bie_ctx* ctx, const bie_net* net);
 
 /* Close-evaluation bookkeeping of the current geometry: number of stored
  * (target, body image) pairs, and pairs closer to the curve than the finest
- * rule (64-fold upsampling) resolves to double precision (their correction is
- * then less accurate). */
+ * rule (4096-fold upsampling) resolves to double precision (their correction
+ * is then less accurate).  The upsampling factor of a pair is the smallest
+ * power of two rho >= 2 with (rho - 1/2) d >= 6.4 h (d its distance to the
+ * curve, h the local node spacing); tables for the factors in use are built
+ * when a geometry first needs them. */
 int bie_close_info(bie_ctx* ctx, int32_t* n_pairs, int32_t* under_resolved);
 
 /* Profiling aid (no counterpart in the paper: it instruments the kernels

@@ -249,7 +249,8 @@ static std::vector<double> current_e2(const bie_ctx* c) {
 }
 
 static int check_opts(const bie_opts& o, std::string& why) {
-    if (o.precision != BIE_FP64 && o.precision != BIE_MIXED) why = "precision must be BIE_FP64 or BIE_MIXED";
+    if (o.precision != BIE_FP64 && o.precision != BIE_MIXED && o.precision != BIE_DF64)
+        why = "precision must be BIE_FP64, BIE_MIXED or BIE_DF64";
     else if (o.n_proxy < 4 || o.n_proxy > kMaxProxy) why = "n_proxy out of range";
     else if (o.n_coll < 2 || o.n_coll > kMaxColl) why = "n_coll out of range";
     else if (!(o.proxy_radius > 0) || !(o.lam_rel >= 0) || !(o.gmres_tol > 0) || !(o.inner_tol > 0))
@@ -337,7 +338,8 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         for (int j = 0; j < in.n_bodies; ++j, ++nb) {
             const bie_body& bd = bodies[nb];
             if (bd.shape != 0) return bad("only shape 0 (ellipse) is supported");
-            if (bd.n_nodes < 8 || bd.n_nodes > 4096 || (bd.n_nodes & 1)) return bad("n_nodes must be even, 8..4096");
+            if (bd.n_nodes < 8 || bd.n_nodes > kMaxBodyNodes || (bd.n_nodes & 1))
+                return bad("n_nodes must be even, 8.." + std::to_string(kMaxBodyNodes));
             if (!(bd.p[0] > 0) || !(bd.p[1] > 0)) return bad("ellipse semi-axes must be positive");
             if (!std::isfinite(bd.xc[0]) || !std::isfinite(bd.xc[1]) || !std::isfinite(bd.theta))
                 return bad("non-finite body position");
@@ -456,8 +458,11 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     {
         int maxn = 0;
         for (int v : c->n_nodes) maxn = std::max(maxn, v);
+        // a given close_capacity is a hard limit; without one the block storage
+        // starts at 1024 bodies' worth of pairs and grows with the geometry
+        c->cl.grow = o.close_capacity <= 0;
         c->cl.cap_pairs = o.close_capacity > 0 ? o.close_capacity : n;
-        c->cl.cap_doubles = (long long)c->cl.cap_pairs * 3 * maxn;
+        c->cl.cap_doubles = (long long)(c->cl.grow ? std::min(c->cl.cap_pairs, 1024) : c->cl.cap_pairs) * 3 * maxn;
         rc = rc ? rc : dalloc(c, &c->cl.slots, (size_t)n * kCloseSlots);
         rc = rc ? rc : dalloc(c, &c->cl.count, n);
         rc = rc ? rc : dalloc(c, &c->cl.pair_base, (size_t)n + 1);
@@ -465,7 +470,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         rc = rc ? rc : dalloc(c, &c->cl.blk_off, c->cl.cap_pairs);
         rc = rc ? rc : dalloc(c, &c->cl.blocks, (size_t)c->cl.cap_doubles);
         rc = rc ? rc : dalloc(c, &c->cl.blocks32, (size_t)c->cl.cap_doubles);
-        rc = rc ? rc : dalloc(c, &c->cl.flags, 6);
+        rc = rc ? rc : dalloc(c, &c->cl.flags, 10);
     }
     c->ws.part_bytes = part;
     // zeroed once: a cell that the solver switches off keeps finite partials
@@ -511,7 +516,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : up(c->e2d, c->e2_0.data(), c->e2_0.size() * sizeof(double));
     rc = rc ? rc : build_near_items(c);
     rc = rc ? rc : build_dot_chunks(c);
-    rc = rc ? rc : build_dirichlet_tables(c);
+    rc = rc ? rc : build_dirichlet_tables(c, 64);
     rc = rc ? rc : rebuild(c);
     rc = rc ? rc : cu(cudaStreamSynchronize(c->stream), "init sync");
     if (rc) {

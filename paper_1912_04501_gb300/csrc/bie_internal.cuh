@@ -63,6 +63,9 @@ constexpr int kDotChunk = 256;        // vector entries per partial dot product 
 constexpr int kMaxProxy = 256;
 constexpr int kMaxColl = 128;
 constexpr int kCloseSlots = 8;        // close body images per target node
+constexpr int kMaxRho = 4096;         // largest fine-rule factor of the close evaluation (a power of two)
+constexpr int kCloseAccNodes = 4096;  // source nodes per CTA of k_close_blocks (shared accumulators)
+constexpr int kMaxBodyNodes = 16384;  // nodes per body
 constexpr int kMaxCells = 4096;
 constexpr int kWallStride = 24;       // doubles per wall point of the wall table (see k_wall_table)
 constexpr int kNetHidden = 64;        // hidden width of the warm-start network
@@ -93,14 +96,17 @@ struct Close {
     long long* blk_off = nullptr; // cap_pairs
     double* blocks = nullptr;     // cap_doubles
     float* blocks32 = nullptr;    // cap_doubles: the blocks divided by the source weights, single precision
-    double* dtab = nullptr;       // Dirichlet tables per distinct node count
+    double* dtab = nullptr;       // Dirichlet tables per distinct node count, rho = 2 .. dtab_rho
     long long* dtab_off = nullptr;  // nb: table base of each body
+    int dtab_rho = 0;             // largest rho the tables hold (grown when a pair needs more)
     int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved,
-                                  //  smallest gap below min_gap (8 bytes)]
+                                  //  smallest gap below min_gap (8 bytes), largest rho, -, block doubles (8 bytes)]
     int cap_pairs = 0;
     long long cap_doubles = 0;
+    bool grow = true;             // storage grows on demand (no close_capacity given)
     int npairs = 0;
-    int under_resolved = 0;       // pairs closer than the finest rule (rho = 64) resolves
+    int rho_max = 0;              // largest fine-rule factor of the current pairs
+    int under_resolved = 0;       // pairs closer than the finest rule (rho = kMaxRho) resolves
     double min_gap = 0;           // smallest node-to-curve gap below opts.min_gap (else infinity)
     float* dmin = nullptr;        // N: distance to the nearest other curve within the zone (else huge)
     float* dmin_prev = nullptr;   // N: the same for the previous geometry
@@ -268,7 +274,7 @@ void gauss_legendre_half(int m, std::vector<double>& s);
 
 // close.cu ------------------------------------------------------------------
 int build_close(bie_ctx* c);                               // per geometry
-int build_dirichlet_tables(bie_ctx* c);                    // once per context
+int build_dirichlet_tables(bie_ctx* c, int rho_max);       // tables for rho = 2 .. rho_max
 // T += C sigma; with src32 (the single-precision path's packed sources) the
 // own-body and close pairs of the single-precision near sum are also redone
 // with positions differenced in double precision

@@ -52,8 +52,8 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
                                const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                                double close_factor, double gap_lim, int kmax, int4* __restrict__ slots,
                                int* __restrict__ count, int* __restrict__ overflow,
-                               unsigned long long* __restrict__ gap_min, float* __restrict__ dmin,
-                               float2* __restrict__ ddir) {
+                               unsigned long long* __restrict__ gap_min, int* __restrict__ rho_max,
+                               float* __restrict__ dmin, float2* __restrict__ ddir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Cell& sh = cells[node_cell[i]];
@@ -117,9 +117,12 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
             // below e^-40; rho >= 2 everywhere in the zone (the smooth rule,
             // rho = 1, errs by exp(-pi d / h), not negligible inside 10 h_b).
             int rho = 2;
-            while ((rho - 0.5) * dcur < 6.4 * hloc && rho < 64) rho <<= 1;
-            if ((rho - 0.5) * dcur < 6.4 * hloc) atomicAdd(overflow + 1, 1);  // closer than rho = 64 resolves
-            if (c < kmax) slots[(size_t)i * kmax + c] = make_int4(b, im, rho, 0);
+            while ((rho - 0.5) * dcur < 6.4 * hloc && rho < kMaxRho) rho <<= 1;
+            if ((rho - 0.5) * dcur < 6.4 * hloc) atomicAdd(overflow + 1, 1);  // closer than kMaxRho resolves
+            if (c < kmax) {
+                slots[(size_t)i * kmax + c] = make_int4(b, im, rho, 0);
+                atomicMax(rho_max, rho);
+            }
             ++c;
         }
     }
@@ -137,7 +140,7 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
 __global__ void k_close_scan(const int* __restrict__ count, int N, int kmax, const int4* __restrict__ slots,
                              const double* __restrict__ body, int* __restrict__ pair_base,
                              long long* __restrict__ blk_off, int4* __restrict__ pairs, int* __restrict__ totals,
-                             long long cap_doubles, int cap_pairs) {
+                             long long* __restrict__ total_doubles, long long cap_doubles, int cap_pairs) {
     __shared__ int s_cnt[1024];
     __shared__ long long s_sz[1024];
     int tid = threadIdx.x, nt = blockDim.x;
@@ -165,6 +168,7 @@ __global__ void k_close_scan(const int* __restrict__ count, int N, int kmax, con
         }
         totals[0] = a;
         totals[1] = (b > cap_doubles || a > cap_pairs) ? 1 : 0;
+        *total_doubles = b;
     }
     __syncthreads();
     int p = s_cnt[tid];
@@ -173,7 +177,7 @@ __global__ void k_close_scan(const int* __restrict__ count, int N, int kmax, con
         pair_base[i] = p;
         for (int k = 0; k < count[i]; ++k) {
             int4 sl = slots[(size_t)i * kmax + k];
-            if (p < cap_pairs) {
+            if (p < cap_pairs && o + 3 * (long long)body[8 * sl.x + 5] <= cap_doubles) {
                 pairs[p] = make_int4(i, sl.x, sl.y, sl.z);
                 blk_off[p] = o;
             }
@@ -185,10 +189,10 @@ __global__ void k_close_scan(const int* __restrict__ count, int N, int kmax, con
 }
 
 // Dirichlet kernel tables D(2 pi j / (rho n)), j < rho n, of the n-point
-// interpolant, for rho = 2, 4, ..., 64: table (n, rho) starts at
+// interpolant, for rho = 2, 4, ..., rho_max: table (n, rho) starts at
 // base + n (rho - 2).  One thread per entry.
-__global__ void k_dirichlet(double* __restrict__ tab, int n) {
-    long long total = 126LL * n;
+__global__ void k_dirichlet(double* __restrict__ tab, int n, int rho_max) {
+    long long total = (2LL * rho_max - 2) * n;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         int rho = 2;
@@ -208,10 +212,12 @@ __global__ void k_dirichlet(double* __restrict__ tab, int n) {
 
 constexpr int kCloseChunk = 2048;  // fine nodes staged in shared memory at a time
 
-// One CTA per close pair.  The fine grid (rho N_b nodes) is streamed through
-// shared memory in chunks; warp w accumulates C_k for k = w, w + 8, ... with
-// its lanes on consecutive fine nodes (coalesced table and shared reads).
-// Dynamic shared memory: 3 kCloseChunk + 3 N_b doubles.
+// One CTA per close pair and range of kCloseAccNodes source nodes
+// (blockIdx.y).  The fine grid (rho N_b nodes) is streamed through shared
+// memory in chunks; warp w accumulates C_k for k = k0 + w, k0 + w + 8, ...
+// with its lanes on consecutive fine nodes (coalesced table and shared
+// reads).  Dynamic shared memory: 3 kCloseChunk + 3 min(N_b, kCloseAccNodes)
+// doubles.
 __global__ void __launch_bounds__(256)
 k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk_off,
                const double* __restrict__ x, const double* __restrict__ y,
@@ -237,7 +243,9 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
     double st, ct;
     sincos(th, &st, &ct);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = threadIdx.x; k < 3 * nbn; k += blockDim.x) acc[k] = 0.0;
+    const int k0 = blockIdx.y * kCloseAccNodes, nk = min(kCloseAccNodes, nbn - k0);
+    if (nk <= 0) return;  // this body has fewer node ranges than the largest one
+    for (int k = threadIdx.x; k < 3 * nk; k += blockDim.x) acc[k] = 0.0;
     for (int f0 = 0; f0 < nf; f0 += kCloseChunk) {
         int cnt = min(kCloseChunk, nf - f0);
         __syncthreads();
@@ -259,7 +267,8 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
             sd[u] = cc * ry * ry;
         }
         __syncthreads();
-        for (int k = wid; k < nbn; k += nw) {
+        for (int kk = wid; kk < nk; kk += nw) {
+            const int k = k0 + kk;
             double A = 0, B = 0, D = 0;
             int base = f0 - rho * k;
             for (int u = lane; u < cnt; u += 32) {
@@ -276,22 +285,23 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
                 D += __shfl_xor_sync(0xffffffffu, D, o);
             }
             if (lane == 0) {
-                acc[3 * k] += A;
-                acc[3 * k + 1] += B;
-                acc[3 * k + 2] += D;
+                acc[3 * kk] += A;
+                acc[3 * kk + 1] += B;
+                acc[3 * kk + 2] += D;
             }
         }
     }
     __syncthreads();
     double* out = blocks + blk_off[blockIdx.x];
-    for (int k = threadIdx.x; k < nbn; k += blockDim.x) {
+    for (int kk = threadIdx.x; kk < nk; kk += blockDim.x) {
         // minus the smooth rule's term for node k of this body image
+        const int k = k0 + kk;
         double rx = X - (x[off + k] + sh.sx[im]), ry = Y - (y[off + k] + sh.sy[im]);
         double r2 = rx * rx + ry * ry;
         double cc = -(rx * n0 + ry * n1) * w[off + k] / (kPi * r2 * r2);
-        const double A = acc[3 * k] - cc * rx * rx;
-        const double B = acc[3 * k + 1] - cc * rx * ry;
-        const double D = acc[3 * k + 2] - cc * ry * ry;
+        const double A = acc[3 * kk] - cc * rx * rx;
+        const double B = acc[3 * kk + 1] - cc * rx * ry;
+        const double D = acc[3 * kk + 2] - cc * ry * ry;
         out[3 * k] = A;
         out[3 * k + 1] = B;
         out[3 * k + 2] = D;
@@ -338,8 +348,19 @@ __global__ void k_close_apply(const int* __restrict__ pair_base, const int4* __r
     }
 }
 
+// Replace *p by a fresh device array of count elements (the old contents are
+// not kept).
+template <typename T>
+static int regrow(bie_ctx* c, T** p, size_t count) {
+    if (*p) BIE_CUDA(c, cudaFree(*p));
+    *p = nullptr;
+    BIE_CUDA(c, cudaMalloc((void**)p, count * sizeof(T) + 16));
+    return BIE_OK;
+}
+
 int build_close(bie_ctx* c) {
     c->cl.npairs = 0;
+    c->cl.rho_max = 0;
     k_body_h<<<c->nb, 256, 0, c->stream>>>(c->w, c->body);
     BIE_LAUNCH(c, "k_body_h");
     c->cl.min_gap = INFINITY;
@@ -347,46 +368,79 @@ int build_close(bie_ctx* c) {
     if (!(c->opts.close_factor > 0) && !(gap_lim > 0)) return BIE_OK;
     const int N = c->N, kmax = kCloseSlots;
     BIE_CUDA(c, cudaMemsetAsync(c->cl.flags, 0, 4 * sizeof(int), c->stream));
+    BIE_CUDA(c, cudaMemsetAsync(c->cl.flags + 6, 0, sizeof(int), c->stream));
     unsigned long long* gap_min = reinterpret_cast<unsigned long long*>(c->cl.flags + 4);
+    long long* need = reinterpret_cast<long long*>(c->cl.flags + 8);
     BIE_CUDA(c, cudaMemsetAsync(gap_min, 0xFF, sizeof(unsigned long long), c->stream));
     k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->node_cell, c->cells, N,
                                                          c->opts.close_factor, gap_lim, kmax, c->cl.slots,
-                                                         c->cl.count, c->cl.flags + 2, gap_min, c->cl.dmin,
-                                                         c->cl.ddir);
+                                                         c->cl.count, c->cl.flags + 2, gap_min, c->cl.flags + 6,
+                                                         c->cl.dmin, c->cl.ddir);
     BIE_LAUNCH(c, "k_close_detect");
-    k_close_scan<<<1, 1024, 0, c->stream>>>(c->cl.count, N, kmax, c->cl.slots, c->body, c->cl.pair_base,
-                                           c->cl.blk_off, c->cl.pairs, c->cl.flags, c->cl.cap_doubles,
-                                           c->cl.cap_pairs);
-    BIE_LAUNCH(c, "k_close_scan");
-    int h[4];
+    int h[7];
+    long long need_doubles = 0;
     unsigned long long gm = 0;
-    BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    BIE_CUDA(c, cudaMemcpyAsync(&gm, gap_min, sizeof gm, cudaMemcpyDeviceToHost, c->stream));
-    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the scan again after growing the storage (never a third time: the
+    // second pass is sized from the first's totals)
+    for (int pass = 0; pass < 2; ++pass) {
+        k_close_scan<<<1, 1024, 0, c->stream>>>(c->cl.count, N, kmax, c->cl.slots, c->body, c->cl.pair_base,
+                                               c->cl.blk_off, c->cl.pairs, c->cl.flags, need, c->cl.cap_doubles,
+                                               c->cl.cap_pairs);
+        BIE_LAUNCH(c, "k_close_scan");
+        BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 7 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(&need_doubles, need, sizeof need_doubles, cudaMemcpyDeviceToHost, c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(&gm, gap_min, sizeof gm, cudaMemcpyDeviceToHost, c->stream));
+        BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (h[2] > 0)
+            return fail(c, BIE_EINVAL, "a node is close to more than " + std::to_string(kmax) +
+                                           " body images (bodies overlap or nearly so)");
+        if (!h[1]) break;
+        if (!c->cl.grow || pass == 1)
+            return fail(c, BIE_EINVAL, "close-evaluation storage exceeded (" + std::to_string(h[0]) +
+                                           " pairs); raise close_capacity");
+        // grow by a quarter beyond what this geometry needs
+        if (h[0] > c->cl.cap_pairs) {
+            const int cap = h[0] + h[0] / 4 + 16;
+            int rc = regrow(c, &c->cl.pairs, cap);
+            rc = rc ? rc : regrow(c, &c->cl.blk_off, cap);
+            if (rc) return rc;
+            c->cl.cap_pairs = cap;
+        }
+        if (need_doubles > c->cl.cap_doubles) {
+            const long long cap = need_doubles + need_doubles / 4 + 1024;
+            int rc = regrow(c, &c->cl.blocks, (size_t)cap);
+            rc = rc ? rc : regrow(c, &c->cl.blocks32, (size_t)cap);
+            if (rc) return rc;
+            c->cl.cap_doubles = cap;
+        }
+    }
     if (gm != ~0ULL) std::memcpy(&c->cl.min_gap, &gm, sizeof gm);
-    if (h[2] > 0)
-        return fail(c, BIE_EINVAL, "a node is close to more than " + std::to_string(kmax) +
-                                       " body images (bodies overlap or nearly so)");
     c->cl.under_resolved = h[3];
-    if (h[1])
-        return fail(c, BIE_EINVAL, "close-evaluation storage exceeded (" + std::to_string(h[0]) +
-                                       " pairs); raise close_capacity");
     c->cl.npairs = h[0];
+    c->cl.rho_max = h[6];
     if (h[0] == 0) return BIE_OK;
+    if (h[6] > c->cl.dtab_rho) {
+        int rc = build_dirichlet_tables(c, h[6]);
+        if (rc) return rc;
+    }
     int maxn = 0;
     for (int n : c->n_nodes) maxn = std::max(maxn, n);
-    size_t shm = sizeof(double) * (3 * (size_t)kCloseChunk + 3 * (size_t)maxn);
+    const int acc = std::min(maxn, kCloseAccNodes);
+    size_t shm = sizeof(double) * (3 * (size_t)kCloseChunk + 3 * (size_t)acc);
     BIE_CUDA(c, cudaFuncSetAttribute(k_close_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     c->cl.shm_limit = shm;
-    k_close_blocks<<<h[0], 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
-                                                  c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off, c->cl.blocks,
-                                                  c->cl.blocks32);
+    dim3 grid(h[0], (maxn + kCloseAccNodes - 1) / kCloseAccNodes);
+    k_close_blocks<<<grid, 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
+                                                  c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off,
+                                                  c->cl.blocks, c->cl.blocks32);
     BIE_LAUNCH(c, "k_close_blocks");
     return BIE_OK;
 }
 
-// Dirichlet tables for every distinct node count (once per context).
-int build_dirichlet_tables(bie_ctx* c) {
+// Dirichlet tables for every distinct node count, rho = 2 .. rho_max
+// (rebuilt, larger, when a geometry needs a finer rule than they hold).
+int build_dirichlet_tables(bie_ctx* c, int rho_max) {
+    rho_max = std::max(rho_max, 64);
     std::vector<long long> off(c->nb);
     std::vector<std::pair<int, long long>> seen;
     long long total = 0;
@@ -398,17 +452,22 @@ int build_dirichlet_tables(bie_ctx* c) {
         if (o < 0) {
             o = total;
             seen.push_back({n, o});
-            total += 126LL * n;
+            total += (2LL * rho_max - 2) * n;
         }
         off[b] = o;
     }
-    BIE_CUDA(c, cudaMalloc((void**)&c->cl.dtab, total * sizeof(double)));
-    BIE_CUDA(c, cudaMalloc((void**)&c->cl.dtab_off, c->nb * sizeof(long long)));
-    BIE_CUDA(c, cudaMemcpy(c->cl.dtab_off, off.data(), c->nb * sizeof(long long), cudaMemcpyHostToDevice));
+    int rc = regrow(c, &c->cl.dtab, (size_t)total);
+    if (rc) return rc;
+    if (!c->cl.dtab_off) BIE_CUDA(c, cudaMalloc((void**)&c->cl.dtab_off, c->nb * sizeof(long long)));
+    BIE_CUDA(c, cudaMemcpyAsync(c->cl.dtab_off, off.data(), c->nb * sizeof(long long), cudaMemcpyHostToDevice,
+                                c->stream));
     for (auto& pr : seen) {
-        k_dirichlet<<<256, 256, 0, c->stream>>>(c->cl.dtab + pr.second, pr.first);
+        k_dirichlet<<<1024, 256, 0, c->stream>>>(c->cl.dtab + pr.second, pr.first, rho_max);
         BIE_LAUNCH(c, "k_dirichlet");
     }
+    // the host vector `off` must outlive the asynchronous copy
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->cl.dtab_rho = rho_max;
     return BIE_OK;
 }
 

@@ -17,7 +17,11 @@
 // BIE_MIXED: iterative refinement -- the residual r = b - A64 x uses the
 // FP64-class operator; the correction solves A32 d = r by GMRES on the
 // single-precision-pair operator to opts.inner_tol; x += d; repeat until
-// ||r_c|| / ||b_c|| <= opts.gmres_tol in every cell c.
+// ||r_c|| / ||b_c|| <= opts.gmres_tol in every cell c.  When a sweep meets
+// its inner tolerance but cuts the FP64-class residual by less than
+// kStallRatio, the remaining sweeps solve for d on the double-float operator
+// to the final tolerance instead.  BIE_FP64 / BIE_DF64:
+// GMRES directly on the native-double / double-float operator.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -25,6 +29,8 @@
 #include "bie_internal.cuh"
 
 namespace bie {
+
+constexpr double kStallRatio = 0.1;
 
 __device__ inline double wsum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -245,32 +251,44 @@ __global__ void k_aug_fac(const double* __restrict__ n0, const double* __restric
     f[q] = (isfinite(b) && b > 0 && b > 1e-20 * a) ? 1.0 / sqrt(b) : 0.0;
 }
 
-static int orthonormalise_aug(bie_ctx* c, double* Ct, double* Ut, int nu) {
+// Direction i of (Ct, Ut) per cell: project out directions 0 .. i-1 of Ct
+// (classical Gram-Schmidt twice, the same operations on Ut so that
+// A Ut_i = Ct_i stays exact up to rounding), then scale both by 1 / |Ct_i|
+// (k_aug_fac).  Scratch: n0, n1, f (ncell each), hq (i x ncell).
+static int orthonormalise_dir(bie_ctx* c, double* Ct, double* Ut, int i, double* n0, double* n1, double* hq,
+                              double* f) {
     const int n = 2 * c->N, nc = c->ncell;
     const size_t ld = (size_t)n;
     const int gu = (int)((8LL * n + 255) / 256), gs = (n + 255) / 256;
-    double* n0 = aug_scratch(c, 0);
-    double* n1 = aug_scratch(c, 1);
-    double* hq = aug_scratch(c, 4);
-    for (int i = 0; i < nu; ++i) {
-        double* ci = Ct + (size_t)i * ld;
-        double* ui = Ut + (size_t)i * ld;
-        if (int rc = mdots(c, ci, 0, 1, ci, n0, nullptr)) return rc;
-        for (int pass = 0; pass < 2 && i > 0; ++pass) {
-            if (int rc = mdots(c, Ct, ld, i, ci, hq, nullptr)) return rc;
-            k_update<<<gu, 256, 0, c->stream>>>(Ct, ld, i, hq, nc, c->node_cell, ci, n);
-            BIE_LAUNCH(c, "k_update");
-            k_update<<<gu, 256, 0, c->stream>>>(Ut, ld, i, hq, nc, c->node_cell, ui, n);
-            BIE_LAUNCH(c, "k_update");
-        }
-        if (int rc = mdots(c, ci, 0, 1, ci, n1, nullptr)) return rc;
-        k_aug_fac<<<(nc + 255) / 256, 256, 0, c->stream>>>(n0, n1, c->sv.fac, nc);
-        BIE_LAUNCH(c, "k_aug_fac");
-        k_scale_copy<<<gs, 256, 0, c->stream>>>(ci, c->sv.fac, c->node_cell, ci, n);
-        BIE_LAUNCH(c, "k_scale_copy");
-        k_scale_copy<<<gs, 256, 0, c->stream>>>(ui, c->sv.fac, c->node_cell, ui, n);
-        BIE_LAUNCH(c, "k_scale_copy");
+    double* ci = Ct + (size_t)i * ld;
+    double* ui = Ut + (size_t)i * ld;
+    if (int rc = mdots(c, ci, 0, 1, ci, n0, nullptr)) return rc;
+    for (int pass = 0; pass < 2 && i > 0; ++pass) {
+        if (int rc = mdots(c, Ct, ld, i, ci, hq, nullptr)) return rc;
+        k_update<<<gu, 256, 0, c->stream>>>(Ct, ld, i, hq, nc, c->node_cell, ci, n);
+        BIE_LAUNCH(c, "k_update");
+        k_update<<<gu, 256, 0, c->stream>>>(Ut, ld, i, hq, nc, c->node_cell, ui, n);
+        BIE_LAUNCH(c, "k_update");
     }
+    if (int rc = mdots(c, ci, 0, 1, ci, n1, nullptr)) return rc;
+    k_aug_fac<<<(nc + 255) / 256, 256, 0, c->stream>>>(n0, n1, f, nc);
+    BIE_LAUNCH(c, "k_aug_fac");
+    k_scale_copy<<<gs, 256, 0, c->stream>>>(ci, f, c->node_cell, ci, n);
+    BIE_LAUNCH(c, "k_scale_copy");
+    k_scale_copy<<<gs, 256, 0, c->stream>>>(ui, f, c->node_cell, ui, n);
+    BIE_LAUNCH(c, "k_scale_copy");
+    return BIE_OK;
+}
+
+// Orthonormalise the nu augmentation directions per cell: C~ = A U~ with
+// orthonormal columns.  A direction whose image is (numerically) in the span
+// of the earlier ones, or zero, is dropped (scaled to zero).  Ct and Ut hold
+// A U and U on entry.
+static int orthonormalise_aug(bie_ctx* c, double* Ct, double* Ut, int nu) {
+    for (int i = 0; i < nu; ++i)
+        if (int rc = orthonormalise_dir(c, Ct, Ut, i, aug_scratch(c, 0), aug_scratch(c, 1), aug_scratch(c, 4),
+                                        c->sv.fac))
+            return rc;
     return BIE_OK;
 }
 
@@ -490,6 +508,17 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
     const double tol = c->opts.gmres_tol;
     const bool mixed = c->opts.precision == BIE_MIXED;
     const int max_outer = mixed ? c->opts.max_refine : 20;
+    // operator of the plain (non-refined) solver: native double or double-float
+    const int plain_prec = c->opts.precision == BIE_DF64 ? BIE_DF64 : BIE_FP64;
+    // operator of the refinement sweeps: single-precision pairs, until a sweep
+    // that met its inner tolerance fails to cut the FP64-class residual
+    // tenfold (the single-precision operator is then too far from the FP64
+    // one for this geometry's conditioning, e.g. bodies ~1e-5 apart); the
+    // remaining sweeps run GMRES on the double-float operator to the final
+    // tolerance
+    int inner_prec = BIE_MIXED;
+    std::vector<double> rn_prev(nc, 0.0);
+    std::vector<char> met(nc, 0);
     // cells still iterating: a zero right-hand side has the solution 0
     std::vector<char> todo(nc, 1);
     for (int q = 0; q < nc; ++q)
@@ -514,7 +543,7 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             BIE_CUDA(c, cudaMemcpyAsync(c->sv.r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
             rn = bnorm;
         } else {
-            rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : BIE_FP64);
+            rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : plain_prec);
             if (rc) return rc;
             ++inf.applies64;
             k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);
@@ -534,8 +563,14 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             }
             left = true;
             beta[q] = rn[q];
-            atol[q] = mixed ? std::max(c->opts.inner_tol * rn[q], 0.5 * tol * bnorm[q]) : 0.5 * tol * bnorm[q];
+            if (mixed && inner_prec == BIE_MIXED && met[q] && rn[q] > kStallRatio * rn_prev[q])
+                inner_prec = BIE_DF64;
         }
+        for (int q = 0; q < nc; ++q)
+            if (beta[q] > 0.0)
+                atol[q] = (mixed && inner_prec == BIE_MIXED)
+                              ? std::max(c->opts.inner_tol * rn[q], 0.5 * tol * bnorm[q])
+                              : 0.5 * tol * bnorm[q];
         if (!left || outer == max_outer) break;
         int napply = 0;
         if (mixed) {
@@ -543,11 +578,15 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             // the second sweep corrects the single-precision operator's error,
             // which changes little from one time step to the next: its last
             // correction is a search direction for this one
-            const bool second = recycle_second && outer == 1;
+            const bool second = recycle_second && outer == 1 && inner_prec == BIE_MIXED;
             const double* Ua = from_zero ? U : ((second && c->sv.have_d2) ? c->sv.d2 : nullptr);
             const int na = from_zero ? nu : ((second && c->sv.have_d2) ? 1 : 0);
-            rc = gmres_cycle(c, BIE_MIXED, c->sv.d, c->sv.r, beta, atol, its, est, &napply, Ua, na);
+            rc = gmres_cycle(c, inner_prec, c->sv.d, c->sv.r, beta, atol, its, est, &napply, Ua, na);
             if (rc) return rc;
+            for (int q = 0; q < nc; ++q) {
+                met[q] = beta[q] > 0.0 && est[q] <= atol[q];
+                rn_prev[q] = rn[q];
+            }
             if (second) {
                 // kept for the next solve if this solve's first sweep was itself
                 // augmented (a start-up solve's correction is not representative)
@@ -557,9 +596,9 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             }
             k_axpy<<<gs, bs, 0, c->stream>>>(1.0, c->sv.d, x, n);
             BIE_LAUNCH(c, "k_axpy");
-            inf.applies32 += napply;
+            (inner_prec == BIE_MIXED ? inf.applies32 : inf.applies64) += napply;
         } else {
-            rc = gmres_cycle(c, BIE_FP64, x, c->sv.r, beta, atol, its, est, &napply, from_zero ? U : nullptr,
+            rc = gmres_cycle(c, plain_prec, x, c->sv.r, beta, atol, its, est, &napply, from_zero ? U : nullptr,
                              from_zero ? nu : 0);
             if (rc) return rc;
             inf.applies64 += napply;
@@ -569,7 +608,7 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             if (beta[q] == 0.0) continue;
             ci[q].iterations += its[q];
             ci[q].refinements += 1;
-            if (mixed) ci[q].applies32 += its[q];
+            if (mixed && inner_prec == BIE_MIXED) ci[q].applies32 += its[q];
             else ci[q].applies64 += its[q];
             kmax_it = std::max(kmax_it, its[q]);
         }

@@ -1,0 +1,74 @@
+"""GPU tests at near contact (Sec. 8, Example 1 at d = 1e-5): the close-
+evaluation blocks with fine rules up to 1024-fold upsampling and bodies of
+more nodes than one block-building CTA holds, against the oracle's
+definition of the correction on the targets nearest the contact.
+
+Tolerances as in the other parity tests: FP64 and double-float 1e-10,
+single-precision pairs 5e-5 (relative to the largest sampled entry).
+"""
+import numpy as np
+import pytest
+
+from paper_1912_04501_gb300 import workloads
+from tests.conftest import oracle_operator
+
+pytestmark = pytest.mark.gpu
+
+bie = pytest.importorskip("paper_1912_04501_gb300.bie")
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("gap,n", [(1e-5, 512), (1e-5, 6144)])
+def test_close_parity_at_gap_1e5(gap, n):
+    """n = 512: the closest targets need the 1024-fold rule (tables beyond
+    the 64-fold ones built at start-up); n = 6144: 128-fold, and each block
+    is built by two CTAs (node ranges of 4096)."""
+    cell = workloads.two_ellipses(gap, n)
+    ctx = bie.Context(cell, precision=bie.BIE_FP64)
+    npairs, under = ctx.close_info()
+    assert npairs > 0 and under == 0
+    x, _, _, _ = ctx.nodes()
+    # targets nearest the contact point on each body, and a few others
+    contact = np.array([0.5625, 0.5])  # the tips face each other there
+    dist = np.linalg.norm(x - contact[None, :], axis=1)
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([np.argsort(dist[:n])[:6], n + np.argsort(dist[n:])[:6],
+                                    rng.choice(2 * n, 4, replace=False)]))
+    op = oracle_operator(cell, close_targets=idx)
+    sigma = rng.standard_normal(2 * ctx.N)
+    ref = op.apply(sigma.reshape(-1, 2), targets=idx)
+    for prec, tol in ((bie.BIE_FP64, 1e-10), (bie.BIE_DF64, 1e-10), (bie.BIE_MIXED, 5e-5)):
+        y = ctx.apply(sigma, precision=prec).reshape(-1, 2)[idx]
+        assert _rel(y, ref) < tol, (prec, _rel(y, ref))
+    ctx.close()
+
+
+def _errors(gap, ns, n_ref):
+    from paper_1912_04501_gb300 import convergence
+    ref, rows = convergence.study(gap, ns, n_ref)
+    return ref, {r["n"]: max(r["err_v"], r["err_omega"]) for r in rows}, rows
+
+
+def test_spectral_convergence_onset_scales_with_gap():
+    """Sec. 8, Example 1: errors in v and omega against a finer solve fall
+    spectrally in N, from an onset that grows like 1/sqrt(d): ~60 nodes per
+    ellipse give ~1e-12 at d = 1e-1, a few hundred are needed at 1e-3."""
+    _, e1, _ = _errors(1e-1, [32, 64], 256)
+    assert e1[32] > 1e-8 and e1[64] < 1e-10, e1
+    _, e3, rows = _errors(1e-3, [256, 768], 2048)
+    assert e3[256] > 1e-6 and e3[768] < 1e-9, e3
+    assert all(r["rel_residual"] <= 1e-10 for r in rows)
+
+
+def test_gap_1e5_converges():
+    """d = 1e-5 (the paper's closest gap): the single-precision sweeps stall
+    and the solve continues on the double-float operator; the errors still
+    fall spectrally (thousands of nodes per ellipse, against a reference of
+    4096 here)."""
+    ref, e, rows = _errors(1e-5, [2048, 3072], 4096)
+    assert ref["under_resolved"] == 0 and ref["rel_residual"] < 1e-8
+    assert all(r["rel_residual"] < 1e-8 for r in rows)
+    assert e[3072] < 1e-6 and e[3072] < 0.1 * e[2048], e

@@ -45,7 +45,7 @@ def test_default_opts(lib):
     lambda c: c.update(e2=[2.0, 0.0]),
     lambda c: c.update(mu=0.0),
     lambda c: c.update(gamma=float("nan")),
-    lambda c: c["bodies"][0].update(n=4098),
+    lambda c: c["bodies"][0].update(n=16386),
     lambda c: c["bodies"][0].update(xc=[float("inf"), 0.5]),
     lambda c: c.update(bodies=[]),
 ])
@@ -68,7 +68,7 @@ def test_null_arguments(lib):
 
 @pytest.mark.parametrize("opt", [dict(n_proxy=2), dict(n_proxy=300), dict(n_coll=1), dict(gmres_max=0),
                                  dict(gmres_max=5000), dict(warm_start=4), dict(residual=1),
-                                 dict(close_factor=-1.0), dict(precision=2), dict(gmres_tol=0.0)])
+                                 dict(close_factor=-1.0), dict(precision=3), dict(gmres_tol=0.0)])
 def test_invalid_options_rejected_without_gpu(lib, opt):
     from paper_1912_04501_gb300 import workloads
     with pytest.raises(bie.BieError) as e:
