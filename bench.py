@@ -244,7 +244,11 @@ def main():
     stream = torch.cuda.Stream()
     net = learn.default_net(device=local)
     mode = 2 if net is not None else 3
-    ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=mode)
+    # the near-sum tile shape timed on this cell (autotune); direct launches
+    # (replaying captured graphs measured no faster on this workload)
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=mode, autotune=1, graph=0)
+    shape, shape_ms = ctx.near_shape()
+    near32 = "k_near32x2" if bie.NEAR32_SHAPES[shape][0] else "k_near32"
     ctx.set_stream(stream.cuda_stream)
     if net is not None:
         net.set_stream(stream.cuda_stream)
@@ -356,12 +360,12 @@ def main():
     ms32 = prof["near32_ms"] / max(1, n32)
     ms64_k = prof["near64_ms"] / max(1, n64)
     msdf = prof["neardf_ms"] / max(1, ndf)
-    roof32 = {"kernel": "k_near32x2", "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
+    roof32 = {"kernel": near32, "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
               "achieved": flops_per_pair * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
               "launch_ms": ms32, "launches": n32, "device_ms_total": prof["near32_ms"],
               "peak_source": f"FP32 CUDA cores 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of "
                              f"{pk_src} peaks file)",
-              "traffic": profiled_traffic("k_near32x2")}
+              "traffic": profiled_traffic(near32)}
     roof64 = {"kernel": "k_near64", "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
               "achieved": flops_per_pair * pairs_per_apply / (ms64_k / 1e3) / 1e12 if n64 else None,
               "launch_ms": ms64_k, "launches": n64, "device_ms_total": prof["near64_ms"],
@@ -398,6 +402,10 @@ def main():
                                       "first GMRES cycle augmented with the previous density and its last change; "
                                       "second sweep with the previous second-sweep correction"),
                        "l2": "flushed between timed steps (256 MB write)",
+                       "near_tile": {"shape": shape, "packed": bool(bie.NEAR32_SHAPES[shape][0]),
+                                     "targets_per_thread": bie.NEAR32_SHAPES[shape][1],
+                                     "ctas_per_sm": bie.NEAR32_SHAPES[shape][2],
+                                     "autotune_ms_per_shape": [round(m, 4) for m in shape_ms]},
                        "parallelism": f"{world} independent replica(s)"},
             "s_per_shear_time": ms_per_step / 1e3 / dt,
             "s_per_shear_time_fp64": ms64 / 1e3 / dt,

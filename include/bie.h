@@ -106,6 +106,14 @@ typedef struct {
     int32_t close_capacity; /* maximum (target, body image) close pairs stored; 0 = no limit
                              * (the storage grows with the geometry) */
     int32_t residual;     /* BIE_MIXED refinement residual: BIE_FP64 (native double) or BIE_DF64 */
+    int32_t autotune;     /* 1: at bie_init, time the single-precision near-sum tile shapes on the
+                             context's own cells and keep the fastest (bie_near_shape); the shape sets
+                             the source splits, so results then agree across contexts to single-
+                             precision rounding only.  0: the default shape (bit-reproducible) */
+    int32_t graph;        /* 1: single-precision operator applications replay CUDA graphs captured
+                             once per geometry (same kernels, same results); 0: direct launches
+                             (the default: on GB300 the replay's extra copies cost about what the
+                             launches it saves do) */
 } bie_opts;
 
 typedef struct {
@@ -120,7 +128,7 @@ typedef struct {
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
  * warm_start 3, min_gap 0, device 0, close_factor 10, close_capacity 0,
- * residual BIE_DF64. */
+ * residual BIE_DF64, autotune 0, graph 0. */
 void bie_default_opts(bie_opts* opts);
 
 /* Create a context for one unit cell: lattice, viscosity mu, shear rate
@@ -310,6 +318,15 @@ int bie_features(bie_ctx* ctx, float* X, int32_t on_device);
  * It must take BIE_NET_FEATURES inputs and live on the context's device; the
  * caller keeps ownership and must not destroy it while attached. */
 int bie_set_warm_net(bie_ctx* ctx, const bie_net* net);
+
+/* Tile shapes of the single-precision near sum (packed = two lattice images
+ * per f32x2 instruction; targets per thread; resident CTAs per SM):
+ * 0 packed 2/5 (the default), 1 packed 1/8, 2 packed 3/4, 3 scalar 3/4,
+ * 4 scalar 2/5.  *shape receives the one in use; ms (BIE_NEAR32_SHAPES
+ * floats, may be NULL) the median launch time of each in milliseconds as
+ * opts.autotune measured it (0 where not measured). */
+#define BIE_NEAR32_SHAPES 5
+int bie_near_shape(bie_ctx* ctx, int32_t* shape, float* ms);
 
 /* Close-evaluation bookkeeping of the current geometry: number of stored
  * (target, body image) pairs, and pairs closer to the curve than the finest

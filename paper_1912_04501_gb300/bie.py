@@ -9,7 +9,7 @@ call raises -- there is no fallback implementation.
 The functions carry the C names:
     bie_default_opts, bie_init, bie_destroy, bie_size, bie_nodes, bie_apply,
     bie_rhs, bie_solve, bie_velocities, bie_step, bie_get_state,
-    bie_set_state, bie_set_stream, bie_close_info, bie_profile, bie_profile_read,
+    bie_set_state, bie_set_stream, bie_close_info, bie_near_shape, bie_profile, bie_profile_read,
     bie_apply_static, bie_init_batch, bie_cells, bie_features, bie_set_warm_net,
     bie_get_history, bie_set_history,
     bie_net_init, bie_net_destroy, bie_net_last_error, bie_net_size,
@@ -29,6 +29,9 @@ LIB_PATH = os.path.join(HERE, "libbie.so")
 BIE_OK, BIE_EINVAL, BIE_ENOCONV, BIE_ECOLLIDE, BIE_ENUMERIC, BIE_ECUDA, BIE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 BIE_FP64, BIE_MIXED, BIE_DF64 = 0, 1, 2
 BIE_NET_FEATURES, BIE_NET_HIDDEN = 13, 64
+BIE_NEAR32_SHAPES = 5
+# (packed, targets per thread, CTAs per SM) of each single-precision near-sum tile shape
+NEAR32_SHAPES = [(1, 2, 5), (1, 1, 8), (1, 3, 4), (0, 3, 4), (0, 2, 5)]
 _NAMES = {0: "BIE_OK", -1: "BIE_EINVAL", -2: "BIE_ENOCONV", -3: "BIE_ECOLLIDE", -4: "BIE_ENUMERIC",
           -5: "BIE_ECUDA", -6: "BIE_ENOMEM"}
 
@@ -53,7 +56,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("n_proxy", c_int32), ("proxy_radius", c_double), ("n_coll", c_int32),
                 ("lam_rel", c_double), ("gmres_tol", c_double), ("gmres_max", c_int32), ("inner_tol", c_double),
                 ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32),
-                ("close_factor", c_double), ("close_capacity", c_int32), ("residual", c_int32)]
+                ("close_factor", c_double), ("close_capacity", c_int32), ("residual", c_int32),
+                ("autotune", c_int32), ("graph", c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -112,6 +116,7 @@ def library():
         "bie_get_state": (c_int32, [vp, vp, vp, vp, vp, vp]),
         "bie_set_state": (c_int32, [vp, c_double, vp, vp, vp, vp]),
         "bie_close_info": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+        "bie_near_shape": (c_int32, [vp, ctypes.POINTER(c_int32), vp]),
         "bie_apply_static": (c_int32, [vp, vp, vp]),
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
@@ -148,7 +153,7 @@ def exported_symbols():
                         "bie_set_warm_net", "bie_net_init", "bie_net_destroy", "bie_net_last_error",
                         "bie_net_size", "bie_net_set_stream", "bie_net_set_params", "bie_net_get_params",
                         "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step", "bie_get_history",
-                        "bie_set_history")
+                        "bie_set_history", "bie_near_shape")
             if hasattr(L, n)]
 
 
@@ -339,6 +344,14 @@ class Context:
         """Attach a Net for warm_start = 2 (None detaches)."""
         self._warm_net = net
         self._check(library().bie_set_warm_net(self.h, None if net is None else net.h))
+
+    def near_shape(self):
+        """(index of the single-precision near-sum tile shape in use, median
+        launch time in ms of each shape as opts.autotune measured it)."""
+        sh = c_int32()
+        ms = (ctypes.c_float * BIE_NEAR32_SHAPES)()
+        self._check(library().bie_near_shape(self.h, ctypes.byref(sh), ms))
+        return sh.value, list(ms)
 
     def close_info(self):
         n, u = c_int32(), c_int32()

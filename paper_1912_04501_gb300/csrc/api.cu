@@ -30,6 +30,7 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 }
 
 static void free_all(bie_ctx* c) {
+    free_graph(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
                     c->tgt32, c->posdf, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
@@ -260,6 +261,8 @@ static int check_opts(const bie_opts& o, std::string& why) {
     else if (o.warm_start < 0 || o.warm_start > 3) why = "warm_start must be 0, 1, 2 or 3";
     else if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
         why = "close_factor must be in [0, 100], close_capacity >= 0";
+    else if ((o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1))
+        why = "autotune and graph must be 0 or 1";
     else return 0;
     return 1;
 }
@@ -288,6 +291,8 @@ void bie_default_opts(bie_opts* o) {
     o->close_factor = 10.0;
     o->close_capacity = 0;
     o->residual = BIE_DF64;
+    o->autotune = 0;
+    o->graph = 0;
 }
 
 int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
@@ -518,6 +523,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : build_dot_chunks(c);
     rc = rc ? rc : build_dirichlet_tables(c, 64);
     rc = rc ? rc : rebuild(c);
+    if (o.autotune) rc = rc ? rc : autotune_near32(c);
     rc = rc ? rc : cu(cudaStreamSynchronize(c->stream), "init sync");
     if (rc) {
         std::string e = c->err;
@@ -874,6 +880,14 @@ int bie_features(bie_ctx* c, float* X, int32_t on_device) {
         BIE_CUDA(c, cudaMemcpyAsync(X, c->sv.feat, (size_t)kNetFeatures * c->N * sizeof(float),
                                     cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_near_shape(bie_ctx* c, int32_t* shape, float* ms) {
+    if (!c) return BIE_EINVAL;
+    if (shape) *shape = c->shape32;
+    if (ms)
+        for (int k = 0; k < kNear32Shapes; ++k) ms[k] = c->tune_ms[k];
     return BIE_OK;
 }
 

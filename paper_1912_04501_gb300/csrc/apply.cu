@@ -85,8 +85,8 @@ __device__ __forceinline__ bool item_range(const int4* items, const Cell* cells,
 // zero-distance self pair is absorbed by a 1e-30 floor on r^2 (its r.n and
 // r.q are exactly zero, so it contributes 0).
 // ---------------------------------------------------------------------------
-template <int TPT, bool COMP>
-__global__ void __launch_bounds__(kNearThreads)
+template <int TPT, bool COMP, int MINB>
+__global__ void __launch_bounds__(kNearThreads, MINB)
 k_near32(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
          const float4* __restrict__ src, float2* __restrict__ part) {
     __shared__ float4 s_src[kNearTile];
@@ -171,8 +171,8 @@ k_near32(const int4* __restrict__ items, const Cell* __restrict__ cells, const f
 // the scalar kernel's (the single-precision close pass relies on that); only
 // the grouping of the accumulations differs (lane 0 sums images 0, 2, 4, 6,
 // lane 1 images 1, 3, 5, 7, a scalar accumulator image 8).
-template <int TPT, bool COMP>
-__global__ void __launch_bounds__(kNearThreads, kNear32CtasPerSM)
+template <int TPT, bool COMP, int MINB>
+__global__ void __launch_bounds__(kNearThreads, MINB)
 k_near32x2(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
            const float4* __restrict__ src, float2* __restrict__ part) {
     __shared__ float4 s_src[kNearTile];
@@ -839,8 +839,12 @@ __global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // near-sum work items
 // ---------------------------------------------------------------------------
-static int near_tile(int prec) { return prec == 0 ? kNearThreads * kNear32TPT : kNearThreads; }
-static int near_ctas_per_sm(int prec) { return prec == 0 ? kNear32CtasPerSM : (prec == 1 ? 5 : 4); }
+static int near_tile(int shape32, int prec) {
+    return prec == 0 ? kNearThreads * kNear32ShapeList[shape32].tpt : kNearThreads;
+}
+static int near_ctas_per_sm(int shape32, int prec) {
+    return prec == 0 ? kNear32ShapeList[shape32].ctas : (prec == 1 ? 5 : 4);
+}
 
 // Source splits of every cell for one precision.  All items of one launch
 // cost about the same per staged source whatever their targets (masked
@@ -879,44 +883,52 @@ static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, s
 
 // Items (cell, target tile, source split) for every precision; also sets each
 // cell's splits and partial offsets and uploads the cell table.
-int build_near_items(bie_ctx* c) {
-    for (int prec = 0; prec < 3; ++prec) {
-        const int tile = near_tile(prec);
-        std::vector<int> splits;
-        choose_splits(c->cells_h, tile, near_ctas_per_sm(prec) * kSMs, splits);
-        std::vector<int4> items;
-        long long off = 0;
-        for (int ci = 0; ci < c->ncell; ++ci) {
-            Cell& cl = c->cells_h[ci];
-            const int n = cl.n_nodes;
-            cl.splits[prec] = splits[ci];
-            cl.part_off[prec] = off;
-            off += (long long)splits[ci] * n;
-            const int tiles = (n + tile - 1) / tile;
-            for (int t = 0; t < tiles; ++t)
-                for (int s = 0; s < splits[ci]; ++s) items.push_back(make_int4(ci, t, s, 0));
-        }
-        const size_t bytes = off * (prec == 0 ? sizeof(float2) : sizeof(double2));
-        if (bytes > c->ws.part_bytes) return fail(c, BIE_EINVAL, "near-sum partial buffer too small");
-        if (c->near[prec].items) cudaFree(c->near[prec].items);
-        c->near[prec].items = nullptr;
-        BIE_CUDA(c, cudaMalloc((void**)&c->near[prec].items, items.size() * sizeof(int4)));
-        BIE_CUDA(c, cudaMemcpy(c->near[prec].items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-        c->near[prec].count = (int)items.size();
+// Items of one precision for the context's current single-precision shape.
+static int build_near_items_prec(bie_ctx* c, int prec) {
+    const int tile = near_tile(c->shape32, prec);
+    std::vector<int> splits;
+    choose_splits(c->cells_h, tile, near_ctas_per_sm(c->shape32, prec) * kSMs, splits);
+    std::vector<int4> items;
+    long long off = 0;
+    for (int ci = 0; ci < c->ncell; ++ci) {
+        Cell& cl = c->cells_h[ci];
+        const int n = cl.n_nodes;
+        cl.splits[prec] = splits[ci];
+        cl.part_off[prec] = off;
+        off += (long long)splits[ci] * n;
+        const int tiles = (n + tile - 1) / tile;
+        for (int t = 0; t < tiles; ++t)
+            for (int s = 0; s < splits[ci]; ++s) items.push_back(make_int4(ci, t, s, 0));
     }
+    const size_t bytes = off * (prec == 0 ? sizeof(float2) : sizeof(double2));
+    if (bytes > c->ws.part_bytes) return fail(c, BIE_EINVAL, "near-sum partial buffer too small");
+    if (c->near[prec].items) BIE_CUDA(c, cudaFree(c->near[prec].items));
+    c->near[prec].items = nullptr;
+    BIE_CUDA(c, cudaMalloc((void**)&c->near[prec].items, items.size() * sizeof(int4)));
+    BIE_CUDA(c, cudaMemcpy(c->near[prec].items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    c->near[prec].count = (int)items.size();
+    return BIE_OK;
+}
+
+int build_near_items(bie_ctx* c) {
+    for (int prec = 0; prec < 3; ++prec)
+        if (int rc = build_near_items_prec(c, prec)) return rc;
+    ++c->epoch;
     return upload_cells(c, c->stream);
 }
 
-// Bytes of the near-sum partial buffer (largest over the precisions).
+// Bytes of the near-sum partial buffer (largest over the precisions and the
+// single-precision shapes the autotuner may pick).
 size_t near_part_bytes(const bie_ctx* c) {
     size_t best = 0;
-    for (int prec = 0; prec < 3; ++prec) {
-        std::vector<int> splits;
-        choose_splits(c->cells_h, near_tile(prec), near_ctas_per_sm(prec) * kSMs, splits);
-        long long off = 0;
-        for (size_t k = 0; k < splits.size(); ++k) off += (long long)splits[k] * c->cells_h[k].n_nodes;
-        best = std::max(best, (size_t)off * (prec == 0 ? sizeof(float2) : sizeof(double2)));
-    }
+    for (int prec = 0; prec < 3; ++prec)
+        for (int sh = 0; sh < (prec == 0 ? kNear32Shapes : 1); ++sh) {
+            std::vector<int> splits;
+            choose_splits(c->cells_h, near_tile(sh, prec), near_ctas_per_sm(sh, prec) * kSMs, splits);
+            long long off = 0;
+            for (size_t k = 0; k < splits.size(); ++k) off += (long long)splits[k] * c->cells_h[k].n_nodes;
+            best = std::max(best, (size_t)off * (prec == 0 ? sizeof(float2) : sizeof(double2)));
+        }
     return best;
 }
 
@@ -926,54 +938,80 @@ size_t near_part32_elems(const bie_ctx* c) {
     return (size_t)(last.part_off[0] + (long long)last.splits[0] * last.n_nodes);
 }
 
+template <int TPT, int MINB, bool PACKED>
+static void near32_variant(bool comp, int blocks, cudaStream_t st, const int4* items, const Cell* cells,
+                           const float4* tgt, const float4* src, float2* part) {
+    if (PACKED) {
+        if (comp)
+            k_near32x2<TPT, true, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+        else
+            k_near32x2<TPT, false, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+    } else {
+        if (comp)
+            k_near32<TPT, true, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+        else
+            k_near32<TPT, false, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+    }
+}
+
 static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
     const NearItems& it = c->near[0];
     if (it.count == 0) return BIE_OK;
     // splits with many sources keep their accuracy through compensated tile sums
     int maxchunk = 0;
     for (const Cell& cl : c->cells_h) maxchunk = std::max(maxchunk, (cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
-    if (kNear32Pack) {
-        if (maxchunk > kNear32CompChunk)
-            k_near32x2<kNear32TPT, true><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src,
-                                                                                  part);
-        else
-            k_near32x2<kNear32TPT, false><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src,
-                                                                                   part);
-    } else if (maxchunk > kNear32CompChunk) {
-        k_near32<kNear32TPT, true><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
-    } else {
-        k_near32<kNear32TPT, false><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+    const bool comp = maxchunk > kNear32CompChunk;
+    // one case per entry of kNear32ShapeList (packed, targets per thread, CTAs per SM)
+    switch (c->shape32) {
+        case 0: near32_variant<2, 5, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        case 1: near32_variant<1, 8, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        case 2: near32_variant<3, 4, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        case 3: near32_variant<3, 4, false>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        default: near32_variant<2, 5, false>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
     }
     BIE_LAUNCH(c, "k_near32");
     return BIE_OK;
 }
+#define BIE_SHAPE_IS(k, p, t, m) \
+    (kNear32ShapeList[k].packed == (p) && kNear32ShapeList[k].tpt == (t) && kNear32ShapeList[k].ctas == (m))
+static_assert(kNear32Shapes == 5 && BIE_SHAPE_IS(0, 1, 2, 5) && BIE_SHAPE_IS(1, 1, 1, 8) && BIE_SHAPE_IS(2, 1, 3, 4) &&
+                  BIE_SHAPE_IS(3, 0, 3, 4) && BIE_SHAPE_IS(4, 0, 2, 5),
+              "launch_near32's cases must match kNear32ShapeList");
+#undef BIE_SHAPE_IS
 
 // ---------------------------------------------------------------------------
-static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precision, Workspace& ws) {
-    if (&ws == &c->ws) c->ws_x = nullptr;  // the workspace is about to change
+// One operator application in three parts: 0 pack the sources and body
+// moments, 1 the near sum (the part the profiler brackets with events),
+// 2 wall discrepancy, proxy fit and correction, close evaluation, assembly.
+static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, int precision, Workspace& ws) {
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
     const bool f32 = precision == BIE_MIXED;
     const bool df = precision == BIE_DF64;
     const int prec = f32 ? 0 : (df ? 2 : 1);
-    k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
-                                                 f32 ? ws.src32 : nullptr, ws.src64,
-                                                 df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
-    BIE_LAUNCH(c, "k_pack_moments");
-    if (int rc = prof_begin(c, prec == 0 ? 0 : (prec == 1 ? 1 : 2))) return rc;
-    if (f32) {
-        if (int rc = launch_near32(c, ws.src32, (float2*)ws.part)) return rc;
-    } else if (df) {
-        k_near_df<<<c->near[2].count, kNearThreads, 0, c->stream>>>(c->near[2].items, c->cells, c->x, c->y, c->nx,
-                                                                    c->ny, (const SrcDF*)ws.srcdf, (double2*)ws.part);
-        BIE_LAUNCH(c, "k_near_df");
-    } else {
-        k_near64<<<c->near[1].count, kNearThreads, 0, c->stream>>>(c->near[1].items, c->cells, c->x, c->y, c->nx,
-                                                                   c->ny, ws.src64, (double2*)ws.part);
-        BIE_LAUNCH(c, "k_near64");
+    if (part == 0) {
+        if (&ws == &c->ws) c->ws_x = nullptr;  // the workspace is about to change
+        k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                     f32 ? ws.src32 : nullptr, ws.src64,
+                                                     df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
+        BIE_LAUNCH(c, "k_pack_moments");
+        return BIE_OK;
     }
-    if (int rc = prof_end(c)) return rc;
+    if (part == 1) {
+        if (f32) return launch_near32(c, ws.src32, (float2*)ws.part);
+        if (df) {
+            k_near_df<<<c->near[2].count, kNearThreads, 0, c->stream>>>(c->near[2].items, c->cells, c->x, c->y,
+                                                                        c->nx, c->ny, (const SrcDF*)ws.srcdf,
+                                                                        (double2*)ws.part);
+            BIE_LAUNCH(c, "k_near_df");
+        } else {
+            k_near64<<<c->near[1].count, kNearThreads, 0, c->stream>>>(c->near[1].items, c->cells, c->x, c->y, c->nx,
+                                                                       c->ny, ws.src64, (double2*)ws.part);
+            BIE_LAUNCH(c, "k_near64");
+        }
+        return BIE_OK;
+    }
     const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
     if (f32)
         k_disc<true><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
@@ -1007,8 +1045,137 @@ static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precisi
     return BIE_OK;
 }
 
+static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precision, Workspace& ws) {
+    const int kind = precision == BIE_MIXED ? 0 : (precision == BIE_DF64 ? 2 : 1);
+    if (int rc = apply_part(c, 0, sigma, yout, precision, ws)) return rc;
+    if (int rc = prof_begin(c, kind)) return rc;
+    if (int rc = apply_part(c, 1, sigma, yout, precision, ws)) return rc;
+    if (int rc = prof_end(c)) return rc;
+    return apply_part(c, 2, sigma, yout, precision, ws);
+}
+
+// The single-precision application replayed from CUDA graphs (opts.graph):
+// the three parts of apply_part are captured once per epoch (any change of
+// their arguments: geometry, proxy fit, close pairs, work items) with fixed
+// input and output buffers, on a stream of the context's own (the caller's
+// stream may be the legacy default stream, which cannot capture).  Each
+// application copies sigma in, replays the parts on the context's stream --
+// with the profiler's events around the near sum, between the parts, as for
+// direct launches -- and copies the result out.  The same kernels in the
+// same order: the results are bit for bit those of the direct launches.
+static int apply_graph(bie_ctx* c, const double* sigma, double* yout) {
+    auto& g = c->graph;
+    const size_t bytes = 2 * (size_t)c->N * sizeof(double);
+    if (!g.in) {
+        BIE_CUDA(c, cudaMalloc((void**)&g.in, bytes));
+        BIE_CUDA(c, cudaMalloc((void**)&g.out, bytes));
+        BIE_CUDA(c, cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
+    }
+    if (!g.exec[0] || g.epoch != c->epoch) {
+        for (auto& e : g.exec)
+            if (e) {
+                BIE_CUDA(c, cudaGraphExecDestroy(e));
+                e = nullptr;
+            }
+        cudaStream_t user = c->stream;
+        c->stream = g.capture;
+        const long long l0 = c->launches;
+        int rc = BIE_OK;
+        cudaError_t e = cudaSuccess;
+        for (int part = 0; part < 3 && !rc && e == cudaSuccess; ++part) {
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) break;
+            rc = apply_part(c, part, g.in, g.out, BIE_MIXED, c->ws);
+            e = cudaStreamEndCapture(g.capture, &graph);
+            if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec[part], graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+        }
+        c->stream = user;
+        g.kernels = c->launches - l0;
+        c->launches = l0;
+        if (rc || e != cudaSuccess) {
+            for (auto& x : g.exec)
+                if (x) {
+                    cudaGraphExecDestroy(x);
+                    x = nullptr;
+                }
+            return rc ? rc : cuda_check(c, e, "graph capture");
+        }
+        g.epoch = c->epoch;
+    }
+    c->ws_x = nullptr;
+    BIE_CUDA(c, cudaMemcpyAsync(g.in, sigma, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    BIE_CUDA(c, cudaGraphLaunch(g.exec[0], c->stream));
+    if (int rc = prof_begin(c, 0)) return rc;
+    BIE_CUDA(c, cudaGraphLaunch(g.exec[1], c->stream));
+    if (int rc = prof_end(c)) return rc;
+    BIE_CUDA(c, cudaGraphLaunch(g.exec[2], c->stream));
+    BIE_CUDA(c, cudaMemcpyAsync(yout, g.out, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->launches += g.kernels;
+    return BIE_OK;
+}
+
+void free_graph(bie_ctx* c) {
+    auto& g = c->graph;
+    for (auto& e : g.exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (g.in) cudaFree(g.in);
+    if (g.out) cudaFree(g.out);
+    if (g.capture) cudaStreamDestroy(g.capture);
+    for (auto& e : g.exec) e = nullptr;
+    g.in = g.out = nullptr;
+    g.capture = nullptr;
+}
+
 int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
+    if (precision == BIE_MIXED && c->opts.graph) return apply_graph(c, sigma, yout);
     return apply_impl(c, sigma, yout, precision, c->ws);
+}
+
+// Time every single-precision tile shape on the context's own cells and keep
+// the fastest (opts.autotune).  The sources are packed from the right-hand
+// side (the work does not depend on the values); per shape one warm-up and
+// three timed launches, the median kept.  The shape decides the source splits
+// and so the rounding of the single-precision sums: contexts tuned to
+// different shapes agree to single-precision accuracy, not bit for bit.
+int autotune_near32(bie_ctx* c) {
+    const int N = c->N;
+    k_rhs<<<(N + 255) / 256, 256, 0, c->stream>>>(c->nx, c->ny, c->node_cell, c->cells, N,
+                                                  reinterpret_cast<double2*>(c->sv.r));
+    BIE_LAUNCH(c, "k_rhs");
+    if (int rc = apply_impl(c, c->sv.r, c->sv.d, BIE_MIXED, c->ws)) return rc;  // packs ws.src32
+    cudaEvent_t ev[2];
+    BIE_CUDA(c, cudaEventCreate(&ev[0]));
+    BIE_CUDA(c, cudaEventCreate(&ev[1]));
+    auto ck = [c](cudaError_t e, const char* what) { return e == cudaSuccess ? BIE_OK : cuda_check(c, e, what); };
+    int best = 0;
+    int rc = BIE_OK;
+    for (int sh = 0; sh < kNear32Shapes && !rc; ++sh) {
+        c->shape32 = sh;
+        if ((rc = build_near_items_prec(c, 0)) || (rc = upload_cells(c, c->stream))) break;
+        float t[3];
+        for (int k = 0; k < 4 && !rc; ++k) {
+            if (k > 0) rc = ck(cudaEventRecord(ev[0], c->stream), "cudaEventRecord");
+            if (!rc) rc = launch_near32(c, c->ws.src32, (float2*)c->ws.part);
+            if (!rc && k > 0) {
+                rc = ck(cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+                if (!rc) rc = ck(cudaEventSynchronize(ev[1]), "cudaEventSynchronize");
+                if (!rc) rc = ck(cudaEventElapsedTime(&t[k - 1], ev[0], ev[1]), "cudaEventElapsedTime");
+            }
+        }
+        if (rc) break;
+        std::sort(t, t + 3);
+        c->tune_ms[sh] = t[1];
+        if (t[1] < c->tune_ms[best]) best = sh;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    c->shape32 = best;
+    if ((rc = build_near_items_prec(c, 0))) return rc;
+    ++c->epoch;
+    return upload_cells(c, c->stream);
 }
 
 // The single-precision-pair operator application with every per-call buffer

@@ -35,26 +35,22 @@ constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
 #ifndef BIE_NEAR_THREADS
 #define BIE_NEAR_THREADS 128
 #endif
-// Tile shape of the single-precision near sum, measured on GB300: the packed
-// kernel (two images per f32x2 instruction) with 2 targets per thread (94
-// registers, 5 CTAs per SM) beats the scalar kernel with 3 targets per thread
-// (the best scalar shape) by 1 % on the 25-ellipse cell, 4 % on the
-// 400-ellipse cell and 9 % on the 64-cell ensemble; 3 and 4 targets per
-// thread packed fall in between.
-#ifndef BIE_NEAR32_PACK
-#define BIE_NEAR32_PACK 1
-#endif
-#ifndef BIE_NEAR32_TPT
-#define BIE_NEAR32_TPT 2
-#endif
-#ifndef BIE_NEAR32_CTAS_PER_SM
-#define BIE_NEAR32_CTAS_PER_SM 5
-#endif
 constexpr int kNearThreads = BIE_NEAR_THREADS;  // threads per near-sum block
 constexpr int kNearTile = 256;                  // sources staged per shared-memory tile
-constexpr int kNear32TPT = BIE_NEAR32_TPT;      // targets per thread, single precision
-constexpr bool kNear32Pack = BIE_NEAR32_PACK != 0;  // two images per packed f32x2 instruction
-constexpr int kNear32CtasPerSM = BIE_NEAR32_CTAS_PER_SM;  // resident k_near32 CTAs per SM (register-limited)
+// Tile shapes of the single-precision near sum: packed (two images per f32x2
+// instruction) or scalar, targets per thread, and the resident CTAs per SM
+// the kernel is compiled for (its register budget; also the wave model's
+// slots).  Measured on GB300, the first (packed, 2 targets per thread, 5 CTAs
+// per SM) beats the best scalar shape (3 targets per thread) by 1 % on the
+// 25-ellipse cell, 4 % on the 400-ellipse cell and 9 % on the 64-cell
+// ensemble, so it is the default; opts.autotune times all of them on the
+// context's own cells and keeps the fastest.
+struct Near32Shape {
+    int packed, tpt, ctas;
+};
+constexpr int kNear32Shapes = 5;
+constexpr Near32Shape kNear32ShapeList[kNear32Shapes] = {{1, 2, 5}, {1, 1, 8}, {1, 3, 4}, {0, 3, 4}, {0, 2, 5}};
+static_assert(kNear32Shapes == BIE_NEAR32_SHAPES, "shape count of the public header");
 constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
 constexpr int kDiscSplits = 8;        // source splits per wall point of the wall-discrepancy kernel
 constexpr int kCorrLanes = 8;         // lanes per target in k_correct (a power of two <= 32)
@@ -227,6 +223,18 @@ struct bie_ctx {
     bie::Solver sv;
     bie::Close cl;
     bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
+    int shape32 = 0;            // tile shape of the single-precision near sum (kNear32ShapeList)
+    unsigned long long epoch = 0;  // bumped whenever a kernel argument of the operator application changes
+    // single-precision application captured as CUDA graphs (opts.graph)
+    struct {
+        cudaStream_t capture = nullptr;   // stream the capture is recorded on
+        cudaGraphExec_t exec[3] = {};     // the three parts of the application
+        unsigned long long epoch = ~0ULL; // epoch the graph was captured at
+        double* in = nullptr;             // 2N: density the graph reads
+        double* out = nullptr;            // 2N: result it writes
+        long long kernels = 0;            // launches one replay stands for
+    } graph;
+    float tune_ms[bie::kNear32Shapes] = {};  // autotuner: median launch time per shape (0 = not timed)
     const bie_net* net = nullptr;  // warm-start network (not owned)
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
@@ -275,6 +283,8 @@ void gauss_legendre_half(int m, std::vector<double>& s);
 // close.cu ------------------------------------------------------------------
 int build_close(bie_ctx* c);                               // per geometry
 int build_dirichlet_tables(bie_ctx* c, int rho_max);       // tables for rho = 2 .. rho_max
+int autotune_near32(bie_ctx* c);                           // opts.autotune: time the tile shapes, keep the fastest
+void free_graph(bie_ctx* c);
 // T += C sigma; with src32 (the single-precision path's packed sources) the
 // own-body and close pairs of the single-precision near sum are also redone
 // with positions differenced in double precision

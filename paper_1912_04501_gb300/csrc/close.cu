@@ -359,6 +359,7 @@ static int regrow(bie_ctx* c, T** p, size_t count) {
 }
 
 int build_close(bie_ctx* c) {
+    ++c->epoch;  // close pairs, blocks and their storage change
     c->cl.npairs = 0;
     c->cl.rho_max = 0;
     k_body_h<<<c->nb, 256, 0, c->stream>>>(c->w, c->body);

@@ -255,6 +255,7 @@ __global__ void k_form_P(const double* __restrict__ Aall, int R, int C, const do
 }
 
 int build_geometry(bie_ctx* c) {
+    ++c->epoch;  // node data and the adopted proxy fit (pointers swapped by a time step)
     c->ws_x = nullptr;  // positions change: the workspace's sources are stale
     int bs = 256, gs = (c->N + bs - 1) / bs;
     k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->node_cell, c->cells, c->N, c->x, c->y, c->nx, c->ny,

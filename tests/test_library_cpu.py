@@ -68,7 +68,8 @@ def test_null_arguments(lib):
 
 @pytest.mark.parametrize("opt", [dict(n_proxy=2), dict(n_proxy=300), dict(n_coll=1), dict(gmres_max=0),
                                  dict(gmres_max=5000), dict(warm_start=4), dict(residual=1),
-                                 dict(close_factor=-1.0), dict(precision=3), dict(gmres_tol=0.0)])
+                                 dict(close_factor=-1.0), dict(precision=3), dict(gmres_tol=0.0),
+                                 dict(autotune=2), dict(graph=-1)])
 def test_invalid_options_rejected_without_gpu(lib, opt):
     from paper_1912_04501_gb300 import workloads
     with pytest.raises(bie.BieError) as e:
