@@ -114,6 +114,10 @@ typedef struct {
                              once per geometry (same kernels, same results); 0: direct launches
                              (the default: on GB300 the replay's extra copies cost about what the
                              launches it saves do) */
+    int32_t precond;      /* 1: right-precondition GMRES with the inverse of the dense operator block
+                             on the nodes inside another curve's close-evaluation zone (at most
+                             2048, the closest kept; I/2 elsewhere), rebuilt with every geometry:
+                             for nearly touching bodies (single-cell contexts only).  0: none */
 } bie_opts;
 
 typedef struct {
@@ -128,7 +132,7 @@ typedef struct {
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
  * warm_start 3, min_gap 0, device 0, close_factor 10, close_capacity 0,
- * residual BIE_DF64, autotune 0, graph 0. */
+ * residual BIE_DF64, autotune 0, graph 0, precond 0. */
 void bie_default_opts(bie_opts* opts);
 
 /* Create a context for one unit cell: lattice, viscosity mu, shear rate

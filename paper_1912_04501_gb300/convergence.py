@@ -26,11 +26,12 @@ STUDY = {
 }
 
 
-def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_max=1000, max_refine=8):
+def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_max=1000, max_refine=8, precond=1):
     """One quasi-static solve; returns a dict with the body velocities, the
     solve statistics and the wall times of the set-up (geometry, proxy fit,
     close-evaluation blocks) and of the solve.  Near contact the system needs
-    hundreds of GMRES iterations per sweep, hence long cycles (gmres_max).
+    hundreds of GMRES iterations per sweep, hence long cycles (gmres_max),
+    and the contact-block preconditioner (precond) cuts them several-fold.
     At d = 1e-5 the single-precision sweeps stall and the solver continues on
     the double-float operator; the residual then levels off near 1e-9, which
     is reported (allow_noconv) rather than raised."""
@@ -39,7 +40,7 @@ def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_m
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx = bie.Context(cell, precision=precision, gmres_tol=gmres_tol, gmres_max=gmres_max,
-                      max_refine=max_refine)
+                      max_refine=max_refine, precond=precond)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     sigma, info = ctx.solve(allow_noconv=True)
@@ -53,16 +54,16 @@ def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_m
                 setup_s=t1 - t0, solve_s=t2 - t1)
 
 
-def study(gap, ns, n_ref, precision=bie.BIE_MIXED, log=None):
+def study(gap, ns, n_ref, precision=bie.BIE_MIXED, precond=1, log=None):
     """Errors max|v - v_ref| and max|omega - omega_ref| over both bodies for
     each N in ns, the reference being the solve with n_ref nodes."""
-    ref = solve_two_ellipses(gap, n_ref, precision)
+    ref = solve_two_ellipses(gap, n_ref, precision, precond=precond)
     if log:
         log(f"d={gap:g} reference N={n_ref}: {ref['iterations']} its, {ref['close_pairs']} close pairs, "
             f"set-up {ref['setup_s']:.2f} s, solve {ref['solve_s']:.2f} s")
     rows = []
     for n in ns:
-        r = solve_two_ellipses(gap, n, precision)
+        r = solve_two_ellipses(gap, n, precision, precond=precond)
         r["err_v"] = float(np.abs(r["v"] - ref["v"]).max())
         r["err_omega"] = float(np.abs(r["omega"] - ref["omega"]).max())
         rows.append(r)
@@ -77,11 +78,12 @@ def main():
     ap = argparse.ArgumentParser(description="two-ellipse convergence study (Sec. 8, Example 1)")
     ap.add_argument("--gaps", type=float, nargs="*", default=sorted(STUDY, reverse=True))
     ap.add_argument("--fp64", action="store_true", help="plain FP64 operator instead of mixed precision")
+    ap.add_argument("--no-precond", action="store_true", help="without the contact-block preconditioner")
     a = ap.parse_args()
     prec = bie.BIE_FP64 if a.fp64 else bie.BIE_MIXED
     for gap in a.gaps:
         ns, n_ref = STUDY[min(STUDY, key=lambda g: abs(np.log(g / gap)))]
-        study(gap, ns, n_ref, prec, log=print)
+        study(gap, ns, n_ref, prec, precond=0 if a.no_precond else 1, log=print)
 
 
 if __name__ == "__main__":

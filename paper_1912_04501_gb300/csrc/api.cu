@@ -31,6 +31,7 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 
 static void free_all(bie_ctx* c) {
     free_graph(c);
+    free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
                     c->tgt32, c->posdf, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
@@ -231,7 +232,9 @@ static int rebuild(bie_ctx* c) {
     if (rc) return rc;
     rc = build_proxy_fit(c);
     if (rc) return rc;
-    return build_close(c);
+    rc = build_close(c);
+    if (rc) return rc;
+    return build_precond(c);
 }
 
 // The current lattices' e2 (host mirror) to the device array the proxy fits read.
@@ -261,8 +264,9 @@ static int check_opts(const bie_opts& o, std::string& why) {
     else if (o.warm_start < 0 || o.warm_start > 3) why = "warm_start must be 0, 1, 2 or 3";
     else if (!(o.close_factor >= 0) || o.close_factor > 100 || o.close_capacity < 0)
         why = "close_factor must be in [0, 100], close_capacity >= 0";
-    else if ((o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1))
-        why = "autotune and graph must be 0 or 1";
+    else if ((o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
+             (o.precond != 0 && o.precond != 1))
+        why = "autotune, graph and precond must be 0 or 1";
     else return 0;
     return 1;
 }
@@ -293,6 +297,7 @@ void bie_default_opts(bie_opts* o) {
     o->residual = BIE_DF64;
     o->autotune = 0;
     o->graph = 0;
+    o->precond = 0;
 }
 
 int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
@@ -313,6 +318,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     {
         std::string why;
         if (check_opts(o, why)) return bad(why);
+        if (o.precond && n_cells > 1) return bad("precond is for single-cell contexts");
     }
     c->device = o.device;
     c->ncell = n_cells;
@@ -747,6 +753,7 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         std::swap(c->cl.dmin, c->cl.dmin_prev);
         c->cl.have_dprev = true;
         if ((rc = build_close(c))) return rc;
+        if ((rc = build_precond(c))) return rc;
         if (c->opts.min_gap > 0 && c->cl.min_gap < c->opts.min_gap) {
             char msg[160];
             snprintf(msg, sizeof msg, "bodies closer than min_gap after the step to t = %.6g: gap %.3e < %.3e", c->t,

@@ -62,6 +62,7 @@ constexpr int kCloseSlots = 8;        // close body images per target node
 constexpr int kMaxRho = 4096;         // largest fine-rule factor of the close evaluation (a power of two)
 constexpr int kCloseAccNodes = 4096;  // source nodes per CTA of k_close_blocks (shared accumulators)
 constexpr int kMaxBodyNodes = 16384;  // nodes per body
+constexpr int kPcMaxNodes = 2048;     // nodes of the contact-block preconditioner (opts.precond)
 constexpr int kMaxCells = 4096;
 constexpr int kWallStride = 24;       // doubles per wall point of the wall table (see k_wall_table)
 constexpr int kNetHidden = 64;        // hidden width of the warm-start network
@@ -225,6 +226,19 @@ struct bie_ctx {
     bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
     int shape32 = 0;            // tile shape of the single-precision near sum (kNear32ShapeList)
     unsigned long long epoch = 0;  // bumped whenever a kernel argument of the operator application changes
+    // contact-block right preconditioner (opts.precond, precond.cu)
+    struct {
+        int s = 0;                  // nodes in S (0: off for this geometry)
+        int cap = 0;                // nodes the block storage holds
+        int* nodes = nullptr;       // s: node of each block row pair
+        int* pos = nullptr;         // N: block index of each node, -1 outside S
+        double* aug = nullptr;      // 2s x 4s: [A_SS | I], after elimination [I | A_SS^-1]
+        double* f = nullptr;        // 2s: Gauss-Jordan column
+        double* prow = nullptr;     // 4s: Gauss-Jordan pivot row
+        int* status = nullptr;      // 1: zero pivot
+        double* z = nullptr;        // 2N: preconditioned vector
+        double* t = nullptr;        // 2N: combination before preconditioning
+    } pc;
     // single-precision application captured as CUDA graphs (opts.graph)
     struct {
         cudaStream_t capture = nullptr;   // stream the capture is recorded on
@@ -284,6 +298,9 @@ void gauss_legendre_half(int m, std::vector<double>& s);
 int build_close(bie_ctx* c);                               // per geometry
 int build_dirichlet_tables(bie_ctx* c, int rho_max);       // tables for rho = 2 .. rho_max
 int autotune_near32(bie_ctx* c);                           // opts.autotune: time the tile shapes, keep the fastest
+int build_precond(bie_ctx* c);                             // opts.precond: contact block of the current geometry
+int precond_apply(bie_ctx* c, const double* v, double* z); // z = M^-1 v
+void free_precond(bie_ctx* c);
 void free_graph(bie_ctx* c);
 // T += C sigma; with src32 (the single-precision path's packed sources) the
 // own-body and close pairs of the single-precision near sum are also redone

@@ -385,10 +385,17 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
         k_scale_copy<<<gs, bs, 0, c->stream>>>(r, fac_d, c->node_cell, Vk, n);
         BIE_LAUNCH(c, "k_scale_copy");
     }
-    // enqueue iteration k: w = A V_k, CGS2 against [C~, V_0 .. V_k],
+    // right preconditioning (opts.precond): the Krylov space is that of A M^-1
+    const bool pc = c->pc.s > 0;
+    // enqueue iteration k: w = A (M^-1) V_k, CGS2 against [C~, V_0 .. V_k],
     // V_{k+1} = w / |w| per cell, and the projections to the pinned host slot k % 2
     auto enqueue = [&](int k) -> int {
-        if (int rc = apply_device(c, Vk + (size_t)k * ld, w, prec)) return rc;
+        if (pc) {
+            if (int rc = precond_apply(c, Vk + (size_t)k * ld, c->pc.z)) return rc;
+            if (int rc = apply_device(c, c->pc.z, w, prec)) return rc;
+        } else if (int rc = apply_device(c, Vk + (size_t)k * ld, w, prec)) {
+            return rc;
+        }
         ++*n_apply;
         const int nv = nu + k + 1;
         double* hb = c->sv.h + (size_t)(k & 1) * slot;
@@ -479,8 +486,18 @@ static int gmres_cycle(bie_ctx* c, int prec, double* x, const double* r, const s
     }
     if (kk > 0) {
         BIE_CUDA(c, cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        k_combine<<<gs, bs, 0, c->stream>>>(Vk, ld, kk, coef, nc, c->node_cell, x, n);
-        BIE_LAUNCH(c, "k_combine");
+        if (pc) {
+            // x += M^-1 (V y)
+            BIE_CUDA(c, cudaMemsetAsync(c->pc.t, 0, ld * sizeof(double), c->stream));
+            k_combine<<<gs, bs, 0, c->stream>>>(Vk, ld, kk, coef, nc, c->node_cell, c->pc.t, n);
+            BIE_LAUNCH(c, "k_combine");
+            if (int rc = precond_apply(c, c->pc.t, c->pc.z)) return rc;
+            k_axpy<<<gs, bs, 0, c->stream>>>(1.0, c->pc.z, x, n);
+            BIE_LAUNCH(c, "k_axpy");
+        } else {
+            k_combine<<<gs, bs, 0, c->stream>>>(Vk, ld, kk, coef, nc, c->node_cell, x, n);
+            BIE_LAUNCH(c, "k_combine");
+        }
     }
     if (nu > 0) {
         double* coef2 = coef + (size_t)kmax * nc;

@@ -69,7 +69,7 @@ def test_null_arguments(lib):
 @pytest.mark.parametrize("opt", [dict(n_proxy=2), dict(n_proxy=300), dict(n_coll=1), dict(gmres_max=0),
                                  dict(gmres_max=5000), dict(warm_start=4), dict(residual=1),
                                  dict(close_factor=-1.0), dict(precision=3), dict(gmres_tol=0.0),
-                                 dict(autotune=2), dict(graph=-1)])
+                                 dict(autotune=2), dict(graph=-1), dict(precond=2)])
 def test_invalid_options_rejected_without_gpu(lib, opt):
     from paper_1912_04501_gb300 import workloads
     with pytest.raises(bie.BieError) as e:
@@ -98,3 +98,10 @@ def test_network_arguments_rejected_without_gpu(lib):
     assert lib.bie_net_init(ctypes.byref(h), 17, 0) == bie.BIE_EINVAL
     assert lib.bie_net_forward(None, None, 0, None) == bie.BIE_EINVAL
     assert lib.bie_features(None, None, 0) == bie.BIE_EINVAL
+
+
+def test_precond_needs_single_cell_without_gpu(lib):
+    from paper_1912_04501_gb300 import workloads
+    with pytest.raises(bie.BieError) as e:
+        bie.Context([workloads.config1(), workloads.config1()], precond=1)
+    assert e.value.code == bie.BIE_EINVAL
