@@ -227,3 +227,64 @@ def euler_step(susp, e2_0, t, dt, op_kwargs, sigma0=None, tol=1e-10):
         bodies.append(nb)
     new = geometry.Suspension(e1, e2, susp.centre, susp.mu, susp.gamma, bodies)
     return new, t1, dict(sigma=sigma, v=v, omega=omega, mu_eff=mu_eff, iters=iters, res=res)
+
+
+# ----------------------------------------------------------------------------
+# the paper's own periodizer, as an independent check of the 3 x 3 reading
+# ----------------------------------------------------------------------------
+class OperatorUtilde(Operator):
+    """The same BIE operator with the paper's periodizer (Def. Gnear, remark
+    after Eq. W): each source node contributes its four lattice images inside
+    the doubled cell U~, chosen per node by its lattice coordinates, and the
+    proxies sit on the walls of U~ (periodic.proxy_points_box).  The wall
+    discrepancy is evaluated literally.  Both periodizers define the same
+    periodic Green's function up to constants, so densities, rotation rates
+    and mu_eff agree to discretisation accuracy.  No close evaluation: used
+    on geometries whose curves are all farther apart than the close zone."""
+
+    def __init__(self, susp, n_proxy=128, n_coll=32, lam_rel=1e-8):
+        self.s = susp
+        self.M = n_proxy
+        self.m = n_coll
+        self.yp = periodic.proxy_points_box(susp.e1, susp.e2, susp.centre, n_proxy)
+        self.Q = periodic.proxy_matrix(susp.e1, susp.e2, susp.centre, n_coll, self.yp, susp.mu)
+        self.Qp = periodic.proxy_solution_operator(self.Q, lam_rel)
+        self.img = periodic.utilde_shifts(susp.e1, susp.e2, susp.centre, susp.x)
+        self.close = None
+        self.zero = [np.zeros(2)]
+
+    def _sources(self, q):
+        return periodic.expand_images(self.s.x, q, self.img)
+
+    def proxy_strengths(self, q):
+        s = self.s
+        Y, Q, _ = self._sources(q)
+        g = periodic.near_discrepancy_images(s.e1, s.e2, s.centre, self.m, Y, Q, s.mu)
+        dt = periodic.corrected_discrepancy(g, q.sum(0), s.e1, s.e2, self.m)
+        return periodic.apply_operator_exact(self.Qp, dt), dt
+
+    def traction(self, sigma, targets=None):
+        s = self.s
+        q, _, _ = self.density_moments(sigma)
+        idx = np.arange(s.N) if targets is None else np.asarray(targets)
+        Y, Q, own = self._sources(q)
+        T = periodic.near_traction(s.x[idx], s.n[idx], Y, Q, self.zero, self_index=own[idx])
+        T += kernels.traction_self(s.kappa[idx], s.tau[idx], q[idx])
+        xi, _ = self.proxy_strengths(q)
+        T += periodic.correction_traction(s.x[idx], s.n[idx], self.yp, xi)
+        return T
+
+    def body_velocities(self, sigma):
+        s = self.s
+        sigma = np.asarray(sigma, dtype=np.float64).reshape(s.N, 2)
+        q, _, _ = self.density_moments(sigma)
+        xi, _ = self.proxy_strengths(q)
+        Y, Q, _ = self._sources(q)
+        u = periodic.near_velocity(s.xc, Y, Q, self.zero, s.mu)
+        u += periodic.correction_velocity(s.xc, self.yp, xi, s.mu)
+        u -= periodic.correction_velocity(s.centre[None, :], self.yp, xi, s.mu)
+        w = periodic.near_vorticity(s.xc, Y, Q, self.zero, s.mu)
+        w += periodic.correction_vorticity(s.xc, self.yp, xi, s.mu)
+        v = u + np.stack([s.gamma * s.xc[:, 1], np.zeros(len(s.bodies))], axis=1)
+        omega = 0.5 * (w - s.gamma)
+        return v, omega

@@ -278,3 +278,47 @@ def proxy_points_box(e1, e2, centre, M):
         pts.append(centre[None, :] + side * e1[None, :] + s[:, None] * e2[None, :])
         pts.append(centre[None, :] + side * e2[None, :] + s[:, None] * e1[None, :])
     return np.concatenate(pts)
+
+
+# ----------------------------------------------------------------------------
+# the paper's own periodizer (Def. Gnear): per-source images inside U~
+# ----------------------------------------------------------------------------
+def utilde_shifts(e1, e2, centre, ys):
+    """Per source point the four lattice translates m e1 + n e2 that place it
+    inside the doubled cell U~ (same centre as U, walls at lattice coordinates
+    -1 and +1, Def. Gnear): with (s, t) the lattice coordinates of y - centre,
+    m runs over the two integers with -1 <= s + m < 1 and n over the two with
+    -1 <= t + n < 1.  Returns (N, 4, 2)."""
+    E = np.column_stack([e1, e2])
+    st = np.linalg.solve(E, (np.asarray(ys) - centre).T).T
+    m0 = np.ceil(-1.0 - st[:, 0])
+    n0 = np.ceil(-1.0 - st[:, 1])
+    out = [(m0 + dm)[:, None] * e1[None, :] + (n0 + dn)[:, None] * e2[None, :] for dm in (0, 1) for dn in (0, 1)]
+    return np.stack(out, axis=1)
+
+
+def expand_images(ys, qs, shifts_js):
+    """Source list of the per-source images: positions (N K, 2), strengths,
+    and for every source the index of its zero-shift copy (-1 if none)."""
+    N, K, _ = shifts_js.shape
+    Y = (np.asarray(ys)[:, None, :] + shifts_js).reshape(-1, 2)
+    Q = np.repeat(np.asarray(qs), K, axis=0)
+    zero = np.all(shifts_js == 0.0, axis=2)
+    own = np.where(zero.any(axis=1), np.arange(N) * K + zero.argmax(axis=1), -1)
+    return Y, Q, own
+
+
+def near_discrepancy_images(e1, e2, centre, m, Y, Q, mu):
+    """g = [g1; g2; g3; g4] of a near sum given as an explicit source list
+    (positions Y, strengths Q), evaluated literally as S(R) - S(L) and
+    S(U) - S(D) at the collocation points (Sec. 6.2 step 2)."""
+    xl, xd, _, _ = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    zero = [np.zeros(2)]
+    nlm = np.repeat(nl[None, :], m, axis=0)
+    ndm = np.repeat(nd[None, :], m, axis=0)
+    g1 = near_velocity(xl + e1, Y, Q, zero, mu) - near_velocity(xl, Y, Q, zero, mu)
+    g2 = near_traction(xl + e1, nlm, Y, Q, zero) - near_traction(xl, nlm, Y, Q, zero)
+    g3 = near_velocity(xd + e2, Y, Q, zero, mu) - near_velocity(xd, Y, Q, zero, mu)
+    g4 = near_traction(xd + e2, ndm, Y, Q, zero) - near_traction(xd, ndm, Y, Q, zero)
+    return np.concatenate([_split(g1), _split(g2), _split(g3), _split(g4)])

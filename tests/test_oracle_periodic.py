@@ -196,3 +196,50 @@ def test_near_split_independence_5x5():
     fix = lambda T: T - (T[0] @ s.n[0]) * s.n
     d = fix(T3) - fix(T5)
     assert np.abs(d).max() < 3e-7 * np.abs(fix(T3)).max()
+
+
+def test_paper_periodizer_agrees_with_3x3():
+    """Reading 1 (3 x 3 images of every body, proxies on a circle) against
+    the paper's own periodizer (Def. Gnear: each node's four images inside
+    the doubled cell, chosen per node by its lattice coordinates; proxies on
+    the doubled cell's walls).  Both define the same periodic Green's
+    function up to constants, so on a skewed cell whose bodies straddle the
+    quadrant lines (nodes on both sides get different image sets) the
+    densities, rotation rates, relative velocities and mu_eff agree to the
+    accuracy of the proxy fits (~1e-9), while the absolute velocities differ
+    by one constant (the free constant of the periodic Green's function)."""
+    from oracle import bie as obie
+    e1, e2, c = np.array([1.0, 0.0]), np.array([0.3, 1.0]), np.array([0.5, 0.5])
+
+    def at(s, t):
+        return (c + s * e1 + t * e2).tolist()
+
+    cell = dict(e1=e1.tolist(), e2=e2.tolist(), centre=c.tolist(), mu=1.0, gamma=1.0,
+                bodies=[dict(a=0.12, b=0.06, xc=at(-0.18, 0.16), theta=0.4, n=128),
+                        dict(a=0.10, b=0.07, xc=at(0.17, -0.15), theta=2.0, n=128),
+                        dict(a=0.09, b=0.05, xc=at(0.02, -0.02), theta=1.1, n=128)],
+                solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24))
+    op = oracle_operator(cell, use_close=False)
+    st = np.linalg.solve(np.column_stack([e1, e2]), (op.s.x - c).T).T
+    assert np.abs(st).max() < 0.5 and (st[:, 0] < 0).any() and (st[:, 0] > 0).any() and (st[:, 1] < 0).any()
+    ou = obie.OperatorUtilde(oracle_suspension(cell), n_proxy=128, n_coll=32)
+    s3, _, r3 = obie.solve(op, tol=1e-12)
+    su, _, ru = obie.solve(ou, tol=1e-12)
+    assert r3 <= 1e-12 and ru <= 1e-12
+    v3, w3 = op.body_velocities(s3)
+    vu, wu = ou.body_velocities(su)
+    assert np.abs(su - s3).max() / np.abs(s3).max() < 1e-8
+    assert np.abs(wu - w3).max() < 1e-9
+    assert np.abs((vu - vu[0]) - (v3 - v3[0])).max() < 1e-9
+    assert abs(ou.mu_eff(su) - op.mu_eff(s3)) < 1e-9
+    const = vu - v3
+    assert np.abs(const - const[0]).max() < 1e-9 and np.abs(const[0]).max() > 1e-6
+    # planted mistake: each node's images taken on the wrong side (shifts
+    # m e1 + n e2 negated, so three of the four lie outside the doubled
+    # cell).  The wall proxies absorb most of it (any image set plus an exact
+    # correction gives the same periodic sum), but the images left just
+    # outside U move sigma by ~1.6e-6, far above the 1e-9 agreement
+    bad = obie.OperatorUtilde(oracle_suspension(cell), n_proxy=128, n_coll=32)
+    bad.img = -bad.img
+    sb, _, _ = obie.solve(bad, tol=1e-12)
+    assert np.abs(sb - s3).max() / np.abs(s3).max() > 1e-7
