@@ -411,6 +411,14 @@ def main():
                        "parallelism": f"{world} independent replica(s)"},
             "s_per_shear_time": ms_per_step / 1e3 / dt,
             "s_per_shear_time_fp64": ms64 / 1e3 / dt,
+            # operator applications per second (all ranks), and the pairs of an
+            # application outside the near sum: wall discrepancy (2m wall
+            # points x the 6 far image rows/columns of every node, velocity
+            # and traction) and proxy correction (every node x M proxies)
+            "matvecs_per_s": world * (applies32 + applies64) / (t_ms / 1e3),
+            "pairs_per_apply": {"near": pairs_per_apply,
+                                "wall": 2.0 * cell["solver"]["n_coll"] * 6 * N,
+                                "proxy": float(N * cell["solver"]["n_proxy"])},
             "solve": {"applies32": applies32, "applies64": applies64, "iterations_mean": statistics.mean(iters),
                       "mu_eff_last": mu[-1], "iterations_per_step_by_start": starts},
             "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},

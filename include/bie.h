@@ -203,7 +203,9 @@ int bie_rhs(bie_ctx* ctx, double* b, int32_t on_device);
  * residual less than tenfold (an operator too ill-conditioned for single-
  * precision pairs, e.g. bodies ~1e-5 apart) switches the remaining sweeps to
  * GMRES on the double-float operator to the final tolerance; those
- * applications count as applies64.
+ * applications count as applies64.  If the double-float sweeps stall the
+ * same way, the residual is at the double-float operator's own accuracy and
+ * is taken in native FP64 from then on.
  * rhs NULL means -T(u0, p0).  sigma holds
  * the initial guess on entry when use_guess != 0 and the solution on exit
  * (2N doubles).  info may be NULL.  Returns BIE_ENOCONV if the tolerance was

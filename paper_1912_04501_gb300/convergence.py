@@ -26,7 +26,7 @@ STUDY = {
 }
 
 
-def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_max=1000, max_refine=8, precond=1):
+def solve_two_ellipses(gap, n, precision=bie.BIE_MIXED, gmres_tol=1e-10, gmres_max=1000, max_refine=12, precond=1):
     """One quasi-static solve; returns a dict with the body velocities, the
     solve statistics and the wall times of the set-up (geometry, proxy fit,
     close-evaluation blocks) and of the solve.  Near contact the system needs

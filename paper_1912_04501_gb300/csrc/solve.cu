@@ -20,7 +20,8 @@
 // ||r_c|| / ||b_c|| <= opts.gmres_tol in every cell c.  When a sweep meets
 // its inner tolerance but cuts the FP64-class residual by less than
 // kStallRatio, the remaining sweeps solve for d on the double-float operator
-// to the final tolerance instead.  BIE_FP64 / BIE_DF64:
+// to the final tolerance instead, and if those stall too the residual is
+// taken with native FP64 pair sums.  BIE_FP64 / BIE_DF64:
 // GMRES directly on the native-double / double-float operator.
 #include <cmath>
 #include <cstdio>
@@ -532,8 +533,12 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
     // tenfold (the single-precision operator is then too far from the FP64
     // one for this geometry's conditioning, e.g. bodies ~1e-5 apart); the
     // remaining sweeps run GMRES on the double-float operator to the final
-    // tolerance
+    // tolerance.  If those stall the same way, the residual itself is at the
+    // double-float operator's accuracy (its rounding of the large, cancelling
+    // near-contact terms, ~1e-8 of the right-hand side at 1e-5 gaps): the
+    // residual switches to native FP64.
     int inner_prec = BIE_MIXED;
+    int res_prec = c->opts.residual;
     std::vector<double> rn_prev(nc, 0.0);
     std::vector<char> met(nc, 0);
     // cells still iterating: a zero right-hand side has the solution 0
@@ -560,7 +565,7 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             BIE_CUDA(c, cudaMemcpyAsync(c->sv.r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
             rn = bnorm;
         } else {
-            rc = apply_device(c, x, c->sv.r, mixed ? c->opts.residual : plain_prec);
+            rc = apply_device(c, x, c->sv.r, mixed ? res_prec : plain_prec);
             if (rc) return rc;
             ++inf.applies64;
             k_sub<<<gs, bs, 0, c->stream>>>(b, c->sv.r, c->sv.r, n);
@@ -580,8 +585,10 @@ int solve_device(bie_ctx* c, const double* b, double* x, bool use_guess, bie_sol
             }
             left = true;
             beta[q] = rn[q];
-            if (mixed && inner_prec == BIE_MIXED && met[q] && rn[q] > kStallRatio * rn_prev[q])
-                inner_prec = BIE_DF64;
+            if (mixed && met[q] && rn[q] > kStallRatio * rn_prev[q]) {
+                if (inner_prec == BIE_MIXED) inner_prec = BIE_DF64;
+                else res_prec = BIE_FP64;
+            }
         }
         for (int q = 0; q < nc; ++q)
             if (beta[q] > 0.0)
