@@ -116,7 +116,7 @@ typedef struct {
                              launches it saves do) */
     int32_t precond;      /* 1: right-precondition GMRES with the inverse of the dense operator block
                              on the nodes inside another curve's close-evaluation zone (at most
-                             2048, the closest kept; I/2 elsewhere), rebuilt with every geometry:
+                             1024, the closest kept; I/2 elsewhere), rebuilt with every geometry:
                              for nearly touching bodies (single-cell contexts only).  0: none */
 } bie_opts;
 

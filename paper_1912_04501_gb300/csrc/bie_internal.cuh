@@ -62,7 +62,7 @@ constexpr int kCloseSlots = 8;        // close body images per target node
 constexpr int kMaxRho = 4096;         // largest fine-rule factor of the close evaluation (a power of two)
 constexpr int kCloseAccNodes = 4096;  // source nodes per CTA of k_close_blocks (shared accumulators)
 constexpr int kMaxBodyNodes = 16384;  // nodes per body
-constexpr int kPcMaxNodes = 2048;     // nodes of the contact-block preconditioner (opts.precond)
+constexpr int kPcMaxNodes = 1024;     // nodes of the contact-block preconditioner: [A_SS | I] (67 MB) stays in L2
 constexpr int kMaxCells = 4096;
 constexpr int kWallStride = 24;       // doubles per wall point of the wall table (see k_wall_table)
 constexpr int kNetHidden = 64;        // hidden width of the warm-start network
