@@ -36,6 +36,9 @@ def test_default_opts(lib):
     o = bie.bie_default_opts()
     assert o.precision == bie.BIE_MIXED and o.n_proxy == 48 and o.n_coll == 24
     assert o.gmres_tol == 1e-10 and o.lam_rel == 1e-8
+    # bit-reproducible by default: the fixed tile shape, direct launches, no preconditioner
+    assert o.autotune == 0 and o.graph == 0 and o.precond == 0
+    assert o.close_capacity == 0 and o.residual == bie.BIE_DF64
 
 
 @pytest.mark.parametrize("mutate", [
