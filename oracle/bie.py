@@ -288,3 +288,51 @@ class OperatorUtilde(Operator):
         v = u + np.stack([s.gamma * s.xc[:, 1], np.zeros(len(s.bodies))], axis=1)
         omega = 0.5 * (w - s.gamma)
         return v, omega
+
+    def mu_eff_contour(self, sigma, m_wall=32):
+        """Sec. 6.4 (Eq. contourdef): mu_eff from the shear force through a
+        contour C that runs from L to R below every body, with no quadrature
+        near any curve.  The curve splits into quadrant pieces by lattice
+        coordinates (1: s >= 0, t >= 0; 2: s < 0, t >= 0; 3: s < 0, t < 0;
+        4: s >= 0, t < 0) and Gamma~ = {Gamma_1 - e1 - e2, Gamma_2 - e2,
+        Gamma_3, Gamma_4 - e1}, so that this periodizer's near sum at x is the
+        potential of Gamma~ at x, x - e1, x - e2 and x - e1 - e2.  Gauss' law
+        (exterior traction integral = -sum of the enclosed forces, outward
+        normals) on the boundary of the two cells below U gives
+            int_C T = 2 int_{D-e2} S~ + 2 int_{D-e1-e2} S~ + int_{R-e2} S~
+                      - int_{L-e1-e2} S~ - sum_{Gamma_1, Gamma_2} q + int_D T(v, q)
+        with the normal (0, 1) on D and the outward normal of L on L and R
+        (reading 2), the signs the paper prints.  (Its printed Gamma~ names
+        Gamma_1 in place of Gamma_2 and Gamma_4 in two pieces; the shifts
+        above are the ones that reproduce the near sum.)"""
+        s = self.s
+        sigma = np.asarray(sigma, dtype=np.float64).reshape(s.N, 2)
+        q, _, _ = self.density_moments(sigma)
+        xi, _ = self.proxy_strengths(q)
+        e1, e2, c = s.e1, s.e2, s.centre
+        st = np.linalg.solve(np.column_stack([e1, e2]), (s.x - c).T).T
+        right, up = st[:, 0] >= 0, st[:, 1] >= 0
+        shift = np.where(right[:, None], -e1[None, :], 0.0) + np.where(up[:, None], -e2[None, :], 0.0)
+        yt = s.x + shift  # Gamma~
+        zero = [np.zeros(2)]
+        gl, wl = periodic.gauss_legendre_unit(m_wall)
+        nl, _ = periodic.wall_normals(e1, e2)
+        nD = np.array([0.0, 1.0])
+
+        def wall_int(start, along, normal):
+            xw = start[None, :] + gl[:, None] * along[None, :]
+            nw = np.repeat(normal[None, :], m_wall, axis=0)
+            T = periodic.near_traction(xw, nw, yt, q, zero)
+            return (T * wl[:, None]).sum(0) * np.hypot(*along)
+
+        d_e2 = c - 1.5 * e2            # midpoint of D - e2
+        d_e1e2 = c - e1 - 1.5 * e2     # D - e1 - e2
+        r_e2 = c + 0.5 * e1 - e2       # R - e2
+        l_e1e2 = c - 1.5 * e1 - e2     # L - e1 - e2
+        F = (2 * wall_int(d_e2, e1, nD) + 2 * wall_int(d_e1e2, e1, nD)
+             + wall_int(r_e2, e2, nl) - wall_int(l_e1e2, e2, nl) - q[up].sum(0))
+        xd = c[None, :] - 0.5 * e2[None, :] + gl[:, None] * e1[None, :]
+        Tv = periodic.correction_traction(xd, np.repeat(nD[None, :], m_wall, axis=0), self.yp, xi)
+        F += (Tv * wl[:, None]).sum(0) * np.hypot(*e1)
+        l1 = np.hypot(*e1)
+        return s.mu + F[0] / (s.gamma * l1)

@@ -317,3 +317,40 @@ def test_periodic_stokeslet_matches_ewald(skew):
     plus = periodic.image_shifts(e1, e2, [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)])
     d = oracle_velocity(plus) - u_a
     assert np.abs(d - d.mean(0)).max() > 1e-4 * scale
+
+
+@pytest.mark.parametrize("crossing", [False, True])
+def test_contour_mu_eff_matches_stresslet(crossing):
+    """Sec. 6.4 (Eq. contourdef, read with Gamma~ = {Gamma_1 - e1 - e2,
+    Gamma_2 - e2, Gamma_3, Gamma_4 - e1}, the shifts that reproduce the
+    per-node near sum): mu_eff from wall integrals half a cell or more from
+    every source equals the particle-stress average (reading 9) to 1e-9, on a
+    skewed cell with all bodies inside U and on one where a body crosses the
+    bottom wall D, where the literal wall formula (Eq. mueff) no longer
+    applies."""
+    from oracle import bie as obie
+    e1, e2, c = np.array([1.0, 0.0]), np.array([0.3, 1.0]), np.array([0.5, 0.5])
+
+    def at(s, t):
+        return (c + s * e1 + t * e2).tolist()
+
+    bodies = [dict(a=0.12, b=0.06, xc=at(-0.18, 0.16), theta=0.4, n=128)]
+    if crossing:
+        bodies.append(dict(a=0.10, b=0.07, xc=at(0.17, -0.46), theta=0.3, n=160))
+    else:
+        bodies += [dict(a=0.10, b=0.07, xc=at(0.17, -0.15), theta=2.0, n=128),
+                   dict(a=0.09, b=0.05, xc=at(0.02, -0.02), theta=1.1, n=128)]
+    cell = dict(e1=e1.tolist(), e2=e2.tolist(), centre=c.tolist(), mu=1.0, gamma=1.0, bodies=bodies,
+                solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24))
+    ou = obie.OperatorUtilde(oracle_suspension(cell), n_proxy=128, n_coll=32)
+    st = np.linalg.solve(np.column_stack([e1, e2]), (ou.s.x - c).T).T
+    assert (st[:, 1] < -0.5).any() == crossing
+    sigma, _, res = obie.solve(ou, tol=1e-12)
+    assert res <= 1e-12
+    mu_s = ou.mu_eff(sigma)
+    assert abs(ou.mu_eff_contour(sigma) - mu_s) < 1e-9
+    wall = oracle_operator(cell, use_close=False).mu_eff_wall(sigma)
+    if crossing:
+        assert abs(wall - mu_s) > 1e-2
+    else:
+        assert abs(wall - mu_s) < 1e-8
