@@ -21,7 +21,10 @@ slow and as literal as the paper's definitions allow:
 * ``bie``       -- the Nystrom operator with rigid completion and pressure
                    fix (Eq. BIEdiscretized, Sec. 5, Sec. 6.2 remark), GMRES,
                    velocity extraction, effective viscosity and forward Euler
-                   (Sec. 3, Sec. 7).
+                   (Sec. 3, Sec. 7); the same operator with the paper's own
+                   per-node doubled-cell periodizer (Def. Gnear) and its
+                   contour-deformation effective viscosity (Sec. 6.4), as
+                   cross-checks of the 3 x 3 image reading.
 * ``mlp``       -- the warm-start network (no counterpart in the paper): a
                    per-node perceptron, its loss gradient and Adam, from their
                    definitions.
