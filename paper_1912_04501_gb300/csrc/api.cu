@@ -814,7 +814,8 @@ int bie_set_state(bie_ctx* c, double t, const double* e2, const double* xc, cons
     }
     int rc = upload_cells(c, c->stream);
     if (rc) return rc;
-    if ((rc = upload_e2(c, c->e2d, current_e2(c), c->stream))) return rc;
+    rc = upload_e2(c, c->e2d, current_e2(c), c->stream);
+    if (rc) return rc;
     BIE_CUDA(c, cudaMemcpyAsync(c->body, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (sigma) {
         BIE_CUDA(c, cudaMemcpyAsync(c->sv.sigma_prev, sigma, 2 * (size_t)c->N * sizeof(double),

@@ -1289,8 +1289,6 @@ __global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __rest
 }
 
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff, bool reuse_ws) {
-    const int N = c->N;
-    const int bs = 256, gs = (N + bs - 1) / bs;
     const double2* sg = reinterpret_cast<const double2*>(sigma);
     // reuse_ws: the time step calls this right after a solve whose last
     // (FP64-class) residual application was of this density over every

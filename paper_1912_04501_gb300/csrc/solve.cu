@@ -164,8 +164,8 @@ static int mdots(bie_ctx* c, const double* V, size_t ld, int nv, const double* w
 }
 
 // dst = a[cell] src; a zero factor writes zeros (switched-off cells)
-__global__ void k_scale_copy(const double* __restrict__ src, const double* __restrict__ a,
-                             const int* __restrict__ node_cell, double* __restrict__ dst, int n) {
+__global__ void k_scale_copy(const double* src, const double* __restrict__ a, const int* __restrict__ node_cell,
+                             double* dst, int n) {  // src and dst may be the same vector
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double f = a[node_cell[i >> 1]];
@@ -178,7 +178,7 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
 }
 
 // y = a - b
-__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y, int n) {
+__global__ void k_sub(const double* a, const double* b, double* y, int n) {  // y may alias a or b
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = a[i] - b[i];
 }
