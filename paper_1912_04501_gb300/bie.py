@@ -198,7 +198,10 @@ class Context:
                 setattr(o, k, sv[k])
         if "gmres_tol" in sv:
             o.gmres_tol = sv["gmres_tol"]
+        known = {name for name, _ in Opts._fields_}
         for k, v in opts.items():
+            if k not in known:
+                raise TypeError(f"unknown option {k!r} (bie_opts has {sorted(known)})")
             setattr(o, k, v)
         all_bodies = [bd for c in cells for bd in c["bodies"]]
         bodies = (Body * len(all_bodies))()

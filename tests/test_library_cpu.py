@@ -108,3 +108,9 @@ def test_precond_needs_single_cell_without_gpu(lib):
     with pytest.raises(bie.BieError) as e:
         bie.Context([workloads.config1(), workloads.config1()], precond=1)
     assert e.value.code == bie.BIE_EINVAL
+
+
+def test_unknown_option_is_an_error(lib):
+    from paper_1912_04501_gb300 import workloads
+    with pytest.raises(TypeError):
+        bie.Context(workloads.config1(), precnod=1)
