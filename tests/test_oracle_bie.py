@@ -169,3 +169,83 @@ def test_euler_first_order():
         finals.append(np.array([b["theta"] for b in s.bodies]))
     e1, e2 = np.abs(finals[0] - finals[2]).max(), np.abs(finals[1] - finals[2]).max()
     assert 2.2 < e1 / e2 < 3.8  # (2 dt - dt/2) / (dt - dt/2) = 3 for first order
+
+
+def _circle_cell(r, xc, e2=(0.0, 1.0)):
+    return dict(e1=[1.0, 0.0], e2=list(e2), centre=[0.5, 0.5], mu=1.0, gamma=1.0,
+                bodies=[dict(a=r, b=r, xc=list(xc), theta=0.0, n=32)])
+
+
+EULER_KW = dict(n_proxy=16, proxy_radius=1.5, n_coll=16)
+
+
+def test_euler_step_dilute_circle_closed_form():
+    """Sec. 7, forward Euler: one step of a dilute circle moves its centre by
+    dt u0(x^c) = dt (gamma y_c, 0) and turns it by -dt gamma / 2 (the dilute
+    rotation rate), up to O(phi) corrections.  A flipped sign of either update
+    (or of the background flow) misses by 2 dt |v| or dt gamma."""
+    r, dt = 0.01, 0.05
+    phi = math.pi * r * r
+    cell = _circle_cell(r, (0.5, 0.7))
+    s = oracle_suspension(cell)
+    s1, t1, out = bie.euler_step(s, cell["e2"], 0.0, dt, EULER_KW)
+    assert t1 == dt
+    dx = np.asarray(s1.bodies[0]["xc"]) - np.array([0.5, 0.7])
+    np.testing.assert_allclose(dx, [dt * 0.7, 0.0], atol=10 * phi * dt)
+    assert abs((s1.bodies[0]["theta"] - 0.0) - (-0.5 * dt)) < 10 * phi * dt
+    # the lattice of the new state is the one at t + dt (Sec. 7: the top of the
+    # cell moves with u0, e2 = (gamma t L2, L2)), not the one at t
+    np.testing.assert_allclose(s1.e2, [dt, 1.0], atol=1e-15)
+    np.testing.assert_allclose(s1.e1, [1.0, 0.0], atol=0)
+
+
+def test_euler_steps_lattice_and_wrap():
+    """After n steps the lattice is e2(n dt) with round() reducing the skew
+    (Sec. 7), and a centre that leaves the cell re-enters through the opposite
+    wall: a dilute circle at y_c = 0.9 moving right with speed ~0.9."""
+    r, dt = 0.01, 0.2
+    cell = _circle_cell(r, (0.8, 0.9))
+    s = oracle_suspension(cell)
+    t = 0.0
+    xs = []
+    for _ in range(3):
+        s, t, out = bie.euler_step(s, cell["e2"], t, dt, EULER_KW)
+        xs.append((np.asarray(s.bodies[0]["xc"]), s.e2.copy()))
+    # gamma t = 0.6 rounds to 1: e2 = (0.6 - 1, 1)
+    np.testing.assert_allclose(s.e2, [-0.4, 1.0], atol=1e-14)
+    np.testing.assert_allclose(t, 0.6, atol=1e-15)
+    # unwrapped, the centre would be at 0.8 + 3 * 0.2 * 0.9 = 1.34; it is the
+    # same point shifted by -e1 = (-1, 0) of the lattice it was wrapped in
+    phi = math.pi * r * r
+    np.testing.assert_allclose(xs[-1][0], [0.34, 0.9], atol=30 * phi * dt)
+    for x, e2 in xs:
+        ab = np.linalg.solve(np.column_stack([[1.0, 0.0], e2]), x - 0.5)
+        assert np.all(ab >= -0.5) and np.all(ab < 0.5)
+
+
+def test_euler_uses_velocities_of_the_current_state():
+    """Forward Euler (Sec. 7) advances with F(t, s(t)): the step equals dt times
+    the rigid motion extracted from an independent solve on the geometry at t
+    (not at t + dt), for two interacting ellipses in a skewed cell."""
+    cell = dict(e1=[1.0, 0.0], e2=[0.2, 1.0], centre=[0.5, 0.5], mu=1.0, gamma=1.0,
+                bodies=[dict(a=0.2, b=0.1, xc=[0.45, 0.55], theta=0.2, n=48),
+                        dict(a=0.12, b=0.08, xc=[0.05, 0.1], theta=1.0, n=40)])
+    dt = 0.01
+    s0 = oracle_suspension(cell)
+    op = oracle_operator(dict(cell, solver=dict(n_proxy=16, proxy_radius=1.5, n_coll=16)))
+    sigma, _, _ = bie.solve(op)
+    v, om = op.body_velocities(sigma)
+    s1, t1, out = bie.euler_step(s0, cell["e2"], 0.0, dt, EULER_KW)
+    for b in range(2):
+        new = np.asarray(s1.bodies[b]["xc"])
+        moved = np.asarray(cell["bodies"][b]["xc"]) + dt * v[b]
+        d = new - moved  # equal up to a lattice vector of the new cell
+        ab = np.linalg.solve(np.column_stack([s1.e1, s1.e2]), d)
+        np.testing.assert_allclose(ab, np.round(ab), atol=1e-12)
+        assert abs(s1.bodies[b]["theta"] - (cell["bodies"][b]["theta"] + dt * om[b])) < 1e-12
+    # the velocities differ measurably between t and t + dt, so a step that
+    # used the new geometry's velocities would fail the check above
+    op1 = oracle_operator(dict(cell, e2=list(s1.e2), bodies=s1.bodies,
+                               solver=dict(n_proxy=16, proxy_radius=1.5, n_coll=16)))
+    v1, om1 = op1.body_velocities(bie.solve(op1)[0])
+    assert np.abs(om1 - om).max() * dt > 1e-9
