@@ -254,15 +254,19 @@ int bie_set_history(bie_ctx* ctx, const double* sigma_prev2, const double* d2, d
 
 /* bie_apply_static: the same operator application as
  * bie_apply(ctx, sigma, out, BIE_MIXED, 1), but it allocates no device memory
- * at all and does not touch the workspace that bie_init allocated.  It has no
- * counterpart in the paper; it exists for callers that may not call cudaMalloc
- * -- for instance code running inside a host application whose own memory
- * manager owns the device heap, or a thread that must not allocate while a
- * solve on the same context holds the context's workspace -- yet need the
- * operator on their own device buffers.
+ * at all and does not touch the per-call buffers that bie_init allocated.  It
+ * has no counterpart in the paper; it exists for callers that may not call
+ * cudaMalloc -- for instance code running inside a host application whose own
+ * memory manager owns the device heap and forbids other allocations -- yet
+ * need the operator on their own device buffers.  Like every call on a
+ * context it must not overlap another call on the same context (it launches
+ * on the context's stream, counts its launches in the context, and records
+ * the profiler's events when bie_profile is on).
  *   sigma, out: device pointers, 2N doubles each (node-major), on the
  *   context's GPU; they must not overlap.  The call is asynchronous on the
- *   context's stream; out is ready when that stream reaches the end of it.
+ *   context's stream (unless bie_profile is on: the profiler may then wait
+ *   for the stream to fold its events); out is ready when that stream
+ *   reaches the end of it.
  * Its per-call scratch is one static device array of 4 MiB inside the
  * library, which every GPU that loads the library keeps until the process
  * exits.  Contexts with more than 8192 nodes (or whose buffers would not fit
@@ -361,6 +365,20 @@ typedef struct {
 
 int bie_profile(bie_ctx* ctx, int32_t enable);
 int bie_profile_read(bie_ctx* ctx, bie_profile_info* info);
+
+/* Streaming multiprocessors of the context's device, as queried at bie_init
+ * (the near-sum work items are sized for them). */
+int bie_device_sms(const bie_ctx* ctx, int32_t* sms);
+
+/* Measurement aid (no counterpart in the paper): the CUDA-core FMA
+ * throughput of a device, the roofline denominators of the pair sums.
+ * Launches full-occupancy grids of independent FMA chains -- scalar
+ * fma.rn.f32, packed fma.rn.f32x2, then fma.rn.f64 -- on the given
+ * cudaStream_t (NULL = legacy default stream), a few milliseconds each, and
+ * returns the best of three timed launches of each in TFLOP/s (2 flops per
+ * FMA lane).  Synchronises the stream.  Outputs (host) may be NULL.
+ * Errors: BIE_EINVAL, BIE_ENOMEM, BIE_ECUDA. */
+int bie_alu_peak(int32_t device, void* stream, double* ffma_tflops, double* ffma2_tflops, double* dfma_tflops);
 
 #ifdef __cplusplus
 }

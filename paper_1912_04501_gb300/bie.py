@@ -118,6 +118,9 @@ def library():
         "bie_close_info": (c_int32, [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
         "bie_near_shape": (c_int32, [vp, ctypes.POINTER(c_int32), vp]),
         "bie_apply_static": (c_int32, [vp, vp, vp]),
+        "bie_device_sms": (c_int32, [vp, ctypes.POINTER(c_int32)]),
+        "bie_alu_peak": (c_int32, [c_int32, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double)]),
         "bie_profile": (c_int32, [vp, c_int32]),
         "bie_profile_read": (c_int32, [vp, ctypes.POINTER(ProfileInfo)]),
         "bie_features": (c_int32, [vp, vp, c_int32]),
@@ -153,7 +156,7 @@ def exported_symbols():
                         "bie_set_warm_net", "bie_net_init", "bie_net_destroy", "bie_net_last_error",
                         "bie_net_size", "bie_net_set_stream", "bie_net_set_params", "bie_net_get_params",
                         "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step", "bie_get_history",
-                        "bie_set_history", "bie_near_shape")
+                        "bie_set_history", "bie_near_shape", "bie_device_sms", "bie_alu_peak")
             if hasattr(L, n)]
 
 
@@ -330,6 +333,16 @@ class Context:
         po, do = _ptr(out)
         if not (ds and do):
             raise ValueError("bie_apply_static takes device tensors")
+        n = 2 * self.N
+        if sigma.numel() != n or out.numel() != n:
+            raise ValueError(f"sigma and out must hold 2N = {n} doubles each")
+        dev = self.opts.device
+        if sigma.device.index != dev or out.device.index != dev:
+            raise ValueError(f"sigma and out must be on the context's device cuda:{dev}")
+        a0, a1 = ps, ps + 8 * n
+        b0, b1 = po, po + 8 * n
+        if a0 < b1 and b0 < a1:
+            raise ValueError("sigma and out must not overlap")
         self._check(library().bie_apply_static(self.h, ps, po))
         return out
 
@@ -355,6 +368,12 @@ class Context:
         ms = (ctypes.c_float * BIE_NEAR32_SHAPES)()
         self._check(library().bie_near_shape(self.h, ctypes.byref(sh), ms))
         return sh.value, list(ms)
+
+    def device_sms(self):
+        """Streaming multiprocessors of the context's device (queried at init)."""
+        n = c_int32()
+        self._check(library().bie_device_sms(self.h, ctypes.byref(n)))
+        return n.value
 
     def close_info(self):
         n, u = c_int32(), c_int32()
@@ -382,6 +401,16 @@ class Context:
         dd = None if d2 is None else np.ascontiguousarray(d2, dtype=np.float64).ravel()
         self._check(library().bie_set_history(self.h, None if s2 is None else s2.ctypes.data,
                                               None if dd is None else dd.ctypes.data, float(dt_prev)))
+
+
+def alu_peak(device=0, stream_handle=None):
+    """Measured FMA throughput of a device in TFLOP/s (bie_alu_peak):
+    dict(ffma=..., ffma2=..., dfma=...)."""
+    a, b, d = c_double(), c_double(), c_double()
+    rc = library().bie_alu_peak(device, c_void_p(stream_handle), ctypes.byref(a), ctypes.byref(b), ctypes.byref(d))
+    if rc != 0:
+        raise BieError(rc, "bie_alu_peak failed")
+    return dict(ffma=a.value, ffma2=b.value, dfma=d.value)
 
 
 class Net:

@@ -887,7 +887,7 @@ static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, s
 static int build_near_items_prec(bie_ctx* c, int prec) {
     const int tile = near_tile(c->shape32, prec);
     std::vector<int> splits;
-    choose_splits(c->cells_h, tile, near_ctas_per_sm(c->shape32, prec) * kSMs, splits);
+    choose_splits(c->cells_h, tile, near_ctas_per_sm(c->shape32, prec) * c->sms, splits);
     std::vector<int4> items;
     long long off = 0;
     for (int ci = 0; ci < c->ncell; ++ci) {
@@ -924,7 +924,7 @@ size_t near_part_bytes(const bie_ctx* c) {
     for (int prec = 0; prec < 3; ++prec)
         for (int sh = 0; sh < (prec == 0 ? kNear32Shapes : 1); ++sh) {
             std::vector<int> splits;
-            choose_splits(c->cells_h, near_tile(sh, prec), near_ctas_per_sm(sh, prec) * kSMs, splits);
+            choose_splits(c->cells_h, near_tile(sh, prec), near_ctas_per_sm(sh, prec) * c->sms, splits);
             long long off = 0;
             for (size_t k = 0; k < splits.size(); ++k) off += (long long)splits[k] * c->cells_h[k].n_nodes;
             best = std::max(best, (size_t)off * (prec == 0 ? sizeof(float2) : sizeof(double2)));
@@ -1180,7 +1180,8 @@ int autotune_near32(bie_ctx* c) {
 
 // The single-precision-pair operator application with every per-call buffer
 // taken from `ws` (used by the allocation-free entry point, whose buffers
-// live in a static device array).  The context is only read.
+// live in a static device array).  Of the context only the launch counter
+// and, with profiling on, the event state change.
 int apply_device_ws(bie_ctx* c, const double* sigma, double* yout, Workspace& ws) {
     return apply_impl(c, sigma, yout, BIE_MIXED, ws);
 }

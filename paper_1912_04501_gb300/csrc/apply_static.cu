@@ -1,8 +1,11 @@
 // bie_apply_static: the single-precision-pair operator application with no
 // device allocation.  Every per-call buffer (source records, near-sum
 // partials, wall-discrepancy partials, body moments, proxy strengths,
-// traction) lives in one file-scope static device array; the context is only
-// read.  See include/bie.h for who needs this and the limits.
+// traction) lives in one file-scope static device array.  Of the context it
+// reads the geometry, proxy fit, close tables and work items; it writes only
+// its launch counter and, with bie_profile on, the profiler's event state, so
+// calls on one context must not overlap (as for every entry point).  See
+// include/bie.h for who needs this and the limits.
 #include <mutex>
 
 #include "bie_internal.cuh"

@@ -2,8 +2,8 @@
 device memory.
 
 Some callers of this library may not call cudaMalloc: code embedded in a
-host application whose memory manager owns the device heap, or a thread that
-must not allocate while a solve holds the context's workspace.  For them the
+host application whose memory manager owns the device heap and forbids other
+allocations.  For them the
 library keeps the per-call scratch of one operator application in a static
 device array.  Here the entry point is called through the C ABI twice in a
 row (the array keeps the previous call's contents) and each result is
@@ -52,4 +52,34 @@ def test_apply_static_rejects_too_many_nodes():
         ctx.apply_static(d, torch.empty_like(d))
     assert e.value.code == bie.BIE_EINVAL
     assert "8192" in str(e.value)
+    ctx.close()
+
+
+def test_apply_static_rejects_too_much_scratch():
+    """A batch of many small cells stays under the node limit but needs more
+    scratch than the array holds: the wall-discrepancy partials and proxy
+    strengths grow with the number of cells, not with the nodes."""
+    cells = []
+    for k in range(400):  # 400 cells x 16 nodes = 6400 nodes <= 8192
+        cells.append(dict(e1=[1.0, 0.0], e2=[0.0, 1.0], centre=[0.5, 0.5], mu=1.0, gamma=1.0,
+                          bodies=[dict(a=0.1, b=0.05, xc=[0.5, 0.5], theta=0.01 * k, n=16)],
+                          solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10)))
+    ctx = bie.Context(cells, precision=bie.BIE_MIXED)
+    assert ctx.N <= 8192
+    d = torch.zeros(2 * ctx.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(bie.BieError) as e:
+        ctx.apply_static(d, torch.empty_like(d))
+    assert e.value.code == bie.BIE_EINVAL
+    assert "bytes of scratch" in str(e.value) and str(4 << 20) in str(e.value)
+    ctx.close()
+
+
+def test_apply_static_checks_tensor_sizes():
+    cell = workloads.small_cell(n_bodies=2, nodes=64, seed=3)
+    ctx = bie.Context(cell, precision=bie.BIE_MIXED)
+    d = torch.zeros(2 * ctx.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        ctx.apply_static(d[:-2], torch.empty_like(d))
+    with pytest.raises(ValueError):
+        ctx.apply_static(d, d)
     ctx.close()
