@@ -383,6 +383,12 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         delete c;
         return rc;
     }
+    // the wave model of the near-sum work items sizes them for this device
+    if ((rc = cu(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device),
+                 "cudaDeviceGetAttribute")) || c->sms <= 0) {
+        delete c;
+        return rc ? rc : BIE_ECUDA;
+    }
     const int n = c->N, M = c->M, m = c->m;
     const size_t nc = (size_t)n_cells, nbs = (size_t)c->nb;
     const int R = 8 * m + 2 * M, Cc = 2 * M;
@@ -888,6 +894,12 @@ int bie_features(bie_ctx* c, float* X, int32_t on_device) {
         BIE_CUDA(c, cudaMemcpyAsync(X, c->sv.feat, (size_t)kNetFeatures * c->N * sizeof(float),
                                     cudaMemcpyDeviceToHost, c->stream));
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_device_sms(const bie_ctx* c, int32_t* sms) {
+    if (!c || !sms) return BIE_EINVAL;
+    *sms = c->sms;
     return BIE_OK;
 }
 

@@ -31,7 +31,6 @@
 namespace bie {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
 #ifndef BIE_NEAR_THREADS
 #define BIE_NEAR_THREADS 128
 #endif
@@ -186,6 +185,7 @@ struct NearItems {
 
 struct bie_ctx {
     int device = 0;
+    int sms = 0;                 // streaming multiprocessors of the device (queried at init)
     cudaStream_t stream = nullptr;
     bie_opts opts{};
     double t = 0;
