@@ -209,10 +209,12 @@ def solve(op, b=None, tol=1e-10, maxiter=500, x0=None, max_restarts=5):
 # ----------------------------------------------------------------------------
 # time stepping (Sec. 7)
 # ----------------------------------------------------------------------------
-def euler_step(susp, e2_0, t, dt, op_kwargs, sigma0=None, tol=1e-10):
+def euler_step(susp, e2_0, t, dt, op_kwargs, sigma0=None, tol=1e-10, operator=None):
     """One forward-Euler step s <- s + dt F(t, s).  Returns the new
-    Suspension, the new time, and (sigma, v, omega, mu_eff) at time t."""
-    op = Operator(susp, **op_kwargs)
+    Suspension, the new time, and (sigma, v, omega, mu_eff) at time t.
+    operator: the Operator class to build (a subclass that evaluates the same
+    matvec in parallel, say); Operator by default."""
+    op = (operator or Operator)(susp, **op_kwargs)
     sigma, iters, res = solve(op, tol=tol, x0=sigma0)
     v, omega = op.body_velocities(sigma)
     mu_eff = op.mu_eff(sigma)
@@ -236,30 +238,63 @@ class OperatorUtilde(Operator):
     """The same BIE operator with the paper's periodizer (Def. Gnear, remark
     after Eq. W): each source node contributes its four lattice images inside
     the doubled cell U~, chosen per node by its lattice coordinates, and the
-    proxies sit on the walls of U~ (periodic.proxy_points_box).  The wall
-    discrepancy is evaluated literally.  Both periodizers define the same
-    periodic Green's function up to constants, so densities, rotation rates
-    and mu_eff agree to discretisation accuracy.  No close evaluation: used
-    on geometries whose curves are all farther apart than the close zone."""
+    proxies sit on the walls of U~ (periodic.proxy_points_box).  The
+    periodic sums of Sec. 6.2 are evaluated at targets in the unit cell U: a
+    node outside U (on a body across a wall) is evaluated at its lattice
+    translate inside U, where the periodic traction takes the same value
+    (with the node's own normal); its self pair is the image of itself
+    that lands there.  The wall discrepancy takes the cancellation form of
+Sec. 6.2 step 2 (periodic.near_discrepancy_utilde), so that no evaluation
+comes near a body that crosses a wall.  Both
+    periodizers define the same periodic Green's function up to constants,
+    so densities, rotation rates and mu_eff agree to discretisation accuracy.
 
-    def __init__(self, susp, n_proxy=128, n_coll=32, lam_rel=1e-8):
+    Close evaluation (Sec. 6.3) is the 3 x 3 operator's, pair for pair, in
+    the nodes' own frame: a pair (target, body, image) is valid here when
+    every node of the body has that image, seen from the target's translate
+    inside U, among its four; with bodies smaller than about half a cell
+    this always holds (images left out lie at least half a cell from U), and
+    a geometry where it does not is refused (ValueError)."""
+
+    def __init__(self, susp, n_proxy=128, n_coll=32, lam_rel=1e-8, close_factor=10.0, use_close=True,
+                 close_targets=None):
         self.s = susp
         self.M = n_proxy
         self.m = n_coll
         self.yp = periodic.proxy_points_box(susp.e1, susp.e2, susp.centre, n_proxy)
         self.Q = periodic.proxy_matrix(susp.e1, susp.e2, susp.centre, n_coll, self.yp, susp.mu)
         self.Qp = periodic.proxy_solution_operator(self.Q, lam_rel)
+        self.imgmn = periodic.utilde_images(susp.e1, susp.e2, susp.centre, susp.x)
         self.img = periodic.utilde_shifts(susp.e1, susp.e2, susp.centre, susp.x)
-        self.close = None
+        self.wrapmn = periodic.wrap_images(susp.e1, susp.e2, susp.centre, susp.x)
+        self.wrap = self.wrapmn[:, :1] * susp.e1[None, :] + self.wrapmn[:, 1:] * susp.e2[None, :]
+        # the copy of node i at its translate inside U (index into the expanded sources)
+        hit = np.all(self.imgmn == self.wrapmn[:, None, :], axis=2)
+        assert hit.sum(axis=1).min() == 1
+        self.own_wrapped = np.arange(susp.N) * 4 + hit.argmax(axis=1)
         self.zero = [np.zeros(2)]
+        self.close = None
+        if use_close:
+            shifts = periodic.image_shifts(susp.e1, susp.e2)
+            self.close = ClosePairs(susp, shifts, close_factor, close_targets)
+            E = np.column_stack([susp.e1, susp.e2])
+            for (i, b, sh, _, _) in self.close.pairs:
+                mn = np.rint(np.linalg.solve(E, sh)).astype(np.int64) + self.wrapmn[i]
+                sl = slice(susp.offsets[b], susp.offsets[b + 1])
+                if not np.all(np.any(np.all(self.imgmn[sl] == mn[None, None, :], axis=2), axis=1)):
+                    raise ValueError("a close pair's body image is not wholly among the doubled-cell images "
+                                     "(a body larger than about half a cell?)")
 
     def _sources(self, q):
         return periodic.expand_images(self.s.x, q, self.img)
 
+    def targets(self, idx):
+        """Translates inside U of the listed nodes."""
+        return self.s.x[idx] + self.wrap[idx]
+
     def proxy_strengths(self, q):
         s = self.s
-        Y, Q, _ = self._sources(q)
-        g = periodic.near_discrepancy_images(s.e1, s.e2, s.centre, self.m, Y, Q, s.mu)
+        g = periodic.near_discrepancy_utilde(s.e1, s.e2, s.centre, self.m, s.x, q, self.imgmn, s.mu)
         dt = periodic.corrected_discrepancy(g, q.sum(0), s.e1, s.e2, self.m)
         return periodic.apply_operator_exact(self.Qp, dt), dt
 
@@ -267,11 +302,14 @@ class OperatorUtilde(Operator):
         s = self.s
         q, _, _ = self.density_moments(sigma)
         idx = np.arange(s.N) if targets is None else np.asarray(targets)
-        Y, Q, own = self._sources(q)
-        T = periodic.near_traction(s.x[idx], s.n[idx], Y, Q, self.zero, self_index=own[idx])
+        Y, Q, _ = self._sources(q)
+        xt = self.targets(idx)
+        T = periodic.near_traction(xt, s.n[idx], Y, Q, self.zero, self_index=self.own_wrapped[idx])
         T += kernels.traction_self(s.kappa[idx], s.tau[idx], q[idx])
         xi, _ = self.proxy_strengths(q)
-        T += periodic.correction_traction(s.x[idx], s.n[idx], self.yp, xi)
+        T += periodic.correction_traction(xt, s.n[idx], self.yp, xi)
+        if self.close is not None:
+            T += self.close.apply(sigma, None if targets is None else idx)
         return T
 
     def body_velocities(self, sigma):

@@ -283,18 +283,38 @@ def proxy_points_box(e1, e2, centre, M):
 # ----------------------------------------------------------------------------
 # the paper's own periodizer (Def. Gnear): per-source images inside U~
 # ----------------------------------------------------------------------------
-def utilde_shifts(e1, e2, centre, ys):
-    """Per source point the four lattice translates m e1 + n e2 that place it
-    inside the doubled cell U~ (same centre as U, walls at lattice coordinates
-    -1 and +1, Def. Gnear): with (s, t) the lattice coordinates of y - centre,
-    m runs over the two integers with -1 <= s + m < 1 and n over the two with
-    -1 <= t + n < 1.  Returns (N, 4, 2)."""
+def lattice_coords(e1, e2, centre, ys):
+    """(s, t) with y - centre = s e1 + t e2, per point (N, 2)."""
     E = np.column_stack([e1, e2])
-    st = np.linalg.solve(E, (np.asarray(ys) - centre).T).T
-    m0 = np.ceil(-1.0 - st[:, 0])
-    n0 = np.ceil(-1.0 - st[:, 1])
-    out = [(m0 + dm)[:, None] * e1[None, :] + (n0 + dn)[:, None] * e2[None, :] for dm in (0, 1) for dn in (0, 1)]
+    return np.linalg.solve(E, (np.asarray(ys) - centre).T).T
+
+
+def utilde_images(e1, e2, centre, ys):
+    """Per source point the integer pairs (m, n) of the four lattice
+    translates y + m e1 + n e2 inside the doubled cell U~ (same centre as U,
+    walls at lattice coordinates -1 and +1, Def. Gnear): with (s, t) the
+    lattice coordinates of y - centre, m runs over the two integers with
+    -1 <= s + m < 1 and n over the two with -1 <= t + n < 1, in the order
+    (m0, n0), (m0, n0 + 1), (m0 + 1, n0), (m0 + 1, n0 + 1).  Returns (N, 4, 2)
+    integers."""
+    st = lattice_coords(e1, e2, centre, ys)
+    m0 = np.ceil(-1.0 - st[:, 0]).astype(np.int64)
+    n0 = np.ceil(-1.0 - st[:, 1]).astype(np.int64)
+    out = [np.stack([m0 + dm, n0 + dn], axis=1) for dm in (0, 1) for dn in (0, 1)]
     return np.stack(out, axis=1)
+
+
+def utilde_shifts(e1, e2, centre, ys):
+    """The translates of utilde_images as vectors m e1 + n e2, (N, 4, 2)."""
+    mn = utilde_images(e1, e2, centre, ys).astype(np.float64)
+    return mn[..., :1] * np.asarray(e1)[None, None, :] + mn[..., 1:] * np.asarray(e2)[None, None, :]
+
+
+def wrap_images(e1, e2, centre, xs):
+    """Per point the integer pair (m, n) with x + m e1 + n e2 inside the unit
+    cell U: lattice coordinates in [-1/2, 1/2).  Returns (N, 2) integers."""
+    st = lattice_coords(e1, e2, centre, xs)
+    return -np.floor(st + 0.5).astype(np.int64)
 
 
 def expand_images(ys, qs, shifts_js):
@@ -306,6 +326,39 @@ def expand_images(ys, qs, shifts_js):
     zero = np.all(shifts_js == 0.0, axis=2)
     own = np.where(zero.any(axis=1), np.arange(N) * K + zero.argmax(axis=1), -1)
     return Y, Q, own
+
+
+def near_discrepancy_utilde(e1, e2, centre, m, ys, qs, imgmn, mu):
+    """g = [g1; g2; g3; g4] of the doubled-cell near sum (Def. Gnear) with
+    the cancellation Sec. 6.2 step 2 points out.  A node y whose images have
+    m in {m0, m0 + 1} (and n in {n0, n0 + 1}) contributes to
+    S_near(x + e1) - S_near(x) on L, by translation invariance,
+        sum_n K(x, y + (m0 - 1) e1 + n e2) - K(x, y + (m0 + 1) e1 + n e2),
+    two terms per image row, each at least half a cell from L even when the
+    node's body crosses a wall; likewise for U - D with the roles of e1 and
+    e2 exchanged.  imgmn: per node its four (m, n) pairs (utilde_images)."""
+    xl, xd, _, _ = collocation(e1, e2, centre, m)
+    nl, nd = wall_normals(e1, e2)
+    e1, e2 = np.asarray(e1), np.asarray(e2)
+    m0 = imgmn[:, 0, 0]
+    n0 = imgmn[:, 0, 1]
+    nlm = np.repeat(nl[None, :], m, axis=0)
+    ndm = np.repeat(nd[None, :], m, axis=0)
+    zero = [np.zeros(2)]
+    g = [np.zeros((m, 2)) for _ in range(4)]
+    for dn in (0, 1):
+        # L - R: rows n0 + dn, columns m0 - 1 (plus) and m0 + 1 (minus)
+        yp = ys + (m0 - 1)[:, None] * e1[None, :] + (n0 + dn)[:, None] * e2[None, :]
+        ym = ys + (m0 + 1)[:, None] * e1[None, :] + (n0 + dn)[:, None] * e2[None, :]
+        g[0] += near_velocity(xl, yp, qs, zero, mu) - near_velocity(xl, ym, qs, zero, mu)
+        g[1] += near_traction(xl, nlm, yp, qs, zero) - near_traction(xl, nlm, ym, qs, zero)
+    for dm in (0, 1):
+        # D - U: columns m0 + dm, rows n0 - 1 (plus) and n0 + 1 (minus)
+        yp = ys + (m0 + dm)[:, None] * e1[None, :] + (n0 - 1)[:, None] * e2[None, :]
+        ym = ys + (m0 + dm)[:, None] * e1[None, :] + (n0 + 1)[:, None] * e2[None, :]
+        g[2] += near_velocity(xd, yp, qs, zero, mu) - near_velocity(xd, ym, qs, zero, mu)
+        g[3] += near_traction(xd, ndm, yp, qs, zero) - near_traction(xd, ndm, ym, qs, zero)
+    return np.concatenate([_split(v) for v in g])
 
 
 def near_discrepancy_images(e1, e2, centre, m, Y, Q, mu):
