@@ -1,30 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the periodized Stokes BIE hot path on one GB300 per rank.
 
-Workload: 25 equal-area ellipses per unit cell, area fraction 0.3, aspect
-ratios in [1, 3], minimum gap 1e-2, 256 nodes per body (6400 nodes), lattice
-(1,0),(0,1), mu = gamma = 1, forward Euler with dt = 1e-3 (synthetic seeded
-suspension).  One timed "step" is one forward-Euler time step: solve the
-mobility BIE to a relative FP64-class residual of 1e-10 (single-precision
-pair sums inside iterative refinement with double-float residuals; the first
-GMRES cycle augmented with the previous density, its last change and the
-shipped warm-start network's predicted change, the second refinement sweep
-with the previous step's second-sweep correction), extract velocities and
-mu_eff, move the bodies, shear the lattice and rebuild the discretisation and
-the proxy fit.  Beside it: iterations per step of the other starts (zero,
-recycled directions without the network) and the plain FP64 solve (zero
-start, double-precision pair sums) in seconds per shear time.
+Workload (the largest single-GPU configuration): 400 ellipses per unit cell,
+area fraction 0.35, aspect ratios in [1, 3], minimum gap 2e-3, 256 nodes per
+body (102400 nodes), lattice (1,0),(0,1), mu = gamma = 1, forward Euler with
+dt = 1e-3 (synthetic seeded suspension).  One timed "step" is one forward-
+Euler time step: solve the mobility BIE to a relative FP64-class residual of
+1e-10 (single-precision pair sums inside iterative refinement with
+double-float residuals; the first GMRES cycle augmented with the previous
+density, its last change and the shipped warm-start network's predicted
+change, the second refinement sweep with the previous step's second-sweep
+correction), extract velocities and mu_eff, move the bodies, shear the
+lattice and rebuild the discretisation, close-evaluation tables and proxy
+fit.  Beside it: GMRES iterations per step of the three starts on the same
+steps (zero, recycled directions, recycled + network), the plain FP64 solve
+(zero start, double-precision pair sums) in seconds per shear time, and the
+25-ellipse cell (6400 nodes) measured the same way.
 
 value: near-image pair evaluations (9 N^2 per operator application, every
-FP32 and FP64 application counted) per second, whole job (all ranks), in
-Gpairs/s.  Multi-GPU runs are independent replicas (weak scaling).
+single-precision and FP64-class application counted) per second, whole job
+(all ranks), in Gpairs/s.  Multi-GPU runs are independent replicas (weak
+scaling).
 
---impl reference times the FP64 CPU oracle (numpy) on a bounded sample of the
-same workload and reports the same metric.
+--impl reference times the FP64 CPU oracle (numpy, all host cores) on a
+bounded sample of the targets of the same workload and reports the same
+metric.
 """
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -37,7 +42,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "periodized matvec Gpairs/s; s per shear time @1e-10, mixed+learned vs plain FP64"
 UNIT = "Gpairs/s"
-WORKLOAD = "25 ellipses/cell, phi 0.3, AR U[1,3], gap>=1e-2, 256 nodes/body (N=6400), dt 1e-3"
+WORKLOADS = {
+    "config5": "400 ellipses/cell, phi 0.35, AR U[1,3], gap>=2e-3, 256 nodes/body (N=102400), dt 1e-3",
+    "config2": "25 ellipses/cell, phi 0.3, AR U[1,3], gap>=1e-2, 256 nodes/body (N=6400), dt 1e-3",
+}
+FLOPS_PER_PAIR = 18.0  # 13 FP32 operations (5 of them FMAs) + 1 reciprocal per near pair
 
 
 def parse():
@@ -46,19 +55,17 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="config5", choices=sorted(WORKLOADS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mixed-only", action="store_true",
-                   help="time the mixed-precision steps only (no plain-FP64 comparison, no end-to-end loop); "
+                   help="time the mixed-precision steps only (no comparisons, no end-to-end loop); "
                         "used for kernel launch lists")
     return p.parse_args()
 
 
-def peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        with open(path) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+def make_cell(name):
+    from paper_1912_04501_gb300 import workloads
+    return getattr(workloads, name)()
 
 
 # ---------------------------------------------------------------------------
@@ -126,10 +133,10 @@ def source_hash(kernel):
     return hashlib.sha256(kernel_source(kernel).encode()).hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the kernel's current source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_config2.md")
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of
+    this workload, if it was taken on the kernel's current source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -148,55 +155,106 @@ def profiled_traffic(kernel):
 # ---------------------------------------------------------------------------
 # oracle timing (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(cell, target_seconds=15.0):
-    """Time the FP64 oracle's operator at a sample of targets; returns
-    (Gpairs/s, description, threads, seconds of the timed application)."""
-    import numpy as np
+_OP = None
+
+
+def _oracle_init(cell, close_targets):
+    global _OP
     from oracle import bie as obie
     from oracle import geometry
     s = geometry.Suspension(cell["e1"], cell["e2"], cell["centre"], cell["mu"], cell["gamma"], cell["bodies"])
     sv = cell["solver"]
-    op = obie.Operator(s, n_proxy=sv["n_proxy"], proxy_radius=sv["proxy_radius"], n_coll=sv["n_coll"])
-    rng = np.random.default_rng(0)
-    sigma = rng.standard_normal((s.N, 2))
-    def timed(S):
-        t0 = time.perf_counter()
-        op.apply(sigma, targets=np.sort(rng.choice(s.N, S, replace=False)))
-        return time.perf_counter() - t0
-    t1, t2 = timed(32), timed(256)  # fixed cost + per-target cost
-    per = max((t2 - t1) / 224, 1e-6)
-    S = int(min(s.N, max(32, (target_seconds - max(t1 - 32 * per, 0.0)) / per)))
-    idx = np.sort(rng.choice(s.N, S, replace=False))
+    _OP = obie.Operator(s, n_proxy=sv["n_proxy"], proxy_radius=sv["proxy_radius"], n_coll=sv["n_coll"],
+                        close_targets=close_targets)
+
+
+def _oracle_apply(args):
+    sigma, idx = args
     t0 = time.perf_counter()
-    op.apply(sigma, targets=idx)
-    dt = time.perf_counter() - t0
-    pairs = 9.0 * S * s.N
-    desc = (f"FP64 numpy oracle: one operator application evaluated at {S} of {s.N} targets "
-            f"({pairs:.3g} near pairs + wall discrepancy + proxy fit), {dt:.1f} s")
-    return pairs / dt / 1e9, desc, 1, dt
+    _OP.apply(sigma, targets=idx)
+    return time.perf_counter() - t0
+
+
+class OracleSample:
+    """The FP64 oracle's operator application at a bounded sample of the
+    targets of a workload, on one core (in process) or on `procs` cores
+    (spawned workers, each with its own share of the sample; the wall time of
+    the whole application is what counts)."""
+
+    def __init__(self, cell, procs, per_proc, seed=0):
+        import numpy as np
+        self.N = sum(b["n"] for b in cell["bodies"])
+        rng = np.random.default_rng(seed)
+        self.idx = np.sort(rng.choice(self.N, min(self.N, procs * per_proc), replace=False))
+        self.sigma = rng.standard_normal((self.N, 2))
+        self.procs = procs
+        self.chunks = np.array_split(self.idx, procs)
+        if procs == 1:
+            _oracle_init(cell, self.idx)
+            self.pool = None
+        else:
+            self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(cell, self.idx))
+            self.pool.map(_oracle_apply, [(self.sigma, c[:1]) for c in self.chunks])  # workers ready
+
+    def run(self):
+        t0 = time.perf_counter()
+        if self.pool is None:
+            _oracle_apply((self.sigma, self.idx))
+        else:
+            self.pool.map(_oracle_apply, [(self.sigma, c) for c in self.chunks])
+        dt = time.perf_counter() - t0
+        pairs = 9.0 * len(self.idx) * self.N
+        return pairs / dt / 1e9, dt
+
+    def describe(self, dt):
+        return (f"FP64 numpy oracle, {self.procs} process(es): one operator application evaluated at "
+                f"{len(self.idx)} of {self.N} sampled targets ({9.0 * len(self.idx) * self.N:.3g} near pairs, plus "
+                f"each process's full wall discrepancy, proxy fit and close pairs of its targets), {dt:.1f} s")
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+
+def cpu_baselines(cell, per_proc_single=96, per_proc_all=48):
+    """Single-core and all-core oracle rates (Gpairs/s) on bounded samples."""
+    out = {}
+    one = OracleSample(cell, 1, per_proc_single)
+    v, dt = one.run()
+    out["single"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": one.describe(dt)}
+    one.close()
+    n = os.cpu_count() or 1
+    if n > 1:
+        allc = OracleSample(cell, n, per_proc_all, seed=1)
+        v, dt = allc.run()
+        out["all"] = {"value": v, "unit": UNIT, "cores": n, "kind": "oracle", "sample": allc.describe(dt)}
+        allc.close()
+    return out
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from paper_1912_04501_gb300 import workloads
-    cell = workloads.config2()
+    cell = make_cell(args.workload)
+    procs = os.cpu_count() or 1
+    smp = OracleSample(cell, procs, 16)
     vals, secs = [], []
-    desc = ""
-    per = max(5.0, 120.0 / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
-        v, desc, cores, dt = oracle_sample(cell, target_seconds=per)
+        v, dt = smp.run()
         if k >= args.warmup:
             vals.append(v)
             secs.append(dt)
+    smp.close()
     v = statistics.mean(vals)
+    desc = smp.describe(statistics.mean(secs))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
         "step": "one oracle application at a bounded sample of the targets", "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": WORKLOADS[args.workload], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -215,6 +273,36 @@ def whole_job(units, ms, dist, device):
     return float(u[0]), float(t[0])
 
 
+def timed_steps(ctx, stream, dt, steps, flush=None):
+    """Per-step device times (CUDA events on the context's stream, L2
+    flushed before each step) and solve statistics of `steps` time steps."""
+    import torch
+    out = dict(ms=[], applies32=0, applies64=0, iters=[], mu=[])
+    for _ in range(steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m, info = ctx.step(dt, 1)
+        e1.record(stream)
+        e1.synchronize()
+        out["ms"].append(e0.elapsed_time(e1))
+        out["applies32"] += info["applies32"]
+        out["applies64"] += info["applies64"]
+        out["iters"].append(info["iterations"])
+        out["mu"].append(float(m[0]))
+    return out
+
+
+def restore(bie, cell, st, stream, **kw):
+    c = bie.Context(cell, precision=bie.BIE_MIXED, **kw)
+    c.set_stream(stream.cuda_stream)
+    c.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"], st["dt_prev"], st["d2"])
+    return c
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -226,7 +314,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1912_04501_gb300 import bie, learn, workloads
+    from paper_1912_04501_gb300 import bie, learn
 
     torch.cuda.set_device(local)
     dist = None
@@ -239,18 +327,19 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    cell = workloads.config2()
+    name = args.workload
+    cell = make_cell(name)
     dt = cell["dt"]
     N = sum(b["n"] for b in cell["bodies"])
+    nb = len(cell["bodies"])
     pairs_per_apply = 9.0 * N * N
     stream = torch.cuda.Stream()
     net = learn.default_net(device=local)
     mode = 2 if net is not None else 3
     # the default near-sum tile shape: fixed, so that a profiler run of this
     # command launches the same kernels as the timed one (the autotuner's
-    # choice depends on timings, which a profiler distorts; on this cell it
-    # differs from the default by ~2%); direct launches (replaying captured
-    # graphs measured no faster here)
+    # choice depends on timings, which a profiler distorts); direct launches
+    # (replaying captured graphs measured no faster)
     ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=mode, autotune=0, graph=0)
     shape, _ = ctx.near_shape()
     near32 = "k_near32x2" if bie.NEAR32_SHAPES[shape][0] else "k_near32"
@@ -262,36 +351,23 @@ def main():
 
     for _ in range(args.warmup):
         ctx.step(dt, 1)
+    torch.cuda.synchronize()
+    st0 = ctx.get_state()  # the trajectory point the start comparison restarts from
     props = torch.cuda.get_device_properties(local)
     uuid = str(getattr(props, "uuid", "") or "")
     ctx.profile_read()
     ctx.profile(True)
     barrier()
     clocks = Clocks(uuid)
-    total_ms = 0.0
-    applies32 = applies64 = 0
-    iters = []
-    mu = []
     t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        m, info = ctx.step(dt, 1)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        applies32 += info["applies32"]
-        applies64 += info["applies64"]
-        iters.append(info["iterations"])
-        mu.append(float(m[0]))
+    run = timed_steps(ctx, stream, dt, args.steps, flush)
     barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile(False)
+    total_ms = sum(run["ms"])
+    applies32, applies64 = run["applies32"], run["applies64"]
     pairs = pairs_per_apply * (applies32 + applies64)  # applies64: FP64-class (double-float) residuals
     # whole job: units of all ranks / slowest rank's time
     pairs_all, t_ms = whole_job(pairs, total_ms, dist, "cuda")
@@ -302,43 +378,75 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": ms_per_step, "mixed_only": True,
+                              "config": {"workload": WORKLOADS[name]},
                               "gpu_launches": prof["launches"], "profile": prof}), flush=True)
         ctx.close()
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    # iterations per step of the other starts on the same trajectory start
+    # GMRES iterations and wall time per step of the three starts, on the same
+    # three steps from the same trajectory point (state and history restored)
     starts = {}
-    st0 = ctx.get_state()
-    for m in (0, 3):
-        cm = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=m)
-        cm.set_stream(stream.cuda_stream)
-        cm.set_state(st0["t"], st0["e2"], st0["xc"], st0["theta"], st0["sigma"], st0["sigma_prev2"], st0["dt_prev"],
-                     st0["d2"])
-        its = [cm.step(dt, 1)[1]["iterations"] for _ in range(3)]
-        starts[{0: "zero", 3: "recycled"}[m]] = statistics.mean(its)
+    for m, label in ((0, "zero"), (3, "recycled"), (mode, "learned" if mode == 2 else "recycled (no network)")):
+        if label in starts:
+            continue
+        cm = restore(bie, cell, st0, stream, device=local, warm_start=m)
+        if m == 2:
+            cm.set_warm_net(net)
+        r = timed_steps(cm, stream, dt, 3)
+        starts[label] = {"iterations": r["iters"], "ms": r["ms"]}
+        if m == 2:
+            cm.set_warm_net(None)
         cm.close()
-    starts["learned" if mode == 2 else "recycled (no network shipped)"] = statistics.mean(iters)
 
-    # plain FP64 solve per step (zero start, double-precision pair sums)
+    # plain FP64 solve (zero start, double-precision pair sums): one operator
+    # application timed on the device, times the plain GMRES iterations plus
+    # one residual application.  The iterations are counted on the
+    # double-float operator (plain GMRES, zero start, same tolerance), which
+    # agrees with the FP64 one to ~1e-13 and takes the same iterations at a
+    # seventh of the time; small cells run the FP64 steps themselves.
     ctx64 = bie.Context(cell, precision=bie.BIE_FP64, device=local, warm_start=0)
     ctx64.set_stream(stream.cuda_stream)
-    ctx64.step(dt, 1)
+    sig = torch.randn(2 * N, dtype=torch.float64, device="cuda")
+    y64 = torch.empty_like(sig)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n64 = 2
-    _, info64 = ctx64.step(dt, n64)
-    torch.cuda.synchronize()
-    ms64 = (time.perf_counter() - t0) * 1e3 / n64
+    ctx64.apply(sig, y64, precision=bie.BIE_FP64)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ctx64.apply(sig, y64, precision=bie.BIE_FP64)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms64_apply = ev0.elapsed_time(ev1)
+    fp64 = None
+    if N > 20000:
+        cdf = bie.Context(cell, precision=bie.BIE_DF64, device=local, warm_start=0)
+        cdf.set_stream(stream.cuda_stream)
+        cdf.set_state(st0["t"], st0["e2"], st0["xc"], st0["theta"])
+        _, idf = cdf.solve()
+        cdf.close()
+        fp64 = {"ms_per_apply": ms64_apply, "iterations_per_step": idf["iterations"],
+                "s_per_shear_time": (idf["iterations"] + 1) * ms64_apply / 1e3 / dt,
+                "how": "extrapolated: one FP64 operator application (CUDA events) x (iterations of a plain zero-start "
+                       "GMRES solve at the same geometry and tolerance, counted on the double-float operator, + 1 "
+                       "residual application)"}
+    else:  # small cells: a full plain FP64 step is measured
+        ctx64.step(dt, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info64 = ctx64.step(dt, 2)
+        torch.cuda.synchronize()
+        fp64 = {"ms_per_apply": ms64_apply, "iterations_per_step": info64["iterations"],
+                "s_per_shear_time": (time.perf_counter() - t0) / 2 / dt, "how": "measured: two plain FP64 steps"}
     ctx64.close()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the state (and the
+    # warm-start history) in from pinned host memory, one step, the state out
     st = ctx.get_state()
     host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
                (("e2", st["e2"]), ("xc", st["xc"].ravel()), ("theta", st["theta"]), ("sigma", st["sigma"]),
                 ("sigma_prev2", st["sigma_prev2"]), ("d2", st["d2"]))}
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, args.steps // 4)
     e2e_pairs = 0.0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -351,54 +459,80 @@ def main():
         e2e_pairs += pairs_per_apply * (info["applies32"] + info["applies64"])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    nb = len(cell["bodies"])
     h2d = (3 * nb + 2 + 3 * 2 * N) * 8   # centroids, angles, e2, density, previous density, sweep correction
     d2h = (8 * nb + 3 * 2 * N + 1) * 8  # body table, density, previous density, sweep correction, mu_eff
+    sms = ctx.device_sms()
+    ctx.set_warm_net(None)
+    ctx.close()
 
-    pk, pk_src = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FFMA = 2 flops
-    fp64_peak = 1.25                                   # TFLOP/s, nominal GB300 FP64 (no measured figure)
-    # plain FP64 solve uses native double near sums (k_near64)
-    flops_per_pair = 18.0
+    # the 25-ellipse cell, measured the same way (an extra key)
+    small = None
+    if name != "config2":
+        c2 = make_cell("config2")
+        N2 = sum(b["n"] for b in c2["bodies"])
+        cx = bie.Context(c2, precision=bie.BIE_MIXED, device=local, warm_start=mode)
+        cx.set_stream(stream.cuda_stream)
+        if net is not None:
+            cx.set_warm_net(net)
+        for _ in range(5):
+            cx.step(c2["dt"], 1)
+        r2 = timed_steps(cx, stream, c2["dt"], 10, flush)
+        cx.set_warm_net(None)
+        cx.close()
+        c64 = bie.Context(c2, precision=bie.BIE_FP64, device=local, warm_start=0)
+        c64.set_stream(stream.cuda_stream)
+        c64.step(c2["dt"], 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c64.step(c2["dt"], 2)
+        torch.cuda.synchronize()
+        s64 = (time.perf_counter() - t0) / 2 / c2["dt"]
+        c64.close()
+        ms2 = statistics.mean(r2["ms"])
+        small = {"workload": WORKLOADS["config2"], "ms_per_step": ms2, "s_per_shear_time": ms2 / 1e3 / c2["dt"],
+                 "s_per_shear_time_fp64": s64,
+                 "value": 9.0 * N2 * N2 * (r2["applies32"] + r2["applies64"]) / (sum(r2["ms"]) / 1e3) / 1e9,
+                 "iterations_mean": statistics.mean(r2["iters"])}
+
+    # rooflines: measured CUDA-core FMA throughput of this device
+    peak = bie.alu_peak(local, stream.cuda_stream)
+    fp32_peak = max(peak["ffma"], peak["ffma2"])
+    fp32_src = (f"measured FP32 FMA throughput of this GPU (bie_alu_peak: scalar FFMA {peak['ffma']:.1f}, packed "
+                f"FFMA2 {peak['ffma2']:.1f} TFLOP/s; the larger is the peak), {sms} SMs queried")
     n32, n64, ndf = prof["near32_launches"], prof["near64_launches"], prof["neardf_launches"]
     ms32 = prof["near32_ms"] / max(1, n32)
-    ms64_k = prof["near64_ms"] / max(1, n64)
     msdf = prof["neardf_ms"] / max(1, ndf)
     roof32 = {"kernel": near32, "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
-              "achieved": flops_per_pair * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
+              "achieved": FLOPS_PER_PAIR * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
               "launch_ms": ms32, "launches": n32, "device_ms_total": prof["near32_ms"],
-              "peak_source": f"FP32 CUDA cores 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz of "
-                             f"{pk_src} peaks file)",
-              "traffic": profiled_traffic(near32)}
-    roof64 = {"kernel": "k_near64", "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
-              "achieved": flops_per_pair * pairs_per_apply / (ms64_k / 1e3) / 1e12 if n64 else None,
-              "launch_ms": ms64_k, "launches": n64, "device_ms_total": prof["near64_ms"],
-              "peak_source": "nominal GB300 FP64 rate (profiling recipe table), not measured",
-              "traffic": profiled_traffic("k_near64")}
+              "peak_source": fp32_src, "traffic": profiled_traffic(near32, name)}
     # double-float pairs run on the FP32 pipe: measured against the FP32 peak,
     # counting the same 18 algorithmic flops per pair (the extra ~120 FP32
     # instructions per pair are the price of the 48-bit arithmetic)
     roofdf = {"kernel": "k_near_df", "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
-              "achieved": flops_per_pair * pairs_per_apply / (msdf / 1e3) / 1e12 if ndf else None,
+              "achieved": FLOPS_PER_PAIR * pairs_per_apply / (msdf / 1e3) / 1e12 if ndf else None,
               "launch_ms": msdf, "launches": ndf, "device_ms_total": prof["neardf_ms"],
-              "peak_source": roof32["peak_source"], "traffic": profiled_traffic("k_near_df")}
-    for r in (roof32, roof64, roofdf):
-        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] else None
-    ranked = sorted([roof32, roof64, roofdf], key=lambda r: -r["device_ms_total"])
-    dom, other = ranked[0], [r for r in ranked[1:] if r["launches"]]
+              "peak_source": fp32_src, "traffic": profiled_traffic("k_near_df", name)}
+    roof64 = {"kernel": "k_near64 (plain FP64 operator, whole application)", "bound": "alu", "unit": "TFLOP/s",
+              "peak": peak["dfma"], "achieved": FLOPS_PER_PAIR * pairs_per_apply / (ms64_apply / 1e3) / 1e12,
+              "launch_ms": ms64_apply, "launches": 1, "device_ms_total": ms64_apply,
+              "peak_source": f"measured FP64 FMA throughput of this GPU (bie_alu_peak: {peak['dfma']:.2f} TFLOP/s)",
+              "traffic": None}
+    for r in (roof32, roofdf, roof64):
+        r["frac"] = r["achieved"] / r["peak"] if r["achieved"] and r["peak"] else None
+    ranked = sorted([roof32, roofdf], key=lambda r: -r["device_ms_total"])
+    dom, other = ranked[0], [r for r in ranked[1:] if r["launches"]] + [roof64]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, cores, _ = oracle_sample(cell)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = cpu_baselines(cell)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "bodies": nb,
+            "config": {"workload": WORKLOADS[name], "N": N, "bodies": nb,
                        "precision": "FP32 pair sums; refinement residual with double-float pair sums",
                        "gmres_tol": 1e-10,
                        "warm_start": ("learned: first GMRES cycle augmented with the previous density, its last "
@@ -410,9 +544,10 @@ def main():
                        "near_tile": {"shape": shape, "packed": bool(bie.NEAR32_SHAPES[shape][0]),
                                      "targets_per_thread": bie.NEAR32_SHAPES[shape][1],
                                      "ctas_per_sm": bie.NEAR32_SHAPES[shape][2]},
-                       "parallelism": f"{world} independent replica(s)"},
+                       "sms": sms, "parallelism": f"{world} independent replica(s)"},
             "s_per_shear_time": ms_per_step / 1e3 / dt,
-            "s_per_shear_time_fp64": ms64 / 1e3 / dt,
+            "s_per_shear_time_fp64": fp64["s_per_shear_time"],
+            "fp64_plain": fp64,
             # operator applications per second (all ranks), and the pairs of an
             # application outside the near sum: wall discrepancy (2m wall
             # points x the 6 far image rows/columns of every node, velocity
@@ -421,20 +556,22 @@ def main():
             "pairs_per_apply": {"near": pairs_per_apply,
                                 "wall": 2.0 * cell["solver"]["n_coll"] * 6 * N,
                                 "proxy": float(N * cell["solver"]["n_proxy"])},
-            "solve": {"applies32": applies32, "applies64": applies64, "iterations_mean": statistics.mean(iters),
-                      "mu_eff_last": mu[-1], "iterations_per_step_by_start": starts},
+            "solve": {"applies32": applies32, "applies64": applies64,
+                      "iterations_mean": statistics.mean(run["iters"]), "mu_eff_last": run["mu"][-1],
+                      "starts_same_steps": starts},
             "roofline": {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
             "roofline_detail": [dom] + other,
-            "cpu_baseline": cpu,
+            "alu_peaks_tflops": peak,
+            "cpu_baseline": cpu["all"] if cpu and "all" in cpu else (cpu or {}).get("single"),
+            "cpu_baseline_single_core": (cpu or {}).get("single"),
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "config2": small,
             "gpu_launches": prof["launches"],
             "clocks": clk,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
-    ctx.set_warm_net(None)
-    ctx.close()
     if net is not None:
         net.close()
     if dist is not None:
