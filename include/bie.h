@@ -118,6 +118,15 @@ typedef struct {
                              on the nodes inside another curve's close-evaluation zone (at most
                              1024, the closest kept; I/2 elsewhere), rebuilt with every geometry:
                              for nearly touching bodies (single-cell contexts only).  0: none */
+    int32_t n_images;     /* near-image set of the periodizer.  9: the 3 x 3 lattice translates of
+                             every body, proxies on a circle of radius proxy_radius about the cell
+                             centre.  4: the paper's own periodizer (Def. Gnear, Sec. 6.1 remark after
+                             Eq. W): each node's four lattice images inside the doubled cell U~ (same
+                             centre, twice the size), chosen per node by its lattice coordinates, n_proxy
+                             proxies (a multiple of 4) on the walls of U~, and the periodic sums taken at
+                             each node's lattice translate inside U (Sec. 6.2); 4N sources per near sum
+                             instead of 9N.  Bodies must be small enough that every close-evaluation pair
+                             sees whole body images (BIE_EINVAL otherwise); autotune must be 0 */
 } bie_opts;
 
 typedef struct {
@@ -132,7 +141,7 @@ typedef struct {
 /* Fill *opts with the defaults: BIE_MIXED, M = 48, radius 1.5, m = 24,
  * lam_rel 1e-8, gmres_tol 1e-10, gmres_max 200, inner_tol 1e-5, max_refine 8,
  * warm_start 3, min_gap 0, device 0, close_factor 10, close_capacity 0,
- * residual BIE_DF64, autotune 0, graph 0, precond 0. */
+ * residual BIE_DF64, autotune 0, graph 0, precond 0, n_images 9. */
 void bie_default_opts(bie_opts* opts);
 
 /* Create a context for one unit cell: lattice, viscosity mu, shear rate

@@ -33,7 +33,9 @@ static void free_all(bie_ctx* c) {
     free_graph(c);
     free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
-                    c->tgt32, c->posdf, c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
+                    c->tgt32, c->posdf, c->xw, c->yw, c->imc, c->bimg, c->ws.src32n, c->ws.src64u, c->next.yp,
+                    c->next.ypf,
+                    c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
                     c->sv.w, c->sv.r, c->sv.x, c->sv.b, c->sv.d, c->sv.h, c->sv.fac, c->sv.dpart,
@@ -78,6 +80,11 @@ void cell_set_lattice(Cell& cl, const double* e1, const double* e2) {
         }
     cl.l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
     cl.l2 = std::sqrt(e2[0] * e2[0] + e2[1] * e2[1]);
+    const double det = e1[0] * e2[1] - e1[1] * e2[0];
+    cl.inv[0] = e2[1] / det;
+    cl.inv[1] = -e2[0] / det;
+    cl.inv[2] = -e1[1] / det;
+    cl.inv[3] = e1[0] / det;
 }
 
 // Stream-ordered upload of the host mirror of the cell table through a
@@ -267,6 +274,9 @@ static int check_opts(const bie_opts& o, std::string& why) {
     else if ((o.autotune != 0 && o.autotune != 1) || (o.graph != 0 && o.graph != 1) ||
              (o.precond != 0 && o.precond != 1))
         why = "autotune, graph and precond must be 0 or 1";
+    else if (o.n_images != 9 && o.n_images != 4) why = "n_images must be 9 or 4";
+    else if (o.n_images == 4 && o.n_proxy % 4 != 0) why = "n_images 4 needs n_proxy a multiple of 4";
+    else if (o.n_images == 4 && o.autotune) why = "the tile-shape autotuner times the 3 x 3 near sum (n_images 9)";
     else return 0;
     return 1;
 }
@@ -298,6 +308,7 @@ void bie_default_opts(bie_opts* o) {
     o->autotune = 0;
     o->graph = 0;
     o->precond = 0;
+    o->n_images = 9;
 }
 
 int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
@@ -321,6 +332,8 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         if (o.precond && n_cells > 1) return bad("precond is for single-cell contexts");
     }
     c->device = o.device;
+    c->utilde = o.n_images == 4;
+    c->srcmul = c->utilde ? 4 : 1;
     c->ncell = n_cells;
     c->M = o.n_proxy;
     c->m = o.n_coll;
@@ -412,6 +425,10 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->body, 8 * nbs);
     rc = rc ? rc : dalloc(c, &c->tgt32, n);
     rc = rc ? rc : dalloc(c, &c->posdf, n);
+    rc = rc ? rc : dalloc(c, &c->xw, n);
+    rc = rc ? rc : dalloc(c, &c->yw, n);
+    rc = rc ? rc : dalloc(c, &c->imc, n);
+    rc = rc ? rc : dalloc(c, &c->bimg, nbs);
     rc = rc ? rc : dalloc(c, &c->gl_s, m);
     rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);
@@ -427,12 +444,19 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
     rc = rc ? rc : dalloc(c, &c->yp, nc * 2 * M);
     rc = rc ? rc : dalloc(c, &c->ypf, nc * M);
+    rc = rc ? rc : dalloc(c, &c->next.yp, nc * 2 * M);
+    rc = rc ? rc : dalloc(c, &c->next.ypf, nc * M);
     rc = rc ? rc : dalloc(c, &c->scal, 3 * nbs + nc + 8);
     rc = rc ? rc : dalloc(c, &c->ws.sigma, 2 * (size_t)n);
     rc = rc ? rc : dalloc(c, &c->ws.out, 2 * (size_t)n);
+    const size_t nsrc = (size_t)n * c->srcmul;  // near-sum source records
     rc = rc ? rc : dalloc(c, &c->ws.src64, n);
-    rc = rc ? rc : dalloc(c, &c->ws.src32, n);
-    rc = rc ? rc : dalloc(c, (char**)&c->ws.srcdf, (size_t)n * 32);
+    rc = rc ? rc : dalloc(c, &c->ws.src32, nsrc);
+    rc = rc ? rc : dalloc(c, (char**)&c->ws.srcdf, nsrc * 32);
+    if (c->utilde) {
+        rc = rc ? rc : dalloc(c, &c->ws.src32n, n);
+        rc = rc ? rc : dalloc(c, &c->ws.src64u, nsrc);
+    }
     rc = rc ? rc : dalloc(c, &c->ws.bodyF, 3 * nbs);
     rc = rc ? rc : dalloc(c, (char**)&c->ws.part, part);
     rc = rc ? rc : dalloc(c, &c->ws.gpart, nc * kDiscSplits * 8 * m);
@@ -521,7 +545,10 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : up(c->body_cell, body_cell.data(), c->nb * sizeof(int));
     rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
     rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
+    // the 3 x 3 periodizer's proxy circle does not move with the lattice: both
+    // fits hold it (the doubled cell's wall proxies are placed with each fit)
     rc = rc ? rc : up(c->yp, yp.data(), yp.size() * sizeof(double));
+    rc = rc ? rc : up(c->next.yp, yp.data(), yp.size() * sizeof(double));
     {
         std::vector<float2> ypf(nc * M);
         for (int k = 0; k < n_cells; ++k)
@@ -529,6 +556,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
                 ypf[(size_t)k * M + p] = make_float2((float)(yp[(size_t)k * 2 * M + 2 * p] - c->cells_h[k].C[0]),
                                                      (float)(yp[(size_t)k * 2 * M + 2 * p + 1] - c->cells_h[k].C[1]));
         rc = rc ? rc : up(c->ypf, ypf.data(), ypf.size() * sizeof(float2));
+        rc = rc ? rc : up(c->next.ypf, ypf.data(), ypf.size() * sizeof(float2));
     }
     rc = rc ? rc : up(c->e2d, c->e2_0.data(), c->e2_0.size() * sizeof(double));
     rc = rc ? rc : build_near_items(c);
@@ -755,6 +783,8 @@ int bie_step(bie_ctx* c, double dt, int32_t n_steps, double* mu_eff_out, bie_sol
         std::swap(c->P, c->next.P);
         std::swap(c->wall, c->next.wall);
         std::swap(c->e2d, c->next.e2);
+        std::swap(c->yp, c->next.yp);
+        std::swap(c->ypf, c->next.ypf);
         if ((rc = build_geometry(c))) return rc;
         std::swap(c->cl.dmin, c->cl.dmin_prev);
         c->cl.have_dprev = true;

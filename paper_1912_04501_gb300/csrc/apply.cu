@@ -61,18 +61,21 @@ struct ItemRange {
     long long out;  // partial base of this split: part_off + split * N_cell - node_off
 };
 
-__device__ __forceinline__ bool item_range(const int4* items, const Cell* cells, int prec, int tile, ItemRange& r) {
+// srcmul: source records per node (1: nodes; 4: the doubled-cell image records).
+__device__ __forceinline__ bool item_range(const int4* items, const Cell* cells, int prec, int tile, ItemRange& r,
+                                           int srcmul = 1) {
     const int4 it = items[blockIdx.x];
     const Cell& cl = cells[it.x];
     if (!cl.active) return false;
     const int sp = cl.splits[prec];
-    const int chunk = (cl.n_nodes + sp - 1) / sp;
+    const int ns = srcmul * cl.n_nodes;
+    const int chunk = (ns + sp - 1) / sp;
     r.c = it.x;
     r.nloc = cl.n_nodes;
     r.i0 = cl.node_off + it.y * tile;
     r.i1 = min(cl.node_off + cl.n_nodes, r.i0 + tile);
-    r.j0 = cl.node_off + it.z * chunk;
-    r.j1 = min(cl.node_off + cl.n_nodes, r.j0 + chunk);
+    r.j0 = srcmul * cl.node_off + it.z * chunk;
+    r.j1 = min(srcmul * cl.node_off + ns, r.j0 + chunk);
     r.out = cl.part_off[prec] + (long long)it.z * cl.n_nodes - cl.node_off;
     return true;
 }
@@ -346,6 +349,55 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
 }
 
 
+// One double-float pair of the near sum: target p = (pxh + pxl, pyh + pyl)
+// with normal n, source record q; the term c r, c = (r.n / r^2)(r.q / r^2),
+// r = p - y, is added to the tile accumulators (TwoSum hi, float error).
+__device__ __forceinline__ void pair_df(float pxh, float pxl, float pyh, float pyl, float nxh, float nxl, float nyh,
+                                        float nyl, const SrcDF& q, float& axh, float& axe, float& ayh, float& aye) {
+    float rxh, rxl, ryh, ryl, e;
+    df_diff(pxh, pxl, q.xh, q.xl, rxh, rxl);
+    df_diff(pyh, pyl, q.yh, q.yl, ryh, ryl);
+    // r^2 (the 1e-30 floor absorbs the zero-distance self pair)
+    float a, ea, b, eb, r2h, r2l;
+    a = rxh * rxh;
+    ea = fmaf(rxh, rxh, -a);
+    ea = fmaf(rxh, rxl + rxl, ea);
+    b = ryh * ryh;
+    eb = fmaf(ryh, ryh, -b);
+    eb = fmaf(ryh, ryl + ryl, eb);
+    two_sum(a, b, r2h, e);
+    r2l = e + ea + eb;
+    r2h += 1e-30f;
+    // 1 / r^2
+    const float ih = rcp_approx(r2h);
+    float res = fmaf(-r2h, ih, 1.0f);
+    res = fmaf(-r2l, ih, res);
+    const float il = ih * res;
+    // r . n and r . q
+    float p1, e1, p2, e2, rnh, rnl, rqh, rql;
+    df_mul(rxh, rxl, nxh, nxl, p1, e1);
+    df_mul(ryh, ryl, nyh, nyl, p2, e2);
+    two_sum(p1, p2, rnh, e);
+    rnl = e + e1 + e2;
+    fast2(rnh, rnl);  // r.n may cancel: renormalise before multiplying
+    df_mul(rxh, rxl, q.qxh, q.qxl, p1, e1);
+    df_mul(ryh, ryl, q.qyh, q.qyl, p2, e2);
+    two_sum(p1, p2, rqh, e);
+    rql = e + e1 + e2;
+    fast2(rqh, rql);
+    // c = (r.n / r^2) (r.q / r^2), term = c r
+    float uh, ul, vh, vl, ch, cl2, th, tl;
+    df_mul(rnh, rnl, ih, il, uh, ul);
+    df_mul(rqh, rql, ih, il, vh, vl);
+    df_mul(uh, ul, vh, vl, ch, cl2);
+    df_mul(ch, cl2, rxh, rxl, th, tl);
+    two_sum(axh, th, axh, e);
+    axe += e + tl;
+    df_mul(ch, cl2, ryh, ryl, th, tl);
+    two_sum(ayh, th, ayh, e);
+    aye += e + tl;
+}
+
 // a1 in one pass, one CTA per body: q = sigma w packed into whichever source
 // records the application needs (single-precision cell-centred, double,
 // double-float), and the body's force and torque moments F_b = sum q,
@@ -428,50 +480,8 @@ k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
         for (int k = 0; k < cnt; ++k) {
             const SrcDF q = s_src[k];
 #pragma unroll
-            for (int im = 0; im < 9; ++im) {
-                float rxh, rxl, ryh, ryl, e;
-                df_diff(pxh[im], pxl[im], q.xh, q.xl, rxh, rxl);
-                df_diff(pyh[im], pyl[im], q.yh, q.yl, ryh, ryl);
-                // r^2 (the 1e-30 floor absorbs the zero-distance self pair)
-                float a, ea, b, eb, r2h, r2l;
-                a = rxh * rxh;
-                ea = fmaf(rxh, rxh, -a);
-                ea = fmaf(rxh, rxl + rxl, ea);
-                b = ryh * ryh;
-                eb = fmaf(ryh, ryh, -b);
-                eb = fmaf(ryh, ryl + ryl, eb);
-                two_sum(a, b, r2h, e);
-                r2l = e + ea + eb;
-                r2h += 1e-30f;
-                // 1 / r^2
-                const float ih = rcp_approx(r2h);
-                float res = fmaf(-r2h, ih, 1.0f);
-                res = fmaf(-r2l, ih, res);
-                const float il = ih * res;
-                // r . n and r . q
-                float p1, e1, p2, e2, rnh, rnl, rqh, rql;
-                df_mul(rxh, rxl, nxh, nxl, p1, e1);
-                df_mul(ryh, ryl, nyh, nyl, p2, e2);
-                two_sum(p1, p2, rnh, e);
-                rnl = e + e1 + e2;
-                fast2(rnh, rnl);  // r.n may cancel: renormalise before multiplying
-                df_mul(rxh, rxl, q.qxh, q.qxl, p1, e1);
-                df_mul(ryh, ryl, q.qyh, q.qyl, p2, e2);
-                two_sum(p1, p2, rqh, e);
-                rql = e + e1 + e2;
-                fast2(rqh, rql);
-                // c = (r.n / r^2) (r.q / r^2), term = c r
-                float uh, ul, vh, vl, ch, cl2, th, tl;
-                df_mul(rnh, rnl, ih, il, uh, ul);
-                df_mul(rqh, rql, ih, il, vh, vl);
-                df_mul(uh, ul, vh, vl, ch, cl2);
-                df_mul(ch, cl2, rxh, rxl, th, tl);
-                two_sum(axh, th, axh, e);
-                axe += e + tl;
-                df_mul(ch, cl2, ryh, ryl, th, tl);
-                two_sum(ayh, th, ayh, e);
-                aye += e + tl;
-            }
+            for (int im = 0; im < 9; ++im)
+                pair_df(pxh[im], pxl[im], pyh[im], pyl[im], nxh, nxl, nyh, nyl, q, axh, axe, ayh, aye);
         }
         dxs += (double)axh + (double)axe;
         dys += (double)ayh + (double)aye;
@@ -482,11 +492,257 @@ k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The doubled-cell periodizer (n_images 4; Def. Gnear, Sec. 6.2).  Node j
+// contributes four image records y_j + (m0 + dm) e1 + (n0 + dn) e2, dm, dn in
+// {0, 1} (record 4 j + dm + 2 dn; m0, n0 from its image code), and every
+// target is taken at its translate inside U (tgt32, xw, yw), so the near
+// sums run over 4 N_cell records with no per-target shifts: 4 N^2 pairs per
+// application instead of 9 N^2.
+// ---------------------------------------------------------------------------
+
+// a1 for the doubled cell, one CTA per body: q = sigma w, the body moments,
+// the per-node records (src64 always; src32n, cell-centred single precision,
+// for the single-precision wall discrepancy) and the four image records per
+// node in the precision in use.  Record positions are formed as
+// (x + shift) - C in double, exactly as the targets' translates, so that a
+// node's record at its own translate coincides with its target bit for bit
+// (the zero-distance self pair then contributes exactly 0).
+__global__ void __launch_bounds__(256)
+k_pack_moments_u(const double2* __restrict__ sigma, const double* __restrict__ x, const double* __restrict__ y,
+                 const double* __restrict__ w, const double* __restrict__ body, const int* __restrict__ body_cell,
+                 const Cell* __restrict__ cells, const int* __restrict__ imc, float4* __restrict__ src32,
+                 float4* __restrict__ src32n, Src64* __restrict__ src64, Src64* __restrict__ src64u,
+                 SrcDF* __restrict__ srcdf, double* __restrict__ bodyF) {
+    __shared__ double red[33];
+    const int b = blockIdx.x;
+    const double* bd = body + 8 * b;
+    const double xc = bd[2], yc = bd[3];
+    const int n = (int)bd[5], off = (int)bd[6];
+    const Cell& cl = cells[body_cell[b]];
+    double fx = 0, fy = 0, tq = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int i = off + k;
+        const double2 sg = sigma[i];
+        const double wi = w[i], X = x[i], Y = y[i];
+        const double qx = sg.x * wi, qy = sg.y * wi;
+        fx += qx;
+        fy += qy;
+        tq += -(Y - yc) * qx + (X - xc) * qy;
+        src64[i] = Src64{X, Y, qx, qy};
+        const int code = imc[i];
+        if (src32n) src32n[i] = make_float4((float)(X - cl.C[0]), (float)(Y - cl.C[1]), (float)qx, (float)qy);
+        SrcDF qd;
+        if (srcdf) {
+            split_df(qx, qd.qxh, qd.qxl);
+            split_df(qy, qd.qyh, qd.qyl);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int sh = img_shift(code, r);
+            const double PX = X + cl.sx[sh], PY = Y + cl.sy[sh];
+            const size_t o = 4 * (size_t)i + r;
+            if (src32) src32[o] = make_float4((float)(PX - cl.C[0]), (float)(PY - cl.C[1]), (float)qx, (float)qy);
+            if (src64u) src64u[o] = Src64{PX, PY, qx, qy};
+            if (srcdf) {
+                split_df(PX - cl.C[0], qd.xh, qd.xl);
+                split_df(PY - cl.C[1], qd.yh, qd.yl);
+                srcdf[o] = qd;
+            }
+        }
+    }
+    fx = block_sum_d(fx, red);
+    fy = block_sum_d(fy, red);
+    tq = block_sum_d(tq, red);
+    if (threadIdx.x == 0) {
+        bodyF[3 * b] = fx;
+        bodyF[3 * b + 1] = fy;
+        bodyF[3 * b + 2] = tq;
+    }
+}
+
+// Single-precision near sum over image records.  Each thread owns TPT
+// targets; two consecutive source records share one packed f32x2 evaluation
+// (the records are staged in shared memory as separate x, y, qx, qy arrays,
+// so a 64-bit load yields the pair), and each half performs exactly the
+// operations of pair32 in its order: every pair's term is bit for bit the
+// one the single-precision close pass recomputes.  A dummy record (far away,
+// zero strength) pads an odd tile.
+template <int TPT, bool COMP, int MINB>
+__global__ void __launch_bounds__(kNearThreads, MINB)
+k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
+          const float4* __restrict__ src, float2* __restrict__ part) {
+    __shared__ __align__(16) float s_x[kNearTile + 2], s_y[kNearTile + 2], s_qx[kNearTile + 2], s_qy[kNearTile + 2];
+    ItemRange rg;
+    if (!item_range(items, cells, 0, kNearThreads * TPT, rg, 4)) return;
+    f32x2 px[TPT], py[TPT], nx2[TPT], ny2[TPT], ax[TPT], ay[TPT];
+    float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
+    const f32x2 eps = pk2(1e-30f, 1e-30f), zero = pk2(0.f, 0.f);
+    const int tbase = rg.i0 + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        const float4 tv = i < rg.i1 ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
+        px[t] = pk2(tv.x, tv.x);
+        py[t] = pk2(tv.y, tv.y);
+        nx2[t] = pk2(tv.z, tv.z);
+        ny2[t] = pk2(tv.w, tv.w);
+        ax[t] = ay[t] = zero;
+        hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
+    }
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        const int cnt = min(kNearTile, rg.j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) {
+            const float4 v = src[jt + k];
+            s_x[k] = v.x;
+            s_y[k] = v.y;
+            s_qx[k] = v.z;
+            s_qy[k] = v.w;
+        }
+        if (threadIdx.x == 0 && (cnt & 1)) {
+            s_x[cnt] = 1e4f;
+            s_y[cnt] = 1e4f;
+            s_qx[cnt] = 0.f;
+            s_qy[cnt] = 0.f;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < cnt; k += 2) {
+            const f32x2 sx = *reinterpret_cast<const f32x2*>(s_x + k);
+            const f32x2 sy = *reinterpret_cast<const f32x2*>(s_y + k);
+            const f32x2 qx = *reinterpret_cast<const f32x2*>(s_qx + k);
+            const f32x2 qy = *reinterpret_cast<const f32x2*>(s_qy + k);
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const f32x2 dx = sub2(px[t], sx);
+                const f32x2 dy = sub2(py[t], sy);
+                const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
+                const f32x2 rn = fma2(dy, ny2[t], mul2(dx, nx2[t]));
+                const f32x2 rq = fma2(dy, qy, mul2(dx, qx));
+                float ra, rb;
+                upk2(r2, ra, rb);
+                const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
+                const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
+                ax[t] = fma2(cc, dx, ax[t]);
+                ay[t] = fma2(cc, dy, ay[t]);
+            }
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float a0, a1, b0, b1, e;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                two_sum(hx[t], a0 + a1, hx[t], e);
+                lx[t] += e;
+                two_sum(hy[t], b0 + b1, hy[t], e);
+                ly[t] += e;
+                ax[t] = ay[t] = zero;
+            }
+        }
+    }
+    const float c = (float)(-1.0 / kPi);
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        if (i < rg.i1) {
+            if constexpr (COMP) {
+                part[rg.out + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
+            } else {
+                float a0, a1, b0, b1;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                part[rg.out + i] = make_float2(c * (a0 + a1), c * (b0 + b1));
+            }
+        }
+    }
+}
+
+// Double-precision near sum over image records (one target per thread).
+__global__ void __launch_bounds__(kNearThreads)
+k_near64u(const int4* __restrict__ items, const Cell* __restrict__ cells, const double* __restrict__ xw,
+          const double* __restrict__ yw, const double* __restrict__ nx, const double* __restrict__ ny,
+          const Src64* __restrict__ src, double2* __restrict__ part) {
+    __shared__ Src64 s_src[kNearTile];
+    ItemRange rg;
+    if (!item_range(items, cells, 1, kNearThreads, rg, 4)) return;
+    const int i = rg.i0 + threadIdx.x;
+    double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
+    if (i < rg.i1) {
+        tx = xw[i];
+        ty = yw[i];
+        tnx = nx[i];
+        tny = ny[i];
+    }
+    double ax = 0, ay = 0;
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        const int cnt = min(kNearTile, rg.j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const Src64 q = s_src[k];
+            const double dx = tx - q.x, dy = ty - q.y;
+            const double r2 = fma(dx, dx, fma(dy, dy, 1e-300));
+            const double rn = fma(dy, tny, dx * tnx);
+            const double rq = fma(dy, q.w, dx * q.z);
+            const double inv = 1.0 / r2;
+            const double cc = (rn * inv) * (rq * inv);
+            ax = fma(cc, dx, ax);
+            ay = fma(cc, dy, ay);
+        }
+    }
+    if (i < rg.i1) {
+        const double c = -1.0 / kPi;
+        part[rg.out + i] = make_double2(c * ax, c * ay);
+    }
+}
+
+// Double-float near sum over image records (one target per thread).
+__global__ void __launch_bounds__(kNearThreads, 4)
+k_near_dfu(const int4* __restrict__ items, const Cell* __restrict__ cells, const double* __restrict__ xw,
+           const double* __restrict__ yw, const double* __restrict__ nx, const double* __restrict__ ny,
+           const SrcDF* __restrict__ src, double2* __restrict__ part) {
+    __shared__ SrcDF s_src[kNearTile];
+    ItemRange rg;
+    if (!item_range(items, cells, 2, kNearThreads, rg, 4)) return;
+    const Cell& cl = cells[rg.c];
+    const int i = rg.i0 + threadIdx.x;
+    double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
+    if (i < rg.i1) {
+        tx = xw[i] - cl.C[0];
+        ty = yw[i] - cl.C[1];
+        tnx = nx[i];
+        tny = ny[i];
+    }
+    float pxh, pxl, pyh, pyl, nxh, nxl, nyh, nyl;
+    split_df(tx, pxh, pxl);
+    split_df(ty, pyh, pyl);
+    split_df(tnx, nxh, nxl);
+    split_df(tny, nyh, nyl);
+    double dxs = 0, dys = 0;
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        const int cnt = min(kNearTile, rg.j1 - jt);
+        float axh = 0, axe = 0, ayh = 0, aye = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) pair_df(pxh, pxl, pyh, pyl, nxh, nxl, nyh, nyl, s_src[k], axh, axe, ayh, aye);
+        dxs += (double)axh + (double)axe;
+        dys += (double)ayh + (double)aye;
+    }
+    if (i < rg.i1) {
+        const double c = -1.0 / kPi;
+        part[rg.out + i] = make_double2(c * dxs, c * dys);
+    }
+}
+
 // Wall table (per geometry and cell): for each collocation point (L points,
-// then D points) the point minus each of its six far-image shifts, and the
-// wall normal used for the traction: 14 doubles (x, y of the six points, then
-// the normal), 2 unused, then the same 14 values as floats in cell-centred
-// coordinates (kWallStride doubles per point).  grid.y = cell.
+// then D points) the point minus each of its six far-image shifts, the wall
+// normal used for the traction and the point itself: 16 doubles (x, y of the
+// six points, the normal, the point), then the same 16 values as floats in
+// cell-centred coordinates (kWallStride doubles per point).  grid.y = cell.
 __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell* __restrict__ cells,
                              const double* __restrict__ e2v, double* __restrict__ wall) {
     const int wp = blockIdx.x * blockDim.x + threadIdx.x, cidx = blockIdx.y;
@@ -517,7 +773,8 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell*
     }
     o[12] = isL ? nl[0] : nd[0];
     o[13] = isL ? nl[1] : nd[1];
-    o[14] = o[15] = 0.0;
+    o[14] = X;  // the collocation point itself (the doubled-cell discrepancy shifts per source)
+    o[15] = Y;
     float* of = reinterpret_cast<float*>(o + 16);
     for (int k = 0; k < 12; k += 2) {
         of[k] = (float)(o[k] - Cx);
@@ -525,7 +782,8 @@ __global__ void k_wall_table(int m, const double* __restrict__ gl_s, const Cell*
     }
     of[12] = (float)o[12];
     of[13] = (float)o[13];
-    of[14] = of[15] = 0.f;
+    of[14] = (float)(X - Cx);
+    of[15] = (float)(Y - Cy);
 }
 
 int build_wall_table(bie_ctx* c, const double* e2, double* wall, cudaStream_t st) {
@@ -548,11 +806,19 @@ __device__ __forceinline__ double fast_log(double x) { return log(x); }
 __device__ __forceinline__ float fast_rcp(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
-template <bool F32>
+//
+// UT (the doubled-cell periodizer): by the same translation invariance a node
+// whose images have m in {m0, m0 + 1}, n in {n0, n0 + 1} contributes on L
+//   sum_{n = n0, n0 + 1} K(x - (m0 - 1) e1 - n e2, y) - K(x - (m0 + 1) e1 - n e2, y)
+// and on D the same with the roles of (m, e1) and (n, e2) exchanged: four
+// evaluations per node, each at least half a cell from the wall even when
+// the node's body crosses it (the point itself comes from the table; src32
+// then holds per-node cell-centred records).
+template <bool F32, bool UT>
 __global__ void __launch_bounds__(256)
 k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const Cell* __restrict__ cells, int m,
        const double* __restrict__ wall, const double* __restrict__ bodyF, double* __restrict__ gpart,
-       unsigned int* __restrict__ ticket, double* __restrict__ gt) {
+       unsigned int* __restrict__ ticket, double* __restrict__ gt, const int* __restrict__ imc) {
     using Real = typename std::conditional<F32, float, double>::type;
     __shared__ double red[4][8];
     __shared__ bool last;
@@ -583,6 +849,24 @@ k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const 
         n1 = wt[13];
     }
     Real ux = 0, uy = 0, tx = 0, ty = 0;
+    // the doubled cell: the collocation point, the lattice vectors, and which
+    // of them the wall's discrepancy steps along (e1 on L, e2 on D)
+    const bool isL = wp < m;
+    Real X0, Y0, e1x, e1y, e2x, e2y;
+    if constexpr (UT) {
+        if constexpr (F32) {
+            const float* wf = reinterpret_cast<const float*>(wt + 16);
+            X0 = wf[14];
+            Y0 = wf[15];
+        } else {
+            X0 = wt[14];
+            Y0 = wt[15];
+        }
+        e1x = (Real)cl.e1[0];
+        e1y = (Real)cl.e1[1];
+        e2x = (Real)cl.e2[0];
+        e2y = (Real)cl.e2[1];
+    }
     const int per = (cl.n_nodes + nsp - 1) / nsp;
     const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -594,9 +878,29 @@ k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const 
             const Src64 q = src64[j];
             sx = q.x; sy = q.y; qx = q.z; qy = q.w;
         }
+        constexpr int NE = UT ? 4 : 6;
+        Real px[NE], py[NE];
+        if constexpr (UT) {
+            const int code = imc[j];
+            const int jm0 = img_m0(code), jn0 = img_n0(code);
+            // evaluation points x - a e1 - b e2: two plus terms, then two minus terms
 #pragma unroll
-        for (int im = 0; im < 6; ++im) {
-            const Real rx = ox[im] - sx, ry = oy[im] - sy;
+            for (int k = 0; k < 4; ++k) {
+                const int d = k & 1, sgn = k < 2 ? -1 : 1;
+                const int a = isL ? jm0 + sgn : jm0 + d, b = isL ? jn0 + d : jn0 + sgn;
+                px[k] = X0 - ((Real)a * e1x + (Real)b * e2x);
+                py[k] = Y0 - ((Real)a * e1y + (Real)b * e2y);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                px[k] = ox[k];
+                py[k] = oy[k];
+            }
+        }
+#pragma unroll
+        for (int im = 0; im < NE; ++im) {
+            const Real rx = px[im] - sx, ry = py[im] - sy;
             const Real r2 = rx * rx + ry * ry;
             const Real inv = fast_rcp(r2);
             const Real rq = rx * qx + ry * qy;
@@ -604,7 +908,7 @@ k_disc(const Src64* __restrict__ src64, const float4* __restrict__ src32, const 
             const Real a = rq * inv;
             const Real vx = l * qx + rx * a, vy = l * qy + ry * a;
             const Real cc = (rx * n0 + ry * n1) * a * inv;
-            if (im < 3) {
+            if (im < NE / 2) {
                 ux += vx; uy += vy; tx += cc * rx; ty += cc * ry;
             } else {
                 ux -= vx; uy -= vy; tx -= cc * rx; ty -= cc * ry;
@@ -839,11 +1143,23 @@ __global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // near-sum work items
 // ---------------------------------------------------------------------------
-static int near_tile(int shape32, int prec) {
-    return prec == 0 ? kNearThreads * kNear32ShapeList[shape32].tpt : kNearThreads;
+// Tile shape of the doubled-cell single-precision near sum: targets per
+// thread and resident CTAs per SM (compile-time overrides for sweeps).
+#ifndef BIE_NEARU_TPT
+#define BIE_NEARU_TPT 4
+#endif
+#ifndef BIE_NEARU_CTAS
+#define BIE_NEARU_CTAS 5
+#endif
+constexpr int kNearUTpt = BIE_NEARU_TPT, kNearUCtas = BIE_NEARU_CTAS;
+
+static int near_tile(int shape32, int prec, bool ut = false) {
+    if (prec == 0) return kNearThreads * (ut ? kNearUTpt : kNear32ShapeList[shape32].tpt);
+    return kNearThreads;
 }
-static int near_ctas_per_sm(int shape32, int prec) {
-    return prec == 0 ? kNear32ShapeList[shape32].ctas : (prec == 1 ? 5 : 4);
+static int near_ctas_per_sm(int shape32, int prec, bool ut = false) {
+    if (prec == 0) return ut ? kNearUCtas : kNear32ShapeList[shape32].ctas;
+    return prec == 1 ? 5 : 4;
 }
 
 // Source splits of every cell for one precision.  All items of one launch
@@ -856,7 +1172,9 @@ static int near_ctas_per_sm(int shape32, int prec) {
 // kItemOverhead sources).  Deterministic: no timing is involved.
 static constexpr int kItemOverhead = 32;
 
-static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, std::vector<int>& splits) {
+// srcmul: source records per node (4 for the doubled-cell image records).
+static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, std::vector<int>& splits,
+                          int srcmul = 1) {
     double W = 0;
     for (const Cell& cl : cells) W += (double)cl.n_nodes * cl.n_nodes;
     double best = 1e300;
@@ -865,13 +1183,13 @@ static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, s
         long long items = 0;
         int maxchunk = 0;
         for (size_t k = 0; k < cells.size(); ++k) {
-            const int n = cells[k].n_nodes;
+            const int n = cells[k].n_nodes, ns = srcmul * n;
             const int tiles = (n + tile - 1) / tile;
             const double share = (double)w * slots * ((double)n * n / W) / tiles;
-            const int s = std::max(1, std::min((n + 63) / 64, (int)share));
+            const int s = std::max(1, std::min((ns + 63) / 64, (int)share));
             sp[k] = s;
             items += (long long)tiles * s;
-            maxchunk = std::max(maxchunk, (n + s - 1) / s);
+            maxchunk = std::max(maxchunk, (ns + s - 1) / s);
         }
         const double cost = (double)((items + slots - 1) / slots) * (maxchunk + kItemOverhead);
         if (cost < best * (1 - 1e-9)) {
@@ -885,9 +1203,9 @@ static void choose_splits(const std::vector<Cell>& cells, int tile, int slots, s
 // cell's splits and partial offsets and uploads the cell table.
 // Items of one precision for the context's current single-precision shape.
 static int build_near_items_prec(bie_ctx* c, int prec) {
-    const int tile = near_tile(c->shape32, prec);
+    const int tile = near_tile(c->shape32, prec, c->utilde);
     std::vector<int> splits;
-    choose_splits(c->cells_h, tile, near_ctas_per_sm(c->shape32, prec) * c->sms, splits);
+    choose_splits(c->cells_h, tile, near_ctas_per_sm(c->shape32, prec, c->utilde) * c->sms, splits, c->srcmul);
     std::vector<int4> items;
     long long off = 0;
     for (int ci = 0; ci < c->ncell; ++ci) {
@@ -922,9 +1240,10 @@ int build_near_items(bie_ctx* c) {
 size_t near_part_bytes(const bie_ctx* c) {
     size_t best = 0;
     for (int prec = 0; prec < 3; ++prec)
-        for (int sh = 0; sh < (prec == 0 ? kNear32Shapes : 1); ++sh) {
+        for (int sh = 0; sh < (prec == 0 && !c->utilde ? kNear32Shapes : 1); ++sh) {
             std::vector<int> splits;
-            choose_splits(c->cells_h, near_tile(sh, prec), near_ctas_per_sm(sh, prec) * c->sms, splits);
+            choose_splits(c->cells_h, near_tile(sh, prec, c->utilde), near_ctas_per_sm(sh, prec, c->utilde) * c->sms,
+                          splits, c->srcmul);
             long long off = 0;
             for (size_t k = 0; k < splits.size(); ++k) off += (long long)splits[k] * c->cells_h[k].n_nodes;
             best = std::max(best, (size_t)off * (prec == 0 ? sizeof(float2) : sizeof(double2)));
@@ -959,8 +1278,19 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
     if (it.count == 0) return BIE_OK;
     // splits with many sources keep their accuracy through compensated tile sums
     int maxchunk = 0;
-    for (const Cell& cl : c->cells_h) maxchunk = std::max(maxchunk, (cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
+    for (const Cell& cl : c->cells_h)
+        maxchunk = std::max(maxchunk, (c->srcmul * cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
     const bool comp = maxchunk > kNear32CompChunk;
+    if (c->utilde) {
+        if (comp)
+            k_near32u<kNearUTpt, true, kNearUCtas><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells,
+                                                                                         c->tgt32, src, part);
+        else
+            k_near32u<kNearUTpt, false, kNearUCtas><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells,
+                                                                                          c->tgt32, src, part);
+        BIE_LAUNCH(c, "k_near32u");
+        return BIE_OK;
+    }
     // one case per entry of kNear32ShapeList (packed, targets per thread, CTAs per SM)
     switch (c->shape32) {
         case 0: near32_variant<2, 5, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
@@ -992,14 +1322,32 @@ static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, i
     const int prec = f32 ? 0 : (df ? 2 : 1);
     if (part == 0) {
         if (&ws == &c->ws) c->ws_x = nullptr;  // the workspace is about to change
-        k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
-                                                     f32 ? ws.src32 : nullptr, ws.src64,
-                                                     df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
+        if (c->utilde)
+            k_pack_moments_u<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                           c->imc, f32 ? ws.src32 : nullptr, f32 ? ws.src32n : nullptr,
+                                                           ws.src64, (!f32 && !df) ? ws.src64u : nullptr,
+                                                           df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
+        else
+            k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                         f32 ? ws.src32 : nullptr, ws.src64,
+                                                         df ? (SrcDF*)ws.srcdf : nullptr, ws.bodyF);
         BIE_LAUNCH(c, "k_pack_moments");
         return BIE_OK;
     }
     if (part == 1) {
         if (f32) return launch_near32(c, ws.src32, (float2*)ws.part);
+        if (c->utilde) {
+            if (df)
+                k_near_dfu<<<c->near[2].count, kNearThreads, 0, c->stream>>>(c->near[2].items, c->cells, c->xw, c->yw,
+                                                                             c->nx, c->ny, (const SrcDF*)ws.srcdf,
+                                                                             (double2*)ws.part);
+            else
+                k_near64u<<<c->near[1].count, kNearThreads, 0, c->stream>>>(c->near[1].items, c->cells, c->xw, c->yw,
+                                                                            c->nx, c->ny, ws.src64u,
+                                                                            (double2*)ws.part);
+            BIE_LAUNCH(c, df ? "k_near_dfu" : "k_near64u");
+            return BIE_OK;
+        }
         if (df) {
             k_near_df<<<c->near[2].count, kNearThreads, 0, c->stream>>>(c->near[2].items, c->cells, c->x, c->y,
                                                                         c->nx, c->ny, (const SrcDF*)ws.srcdf,
@@ -1013,12 +1361,20 @@ static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, i
         return BIE_OK;
     }
     const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
-    if (f32)
-        k_disc<true><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
-                                                   ws.dticket, ws.gt);
-    else
-        k_disc<false><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
-                                                    ws.dticket, ws.gt);
+    if (c->utilde) {
+        if (f32)
+            k_disc<true, true><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32n, c->cells, c->m, c->wall, ws.bodyF,
+                                                             ws.gpart, ws.dticket, ws.gt, c->imc);
+        else
+            k_disc<false, true><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF,
+                                                              ws.gpart, ws.dticket, ws.gt, c->imc);
+    } else if (f32) {
+        k_disc<true, false><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF,
+                                                          ws.gpart, ws.dticket, ws.gt, nullptr);
+    } else {
+        k_disc<false, false><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF,
+                                                           ws.gpart, ws.dticket, ws.gt, nullptr);
+    }
     BIE_LAUNCH(c, "k_disc");
     k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(ws.gt, c->m, c->M, c->cells, c->P, ws.xi, ws.xif);
     BIE_LAUNCH(c, "k_xi");
@@ -1028,8 +1384,8 @@ static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, i
         k_correct32<<<gsc, 256, 0, c->stream>>>((const float2*)ws.part, N, c->node_cell, c->cells, sg, c->tgt32, c->nx,
                                                 c->ny, c->w, c->kap, c->ypf, ws.xif, c->M, T);
     else
-        k_correct<<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell, c->cells, sg, c->x, c->y,
-                                              c->nx, c->ny, c->w, c->kap, c->yp, ws.xi, c->M, T);
+        k_correct<<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell, c->cells, sg, c->xw,
+                                              c->yw, c->nx, c->ny, c->w, c->kap, c->yp, ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
     if (int rc = close_apply(c, sigma, ws.T, f32 ? ws.src32 : nullptr)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
@@ -1200,10 +1556,12 @@ int rhs_device(bie_ctx* c, double* b) {
 // Block (b, s): body b's centroid against source split s of its cell; split 0
 // also adds the proxy terms.  vpart[(b * splits + s) * 3 + c].
 // ---------------------------------------------------------------------------
+// With the doubled-cell periodizer (imc non-null) each source node has its
+// four images instead of the 3 x 3.
 __global__ void __launch_bounds__(256)
 k_velocities(const Src64* __restrict__ src, const double* __restrict__ body, const int* __restrict__ body_cell,
              const Cell* __restrict__ cells, const double* __restrict__ ypall, const double* __restrict__ xiall,
-             int M, double* __restrict__ vpart) {
+             int M, double* __restrict__ vpart, const int* __restrict__ imc) {
     __shared__ double red[33];
     const int b = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
     const int cidx = body_cell[b];
@@ -1214,7 +1572,9 @@ k_velocities(const Src64* __restrict__ src, const double* __restrict__ body, con
     const int j0 = cl.node_off + sp * per, j1 = min(cl.node_off + cl.n_nodes, j0 + per);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         Src64 q = src[j];
-        for (int k = 0; k < 9; ++k) {
+        const int code = imc ? imc[j] : 0;
+        for (int kk = 0; kk < (imc ? 4 : 9); ++kk) {
+            const int k = imc ? img_shift(code, kk) : kk;
             double rx = X - (q.x + cl.sx[k]), ry = Y - (q.y + cl.sy[k]);
             double r2 = rx * rx + ry * ry;
             double rq = (rx * q.z + ry * q.w) / r2;
@@ -1295,11 +1655,22 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     // (FP64-class) residual application was of this density over every
     // cell, so its sources, body moments and proxy strengths are reused
     if (!(reuse_ws && c->ws_x == sigma)) {
-        k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells, nullptr,
-                                                     c->ws.src64, nullptr, c->ws.bodyF);
+        if (c->utilde)
+            k_pack_moments_u<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                           c->imc, nullptr, nullptr, c->ws.src64, nullptr, nullptr,
+                                                           c->ws.bodyF);
+        else
+            k_pack_moments<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
+                                                         nullptr, c->ws.src64, nullptr, c->ws.bodyF);
         BIE_LAUNCH(c, "k_pack_moments");
-        k_disc<false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
-            c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt);
+        if (c->utilde)
+            k_disc<false, true><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
+                c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt,
+                c->imc);
+        else
+            k_disc<false, false><<<dim3(2 * c->m, kDiscSplits, c->ncell), 256, 0, c->stream>>>(
+                c->ws.src64, nullptr, c->cells, c->m, c->wall, c->ws.bodyF, c->ws.gpart, c->ws.dticket, c->ws.gt,
+                nullptr);
         BIE_LAUNCH(c, "k_disc");
         k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(c->ws.gt, c->m, c->M, c->cells, c->P, c->ws.xi,
                                                                c->ws.xif);
@@ -1307,7 +1678,8 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
     }
     if (v || omega) {
         k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, c->body, c->body_cell, c->cells,
-                                                                     c->yp, c->ws.xi, c->M, c->ws.vpart);
+                                                                     c->yp, c->ws.xi, c->M, c->ws.vpart,
+                                                                     c->utilde ? c->imc : nullptr);
         BIE_LAUNCH(c, "k_velocities");
         k_velocities_fin<<<(c->nb + 127) / 128, 128, 0, c->stream>>>(c->ws.vpart, c->nb, kVelSplits, c->body,
                                                                      c->body_cell, c->cells, v, omega);

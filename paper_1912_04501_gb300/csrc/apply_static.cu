@@ -36,8 +36,10 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
                                        std::to_string(BIE_STATIC_MAX_NODES));
     if (c->device < 0 || c->device >= BIE_STATIC_MAX_DEVICES)
         return fail(c, BIE_EINVAL, "bie_apply_static: device ordinal out of range");
-    // layout of the per-call buffers inside the static array
-    const size_t b_src32 = round256(N * sizeof(float4));
+    // layout of the per-call buffers inside the static array (the doubled-cell
+    // periodizer has four image records per node, plus per-node records)
+    const size_t b_src32 = round256(N * c->srcmul * sizeof(float4));
+    const size_t b_src32n = c->utilde ? round256(N * sizeof(float4)) : 0;
     const size_t b_src64 = round256(N * sizeof(Src64));
     const size_t nc = (size_t)c->ncell;
     const size_t b_part = round256(near_part32_elems(c) * sizeof(float2));
@@ -48,7 +50,7 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
     const size_t b_gt = round256(nc * 8 * c->m * sizeof(double));
     const size_t b_tk = round256(nc * 2 * c->m * sizeof(unsigned int));
     const size_t b_T = round256(2 * N * sizeof(double));
-    const size_t need = b_src32 + b_src64 + b_part + b_body + b_gpart + b_xi + b_xif + b_gt + b_tk + b_T;
+    const size_t need = b_src32 + b_src32n + b_src64 + b_part + b_body + b_gpart + b_xi + b_xif + b_gt + b_tk + b_T;
     if (need > BIE_STATIC_SCRATCH_BYTES)
         return fail(c, BIE_EINVAL, "bie_apply_static: this context needs " + std::to_string(need) +
                                        " bytes of scratch; the static array holds " +
@@ -74,6 +76,8 @@ extern "C" int bie_apply_static(bie_ctx* c, const double* sigma, double* out) {
     size_t o = 0;
     ws.src32 = reinterpret_cast<float4*>(base + o);
     o += b_src32;
+    if (c->utilde) ws.src32n = reinterpret_cast<float4*>(base + o);
+    o += b_src32n;
     ws.src64 = reinterpret_cast<Src64*>(base + o);
     o += b_src64;
     ws.part = base + o;

@@ -76,6 +76,7 @@ struct Cell {
     double sx[9], sy[9];      // image shifts m e1 + n e2, index (n + 1) * 3 + (m + 1); index 4 is zero
     float sxf[9], syf[9];
     float sxl[9], syl[9];     // sx - sxf, sy - syf: the shifts as double-float pairs
+    double inv[4];            // inverse of [e1 e2]: lattice coordinates (s, t) = inv (x - C), row-major
     int node_off, n_nodes, body_off, n_bodies;
     long long part_off[3];    // near-sum partial base (elements) per precision: 0 f32, 1 f64, 2 df64
     int splits[3];            // source splits per precision
@@ -96,7 +97,9 @@ struct Close {
     long long* dtab_off = nullptr;  // nb: table base of each body
     int dtab_rho = 0;             // largest rho the tables hold (grown when a pair needs more)
     int* flags = nullptr;         // [total pairs, capacity exceeded, slot overflow, under-resolved,
-                                  //  smallest gap below min_gap (8 bytes), largest rho, -, block doubles (8 bytes)]
+                                  //  smallest gap below min_gap (8 bytes), largest rho, doubled-cell
+                                  //  violations (bit 0: a node beyond the doubled cell, bit 1: a close
+                                  //  pair's body image not wholly among its nodes' images), block doubles (8 bytes)]
     int cap_pairs = 0;
     long long cap_doubles = 0;
     bool grow = true;             // storage grows on demand (no close_capacity given)
@@ -119,9 +122,11 @@ struct __align__(16) Src64 {
 struct Workspace {
     double* sigma = nullptr;    // 2N  staging for host inputs
     double* out = nullptr;      // 2N  staging for host outputs
-    Src64* src64 = nullptr;     // N
-    float4* src32 = nullptr;    // N
-    void* srcdf = nullptr;      // N double-float source records (32 B)
+    Src64* src64 = nullptr;     // N   per node (absolute position)
+    float4* src32 = nullptr;    // N, or 4N image records (n_images 4)
+    float4* src32n = nullptr;   // N   per node, cell-centred (n_images 4: the wall discrepancy's sources)
+    Src64* src64u = nullptr;    // 4N  image records (n_images 4)
+    void* srcdf = nullptr;      // N, or 4N image records: double-float source records (32 B)
     double* bodyF = nullptr;    // 3 nb  (F_x, F_y, tau) per body
     void* part = nullptr;       // near-sum partials (see Cell::part_off)
     size_t part_bytes = 0;
@@ -143,7 +148,21 @@ struct ProxyFit {
     double* P = nullptr;
     double* wall = nullptr;
     double* e2 = nullptr;   // 2 x ncell: the lattice vectors e2 the fits are for
+    double* yp = nullptr;   // ncell x M x 2 proxy points (on U~'s walls they move with the lattice)
+    float2* ypf = nullptr;  // ncell x M proxy points minus the cell centre (single precision)
 };
+
+// Per-node image code (n_images 4): bit 0 m0 + 1, bit 1 n0 + 1 (the node's
+// four images are (m0 + dm) e1 + (n0 + dn) e2, dm, dn in {0, 1}); bits 2..5
+// the index (n + 1) * 3 + (m + 1) of the lattice translate m e1 + n e2 that
+// takes the node into U (its wrap).
+__host__ __device__ inline int img_m0(int code) { return (code & 1) - 1; }
+__host__ __device__ inline int img_n0(int code) { return ((code >> 1) & 1) - 1; }
+__host__ __device__ inline int img_wrap(int code) { return (code >> 2) & 15; }
+// shift-table index (n + 1) * 3 + (m + 1) of image k = dm + 2 dn of a node
+__host__ __device__ inline int img_shift(int code, int k) {
+    return (img_n0(code) + (k >> 1) + 1) * 3 + (img_m0(code) + (k & 1) + 1);
+}
 
 struct Solver {
     int kmax = 0;
@@ -186,6 +205,8 @@ struct NearItems {
 struct bie_ctx {
     int device = 0;
     int sms = 0;                 // streaming multiprocessors of the device (queried at init)
+    bool utilde = false;         // opts.n_images == 4: the doubled-cell periodizer
+    int srcmul = 1;              // source records per node in the near sums (1, or 4)
     cudaStream_t stream = nullptr;
     bie_opts opts{};
     double t = 0;
@@ -203,8 +224,12 @@ struct bie_ctx {
     double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *w = nullptr, *kap = nullptr;
     int* owner = nullptr;
     double* body = nullptr;
-    float4* tgt32 = nullptr;
+    float4* tgt32 = nullptr;    // N: target x - C, y - C (the translate inside U with n_images 4), normal
     float4* posdf = nullptr;    // N: x - C, y - C as double-float (xh, xl, yh, yl)
+    double* xw = nullptr;       // N: target positions of the periodic sums (x, or its translate inside U)
+    double* yw = nullptr;
+    int* imc = nullptr;         // N: image code (img_m0, img_n0, img_wrap), n_images 4
+    int4* bimg = nullptr;       // nb: (min m0, max m0, min n0, max n0) over the body's nodes, n_images 4
     // proxy fits of the current lattices, and of the next time step's (built on
     // a side stream during the current solve)
     double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
@@ -216,7 +241,7 @@ struct bie_ctx {
     bie::ProxyFit next;
     cudaStream_t side = nullptr;
     cudaEvent_t next_done = nullptr;
-    double* yp = nullptr;       // ncell x M x 2 proxy points
+    double* yp = nullptr;       // ncell x M x 2 proxy points of the current fit
     float2* ypf = nullptr;      // ncell x M proxy points minus the cell centre (single precision)
     double* scal = nullptr;     // 3 nb + ncell + 8: velocities, rotation rates, mu_eff
     bie::Workspace ws;

@@ -47,16 +47,21 @@ __global__ void k_body_h(const double* __restrict__ w, double* __restrict__ body
 // record: int4 (body, image, rho, 0).  Distances to the curve below gap_lim
 // (other bodies and the target's own periodic images) lower *gap_min, the
 // bit pattern of a non-negative double (such patterns order like integers).
+// With the doubled-cell periodizer (imc non-null) a pair is valid only when
+// the body image, seen from the target's translate inside U, is among the
+// images of every node of the body (bimg); otherwise bit 1 of *gflag is set.
 __global__ void k_close_detect(const double* __restrict__ x, const double* __restrict__ y,
                                const int* __restrict__ owner, const double* __restrict__ body,
                                const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                                double close_factor, double gap_lim, int kmax, int4* __restrict__ slots,
                                int* __restrict__ count, int* __restrict__ overflow,
                                unsigned long long* __restrict__ gap_min, int* __restrict__ rho_max,
-                               float* __restrict__ dmin, float2* __restrict__ ddir) {
+                               float* __restrict__ dmin, float2* __restrict__ ddir, const int* __restrict__ imc,
+                               const int4* __restrict__ bimg, int* __restrict__ gflag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Cell& sh = cells[node_cell[i]];
+    const int wi = imc ? img_wrap(imc[i]) : 4;  // the target's translate into U
     double X = x[i], Y = y[i];
     int own = owner[i];
     int c = 0;
@@ -119,6 +124,12 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
             int rho = 2;
             while ((rho - 0.5) * dcur < 6.4 * hloc && rho < kMaxRho) rho <<= 1;
             if ((rho - 0.5) * dcur < 6.4 * hloc) atomicAdd(overflow + 1, 1);  // closer than kMaxRho resolves
+            if (imc) {
+                // image (m, n) of body b seen from the translate of the target
+                const int m = (im % 3 - 1) + (wi % 3 - 1), nn = (im / 3 - 1) + (wi / 3 - 1);
+                const int4 r = bimg[b];
+                if (!(r.y <= m && m <= r.x + 1 && r.w <= nn && nn <= r.z + 1)) atomicOr(gflag, 2);
+            }
             if (c < kmax) {
                 slots[(size_t)i * kmax + c] = make_int4(b, im, rho, 0);
                 atomicMax(rho_max, rho);
@@ -358,6 +369,17 @@ static int regrow(bie_ctx* c, T** p, size_t count) {
     return BIE_OK;
 }
 
+// The doubled-cell periodizer's geometry conditions (flags[7], set by
+// k_geometry and k_close_detect).
+static int doubled_cell_check(bie_ctx* c, int f) {
+    if (f & 1)
+        return fail(c, BIE_EINVAL, "n_images 4: a node lies beyond the doubled cell (a body larger than the cell?)");
+    if (f & 2)
+        return fail(c, BIE_EINVAL, "n_images 4: a close-evaluation pair sees a body image that is not among all its "
+                                   "nodes' doubled-cell images (a body larger than about half a cell)");
+    return BIE_OK;
+}
+
 int build_close(bie_ctx* c) {
     ++c->epoch;  // close pairs, blocks and their storage change
     c->cl.npairs = 0;
@@ -366,7 +388,15 @@ int build_close(bie_ctx* c) {
     BIE_LAUNCH(c, "k_body_h");
     c->cl.min_gap = INFINITY;
     const double gap_lim = c->opts.min_gap > 0 ? c->opts.min_gap : 0.0;
-    if (!(c->opts.close_factor > 0) && !(gap_lim > 0)) return BIE_OK;
+    if (!(c->opts.close_factor > 0) && !(gap_lim > 0)) {
+        if (c->utilde) {
+            int f = 0;
+            BIE_CUDA(c, cudaMemcpyAsync(&f, c->cl.flags + 7, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+            return doubled_cell_check(c, f);
+        }
+        return BIE_OK;
+    }
     const int N = c->N, kmax = kCloseSlots;
     BIE_CUDA(c, cudaMemsetAsync(c->cl.flags, 0, 4 * sizeof(int), c->stream));
     BIE_CUDA(c, cudaMemsetAsync(c->cl.flags + 6, 0, sizeof(int), c->stream));
@@ -376,9 +406,10 @@ int build_close(bie_ctx* c) {
     k_close_detect<<<(N + 127) / 128, 128, 0, c->stream>>>(c->x, c->y, c->owner, c->body, c->node_cell, c->cells, N,
                                                          c->opts.close_factor, gap_lim, kmax, c->cl.slots,
                                                          c->cl.count, c->cl.flags + 2, gap_min, c->cl.flags + 6,
-                                                         c->cl.dmin, c->cl.ddir);
+                                                         c->cl.dmin, c->cl.ddir, c->utilde ? c->imc : nullptr,
+                                                         c->bimg, c->cl.flags + 7);
     BIE_LAUNCH(c, "k_close_detect");
-    int h[7];
+    int h[8];
     long long need_doubles = 0;
     unsigned long long gm = 0;
     // the scan again after growing the storage (never a third time: the
@@ -388,10 +419,11 @@ int build_close(bie_ctx* c) {
                                                c->cl.blk_off, c->cl.pairs, c->cl.flags, need, c->cl.cap_doubles,
                                                c->cl.cap_pairs);
         BIE_LAUNCH(c, "k_close_scan");
-        BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 7 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        BIE_CUDA(c, cudaMemcpyAsync(h, c->cl.flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         BIE_CUDA(c, cudaMemcpyAsync(&need_doubles, need, sizeof need_doubles, cudaMemcpyDeviceToHost, c->stream));
         BIE_CUDA(c, cudaMemcpyAsync(&gm, gap_min, sizeof gm, cudaMemcpyDeviceToHost, c->stream));
         BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (int rc = doubled_cell_check(c, h[7])) return rc;
         if (h[2] > 0)
             return fail(c, BIE_EINVAL, "a node is close to more than " + std::to_string(kmax) +
                                            " body images (bodies overlap or nearly so)");
@@ -483,6 +515,11 @@ int build_dirichlet_tables(bie_ctx* c, int rho_max) {
 // positions (then rounded to single precision); the close-evaluation blocks
 // are applied in single precision (stored divided by the weights, acting on
 // q = sigma w).  Everything runs on the FP32 pipe.
+//
+// With the doubled-cell periodizer (imc non-null) the near sum evaluated the
+// pair at the target's translate inside U (tgt32) against the source's image
+// record src32[4 j + k], k the node's image that lands the body image where
+// it is seen from that translate; the redo recomputes that term.
 __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
                                 const long long* __restrict__ blk_off, const float* __restrict__ blocks32,
                                 int use_pairs, const double* __restrict__ body, const int* __restrict__ owner,
@@ -490,12 +527,13 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
                                 const float4* __restrict__ src32, const float4* __restrict__ posdf,
                                 const double* __restrict__ x, const double* __restrict__ y,
                                 const int* __restrict__ node_cell, const Cell* __restrict__ cells,
-                                double2* __restrict__ T) {
+                                const int* __restrict__ imc, double2* __restrict__ T) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= N) return;
     const Cell& cl = cells[node_cell[i]];
     const float4 tv = tgt32[i];
     const float4 pi = posdf[i];
+    const int wi = imc ? img_wrap(imc[i]) : 4;
     float fx = 0.f, fy = 0.f;  // sum of (exactly differenced term - single-precision term)
     // target minus the image shift, exactly, as a double-float pair (xh, xl, yh, yl)
     auto shifted = [&](int im) {
@@ -505,9 +543,24 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
         return p;
     };
     auto redo = [&](int j, int im, const float4& p) {
-        const float4 s = src32[j];
-        const float dx = (tv.x - cl.sxf[im]) - s.x;
-        const float dy = (tv.y - cl.syf[im]) - s.y;
+        float4 s;
+        float dx, dy;
+        if (imc) {
+            // image (m, n) of node j seen from the translate: its record index
+            const int code = imc[j];
+            const int dm = (im % 3 - 1) + (wi % 3 - 1) - img_m0(code);
+            const int dn = (im / 3 - 1) + (wi / 3 - 1) - img_n0(code);
+            // not among the node's images: the near sum has no such term (on
+            // a body wider than half a cell, far from the target)
+            if (dm < 0 || dm > 1 || dn < 0 || dn > 1) return;
+            s = src32[4 * (size_t)j + (dm + 2 * dn)];
+            dx = tv.x - s.x;
+            dy = tv.y - s.y;
+        } else {
+            s = src32[j];
+            dx = (tv.x - cl.sxf[im]) - s.x;
+            dy = (tv.y - cl.syf[im]) - s.y;
+        }
         const float c0 = pair32(dx, dy, tv.z, tv.w, s.z, s.w);
         const float4 q = posdf[j];
         float rh, rl, sh, sl;
@@ -536,7 +589,7 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
             const float4 p = shifted(im);
             for (int k = lane; k < nbn; k += 32) {
                 redo(off + k, im, p);
-                const float4 s = src32[off + k];
+                const float4 s = src32[imc ? 4 * (size_t)(off + k) : (size_t)(off + k)];  // q: the same in every record
                 const float A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
                 bx = fmaf(A, s.z, fmaf(B, s.w, bx));
                 by = fmaf(B, s.z, fmaf(D, s.w, by));
@@ -565,7 +618,8 @@ int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32)
         k_close_apply32<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks32,
                                                  c->cl.npairs > 0 ? 1 : 0, c->body, c->owner,
                                                  reinterpret_cast<const double2*>(sigma), N, c->tgt32, src32, c->posdf,
-                                                 c->x, c->y, c->node_cell, c->cells, reinterpret_cast<double2*>(T));
+                                                 c->x, c->y, c->node_cell, c->cells, c->utilde ? c->imc : nullptr,
+                                                 reinterpret_cast<double2*>(T));
         BIE_LAUNCH(c, "k_close_apply32");
         return BIE_OK;
     }

@@ -17,11 +17,20 @@ namespace bie {
 // ---------------------------------------------------------------------------
 // nodes, normals, weights, curvature
 // ---------------------------------------------------------------------------
+// With utilde (n_images 4) also each node's image code (Def. Gnear: the two
+// integers m with -1 <= s + m < 1 are m0 = ceil(-1 - s) and m0 + 1, likewise
+// n0 for t; (s, t) its lattice coordinates about the cell centre) and its
+// translate into U (lattice coordinates rounded into [-1/2, 1/2)), where the
+// periodic sums are evaluated (Sec. 6.2): xw, yw and tgt32 hold that
+// translate.  A node whose images would leave the 3 x 3 shift table (a body
+// reaching beyond the doubled cell) raises bit 0 of *gflag.
 __global__ void k_geometry(const double* __restrict__ body, const int* __restrict__ owner,
                            const int* __restrict__ node_cell, const Cell* __restrict__ cells, int N,
                            double* __restrict__ x, double* __restrict__ y, double* __restrict__ nx,
                            double* __restrict__ ny, double* __restrict__ w, double* __restrict__ kap,
-                           float4* __restrict__ tgt32, float4* __restrict__ posdf) {
+                           float4* __restrict__ tgt32, float4* __restrict__ posdf, int utilde,
+                           double* __restrict__ xw, double* __restrict__ yw, int* __restrict__ imc,
+                           int* __restrict__ gflag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double* bd = body + 8 * owner[i];
@@ -45,7 +54,25 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
     ny[i] = -tx;
     w[i] = (2.0 * kPi / n) * sp;
     kap[i] = (dX * ddY - dY * ddX) / (sp * sp * sp);
-    tgt32[i] = make_float4((float)(X - cl.C[0]), (float)(Y - cl.C[1]), (float)ty, (float)(-tx));
+    double XW = X, YW = Y;
+    if (utilde) {
+        const double px_ = X - cl.C[0], py_ = Y - cl.C[1];
+        const double ls = cl.inv[0] * px_ + cl.inv[1] * py_, lt = cl.inv[2] * px_ + cl.inv[3] * py_;
+        const int m0 = (int)ceil(-1.0 - ls), n0 = (int)ceil(-1.0 - lt);
+        const int wm = -(int)floor(ls + 0.5), wn = -(int)floor(lt + 0.5);
+        if (m0 < -1 || m0 > 0 || n0 < -1 || n0 > 0 || wm < -1 || wm > 1 || wn < -1 || wn > 1) {
+            atomicOr(gflag, 1);
+            imc[i] = 0 | (0 << 1) | (4 << 2);
+        } else {
+            const int wi = (wn + 1) * 3 + (wm + 1);
+            imc[i] = (m0 + 1) | ((n0 + 1) << 1) | (wi << 2);
+            XW = X + cl.sx[wi];
+            YW = Y + cl.sy[wi];
+        }
+    }
+    xw[i] = XW;
+    yw[i] = YW;
+    tgt32[i] = make_float4((float)(XW - cl.C[0]), (float)(YW - cl.C[1]), (float)ty, (float)(-tx));
     float4 pd;
     split_df(X - cl.C[0], pd.x, pd.y);
     split_df(Y - cl.C[1], pd.z, pd.w);
@@ -254,21 +281,88 @@ __global__ void k_form_P(const double* __restrict__ Aall, int R, int C, const do
     for (int r = tid; r < C; r += nt) P[(size_t)r * Qrows + c] = z[r];
 }
 
+// Per body the range of its nodes' image codes: (min m0, max m0, min n0,
+// max n0); a body image (m, n) is wholly among its nodes' images when
+// max m0 <= m <= min m0 + 1 and max n0 <= n <= min n0 + 1.
+__global__ void k_body_img(const int* __restrict__ imc, const double* __restrict__ body, int4* __restrict__ bimg) {
+    __shared__ int r[4];
+    const int b = blockIdx.x;
+    const int n = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+    if (threadIdx.x == 0) {
+        r[0] = 1;
+        r[1] = -2;
+        r[2] = 1;
+        r[3] = -2;
+    }
+    __syncthreads();
+    int a0 = 1, a1 = -2, b0 = 1, b1 = -2;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int code = imc[off + k];
+        a0 = min(a0, img_m0(code));
+        a1 = max(a1, img_m0(code));
+        b0 = min(b0, img_n0(code));
+        b1 = max(b1, img_n0(code));
+    }
+    atomicMin(&r[0], a0);
+    atomicMax(&r[1], a1);
+    atomicMin(&r[2], b0);
+    atomicMax(&r[3], b1);
+    __syncthreads();
+    if (threadIdx.x == 0) bimg[b] = make_int4(r[0], r[1], r[2], r[3]);
+}
+
 int build_geometry(bie_ctx* c) {
     ++c->epoch;  // node data and the adopted proxy fit (pointers swapped by a time step)
     c->ws_x = nullptr;  // positions change: the workspace's sources are stale
     int bs = 256, gs = (c->N + bs - 1) / bs;
+    int* gflag = c->cl.flags + 6 + 1;  // doubled-cell violations (read with the close pairs)
+    BIE_CUDA(c, cudaMemsetAsync(gflag, 0, sizeof(int), c->stream));
     k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->node_cell, c->cells, c->N, c->x, c->y, c->nx, c->ny,
-                                        c->w, c->kap, c->tgt32, c->posdf);
+                                        c->w, c->kap, c->tgt32, c->posdf, c->utilde ? 1 : 0, c->xw, c->yw, c->imc,
+                                        gflag);
     BIE_LAUNCH(c, "k_geometry");
+    if (c->utilde) {
+        k_body_img<<<c->nb, 128, 0, c->stream>>>(c->imc, c->body, c->bimg);
+        BIE_LAUNCH(c, "k_body_img");
+    }
     return BIE_OK;
+}
+
+// Proxies on the walls of the doubled cell U~ (Sec. 6.1, remark after Eq. W):
+// M / 4 per wall at the midpoints of equal sub-intervals, walls at lattice
+// coordinates -1 and +1 about the cell centre (for side -1, then +1: the
+// points C + side e1 + s e2, then C + side e2 + s e1).  grid.y = cell.
+__global__ void k_proxy_box(int M, const Cell* __restrict__ cells, const double* __restrict__ e2v,
+                            double* __restrict__ yp, float2* __restrict__ ypf) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x, cidx = blockIdx.y;
+    if (p >= M) return;
+    const Cell& cl = cells[cidx];
+    const int k = M / 4;
+    const int side = p < 2 * k ? -1 : 1, q = p % (2 * k), j = q % k;
+    const double s = (j + 0.5) / k * 2.0 - 1.0;
+    const double e1x = cl.e1[0], e1y = cl.e1[1], e2x = e2v[2 * cidx], e2y = e2v[2 * cidx + 1];
+    double X, Y;
+    if (q < k) {
+        X = cl.C[0] + side * e1x + s * e2x;
+        Y = cl.C[1] + side * e1y + s * e2y;
+    } else {
+        X = cl.C[0] + side * e2x + s * e1x;
+        Y = cl.C[1] + side * e2y + s * e1y;
+    }
+    yp[(size_t)cidx * 2 * M + 2 * p] = X;
+    yp[(size_t)cidx * 2 * M + 2 * p + 1] = Y;
+    ypf[(size_t)cidx * M + p] = make_float2((float)(X - cl.C[0]), (float)(Y - cl.C[1]));
 }
 
 int build_proxy_fit_to(bie_ctx* c, ProxyFit& f, cudaStream_t st) {
     const int m = c->m, M = c->M;
     const int Qrows = 8 * m, C = 2 * M, R = Qrows + C;
     const int bs = 128;
-    k_build_Q<<<dim3((m * M + bs - 1) / bs, c->ncell), bs, 0, st>>>(f.A, R, m, M, c->gl_s, c->yp, c->cells, f.e2);
+    if (c->utilde) {
+        k_proxy_box<<<dim3((M + 63) / 64, c->ncell), 64, 0, st>>>(M, c->cells, f.e2, f.yp, f.ypf);
+        BIE_LAUNCH(c, "k_proxy_box");
+    }
+    k_build_Q<<<dim3((m * M + bs - 1) / bs, c->ncell), bs, 0, st>>>(f.A, R, m, M, c->gl_s, f.yp, c->cells, f.e2);
     BIE_LAUNCH(c, "k_build_Q");
     k_qr<<<c->ncell, 1024, 0, st>>>(f.A, R, C, Qrows, c->opts.lam_rel, f.beta);
     BIE_LAUNCH(c, "k_qr");
@@ -278,7 +372,7 @@ int build_proxy_fit_to(bie_ctx* c, ProxyFit& f, cudaStream_t st) {
 }
 
 int build_proxy_fit(bie_ctx* c) {
-    ProxyFit f{c->A, c->beta, c->P, c->wall, c->e2d};
+    ProxyFit f{c->A, c->beta, c->P, c->wall, c->e2d, c->yp, c->ypf};
     return build_proxy_fit_to(c, f, c->stream);
 }
 
