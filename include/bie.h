@@ -231,6 +231,21 @@ int bie_solve(bie_ctx* ctx, const double* rhs, double* sigma, int32_t use_guess,
 int bie_velocities(bie_ctx* ctx, const double* sigma, double* v, double* omega, double* mu_eff,
                    int32_t on_device);
 
+/* Effective viscosity per cell by the contour-deformation formula of
+ * Sec. 6.4 (Eq. contourdef): the shear force per unit shear through a contour
+ * from L to R below every body, moved by Gauss' law to the walls
+ * D - e2, D - e1 - e2, R - e2 and L - e1 - e2 (each at least half a cell from
+ * every source, so the trapezoidal quadrature is never evaluated near a
+ * curve) with the density's near sum taken from each curve's quadrant pieces
+ * translated by -e1 (right half) and -e2 (upper half), minus the net force of
+ * the upper pieces, plus the proxy correction's traction on D; 32-point
+ * Gauss-Legendre rules per wall.  Unlike Eq. (mueff) on D it holds when
+ * bodies cross D, and it agrees with the particle-stress average of
+ * bie_velocities to discretisation accuracy.  Needs opts.n_images = 4
+ * (BIE_EINVAL otherwise).  sigma: 2N doubles; mu_eff: one per cell; host
+ * pointers unless on_device. */
+int bie_mu_eff_contour(bie_ctx* ctx, const double* sigma, double* mu_eff, int32_t on_device);
+
 /* Advance n_steps forward-Euler steps of size dt (Sec. 7): solve, extract
  * (v, omega, mu_eff), move and rotate the bodies, shear the lattice
  * e2(t) = (gamma t L2 reduced by the nearest multiple of e1, L2) and re-wrap
@@ -374,6 +389,25 @@ typedef struct {
 
 int bie_profile(bie_ctx* ctx, int32_t enable);
 int bie_profile_read(bie_ctx* ctx, bie_profile_info* info);
+
+/* Target partition for a solve sharded across processes, one GPU each
+ * (Sec. 6.2: the near sum, the dominant cost, splits by target).  Every
+ * process holds the whole cell (geometry, proxy fit and density are
+ * replicated) and owns the targets of bodies [body_begin, body_end) (whole
+ * bodies, so each close-evaluation row stays with its target).  Every
+ * operator application -- bie_apply, and each one inside bie_solve and
+ * bie_step -- then evaluates the near sum only for its own targets (and node
+ * 0, whose traction fixes the pressure constant), and calls exchange(y, 2N,
+ * user) with the device vector y once its own rows are final and the stream
+ * is synchronised; exchange must fill every other process's rows (an
+ * all-gather of the slices) before returning, and return 0 (non-zero makes
+ * the call fail with BIE_ECUDA).  The rest of the solve (wall discrepancy,
+ * proxy fit, GMRES, extraction) runs replicated and bit-identical on every
+ * process, so no other collective is needed.  The whole range (0, n_bodies)
+ * with exchange NULL switches partitioning off.  Single-cell contexts only.
+ * The paper has no multi-process design; this is the hot path's data split. */
+int bie_set_partition(bie_ctx* ctx, int32_t body_begin, int32_t body_end,
+                      int (*exchange)(double* y, int64_t n2, void* user), void* user);
 
 /* Streaming multiprocessors of the context's device, as queried at bie_init
  * (the near-sum work items are sized for them). */

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbie.so")
-SOURCES = ["geometry.cu", "apply.cu", "close.cu", "solve.cu", "api.cu", "apply_static.cu", "net.cu", "precond.cu", "peak.cu"]
+SOURCES = ["geometry.cu", "apply.cu", "close.cu", "solve.cu", "api.cu", "apply_static.cu", "net.cu", "precond.cu", "peak.cu", "contour.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -119,6 +119,8 @@ def library():
         "bie_near_shape": (c_int32, [vp, ctypes.POINTER(c_int32), vp]),
         "bie_apply_static": (c_int32, [vp, vp, vp]),
         "bie_device_sms": (c_int32, [vp, ctypes.POINTER(c_int32)]),
+        "bie_mu_eff_contour": (c_int32, [vp, vp, vp, c_int32]),
+        "bie_set_partition": (c_int32, [vp, c_int32, c_int32, vp, vp]),
         "bie_alu_peak": (c_int32, [c_int32, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                    ctypes.POINTER(c_double)]),
         "bie_profile": (c_int32, [vp, c_int32]),
@@ -156,7 +158,7 @@ def exported_symbols():
                         "bie_set_warm_net", "bie_net_init", "bie_net_destroy", "bie_net_last_error",
                         "bie_net_size", "bie_net_set_stream", "bie_net_set_params", "bie_net_get_params",
                         "bie_net_forward", "bie_net_loss_grad", "bie_net_adam_step", "bie_get_history",
-                        "bie_set_history", "bie_near_shape", "bie_device_sms", "bie_alu_peak")
+                        "bie_set_history", "bie_near_shape", "bie_device_sms", "bie_alu_peak", "bie_mu_eff_contour", "bie_set_partition")
             if hasattr(L, n)]
 
 
@@ -301,6 +303,21 @@ class Context:
         self._check(library().bie_velocities(self.h, s.ctypes.data, v.ctypes.data, om.ctypes.data,
                                              mu.ctypes.data, 0))
         return v.reshape(-1, 2), om, (mu if self.batch else float(mu[0]))
+
+    def set_partition(self, body_begin, body_end, exchange):
+        """bie_set_partition: own the targets of bodies [body_begin, body_end);
+        exchange is a ctypes callback (shard.EXCHANGE) or None to switch off."""
+        fn = ctypes.cast(exchange, c_void_p) if exchange is not None else None
+        self._exchange = exchange
+        self._check(library().bie_set_partition(self.h, int(body_begin), int(body_end), fn, None))
+
+    def mu_eff_contour(self, sigma):
+        """mu_eff by the contour-deformation formula (n_images 4 contexts):
+        a float for one cell, one value per cell for a batch."""
+        mu = np.zeros(self.n_cells)
+        s = np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+        self._check(library().bie_mu_eff_contour(self.h, s.ctypes.data, mu.ctypes.data, 0))
+        return mu if self.batch else float(mu[0])
 
     def step(self, dt, n_steps=1):
         """mu_eff per step (n_steps) for one cell, (n_steps x n_cells) for a batch."""

@@ -34,7 +34,7 @@ static void free_all(bie_ctx* c) {
     free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
                     c->tgt32, c->posdf, c->xw, c->yw, c->imc, c->bimg, c->ws.src32n, c->ws.src64u, c->next.yp,
-                    c->next.ypf,
+                    c->next.ypf, c->glc, c->contour_part,
                     c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
@@ -923,6 +923,28 @@ int bie_features(bie_ctx* c, float* X, int32_t on_device) {
     if (!on_device)
         BIE_CUDA(c, cudaMemcpyAsync(X, c->sv.feat, (size_t)kNetFeatures * c->N * sizeof(float),
                                     cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return BIE_OK;
+}
+
+int bie_set_partition(bie_ctx* c, int32_t body_begin, int32_t body_end,
+                      int (*exchange)(double* y, int64_t n2, void* user), void* user) {
+    if (!c) return BIE_EINVAL;
+    if (c->ncell != 1) return fail(c, BIE_EINVAL, "a target partition is for single-cell contexts");
+    if (body_begin < 0 || body_end > c->nb || body_begin >= body_end)
+        return fail(c, BIE_EINVAL, "body range out of bounds");
+    const bool whole = body_begin == 0 && body_end == c->nb;
+    if (!whole && !exchange) return fail(c, BIE_EINVAL, "a proper partition needs an exchange callback");
+    BIE_CUDA(c, cudaSetDevice(c->device));
+    c->shard.on = !whole;
+    c->shard.b0 = body_begin;
+    c->shard.b1 = body_end;
+    c->shard.n0 = c->offsets[body_begin];
+    c->shard.n1 = c->offsets[body_end];
+    c->shard.exchange = whole ? nullptr : exchange;
+    c->shard.user = whole ? nullptr : user;
+    int rc = build_near_items(c);
+    if (rc) return rc;
     BIE_CUDA(c, cudaStreamSynchronize(c->stream));
     return BIE_OK;
 }

@@ -1215,8 +1215,15 @@ static int build_near_items_prec(bie_ctx* c, int prec) {
         cl.part_off[prec] = off;
         off += (long long)splits[ci] * n;
         const int tiles = (n + tile - 1) / tile;
-        for (int t = 0; t < tiles; ++t)
+        for (int t = 0; t < tiles; ++t) {
+            // a target partition (bie_set_partition) keeps the tiles that meet
+            // its node range, and the first tile (node 0's traction fixes the
+            // pressure); the splits stay those of the whole cell, so every
+            // kept target's partial sums are the unpartitioned ones bit for bit
+            const int a = cl.node_off + t * tile, b = std::min(cl.node_off + n, a + tile);
+            if (c->shard.on && t > 0 && (b <= c->shard.n0 || a >= c->shard.n1)) continue;
             for (int s = 0; s < splits[ci]; ++s) items.push_back(make_int4(ci, t, s, 0));
+        }
     }
     const size_t bytes = off * (prec == 0 ? sizeof(float2) : sizeof(double2));
     if (bytes > c->ws.part_bytes) return fail(c, BIE_EINVAL, "near-sum partial buffer too small");
@@ -1485,8 +1492,15 @@ void free_graph(bie_ctx* c) {
 }
 
 int apply_device(bie_ctx* c, const double* sigma, double* yout, int precision) {
-    if (precision == BIE_MIXED && c->opts.graph) return apply_graph(c, sigma, yout);
-    return apply_impl(c, sigma, yout, precision, c->ws);
+    int rc = (precision == BIE_MIXED && c->opts.graph) ? apply_graph(c, sigma, yout)
+                                                       : apply_impl(c, sigma, yout, precision, c->ws);
+    if (rc || !c->shard.on) return rc;
+    // sharded by target: this process's rows are final; the exchange fills
+    // the others from the processes that own them before anything reads them
+    BIE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->shard.exchange(yout, 2 * (int64_t)c->N, c->shard.user) != 0)
+        return fail(c, BIE_ECUDA, "target-partition exchange failed");
+    return BIE_OK;
 }
 
 // Time every single-precision tile shape on the context's own cells and keep
@@ -1649,11 +1663,11 @@ __global__ void k_mu_eff(const double2* __restrict__ sigma, const double* __rest
     if (threadIdx.x == 0) out[blockIdx.x] = cl.mu - s / (cl.gamma * area);
 }
 
-int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff, bool reuse_ws) {
+// The double-precision per-node sources, body moments and proxy strengths of
+// sigma in the workspace (Sec. 6.2 steps 1-3 without the near sum); skipped
+// when the workspace already holds them (reuse_ws).
+int fp64_moments_and_xi(bie_ctx* c, const double* sigma, bool reuse_ws) {
     const double2* sg = reinterpret_cast<const double2*>(sigma);
-    // reuse_ws: the time step calls this right after a solve whose last
-    // (FP64-class) residual application was of this density over every
-    // cell, so its sources, body moments and proxy strengths are reused
     if (!(reuse_ws && c->ws_x == sigma)) {
         if (c->utilde)
             k_pack_moments_u<<<c->nb, 256, 0, c->stream>>>(sg, c->x, c->y, c->w, c->body, c->body_cell, c->cells,
@@ -1676,6 +1690,15 @@ int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega,
                                                                c->ws.xif);
         BIE_LAUNCH(c, "k_xi");
     }
+    return BIE_OK;
+}
+
+int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff, bool reuse_ws) {
+    const double2* sg = reinterpret_cast<const double2*>(sigma);
+    // reuse_ws: the time step calls this right after a solve whose last
+    // (FP64-class) residual application was of this density over every
+    // cell, so its sources, body moments and proxy strengths are reused
+    if (int rc = fp64_moments_and_xi(c, sigma, reuse_ws)) return rc;
     if (v || omega) {
         k_velocities<<<dim3(c->nb, kVelSplits), 256, 0, c->stream>>>(c->ws.src64, c->body, c->body_cell, c->cells,
                                                                      c->yp, c->ws.xi, c->M, c->ws.vpart,

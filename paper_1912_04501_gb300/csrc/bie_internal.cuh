@@ -230,6 +230,9 @@ struct bie_ctx {
     double* yw = nullptr;
     int* imc = nullptr;         // N: image code (img_m0, img_n0, img_wrap), n_images 4
     int4* bimg = nullptr;       // nb: (min m0, max m0, min n0, max n0) over the body's nodes, n_images 4
+    double* glc = nullptr;      // contour mu_eff: Gauss-Legendre nodes and weights on (-1/2, 1/2) (on demand)
+    double* contour_part = nullptr;  // its per-split wall sums (on demand)
+    size_t contour_part_n = 0;
     // proxy fits of the current lattices, and of the next time step's (built on
     // a side stream during the current solve)
     double* gl_s = nullptr;     // m Gauss-Legendre nodes on (-1/2, 1/2)
@@ -275,6 +278,14 @@ struct bie_ctx {
     } graph;
     float tune_ms[bie::kNear32Shapes] = {};  // autotuner: median launch time per shape (0 = not timed)
     const bie_net* net = nullptr;  // warm-start network (not owned)
+    // target partition across processes (bie_set_partition)
+    struct {
+        bool on = false;
+        int b0 = 0, b1 = 0;          // owned bodies [b0, b1)
+        int n0 = 0, n1 = 0;          // their nodes [n0, n1)
+        int (*exchange)(double*, int64_t, void*) = nullptr;
+        void* user = nullptr;
+    } shard;
     // profiling (bie_profile): launch counter and event pairs around near sums
     bool prof = false;
     long long launches = 0;
@@ -342,6 +353,10 @@ int apply_device(bie_ctx* c, const double* sigma, double* y, int precision);
 // single-precision-pair application with caller-provided per-call buffers
 int apply_device_ws(bie_ctx* c, const double* sigma, double* y, Workspace& ws);
 int rhs_device(bie_ctx* c, double* b);
+// double-precision per-node sources, body moments and proxy strengths of sigma
+int fp64_moments_and_xi(bie_ctx* c, const double* sigma, bool reuse_ws = false);
+// per cell mu_eff by the contour-deformation formula (doubled-cell periodizer; contour.cu)
+int mu_eff_contour_device(bie_ctx* c, const double* sigma, double* mu_eff);
 // per body v (2 nb), omega (nb); per cell mu_eff (ncell)
 int velocities_device(bie_ctx* c, const double* sigma, double* v, double* omega, double* mu_eff,
                       bool reuse_ws = false);

@@ -175,3 +175,50 @@ def test_utilde_rejects_a_body_too_large():
     with pytest.raises(bie.BieError) as e:
         bie.Context(cell, precision=bie.BIE_FP64, n_images=4)
     assert e.value.code == bie.BIE_EINVAL
+
+
+@pytest.mark.parametrize("crossing", [False, True])
+def test_utilde_contour_mu_eff(crossing):
+    """Sec. 6.4 (Eq. contourdef) on the GPU: against the oracle's contour
+    formula on the same density (same sums in another order: 1e-12), and
+    against the particle-stress average (agreement to discretisation
+    accuracy); with a body across the bottom wall D, Eq. (mueff) on D itself
+    is far off while the contour formula still holds.  (The 1e-10 bar is
+    that of every FP64 comparison with the oracle: each side fits its own
+    proxy strengths, whose Tikhonov fit carries rounding of Q into the
+    correction at ~1e-11.)"""
+    e1, e2, c = np.array([1.0, 0.0]), np.array([0.3, 1.0]), np.array([0.5, 0.5])
+
+    def at(s, t):
+        return (c + s * e1 + t * e2).tolist()
+
+    bodies = [dict(a=0.12, b=0.06, xc=at(-0.18, 0.16), theta=0.4, n=128)]
+    if crossing:
+        bodies.append(dict(a=0.10, b=0.07, xc=at(0.17, -0.46), theta=0.3, n=160))
+    else:
+        bodies += [dict(a=0.10, b=0.07, xc=at(0.17, -0.15), theta=2.0, n=128),
+                   dict(a=0.09, b=0.05, xc=at(0.02, -0.02), theta=1.1, n=128)]
+    cell = dict(e1=e1.tolist(), e2=e2.tolist(), centre=c.tolist(), mu=1.0, gamma=1.0, bodies=bodies,
+                solver=dict(n_proxy=M_BOX, proxy_radius=1.5, n_coll=M_COLL))
+    ctx = bie.Context(cell, precision=bie.BIE_FP64, gmres_tol=1e-12, n_images=4)
+    sig, info = ctx.solve()
+    ou = obie.OperatorUtilde(oracle_suspension(cell), n_proxy=M_BOX, n_coll=M_COLL)
+    ref = ou.mu_eff_contour(sig.reshape(-1, 2))
+    got = ctx.mu_eff_contour(sig)
+    assert abs(got - ref) < 1e-10 * abs(ref)
+    _, _, mu_ps = ctx.velocities(sig)
+    assert abs(got - mu_ps) < 1e-9
+    if crossing:
+        from tests.conftest import oracle_operator
+        wall = oracle_operator(cell, use_close=False).mu_eff_wall(sig.reshape(-1, 2))
+        assert abs(wall - got) > 1e-2
+    ctx.close()
+
+
+def test_contour_mu_eff_needs_the_doubled_cell():
+    cell = _cell("crossing")
+    ctx = bie.Context(cell, precision=bie.BIE_FP64)
+    with pytest.raises(bie.BieError) as e:
+        ctx.mu_eff_contour(np.zeros(2 * ctx.N))
+    assert e.value.code == bie.BIE_EINVAL
+    ctx.close()
