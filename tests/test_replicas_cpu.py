@@ -1,7 +1,8 @@
-"""The multi-GPU path of bench.py is independent replicas (one per rank, no
-data-path collective): these CPU tests run it as two gloo ranks.  They check
-the whole-job aggregation (units summed over ranks, the slowest rank's time)
-and that the reference arm does its work on rank 0 only."""
+"""Whole-job aggregation of bench.py over ranks, as two gloo ranks on the
+CPU: the slowest rank's time, and the units summed over independent
+replicas or (the multi-GPU benchmark, which shards one cell by target) those
+of the one shared problem; and the reference arm works on rank 0 only.  The
+sharded solve's exchange itself is tested in test_shard_cpu.py."""
 import os
 import socket
 
@@ -25,9 +26,10 @@ def _rank(rank, world, port, out):
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
     units, ms = bench.whole_job(100.0 * (rank + 1), 10.0 + 5.0 * rank, dist, "cpu")
+    shared = bench.whole_job(300.0, 10.0 + 5.0 * rank, dist, "cpu", shared=True)
     dist.barrier()
     dist.destroy_process_group()
-    out[rank] = (units, ms)
+    out[rank] = (units, ms, shared)
 
 
 def test_whole_job_over_two_gloo_ranks():
@@ -42,7 +44,7 @@ def test_whole_job_over_two_gloo_ranks():
             p.join(120)
             assert p.exitcode == 0
         res = dict(out)
-    assert res[0] == res[1] == (300.0, 15.0)
+    assert res[0] == res[1] == (300.0, 15.0, (300.0, 15.0))
 
 
 def test_single_process_whole_job():
