@@ -83,7 +83,7 @@ def _solve_rank(rank, world, port, out):
     import torch.distributed as dist
     from paper_1912_04501_gb300 import bie as b, shard, workloads as w
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    cell = w.small_cell(n_bodies=6, nodes=(lambda a, c: 96 + int(160 * a)), seed=9, e2=(0.2, 1.0))
+    cell = w.small_cell(n_bodies=6, nodes=(lambda a, c: 96 + 2 * int(80 * a)), seed=9, e2=(0.2, 1.0))
     ctx = b.Context(cell, precision=b.BIE_MIXED)
     sh = shard.ShardedSolve(ctx, [bd["n"] for bd in cell["bodies"]], rank, world)
     sig, info = ctx.solve()
@@ -117,7 +117,7 @@ def test_sharded_solve_two_processes_one_gpu():
             p.join(300)
             assert p.exitcode == 0
         res = dict(out)
-    cell = workloads.small_cell(n_bodies=6, nodes=(lambda a, c: 96 + int(160 * a)), seed=9, e2=(0.2, 1.0))
+    cell = workloads.small_cell(n_bodies=6, nodes=(lambda a, c: 96 + 2 * int(80 * a)), seed=9, e2=(0.2, 1.0))
     ref = bie.Context(cell, precision=bie.BIE_MIXED)
     sig, info = ref.solve()
     mus, _ = ref.step(cell.get("dt", 1e-3), 2)
