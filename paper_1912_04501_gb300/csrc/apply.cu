@@ -1145,11 +1145,13 @@ __global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // Tile shape of the doubled-cell single-precision near sum: targets per
 // thread and resident CTAs per SM (compile-time overrides for sweeps).
+// Measured on GB300 (400-ellipse cell, per launch): 2/6 16.69 ms, 8/4 16.71,
+// 8/3 16.89, 4/5 17.15, 4/4 17.32, 4/6 17.32, 6/4 17.51, 2/8 18.41.
 #ifndef BIE_NEARU_TPT
-#define BIE_NEARU_TPT 4
+#define BIE_NEARU_TPT 2
 #endif
 #ifndef BIE_NEARU_CTAS
-#define BIE_NEARU_CTAS 5
+#define BIE_NEARU_CTAS 6
 #endif
 constexpr int kNearUTpt = BIE_NEARU_TPT, kNearUCtas = BIE_NEARU_CTAS;
 
