@@ -61,9 +61,16 @@ typedef struct {
     double center[2];
 } bie_lattice;
 
-/* One rigid body: an ellipse with semi-axes a = p[0], b = p[1] (shape 0; the
- * only shape of this version), centroid xc and angle theta, discretised by
- * n_nodes trapezoidal nodes (n_nodes even, 8 <= n_nodes <= 16384). */
+/* One rigid body with centre xc and angle theta, discretised by n_nodes
+ * trapezoidal nodes (n_nodes even, 8 <= n_nodes <= 16384), of one of two
+ * shapes, given in the body frame and rotated by theta:
+ *   shape 0, ellipse: (a cos t, b sin t), a = p[0], b = p[1];
+ *   shape 1, star (Sec. 8 Examples 4-5): r(t) (cos t, sin t) with
+ *            r(t) = r0 (1 + eps cos(k t)), r0 = p[0] > 0, 0 <= eps = p[1] < 1,
+ *            k = p[2] an integer in 1..64.
+ * xc is the reference point of the rigid motion (velocities are reported
+ * there); for ellipses and stars with k >= 2 it is the boundary's arc-length
+ * centroid (Sec. 2). */
 typedef struct {
     int32_t n_nodes;
     int32_t shape;

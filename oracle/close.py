@@ -49,10 +49,23 @@ def fine_factor(h, d):
 
 
 def closest_point(body, x, shift, t0, n_iter=8):
-    """Distance from x to the exact ellipse `body` translated by shift, and
+    """Distance from x to the exact curve of `body` translated by shift, and
     the local node spacing 2 pi |x'(t*)| / N_b there, by Newton's method on
     the stationarity condition (y(t) - x) . y'(t) = 0 started at t0 (the
     parameter of the nearest node); steps are capped at one node spacing."""
+    if body.get("shape", "ellipse") == "star":
+        dt_max = 2.0 * math.pi / body["n"]
+        t = t0
+        xs = np.asarray(x, dtype=np.float64) - np.asarray(shift, dtype=np.float64)
+        for _ in range(n_iter):
+            y, dy, ddy = geometry.curve_point(body, [t])
+            d = y[0] - xs
+            g = d @ dy[0]
+            gp = dy[0] @ dy[0] + d @ ddy[0]
+            step = g / gp if gp > 0 else math.copysign(dt_max, g)
+            t -= max(-dt_max, min(dt_max, step))
+        y, dy, _ = geometry.curve_point(body, [t])
+        return float(np.hypot(*(y[0] - xs))), 2.0 * math.pi * float(np.hypot(*dy[0])) / body["n"]
     a, b, th = body["a"], body["b"], body["theta"]
     c, s = math.cos(th), math.sin(th)
     px = x[0] - body["xc"][0] - shift[0]
@@ -71,14 +84,18 @@ def closest_point(body, x, shift, t0, n_iter=8):
 
 
 def fine_integral(body, sigma_b, x, nx, shift, rho):
-    """int over the exact ellipse `body` (translated by shift) of
+    """int over the exact curve of `body` (translated by shift) of
     G^t(x, y; nx) sigma^(y) ds_y, sigma^ the trigonometric interpolant of the
     body's nodal density sigma_b (n_b, 2), by the trapezoidal rule on
     rho * n_b points."""
     nb = sigma_b.shape[0]
     nf = rho * nb
     tf = 2.0 * np.pi * np.arange(nf) / nf
-    yf, speed = geometry.ellipse_point(body["a"], body["b"], body["xc"], body["theta"], tf)
+    if body.get("shape", "ellipse") == "star":
+        yf, dyf, _ = geometry.curve_point(body, tf)
+        speed = np.hypot(dyf[:, 0], dyf[:, 1])
+    else:
+        yf, speed = geometry.ellipse_point(body["a"], body["b"], body["xc"], body["theta"], tf)
     wf = (2.0 * np.pi / nf) * speed
     sf = trig_interp(sigma_b, nf)
     r = np.asarray(x)[None, :] - (yf + np.asarray(shift)[None, :])

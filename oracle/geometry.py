@@ -39,6 +39,59 @@ def ellipse_nodes(a, b, centre, theta, n):
     return dict(x=x, tau=tau, n=nrm, w=w, kappa=kappa, t=t)
 
 
+def star_radius(r0, eps, k, t):
+    """Polar radius r(t) = r0 (1 + eps cos(k t)) of a star-shaped body and its
+    first two derivatives in t (Sec. 8 Examples 4-5: x(t) = (r(t) cos t,
+    r(t) sin t) about the centre)."""
+    t = np.asarray(t, dtype=np.float64)
+    r = r0 * (1.0 + eps * np.cos(k * t))
+    dr = -r0 * eps * k * np.sin(k * t)
+    ddr = -r0 * eps * k * k * np.cos(k * t)
+    return r, dr, ddr
+
+
+def curve_point(body, t):
+    """Point, first and second derivative in t of a body's boundary
+    x(t) = x^c + R(theta) p(t): an ellipse p = (a cos t, b sin t), or a star
+    p = r(t) (cos t, sin t) (body["shape"] == "star": r0, eps, k).  Returns
+    three (len(t), 2) arrays."""
+    t = np.asarray(t, dtype=np.float64)
+    if body.get("shape", "ellipse") == "star":
+        r, dr, ddr = star_radius(body["r0"], body["eps"], body["k"], t)
+        c_, s_ = np.cos(t), np.sin(t)
+        p = np.stack([r * c_, r * s_], axis=1)
+        dp = np.stack([dr * c_ - r * s_, dr * s_ + r * c_], axis=1)
+        ddp = np.stack([ddr * c_ - 2 * dr * s_ - r * c_, ddr * s_ + 2 * dr * c_ - r * s_], axis=1)
+    else:
+        a, b = body["a"], body["b"]
+        p = np.stack([a * np.cos(t), b * np.sin(t)], axis=1)
+        dp = np.stack([-a * np.sin(t), b * np.cos(t)], axis=1)
+        ddp = -p
+    c, s = math.cos(body["theta"]), math.sin(body["theta"])
+    rot = np.array([[c, -s], [s, c]])
+    return np.asarray(body["xc"], dtype=np.float64)[None, :] + p @ rot.T, dp @ rot.T, ddp @ rot.T
+
+
+def body_nodes(body):
+    """Trapezoidal discretisation of any body (as ellipse_nodes)."""
+    n = body["n"]
+    t = 2.0 * np.pi * np.arange(n) / n
+    x, dx, ddx = curve_point(body, t)
+    speed = np.hypot(dx[:, 0], dx[:, 1])
+    tau = dx / speed[:, None]
+    nrm = np.stack([tau[:, 1], -tau[:, 0]], axis=1)
+    w = (2.0 * np.pi / n) * speed
+    kappa = (dx[:, 0] * ddx[:, 1] - dx[:, 1] * ddx[:, 0]) / speed**3
+    return dict(x=x, tau=tau, n=nrm, w=w, kappa=kappa, t=t)
+
+
+def body_radius(body):
+    """Largest distance from the centre to the boundary."""
+    if body.get("shape", "ellipse") == "star":
+        return body["r0"] * (1.0 + abs(body["eps"]))
+    return max(body["a"], body["b"])
+
+
 def ellipse_point(a, b, centre, theta, t):
     """Position and speed on the exact ellipse at parameter values t."""
     t = np.asarray(t, dtype=np.float64)
@@ -83,7 +136,10 @@ def wrap_into_cell(p, e1, e2, centre):
 class Suspension:
     """One unit cell: lattice, fluid, and a list of ellipses.
 
-    bodies: list of dicts with keys a, b, xc (2,), theta, n.
+    bodies: list of dicts with keys xc (2,), theta, n and the shape: a, b
+    (ellipse), or shape = "star" with r0, eps, k (r(t) = r0 (1 + eps cos kt)).
+    The centre xc is the reference point of the rigid motion (for an ellipse
+    and a star with k >= 2 also the boundary's arc-length centroid).
     """
 
     def __init__(self, e1, e2, centre, mu, gamma, bodies):
@@ -99,7 +155,8 @@ class Suspension:
         xs, taus, ns, ws, ks, ts, owner = [], [], [], [], [], [], []
         offsets = [0]
         for i, bd in enumerate(self.bodies):
-            g = ellipse_nodes(bd["a"], bd["b"], bd["xc"], bd["theta"], bd["n"])
+            g = (body_nodes(bd) if bd.get("shape", "ellipse") == "star"
+                 else ellipse_nodes(bd["a"], bd["b"], bd["xc"], bd["theta"], bd["n"]))
             xs.append(g["x"])
             taus.append(g["tau"])
             ns.append(g["n"])

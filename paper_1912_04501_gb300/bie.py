@@ -212,8 +212,12 @@ class Context:
         bodies = (Body * len(all_bodies))()
         for b, bd in zip(bodies, all_bodies):
             b.n_nodes = int(bd["n"])
-            b.shape = 0
-            b.p = (c_double * 4)(bd["a"], bd["b"], 0.0, 0.0)
+            if bd.get("shape", "ellipse") == "star":
+                b.shape = 1
+                b.p = (c_double * 4)(bd["r0"], bd["eps"], float(bd["k"]), 0.0)
+            else:
+                b.shape = 0
+                b.p = (c_double * 4)(bd["a"], bd["b"], 0.0, 0.0)
             b.xc = (c_double * 2)(*bd["xc"])
             b.theta = bd["theta"]
         h = c_void_p()

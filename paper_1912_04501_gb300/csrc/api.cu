@@ -34,7 +34,7 @@ static void free_all(bie_ctx* c) {
     free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
                     c->tgt32, c->posdf, c->xw, c->yw, c->imc, c->bimg, c->ws.src32n, c->ws.src64u, c->next.yp,
-                    c->next.ypf, c->glc, c->contour_part,
+                    c->next.ypf, c->glc, c->contour_part, c->bshape,
                     c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
@@ -361,18 +361,25 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         cl.node_off = (int)N;
         for (int j = 0; j < in.n_bodies; ++j, ++nb) {
             const bie_body& bd = bodies[nb];
-            if (bd.shape != 0) return bad("only shape 0 (ellipse) is supported");
+            if (bd.shape != 0 && bd.shape != 1) return bad("shape must be 0 (ellipse) or 1 (star)");
             if (bd.n_nodes < 8 || bd.n_nodes > kMaxBodyNodes || (bd.n_nodes & 1))
                 return bad("n_nodes must be even, 8.." + std::to_string(kMaxBodyNodes));
-            if (!(bd.p[0] > 0) || !(bd.p[1] > 0)) return bad("ellipse semi-axes must be positive");
+            if (bd.shape == 0 && (!(bd.p[0] > 0) || !(bd.p[1] > 0))) return bad("ellipse semi-axes must be positive");
+            if (bd.shape == 1 && (!(bd.p[0] > 0) || !(bd.p[1] >= 0 && bd.p[1] < 1) || !(bd.p[2] >= 1) ||
+                                  bd.p[2] > 64 || bd.p[2] != std::floor(bd.p[2])))
+                return bad("star: r0 > 0, 0 <= eps < 1 and an integer k in 1..64");
             if (!std::isfinite(bd.xc[0]) || !std::isfinite(bd.xc[1]) || !std::isfinite(bd.theta))
                 return bad("non-finite body position");
             c->n_nodes.push_back(bd.n_nodes);
             c->offsets.push_back((int)N);
             for (int q = 0; q < 8; ++q) c->body_host.push_back(0.0);
             double* h = &c->body_host[8 * (size_t)nb];
-            h[0] = bd.p[0];
-            h[1] = bd.p[1];
+            // ellipse: the semi-axes; star: its bounding radius twice (the
+            // kernels that only need a size read max(h[0], h[1]))
+            h[0] = bd.shape == 1 ? bd.p[0] * (1.0 + bd.p[1]) : bd.p[0];
+            h[1] = bd.shape == 1 ? bd.p[0] * (1.0 + bd.p[1]) : bd.p[1];
+            c->bshape_host.push_back(bd.shape);
+            for (int q = 0; q < 3; ++q) c->bshape_host.push_back(bd.shape == 1 ? bd.p[q] : (q < 2 ? bd.p[q] : 0.0));
             h[2] = bd.xc[0];
             h[3] = bd.xc[1];
             h[4] = bd.theta;
@@ -429,6 +436,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->yw, n);
     rc = rc ? rc : dalloc(c, &c->imc, n);
     rc = rc ? rc : dalloc(c, &c->bimg, nbs);
+    rc = rc ? rc : dalloc(c, &c->bshape, 4 * nbs);
     rc = rc ? rc : dalloc(c, &c->gl_s, m);
     rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);
@@ -544,6 +552,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : up(c->node_cell, node_cell.data(), n * sizeof(int));
     rc = rc ? rc : up(c->body_cell, body_cell.data(), c->nb * sizeof(int));
     rc = rc ? rc : up(c->body, c->body_host.data(), c->body_host.size() * sizeof(double));
+    rc = rc ? rc : up(c->bshape, c->bshape_host.data(), c->bshape_host.size() * sizeof(double));
     rc = rc ? rc : up(c->gl_s, c->gl_host.data(), m * sizeof(double));
     // the 3 x 3 periodizer's proxy circle does not move with the lattice: both
     // fits hold it (the doubled cell's wall proxies are placed with each fit)

@@ -213,6 +213,7 @@ struct bie_ctx {
     int ncell = 0, nb = 0, N = 0, M = 0, m = 0;
     std::vector<int> n_nodes, offsets;     // per body
     std::vector<double> body_host;         // nb x 8 (a, b, xc, yc, theta, n, off, h)
+    std::vector<double> bshape_host;       // nb x 4 (shape, p0, p1, p2)
     std::vector<bie::Cell> cells_h;        // host mirror of the cell table
     std::vector<double> e2_0;              // 2 x ncell lattice vectors e2 at t = 0
     bie::Cell* cells = nullptr;            // device cell table
@@ -230,6 +231,7 @@ struct bie_ctx {
     double* yw = nullptr;
     int* imc = nullptr;         // N: image code (img_m0, img_n0, img_wrap), n_images 4
     int4* bimg = nullptr;       // nb: (min m0, max m0, min n0, max n0) over the body's nodes, n_images 4
+    double* bshape = nullptr;   // nb x 4: (shape, p0, p1, p2) -- 0 ellipse (a, b), 1 star (r0, eps, k)
     double* glc = nullptr;      // contour mu_eff: Gauss-Legendre nodes and weights on (-1/2, 1/2) (on demand)
     double* contour_part = nullptr;  // its per-split wall sums (on demand)
     size_t contour_part_n = 0;
@@ -453,6 +455,24 @@ __device__ __forceinline__ float pair32(float dx, float dy, float nx, float ny, 
     const float rq = fmaf(dy, qy, dx * qx);
     const float inv = rcp_approx(r2);
     return (rn * inv) * (rq * inv);
+}
+
+// Star-shaped body (bie_body shape 1): in its own frame the boundary is
+// p(t) = r(t) (cos t, sin t), r(t) = r0 (1 + eps cos kt) (Sec. 8 Examples 4-5);
+// p, p' and p'' at parameter t.  shp = (1, r0, eps, k).
+__device__ inline void star_curve(const double* shp, double t, double& px, double& py, double& dpx, double& dpy,
+                                  double& ddpx, double& ddpy) {
+    const double r0 = shp[1], eps = shp[2], k = shp[3];
+    double st, ct, sk, ck;
+    sincos(t, &st, &ct);
+    sincos(k * t, &sk, &ck);
+    const double r = r0 * (1.0 + eps * ck), dr = -r0 * eps * k * sk, ddr = -r0 * eps * k * k * ck;
+    px = r * ct;
+    py = r * st;
+    dpx = dr * ct - r * st;
+    dpy = dr * st + r * ct;
+    ddpx = ddr * ct - 2.0 * dr * st - r * ct;
+    ddpy = ddr * st + 2.0 * dr * ct - r * st;
 }
 
 __host__ __device__ inline void wall_normals(const double* e1, const double* e2, double* nl, double* nd) {

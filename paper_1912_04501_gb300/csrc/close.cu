@@ -57,7 +57,8 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
                                int* __restrict__ count, int* __restrict__ overflow,
                                unsigned long long* __restrict__ gap_min, int* __restrict__ rho_max,
                                float* __restrict__ dmin, float2* __restrict__ ddir, const int* __restrict__ imc,
-                               const int4* __restrict__ bimg, int* __restrict__ gflag) {
+                               const int4* __restrict__ bimg, int* __restrict__ gflag,
+                               const double* __restrict__ bshape) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Cell& sh = cells[node_cell[i]];
@@ -89,7 +90,32 @@ __global__ void k_close_detect(const double* __restrict__ x, const double* __res
             // distance to the exact curve and local node spacing at the closest
             // point: Newton on (y(t) - x) . y'(t) = 0 from the nearest node
             double dcur, hloc;
-            {
+            const double* shp = bshape + 4 * b;
+            if (shp[0] == 1.0) {
+                // star: Newton on g(t) = (p(t) - u) . p'(t), g' = |p'|^2 + (p - u) . p''
+                double st, ct;
+                sincos(bd[4], &st, &ct);
+                const double px = X - cx, py = Y - cy;
+                const double u = ct * px + st * py, v = -st * px + ct * py;
+                const double dtm = 2.0 * kPi / n;
+                double t = dtm * kbest, qx, qy, dqx, dqy, ddqx, ddqy;
+                for (int it = 0; it < 8; ++it) {
+                    star_curve(shp, t, qx, qy, dqx, dqy, ddqx, ddqy);
+                    const double g = (qx - u) * dqx + (qy - v) * dqy;
+                    const double gp = dqx * dqx + dqy * dqy + (qx - u) * ddqx + (qy - v) * ddqy;
+                    const double step = gp > 0 ? g / gp : copysign(dtm, g);
+                    t -= fmax(-dtm, fmin(dtm, step));
+                }
+                star_curve(shp, t, qx, qy, dqx, dqy, ddqx, ddqy);
+                dcur = sqrt((qx - u) * (qx - u) + (qy - v) * (qy - v));
+                hloc = 2.0 * kPi * sqrt(dqx * dqx + dqy * dqy) / n;
+                if (dcur < dbest && dcur > 0) {
+                    const double ex = (qx - u) / dcur, ey = (qy - v) / dcur;
+                    dbest = dcur;
+                    dirx = ct * ex - st * ey;
+                    diry = st * ex + ct * ey;
+                }
+            } else {
                 double a = bd[0], b2 = bd[1], st, ct;
                 sincos(bd[4], &st, &ct);
                 double px = X - cx, py = Y - cy;
@@ -236,7 +262,7 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
                const double* __restrict__ w, const double* __restrict__ body,
                const int* __restrict__ node_cell, const Cell* __restrict__ cells,
                const double* __restrict__ dtab, const long long* __restrict__ dtab_off,
-               double* __restrict__ blocks, float* __restrict__ blocks32) {
+               double* __restrict__ blocks, float* __restrict__ blocks32, const double* __restrict__ bshape) {
     extern __shared__ double sm[];
     double* sa = sm;
     double* sb = sm + kCloseChunk;
@@ -260,14 +286,19 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
     for (int f0 = 0; f0 < nf; f0 += kCloseChunk) {
         int cnt = min(kCloseChunk, nf - f0);
         __syncthreads();
+        const double* shp = bshape + 4 * b;
         for (int u = threadIdx.x; u < cnt; u += blockDim.x) {
             int f = f0 + u;
             double t = (2.0 * kPi * f) / nf;
             double s, c;
             sincos(t, &s, &c);
             double px = a * c, py = bb * s;
-            double yx = xc + (ct * px - st * py), yy = yc + (st * px + ct * py);
             double dpx = -a * s, dpy = bb * c;
+            if (shp[0] == 1.0) {
+                double ddpx, ddpy;
+                star_curve(shp, t, px, py, dpx, dpy, ddpx, ddpy);
+            }
+            double yx = xc + (ct * px - st * py), yy = yc + (st * px + ct * py);
             double dx = ct * dpx - st * dpy, dy = st * dpx + ct * dpy;
             double wf = (2.0 * kPi / nf) * sqrt(dx * dx + dy * dy);
             double rx = X - yx, ry = Y - yy;
@@ -407,7 +438,7 @@ int build_close(bie_ctx* c) {
                                                          c->opts.close_factor, gap_lim, kmax, c->cl.slots,
                                                          c->cl.count, c->cl.flags + 2, gap_min, c->cl.flags + 6,
                                                          c->cl.dmin, c->cl.ddir, c->utilde ? c->imc : nullptr,
-                                                         c->bimg, c->cl.flags + 7);
+                                                         c->bimg, c->cl.flags + 7, c->bshape);
     BIE_LAUNCH(c, "k_close_detect");
     int h[8];
     long long need_doubles = 0;
@@ -465,7 +496,7 @@ int build_close(bie_ctx* c) {
     dim3 grid(h[0], (maxn + kCloseAccNodes - 1) / kCloseAccNodes);
     k_close_blocks<<<grid, 256, shm, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx, c->ny, c->w,
                                                   c->body, c->node_cell, c->cells, c->cl.dtab, c->cl.dtab_off,
-                                                  c->cl.blocks, c->cl.blocks32);
+                                                  c->cl.blocks, c->cl.blocks32, c->bshape);
     BIE_LAUNCH(c, "k_close_blocks");
     return BIE_OK;
 }

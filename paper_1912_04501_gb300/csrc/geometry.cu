@@ -30,7 +30,7 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
                            double* __restrict__ ny, double* __restrict__ w, double* __restrict__ kap,
                            float4* __restrict__ tgt32, float4* __restrict__ posdf, int utilde,
                            double* __restrict__ xw, double* __restrict__ yw, int* __restrict__ imc,
-                           int* __restrict__ gflag) {
+                           int* __restrict__ gflag, const double* __restrict__ bshape) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double* bd = body + 8 * owner[i];
@@ -42,10 +42,12 @@ __global__ void k_geometry(const double* __restrict__ body, const int* __restric
     double st, ct, s, c;
     sincos(t, &st, &ct);
     sincos(th, &s, &c);
-    double px = a * ct, py = b * st, dpx = -a * st, dpy = b * ct;
+    double px = a * ct, py = b * st, dpx = -a * st, dpy = b * ct, ddpx = -px, ddpy = -py;
+    const double* shp = bshape + 4 * owner[i];
+    if (shp[0] == 1.0) star_curve(shp, t, px, py, dpx, dpy, ddpx, ddpy);
     double X = xc + (c * px - s * py), Y = yc + (s * px + c * py);
     double dX = c * dpx - s * dpy, dY = s * dpx + c * dpy;
-    double ddX = -(c * px - s * py), ddY = -(s * px + c * py);
+    double ddX = c * ddpx - s * ddpy, ddY = s * ddpx + c * ddpy;
     double sp = sqrt(dX * dX + dY * dY);
     double tx = dX / sp, ty = dY / sp;
     x[i] = X;
@@ -319,7 +321,7 @@ int build_geometry(bie_ctx* c) {
     BIE_CUDA(c, cudaMemsetAsync(gflag, 0, sizeof(int), c->stream));
     k_geometry<<<gs, bs, 0, c->stream>>>(c->body, c->owner, c->node_cell, c->cells, c->N, c->x, c->y, c->nx, c->ny,
                                         c->w, c->kap, c->tgt32, c->posdf, c->utilde ? 1 : 0, c->xw, c->yw, c->imc,
-                                        gflag);
+                                        gflag, c->bshape);
     BIE_LAUNCH(c, "k_geometry");
     if (c->utilde) {
         k_body_img<<<c->nb, 128, 0, c->stream>>>(c->imc, c->body, c->bimg);

@@ -271,3 +271,23 @@ def config5(seed=5):
     cell = random_cell(400, 0.35, (1.0, 3.0), 2e-3, 256, seed, max_tries=2000000)
     cell.update(solver=dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10), dt=1e-3, steps=50)
     return cell
+
+
+# Arms of the star shapes of Sec. 8 Examples 4-5.  The printed radius
+# r = 0.25 (1 + 0.5 cos theta) has a single lobe (the multiplier of theta is
+# lost in the text); four arms keep both examples' initial stars apart
+# (three, five and six arms overlap the second example's rotated star).
+STAR_ARMS = 4
+
+
+def stars(example=4, n=2500, arms=STAR_ARMS):
+    """Two star-shaped bodies r(t) = r0 (1 + 0.5 cos(arms t)) in the unit
+    square cell, centred at (0.25, 0.25) and (0.75, 0.75), mu = gamma = 1,
+    forward Euler with dt = 5e-4 (Sec. 8 Example 4: r0 = 0.25; Example 5:
+    r0 = 0.275 and the second star turned by pi/4), n nodes per body."""
+    r0 = 0.25 if example == 4 else 0.275
+    th2 = 0.0 if example == 4 else np.pi / 4
+    bodies = [dict(shape="star", r0=r0, eps=0.5, k=arms, xc=[0.25, 0.25], theta=0.0, n=n),
+              dict(shape="star", r0=r0, eps=0.5, k=arms, xc=[0.75, 0.75], theta=th2, n=n)]
+    return dict(e1=[1.0, 0.0], e2=[0.0, 1.0], centre=[0.5, 0.5], mu=1.0, gamma=1.0, bodies=bodies,
+                solver=dict(n_proxy=64, proxy_radius=1.5, n_coll=32, gmres_tol=1e-10), dt=5e-4, steps=920)
