@@ -47,7 +47,16 @@ WORKLOADS = {
     "config5": "400 ellipses/cell, phi 0.35, AR U[1,3], gap>=2e-3, 256 nodes/body (N=102400), dt 1e-3",
     "config2": "25 ellipses/cell, phi 0.3, AR U[1,3], gap>=1e-2, 256 nodes/body (N=6400), dt 1e-3",
 }
-FLOPS_PER_PAIR = 18.0  # 13 FP32 operations (5 of them FMAs) + 1 reciprocal per near pair
+# algorithmic flops of one near pair (the double-layer kernel of Eq. 3.1): the
+# difference r (2), |r|^2 (3), r.n and r.q (3 + 3), their product over |r|^4
+# (3, one reciprocal of |r|^2 not counted) and the accumulation of c r (4)
+FLOPS_PER_PAIR = 18.0
+# the same with the three images of a lattice row sharing r_y, r_y^2, r_y n_y
+# and r_y q_y (4 flops per row of 3 pairs): the row-shared kernel k_near32r
+FLOPS_PER_PAIR_ROWS = 14.0 + 4.0 / 3.0
+# FP32 instructions per pair of k_near32r (an FMA counts once): the FP32
+# pipe's issue limit is half the FMA flop peak in these units
+OPS_PER_PAIR_ROWS = 9.0 + 4.0 / 3.0
 
 
 def parse():
@@ -352,9 +361,13 @@ def main():
     # (replaying captured graphs measured no faster)
     ctx = bie.Context(cell, precision=bie.BIE_MIXED, device=local, warm_start=mode, autotune=0, graph=0, **img_opts)
     shape, _ = ctx.near_shape()
-    near32 = "k_near32x2" if bie.NEAR32_SHAPES[shape][0] else "k_near32"
+    # the packed shapes share each lattice row's r_y when e1 = (L1, 0), as in
+    # every sheared cell here
+    rows = bool(bie.NEAR32_SHAPES[shape][0]) and cell["e1"][1] == 0.0 and args.images == 9
+    near32 = "k_near32r" if rows else ("k_near32x2" if bie.NEAR32_SHAPES[shape][0] else "k_near32")
     if args.images == 4:
         near32 = "k_near32u"
+    fpp32 = FLOPS_PER_PAIR_ROWS if rows else FLOPS_PER_PAIR
     ctx.set_stream(stream.cuda_stream)
     if net is not None:
         net.set_stream(stream.cuda_stream)
@@ -572,14 +585,18 @@ def main():
     ms32 = prof["near32_ms"] / max(1, n32)
     msdf = prof["neardf_ms"] / max(1, ndf)
     roof32 = {"kernel": near32, "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
-              "achieved": FLOPS_PER_PAIR * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
-              "launch_ms": ms32, "launches": n32, "device_ms_total": prof["near32_ms"],
+              "achieved": fpp32 * pairs_per_apply / (ms32 / 1e3) / 1e12 if n32 else None,
+              "flops_per_pair": fpp32, "launch_ms": ms32, "launches": n32, "device_ms_total": prof["near32_ms"],
               "peak_source": fp32_src, "traffic": profiled_traffic(near32, name)}
+    if rows and n32:
+        # the same launches as a fraction of the FP32 pipe's instruction rate
+        roof32["fp32_issue_frac"] = OPS_PER_PAIR_ROWS * pairs_per_apply / (ms32 / 1e3) / 1e12 / (fp32_peak / 2)
     # double-float pairs run on the FP32 pipe: measured against the FP32 peak,
-    # counting the same 18 algorithmic flops per pair (the extra ~120 FP32
-    # instructions per pair are the price of the 48-bit arithmetic)
+    # counting the same algorithmic flops per pair as the single-precision
+    # kernel (the extra ~100 FP32 instructions per pair are the price of the
+    # 48-bit arithmetic)
     roofdf = {"kernel": "k_near_df", "bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
-              "achieved": FLOPS_PER_PAIR * pairs_per_apply / (msdf / 1e3) / 1e12 if ndf else None,
+              "achieved": fpp32 * pairs_per_apply / (msdf / 1e3) / 1e12 if ndf else None,
               "launch_ms": msdf, "launches": ndf, "device_ms_total": prof["neardf_ms"],
               "peak_source": fp32_src, "traffic": profiled_traffic("k_near_df", name)}
     roof64 = {"kernel": "k_near64 (plain FP64 operator, whole application)", "bound": "alu", "unit": "TFLOP/s",

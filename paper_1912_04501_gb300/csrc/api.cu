@@ -34,7 +34,7 @@ static void free_all(bie_ctx* c) {
     free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
                     c->tgt32, c->posdf, c->xw, c->yw, c->imc, c->bimg, c->ws.src32n, c->ws.src64u, c->next.yp,
-                    c->next.ypf, c->glc, c->contour_part, c->bshape,
+                    c->next.ypf, c->glc, c->contour_part, c->bshape, c->near_ctr,
                     c->gl_s, c->A, c->beta, c->P, c->wall, c->e2d, c->next.A, c->next.beta, c->next.P,
                     c->next.wall, c->next.e2, c->yp, c->ypf, c->scal, c->ws.sigma, c->ws.out, c->ws.src64, c->ws.src32,
                     c->ws.srcdf, c->ws.bodyF, c->ws.part, c->ws.gpart, c->ws.gt, c->ws.dticket, c->sv.ticket, c->ws.xi, c->ws.xif, c->ws.T, c->ws.vpart, c->sv.V,
@@ -437,6 +437,7 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->imc, n);
     rc = rc ? rc : dalloc(c, &c->bimg, nbs);
     rc = rc ? rc : dalloc(c, &c->bshape, 4 * nbs);
+    rc = rc ? rc : dalloc(c, &c->near_ctr, 1);
     rc = rc ? rc : dalloc(c, &c->gl_s, m);
     rc = rc ? rc : dalloc(c, &c->A, nc * R * Cc);
     rc = rc ? rc : dalloc(c, &c->beta, nc * 2 * Cc);

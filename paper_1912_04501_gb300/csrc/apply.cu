@@ -63,8 +63,8 @@ struct ItemRange {
 
 // srcmul: source records per node (1: nodes; 4: the doubled-cell image records).
 __device__ __forceinline__ bool item_range(const int4* items, const Cell* cells, int prec, int tile, ItemRange& r,
-                                           int srcmul = 1) {
-    const int4 it = items[blockIdx.x];
+                                           int srcmul = 1, int item = -1) {
+    const int4 it = items[item < 0 ? (int)blockIdx.x : item];
     const Cell& cl = cells[it.x];
     if (!cl.active) return false;
     const int sp = cl.splits[prec];
@@ -222,8 +222,8 @@ k_near32x2(const int4* __restrict__ items, const Cell* __restrict__ cells, const
                     const f32x2 dx = sub2(px[t][p], sx);
                     const f32x2 dy = sub2(py[t][p], sy);
                     const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
-                    const f32x2 rn = fma2(dy, ny2[t], mul2(dx, nx2[t]));
-                    const f32x2 rq = fma2(dy, qy, mul2(dx, qx));
+                    const f32x2 rn = fma2(dx, nx2[t], mul2(dy, ny2[t]));
+                    const f32x2 rq = fma2(dx, qx, mul2(dy, qy));
                     float ra, rb;
                     upk2(r2, ra, rb);
                     const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
@@ -267,6 +267,150 @@ k_near32x2(const int4* __restrict__ items, const Cell* __restrict__ cells, const
                 part[rg.out + i] = make_float2(c * ((a0 + a1) + ax8[t]), c * ((b0 + b1) + ay8[t]));
             }
         }
+    }
+}
+
+// The same sum for lattices with e1 = (L1, 0), the time-stepping case
+// (Sec. 7): the three images of a lattice row share dy, and with it the
+// y-parts of r^2, r.n and r.q (pair32's order), which leaves 9 FP32
+// operations per pair and 4 per row instead of 13 per pair.  Rows n = -1
+// and n = 0 share the packed f32x2 instructions (one row per half), row
+// n = +1 runs scalar; every term is bit for bit pair32's.
+template <int TPT, bool COMP>
+__device__ __forceinline__ void near32r_item(int item, const int4* __restrict__ items, const Cell* __restrict__ cells,
+                                             const float4* __restrict__ tgt, const float4* __restrict__ src,
+                                             float2* __restrict__ part) {
+    __shared__ float4 s_src[kNearTile];
+    ItemRange rg;
+    if (!item_range(items, cells, 0, kNearThreads * TPT, rg, 1, item)) return;
+    const Cell& cl = cells[rg.c];
+    // per target: packed x for the three columns (halves: rows -1, 0), packed
+    // y of the two rows; scalar x of row +1's columns and its y
+    f32x2 px[TPT][3], py[TPT], nx2[TPT], ny2[TPT], ax[TPT], ay[TPT];
+    float px8[TPT][3], py8[TPT], nxv[TPT], nyv[TPT], ax8[TPT], ay8[TPT];
+    float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
+    const f32x2 eps = pk2(1e-30f, 1e-30f), zero = pk2(0.f, 0.f);
+    const int tbase = rg.i0 + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        const float4 tv = i < rg.i1 ? tgt[i] : make_float4(1e4f, 1e4f, 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            px[t][m] = pk2(tv.x - cl.sxf[m], tv.x - cl.sxf[3 + m]);
+            px8[t][m] = tv.x - cl.sxf[6 + m];
+        }
+        py[t] = pk2(tv.y - cl.syf[0], tv.y - cl.syf[3]);
+        py8[t] = tv.y - cl.syf[6];
+        nxv[t] = tv.z;
+        nyv[t] = tv.w;
+        nx2[t] = pk2(tv.z, tv.z);
+        ny2[t] = pk2(tv.w, tv.w);
+        ax[t] = ay[t] = zero;
+        ax8[t] = ay8[t] = 0.f;
+        hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
+    }
+    for (int jt = rg.j0; jt < rg.j1; jt += kNearTile) {
+        const int cnt = min(kNearTile, rg.j1 - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < cnt; ++k) {
+            const float4 s = s_src[k];
+            const f32x2 sx = pk2(s.x, s.x), sy = pk2(s.y, s.y), qx = pk2(s.z, s.z), qy = pk2(s.w, s.w);
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const f32x2 dy = sub2(py[t], sy);
+                const f32x2 dy2 = fma2(dy, dy, eps);
+                const f32x2 dyn = mul2(dy, ny2[t]);
+                const f32x2 dyq = mul2(dy, qy);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const f32x2 dx = sub2(px[t][m], sx);
+                    const f32x2 r2 = fma2(dx, dx, dy2);
+                    const f32x2 rn = fma2(dx, nx2[t], dyn);
+                    const f32x2 rq = fma2(dx, qx, dyq);
+                    float ra, rb;
+                    upk2(r2, ra, rb);
+                    const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
+                    const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
+                    ax[t] = fma2(cc, dx, ax[t]);
+                    ay[t] = fma2(cc, dy, ay[t]);
+                }
+                const float ey = py8[t] - s.y;
+                const float ey2 = fmaf(ey, ey, 1e-30f);
+                const float eyn = ey * nyv[t];
+                const float eyq = ey * s.w;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float dx = px8[t][m] - s.x;
+                    const float r2 = fmaf(dx, dx, ey2);
+                    const float rn = fmaf(dx, nxv[t], eyn);
+                    const float rq = fmaf(dx, s.z, eyq);
+                    const float inv = rcp_approx(r2);
+                    const float cc = (rn * inv) * (rq * inv);
+                    ax8[t] = fmaf(cc, dx, ax8[t]);
+                    ay8[t] = fmaf(cc, ey, ay8[t]);
+                }
+            }
+        }
+        if constexpr (COMP) {
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float a0, a1, b0, b1, e;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                two_sum(hx[t], (a0 + a1) + ax8[t], hx[t], e);
+                lx[t] += e;
+                two_sum(hy[t], (b0 + b1) + ay8[t], hy[t], e);
+                ly[t] += e;
+                ax[t] = ay[t] = zero;
+                ax8[t] = ay8[t] = 0.f;
+            }
+        }
+    }
+    const float c = (float)(-1.0 / kPi);
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int i = tbase + t * kNearThreads;
+        if (i < rg.i1) {
+            if constexpr (COMP) {
+                part[rg.out + i] = make_float2(c * (hx[t] + lx[t]), c * (hy[t] + ly[t]));
+            } else {
+                float a0, a1, b0, b1;
+                upk2(ax[t], a0, a1);
+                upk2(ay[t], b0, b1);
+                part[rg.out + i] = make_float2(c * ((a0 + a1) + ax8[t]), c * ((b0 + b1) + ay8[t]));
+            }
+        }
+    }
+}
+
+// One work item per CTA.
+template <int TPT, bool COMP, int MINB>
+__global__ void __launch_bounds__(kNearThreads, MINB)
+k_near32r(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
+          const float4* __restrict__ src, float2* __restrict__ part) {
+    near32r_item<TPT, COMP>(blockIdx.x, items, cells, tgt, src, part);
+}
+
+// Persistent form for batches of uneven cells: a grid of the resident CTA
+// slots takes the work items (longest first) from a queue counter, *ctr = 0
+// at launch; no CTA ever waits on another.  Each item's partial sums are
+// those of k_near32r bit for bit.
+template <int TPT, bool COMP, int MINB>
+__global__ void __launch_bounds__(kNearThreads, MINB)
+k_near32r_queue(const int4* __restrict__ items, int count, int* __restrict__ ctr, const Cell* __restrict__ cells,
+                const float4* __restrict__ tgt, const float4* __restrict__ src, float2* __restrict__ part) {
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous item
+        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= count) return;
+        near32r_item<TPT, COMP>(item, items, cells, tgt, src, part);
     }
 }
 
@@ -349,24 +493,39 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
 }
 
 
-// One double-float pair of the near sum: target p = (pxh + pxl, pyh + pyl)
-// with normal n, source record q; the term c r, c = (r.n / r^2)(r.q / r^2),
-// r = p - y, is added to the tile accumulators (TwoSum hi, float error).
-__device__ __forceinline__ void pair_df(float pxh, float pxl, float pyh, float pyl, float nxh, float nxl, float nyh,
-                                        float nyl, const SrcDF& q, float& axh, float& axe, float& ayh, float& aye) {
-    float rxh, rxl, ryh, ryl, e;
+// The y-parts of a double-float pair, shared by every image with the same
+// r_y: r_y itself, its square (b + eb) and its products with n_y and q_y.
+struct DFy {
+    float ryh, ryl, b, eb, pn, en, pq, eq;
+};
+
+__device__ __forceinline__ DFy pair_df_y(float pyh, float pyl, float nyh, float nyl, const SrcDF& q) {
+    DFy y;
+    df_diff(pyh, pyl, q.yh, q.yl, y.ryh, y.ryl);
+    y.b = y.ryh * y.ryh;
+    y.eb = fmaf(y.ryh, y.ryh, -y.b);
+    y.eb = fmaf(y.ryh, y.ryl + y.ryl, y.eb);
+    df_mul(y.ryh, y.ryl, nyh, nyl, y.pn, y.en);
+    df_mul(y.ryh, y.ryl, q.qyh, q.qyl, y.pq, y.eq);
+    return y;
+}
+
+// One double-float pair of the near sum from its y-parts: target
+// x = pxh + pxl with normal x-component nx, source record q; the term c r,
+// c = (r.n / r^2)(r.q / r^2), r = p - y, is added to the tile accumulators
+// (TwoSum hi, float error).
+__device__ __forceinline__ void pair_df_x(float pxh, float pxl, float nxh, float nxl, const DFy& y, const SrcDF& q,
+                                          float& axh, float& axe, float& ayh, float& aye) {
+    float rxh, rxl, e;
+    const float ryh = y.ryh, ryl = y.ryl;
     df_diff(pxh, pxl, q.xh, q.xl, rxh, rxl);
-    df_diff(pyh, pyl, q.yh, q.yl, ryh, ryl);
     // r^2 (the 1e-30 floor absorbs the zero-distance self pair)
-    float a, ea, b, eb, r2h, r2l;
+    float a, ea, r2h, r2l;
     a = rxh * rxh;
     ea = fmaf(rxh, rxh, -a);
     ea = fmaf(rxh, rxl + rxl, ea);
-    b = ryh * ryh;
-    eb = fmaf(ryh, ryh, -b);
-    eb = fmaf(ryh, ryl + ryl, eb);
-    two_sum(a, b, r2h, e);
-    r2l = e + ea + eb;
+    two_sum(a, y.b, r2h, e);
+    r2l = e + ea + y.eb;
     r2h += 1e-30f;
     // 1 / r^2
     const float ih = rcp_approx(r2h);
@@ -374,16 +533,14 @@ __device__ __forceinline__ void pair_df(float pxh, float pxl, float pyh, float p
     res = fmaf(-r2l, ih, res);
     const float il = ih * res;
     // r . n and r . q
-    float p1, e1, p2, e2, rnh, rnl, rqh, rql;
+    float p1, e1, rnh, rnl, rqh, rql;
     df_mul(rxh, rxl, nxh, nxl, p1, e1);
-    df_mul(ryh, ryl, nyh, nyl, p2, e2);
-    two_sum(p1, p2, rnh, e);
-    rnl = e + e1 + e2;
+    two_sum(p1, y.pn, rnh, e);
+    rnl = e + e1 + y.en;
     fast2(rnh, rnl);  // r.n may cancel: renormalise before multiplying
     df_mul(rxh, rxl, q.qxh, q.qxl, p1, e1);
-    df_mul(ryh, ryl, q.qyh, q.qyl, p2, e2);
-    two_sum(p1, p2, rqh, e);
-    rql = e + e1 + e2;
+    two_sum(p1, y.pq, rqh, e);
+    rql = e + e1 + y.eq;
     fast2(rqh, rql);
     // c = (r.n / r^2) (r.q / r^2), term = c r
     float uh, ul, vh, vl, ch, cl2, th, tl;
@@ -396,6 +553,13 @@ __device__ __forceinline__ void pair_df(float pxh, float pxl, float pyh, float p
     df_mul(ch, cl2, ryh, ryl, th, tl);
     two_sum(ayh, th, ayh, e);
     aye += e + tl;
+}
+
+// One double-float pair with its own y-parts.
+__device__ __forceinline__ void pair_df(float pxh, float pxl, float pyh, float pyl, float nxh, float nxl, float nyh,
+                                        float nyl, const SrcDF& q, float& axh, float& axe, float& ayh, float& aye) {
+    const DFy y = pair_df_y(pyh, pyl, nyh, nyl, q);
+    pair_df_x(pxh, pxl, nxh, nxl, y, q, axh, axe, ayh, aye);
 }
 
 // a1 in one pass, one CTA per body: q = sigma w packed into whichever source
@@ -451,6 +615,7 @@ k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
     ItemRange rg;
     if (!item_range(items, cells, 2, kNearThreads, rg)) return;
     const Cell& cl = cells[rg.c];
+    const bool rows = cl.e1[1] == 0.0;
     const int i = rg.i0 + threadIdx.x;
     double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
     if (i < rg.i1) {
@@ -479,9 +644,20 @@ k_near_df(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
             const SrcDF q = s_src[k];
+            if (rows) {
+                // e1 = (L1, 0): the three images of a lattice row share r_y
 #pragma unroll
-            for (int im = 0; im < 9; ++im)
-                pair_df(pxh[im], pxl[im], pyh[im], pyl[im], nxh, nxl, nyh, nyl, q, axh, axe, ayh, aye);
+                for (int n = 0; n < 3; ++n) {
+                    const DFy yp = pair_df_y(pyh[3 * n], pyl[3 * n], nyh, nyl, q);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        pair_df_x(pxh[3 * n + m], pxl[3 * n + m], nxh, nxl, yp, q, axh, axe, ayh, aye);
+                }
+            } else {
+#pragma unroll
+                for (int im = 0; im < 9; ++im)
+                    pair_df(pxh[im], pxl[im], pyh[im], pyl[im], nxh, nxl, nyh, nyl, q, axh, axe, ayh, aye);
+            }
         }
         dxs += (double)axh + (double)axe;
         dys += (double)ayh + (double)aye;
@@ -618,8 +794,8 @@ k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
                 const f32x2 dx = sub2(px[t], sx);
                 const f32x2 dy = sub2(py[t], sy);
                 const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
-                const f32x2 rn = fma2(dy, ny2[t], mul2(dx, nx2[t]));
-                const f32x2 rq = fma2(dy, qy, mul2(dx, qx));
+                const f32x2 rn = fma2(dx, nx2[t], mul2(dy, ny2[t]));
+                const f32x2 rq = fma2(dx, qx, mul2(dy, qy));
                 float ra, rb;
                 upk2(r2, ra, rb);
                 const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
@@ -1154,6 +1330,12 @@ __global__ void k_rhs(const double* __restrict__ nx, const double* __restrict__ 
 #define BIE_NEARU_CTAS 6
 #endif
 constexpr int kNearUTpt = BIE_NEARU_TPT, kNearUCtas = BIE_NEARU_CTAS;
+// Batches (more than one cell) run the single-precision near sum in its
+// persistent queue form (compile-time switch for comparisons).
+#ifndef BIE_NEAR_QUEUE
+#define BIE_NEAR_QUEUE 1
+#endif
+constexpr bool kNearQueue = BIE_NEAR_QUEUE != 0;
 
 static int near_tile(int shape32, int prec, bool ut = false) {
     if (prec == 0) return kNearThreads * (ut ? kNearUTpt : kNear32ShapeList[shape32].tpt);
@@ -1227,6 +1409,15 @@ static int build_near_items_prec(bie_ctx* c, int prec) {
             for (int s = 0; s < splits[ci]; ++s) items.push_back(make_int4(ci, t, s, 0));
         }
     }
+    // longest items first (a cell's items cost its source chunk each): the
+    // order of the launch's CTAs and of the persistent queue
+    std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) {
+        const Cell& ca = c->cells_h[a.x];
+        const Cell& cb = c->cells_h[b.x];
+        const int la = (c->srcmul * ca.n_nodes + ca.splits[prec] - 1) / ca.splits[prec];
+        const int lb = (c->srcmul * cb.n_nodes + cb.splits[prec] - 1) / cb.splits[prec];
+        return la > lb;
+    });
     const size_t bytes = off * (prec == 0 ? sizeof(float2) : sizeof(double2));
     if (bytes > c->ws.part_bytes) return fail(c, BIE_EINVAL, "near-sum partial buffer too small");
     if (c->near[prec].items) BIE_CUDA(c, cudaFree(c->near[prec].items));
@@ -1266,10 +1457,24 @@ size_t near_part32_elems(const bie_ctx* c) {
     return (size_t)(last.part_off[0] + (long long)last.splits[0] * last.n_nodes);
 }
 
+// queue: the counter of the persistent form (batches), slots its grid size
 template <int TPT, int MINB, bool PACKED>
-static void near32_variant(bool comp, int blocks, cudaStream_t st, const int4* items, const Cell* cells,
-                           const float4* tgt, const float4* src, float2* part) {
-    if (PACKED) {
+static void near32_variant(bool comp, bool rows, int blocks, cudaStream_t st, const int4* items, const Cell* cells,
+                           const float4* tgt, const float4* src, float2* part, int* queue = nullptr, int slots = 0) {
+    if (PACKED && rows && queue) {
+        cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (comp)
+            k_near32r_queue<TPT, true, MINB><<<slots, kNearThreads, 0, st>>>(items, blocks, queue, cells, tgt, src,
+                                                                            part);
+        else
+            k_near32r_queue<TPT, false, MINB><<<slots, kNearThreads, 0, st>>>(items, blocks, queue, cells, tgt, src,
+                                                                             part);
+    } else if (PACKED && rows) {
+        if (comp)
+            k_near32r<TPT, true, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+        else
+            k_near32r<TPT, false, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
+    } else if (PACKED) {
         if (comp)
             k_near32x2<TPT, true, MINB><<<blocks, kNearThreads, 0, st>>>(items, cells, tgt, src, part);
         else
@@ -1300,13 +1505,19 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
         BIE_LAUNCH(c, "k_near32u");
         return BIE_OK;
     }
+    // lattice rows share dy when every cell has e1 = (L1, 0)
+    bool rows = true;
+    for (const Cell& cl : c->cells_h) rows = rows && cl.e1[1] == 0.0;
+    // batches of uneven cells take their items from a queue (longest first)
+    int* q = (kNearQueue && c->ncell > 1) ? c->near_ctr : nullptr;
+    const int sl = kNear32ShapeList[c->shape32].ctas * c->sms;
     // one case per entry of kNear32ShapeList (packed, targets per thread, CTAs per SM)
     switch (c->shape32) {
-        case 0: near32_variant<2, 5, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
-        case 1: near32_variant<1, 8, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
-        case 2: near32_variant<3, 4, true>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
-        case 3: near32_variant<3, 4, false>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
-        default: near32_variant<2, 5, false>(comp, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        case 0: near32_variant<2, 5, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
+        case 1: near32_variant<1, 8, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
+        case 2: near32_variant<3, 4, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
+        case 3: near32_variant<3, 4, false>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
+        default: near32_variant<2, 5, false>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
     }
     BIE_LAUNCH(c, "k_near32");
     return BIE_OK;

@@ -255,6 +255,7 @@ struct bie_ctx {
     bie::Close cl;
     bie::NearItems near[3];     // 0 single precision, 1 double, 2 double-float
     int shape32 = 0;            // tile shape of the single-precision near sum (kNear32ShapeList)
+    int* near_ctr = nullptr;    // work-queue counter of the persistent near sum (batches)
     unsigned long long epoch = 0;  // bumped whenever a kernel argument of the operator application changes
     // contact-block right preconditioner (opts.precond, precond.cu)
     struct {
@@ -449,10 +450,14 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
 // zero-distance self pair contribute 0.  k_near32 and the mixed-precision
 // close pass both evaluate pairs through this function, so that the second
 // can recompute the first's terms bit for bit.
+//
+// The y-parts (dy^2 + floor, dy ny, dy qy) are formed first so that a kernel
+// can share them between images with the same dy (the three images of a
+// lattice row when e1 = (L1, 0)) and still reproduce every term bit for bit.
 __device__ __forceinline__ float pair32(float dx, float dy, float nx, float ny, float qx, float qy) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, 1e-30f));
-    const float rn = fmaf(dy, ny, dx * nx);
-    const float rq = fmaf(dy, qy, dx * qx);
+    const float rn = fmaf(dx, nx, dy * ny);
+    const float rq = fmaf(dx, qx, dy * qy);
     const float inv = rcp_approx(r2);
     return (rn * inv) * (rq * inv);
 }
