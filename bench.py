@@ -127,18 +127,62 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _function_text(text, name, qualifier):
+    """The definition of function `name` whose declaration carries
+    `qualifier` (with a template line just above it), or ""."""
+    import re
+    for m in re.finditer(r"\b%s\s*\(" % re.escape(name), text):
+        q = text.rfind(qualifier, 0, m.start())
+        if q < 0 or any(ch in text[q:m.start()] for ch in ";{}"):
+            continue
+        i, depth = m.end() - 1, 0
+        while i < len(text):
+            depth += {"(": 1, ")": -1}.get(text[i], 0)
+            if depth == 0:
+                break
+            i += 1
+        j = i + 1
+        while j < len(text) and text[j] in " \t\n":
+            j += 1
+        if j >= len(text) or text[j] != "{":
+            continue  # a declaration or a call, not the definition
+        k, depth = j, 0
+        while k < len(text):
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            if depth == 0:
+                break
+            k += 1
+        start = text.rfind("\n", 0, q) + 1
+        prev = text.rfind("\n", 0, max(0, start - 1)) + 1
+        if text[prev:start].lstrip().startswith("template"):
+            start = prev
+        return text[start:k + 1]
+    return ""
+
+
 def kernel_source(kernel):
-    """Source text of a kernel in the library (from its name to the closing
-    brace at column 0), the unit the committed ncu summaries are keyed on."""
+    """Source text of a kernel in the library and of the library's device
+    functions it calls (directly or through others), the unit the committed
+    ncu summaries are keyed on."""
     import glob
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1912_04501_gb300", "csrc", "*.cu"))):
-        text = open(path).read()
-        k = text.find(kernel + "(")
-        while k >= 0 and text.rfind("\n", 0, k) >= 0 and "__global__" not in text[text.rfind("__global__", 0, k):k][:400]:
-            k = text.find(kernel + "(", k + 1)
-        if k >= 0:
-            e = text.find("\n}\n", k)
-            return text[text.rfind("__global__", 0, k):e + 3]
+    import re
+    texts = [open(p).read() for p in sorted(glob.glob(os.path.join(ROOT, "paper_1912_04501_gb300", "csrc", "*.c*")))]
+    for text in texts:
+        body = _function_text(text, kernel, "__global__")
+        if body:
+            seen, todo, helpers = {kernel}, [body], []
+            while todo:  # device functions it calls, and theirs
+                for name in sorted(set(re.findall(r"\b([a-z][a-z0-9_]*)\s*(?:<[^<>;]*>)?\s*\(", todo.pop()))):
+                    if name in seen:
+                        continue
+                    seen.add(name)
+                    for t in texts:
+                        h = _function_text(t, name, "__device__")
+                        if h:
+                            helpers.append(h)
+                            todo.append(h)
+                            break
+            return body + "".join(sorted(helpers))
     return ""
 
 
