@@ -30,6 +30,7 @@ static int dalloc(bie_ctx* c, T** p, size_t count) {
 }
 
 static void free_all(bie_ctx* c) {
+    if (c->aux) cudaStreamSynchronize(c->aux);  // nothing of an application left in flight
     free_graph(c);
     free_precond(c);
     void* ptrs[] = {c->cells, c->node_cell, c->body_cell, c->x, c->y, c->nx, c->ny, c->w, c->kap, c->owner, c->body,
@@ -50,11 +51,14 @@ static void free_all(bie_ctx* c) {
         if (e) cudaEventDestroy(e);
     c->ev_pool.clear();
     if (c->next_done) cudaEventDestroy(c->next_done);
+    if (c->aux_fork) cudaEventDestroy(c->aux_fork);
+    if (c->aux_join) cudaEventDestroy(c->aux_join);
     for (auto e : c->sv.ev)
         if (e) cudaEventDestroy(e);
     if (c->sv.pinned) cudaFreeHost(c->sv.pinned);
     if (c->cells_pinned) cudaFreeHost(c->cells_pinned);
     if (c->cells_ev) cudaEventDestroy(c->cells_ev);
+    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->side) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
@@ -143,7 +147,7 @@ static int push_density(bie_ctx* c, const double* x) {
 
 // The augmentation directions of the next solve (warm_start 2 and 3): the
 // previous density, its change over the last step, and (2) the network's
-// predicted change.  Returns their number.
+// direction.  Returns their number.
 static int prepare_aug(bie_ctx* c, double dt, int* nu) {
     *nu = 0;
     const int mode = c->opts.warm_start;
@@ -451,6 +455,9 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
     rc = rc ? rc : dalloc(c, &c->next.e2, 2 * nc);
     if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!rc) rc = cu(cudaEventCreateWithFlags(&c->next_done, cudaEventDisableTiming), "cudaEventCreate");
+    if (!rc) rc = cu(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!rc) rc = cu(cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (!rc) rc = cu(cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming), "cudaEventCreate");
     rc = rc ? rc : dalloc(c, &c->yp, nc * 2 * M);
     rc = rc ? rc : dalloc(c, &c->ypf, nc * M);
     rc = rc ? rc : dalloc(c, &c->next.yp, nc * 2 * M);

@@ -2,20 +2,27 @@
 // and the velocity / effective-viscosity extraction, for every cell of the
 // batch at once.
 //
-// Launch sequence of one application (all on the context stream):
+// Launch sequence of one application (context stream; the wall discrepancy
+// and the proxy strengths run on an auxiliary stream beside the near sum):
 //   k_pack_moments  q = sigma w as single-, double- or double-float source records, and
 //                   F_b = sum q, tau_b = sum (x - x^c)^perp . q  (one CTA per body)
-//   k_near32/64/df  3x3 near image sum of G^t at every node (Sec. 6.2 step 1): one
+//   k_near32r/64/df 3x3 near image sum of G^t at every node (Sec. 6.2 step 1): one
 //                   launch over the work items (cell, target tile, source split) of
 //                   all cells -> partial sums per split
-//   k_disc          wall discrepancy of the near sum with the far-image
-//                   cancellation (Sec. 6.2 step 2), per (wall point, split, cell)
-//                   (its last block per wall point forms g~ = g0 - g, Sec. 6.2 step 3)
-//   k_xi            xi = P g~ per (row, cell) (Sec. 6.2 step 3)
+//   k_disc          (auxiliary stream) wall discrepancy of the near sum with the
+//                   far-image cancellation (Sec. 6.2 step 2), per (wall point,
+//                   split, cell) (its last block per wall point forms
+//                   g~ = g0 - g, Sec. 6.2 step 3)
+//   k_xi            (auxiliary stream) xi = P g~ per (row, cell) (Sec. 6.2 step 3)
+// then, single precision (close.cu):
+//   k_alpha32       alpha = -T_0 . n_0 per cell
+//   k_assemble32    per target: T = partials + on-curve diagonal + proxy traction
+//                   (step 4) + close evaluation (Sec. 6.3) with the own-body and
+//                   close pairs redone from positions differenced in double-float;
+//                   y = sigma/2 + T + alpha n + L sigma
+// or, FP64 and double-float:
 //   k_correct       T = sum of partials + on-curve diagonal + proxy traction (step 4)
-//   k_close_apply   close-evaluation correction (Sec. 6.3); on the single-
-//                   precision path also the own-body and close pairs redone
-//                   with positions differenced in double (k_close_apply32)
+//   k_close_apply   close-evaluation correction (Sec. 6.3)
 //   k_finish        alpha = -T_0 . n_0 per cell;  y = sigma/2 + T + alpha n + L sigma
 #include <algorithm>
 #include <cmath>
@@ -1235,57 +1242,6 @@ k_correct(const double2* __restrict__ part, int prec, int N, const int* __restri
 // added with TwoSum compensation, the proxy traction uses the cell-centred
 // single-precision targets, proxies and strengths; only the per-target
 // results and the diagonal term are formed in double.
-__global__ void __launch_bounds__(256)
-k_correct32(const float2* __restrict__ part, int N, const int* __restrict__ node_cell,
-            const Cell* __restrict__ cells, const double2* __restrict__ sigma, const float4* __restrict__ tgt32,
-            const double* __restrict__ nx, const double* __restrict__ ny, const double* __restrict__ w,
-            const double* __restrict__ kap, const float2* __restrict__ ypfall, const float* __restrict__ xifall,
-            int M, double2* __restrict__ T) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kCorrLanes;
-    const int sub = threadIdx.x % kCorrLanes;
-    const int i = g < N ? g : N - 1;
-    const int cidx = node_cell[i];
-    const Cell& cl = cells[cidx];
-    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, e;
-    const int splits = cl.splits[0];
-    const long long base = cl.part_off[0] + (i - cl.node_off);
-    for (int s = sub; s < splits; s += kCorrLanes) {
-        const float2 p = part[base + (long long)s * cl.n_nodes];
-        two_sum(hx, p.x, hx, e);
-        lx += e;
-        two_sum(hy, p.y, hy, e);
-        ly += e;
-    }
-    const float4 tv = tgt32[i];
-    const float2* yp = ypfall + (size_t)cidx * M;
-    const float* xi = xifall + (size_t)cidx * 2 * M;
-    float cx = 0.f, cy = 0.f;
-    for (int p = sub; p < M; p += kCorrLanes) {
-        const float2 q = yp[p];
-        const float rx = tv.x - q.x, ry = tv.y - q.y;
-        const float fx = xi[p], fy = xi[M + p];
-        const float inv = rcp_approx(fmaf(rx, rx, ry * ry));
-        const float cc = (fmaf(rx, tv.z, ry * tv.w) * inv) * (fmaf(rx, fx, ry * fy) * inv);
-        cx = fmaf(cc, rx, cx);
-        cy = fmaf(cc, ry, cy);
-    }
-    const double c = -1.0 / kPi;
-    double tx = (double)hx + (double)lx + c * (double)cx;
-    double ty = (double)hy + (double)ly + c * (double)cy;
-#pragma unroll
-    for (int o = kCorrLanes / 2; o > 0; o >>= 1) {
-        tx += __shfl_xor_sync(0xffffffffu, tx, o);
-        ty += __shfl_xor_sync(0xffffffffu, ty, o);
-    }
-    if (sub != 0 || g >= N) return;
-    const double n0 = nx[i], n1 = ny[i];
-    const double2 sg = sigma[i];
-    const double t0 = -n1, t1 = n0;  // unit tangent
-    const double qx = sg.x * w[i], qy = sg.y * w[i];
-    const double dg = -(kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
-    T[i] = make_double2(tx + dg * t0, ty + dg * t1);
-}
-
 __global__ void k_finish(const double2* __restrict__ T, const double2* __restrict__ sigma, int N,
                          const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ nx, const double* __restrict__ ny,
@@ -1533,6 +1489,34 @@ static_assert(kNear32Shapes == 5 && BIE_SHAPE_IS(0, 1, 2, 5) && BIE_SHAPE_IS(1, 
 // One operator application in three parts: 0 pack the sources and body
 // moments, 1 the near sum (the part the profiler brackets with events),
 // 2 wall discrepancy, proxy fit and correction, close evaluation, assembly.
+// a3 + a4: the wall discrepancy g~ of the packed sources and the proxy
+// strengths xi = P g~ on stream st (independent of the near sum)
+static int launch_disc_xi(bie_ctx* c, bool f32, Workspace& ws, cudaStream_t st) {
+    const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
+    if (c->utilde) {
+        if (f32)
+            k_disc<true, true><<<dgrid, 256, 0, st>>>(ws.src64, ws.src32n, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                      ws.dticket, ws.gt, c->imc);
+        else
+            k_disc<false, true><<<dgrid, 256, 0, st>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                       ws.dticket, ws.gt, c->imc);
+    } else if (f32) {
+        k_disc<true, false><<<dgrid, 256, 0, st>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                   ws.dticket, ws.gt, nullptr);
+    } else {
+        k_disc<false, false><<<dgrid, 256, 0, st>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF, ws.gpart,
+                                                    ws.dticket, ws.gt, nullptr);
+    }
+    BIE_LAUNCH(c, "k_disc");
+    k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, st>>>(ws.gt, c->m, c->M, c->cells, c->P, ws.xi, ws.xif);
+    BIE_LAUNCH(c, "k_xi");
+    return BIE_OK;
+}
+
+// One operator application in four parts: 0 packs the sources and body
+// moments, 1 is the near sum, 2 the wall discrepancy and proxy strengths
+// (independent of 1), 3 the assembly (traction, close evaluation, pressure
+// fix, rigid completion).
 static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, int precision, Workspace& ws) {
     const int N = c->N;
     const int bs = 256, gs = (N + bs - 1) / bs;
@@ -1580,40 +1564,20 @@ static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, i
         }
         return BIE_OK;
     }
-    const dim3 dgrid(2 * c->m, kDiscSplits, c->ncell);
-    if (c->utilde) {
-        if (f32)
-            k_disc<true, true><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32n, c->cells, c->m, c->wall, ws.bodyF,
-                                                             ws.gpart, ws.dticket, ws.gt, c->imc);
-        else
-            k_disc<false, true><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF,
-                                                              ws.gpart, ws.dticket, ws.gt, c->imc);
-    } else if (f32) {
-        k_disc<true, false><<<dgrid, 256, 0, c->stream>>>(ws.src64, ws.src32, c->cells, c->m, c->wall, ws.bodyF,
-                                                          ws.gpart, ws.dticket, ws.gt, nullptr);
-    } else {
-        k_disc<false, false><<<dgrid, 256, 0, c->stream>>>(ws.src64, nullptr, c->cells, c->m, c->wall, ws.bodyF,
-                                                           ws.gpart, ws.dticket, ws.gt, nullptr);
-    }
-    BIE_LAUNCH(c, "k_disc");
-    k_xi<<<dim3(2 * c->M, c->ncell), 32, 0, c->stream>>>(ws.gt, c->m, c->M, c->cells, c->P, ws.xi, ws.xif);
-    BIE_LAUNCH(c, "k_xi");
+    if (part == 2) return launch_disc_xi(c, f32, ws, c->stream);
+    if (f32) return assemble32(c, sigma, ws, yout);
     double2* T = reinterpret_cast<double2*>(ws.T);
     const int gsc = (N * kCorrLanes + 255) / 256;
-    if (f32)
-        k_correct32<<<gsc, 256, 0, c->stream>>>((const float2*)ws.part, N, c->node_cell, c->cells, sg, c->tgt32, c->nx,
-                                                c->ny, c->w, c->kap, c->ypf, ws.xif, c->M, T);
-    else
-        k_correct<<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell, c->cells, sg, c->xw,
-                                              c->yw, c->nx, c->ny, c->w, c->kap, c->yp, ws.xi, c->M, T);
+    k_correct<<<gsc, 256, 0, c->stream>>>((const double2*)ws.part, prec, N, c->node_cell, c->cells, sg, c->xw, c->yw,
+                                          c->nx, c->ny, c->w, c->kap, c->yp, ws.xi, c->M, T);
     BIE_LAUNCH(c, "k_correct");
-    if (int rc = close_apply(c, sigma, ws.T, f32 ? ws.src32 : nullptr)) return rc;
+    if (int rc = close_apply(c, sigma, ws.T)) return rc;
     k_finish<<<gs, bs, 0, c->stream>>>(T, sg, N, c->x, c->y, c->nx, c->ny, c->owner, c->body, ws.bodyF, c->node_cell,
                                        c->cells, reinterpret_cast<double2*>(yout));
     BIE_LAUNCH(c, "k_finish");
     // an FP64-class application over every cell leaves the double-precision
     // sources, body moments and proxy strengths of sigma in the workspace
-    if (&ws == &c->ws && !f32) {
+    if (&ws == &c->ws) {
         bool all = true;
         for (const Cell& cl : c->cells_h) all = all && cl.active;
         if (all) c->ws_x = sigma;
@@ -1624,21 +1588,29 @@ static int apply_part(bie_ctx* c, int part, const double* sigma, double* yout, i
 static int apply_impl(bie_ctx* c, const double* sigma, double* yout, int precision, Workspace& ws) {
     const int kind = precision == BIE_MIXED ? 0 : (precision == BIE_DF64 ? 2 : 1);
     if (int rc = apply_part(c, 0, sigma, yout, precision, ws)) return rc;
+    // part 2 on the auxiliary stream, overlapping the near sum
+    BIE_CUDA(c, cudaEventRecord(c->aux_fork, c->stream));
+    BIE_CUDA(c, cudaStreamWaitEvent(c->aux, c->aux_fork, 0));
+    if (int rc = launch_disc_xi(c, precision == BIE_MIXED, ws, c->aux)) return rc;
+    BIE_CUDA(c, cudaEventRecord(c->aux_join, c->aux));
     if (int rc = prof_begin(c, kind)) return rc;
     if (int rc = apply_part(c, 1, sigma, yout, precision, ws)) return rc;
     if (int rc = prof_end(c)) return rc;
-    return apply_part(c, 2, sigma, yout, precision, ws);
+    BIE_CUDA(c, cudaStreamWaitEvent(c->stream, c->aux_join, 0));
+    return apply_part(c, 3, sigma, yout, precision, ws);
 }
 
 // The single-precision application replayed from CUDA graphs (opts.graph):
-// the three parts of apply_part are captured once per epoch (any change of
-// their arguments: geometry, proxy fit, close pairs, work items) with fixed
-// input and output buffers, on a stream of the context's own (the caller's
-// stream may be the legacy default stream, which cannot capture).  Each
-// application copies sigma in, replays the parts on the context's stream --
-// with the profiler's events around the near sum, between the parts, as for
-// direct launches -- and copies the result out.  The same kernels in the
-// same order: the results are bit for bit those of the direct launches.
+// the parts of apply_part are captured once per epoch (any change of their
+// arguments: geometry, proxy fit, close pairs, work items) as three graphs
+// (pack with the wall discrepancy and proxy strengths; near sum; assembly)
+// with fixed input and output buffers, on a stream of the context's own (the
+// caller's stream may be the legacy default stream, which cannot capture).
+// Each application copies sigma in, replays the graphs on the context's
+// stream -- with the profiler's events around the near sum, between the
+// graphs, as for direct launches -- and copies the result out.  The same
+// kernels with the same inputs (part 2 runs before the near sum instead of
+// beside it): the results are bit for bit those of the direct launches.
 static int apply_graph(bie_ctx* c, const double* sigma, double* yout) {
     auto& g = c->graph;
     const size_t bytes = 2 * (size_t)c->N * sizeof(double);
@@ -1662,7 +1634,10 @@ static int apply_graph(bie_ctx* c, const double* sigma, double* yout) {
             cudaGraph_t graph = nullptr;
             e = cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) break;
-            rc = apply_part(c, part, g.in, g.out, BIE_MIXED, c->ws);
+            // graphs: pack + wall discrepancy and proxy strengths; near sum; assembly
+            static constexpr int kFirst[3] = {0, 1, 3};
+            rc = apply_part(c, kFirst[part], g.in, g.out, BIE_MIXED, c->ws);
+            if (!rc && part == 0) rc = apply_part(c, 2, g.in, g.out, BIE_MIXED, c->ws);
             e = cudaStreamEndCapture(g.capture, &graph);
             if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec[part], graph, 0);
             if (graph) cudaGraphDestroy(graph);

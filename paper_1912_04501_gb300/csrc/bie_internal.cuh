@@ -246,6 +246,10 @@ struct bie_ctx {
     bie::ProxyFit next;
     cudaStream_t side = nullptr;
     cudaEvent_t next_done = nullptr;
+    // the wall discrepancy and proxy strengths of an application run on this
+    // stream while the near sum runs on the context's stream (direct launches)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
     double* yp = nullptr;       // ncell x M x 2 proxy points of the current fit
     float2* ypf = nullptr;      // ncell x M proxy points minus the cell centre (single precision)
     double* scal = nullptr;     // 3 nb + ncell + 8: velocities, rotation rates, mu_eff
@@ -344,7 +348,10 @@ void free_graph(bie_ctx* c);
 // T += C sigma; with src32 (the single-precision path's packed sources) the
 // own-body and close pairs of the single-precision near sum are also redone
 // with positions differenced in double precision
-int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32);
+int close_apply(bie_ctx* c, const double* sigma, double* T);
+// the single-precision application's assembly: traction, close evaluation,
+// pressure fix and rigid completion in two launches (close.cu)
+int assemble32(bie_ctx* c, const double* sigma, const Workspace& ws, double* yout);
 
 // apply.cu ------------------------------------------------------------------
 // near-sum work items (and partial offsets) for the current cell sizes

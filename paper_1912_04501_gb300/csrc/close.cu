@@ -535,36 +535,95 @@ int build_dirichlet_tables(bie_ctx* c, int rho_max) {
     return BIE_OK;
 }
 
-// Single-precision path, one warp per target.  k_near32 sums every pair
-// from single-precision positions relative to the cell centre, whose rounding
-// (~1e-7 of the cell size) is a large relative error in r = x_i - y_j for
-// nodes close to the target, and larger still in r . n_i for the nearly
-// tangent r between neighbours on one curve.  For the target's own body
-// (unshifted) and for each of its close (body, image) pairs, the single-
-// precision terms are recomputed bit for bit (same inputs, same pair32) and
-// replaced by the same terms with r formed exactly from double-float
-// positions (then rounded to single precision); the close-evaluation blocks
-// are applied in single precision (stored divided by the weights, acting on
-// q = sigma w).  Everything runs on the FP32 pipe.
+// Single-precision assembly (a5 + a6 + a7 of one application), one warp
+// per target: the traction T_i is summed from
+//   - the target's near-sum partials (one per source split, TwoSum per lane),
+//   - the proxy traction sum_p G^t(x_i, y_p; n_i) xi_p (single precision),
+//   - the on-curve diagonal -(kappa_i / 2 pi) tau_i (tau_i . q_i),
+//   - the close-evaluation corrections below,
+// and the output is y_i = sigma_i / 2 + T_i + alpha n_i + F_b + (x_i - x^c)^perp tau_b
+// with alpha = -T(x_1) . n_1 per cell (Sec. 6.2 remark on the pressure).
+//
+// Close-evaluation corrections.  k_near32 sums every pair from single-
+// precision positions relative to the cell centre, whose rounding (~1e-7 of
+// the cell size) is a large relative error in r = x_i - y_j for nodes close
+// to the target, and larger still in r . n_i for the nearly tangent r between
+// neighbours on one curve.  For the target's own body (unshifted) and for
+// each of its close (body, image) pairs, the single-precision terms are
+// recomputed bit for bit (same inputs, same pair32) and replaced by the same
+// terms with r formed exactly from double-float positions (then rounded to
+// single precision); the close-evaluation blocks are applied in single
+// precision (stored divided by the weights, acting on q = sigma w).
+// Everything but the final sums runs on the FP32 pipe.
 //
 // With the doubled-cell periodizer (imc non-null) the near sum evaluated the
 // pair at the target's translate inside U (tgt32) against the source's image
 // record src32[4 j + k], k the node's image that lands the body image where
 // it is seen from that translate; the redo recomputes that term.
-__global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
-                                const long long* __restrict__ blk_off, const float* __restrict__ blocks32,
-                                int use_pairs, const double* __restrict__ body, const int* __restrict__ owner,
-                                const double2* __restrict__ sigma, int N, const float4* __restrict__ tgt32,
-                                const float4* __restrict__ src32, const float4* __restrict__ posdf,
-                                const double* __restrict__ x, const double* __restrict__ y,
-                                const int* __restrict__ node_cell, const Cell* __restrict__ cells,
-                                const int* __restrict__ imc, double2* __restrict__ T) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (i >= N) return;
-    const Cell& cl = cells[node_cell[i]];
-    const float4 tv = tgt32[i];
-    const float4 pi = posdf[i];
-    const int wi = imc ? img_wrap(imc[i]) : 4;
+struct Asm32 {
+    const float2* part;
+    const float2* ypf;
+    const float* xif;
+    int M;
+    const int* pair_base;
+    const int4* pairs;
+    const long long* blk_off;
+    const float* blocks32;
+    int use_pairs;
+    const double* body;
+    const int* owner;
+    const double2* sigma;
+    int N;
+    const float4* tgt32;
+    const float4* src32;
+    const float4* posdf;
+    const double* x;
+    const double* y;
+    const double* nx;
+    const double* ny;
+    const double* w;
+    const double* kap;
+    const int* node_cell;
+    const Cell* cells;
+    const int* imc;
+    const double* bodyF;
+};
+
+// T_i on every thread of the calling group of NL threads (a warp, NL = 32,
+// or a whole CTA, NL = blockDim.x = 256; red: 6 NL / 32 doubles of shared
+// memory for NL > 32); fixed reduction order.
+template <int NL>
+__device__ __forceinline__ double2 traction32(const Asm32& a, int i, int lane, double* red) {
+    const int cidx = a.node_cell[i];
+    const Cell& cl = a.cells[cidx];
+    // near-sum partials
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, e;
+    const int splits = cl.splits[0];
+    const long long base = cl.part_off[0] + (i - cl.node_off);
+    for (int s = lane; s < splits; s += NL) {
+        const float2 p = a.part[base + (long long)s * cl.n_nodes];
+        two_sum(hx, p.x, hx, e);
+        lx += e;
+        two_sum(hy, p.y, hy, e);
+        ly += e;
+    }
+    // proxy traction
+    const float4 tv = a.tgt32[i];
+    const float2* yp = a.ypf + (size_t)cidx * a.M;
+    const float* xi = a.xif + (size_t)cidx * 2 * a.M;
+    float cx = 0.f, cy = 0.f;
+    for (int p = lane; p < a.M; p += NL) {
+        const float2 q = yp[p];
+        const float rx = tv.x - q.x, ry = tv.y - q.y;
+        const float fx = xi[p], fy = xi[a.M + p];
+        const float inv = rcp_approx(fmaf(rx, rx, ry * ry));
+        const float cc = (fmaf(rx, tv.z, ry * tv.w) * inv) * (fmaf(rx, fx, ry * fy) * inv);
+        cx = fmaf(cc, rx, cx);
+        cy = fmaf(cc, ry, cy);
+    }
+    // close-evaluation corrections
+    const float4 pi = a.posdf[i];
+    const int wi = a.imc ? img_wrap(a.imc[i]) : 4;
     float fx = 0.f, fy = 0.f;  // sum of (exactly differenced term - single-precision term)
     // target minus the image shift, exactly, as a double-float pair (xh, xl, yh, yl)
     auto shifted = [&](int im) {
@@ -576,24 +635,24 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
     auto redo = [&](int j, int im, const float4& p) {
         float4 s;
         float dx, dy;
-        if (imc) {
+        if (a.imc) {
             // image (m, n) of node j seen from the translate: its record index
-            const int code = imc[j];
+            const int code = a.imc[j];
             const int dm = (im % 3 - 1) + (wi % 3 - 1) - img_m0(code);
             const int dn = (im / 3 - 1) + (wi / 3 - 1) - img_n0(code);
             // not among the node's images: the near sum has no such term (on
             // a body wider than half a cell, far from the target)
             if (dm < 0 || dm > 1 || dn < 0 || dn > 1) return;
-            s = src32[4 * (size_t)j + (dm + 2 * dn)];
+            s = a.src32[4 * (size_t)j + (dm + 2 * dn)];
             dx = tv.x - s.x;
             dy = tv.y - s.y;
         } else {
-            s = src32[j];
+            s = a.src32[j];
             dx = (tv.x - cl.sxf[im]) - s.x;
             dy = (tv.y - cl.syf[im]) - s.y;
         }
         const float c0 = pair32(dx, dy, tv.z, tv.w, s.z, s.w);
-        const float4 q = posdf[j];
+        const float4 q = a.posdf[j];
         float rh, rl, sh, sl;
         df_diff(p.x, p.y, q.x, q.y, rh, rl);
         df_diff(p.z, p.w, q.z, q.w, sh, sl);
@@ -603,60 +662,150 @@ __global__ void k_close_apply32(const int* __restrict__ pair_base, const int4* _
         fy += c1 * ry - c0 * dy;
     };
     {
-        const int b = owner[i];
-        const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
+        const int b = a.owner[i];
+        const int nbn = (int)a.body[8 * b + 5], off = (int)a.body[8 * b + 6];
         const float4 p = shifted(4);
-        for (int k = lane; k < nbn; k += 32)
+#pragma unroll 4
+        for (int k = lane; k < nbn; k += NL)
             if (off + k != i) redo(off + k, 4, p);
     }
     float bx = 0.f, by = 0.f;  // close-evaluation blocks applied to q
-    if (use_pairs) {
-        const int p0 = pair_base[i], p1 = pair_base[i + 1];
+    if (a.use_pairs) {
+        const int p0 = a.pair_base[i], p1 = a.pair_base[i + 1];
         for (int pp = p0; pp < p1; ++pp) {
-            const int4 pr = pairs[pp];
+            const int4 pr = a.pairs[pp];
             const int b = pr.y, im = pr.z;
-            const int nbn = (int)body[8 * b + 5], off = (int)body[8 * b + 6];
-            const float* C = blocks32 + blk_off[pp];
+            const int nbn = (int)a.body[8 * b + 5], off = (int)a.body[8 * b + 6];
+            const float* C = a.blocks32 + a.blk_off[pp];
             const float4 p = shifted(im);
-            for (int k = lane; k < nbn; k += 32) {
+#pragma unroll 2
+            for (int k = lane; k < nbn; k += NL) {
                 redo(off + k, im, p);
-                const float4 s = src32[imc ? 4 * (size_t)(off + k) : (size_t)(off + k)];  // q: the same in every record
+                const float4 s = a.src32[a.imc ? 4 * (size_t)(off + k) : (size_t)(off + k)];  // q: the same in every record
                 const float A = C[3 * k], B = C[3 * k + 1], D = C[3 * k + 2];
                 bx = fmaf(A, s.z, fmaf(B, s.w, bx));
                 by = fmaf(B, s.z, fmaf(D, s.w, by));
             }
         }
     }
+    const double c = -1.0 / kPi;
+    double tx = (double)hx + (double)lx + c * (double)cx;
+    double ty = (double)hy + (double)ly + c * (double)cy;
     for (int o = 16; o > 0; o >>= 1) {
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        ty += __shfl_xor_sync(0xffffffffu, ty, o);
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
         bx += __shfl_xor_sync(0xffffffffu, bx, o);
         by += __shfl_xor_sync(0xffffffffu, by, o);
     }
-    if (lane == 0) {
-        const double c = -1.0 / kPi;
-        const double2 t = T[i];
-        T[i] = make_double2(t.x + (double)bx + c * (double)fx, t.y + (double)by + c * (double)fy);
+    if constexpr (NL > 32) {  // the warps' sums, added in warp order
+        constexpr int nw = NL / 32;
+        const int wid = lane >> 5;
+        if ((lane & 31) == 0) {
+            red[wid] = tx;
+            red[nw + wid] = ty;
+            red[2 * nw + wid] = fx;
+            red[3 * nw + wid] = fy;
+            red[4 * nw + wid] = bx;
+            red[5 * nw + wid] = by;
+        }
+        __syncthreads();
+        tx = ty = 0.0;
+        double sfx = 0.0, sfy = 0.0, sbx = 0.0, sby = 0.0;
+        for (int k = 0; k < nw; ++k) {
+            tx += red[k];
+            ty += red[nw + k];
+            sfx += red[2 * nw + k];
+            sfy += red[3 * nw + k];
+            sbx += red[4 * nw + k];
+            sby += red[5 * nw + k];
+        }
+        fx = (float)sfx;
+        fy = (float)sfy;
+        bx = (float)sbx;
+        by = (float)sby;
     }
+    // on-curve diagonal
+    const double n0 = a.nx[i], n1 = a.ny[i];
+    const double2 sg = a.sigma[i];
+    const double t0 = -n1, t1 = n0;  // unit tangent
+    const double qx = sg.x * a.w[i], qy = sg.y * a.w[i];
+    const double dg = -(a.kap[i] / (2.0 * kPi)) * (t0 * qx + t1 * qy);
+    return make_double2((tx + dg * t0) + (double)bx + c * (double)fx, (ty + dg * t1) + (double)by + c * (double)fy);
 }
 
-int close_apply(bie_ctx* c, const double* sigma, double* T, const float4* src32) {
-    const int N = c->N;
-    const long long threads = 32LL * N;
+// alpha = -T(x_1) . n_1 of every cell (x_1: node 0 of its first body), one CTA per cell.
+constexpr int kAlphaThreads = 256;
+__global__ void __launch_bounds__(kAlphaThreads, 1) k_alpha32(Asm32 a, double* __restrict__ alpha) {
+    __shared__ double red[6 * kAlphaThreads / 32];
+    const int ci = blockIdx.x;
+    const int i0 = a.cells[ci].node_off;
+    const double2 T = traction32<kAlphaThreads>(a, i0, threadIdx.x, red);
+    if (threadIdx.x == 0) alpha[ci] = -(T.x * a.nx[i0] + T.y * a.ny[i0]);
+}
+
+// y_i = sigma_i / 2 + T_i + alpha n_i + F_b + (x_i - x^c)^perp tau_b, one warp per target.
+__global__ void __launch_bounds__(256, 3) k_assemble32(Asm32 a, const double* __restrict__ alpha,
+                                                    double2* __restrict__ out) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= a.N) return;
+    const double2 T = traction32<32>(a, i, lane, nullptr);
+    if (lane != 0) return;
+    const double al = alpha[a.node_cell[i]];
+    const int b = a.owner[i];
+    const double xc = a.body[8 * b + 2], yc = a.body[8 * b + 3];
+    const double Fx = a.bodyF[3 * b], Fy = a.bodyF[3 * b + 1], tq = a.bodyF[3 * b + 2];
+    const double2 s = a.sigma[i];
+    const double ox = 0.5 * s.x + T.x + al * a.nx[i] + Fx - (a.y[i] - yc) * tq;
+    const double oy = 0.5 * s.y + T.y + al * a.ny[i] + Fy + (a.x[i] - xc) * tq;
+    out[i] = make_double2(ox, oy);
+}
+
+int assemble32(bie_ctx* c, const double* sigma, const Workspace& ws, double* yout) {
+    Asm32 a;
+    a.part = (const float2*)ws.part;
+    a.ypf = c->ypf;
+    a.xif = ws.xif;
+    a.M = c->M;
+    a.pair_base = c->cl.pair_base;
+    a.pairs = c->cl.pairs;
+    a.blk_off = c->cl.blk_off;
+    a.blocks32 = c->cl.blocks32;
+    a.use_pairs = c->cl.npairs > 0 ? 1 : 0;
+    a.body = c->body;
+    a.owner = c->owner;
+    a.sigma = reinterpret_cast<const double2*>(sigma);
+    a.N = c->N;
+    a.tgt32 = c->tgt32;
+    a.src32 = ws.src32;
+    a.posdf = c->posdf;
+    a.x = c->x;
+    a.y = c->y;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.w = c->w;
+    a.kap = c->kap;
+    a.node_cell = c->node_cell;
+    a.cells = c->cells;
+    a.imc = c->utilde ? c->imc : nullptr;
+    a.bodyF = ws.bodyF;
+    double* alpha = ws.T;  // the single-precision path keeps no T: its first ncell entries hold alpha
+    k_alpha32<<<c->ncell, kAlphaThreads, 0, c->stream>>>(a, alpha);
+    BIE_LAUNCH(c, "k_alpha32");
     const int bs = 256;
-    const int gs = (int)((threads + bs - 1) / bs);
-    if (src32) {
-        k_close_apply32<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks32,
-                                                 c->cl.npairs > 0 ? 1 : 0, c->body, c->owner,
-                                                 reinterpret_cast<const double2*>(sigma), N, c->tgt32, src32, c->posdf,
-                                                 c->x, c->y, c->node_cell, c->cells, c->utilde ? c->imc : nullptr,
-                                                 reinterpret_cast<double2*>(T));
-        BIE_LAUNCH(c, "k_close_apply32");
-        return BIE_OK;
-    }
+    const int gs = (int)((32LL * c->N + bs - 1) / bs);
+    k_assemble32<<<gs, bs, 0, c->stream>>>(a, alpha, reinterpret_cast<double2*>(yout));
+    BIE_LAUNCH(c, "k_assemble32");
+    return BIE_OK;
+}
+
+int close_apply(bie_ctx* c, const double* sigma, double* T) {
     if (c->cl.npairs == 0) return BIE_OK;
+    const int bs = 256;
+    const int gs = (int)((32LL * c->N + bs - 1) / bs);
     k_close_apply<<<gs, bs, 0, c->stream>>>(c->cl.pair_base, c->cl.pairs, c->cl.blk_off, c->cl.blocks, c->body,
-                                           reinterpret_cast<const double2*>(sigma), N,
+                                           reinterpret_cast<const double2*>(sigma), c->N,
                                            reinterpret_cast<double2*>(T));
     BIE_LAUNCH(c, "k_close_apply");
     return BIE_OK;
