@@ -101,7 +101,7 @@ typedef struct {
     int32_t max_refine;   /* maximum outer refinement sweeps (BIE_MIXED) */
     int32_t warm_start;   /* bie_step start: 0 = zero; 1 = previous step's density as the initial
                              guess; 2 = zero start, first GMRES cycle augmented with the previous
-                             density, its last change and the warm-start network's predicted change
+                             density, its last change and the warm-start network's direction
                              (bie_set_warm_net); with BIE_MIXED the second refinement sweep is
                              augmented with the previous step's second-sweep correction (the
                              single-precision operator's error changes little per step);
@@ -312,11 +312,16 @@ int bie_apply_static(bie_ctx* ctx, const double* sigma, double* out);
 /* ------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper).  A per-node multilayer
  * perceptron, x (BIE_NET_FEATURES) -> tanh(W1 x + b1) -> tanh(W2 . + b2) ->
- * W3 . + b3 (2 outputs), hidden width BIE_NET_HIDDEN, predicts the change of
- * the density over one time step in units of mu |gamma| dt from local features
- * (bie_features).  Parameters: one float array, W1 (row-major), b1, W2, b2,
- * W3, b3.  The kernels read bfloat16 weights and compute in FP32; training
- * keeps FP32 master weights and Adam moments.  With warm_start = 2, bie_step
+ * W3 . + b3 (2 outputs), hidden width BIE_NET_HIDDEN, maps local features
+ * (bie_features) to a density direction in units of mu |gamma| dt; the
+ * shipped parameters are trained on the density change over one time step.  Parameters: one float array, W1 (row-major), b1, W2, b2,
+ * W3, b3.  The kernels read bfloat16 weights; layers 1 and 2 and the weight
+ * gradients are tensor-core products of bfloat16 operands (the inputs and
+ * the first hidden layer rounded to bfloat16, and in the gradient the
+ * back-propagated errors too) with FP32 accumulation; tanh, the last layer
+ * and the bias sums are FP32.  Training keeps FP32 master weights and Adam
+ * moments.  BIE_ECUDA also reports a tensor-core completion wait that timed
+ * out (the kernels never wait without a limit).  With warm_start = 2, bie_step
  * adds the prediction to the directions of the first GMRES cycle's search
  * space (see bie_opts.warm_start), so the GMRES residual test at gmres_tol
  * still decides convergence.

@@ -1,7 +1,8 @@
 // The warm-start network: a per-node multilayer perceptron that maps local
 // features of a node (geometry, gap to the nearest other curve, previous
-// densities) to a predicted change of the density over one time step.  It is
-// trained by the kernels below on densities the solver itself produced, and
+// densities) to a density direction (trained on the change over one time
+// step).  It is trained by the kernels below on densities the solver itself
+// produced, and
 // the solver uses its output only as an extra direction of the first GMRES
 // search space (solve.cu), so a poor prediction costs iterations at most.
 //
@@ -9,9 +10,12 @@
 //   a1 = tanh(W1 x + b1)      W1: H x n_in
 //   a2 = tanh(W2 a1 + b2)     W2: H x H
 //   y  = W3 a2 + b3           W3: 2 x H
-// Parameters are one flat array in that order (W row-major).  The forward
-// passes read the weights in bfloat16 (the training copy keeps FP32 master
-// weights and Adam moments); every product and sum is in FP32.
+// Parameters are one flat array in that order (W row-major).  The kernels
+// read the weights in bfloat16 (the training copy keeps FP32 master weights
+// and Adam moments).  Layers 1 and 2 and the weight gradients are tcgen05
+// tensor-core products (bfloat16 operands, FP32 accumulation in tensor
+// memory); tanh, the last layer and the biases are FP32 on the CUDA cores.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -21,6 +25,7 @@
 #include <cuda_bf16.h>
 
 #include "bie_internal.cuh"
+#include "tc.cuh"
 
 namespace bie {
 
@@ -44,183 +49,421 @@ __host__ __device__ inline NetLayout net_layout(int n_in) {
     return L;
 }
 
-// bfloat16 weights -> FP32 shared-memory copy (all threads of the block)
-__device__ inline void load_weights(const __nv_bfloat16* __restrict__ wb, int n, float* __restrict__ s) {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) s[k] = __bfloat162float(wb[k]);
-    __syncthreads();
+// ---------------------------------------------------------------------------
+// Tensor-core kernels (tcgen05).  A tile is 128 nodes, one per thread and one
+// per TMEM lane (4 warps = the 4 lane quarters), the M of every MMA.  The
+// matrix products take bfloat16 operands and accumulate in float32 in TMEM:
+//   layer 1   Z1 [128 x 64] = bf(X) [128 x 16] . W1^T          (1 MMA, K = 16)
+//   layer 2   Z2 [128 x 64] = bf(a1) [128 x 64] . W2^T         (4 MMAs)
+//   layer 3   y = W3 a2 + b3 per thread (2 outputs: CUDA cores)
+// and for the gradient (d3 = 2 w (y - t) per node, unnormalised):
+//   d1 GEMM   Z [128 x 64] = bf(d2) [128 x 64] . W2              (4 MMAs)
+//   weights   G [128 x 96] += [bf(d2)^T; bf(d1)^T] [128 x 128 nodes] . [bf(a1)^T; bf(x)^T; 1]^T
+//             (8 MMAs, K = the tile's 128 nodes): rows 0-63 give gW2 (columns
+//             0-63) and gb2 (column 80), rows 64-127 give gW1 (columns 64-79)
+//             and gb1 (column 80)
+//             G3 [128 x 16] += [bf(a2)^T; 0] . [bf(d3_0); bf(d3_1); 0]^T   (8 MMAs): gW3
+// accumulated in TMEM over the CTA's tiles.  bf = round to nearest bfloat16.
+// ---------------------------------------------------------------------------
+constexpr int kTcTile = 128;     // nodes per tile
+constexpr int kTcThreads = 128;  // one thread per node of the tile
+constexpr int kK1 = 16;          // layer-1 K: the inputs padded to 16
+
+static_assert(H == 64 && kNetMaxIn <= kK1, "the tensor-core tiles assume 64 hidden units and <= 16 inputs");
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ void st_bf16(uint8_t* p, float v) { *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st_row16(uint8_t* base, int r, int k0, int kext, const uint32_t* pk) {
+    *reinterpret_cast<uint4*>(base + tc::kmajor_off(r, k0, kext)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
-// Inference: one thread per node; y (N x 2) = net(x (N x n_in)).
-__global__ void __launch_bounds__(128)
-k_net_forward(const __nv_bfloat16* __restrict__ wb, int n_in, const float* __restrict__ X, int N,
-              float* __restrict__ Y) {
-    extern __shared__ float sw[];
-    const NetLayout L = net_layout(n_in);
-    load_weights(wb, L.total, sw);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    float x[kNetMaxIn];
-#pragma unroll
-    for (int f = 0; f < kNetMaxIn; ++f) x[f] = f < n_in ? X[(size_t)i * n_in + f] : 0.f;
-    float a1[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-        float z = sw[L.b1 + j];
-#pragma unroll
-        for (int f = 0; f < kNetMaxIn; ++f)
-            if (f < n_in) z = fmaf(sw[L.w1 + j * n_in + f], x[f], z);
-        a1[j] = tanhf(z);
-    }
-    float y0 = sw[L.b3], y1 = sw[L.b3 + 1];
-    for (int k = 0; k < H; ++k) {
-        float z = sw[L.b2 + k];
-#pragma unroll
-        for (int j = 0; j < H; ++j) z = fmaf(sw[L.w2 + k * H + j], a1[j], z);
-        const float a2 = tanhf(z);
-        y0 = fmaf(sw[L.w3 + k], a2, y0);
-        y1 = fmaf(sw[L.w3 + H + k], a2, y1);
-    }
-    Y[2 * (size_t)i] = y0;
-    Y[2 * (size_t)i + 1] = y1;
+// shared memory (bytes) common to both kernels
+constexpr uint32_t kSmXA = 0;                          // 128 x 16 bf(x)      A of layer 1
+constexpr uint32_t kSmW1 = kSmXA + kTcTile * kK1 * 2;  // 64 x 16 W1          B of layer 1
+constexpr uint32_t kSmA1 = kSmW1 + H * kK1 * 2;        // 128 x 64 bf(a1)     A of layer 2
+constexpr uint32_t kSmW2 = kSmA1 + kTcTile * H * 2;    // 64 x 64 W2 [k][j]   B of layer 2
+constexpr uint32_t kSmFwdEnd = kSmW2 + H * H * 2;
+// the gradient kernel's operands after those
+constexpr uint32_t kSmW2T = kSmFwdEnd;                 // 64 x 64 W2^T [j][k] B of the d1 GEMM
+constexpr uint32_t kSmD2 = kSmW2T + H * H * 2;         // 128 x 64 bf(d2)     A of the d1 GEMM
+constexpr uint32_t kSmAS = kSmD2 + kTcTile * H * 2;    // 128 x 128           A of the weight GEMM
+constexpr uint32_t kSmBS = kSmAS + 128 * kTcTile * 2;  // 96 x 128            B of the weight GEMM
+constexpr uint32_t kSmA3 = kSmBS + 96 * kTcTile * 2;   // 128 x 128 (64 used) A of the W3 GEMM
+constexpr uint32_t kSmB3 = kSmA3 + 128 * kTcTile * 2;  // 16 x 128 (2 used)   B of the W3 GEMM
+constexpr uint32_t kSmGradEnd = kSmB3 + 16 * kTcTile * 2;
+// parameters in float32, TMEM base, mbarrier, error flag, warp partial sums
+constexpr uint32_t kSmParBytes = (2 * H + 2 * H + 2) * 4;
+constexpr uint32_t kSmMisc = 64 + 4 * 4 * 4;
+
+__host__ __device__ constexpr uint32_t par_off(uint32_t end) { return (end + 15) & ~15u; }
+// forward: 3 CTAs per SM at most (3 x 128 TMEM columns), however small the footprint
+constexpr uint32_t kFwdSmem = 60 * 1024;
+constexpr uint32_t kGradSmem = par_off(kSmGradEnd) + kSmParBytes + kSmMisc;
+static_assert(par_off(kSmFwdEnd) + kSmParBytes + kSmMisc <= kFwdSmem, "forward shared memory");
+static_assert(kGradSmem <= 227 * 1024, "gradient shared memory");
+
+struct TcShared {
+    float *b1, *b2, *w3, *b3, *part;
+    uint32_t* tslot;
+    uint64_t* mbar;
+    int* err;
+};
+
+__device__ inline TcShared tc_shared(uint8_t* sm, uint32_t end) {
+    TcShared s;
+    s.b1 = reinterpret_cast<float*>(sm + par_off(end));
+    s.b2 = s.b1 + H;
+    s.w3 = s.b2 + H;
+    s.b3 = s.w3 + 2 * H;
+    uint8_t* misc = sm + par_off(end) + kSmParBytes;
+    s.tslot = reinterpret_cast<uint32_t*>(misc);
+    s.mbar = reinterpret_cast<uint64_t*>(misc + 8);
+    s.err = reinterpret_cast<int*>(misc + 16);
+    s.part = reinterpret_cast<float*>(misc + 64);  // 4 warps x 4
+    return s;
 }
 
-// Training: loss L = sum_i w_i |y_i - t_i|^2 / sum_i w_i over the batch, its
-// gradient with respect to every parameter.  Block of kNetBlock nodes:
-// activations and back-propagated errors live in shared memory, each
-// weight-gradient entry is summed over the block's nodes by one thread, and
-// the block writes its partial gradient (and partial loss) to
-// part[block][...]; k_net_reduce adds the blocks in order.
-constexpr int kNetBlock = 128;
-constexpr int kRow = H + 1;  // padded row of the per-node activation tables
-
-__global__ void __launch_bounds__(kNetBlock)
-k_net_grad(const __nv_bfloat16* __restrict__ wb, int n_in, const float* __restrict__ X,
-           const float* __restrict__ T, const float* __restrict__ Wt, int N, float* __restrict__ part) {
-    extern __shared__ float sm[];
+// weights into the operand tiles (bf16) and parameters (f32); W2T only for the gradient
+__device__ inline void tc_load_weights(const __nv_bfloat16* __restrict__ wb, int n_in, uint8_t* sm, const TcShared& S,
+                                       bool w2t) {
     const NetLayout L = net_layout(n_in);
-    float* sw = sm;                                  // L.total weights
-    float* A1 = sw + ((L.total + 3) & ~3);           // kNetBlock x kRow: a1, later delta1
-    float* A2 = A1 + kNetBlock * kRow;               // kNetBlock x kRow: a2, later delta2
-    float* SX = A2 + kNetBlock * kRow;               // kNetBlock x n_in
-    float* D3 = SX + kNetBlock * kNetMaxIn;          // kNetBlock x 2
-    float* RL = D3 + 2 * kNetBlock;                  // kNetBlock: per-node loss
-    float* RW = RL + kNetBlock;                      // kNetBlock: per-node weight
-    load_weights(wb, L.total, sw);
     const int t = threadIdx.x;
-    const int i = blockIdx.x * kNetBlock + t;
-    const bool valid = i < N;
-    // forward, one thread per node
-    {
-        float x[kNetMaxIn];
+    for (int e = t; e < H * kK1; e += kTcThreads) {
+        const int j = e / kK1, f = e % kK1;
+        *reinterpret_cast<__nv_bfloat16*>(sm + kSmW1 + tc::kmajor_off(j, f, kK1)) =
+            f < n_in ? wb[L.w1 + j * n_in + f] : __float2bfloat16_rn(0.f);
+    }
+    for (int e = t; e < H * H; e += kTcThreads) {
+        const int k = e / H, j = e % H;
+        *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2 + tc::kmajor_off(k, j, H)) = wb[L.w2 + e];
+        if (w2t) *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2T + tc::kmajor_off(j, k, H)) = wb[L.w2 + e];
+    }
+    for (int e = t; e < H; e += kTcThreads) {
+        S.b1[e] = __bfloat162float(wb[L.b1 + e]);
+        S.b2[e] = __bfloat162float(wb[L.b2 + e]);
+        S.w3[e] = __bfloat162float(wb[L.w3 + e]);
+        S.w3[H + e] = __bfloat162float(wb[L.w3 + H + e]);
+    }
+    if (t < 2) S.b3[t] = __bfloat162float(wb[L.b3 + t]);
+}
+
+// the CTA's set-up: mbarrier, error flag, TMEM columns (warp 0); returns the TMEM base
+__device__ inline uint32_t tc_setup(const TcShared& S, uint32_t ncols) {
+    if (threadIdx.x == 0) {
+        tc::mbar_init(S.mbar, 1);
+        *S.err = 0;
+    }
+    if (threadIdx.x < 32) tc::tmem_alloc(S.tslot, ncols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    return *S.tslot;
+}
+
+// operands written -> the MMAs issued by thread 0 -> completion waited for by
+// every thread (bounded); false (and the CTA's error flag set) on timeout
+template <class Issue>
+__device__ inline bool tc_step(const TcShared& S, uint32_t& phase, Issue issue) {
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        issue();
+        tc::commit(S.mbar);
+    }
+    if (!tc::mbar_wait(S.mbar, phase)) *S.err = 1;
+    phase ^= 1;
+    tc::fence_after_sync();
+    __syncthreads();
+    return *S.err == 0;
+}
+
+// release TMEM; a CTA whose wait timed out first waits (bounded) for its MMAs
+__device__ inline void tc_teardown(const TcShared& S, uint32_t tmem, uint32_t ncols, uint32_t phase, int* err) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (*S.err) tc::mbar_wait(S.mbar, phase ^ 1, 1 << 20);
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, ncols);
+    if (threadIdx.x == 0 && *S.err) atomicExch(err, 1);
+}
+
+// layer 1 operand: node i's inputs in bfloat16, zero padded (and, for the
+// gradient, their transpose into rows 64.. of the weight GEMM's B)
+__device__ inline void tc_inputs(const float* __restrict__ X, int n_in, int i, int N, uint8_t* sm, bool grad) {
+    const int t = threadIdx.x;
+    float x[kK1];
 #pragma unroll
-        for (int f = 0; f < kNetMaxIn; ++f) {
-            x[f] = (valid && f < n_in) ? X[(size_t)i * n_in + f] : 0.f;
-            SX[t * kNetMaxIn + f] = x[f];
-        }
-        for (int j = 0; j < H; ++j) {
-            float z = sw[L.b1 + j];
+    for (int f = 0; f < kK1; ++f) x[f] = (i < N && f < n_in) ? X[(size_t)i * n_in + f] : 0.f;
+    uint32_t pk[8];
 #pragma unroll
-            for (int f = 0; f < kNetMaxIn; ++f)
-                if (f < n_in) z = fmaf(sw[L.w1 + j * n_in + f], x[f], z);
-            A1[t * kRow + j] = tanhf(z);
+    for (int q = 0; q < 8; ++q) pk[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+    st_row16(sm + kSmXA, t, 0, kK1, pk);
+    st_row16(sm + kSmXA, t, 8, kK1, pk + 4);
+    if (grad)
+#pragma unroll
+        for (int f = 0; f < kK1; ++f) st_bf16(sm + kSmBS + tc::kmajor_off(H + f, t, kTcTile), x[f]);
+}
+
+__device__ inline uint64_t desc_k(uint32_t addr, int kext) { return tc::sdesc(addr, 128, (uint32_t)kext * 16); }
+
+// layer 1 and 2 MMAs issued by thread 0
+__device__ inline void issue_layer1(uint32_t sbase, uint32_t d1) {
+    tc::mma_bf16(d1, desc_k(sbase + kSmXA, kK1), desc_k(sbase + kSmW1, kK1), tc::idesc_bf16(128, H), 0);
+}
+__device__ inline void issue_layer2(uint32_t sbase, uint32_t d2) {
+#pragma unroll
+    for (int s = 0; s < H / 16; ++s)
+        tc::mma_bf16(d2, desc_k(sbase + kSmA1 + 256 * s, H), desc_k(sbase + kSmW2 + 256 * s, H),
+                     tc::idesc_bf16(128, H), s > 0);
+}
+
+// layer-1 epilogue: a1 = tanh(z1 + b1) in bfloat16 into row t of layer 2's A
+// (and, for the gradient, its transpose into rows 0..63 of the weight GEMM's B)
+__device__ inline void tc_layer1_out(uint32_t taddr, const TcShared& S, uint8_t* sm, bool grad) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < H / 16; ++c) {
+        float z[16];
+        tc::tmem_ld16(taddr + 16 * c, z);
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            pk[q] = pack_bf16(tanhf(z[2 * q] + S.b1[16 * c + 2 * q]), tanhf(z[2 * q + 1] + S.b1[16 * c + 2 * q + 1]));
+        st_row16(sm + kSmA1, t, 16 * c, H, pk);
+        st_row16(sm + kSmA1, t, 16 * c + 8, H, pk + 4);
+        if (grad)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t w = pk[q >> 1];
+                const uint16_t h = (q & 1) ? (uint16_t)(w >> 16) : (uint16_t)(w & 0xFFFFu);
+                *reinterpret_cast<uint16_t*>(sm + kSmBS + tc::kmajor_off(16 * c + q, t, kTcTile)) = h;
+            }
+    }
+}
+
+// Inference: y (N x 2) = net(x (N x n_in)) with the bfloat16 roundings of
+// the header comment; persistent over tiles.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_net_forward(const __nv_bfloat16* __restrict__ wb, int n_in, const float* __restrict__ X, int N,
+              float* __restrict__ Y, int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const TcShared S = tc_shared(sm, kSmFwdEnd);
+    tc_load_weights(wb, n_in, sm, S, false);
+    const uint32_t tmem = tc_setup(S, 128);
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
+    const uint32_t sbase = tc::smem_u32(sm);
+    uint32_t phase = 0;
+    const int ntiles = (N + kTcTile - 1) / kTcTile;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * kTcTile + t;
+        tc_inputs(X, n_in, i, N, sm, false);
+        if (!tc_step(S, phase, [&] { issue_layer1(sbase, tmem); })) break;
+        tc_layer1_out(tmem + lane, S, sm, false);
+        if (!tc_step(S, phase, [&] { issue_layer2(sbase, tmem + H); })) break;
+        float y0 = S.b3[0], y1 = S.b3[1];
+#pragma unroll
+        for (int c = 0; c < H / 16; ++c) {
+            float z[16];
+            tc::tmem_ld16(tmem + H + lane + 16 * c, z);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int k = 16 * c + q;
+                const float a2 = tanhf(z[q] + S.b2[k]);
+                y0 = fmaf(S.w3[k], a2, y0);
+                y1 = fmaf(S.w3[H + k], a2, y1);
+            }
         }
-        float y0 = sw[L.b3], y1 = sw[L.b3 + 1];
-        for (int k = 0; k < H; ++k) {
-            float z = sw[L.b2 + k];
-            for (int j = 0; j < H; ++j) z = fmaf(sw[L.w2 + k * H + j], A1[t * kRow + j], z);
-            const float a2 = tanhf(z);
-            A2[t * kRow + k] = a2;
-            y0 = fmaf(sw[L.w3 + k], a2, y0);
-            y1 = fmaf(sw[L.w3 + H + k], a2, y1);
+        if (i < N) {
+            Y[2 * (size_t)i] = y0;
+            Y[2 * (size_t)i + 1] = y1;
         }
-        float d0 = 0.f, d1 = 0.f, l = 0.f, w = 0.f;
+    }
+    tc_teardown(S, tmem, 128, phase, err);
+}
+
+// Training: loss L = sum_i w_i |y_i - t_i|^2 / sum_i w_i over the batch and
+// its gradient, with the bfloat16 roundings of the header comment.  Each CTA
+// takes tiles blockIdx.x, blockIdx.x + gridDim.x, ..., accumulates its
+// weight gradients in TMEM and writes them, with its partial loss, bias-3
+// gradient and weight sum, to part[block]; k_net_reduce adds the blocks in
+// order and normalises.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_net_grad(const __nv_bfloat16* __restrict__ wb, int n_in, const float* __restrict__ X, const float* __restrict__ T,
+           const float* __restrict__ Wt, int N, float* __restrict__ part, int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const NetLayout L = net_layout(n_in);
+    const TcShared S = tc_shared(sm, kSmGradEnd);
+    tc_load_weights(wb, n_in, sm, S, true);
+    const int t = threadIdx.x, warp = t >> 5;
+    // fixed parts of the weight GEMMs' operands: B's ones row (80) and zero
+    // rows (81..95), the zero upper half of A3 and rows 2..15 of B3
+    for (int e = t; e < 16 * kTcTile; e += kTcThreads) {
+        const int r = e / kTcTile, n = e % kTcTile;
+        st_bf16(sm + kSmBS + tc::kmajor_off(80 + r, n, kTcTile), r == 0 ? 1.f : 0.f);
+        if (r >= 2) st_bf16(sm + kSmB3 + tc::kmajor_off(r, n, kTcTile), 0.f);
+    }
+    for (int e = t; e < 64 * kTcTile; e += kTcThreads)
+        st_bf16(sm + kSmA3 + tc::kmajor_off(64 + e / kTcTile, e % kTcTile, kTcTile), 0.f);
+    const uint32_t tmem = tc_setup(S, 256);
+    const uint32_t lane = (uint32_t)(warp * 32) << 16;
+    const uint32_t sbase = tc::smem_u32(sm);
+    const uint32_t dZ = tmem, dZ2 = tmem + H, dG = tmem + 128, dG3 = tmem + 224;
+    uint32_t phase = 0;
+    float acc_l = 0.f, acc_w = 0.f, acc_g0 = 0.f, acc_g1 = 0.f;  // this node slot's loss, weight, gb3
+    const int ntiles = (N + kTcTile - 1) / kTcTile;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int i = tile * kTcTile + t;
+        const bool valid = i < N;
+        tc_inputs(X, n_in, i, N, sm, true);
+        if (!tc_step(S, phase, [&] { issue_layer1(sbase, dZ); })) break;
+        tc_layer1_out(dZ + lane, S, sm, true);
+        if (!tc_step(S, phase, [&] { issue_layer2(sbase, dZ2); })) break;
+        // y, then d3 = 2 w (y - t) (zero for rows past N)
+        float y0 = S.b3[0], y1 = S.b3[1];
+#pragma unroll
+        for (int c = 0; c < H / 16; ++c) {
+            float z[16];
+            tc::tmem_ld16(dZ2 + lane + 16 * c, z);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int k = 16 * c + q;
+                const float a2 = tanhf(z[q] + S.b2[k]);
+                y0 = fmaf(S.w3[k], a2, y0);
+                y1 = fmaf(S.w3[H + k], a2, y1);
+            }
+        }
+        float d0 = 0.f, d1 = 0.f;
         if (valid) {
-            w = Wt[i];
+            const float w = Wt[i];
             const float e0 = y0 - T[2 * (size_t)i], e1 = y1 - T[2 * (size_t)i + 1];
-            l = w * (e0 * e0 + e1 * e1);
+            acc_l += w * (e0 * e0 + e1 * e1);
+            acc_w += w;
             d0 = 2.f * w * e0;
             d1 = 2.f * w * e1;
+            acc_g0 += d0;
+            acc_g1 += d1;
         }
-        D3[2 * t] = d0;
-        D3[2 * t + 1] = d1;
-        RL[t] = l;
-        RW[t] = w;
+        st_bf16(sm + kSmB3 + tc::kmajor_off(0, t, kTcTile), d0);
+        st_bf16(sm + kSmB3 + tc::kmajor_off(1, t, kTcTile), d1);
+        // d2 = (d3 W3) (1 - a2^2): bf(d2) as row t of the d1 GEMM's A and column t
+        // of rows 0..63 of the weight GEMM's A; bf(a2) as column t of A3
+#pragma unroll
+        for (int c = 0; c < H / 16; ++c) {
+            float z[16];
+            tc::tmem_ld16(dZ2 + lane + 16 * c, z);
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 16; q += 2) {
+                float dv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = 16 * c + q + u;
+                    const float a2 = tanhf(z[q + u] + S.b2[k]);
+                    st_bf16(sm + kSmA3 + tc::kmajor_off(k, t, kTcTile), a2);
+                    dv[u] = (d0 * S.w3[k] + d1 * S.w3[H + k]) * (1.f - a2 * a2);
+                    st_bf16(sm + kSmAS + tc::kmajor_off(k, t, kTcTile), dv[u]);
+                }
+                pk[q >> 1] = pack_bf16(dv[0], dv[1]);
+            }
+            st_row16(sm + kSmD2, t, 16 * c, H, pk);
+            st_row16(sm + kSmD2, t, 16 * c + 8, H, pk + 4);
+        }
+        // Z = bf(d2) W2, then d1 = Z (1 - a1^2) with the rounded a1 of layer 2's A
+        if (!tc_step(S, phase, [&] {
+#pragma unroll
+                for (int s = 0; s < H / 16; ++s)
+                    tc::mma_bf16(dZ, desc_k(sbase + kSmD2 + 256 * s, H), desc_k(sbase + kSmW2T + 256 * s, H),
+                                 tc::idesc_bf16(128, H), s > 0);
+            }))
+            break;
+#pragma unroll
+        for (int c = 0; c < H / 16; ++c) {
+            float z[16];
+            tc::tmem_ld16(dZ + lane + 16 * c, z);
+            const uint4 lo = *reinterpret_cast<const uint4*>(sm + kSmA1 + tc::kmajor_off(t, 16 * c, H));
+            const uint4 hi = *reinterpret_cast<const uint4*>(sm + kSmA1 + tc::kmajor_off(t, 16 * c + 8, H));
+            const uint32_t a[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t bits = (q & 1) ? (a[q >> 1] & 0xFFFF0000u) : (a[q >> 1] << 16);
+                const float a1 = __uint_as_float(bits);
+                st_bf16(sm + kSmAS + tc::kmajor_off(H + 16 * c + q, t, kTcTile), z[q] * (1.f - a1 * a1));
+            }
+        }
+        // weight gradients, accumulated over the tiles in TMEM
+        const uint32_t acc = it > 0 ? 1u : 0u;
+        if (!tc_step(S, phase, [&] {
+#pragma unroll
+                for (int s = 0; s < kTcTile / 16; ++s) {
+                    tc::mma_bf16(dG, desc_k(sbase + kSmAS + 256 * s, kTcTile), desc_k(sbase + kSmBS + 256 * s, kTcTile),
+                                 tc::idesc_bf16(128, 96), acc | (s > 0));
+                    tc::mma_bf16(dG3, desc_k(sbase + kSmA3 + 256 * s, kTcTile),
+                                 desc_k(sbase + kSmB3 + 256 * s, kTcTile), tc::idesc_bf16(128, 16), acc | (s > 0));
+                }
+            }))
+            break;
     }
-    __syncthreads();
     float* P = part + (size_t)blockIdx.x * (L.total + 2);
-    // layer 3: dW3[k][c] = sum_n D3[n][c] a2[n][c]; db3
-    for (int e = t; e < 2 * H + 2; e += kNetBlock) {
-        float s = 0.f;
-        if (e < 2 * H) {
-            const int c = e / H, k = e - c * H;
-            for (int n = 0; n < kNetBlock; ++n) s = fmaf(D3[2 * n + c], A2[n * kRow + k], s);
-            P[L.w3 + e] = s;
-        } else {
-            const int c = e - 2 * H;
-            for (int n = 0; n < kNetBlock; ++n) s += D3[2 * n + c];
-            P[L.b3 + c] = s;
-        }
-    }
-    __syncthreads();
-    // delta2 = (1 - a2^2) W3^T d3, in place of a2
-    for (int k = 0; k < H; ++k) {
-        const float a2 = A2[t * kRow + k];
-        A2[t * kRow + k] = (1.f - a2 * a2) * (sw[L.w3 + k] * D3[2 * t] + sw[L.w3 + H + k] * D3[2 * t + 1]);
-    }
-    __syncthreads();
-    // layer 2: dW2[k][j] = sum_n delta2[n][k] a1[n][j]; db2
-    for (int e = t; e < H * H + H; e += kNetBlock) {
-        float s = 0.f;
-        if (e < H * H) {
-            const int k = e / H, j = e - k * H;
-            for (int n = 0; n < kNetBlock; ++n) s = fmaf(A2[n * kRow + k], A1[n * kRow + j], s);
-            P[L.w2 + e] = s;
-        } else {
-            const int k = e - H * H;
-            for (int n = 0; n < kNetBlock; ++n) s += A2[n * kRow + k];
-            P[L.b2 + k] = s;
-        }
-    }
-    __syncthreads();
-    // delta1 = (1 - a1^2) W2^T delta2, in place of a1
-    {
-        float d1[H];
+    if (*S.err == 0 && it > 0) {
+        // TMEM -> this CTA's partial gradient
+        float v[16];
+        if (warp < 2) {  // rows k = 0..63: gW2[k][.], gb2[k], gW3[.][k]
+            const int k = t;
 #pragma unroll
-        for (int j = 0; j < H; ++j) d1[j] = 0.f;
-        for (int k = 0; k < H; ++k) {
-            const float d2 = A2[t * kRow + k];
+            for (int c = 0; c < H / 16; ++c) {
+                tc::tmem_ld16(dG + lane + 16 * c, v);
 #pragma unroll
-            for (int j = 0; j < H; ++j) d1[j] = fmaf(sw[L.w2 + k * H + j], d2, d1[j]);
+                for (int q = 0; q < 16; ++q) P[L.w2 + k * H + 16 * c + q] = v[q];
+            }
+            tc::tmem_ld16(dG + lane + 80, v);
+            P[L.b2 + k] = v[0];
+            tc::tmem_ld16(dG3 + lane, v);
+            P[L.w3 + k] = v[0];
+            P[L.w3 + H + k] = v[1];
+        } else {  // rows 64 + j: gW1[j][.], gb1[j]
+            const int j = t - 64;
+            tc::tmem_ld16(dG + lane + 64, v);
+            for (int f = 0; f < n_in; ++f) P[L.w1 + j * n_in + f] = v[f];
+            tc::tmem_ld16(dG + lane + 80, v);
+            P[L.b1 + j] = v[0];
         }
+    }
+    // loss, weight and gb3 sums: warps, then the warps in order
 #pragma unroll
-        for (int j = 0; j < H; ++j) {
-            const float a1 = A1[t * kRow + j];
-            A1[t * kRow + j] = (1.f - a1 * a1) * d1[j];
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_l += __shfl_xor_sync(0xffffffffu, acc_l, o);
+        acc_w += __shfl_xor_sync(0xffffffffu, acc_w, o);
+        acc_g0 += __shfl_xor_sync(0xffffffffu, acc_g0, o);
+        acc_g1 += __shfl_xor_sync(0xffffffffu, acc_g1, o);
+    }
+    if ((t & 31) == 0) {
+        S.part[4 * warp] = acc_l;
+        S.part[4 * warp + 1] = acc_w;
+        S.part[4 * warp + 2] = acc_g0;
+        S.part[4 * warp + 3] = acc_g1;
     }
     __syncthreads();
-    // layer 1: dW1[j][f] = sum_n delta1[n][j] x[n][f]; db1
-    for (int e = t; e < H * n_in + H; e += kNetBlock) {
-        float s = 0.f;
-        if (e < H * n_in) {
-            const int j = e / n_in, f = e - j * n_in;
-            for (int n = 0; n < kNetBlock; ++n) s = fmaf(A1[n * kRow + j], SX[n * kNetMaxIn + f], s);
-            P[L.w1 + e] = s;
-        } else {
-            const int j = e - H * n_in;
-            for (int n = 0; n < kNetBlock; ++n) s += A1[n * kRow + j];
-            P[L.b1 + j] = s;
-        }
-    }
     if (t == 0) {
-        float s = 0.f, sw_ = 0.f;
-        for (int n = 0; n < kNetBlock; ++n) {
-            s += RL[n];
-            sw_ += RW[n];
+        float l = 0.f, w = 0.f, g0 = 0.f, g1 = 0.f;
+        for (int k = 0; k < kTcThreads / 32; ++k) {
+            l += S.part[4 * k];
+            w += S.part[4 * k + 1];
+            g0 += S.part[4 * k + 2];
+            g1 += S.part[4 * k + 3];
         }
-        P[L.total] = s;
-        P[L.total + 1] = sw_;
+        P[L.b3] = g0;
+        P[L.b3 + 1] = g1;
+        P[L.total] = l;
+        P[L.total + 1] = w;
     }
+    tc_teardown(S, tmem, 256, phase, err);
 }
 
 // g[p] = (sum over blocks of part[block][p], in block order) / (sum of the
@@ -260,10 +503,6 @@ __global__ void k_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict
     if (p < n) wb[p] = __float2bfloat16_rn(w[p]);
 }
 
-size_t net_grad_smem(int n_in) {
-    const NetLayout L = net_layout(n_in);
-    return sizeof(float) * (((L.total + 3) & ~3) + 2 * kNetBlock * kRow + kNetBlock * kNetMaxIn + 4 * kNetBlock);
-}
 
 }  // namespace bie
 
@@ -280,6 +519,8 @@ struct bie_net {
     float* g = nullptr;             // n_params + 1 (loss)
     float* part = nullptr;          // per-block partial gradients
     int part_blocks = 0;
+    int sms = 0;                    // streaming multiprocessors of the device
+    int* tc_err = nullptr;          // set by a kernel whose tensor-core wait timed out
     long long adam_t = 0;
     std::string err;
 };
@@ -300,9 +541,24 @@ int net_fail(bie_net* n, int code, const std::string& m) {
     } while (0)
 
 void net_free(bie_net* n) {
-    void* ptrs[] = {n->w, n->wb, n->m1, n->m2, n->g, n->part};
+    void* ptrs[] = {n->w, n->wb, n->m1, n->m2, n->g, n->part, n->tc_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+}
+
+// the forward's grid: at most 3 CTAs per SM (3 x 128 TMEM columns), each
+// over every gridDim-th tile
+int forward_grid(const bie_net* n, int N) {
+    return std::min((N + kTcTile - 1) / kTcTile, 3 * std::max(1, n->sms));
+}
+
+// waits for the network's stream; an error if a tensor-core wait timed out
+int check_tc(bie_net* n) {
+    int flag = 0;
+    NET_CUDA(n, cudaMemcpyAsync(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NET_CUDA(n, cudaStreamSynchronize(n->stream));
+    if (flag) return net_fail(n, BIE_ECUDA, "tensor-core completion wait timed out");
+    return BIE_OK;
 }
 
 int ensure_part(bie_net* n, int blocks) {
@@ -341,12 +597,14 @@ int bie_net_init(bie_net** out, int32_t n_in, int32_t device) {
     al((void**)&n->m1, n->n_params * sizeof(float));
     al((void**)&n->m2, n->n_params * sizeof(float));
     al((void**)&n->g, (n->n_params + 1) * sizeof(float));
+    al((void**)&n->tc_err, sizeof(int));
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = BIE_ECUDA;
-    if (!rc) {
-        const size_t smem = net_grad_smem(n_in);
-        if (cudaFuncSetAttribute(k_net_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            rc = BIE_ECUDA;
-    }
+    if (!rc && cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = BIE_ECUDA;
+    if (!rc && (cudaFuncSetAttribute(k_net_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(k_net_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem) !=
+                    cudaSuccess))
+        rc = BIE_ECUDA;
     if (rc) {
         net_free(n);
         delete n;
@@ -405,28 +663,29 @@ int bie_net_forward(bie_net* n, const float* X, int32_t N, float* Y) {
     if (!n || (N > 0 && (!X || !Y)) || N < 0) return BIE_EINVAL;
     if (N == 0) return BIE_OK;
     NET_CUDA(n, cudaSetDevice(n->device));
-    const size_t smem = n->n_params * sizeof(float);
-    k_net_forward<<<(N + 127) / 128, 128, smem, n->stream>>>(n->wb, n->n_in, X, N, Y);
+    NET_CUDA(n, cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->stream));
+    k_net_forward<<<forward_grid(n, N), kTcThreads, kFwdSmem, n->stream>>>(n->wb, n->n_in, X, N, Y, n->tc_err);
     NET_CUDA(n, cudaGetLastError());
-    NET_CUDA(n, cudaStreamSynchronize(n->stream));
-    return BIE_OK;
+    return check_tc(n);
 }
 
 int bie_net_loss_grad(bie_net* n, const float* X, const float* T, const float* W, int32_t N, float* grad,
                       double* loss) {
     if (!n || !X || !T || !W || N <= 0) return BIE_EINVAL;
     NET_CUDA(n, cudaSetDevice(n->device));
-    const int blocks = (N + kNetBlock - 1) / kNetBlock;
+    // one CTA per SM at most (its shared memory and 256 TMEM columns), each
+    // over every gridDim-th tile
+    const int blocks = std::min((N + kTcTile - 1) / kTcTile, std::max(1, n->sms));
     if (int rc = ensure_part(n, blocks)) return rc;
-    const size_t smem = net_grad_smem(n->n_in);
-    k_net_grad<<<blocks, kNetBlock, smem, n->stream>>>(n->wb, n->n_in, X, T, W, N, n->part);
+    NET_CUDA(n, cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->stream));
+    k_net_grad<<<blocks, kTcThreads, kGradSmem, n->stream>>>(n->wb, n->n_in, X, T, W, N, n->part, n->tc_err);
     NET_CUDA(n, cudaGetLastError());
     k_net_reduce<<<(n->n_params + 256) / 256, 256, 0, n->stream>>>(n->part, blocks, n->n_params, n->g);
     NET_CUDA(n, cudaGetLastError());
     if (grad) NET_CUDA(n, cudaMemcpyAsync(grad, n->g, n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     float l = 0;
     NET_CUDA(n, cudaMemcpyAsync(&l, n->g + n->n_params, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
-    NET_CUDA(n, cudaStreamSynchronize(n->stream));
+    if (int rc = check_tc(n)) return rc;
     if (loss) *loss = l;
     return BIE_OK;
 }
@@ -452,8 +711,7 @@ namespace bie {
 
 // device-side inference for the solver (no synchronisation)
 int net_forward_async(bie_ctx* c, const bie_net* n, const float* X, int N, float* Y) {
-    const size_t smem = n->n_params * sizeof(float);
-    k_net_forward<<<(N + 127) / 128, 128, smem, c->stream>>>(n->wb, n->n_in, X, N, Y);
+    k_net_forward<<<forward_grid(n, N), kTcThreads, kFwdSmem, c->stream>>>(n->wb, n->n_in, X, N, Y, n->tc_err);
     BIE_LAUNCH(c, "k_net_forward");
     return BIE_OK;
 }

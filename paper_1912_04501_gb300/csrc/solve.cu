@@ -230,6 +230,8 @@ static int set_active(bie_ctx* c, const std::vector<char>& on) {
 // scratch of the augmentation set-up, after the normalisation factors and the
 // per-cell norms: squared norms before / after projection, projection
 // coefficients of the two passes over r and of the orthonormalisation
+constexpr double kAugMinRatio = 1e-4;  // smallest kept |projected| / |original| of an augmentation image
+
 static double* aug_scratch(bie_ctx* c, int slot) {
     const size_t nc = c->ncell;
     switch (slot) {
@@ -242,14 +244,16 @@ static double* aug_scratch(bie_ctx* c, int slot) {
 }
 
 // f = 1 / |c| per cell from squared norms n0 (before) and n1 (after
-// projection); 0 when the direction is (numerically) in the span of the
-// earlier ones or zero
+// projection); 0 when the direction is zero or within a relative 1e-4 of the
+// span of the earlier ones: normalising the small remainder would magnify
+// the error of A U (single-precision pairs: ~1e-7 relative) past 1e-3 and
+// break the relation A U~ = C~ the augmented cycle relies on
 __global__ void k_aug_fac(const double* __restrict__ n0, const double* __restrict__ n1, double* __restrict__ f,
                           int nc) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nc) return;
     const double a = n0[q], b = n1[q];
-    f[q] = (isfinite(b) && b > 0 && b > 1e-20 * a) ? 1.0 / sqrt(b) : 0.0;
+    f[q] = (isfinite(b) && b > 0 && b > kAugMinRatio * kAugMinRatio * a) ? 1.0 / sqrt(b) : 0.0;
 }
 
 // Direction i of (Ct, Ut) per cell: project out directions 0 .. i-1 of Ct

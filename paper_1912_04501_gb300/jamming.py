@@ -29,13 +29,17 @@ from . import bie, workloads
 TOLERANCES = (1e-10, 1e-9, 1e-8)
 
 
+MIN_GAP = 1e-6  # a smaller gap between the bodies ends the run (BIE_ECOLLIDE): they touch
+
+
 def _context(cell, tol):
-    return bie.Context(cell, precision=bie.BIE_MIXED, gmres_max=1000, max_refine=40, precond=1, gmres_tol=tol)
+    return bie.Context(cell, precision=bie.BIE_MIXED, gmres_max=1000, max_refine=40, precond=1, gmres_tol=tol,
+                       min_gap=MIN_GAP)
 
 
 def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print):
-    """Time steps until t_end, a mu_eff above mu_stop, or a step the solver
-    cannot finish; returns the record.  Steps solve to a relative residual
+    """Time steps until t_end, a mu_eff above mu_stop, bodies closer than
+    MIN_GAP, or a step the solver cannot finish; returns the record.  Steps solve to a relative residual
     of 1e-10; when the gaps get so small that a solve stops above it (the
     double-float residual of the near-contact terms, a few 1e-10 of the
     right-hand side), the run continues from the same state at the next
@@ -90,7 +94,7 @@ def fit_blowup(t, mu, window):
     from scipy.optimize import least_squares
     t = np.asarray(t, dtype=np.float64)
     mu = np.asarray(mu, dtype=np.float64)
-    sel = (t >= window[0]) & (t <= window[1])
+    sel = (t >= window[0]) & (t <= window[1]) & (mu > 0)
     ts, ms = t[sel], mu[sel]
     if ts.size < 5:
         raise ValueError("too few points in the fitting window")

@@ -6,7 +6,8 @@ shaped like the 25-ellipse cell (seeded placements distinct from the
 evaluation seeds) are stepped forward in time; before every step the node
 features of the context are recorded (bie_features), after it the converged
 density, and the training target is the density change over the step in
-units of mu |gamma| dt.  The loss weights each node by its quadrature weight,
+units of mu |gamma| dt (or, with --target second, the part of it beyond the
+linear extrapolation of the last two densities).  The loss weights each node by its quadrature weight,
 so that it measures the change in the L2 norm on the curves.
 
 All arithmetic runs in the library's kernels (features, forward, gradient,
@@ -30,6 +31,7 @@ DEFAULT_PARAMS = os.path.join(HERE, "warm_net_params.npy")
 TRAIN_SEEDS = list(range(100, 112))
 TRAIN_STEPS = 20
 TRAIN = dict(epochs=30, batch=8192, lr=2e-3, lr_end=1e-4, seed=0)
+TARGET = "change"
 
 
 def init_params(n_in=bie.BIE_NET_FEATURES, hidden=bie.BIE_NET_HIDDEN, seed=0, out_scale=1e-2):
@@ -54,11 +56,16 @@ def training_cell(seed, n_bodies=25, phi=0.3, nodes=256, gap=1e-2):
     return cell
 
 
-def generate(seeds, steps, dt=1e-3, lead=2, cell_fn=training_cell, log=None):
+def generate(seeds, steps, dt=1e-3, lead=2, cell_fn=training_cell, log=None, target=None):
     """Run each seeded cell `lead` steps (so two earlier densities exist),
     then record `steps` (features, target, weight) triples.  Returns host
     arrays X (M x F float32), T (M x 2 float32), W (M float32) and the number
-    of solves."""
+    of solves.  target "change" (default TARGET): the density change over the
+    step; "second": the change beyond the linear extrapolation of the last
+    two densities, sigma_{n+1} - sigma_n - (sigma_n - sigma_{n-1}) dt / dt_prev,
+    the part of the new density the recycled directions (sigma_n and its last
+    change) do not span; both in units of mu |gamma| dt."""
+    target = target or TARGET
     Xs, Ts, Ws = [], [], []
     solves = 0
     for seed in seeds:
@@ -69,11 +76,15 @@ def generate(seeds, steps, dt=1e-3, lead=2, cell_fn=training_cell, log=None):
         for _ in range(steps):
             X = ctx.features()
             w = ctx.nodes()[2]
-            s0 = ctx.get_state()["sigma"]
+            st = ctx.get_state()
+            s0 = st["sigma"]
             ctx.step(dt, 1)
             s1 = ctx.get_state()["sigma"]
+            d = s1 - s0
+            if target == "second":
+                d = d - (s0 - st["sigma_prev2"]) * (dt / st["dt_prev"])
             Xs.append(X)
-            Ts.append(((s1 - s0) / scale).reshape(-1, 2).astype(np.float32))
+            Ts.append((d / scale).reshape(-1, 2).astype(np.float32))
             Ws.append(w.astype(np.float32))
             solves += 1
         ctx.close()
@@ -168,15 +179,29 @@ def default_net(device=0):
 
 
 def main():
-    ap = argparse.ArgumentParser(description="train the warm-start network on solver-generated densities")
+    ap = argparse.ArgumentParser(description="train the warm-start network on solver-generated densities, or "
+                                             "compare the warm starts on a workload (--evaluate)")
     ap.add_argument("--out", default=DEFAULT_PARAMS)
     ap.add_argument("--seeds", type=int, nargs="*", default=TRAIN_SEEDS)
     ap.add_argument("--steps", type=int, default=TRAIN_STEPS)
+    ap.add_argument("--epochs", type=int, default=TRAIN["epochs"])
+    ap.add_argument("--evaluate", nargs="*", default=None,
+                    help="workloads (e.g. config2 config5) on which to compare the starts with --params")
+    ap.add_argument("--params", default=DEFAULT_PARAMS)
+    ap.add_argument("--eval-steps", type=int, default=10)
+    ap.add_argument("--target", choices=("change", "second"), default=TARGET)
     a = ap.parse_args()
-    X, T, W, solves = generate(a.seeds, a.steps, log=print)
+    if a.evaluate is not None:
+        import json
+        for name in a.evaluate:
+            ev = evaluate(getattr(workloads, name)(), load_params(a.params), a.eval_steps, modes=(3, 2))
+            print(json.dumps({"workload": name, "params": os.path.basename(a.params), "steps": a.eval_steps,
+                              "recycled": ev[3], "learned": ev[2]}), flush=True)
+        return
+    X, T, W, solves = generate(a.seeds, a.steps, log=print, target=a.target)
     net = bie.Net()
     net.set_params(init_params(seed=0))
-    res = train(net, X, T, W, log=print, **TRAIN)
+    res = train(net, X, T, W, log=print, **dict(TRAIN, epochs=a.epochs))
     np.save(a.out, net.get_params())
     print(f"{solves} solves, {X.shape[0]} nodes; held-out loss / zero predictor = {res['val_rel']:.3g}; "
           f"wrote {a.out}")

@@ -65,3 +65,51 @@ def test_round_bf16():
     assert r[2] == np.float32(1.0 + 2 ** -7)
     assert (r.view(np.uint32) & 0xFFFF == 0).all()
     assert np.abs(r - a).max() <= np.abs(a).max() * 2 ** -8
+
+
+def test_bf16_forward_reduces_to_exact_when_rounding_is_the_identity():
+    """Inputs that bfloat16 represents and a first layer whose activations it
+    represents (W1 = 0, b1 = atanh(v) with v bfloat16 values): the rounded
+    network is the exact one, whatever the other layers."""
+    rng = np.random.default_rng(7)
+    n_in, H, N = 5, 8, 9
+    p = rng.standard_normal(mlp.n_params(n_in, H)) * 0.5
+    W1, b1 = mlp.unpack(p, n_in, H)[:2]
+    v = mlp.round_bf16(rng.uniform(-0.9, 0.9, H).astype(np.float32)).astype(np.float64)
+    W1[:] = 0.0
+    b1[:] = np.arctanh(v)
+    X = mlp.round_bf16(rng.standard_normal((N, n_in)).astype(np.float32)).astype(np.float64)
+    a1 = mlp.hidden1(p, X, H, bf16=True)
+    assert np.abs(a1 - v).max() < 1e-15
+    assert np.array_equal(mlp.round_bf16(a1.astype(np.float32)), np.broadcast_to(v.astype(np.float32), (N, H)))
+    y, yb = mlp.forward(p, X, H), mlp.forward(p, X, H, bf16=True)
+    assert np.abs(y - yb).max() < 1e-14 * np.abs(y).max()
+
+
+def test_bf16_forward_and_gradient_within_rounding_bounds():
+    """The rounded network differs from the exact one by the bfloat16
+    rounding (relative 2^-9 per rounded value): the outputs by at most
+    |W3| |W2| (2^-9 |a1| + |W1| 2^-9 |x|) entrywise (tanh' <= 1), the
+    gradient by a few 2^-8 of its scale; a transposed operand or a dropped
+    term is an O(1) change."""
+    n_in, H, N = 6, 16, 40
+    rng = np.random.default_rng(11)
+    p = rng.standard_normal(mlp.n_params(n_in, H)) * 0.4
+    X = rng.standard_normal((N, n_in))
+    T = rng.standard_normal((N, 2))
+    w = rng.uniform(0.5, 2.0, N)
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, n_in, H)
+    a1 = np.tanh(X @ W1.T + b1)
+    bound = (2.0 ** -9 * np.abs(a1) + 2.0 ** -9 * np.abs(X) @ np.abs(W1).T) @ np.abs(W2).T @ np.abs(W3).T
+    dy = np.abs(mlp.forward(p, X, H, bf16=True) - mlp.forward(p, X, H))
+    assert (dy <= 1.01 * bound + 1e-15).all()
+    assert dy.max() > 0.0
+    L, g = mlp.loss_grad(p, X, T, w, H)
+    Lb, gb = mlp.loss_grad(p, X, T, w, H, bf16=True)
+    assert abs(Lb - L) <= 1e-2 * L
+    sizes = [H * n_in, H, H * H, H, 2 * H, 2]
+    o = 0
+    for k in sizes:  # every parameter block: the rounded gradient tracks the exact one
+        ge, gr = g[o:o + k], gb[o:o + k]
+        assert np.abs(gr - ge).max() <= 2e-2 * np.abs(ge).max(), o
+        o += k
