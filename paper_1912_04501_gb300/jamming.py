@@ -87,6 +87,64 @@ def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print):
     return rec
 
 
+def _advance(ctx, make, dt, t, t_end, tol_k, rec=None, log=None, tag=""):
+    """Step ctx from t to t_end, falling back to looser TOLERANCES when a
+    solve stops above its tolerance (make(tol) builds a fresh context);
+    returns (ctx, t, tol_k, stop) and appends (t, mu_eff) to rec."""
+    while t < t_end - 0.5 * dt:
+        try:
+            mu, _ = ctx.step(dt, 1)
+        except bie.BieError as e:
+            if e.code == bie.BIE_ENOCONV and tol_k + 1 < len(TOLERANCES):
+                st = ctx.get_state()
+                ctx.close()
+                tol_k += 1
+                ctx = make(TOLERANCES[tol_k])
+                ctx.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"],
+                              st["dt_prev"], st["d2"])
+                continue
+            return ctx, t, tol_k, str(e)
+        if rec is not None:
+            rec.append((t, float(mu[0])))
+            if log:
+                log(f"{tag} t = {t:.5f} mu_eff = {mu[0]:.6g} (tolerance {TOLERANCES[tol_k]:g})")
+        t += dt
+    return ctx, t, tol_k, "t_end"
+
+
+def convergence_check(example=5, n=2500, dt=5e-4, t0=0.39, t1=0.405, log=print):
+    """mu_eff(t) on [t0, t1] from the state the run reaches at t0, four ways:
+    as run (mixed precision), with plain FP64 solves, with 1.6 n nodes per
+    body (the bodies' positions and orientations carried over), and with
+    dt / 2.  Returns {variant: [(t, mu_eff), ...], "stop": {...}}."""
+    cell = workloads.stars(example, n)
+    ctx = _context(cell, TOLERANCES[0])
+    ctx, t, tol_k, stop = _advance(ctx, lambda tol: _context(cell, tol), dt, 0.0, t0, 0)
+    st = ctx.get_state()
+    ctx.close()
+    out = {"stop": {}}
+    n2 = int(round(1.6 * n / 8)) * 8
+    variants = (("mixed", cell, bie.BIE_MIXED, dt, True), ("fp64", cell, bie.BIE_FP64, dt, True),
+                (f"n{n2}", workloads.stars(example, n2), bie.BIE_MIXED, dt, False),
+                ("dt/2", cell, bie.BIE_MIXED, dt / 2, True))
+    for tag, c, prec, h, history in variants:
+        def make(tol, c=c, prec=prec):
+            return bie.Context(c, precision=prec, gmres_max=1000, max_refine=40, precond=1, gmres_tol=tol,
+                               min_gap=MIN_GAP)
+        ctx = make(TOLERANCES[tol_k])
+        if history:
+            ctx.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"],
+                          st["dt_prev"], st["d2"])
+        else:
+            ctx.set_state(st["t"], st["e2"], st["xc"], st["theta"])
+        rec = []
+        ctx, _, _, stop = _advance(ctx, make, h, st["t"], t1, tol_k, rec, log, tag)
+        ctx.close()
+        out[tag] = rec
+        out["stop"][tag] = stop
+    return out
+
+
 def fit_blowup(t, mu, window):
     """Nonlinear least squares for mu ~ c |t - t*|^-beta (Eq. blowup) on
     window = (t0, t1): the residual is taken in log mu; returns c, t*, beta
@@ -121,7 +179,19 @@ def main():
     ap.add_argument("--n", type=int, default=2500)
     ap.add_argument("--t-end", type=float, default=0.5)
     ap.add_argument("--out", default=None, help="directory for the mu_eff(t) records (JSON)")
+    ap.add_argument("--check", nargs=2, type=float, default=None, metavar=("T0", "T1"),
+                    help="instead of the runs: mu_eff on [T0, T1] as run, with FP64 solves, 1.6x the nodes "
+                         "and half the step, all from the state at T0")
     a = ap.parse_args()
+    if a.check:
+        for ex in a.example:
+            res = convergence_check(ex, a.n, t0=a.check[0], t1=a.check[1], log=None)
+            print(json.dumps({"example": ex, **res}), flush=True)
+            if a.out:
+                os.makedirs(a.out, exist_ok=True)
+                with open(os.path.join(a.out, f"jamming_check{ex}.json"), "w") as f:
+                    json.dump(res, f)
+        return
     for ex in a.example:
         rec = run(ex, a.n, t_end=a.t_end)
         out = dict(example=ex, n=a.n, steps=len(rec["t"]), stop=rec["stop"],

@@ -181,9 +181,15 @@ def test_augmented_start_meets_tolerance(mode):
 
 
 def test_trained_network_gain():
-    """Train on a few small seeded suspensions, then on a held-out one: the
-    network predicts the density change better than predicting no change, and
-    the learned start needs no more iterations than a zero start."""
+    """Train on a few small seeded suspensions, then step a held-out one from
+    the same trajectory point with each start, all to the same 1e-10
+    residual: the network predicts the density change better than predicting
+    no change; the learned start (recycled directions + the network's)
+    needs fewer iterations than a zero start and no more than 15% above the
+    recycled directions alone (warm_start 3) -- the recycled directions
+    already span most of a step's change, so the network's direction adds
+    little on these cells (the 400- and 25-ellipse figures are in the
+    design notes)."""
     def small(seed):
         c = workloads.small_cell(n_bodies=6, nodes=128, seed=seed, phi=0.3, gap=2e-2)
         return c
@@ -192,6 +198,11 @@ def test_trained_network_gain():
     net.set_params(learn.init_params(seed=0))
     res = learn.train(net, X, T, W, epochs=40, batch=2048, lr=3e-3, lr_end=3e-4)
     assert res["val_rel"] < 0.9, res
-    ev = learn.evaluate(small(24), net.get_params(), steps=4, modes=(0, 2))
-    assert ev[2]["mean_iterations"] <= ev[0]["mean_iterations"], ev
+    ev = learn.evaluate(small(24), net.get_params(), steps=4, modes=(0, 3, 2))
+    for m in (0, 3, 2):
+        assert max(ev[m]["rel_residual"]) <= 1e-10
+    print("iterations per step: zero %.1f, recycled %.1f, learned %.1f" % tuple(
+        ev[m]["mean_iterations"] for m in (0, 3, 2)))
+    assert ev[2]["mean_iterations"] < ev[0]["mean_iterations"], ev
+    assert ev[2]["mean_iterations"] <= 1.15 * ev[3]["mean_iterations"], ev
     net.close()
