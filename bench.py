@@ -70,6 +70,7 @@ def parse():
                    help="periodizer of the timed context: 9 = 3x3 images of every body (the headline), 4 = the "
                         "paper's doubled cell (four images per node)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the 64-cell ensemble's extra key")
     p.add_argument("--mixed-only", action="store_true",
                    help="time the mixed-precision steps only (no comparisons, no end-to-end loop); "
                         "used for kernel launch lists")
@@ -376,7 +377,7 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1912_04501_gb300 import bie, learn
+    from paper_1912_04501_gb300 import bie, learn, workloads
 
     torch.cuda.set_device(local)
     dist = None
@@ -620,6 +621,35 @@ def main():
                  "value": 9.0 * N2 * N2 * (r2["applies32"] + r2["applies64"]) / (sum(r2["ms"]) / 1e3) / 1e9,
                  "iterations_mean": statistics.mean(r2["iters"])}
 
+    # the 64-cell ensemble (uneven cells in one context; its near sums from the
+    # persistent work queue), measured the same way: an extra key
+    batch = None
+    if world == 1 and not args.no_batch:
+        cells4 = workloads.config4()
+        N4 = sum(sum(b["n"] for b in c["bodies"]) for c in cells4)
+        pairs4 = sum(9.0 * sum(b["n"] for b in c["bodies"]) ** 2 for c in cells4)
+        cb = bie.Context(cells4, precision=bie.BIE_MIXED, device=local, warm_start=mode)
+        cb.set_stream(stream.cuda_stream)
+        if net is not None:
+            cb.set_warm_net(net)
+        for _ in range(3):
+            cb.step(cells4[0]["dt"], 1)
+        cb.profile(True)
+        r4 = timed_steps(cb, stream, cells4[0]["dt"], 5, flush)
+        p4 = cb.profile_read()
+        cb.profile(False)
+        cb.set_warm_net(None)
+        cb.close()
+        ms4 = statistics.mean(r4["ms"])
+        batch = {"workload": "64 cells, 5-50 ellipses each, phi U[0.1, 0.4], AR U[1,3], gap>=1e-2, 128-256 "
+                             "nodes/body (N=%d), dt 1e-3, mixed+learned, lockstep solves" % N4,
+                 "ms_per_step": ms4, "iterations_mean": statistics.mean(r4["iters"]),
+                 "value": pairs4 * (r4["applies32"] + r4["applies64"]) / (sum(r4["ms"]) / 1e3) / 1e9,
+                 "near32_ms_per_launch": p4["near32_ms"] / max(1, p4["near32_launches"]),
+                 "near32_gpairs_per_s": pairs4 / (p4["near32_ms"] / max(1, p4["near32_launches"]) / 1e3) / 1e9
+                 if p4["near32_launches"] else None,
+                 "near_sum": "persistent work queue (k_near32r_queue), items sorted longest first"}
+
     # rooflines: measured CUDA-core FMA throughput of this device
     peak = bie.alu_peak(local, stream.cuda_stream)
     fp32_peak = max(peak["ffma"], peak["ffma2"])
@@ -697,6 +727,7 @@ def main():
             "e2e": {"value": e2e_pairs / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "config2": small,
+            "config4": batch,
             "utilde": utilde,
             "gpu_launches": prof["launches"],
             "clocks": clk,
