@@ -1469,7 +1469,7 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
     const int sl = kNear32ShapeList[c->shape32].ctas * c->sms;
     // one case per entry of kNear32ShapeList (packed, targets per thread, CTAs per SM)
     switch (c->shape32) {
-        case 0: near32_variant<2, 5, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
+        case 0: near32_variant<BIE_NEAR32_TPT, BIE_NEAR32_CTAS, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
         case 1: near32_variant<1, 8, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
         case 2: near32_variant<3, 4, true>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part, q, sl); break;
         case 3: near32_variant<3, 4, false>(comp, rows, it.count, c->stream, it.items, c->cells, c->tgt32, src, part); break;
@@ -1480,7 +1480,7 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
 }
 #define BIE_SHAPE_IS(k, p, t, m) \
     (kNear32ShapeList[k].packed == (p) && kNear32ShapeList[k].tpt == (t) && kNear32ShapeList[k].ctas == (m))
-static_assert(kNear32Shapes == 5 && BIE_SHAPE_IS(0, 1, 2, 5) && BIE_SHAPE_IS(1, 1, 1, 8) && BIE_SHAPE_IS(2, 1, 3, 4) &&
+static_assert(kNear32Shapes == 5 && BIE_SHAPE_IS(0, 1, BIE_NEAR32_TPT, BIE_NEAR32_CTAS) && BIE_SHAPE_IS(1, 1, 1, 8) && BIE_SHAPE_IS(2, 1, 3, 4) &&
                   BIE_SHAPE_IS(3, 0, 3, 4) && BIE_SHAPE_IS(4, 0, 2, 5),
               "launch_near32's cases must match kNear32ShapeList");
 #undef BIE_SHAPE_IS

@@ -48,7 +48,15 @@ struct Near32Shape {
     int packed, tpt, ctas;
 };
 constexpr int kNear32Shapes = 5;
-constexpr Near32Shape kNear32ShapeList[kNear32Shapes] = {{1, 2, 5}, {1, 1, 8}, {1, 3, 4}, {0, 3, 4}, {0, 2, 5}};
+// the default shape (entry 0) can be rebuilt with other values for measurement
+#ifndef BIE_NEAR32_TPT
+#define BIE_NEAR32_TPT 2
+#endif
+#ifndef BIE_NEAR32_CTAS
+#define BIE_NEAR32_CTAS 5
+#endif
+constexpr Near32Shape kNear32ShapeList[kNear32Shapes] = {
+    {1, BIE_NEAR32_TPT, BIE_NEAR32_CTAS}, {1, 1, 8}, {1, 3, 4}, {0, 3, 4}, {0, 2, 5}};
 static_assert(kNear32Shapes == BIE_NEAR32_SHAPES, "shape count of the public header");
 constexpr int kNear32CompChunk = 2048;  // splits with more sources use compensated tile accumulation
 constexpr int kDiscSplits = 8;        // source splits per wall point of the wall-discrepancy kernel
