@@ -57,6 +57,9 @@ FLOPS_PER_PAIR_ROWS = 14.0 + 4.0 / 3.0
 # FP32 instructions per pair of k_near32r (an FMA counts once): the FP32
 # pipe's issue limit is half the FMA flop peak in these units
 OPS_PER_PAIR_ROWS = 9.0 + 4.0 / 3.0
+# the doubled-cell kernel shares the r_y terms between a node's two images
+# at one lattice row (dm = 0, 1): 14 per pair + 4 per two pairs
+FLOPS_PER_PAIR_UROWS = 14.0 + 4.0 / 2.0
 
 
 def parse():
@@ -525,8 +528,8 @@ def main():
               "iterations_mean": statistics.mean(ru["iters"]), "mu_eff_last": ru["mu"][-1],
               "near32_ms_per_launch": pu["near32_ms"] / max(1, pu["near32_launches"]),
               "neardf_ms_per_launch": pu["neardf_ms"] / max(1, pu["neardf_launches"]),
-              "near32_tflops": FLOPS_PER_PAIR * pairs_u / (pu["near32_ms"] / max(1, pu["near32_launches"]) / 1e3)
-              / 1e12 if pu["near32_launches"] else None}
+              "near32_tflops": (FLOPS_PER_PAIR_UROWS if cell["e1"][1] == 0.0 else FLOPS_PER_PAIR) * pairs_u
+              / (pu["near32_ms"] / max(1, pu["near32_launches"]) / 1e3) / 1e12 if pu["near32_launches"] else None}
 
     # plain FP64 solve (zero start, double-precision pair sums): one operator
     # application timed on the device, times the plain GMRES iterations plus

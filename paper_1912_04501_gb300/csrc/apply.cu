@@ -76,7 +76,8 @@ __device__ __forceinline__ bool item_range(const int4* items, const Cell* cells,
     if (!cl.active) return false;
     const int sp = cl.splits[prec];
     const int ns = srcmul * cl.n_nodes;
-    const int chunk = (ns + sp - 1) / sp;
+    // per-node records (srcmul > 1) split at node boundaries: a node's records stay together
+    const int chunk = (ns + sp * srcmul - 1) / (sp * srcmul) * srcmul;
     r.c = it.x;
     r.nloc = cl.n_nodes;
     r.i0 = cl.node_off + it.y * tile;
@@ -751,7 +752,7 @@ k_pack_moments_u(const double2* __restrict__ sigma, const double* __restrict__ x
 // operations of pair32 in its order: every pair's term is bit for bit the
 // one the single-precision close pass recomputes.  A dummy record (far away,
 // zero strength) pads an odd tile.
-template <int TPT, bool COMP, int MINB>
+template <int TPT, bool COMP, int MINB, bool ROWS>
 __global__ void __launch_bounds__(kNearThreads, MINB)
 k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const float4* __restrict__ tgt,
           const float4* __restrict__ src, float2* __restrict__ part) {
@@ -759,6 +760,7 @@ k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
     ItemRange rg;
     if (!item_range(items, cells, 0, kNearThreads * TPT, rg, 4)) return;
     f32x2 px[TPT], py[TPT], nx2[TPT], ny2[TPT], ax[TPT], ay[TPT];
+    float pys[TPT], nys[TPT];
     float hx[TPT], lx[TPT], hy[TPT], ly[TPT];
     const f32x2 eps = pk2(1e-30f, 1e-30f), zero = pk2(0.f, 0.f);
     const int tbase = rg.i0 + threadIdx.x;
@@ -770,6 +772,8 @@ k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
         py[t] = pk2(tv.y, tv.y);
         nx2[t] = pk2(tv.z, tv.z);
         ny2[t] = pk2(tv.w, tv.w);
+        pys[t] = tv.y;
+        nys[t] = tv.w;
         ax[t] = ay[t] = zero;
         hx[t] = lx[t] = hy[t] = ly[t] = 0.f;
     }
@@ -790,25 +794,52 @@ k_near32u(const int4* __restrict__ items, const Cell* __restrict__ cells, const 
             s_qy[cnt] = 0.f;
         }
         __syncthreads();
+        if constexpr (ROWS) {
+            // e1 = (L1, 0): records 2k and 2k + 1 (a node's images dm = 0, 1 at
+            // one dn) have the same y and q, so r_y, r_y^2, r_y n_y and r_y q_y
+            // are computed once for both (the same roundings as per record)
 #pragma unroll 2
-        for (int k = 0; k < cnt; k += 2) {
-            const f32x2 sx = *reinterpret_cast<const f32x2*>(s_x + k);
-            const f32x2 sy = *reinterpret_cast<const f32x2*>(s_y + k);
-            const f32x2 qx = *reinterpret_cast<const f32x2*>(s_qx + k);
-            const f32x2 qy = *reinterpret_cast<const f32x2*>(s_qy + k);
+            for (int k = 0; k < cnt; k += 2) {
+                const f32x2 sx = *reinterpret_cast<const f32x2*>(s_x + k);
+                const float sy = s_y[k], qxs = s_qx[k], qys = s_qy[k];
+                const f32x2 qx = pk2(qxs, qxs);
 #pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                const f32x2 dx = sub2(px[t], sx);
-                const f32x2 dy = sub2(py[t], sy);
-                const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
-                const f32x2 rn = fma2(dx, nx2[t], mul2(dy, ny2[t]));
-                const f32x2 rq = fma2(dx, qx, mul2(dy, qy));
-                float ra, rb;
-                upk2(r2, ra, rb);
-                const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
-                const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
-                ax[t] = fma2(cc, dx, ax[t]);
-                ay[t] = fma2(cc, dy, ay[t]);
+                for (int t = 0; t < TPT; ++t) {
+                    const float ey = pys[t] - sy;
+                    const float ey2 = fmaf(ey, ey, 1e-30f), eyn = ey * nys[t], eyq = ey * qys;
+                    const f32x2 dx = sub2(px[t], sx);
+                    const f32x2 r2 = fma2(dx, dx, pk2(ey2, ey2));
+                    const f32x2 rn = fma2(dx, nx2[t], pk2(eyn, eyn));
+                    const f32x2 rq = fma2(dx, qx, pk2(eyq, eyq));
+                    float ra, rb;
+                    upk2(r2, ra, rb);
+                    const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
+                    const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
+                    ax[t] = fma2(cc, dx, ax[t]);
+                    ay[t] = fma2(cc, pk2(ey, ey), ay[t]);
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (int k = 0; k < cnt; k += 2) {
+                const f32x2 sx = *reinterpret_cast<const f32x2*>(s_x + k);
+                const f32x2 sy = *reinterpret_cast<const f32x2*>(s_y + k);
+                const f32x2 qx = *reinterpret_cast<const f32x2*>(s_qx + k);
+                const f32x2 qy = *reinterpret_cast<const f32x2*>(s_qy + k);
+#pragma unroll
+                for (int t = 0; t < TPT; ++t) {
+                    const f32x2 dx = sub2(px[t], sx);
+                    const f32x2 dy = sub2(py[t], sy);
+                    const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, eps));
+                    const f32x2 rn = fma2(dx, nx2[t], mul2(dy, ny2[t]));
+                    const f32x2 rq = fma2(dx, qx, mul2(dy, qy));
+                    float ra, rb;
+                    upk2(r2, ra, rb);
+                    const f32x2 inv = pk2(rcp_approx(ra), rcp_approx(rb));
+                    const f32x2 cc = mul2(mul2(rn, inv), mul2(rq, inv));
+                    ax[t] = fma2(cc, dx, ax[t]);
+                    ay[t] = fma2(cc, dy, ay[t]);
+                }
             }
         }
         if constexpr (COMP) {
@@ -1451,19 +1482,18 @@ static int launch_near32(bie_ctx* c, const float4* src, float2* part) {
     for (const Cell& cl : c->cells_h)
         maxchunk = std::max(maxchunk, (c->srcmul * cl.n_nodes + cl.splits[0] - 1) / cl.splits[0]);
     const bool comp = maxchunk > kNear32CompChunk;
-    if (c->utilde) {
-        if (comp)
-            k_near32u<kNearUTpt, true, kNearUCtas><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells,
-                                                                                         c->tgt32, src, part);
-        else
-            k_near32u<kNearUTpt, false, kNearUCtas><<<it.count, kNearThreads, 0, c->stream>>>(it.items, c->cells,
-                                                                                          c->tgt32, src, part);
-        BIE_LAUNCH(c, "k_near32u");
-        return BIE_OK;
-    }
     // lattice rows share dy when every cell has e1 = (L1, 0)
     bool rows = true;
     for (const Cell& cl : c->cells_h) rows = rows && cl.e1[1] == 0.0;
+    if (c->utilde) {
+        const dim3 g(it.count), b(kNearThreads);
+        if (comp && rows) k_near32u<kNearUTpt, true, kNearUCtas, true><<<g, b, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+        else if (comp) k_near32u<kNearUTpt, true, kNearUCtas, false><<<g, b, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+        else if (rows) k_near32u<kNearUTpt, false, kNearUCtas, true><<<g, b, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+        else k_near32u<kNearUTpt, false, kNearUCtas, false><<<g, b, 0, c->stream>>>(it.items, c->cells, c->tgt32, src, part);
+        BIE_LAUNCH(c, "k_near32u");
+        return BIE_OK;
+    }
     // batches of uneven cells take their items from a queue (longest first)
     int* q = (kNearQueue && c->ncell > 1) ? c->near_ctr : nullptr;
     const int sl = kNear32ShapeList[c->shape32].ctas * c->sms;
