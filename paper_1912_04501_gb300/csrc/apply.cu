@@ -922,6 +922,7 @@ k_near_dfu(const int4* __restrict__ items, const Cell* __restrict__ cells, const
     ItemRange rg;
     if (!item_range(items, cells, 2, kNearThreads, rg, 4)) return;
     const Cell& cl = cells[rg.c];
+    const bool rows = cl.e1[1] == 0.0;
     const int i = rg.i0 + threadIdx.x;
     double tx = 1e4, ty = 1e4, tnx = 0, tny = 0;
     if (i < rg.i1) {
@@ -942,7 +943,19 @@ k_near_dfu(const int4* __restrict__ items, const Cell* __restrict__ cells, const
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kNearThreads) s_src[k] = src[jt + k];
         __syncthreads();
-        for (int k = 0; k < cnt; ++k) pair_df(pxh, pxl, pyh, pyl, nxh, nxl, nyh, nyl, s_src[k], axh, axe, ayh, aye);
+        if (rows) {
+            // e1 = (L1, 0): a node's images dm = 0, 1 at one dn (records 2k,
+            // 2k + 1) share their y-parts; the same arithmetic, pair by pair
+            for (int k = 0; k + 1 < cnt; k += 2) {
+                const DFy yp = pair_df_y(pyh, pyl, nyh, nyl, s_src[k]);
+                pair_df_x(pxh, pxl, nxh, nxl, yp, s_src[k], axh, axe, ayh, aye);
+                pair_df_x(pxh, pxl, nxh, nxl, yp, s_src[k + 1], axh, axe, ayh, aye);
+            }
+            if (cnt & 1) pair_df(pxh, pxl, pyh, pyl, nxh, nxl, nyh, nyl, s_src[cnt - 1], axh, axe, ayh, aye);
+        } else {
+            for (int k = 0; k < cnt; ++k)
+                pair_df(pxh, pxl, pyh, pyl, nxh, nxl, nyh, nyl, s_src[k], axh, axe, ayh, aye);
+        }
         dxs += (double)axh + (double)axe;
         dys += (double)ayh + (double)aye;
     }
