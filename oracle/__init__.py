@@ -18,6 +18,9 @@ slow and as literal as the paper's definitions allow:
                    periodizing correction (Sec. 4.2, Sec. 6.1, Sec. 6.2).
 * ``close``     -- close-evaluation correction (Sec. 6.3), by its definition:
                    the exact integral of the trigonometric interpolant.
+* ``barycentric`` -- the same integral by the paper's special quadrature
+                   (Sec. 6.3): compensated barycentric rules for the Cauchy
+                   integrals the single-layer traction reduces to.
 * ``bie``       -- the Nystrom operator with rigid completion and pressure
                    fix (Eq. BIEdiscretized, Sec. 5, Sec. 6.2 remark), GMRES,
                    velocity extraction, effective viscosity and forward Euler

@@ -30,7 +30,7 @@ def perp(v):
 
 class Operator:
     def __init__(self, susp, n_proxy=16, proxy_radius=1.5, n_coll=16,
-                 close_factor=10.0, lam_rel=1e-8, use_close=True, close_targets=None):
+                 close_factor=10.0, lam_rel=1e-8, use_close=True, close_targets=None, close_rule="fine"):
         self.s = susp
         self.M = n_proxy
         self.m = n_coll
@@ -41,7 +41,8 @@ class Operator:
         self.self_index = np.arange(susp.N)
         # close_targets restricts the close-pair search (sampled evaluation of
         # large cells); apply() is then valid at those targets and node 0 only
-        self.close = ClosePairs(susp, self.shifts, close_factor, close_targets) if use_close else None
+        # close_rule: "fine" (the definition) or "barycentric" (the paper's Sec. 6.3 rule)
+        self.close = ClosePairs(susp, self.shifts, close_factor, close_targets, close_rule) if use_close else None
 
     # -- pieces ----------------------------------------------------------------
     def density_moments(self, sigma):

@@ -107,8 +107,14 @@ class ClosePairs:
     close_factor * h_b, with the same-body zero-shift case excluded (that
     interaction is the smooth rule plus the on-curve diagonal)."""
 
-    def __init__(self, susp, shifts, close_factor=10.0, targets=None):
-        """targets: restrict the search to these target nodes (None = all)."""
+    def __init__(self, susp, shifts, close_factor=10.0, targets=None, rule="fine"):
+        """targets: restrict the search to these target nodes (None = all).
+        rule: "fine" evaluates the integral of the interpolated density by
+        the fine trapezoidal rule (its definition); "barycentric" by the
+        paper's special quadrature (oracle/barycentric.py)."""
+        if rule not in ("fine", "barycentric"):
+            raise ValueError("rule is 'fine' or 'barycentric'")
+        self.rule = rule
         self.susp = susp
         self.pairs = []  # (target index, body, shift vector, curve distance, local spacing)
         off = susp.offsets
@@ -143,7 +149,11 @@ class ClosePairs:
             sl = slice(off[b], off[b + 1])
             xi = susp.x[i]
             ni = susp.n[i]
-            fine = fine_integral(bd, sigma[sl], xi, ni, sh, fine_factor(hl, d))
+            if self.rule == "barycentric":
+                from . import barycentric
+                fine = barycentric.slp_traction(bd, sigma[sl], xi, ni, sh)
+            else:
+                fine = fine_integral(bd, sigma[sl], xi, ni, sh, fine_factor(hl, d))
             coarse = kernels.traction(xi[None, :] - (susp.x[sl] + sh), ni[None, :],
                                       sigma[sl] * susp.w[sl, None]).sum(0)
             k = i if want is None else want[i]

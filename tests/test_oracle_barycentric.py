@@ -1,0 +1,163 @@
+"""Pins of the paper's close-evaluation rule in the oracle
+(oracle/barycentric.py, Sec. 6.3).
+
+- The compensated exterior barycentric formula reproduces a function analytic
+  outside the curve and vanishing at infinity, 1/(z - z0) with z0 inside, at
+  targets from 0.1 down to 1e-8 from the curve (closed form).
+- The exterior boundary values of a Cauchy integral (Plemelj): for h the
+  boundary values of such an exterior function v they are -v, for an entire
+  function they vanish (closed forms).
+- The complex decomposition of the traction kernel equals Eq. (Gt).
+- The single-layer traction by the rule equals the smooth N-point rule far
+  from the curve (where that rule is exact), and the brute-force integral of
+  the interpolated density (oracle/close.py, by its definition) near it, on
+  smooth densities, down to 1e-3 of the node spacing (spectrally convergent
+  in the node count: a star needs 1024 nodes for 1e-12).
+- A dropped term of the decomposition, a wrong sign of the compensation or a
+  missing conjugate each fail one of these (planted in copies of the pieces).
+"""
+import numpy as np
+import pytest
+
+from oracle import barycentric as bc
+from oracle import close, geometry, kernels
+
+BODY = dict(a=0.2, b=0.1, xc=[0.5, 0.5], theta=0.3, n=128)
+# a four-armed star needs more nodes than the ellipse before the global rule
+# resolves it (256: 6e-3, 512: 3e-6, 1024: 2e-12 against the definition at
+# 1e-4 from the curve)
+STAR = dict(shape="star", r0=0.25, eps=0.5, k=4, xc=[0.5, 0.5], theta=0.2, n=1024)
+
+
+def _target(body, t, d):
+    x, dx, _ = geometry.curve_point(body, np.array([t]))
+    tv = dx[0] / np.linalg.norm(dx[0])
+    return x[0] + d * np.array([tv[1], -tv[0]])
+
+
+def test_exterior_barycentric_closed_form():
+    zeta, dz, _ = bc.curve(BODY)
+    z0 = 0.52 + 0.49j
+    v = 1.0 / (zeta - z0)
+    for d in (1e-1, 1e-2, 1e-3, 1e-5, 1e-8):
+        p = _target(BODY, 0.7, d)
+        z = p[0] + 1j * p[1]
+        assert abs(bc.exterior_barycentric(zeta, dz, v, z) - 1.0 / (z - z0)) < 1e-13
+    # without the compensation (plain trapezoid of the Cauchy integral) it fails near the curve
+    p = _target(BODY, 0.7, 1e-3)
+    z = p[0] + 1j * p[1]
+    W = dz * (2 * np.pi / BODY["n"]) / (zeta - z)
+    assert abs(-(W @ v) / (2j * np.pi) - 1.0 / (z - z0)) > 1e-3
+
+
+def test_exterior_values_closed_forms():
+    zeta, dz, _ = bc.curve(BODY)
+    v = 1.0 / (zeta - (0.48 + 0.51j))
+    assert np.abs(bc.exterior_values(zeta, dz, v) + v).max() < 1e-10
+    assert np.abs(bc.exterior_values(zeta, dz, np.exp(zeta) * zeta ** 2)).max() < 1e-12
+
+
+def test_complex_form_of_the_traction_kernel():
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal((20, 2))
+    n = rng.standard_normal((20, 2))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    s = rng.standard_normal((20, 2))
+    T = kernels.traction(r, n, s)
+    rc, nc, sc = (a[:, 0] + 1j * a[:, 1] for a in (r, n, s))
+    Tc = -(np.conj(nc) * np.conj(sc) * rc / np.conj(rc) ** 2 + (np.conj(nc) * sc + nc * np.conj(sc)) / np.conj(rc)
+           + nc * sc / rc) / (4 * np.pi)
+    assert np.abs(T[:, 0] + 1j * T[:, 1] - Tc).max() < 1e-14 * np.abs(Tc).max()
+
+
+def _smooth_density(body):
+    t = 2 * np.pi * np.arange(body["n"]) / body["n"]
+    return np.stack([np.cos(3 * t) + 0.5 * np.sin(5 * t) + 0.2, np.sin(2 * t) - 0.3 * np.cos(7 * t)], axis=1)
+
+
+@pytest.mark.parametrize("body", [BODY, STAR], ids=["ellipse", "star"])
+def test_traction_matches_smooth_rule_far_and_definition_near(body):
+    nodes = geometry.body_nodes(body)
+    h = nodes["w"].mean()
+    sig = _smooth_density(body)
+    nx = np.array([0.6, 0.8])
+    far = _target(body, 1.1, 20 * h)
+    smooth = kernels.traction(far[None, :] - nodes["x"], nx[None, :], sig * nodes["w"][:, None]).sum(0)
+    assert np.abs(bc.slp_traction(body, sig, far, nx) - smooth).max() < 1e-12 * np.abs(smooth).max()
+    for d in (5 * h, h, 0.1 * h, 1e-2 * h, 1e-3 * h):
+        p = _target(body, 1.1, d)
+        ref = close.fine_integral(body, sig, p, nx, (0.0, 0.0), close.fine_factor(h, d))
+        got = bc.slp_traction(body, sig, p, nx)
+        assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max(), d / h
+    # a shifted image of the body: the same integral as the translated target
+    sh = np.array([1.0, 0.3])
+    p = _target(body, 2.0, 0.05 * h)
+    assert np.abs(bc.slp_traction(body, sig, p + sh, nx, tuple(sh)) - bc.slp_traction(body, sig, p, nx)).max() < 1e-11
+
+
+def test_planted_mistakes_fail():
+    body = BODY
+    nodes = geometry.body_nodes(body)
+    h = nodes["w"].mean()
+    sig = _smooth_density(body)
+    nx = np.array([0.6, 0.8])
+    p = _target(body, 1.1, 0.1 * h)
+    ref = close.fine_integral(body, sig, p, nx, (0.0, 0.0), close.fine_factor(h, 0.1 * h))
+    zeta, dz, tau = bc.curve(body)
+    s = sig[:, 0] + 1j * sig[:, 1]
+    z = p[0] + 1j * p[1]
+    n = nx[0] + 1j * nx[1]
+
+    def total(C, Cp, drop=None):
+        I1 = -2j * np.pi * C[0]
+        I2 = -2j * np.pi * C[1]
+        I3 = 2j * np.pi * (np.conj(z) * Cp[0] - Cp[2])
+        parts = [np.conj(n) * np.conj(I3), np.conj(n) * np.conj(I2), n * np.conj(I1), n * I1]
+        if drop is not None:
+            parts[drop] = 0.0
+        T = -sum(parts) / (4 * np.pi)
+        return np.array([T.real, T.imag])
+
+    h3 = np.stack([s / tau, np.conj(s) / tau, s * np.conj(zeta) / tau], axis=1)
+    phi = bc.exterior_values(zeta, dz, h3)
+    dphi = bc.spectral_dt(phi) / dz[:, None]
+    C = bc.exterior_barycentric(zeta, dz, phi, z)
+    Cp = bc.exterior_barycentric(zeta, dz, dphi, z)
+    assert np.abs(total(C, Cp) - ref).max() < 1e-10 * np.abs(ref).max()
+    for k in range(4):  # a dropped term
+        assert np.abs(total(C, Cp, drop=k) - ref).max() > 1e-3 * np.abs(ref).max()
+    # the compensation with the wrong sign
+    W = dz * (2 * np.pi / body["n"]) / (zeta - z)
+    Cw = (W @ phi) / (W.sum() + 2j * np.pi)
+    assert np.abs(total(Cw, Cp) - ref).max() > 1e-3 * np.abs(ref).max()
+    # sigma instead of its conjugate in I2
+    h_bad = np.stack([s / tau, s / tau, s * np.conj(zeta) / tau], axis=1)
+    Cb = bc.exterior_barycentric(zeta, dz, bc.exterior_values(zeta, dz, h_bad), z)
+    assert np.abs(total(Cb, Cp) - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def _smooth_nodes(cell):
+    """A smooth density on every body: low Fourier modes of its parameter."""
+    out = []
+    for k, b in enumerate(cell["bodies"]):
+        t = 2 * np.pi * np.arange(b["n"]) / b["n"]
+        out.append(np.stack([np.cos(2 * t + k) + 0.3 * np.sin(5 * t), 0.5 * np.sin(3 * t - k) + 0.2], axis=1))
+    return np.concatenate(out)
+
+
+def test_operator_with_the_paper_rule_equals_the_definition():
+    """The oracle operator with its close-evaluation pairs by the paper's rule
+    and by the definition (the fine rule) agree on a smooth density across a
+    gap of 1e-3 (the two ellipses of Sec. 8 Example 1)."""
+    from oracle import bie as obie
+    from paper_1912_04501_gb300 import workloads
+    cell = workloads.two_ellipses(1e-3, 256)
+    susp = geometry.Suspension(cell["e1"], cell["e2"], cell["centre"], cell["mu"], cell["gamma"], cell["bodies"])
+    sv = cell["solver"]
+    kw = dict(n_proxy=sv["n_proxy"], proxy_radius=sv["proxy_radius"], n_coll=sv["n_coll"])
+    sigma = _smooth_nodes(cell)
+    yf = obie.Operator(susp, close_rule="fine", **kw).apply(sigma)
+    ob = obie.Operator(susp, close_rule="barycentric", **kw)
+    assert len(ob.close.pairs) > 20
+    yb = ob.apply(sigma)
+    assert np.abs(yb - yf).max() < 1e-10 * np.abs(yf).max()
