@@ -46,6 +46,34 @@ def test_close_parity_at_gap_1e5(gap, n):
     ctx.close()
 
 
+@pytest.mark.parametrize("gap", [2e-3, 1e-5])
+def test_close_evaluation_matches_the_papers_rule(gap):
+    """The GPU's close-evaluation blocks (the fine rule of the interpolated
+    density) against the oracle evaluating the same pairs by the paper's own
+    special quadrature (Sec. 6.3: compensated barycentric Cauchy integrals,
+    oracle/barycentric.py), on a smooth density, at the targets nearest the
+    contact: FP64 and double-float to 1e-10."""
+    n = 512
+    cell = workloads.two_ellipses(gap, n)
+    ctx = bie.Context(cell, precision=bie.BIE_FP64)
+    x, _, _, _ = ctx.nodes()
+    contact = np.array([0.5625, 0.5])
+    dist = np.linalg.norm(x - contact[None, :], axis=1)
+    idx = np.unique(np.concatenate([np.argsort(dist[:n])[:8], n + np.argsort(dist[n:])[:8]]))
+    op = oracle_operator(cell, close_targets=idx, close_rule="barycentric")
+    assert len(op.close.pairs) >= 16
+    sigma = []
+    for k, b in enumerate(cell["bodies"]):
+        t = 2 * np.pi * np.arange(b["n"]) / b["n"]
+        sigma.append(np.stack([np.cos(2 * t + k) + 0.3 * np.sin(5 * t), 0.5 * np.sin(3 * t - k) + 0.2], axis=1))
+    sigma = np.concatenate(sigma)
+    ref = op.apply(sigma, targets=idx)
+    for prec in (bie.BIE_FP64, bie.BIE_DF64):
+        y = ctx.apply(sigma.ravel(), precision=prec).reshape(-1, 2)[idx]
+        assert _rel(y, ref) < 1e-10, (prec, _rel(y, ref))
+    ctx.close()
+
+
 def _errors(gap, ns, n_ref):
     from paper_1912_04501_gb300 import convergence
     ref, rows = convergence.study(gap, ns, n_ref)
