@@ -134,6 +134,14 @@ typedef struct {
                              each node's lattice translate inside U (Sec. 6.2); 4N sources per near sum
                              instead of 9N.  Bodies must be small enough that every close-evaluation pair
                              sees whole body images (BIE_EINVAL otherwise); autotune must be 0 */
+    int32_t close_rule;   /* how each close-evaluation block (the integral of G^t times the trigonometric
+                             interpolant of the nodal density over the exact curve, Sec. 6.3) is built.
+                             0: the fine trapezoidal rule on rho N_b points of the interpolant (rho from the
+                             target's distance, up to 4096).  1: the paper's special quadrature: compensated
+                             barycentric rules for the Cauchy integrals the single-layer traction reduces to
+                             (exterior boundary values by the Plemelj formula), O(N_b^2) per block whatever
+                             the distance; exact for the interpolant of sigma / tau rather than of sigma, so
+                             the two rules agree on smooth densities (to ~1e-12) and differ on rough ones */
 } bie_opts;
 
 typedef struct {

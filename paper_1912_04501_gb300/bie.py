@@ -57,7 +57,8 @@ class Opts(ctypes.Structure):
                 ("lam_rel", c_double), ("gmres_tol", c_double), ("gmres_max", c_int32), ("inner_tol", c_double),
                 ("max_refine", c_int32), ("warm_start", c_int32), ("min_gap", c_double), ("device", c_int32),
                 ("close_factor", c_double), ("close_capacity", c_int32), ("residual", c_int32),
-                ("autotune", c_int32), ("graph", c_int32), ("precond", c_int32), ("n_images", c_int32)]
+                ("autotune", c_int32), ("graph", c_int32), ("precond", c_int32), ("n_images", c_int32),
+                ("close_rule", c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

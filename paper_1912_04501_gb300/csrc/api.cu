@@ -43,7 +43,8 @@ static void free_all(bie_ctx* c) {
                     c->sv.chunks,
                     c->sv.cell_chunks, c->sv.sigma_prev, c->sv.sigma_prev2, c->sv.aug, c->sv.d2,
                     c->sv.feat, c->sv.pred, c->cl.dmin, c->cl.dmin_prev, c->cl.ddir, c->cl.slots, c->cl.count, c->cl.pair_base, c->cl.pairs,
-                    c->cl.blk_off, c->cl.blocks, c->cl.blocks32, c->cl.flags, c->cl.dtab, c->cl.dtab_off, c->near[0].items,
+                    c->cl.blk_off, c->cl.blocks, c->cl.blocks32, c->cl.flags, c->cl.dtab, c->cl.dtab_off,
+                    c->cl.bkd, c->cl.bcot, c->cl.bary, c->near[0].items,
                     c->near[1].items, c->near[2].items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -281,6 +282,7 @@ static int check_opts(const bie_opts& o, std::string& why) {
     else if (o.n_images != 9 && o.n_images != 4) why = "n_images must be 9 or 4";
     else if (o.n_images == 4 && o.n_proxy % 4 != 0) why = "n_images 4 needs n_proxy a multiple of 4";
     else if (o.n_images == 4 && o.autotune) why = "the tile-shape autotuner times the 3 x 3 near sum (n_images 9)";
+    else if (o.close_rule != 0 && o.close_rule != 1) why = "close_rule must be 0 or 1";
     else return 0;
     return 1;
 }
@@ -313,6 +315,7 @@ void bie_default_opts(bie_opts* o) {
     o->graph = 0;
     o->precond = 0;
     o->n_images = 9;
+    o->close_rule = 0;
 }
 
 int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const bie_body* bodies,
@@ -528,6 +531,13 @@ int bie_init_batch(bie_ctx** out, int32_t n_cells, const bie_cell* cells, const 
         rc = rc ? rc : dalloc(c, &c->cl.blocks, (size_t)c->cl.cap_doubles);
         rc = rc ? rc : dalloc(c, &c->cl.blocks32, (size_t)c->cl.cap_doubles);
         rc = rc ? rc : dalloc(c, &c->cl.flags, 10);
+        c->cl.rule = o.close_rule;
+        if (o.close_rule == 1) {
+            c->cl.cap_bary = 2 * (c->cl.cap_doubles / 3) + 2;
+            rc = rc ? rc : dalloc(c, &c->cl.bkd, n);
+            rc = rc ? rc : dalloc(c, &c->cl.bcot, n);
+            rc = rc ? rc : dalloc(c, &c->cl.bary, (size_t)c->cl.cap_bary);
+        }
     }
     c->ws.part_bytes = part;
     // zeroed once: a cell that the solver switches off keeps finite partials

@@ -120,6 +120,11 @@ struct Close {
     float2* ddir = nullptr;       // N: unit vector towards that nearest point (0 if none)
     bool have_dprev = false;
     size_t shm_limit = 0;
+    int rule = 0;                 // opts.close_rule: 0 fine trapezoidal rule, 1 barycentric
+    double2* bkd = nullptr;       // N: Plemelj diagonal of each body node (barycentric rule)
+    double* bcot = nullptr;       // N: spectral-derivative table of each body (barycentric rule)
+    double2* bary = nullptr;      // 2 per stored block node: the rule's intermediate vectors
+    long long cap_bary = 0;       // bary capacity (double2)
 };
 
 // Double-precision source record: position and premultiplied density q = sigma w.

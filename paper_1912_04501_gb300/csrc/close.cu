@@ -356,6 +356,235 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's special quadrature (Sec. 6.3, opts.close_rule = 1).  In complex
+// notation (z the target, n its normal, zeta the source point, s = sigma) the
+// traction kernel of Eq. Gt is
+//   -(1/4pi) [ conj(n) conj(s) r / conj(r)^2 + (conj(n) s + n conj(s)) / conj(r) + n s / r ],
+// r = z - zeta, so the integral over a body's curve is made of the Cauchy
+// integrals C[h](z) = (1/2 pi i) oint h / (zeta - z) dzeta (and C') of
+// h = s / tau, conj(s) / tau, s conj(zeta) / tau.  For a target outside the
+// curve C[h] is analytic outside it and vanishes at infinity: its boundary
+// values phi = E h follow from the Plemelj formula with a smooth integrand,
+//   E = (K + (2 pi / N) Dspec) / (2 pi i),  K_jk = wt_k / (zeta_k - zeta_j) (k != j),
+//   K_jj = -sum_{k != j} K_jk,  wt_k = w_k tau_k = zeta'(t_k) 2 pi / N,
+// Dspec the spectral differentiation matrix of the N-point interpolant
+// (Dspec_jk = d[(j - k) mod N], d_m = (-1)^m cot(pi m / N) / 2), and its value
+// near the curve from the compensated exterior barycentric rule
+//   C[h](z) = sum_j beta_j phi_j,  beta_j = W_j / (sum_i W_i - 2 pi i),  W_j = wt_j / (zeta_j - z);
+// C'[h] the same with phi' = diag(1 / zeta') Dspec phi.  As a linear map of
+// the nodal density this gives per node k, with a = E^T beta and
+// b = E^T Dspec^T (beta / zeta'),
+//   p_k = -2 pi i a_k conj(tau_k),  q_k = 2 pi i b_k (conj(z) - conj(zeta_k)) conj(tau_k),
+//   alpha_k = -2 Re(n p_k) / (4 pi),  gamma_k = -(n conj(p_k) + conj(n) conj(q_k)) / (4 pi),
+// T = sum_k alpha_k s_k + gamma_k conj(s_k): alpha is real, so the block of
+// node k is the symmetric [[alpha + Re gamma, Im gamma], [Im gamma, alpha - Re gamma]]
+// (the same storage as the fine rule's blocks), minus the smooth rule's term.
+// All in FP64; O(N_b^2) per block whatever the target's distance.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// a / b
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double inv = 1.0 / (b.x * b.x + b.y * b.y);
+    return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+// wt = w tau with the unit tangent tau = (-n_y, n_x) (the outward normal is tau turned clockwise)
+__device__ __forceinline__ double2 node_wt(const double* w, const double* nx, const double* ny, int j) {
+    return make_double2(-w[j] * ny[j], w[j] * nx[j]);
+}
+
+// Per body (one CTA each): K_kk = -sum_{m != k} wt_m / (zeta_m - zeta_k) (shift-
+// invariant) and the body's spectral-derivative table d_m.
+__global__ void __launch_bounds__(256)
+k_bary_pre(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
+           const double* __restrict__ ny, const double* __restrict__ w, const double* __restrict__ body,
+           double2* __restrict__ kd, double* __restrict__ dcot) {
+    const double* bd = body + 8 * blockIdx.x;
+    const int n = (int)bd[5], off = (int)bd[6];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double zx = x[off + k], zy = y[off + k];
+        double sr = 0.0, si = 0.0;
+        for (int m = 0; m < n; ++m) {
+            if (m == k) continue;
+            const double2 q = cdiv(node_wt(w, nx, ny, off + m), make_double2(x[off + m] - zx, y[off + m] - zy));
+            sr += q.x;
+            si += q.y;
+        }
+        kd[off + k] = make_double2(-sr, -si);
+        dcot[off + k] = k == 0 ? 0.0 : 0.5 * ((k & 1) ? -1.0 : 1.0) / tan(kPi * k / n);
+    }
+}
+
+constexpr int kBaryTile = 256;
+
+// One CTA per (target, body image) pair: the block of every node of the body
+// image by the barycentric rule.  scratch holds a_k and u_k = (Dspec^T (beta /
+// zeta'))_k per node (2 double2 at 2 (blk_off / 3 + k)).
+__global__ void __launch_bounds__(kBaryTile)
+k_close_blocks_bary(const int4* __restrict__ pairs, const long long* __restrict__ blk_off,
+                    const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ nx,
+                    const double* __restrict__ ny, const double* __restrict__ w, const double* __restrict__ body,
+                    const int* __restrict__ node_cell, const Cell* __restrict__ cells,
+                    const double2* __restrict__ kd, const double* __restrict__ dcot, double2* __restrict__ scratch,
+                    double* __restrict__ blocks, float* __restrict__ blocks32) {
+    __shared__ double2 s_z[kBaryTile], s_v[kBaryTile], s_u[kBaryTile];
+    __shared__ double red[2][kBaryTile / 32];
+    const int4 pr = pairs[blockIdx.x];
+    const int i = pr.x, b = pr.y, im = pr.z;
+    const Cell& cl = cells[node_cell[i]];
+    const double* bd = body + 8 * b;
+    const int n = (int)bd[5], off = (int)bd[6];
+    const double sx = cl.sx[im], sy = cl.sy[im];
+    const double2 z = make_double2(x[i], y[i]);
+    const double2 nn = make_double2(nx[i], ny[i]);
+    const long long bo = blk_off[blockIdx.x];
+    double2* sc = scratch + 2 * (bo / 3);
+    const int t = threadIdx.x;
+    const double two_pi = 2.0 * kPi;
+    // S' = sum_j W_j - 2 pi i (fixed-order block reduction)
+    double sr = 0.0, si = 0.0;
+    for (int j = t; j < n; j += kBaryTile) {
+        const double2 q = cdiv(node_wt(w, nx, ny, off + j), make_double2(x[off + j] + sx - z.x, y[off + j] + sy - z.y));
+        sr += q.x;
+        si += q.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = sr;
+        red[1][t >> 5] = si;
+    }
+    __syncthreads();
+    double2 Sp = make_double2(0.0, 0.0);
+    for (int k = 0; k < kBaryTile / 32; ++k) {
+        Sp.x += red[0][k];
+        Sp.y += red[1][k];
+    }
+    Sp.y -= two_pi;
+    auto beta = [&](int j, double2 zj) {  // W_j / S'
+        return cdiv(cdiv(node_wt(w, nx, ny, off + j), make_double2(zj.x - z.x, zj.y - z.y)), Sp);
+    };
+    auto zeta = [&](int j) { return make_double2(x[off + j] + sx, y[off + j] + sy); };
+    const double scale = two_pi / n;
+    // pass 1: a = E^T beta and u = Dspec^T (beta / zeta'), zeta' = wt / scale
+    for (int kc = 0; kc < n; kc += kBaryTile) {
+        const int k = kc + t;
+        const bool valid = k < n;
+        const double2 zk = valid ? zeta(k) : make_double2(0.0, 0.0);
+        double2 aA = make_double2(0, 0), aD = make_double2(0, 0), aU = make_double2(0, 0);
+        for (int jt = 0; jt < n; jt += kBaryTile) {
+            __syncthreads();
+            const int j = jt + t;
+            if (j < n) {
+                const double2 zj = zeta(j);
+                const double2 bj = beta(j, zj);
+                s_z[t] = zj;
+                s_v[t] = bj;
+                s_u[t] = cdiv(cmul(bj, make_double2(scale, 0.0)), node_wt(w, nx, ny, off + j));  // beta / zeta'
+            }
+            __syncthreads();
+            if (!valid) continue;
+            const int cnt = min(kBaryTile, n - jt);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const int jg = jt + jj;
+                const double2 bj = s_v[jj];
+                if (jg != k) {
+                    const double2 r = cdiv(bj, make_double2(zk.x - s_z[jj].x, zk.y - s_z[jj].y));
+                    aA.x += r.x;
+                    aA.y += r.y;
+                }
+                int m = jg - k;
+                m += m < 0 ? n : 0;
+                const double dd = dcot[off + m];
+                aD.x = fma(dd, bj.x, aD.x);
+                aD.y = fma(dd, bj.y, aD.y);
+                aU.x = fma(dd, s_u[jj].x, aU.x);
+                aU.y = fma(dd, s_u[jj].y, aU.y);
+            }
+        }
+        if (valid) {
+            const double2 bk = beta(k, zk);
+            double2 v = cmul(node_wt(w, nx, ny, off + k), aA);
+            const double2 kb = cmul(kd[off + k], bk);
+            v.x += kb.x + scale * aD.x;
+            v.y += kb.y + scale * aD.y;
+            sc[2 * k] = make_double2(v.y / two_pi, -v.x / two_pi);  // v / (2 pi i)
+            sc[2 * k + 1] = aU;
+        }
+    }
+    __syncthreads();
+    // pass 2: b = E^T u, then the node blocks
+    for (int kc = 0; kc < n; kc += kBaryTile) {
+        const int k = kc + t;
+        const bool valid = k < n;
+        const double2 zk = valid ? zeta(k) : make_double2(0.0, 0.0);
+        double2 aB = make_double2(0, 0), aE = make_double2(0, 0);
+        for (int jt = 0; jt < n; jt += kBaryTile) {
+            __syncthreads();
+            const int j = jt + t;
+            if (j < n) {
+                s_z[t] = zeta(j);
+                s_u[t] = sc[2 * j + 1];
+            }
+            __syncthreads();
+            if (!valid) continue;
+            const int cnt = min(kBaryTile, n - jt);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const int jg = jt + jj;
+                const double2 uj = s_u[jj];
+                if (jg != k) {
+                    const double2 r = cdiv(uj, make_double2(zk.x - s_z[jj].x, zk.y - s_z[jj].y));
+                    aB.x += r.x;
+                    aB.y += r.y;
+                }
+                int m = jg - k;
+                m += m < 0 ? n : 0;
+                const double dd = dcot[off + m];
+                aE.x = fma(dd, uj.x, aE.x);
+                aE.y = fma(dd, uj.y, aE.y);
+            }
+        }
+        if (!valid) continue;
+        const double2 wtk = node_wt(w, nx, ny, off + k);
+        double2 v = cmul(wtk, aB);
+        const double2 ku = cmul(kd[off + k], sc[2 * k + 1]);
+        v.x += ku.x + scale * aE.x;
+        v.y += ku.y + scale * aE.y;
+        const double2 bk = make_double2(v.y / two_pi, -v.x / two_pi);
+        const double2 ak = sc[2 * k];
+        const double2 tauc = make_double2(-ny[off + k], -nx[off + k]);  // conj(tau)
+        // p = -2 pi i a conj(tau), q = 2 pi i b (conj(z) - conj(zeta_k)) conj(tau)
+        const double2 at = cmul(ak, tauc);
+        const double2 p = make_double2(two_pi * at.y, -two_pi * at.x);
+        const double2 bt = cmul(cmul(bk, make_double2(z.x - zk.x, -(z.y - zk.y))), tauc);
+        const double2 q = make_double2(-two_pi * bt.y, two_pi * bt.x);
+        const double al = -2.0 * (nn.x * p.x - nn.y * p.y) / (4.0 * kPi);
+        const double2 g1 = cmul(nn, cconj(p)), g2 = cmul(cconj(nn), cconj(q));
+        const double gr = -(g1.x + g2.x) / (4.0 * kPi), gi = -(g1.y + g2.y) / (4.0 * kPi);
+        // minus the smooth rule's term for node k of this body image
+        const double rx = z.x - zk.x, ry = z.y - zk.y;
+        const double r2 = rx * rx + ry * ry;
+        const double cc = -(rx * nn.x + ry * nn.y) * w[off + k] / (kPi * r2 * r2);
+        const double A = al + gr - cc * rx * rx;
+        const double B = gi - cc * rx * ry;
+        const double D = al - gr - cc * ry * ry;
+        double* out = blocks + bo + 3 * k;
+        out[0] = A;
+        out[1] = B;
+        out[2] = D;
+        const double iw = 1.0 / w[off + k];
+        float* o32 = blocks32 + bo + 3 * k;
+        o32[0] = (float)(A * iw);
+        o32[1] = (float)(B * iw);
+        o32[2] = (float)(D * iw);
+    }
+}
+
 // One warp per target: T_i += sum over its pairs of C sigma_b (slot order).
 __global__ void k_close_apply(const int* __restrict__ pair_base, const int4* __restrict__ pairs,
                               const long long* __restrict__ blk_off, const double* __restrict__ blocks,
@@ -474,15 +703,29 @@ int build_close(bie_ctx* c) {
             const long long cap = need_doubles + need_doubles / 4 + 1024;
             int rc = regrow(c, &c->cl.blocks, (size_t)cap);
             rc = rc ? rc : regrow(c, &c->cl.blocks32, (size_t)cap);
+            if (!rc && c->cl.rule == 1) {
+                rc = regrow(c, &c->cl.bary, (size_t)(2 * (cap / 3) + 2));
+                c->cl.cap_bary = 2 * (cap / 3) + 2;
+            }
             if (rc) return rc;
             c->cl.cap_doubles = cap;
         }
     }
     if (gm != ~0ULL) std::memcpy(&c->cl.min_gap, &gm, sizeof gm);
-    c->cl.under_resolved = h[3];
+    c->cl.under_resolved = c->cl.rule == 1 ? 0 : h[3];  // the barycentric rule has no finest factor
     c->cl.npairs = h[0];
     c->cl.rho_max = h[6];
     if (h[0] == 0) return BIE_OK;
+    if (c->cl.rule == 1) {
+        k_bary_pre<<<c->nb, 256, 0, c->stream>>>(c->x, c->y, c->nx, c->ny, c->w, c->body, c->cl.bkd, c->cl.bcot);
+        BIE_LAUNCH(c, "k_bary_pre");
+        k_close_blocks_bary<<<h[0], kBaryTile, 0, c->stream>>>(c->cl.pairs, c->cl.blk_off, c->x, c->y, c->nx,
+                                                              c->ny, c->w, c->body, c->node_cell, c->cells,
+                                                              c->cl.bkd, c->cl.bcot, c->cl.bary, c->cl.blocks,
+                                                              c->cl.blocks32);
+        BIE_LAUNCH(c, "k_close_blocks_bary");
+        return BIE_OK;
+    }
     if (h[6] > c->cl.dtab_rho) {
         int rc = build_dirichlet_tables(c, h[6]);
         if (rc) return rc;

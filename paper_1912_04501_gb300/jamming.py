@@ -32,12 +32,12 @@ TOLERANCES = (1e-10, 1e-9, 1e-8)
 MIN_GAP = 1e-6  # a smaller gap between the bodies ends the run (BIE_ECOLLIDE): they touch
 
 
-def _context(cell, tol):
+def _context(cell, tol, close_rule=0):
     return bie.Context(cell, precision=bie.BIE_MIXED, gmres_max=1000, max_refine=40, precond=1, gmres_tol=tol,
-                       min_gap=MIN_GAP)
+                       min_gap=MIN_GAP, close_rule=close_rule)
 
 
-def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print):
+def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print, close_rule=0):
     """Time steps until t_end, a mu_eff above mu_stop, bodies closer than
     MIN_GAP, or a step the solver cannot finish; returns the record.  Steps solve to a relative residual
     of 1e-10; when the gaps get so small that a solve stops above it (the
@@ -46,7 +46,7 @@ def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print):
     looser tolerance of TOLERANCES, and the record notes where."""
     cell = workloads.stars(example, n)
     tol_k = 0
-    ctx = _context(cell, TOLERANCES[tol_k])
+    ctx = _context(cell, TOLERANCES[tol_k], close_rule)
     rec = dict(example=example, n=n, dt=dt, t=[], mu_eff=[], iterations=[], residual=[], close_pairs=[],
                seconds=[], tolerance=[], stop="t_end")
     t = 0.0
@@ -60,7 +60,7 @@ def run(example=4, n=2500, dt=5e-4, t_end=0.5, mu_stop=1e5, log=print):
                 st = ctx.get_state()
                 ctx.close()
                 tol_k += 1
-                ctx = _context(cell, TOLERANCES[tol_k])
+                ctx = _context(cell, TOLERANCES[tol_k], close_rule)
                 ctx.set_state(st["t"], st["e2"], st["xc"], st["theta"], st["sigma"], st["sigma_prev2"],
                               st["dt_prev"], st["d2"])
                 if log:
@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--n", type=int, default=2500)
     ap.add_argument("--t-end", type=float, default=0.5)
     ap.add_argument("--out", default=None, help="directory for the mu_eff(t) records (JSON)")
+    ap.add_argument("--close-rule", type=int, choices=(0, 1), default=0,
+                    help="close-evaluation blocks: 0 fine trapezoidal rule, 1 the paper's barycentric rule")
     ap.add_argument("--check", nargs=2, type=float, default=None, metavar=("T0", "T1"),
                     help="instead of the runs: mu_eff on [T0, T1] as run, with FP64 solves, 1.6x the nodes "
                          "and half the step, all from the state at T0")
@@ -193,7 +195,7 @@ def main():
                     json.dump(res, f)
         return
     for ex in a.example:
-        rec = run(ex, a.n, t_end=a.t_end)
+        rec = run(ex, a.n, t_end=a.t_end, close_rule=a.close_rule)
         out = dict(example=ex, n=a.n, steps=len(rec["t"]), stop=rec["stop"],
                    t_last=rec["t"][-1] if rec["t"] else None, mu_last=rec["mu_eff"][-1] if rec["mu_eff"] else None,
                    seconds=float(np.sum(rec["seconds"])),

@@ -40,6 +40,7 @@ def test_default_opts(lib):
     assert o.autotune == 0 and o.graph == 0 and o.precond == 0
     assert o.close_capacity == 0 and o.residual == bie.BIE_DF64
     assert o.n_images == 9
+    assert o.close_rule == 0
 
 
 @pytest.mark.parametrize("mutate", [
@@ -74,7 +75,7 @@ def test_null_arguments(lib):
                                  dict(gmres_max=5000), dict(warm_start=4), dict(residual=1),
                                  dict(close_factor=-1.0), dict(precision=3), dict(gmres_tol=0.0),
                                  dict(autotune=2), dict(graph=-1), dict(precond=2), dict(n_images=5),
-                                 dict(n_images=4, n_proxy=50), dict(n_images=4, autotune=1)])
+                                 dict(n_images=4, n_proxy=50), dict(n_images=4, autotune=1), dict(close_rule=2)])
 def test_invalid_options_rejected_without_gpu(lib, opt):
     from paper_1912_04501_gb300 import workloads
     with pytest.raises(bie.BieError) as e:
