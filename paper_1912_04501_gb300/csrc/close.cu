@@ -369,7 +369,8 @@ k_close_blocks(const int4* __restrict__ pairs, const long long* __restrict__ blk
 //   E = (K + (2 pi / N) Dspec) / (2 pi i),  K_jk = wt_k / (zeta_k - zeta_j) (k != j),
 //   K_jj = -sum_{k != j} K_jk,  wt_k = w_k tau_k = zeta'(t_k) 2 pi / N,
 // Dspec the spectral differentiation matrix of the N-point interpolant
-// (Dspec_jk = d[(j - k) mod N], d_m = (-1)^m cot(pi m / N) / 2), and its value
+// (Dspec_jk = d[(j - k) mod N], d_m = (-1)^m cot(pi m / N) / 2 for even N,
+// (-1)^m / (2 sin(pi m / N)) for odd N), and its value
 // near the curve from the compensated exterior barycentric rule
 //   C[h](z) = sum_j beta_j phi_j,  beta_j = W_j / (sum_i W_i - 2 pi i),  W_j = wt_j / (zeta_j - z);
 // C'[h] the same with phi' = diag(1 / zeta') Dspec phi.  As a linear map of
@@ -414,7 +415,10 @@ k_bary_pre(const double* __restrict__ x, const double* __restrict__ y, const dou
             si += q.y;
         }
         kd[off + k] = make_double2(-sr, -si);
-        dcot[off + k] = k == 0 ? 0.0 : 0.5 * ((k & 1) ? -1.0 : 1.0) / tan(kPi * k / n);
+        // even N (bie_init requires it): cot, the Nyquist mode's derivative zero at the
+        // nodes; odd N would take csc
+        const double sg = (k & 1) ? -1.0 : 1.0;
+        dcot[off + k] = k == 0 ? 0.0 : 0.5 * sg / ((n & 1) ? sin(kPi * k / n) : tan(kPi * k / n));
     }
 }
 
