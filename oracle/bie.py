@@ -258,7 +258,7 @@ comes near a body that crosses a wall.  Both
     a geometry where it does not is refused (ValueError)."""
 
     def __init__(self, susp, n_proxy=128, n_coll=32, lam_rel=1e-8, close_factor=10.0, use_close=True,
-                 close_targets=None):
+                 close_targets=None, close_rule="fine"):
         self.s = susp
         self.M = n_proxy
         self.m = n_coll
@@ -277,7 +277,7 @@ comes near a body that crosses a wall.  Both
         self.close = None
         if use_close:
             shifts = periodic.image_shifts(susp.e1, susp.e2)
-            self.close = ClosePairs(susp, shifts, close_factor, close_targets)
+            self.close = ClosePairs(susp, shifts, close_factor, close_targets, close_rule)
             E = np.column_stack([susp.e1, susp.e2])
             for (i, b, sh, _, _) in self.close.pairs:
                 mn = np.rint(np.linalg.solve(E, sh)).astype(np.int64) + self.wrapmn[i]

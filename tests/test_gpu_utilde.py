@@ -78,6 +78,23 @@ def test_utilde_apply_fp64_df64_mixed(pair):
     assert _rel(ctx.apply(sigma, precision=bie.BIE_MIXED), ref) < 2e-5
 
 
+def test_utilde_with_the_papers_close_rule():
+    """The doubled cell with the close-evaluation blocks by the paper's
+    barycentric rule (opts.close_rule = 1) against the oracle's doubled cell
+    with the same rule, on a random density: FP64 and double-float 1e-10,
+    mixed 2e-5."""
+    cell = _cell("close")
+    ctx = bie.Context(cell, precision=bie.BIE_FP64, n_images=4, close_rule=1)
+    ou = obie.OperatorUtilde(oracle_suspension(cell), n_proxy=M_BOX, n_coll=M_COLL, close_rule="barycentric")
+    assert ctx.close_info()[0] > 0 and len(ou.close.pairs) > 0
+    sigma = np.random.default_rng(22).standard_normal(2 * ctx.N)
+    ref = ou.apply(sigma.reshape(-1, 2)).ravel()
+    assert _rel(ctx.apply(sigma, precision=bie.BIE_FP64), ref) < 1e-10
+    assert _rel(ctx.apply(sigma, precision=bie.BIE_DF64), ref) < 1e-10
+    assert _rel(ctx.apply(sigma, precision=bie.BIE_MIXED), ref) < 2e-5
+    ctx.close()
+
+
 def test_utilde_differs_from_3x3_operator(pair):
     """The two periodizers define the same periodic operator only up to the
     pressure constant: the applications themselves differ (by far more than
