@@ -161,3 +161,21 @@ def test_operator_with_the_paper_rule_equals_the_definition():
     assert len(ob.close.pairs) > 20
     yb = ob.apply(sigma)
     assert np.abs(yb - yf).max() < 1e-10 * np.abs(yf).max()
+
+
+def test_doubled_cell_operator_with_the_paper_rule():
+    """The same agreement for the paper's own periodizer (OperatorUtilde): a
+    small body 2e-3 from another, smooth density, fine rule against the
+    barycentric rule."""
+    from oracle import bie as obie
+    e1, e2, c = np.array([1.0, 0.0]), np.array([0.3, 1.0]), np.array([0.5, 0.5])
+    b0 = dict(a=0.12, b=0.06, xc=(c - 0.18 * e1 + 0.16 * e2).tolist(), theta=0.4, n=160)
+    up = np.array([-np.sin(0.4), np.cos(0.4)])
+    b1 = dict(a=0.05, b=0.03, xc=(np.array(b0["xc"]) + (0.06 + 0.03 + 2e-3) * up).tolist(), theta=0.4, n=128)
+    cell = dict(e1=e1.tolist(), e2=e2.tolist(), centre=c.tolist(), mu=1.0, gamma=1.0, bodies=[b0, b1])
+    susp = geometry.Suspension(cell["e1"], cell["e2"], cell["centre"], 1.0, 1.0, cell["bodies"])
+    sigma = _smooth_nodes(cell)
+    yf = obie.OperatorUtilde(susp, n_proxy=64, n_coll=16).apply(sigma)
+    ob = obie.OperatorUtilde(susp, n_proxy=64, n_coll=16, close_rule="barycentric")
+    assert len(ob.close.pairs) > 10
+    assert np.abs(ob.apply(sigma) - yf).max() < 1e-10 * np.abs(yf).max()
