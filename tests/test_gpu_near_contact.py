@@ -98,6 +98,33 @@ def test_barycentric_blocks_match_the_oracle(gap, n):
     ctx.close()
 
 
+def test_barycentric_blocks_in_a_batch_and_with_the_preconditioner():
+    """The barycentric blocks of a batch are those of each cell's own context
+    (FP64 applications to 1e-12, as for the fine rule: the near-sum splits
+    change the rounding order), and the contact-block preconditioner
+    assembled from them brings a near-contact solve to 1e-10."""
+    cells = [workloads.two_ellipses(2e-3, 256),
+             workloads.small_cell(n_bodies=4, nodes=128, seed=3, phi=0.3, gap=3e-3)]
+    for c in cells:  # one set of proxy and collocation counts for the batch and the single contexts
+        c["solver"] = dict(n_proxy=48, proxy_radius=1.5, n_coll=24, gmres_tol=1e-10)
+    ctx = bie.Context(cells, precision=bie.BIE_FP64, close_rule=1)
+    rng = np.random.default_rng(12)
+    sigma = rng.standard_normal(2 * ctx.N)
+    y = ctx.apply(sigma, precision=bie.BIE_FP64)
+    no = ctx.node_offsets
+    for k, c in enumerate(cells):
+        s = bie.Context(c, precision=bie.BIE_FP64, close_rule=1)
+        sl = slice(2 * no[k], 2 * no[k + 1])
+        assert _rel(y[sl], s.apply(sigma[sl], precision=bie.BIE_FP64)) < 1e-12
+        s.close()
+    ctx.close()
+    pc = bie.Context(workloads.two_ellipses(1e-5, 512), precision=bie.BIE_MIXED, close_rule=1, precond=1,
+                     gmres_max=1000, max_refine=40)
+    _, info = pc.solve()
+    assert info["rel_residual"] <= 1e-10
+    pc.close()
+
+
 def test_barycentric_and_fine_rules_solve_alike():
     """The two close-evaluation rules are two spectrally accurate
     discretisations of the same integral (they differ in the high modes of
